@@ -1,0 +1,102 @@
+"""Literal space-time interpolation of reconstruction-grid values onto points (oracle; test only).
+
+The reconstruction section interpolates the fields from the uniform horizontal grid with
+arbitrary vertical levels onto the CFD cell and face centres. The scheme is written here
+directly as tensor-product Lagrange polynomials (the "LAGRANGE3" reading):
+
+- x and y: uniform periodic nodes; the 4 nodes i0-1 .. i0+2 around the cell [i0, i0+1] that
+  holds the point;
+- z: arbitrary levels; the bracket [z_j, z_{j+1}] with z_j <= z (j <= nz-2), the 4 levels
+  j-1 .. j+2 shifted inside [0, nz-1] at the ends; points below z_0 or above z_{nz-1} are out of
+  range (NaN velocity and pressure);
+- time: Lagrange over all stored time levels (linear for two, cubic for four);
+- pressure from the interpolated u, v, w, dphi/dt by Bernoulli.
+"""
+import numpy as np
+
+from .modal import bernoulli
+
+
+def lagrange_basis(nodes, x):
+    """Lagrange basis polynomials of ``nodes`` (last axis) evaluated at ``x`` (broadcast)."""
+    nodes = np.asarray(nodes, np.float64)
+    x = np.asarray(x, np.float64)
+    k = nodes.shape[-1]
+    out = []
+    for a in range(k):
+        w = np.ones(np.broadcast_shapes(nodes.shape[:-1], x.shape))
+        for b in range(k):
+            if b != a:
+                w = w * (x - nodes[..., b]) / (nodes[..., a] - nodes[..., b])
+        out.append(w)
+    return np.stack(out, axis=-1)
+
+
+def _periodic_stencil(coord, length, count):
+    """Indices (4 per point) and Lagrange weights of the periodic uniform axis."""
+    s = np.asarray(coord, np.float64) * (count / length)
+    i0 = np.floor(s)
+    fx = s - i0
+    idx = (i0.astype(np.int64)[:, None] + np.arange(-1, 3)) % count
+    w = lagrange_basis(np.array([-1.0, 0.0, 1.0, 2.0]), fx)
+    return idx, w
+
+
+def level_stencil(z, z_levels):
+    """First level index j0 of the 4-level stencil, its weights, and the in-range mask."""
+    zl = np.asarray(z_levels, np.float64)
+    nz = len(zl)
+    z = np.asarray(z, np.float64)
+    inside = (z >= zl[0]) & (z <= zl[-1])
+    j = np.searchsorted(zl, z, side="right") - 1       # largest j with z_j <= z
+    j = np.clip(j, 0, nz - 2)
+    j0 = np.clip(j - 1, 0, nz - 4)
+    nodes = zl[j0[:, None] + np.arange(4)]
+    w = lagrange_basis(nodes, z)
+    return j0, w, inside
+
+
+def interp_points(nodes_tl, eta_tl, Lx, Ly, z_levels, t_levels, pts, t,
+                  rho=1000.0, g=9.81, p_mode="dyn"):
+    """Interpolate grid fields at time t onto points.
+
+    nodes_tl: [TL][nz][ny_r][nx_r][4] (u, v, w, phit); eta_tl: [TL][ny_r][nx_r]; pts [n][3].
+    Returns float64 eta, u, v, w, phit, p and the out-of-range mask.
+    """
+    nodes_tl = np.asarray(nodes_tl, np.float64)
+    eta_tl = np.asarray(eta_tl, np.float64)
+    TL, nz, nyr, nxr, _ = nodes_tl.shape
+    pts = np.asarray(pts, np.float64)
+    n = len(pts)
+    wt = lagrange_basis(np.asarray(t_levels, np.float64), np.float64(t))          # [TL]
+    ix, wx = _periodic_stencil(pts[:, 0], Lx, nxr)
+    if nyr > 1:
+        iy, wy = _periodic_stencil(pts[:, 1], Ly, nyr)
+    else:
+        iy, wy = np.zeros((n, 1), np.int64), np.ones((n, 1))
+    j0, wz, inside = level_stencil(pts[:, 2], z_levels)
+    iz = j0[:, None] + np.arange(4)
+
+    # grid blended in time first: sum_t w_t G_t (linear, so the order does not matter)
+    G = np.tensordot(wt, nodes_tl, axes=(0, 0))                                   # [nz][ny][nx][4]
+    E = np.tensordot(wt, eta_tl, axes=(0, 0))                                     # [ny][nx]
+    out4 = np.zeros((n, 4))
+    for a in range(4):
+        for b in range(iy.shape[1]):
+            for cidx in range(4):
+                vals = G[iz[:, a], iy[:, b], ix[:, cidx]]                          # [n][4]
+                out4 += (wz[:, a] * wy[:, b] * wx[:, cidx])[:, None] * vals
+    eta = np.zeros(n)
+    for b in range(iy.shape[1]):
+        for cidx in range(4):
+            eta += wy[:, b] * wx[:, cidx] * E[iy[:, b], ix[:, cidx]]
+    u, v, w, phit = (out4[:, q].copy() for q in range(4))
+    for arr in (u, v, w, phit):
+        arr[~inside] = np.nan
+    p = bernoulli(phit, u, v, w, pts[:, 2], rho, g, p_mode)
+    return {"eta": eta, "u": u, "v": v, "w": w, "phit": phit, "p": p, "out_of_range": ~inside}
+
+
+def time_weights(t_levels, t):
+    """Lagrange weights over the time levels at time t."""
+    return lagrange_basis(np.asarray(t_levels, np.float64), np.float64(t))

@@ -1,0 +1,74 @@
+"""Named synthetic workloads (sizes, seeds and recipes).
+
+Lengths are in metres with the peak (or regular) wavelength set to 1 m, g = 9.81 m/s^2,
+rho = 1000 kg/m^3. Seeds are 20051270 + workload number.
+
+- ``stokes2d``     2-D (x,z) deep-water third-order Stokes wave, ka = 0.1, wavelength L/16,
+                   256 modes, 33 levels (25 stretched on [-L/2, 0], 8 uniform on (0, L/10]),
+                   50,000 uniform points in [0,L] x [-L/2, L/10], two time levels at 0 and T/32.
+- ``jonswap3d``    3-D JONSWAP sea, Hs = 0.05 lambda_p, gamma = 3.3, cos^2 spreading, random
+                   phases, 512 x 256 modes on 32 x 16 lambda_p, 64 levels on [-lambda_p,
+                   0.075 lambda_p]; points = the cell centres and face centres of a graded hex
+                   O-grid (160 radial x 128 angular x 100 vertical cells) around a vertical
+                   cylinder of radius 0.039 lambda_p at the domain centre; two time levels.
+- ``*_small``      the same recipes shrunk so the oracle finishes in seconds.
+"""
+import numpy as np
+
+from . import seas, points as P, mesh as M
+
+SEED0 = 20051270
+
+
+def stokes2d(n_points=50_000, nx=256, seed=SEED0 + 1):
+    L = 16.0
+    sea = seas.stokes3_deep(nx, L, m1=16, ka=0.1)
+    z = P.levels_two_zone(-0.5 * L, 0.1 * L, n_below=25, n_above=8)
+    T = 2 * np.pi / sea["stokes"]["omega"]
+    pts = P.uniform_points(n_points, (0.0, 0.0, -0.5 * L), (L, 0.0, 0.1 * L), seed)
+    t_levels = np.array([0.0, T / 32])
+    return {
+        "name": "stokes2d", "sea": sea, "z_levels": z, "pad_n": 1, "points": pts,
+        "t_levels": t_levels, "t_query": float(t_levels[0] + 0.37 * (t_levels[1] - t_levels[0])),
+        "period": T,
+    }
+
+
+def stokes2d_small(n_points=3000, seed=SEED0 + 101):
+    return stokes2d(n_points=n_points, seed=seed)
+
+
+def jonswap3d(nx=512, ny=256, lx_over_lp=32.0, ly_over_lp=16.0, n_levels=64, pad_n=1,
+              mesh_dims=(160, 128, 100), seed=SEED0 + 2, n_tl=2):
+    lp = 1.0
+    Hs = 0.05 * lp
+    sea = seas.jonswap_sea(nx, ny, lx_over_lp * lp, ly_over_lp * lp, Hs, lp, gamma=3.3,
+                           heading=0.0, seed=seed)
+    z = P.levels_surface_clustered(-lp, 1.5 * Hs, n_levels, n_band=max(4, (3 * n_levels) // 8),
+                                   band=1.5 * Hs)
+    n_r, n_t, n_z = mesh_dims
+    n_band = max(2, int(round(0.6 * n_z)))
+    z_edges = M.clustered_z_edges(-0.9 * lp, 0.07 * lp, n_z, -1.5 * Hs, 0.07 * lp, n_band)
+    mesh = M.cylinder_ogrid((0.5 * lx_over_lp * lp, 0.5 * ly_over_lp * lp), 0.039 * lp,
+                            2.0 * lp, n_r, n_t, z_edges,
+                            radial_ratio=(1.02 ** (160.0 / n_r)))
+    Tp = 2 * np.pi / sea["jonswap"]["omega_p"]
+    dt = Tp / 16
+    t_levels = np.arange(n_tl) * dt
+    return {
+        "name": "jonswap3d", "sea": sea, "z_levels": z, "pad_n": pad_n, "mesh": mesh,
+        "t_levels": t_levels,
+        "t_query": float(t_levels[(n_tl - 1) // 2] + 0.37 * dt),
+        "period": Tp,
+    }
+
+
+def jonswap3d_small(pad_n=1, n_tl=2, seed=SEED0 + 102):
+    """64 x 32 modes on 8 x 4 lambda_p (8 points per lambda_p), 12 levels, 12 x 16 x 10 mesh."""
+    return jonswap3d(nx=64, ny=32, lx_over_lp=8.0, ly_over_lp=4.0, n_levels=12, pad_n=pad_n,
+                     mesh_dims=(12, 16, 10), seed=seed, n_tl=n_tl)
+
+
+def mesh_points(mesh):
+    """Cell centres followed by face centres, float32 [n][3], mesh order."""
+    return np.concatenate([mesh["cell_centres"], mesh["face_centres"]]).astype(np.float32)
