@@ -1,0 +1,398 @@
+#!/usr/bin/env python
+"""Throughput of the incident-wave reconstruction hot path on GB300.
+
+One step = the whole path over one batch: stage 1 (modes -> zero-padded grid at every level,
+for each of the time levels) and stage 2 (space-time interpolation of eta, u, v, w, p onto every
+cell and face centre of the mesh). Default workload: 3-D JONSWAP sea, 512 x 256 modes, 64
+levels, two time levels, 2.05 M cell centres + 6.18 M face centres of a graded O-grid around a
+vertical cylinder (``wavegen.configs.jonswap3d``); inputs are synthetic and seeded.
+
+Prints one JSON line (rank 0). ``--impl reference`` times the FP64 CPU oracle (direct modal sum)
+on the host cores instead, on bounded samples of the same workload.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FALLBACK_HBM_GBS = 6800.0
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", choices=["jonswap3d", "stokes2d"], default="jonswap3d")
+    ap.add_argument("--pad", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- workload
+
+def workload(name, pad):
+    from wavegen import configs
+    if name == "jonswap3d":
+        cfg = configs.jonswap3d(pad_n=pad)
+        pts = configs.mesh_points(cfg["mesh"])
+        desc = (f"jonswap3d: 512x256 modes, 64 levels, pad {pad}, 2 time levels, "
+                f"{len(cfg['mesh']['cell_centres'])} cell + {len(cfg['mesh']['face_centres'])} "
+                f"face centres (cylinder O-grid)")
+    else:
+        cfg = configs.stokes2d()
+        cfg["pad_n"] = pad
+        pts = cfg["points"]
+        desc = f"stokes2d: 256 modes (x,z), 33 levels, pad {pad}, 2 time levels, {len(pts)} points"
+    return cfg, np.ascontiguousarray(pts, np.float32), desc
+
+
+def touched_grid_bytes(cfg, pts, nxr, nyr, n_tl):
+    """Unique grid bytes the gather reads: the union of every point's 4x4x4 node stencil (float4
+    per node and time level) plus its 4x4 eta columns, counted with a bitmap."""
+    from wavegen import configs  # noqa: F401  (workload helpers only)
+    sea, z = cfg["sea"], np.asarray(cfg["z_levels"], np.float64)
+    nz = len(z)
+    mark = np.zeros((nz, nyr, nxr), bool)
+    col = np.zeros((nyr, nxr), bool)
+    for s in range(0, len(pts), 1 << 20):
+        p = pts[s:s + (1 << 20)].astype(np.float64)
+        ix = np.floor(p[:, 0] * nxr / sea["Lx"]).astype(np.int64)
+        iy = np.floor(p[:, 1] * nyr / sea["Ly"]).astype(np.int64) if nyr > 1 else np.zeros(len(p), np.int64)
+        j = np.clip(np.searchsorted(z, p[:, 2], side="right") - 1, 0, nz - 2)
+        j0 = np.clip(j - 1, 0, nz - 4)
+        dys = range(-1, 3) if nyr > 1 else (0,)
+        for dx in range(-1, 3):
+            xi = (ix + dx) % nxr
+            for dy in dys:
+                yi = (iy + dy) % nyr
+                col[yi, xi] = True
+                for dz in range(4):
+                    mark[j0 + dz, yi, xi] = True
+    return int(mark.sum()) * 16 * n_tl + int(col.sum()) * 4 * n_tl
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+
+def cpu_oracle_sample(cfg, pts, seconds, seed=1):
+    """Direct FP64 modal sum (the oracle) at a seeded sample of the workload's points, sized to
+    take about ``seconds`` on one host core. Returns (points/s, n, values, idx)."""
+    from oracle import modal
+    sea = modal.propagate(cfg["sea"], cfg["t_query"])
+    rng = np.random.default_rng(seed)
+    probe = rng.choice(len(pts), 16, replace=False)
+    t0 = time.perf_counter()
+    modal.fields_at_points(sea, pts[probe].astype(np.float64))
+    per = (time.perf_counter() - t0) / 16
+    n = int(min(max(32, seconds / max(per, 1e-9)), 50_000))
+    idx = rng.choice(len(pts), n, replace=False)
+    t0 = time.perf_counter()
+    vals = modal.fields_at_points(sea, pts[idx].astype(np.float64))
+    dt = time.perf_counter() - t0
+    return n / dt, n, vals, idx
+
+
+def n_modes(sea):
+    return int(np.count_nonzero((sea["A_eta"] != 0) | (sea["A_phi"] != 0) | (sea["A_phit"] != 0)))
+
+
+# ----------------------------------------------------------------------------- arms
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    cfg, pts, desc = workload(args.config, args.pad)
+    nm = n_modes(cfg["sea"])
+    budget = 150.0 / max(1, args.steps + args.warmup)
+    per_step = []
+    n_total = 0
+    for s in range(args.warmup + args.steps):
+        rate, n, _, _ = cpu_oracle_sample(cfg, pts, min(budget, 20.0), seed=100 + s)
+        if s >= args.warmup:
+            per_step.append(rate)
+            n_total += n
+    value = float(np.mean(per_step))
+    line = {
+        "impl": "reference", "metric": "wave-field points/sec at stated err vs FP64 oracle; % of HBM roofline",
+        "value": value, "unit": "points/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": len(pts) / value * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": desc},
+        "cpu_baseline": {"value": value, "unit": "points/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{n_total} seeded points of the workload over {args.steps} "
+                                   f"steps; direct FP64 modal sum over {nm} modes; "
+                                   f"ms_per_step extrapolated to all {len(pts)} points"},
+        "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("interp.cu", "grid_ifft.cu", "fft.cuh"):
+        with open(os.path.join(ROOT, "paper_2005_12716_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+# DRAM bytes per launch from ncu captures (dram__bytes_read.sum + dram__bytes_write.sum) with
+# the kernel-source hash they were taken at; a changed kernel invalidates them.
+NCU_TRAFFIC = {}
+
+
+def run_ours(args, rank, world):
+    import torch
+    from paper_2005_12716_gb300 import _swense as S
+    from paper_2005_12716_gb300 import api
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    cfg, pts_np, desc = workload(args.config, args.pad)
+    sea, z, tl, tq, pad = cfg["sea"], cfg["z_levels"], cfg["t_levels"], cfg["t_query"], cfg["pad_n"]
+    npts = len(pts_np)
+    modes = api.upload_modes(sea, dev)
+    grid = api.alloc_grid(modes, z, pad, tl, dev)
+    pts = torch.from_numpy(pts_np).to(dev)
+    outs = {k: torch.empty(npts, dtype=torch.float32, device=dev) for k in ("eta", "u", "v", "w", "p")}
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        api.fields_on_grid(modes, z, pad, tl, out=grid)
+        api.interp(grid, tq, pts, out=outs)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    launches0 = S.swense_launches()
+    t_wall = time.perf_counter()
+    for s in range(args.steps):
+        flush.zero_()                     # L2 flush between timed steps (outside the events)
+        ev[s][0].record(stream)
+        api.fields_on_grid(modes, z, pad, tl, out=grid)
+        ev[s][1].record(stream)
+        api.interp(grid, tq, pts, out=outs)
+        ev[s][2].record(stream)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    launches = S.swense_launches() - launches0
+    clk = clocks.stop()
+    k1 = np.array([ev[s][0].elapsed_time(ev[s][1]) for s in range(args.steps)])
+    k2 = np.array([ev[s][1].elapsed_time(ev[s][2]) for s in range(args.steps)])
+    total_ms = float((k1 + k2).sum())
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+        torch.distributed.barrier()
+    ms_per_step = total_ms / args.steps
+    value = world * npts / (ms_per_step * 1e-3)
+
+    # ---- algorithmic bytes and roofline
+    nxr, nyr = api.grid_dims(modes, pad)
+    nz, n_tl = len(z), len(tl)
+    nslot = sea["A_eta"].size
+    k1_bytes = n_tl * (nz * nyr * nxr * 16 + nyr * nxr * 4) + nslot * (3 * 8 + 8)
+    touched = touched_grid_bytes(cfg, pts_np, nxr, nyr, n_tl)
+    k2_bytes = touched + npts * (12 + 20)
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(peaks_path):
+        with open(peaks_path) as fh:
+            hbm = float(json.load(fh)["hbm_gbs"])
+        peak_src = "measured"
+    else:
+        hbm, peak_src = FALLBACK_HBM_GBS, "fallback"
+    k1_ms, k2_ms = float(k1.mean()), float(k2.mean())
+    src_hash = kernel_source_hash()
+    stages = {
+        "grid_ifft": {"ms": k1_ms, "algorithmic_bytes": k1_bytes,
+                      "achieved_gbs": k1_bytes / (k1_ms * 1e-3) / 1e9,
+                      "frac_hbm": k1_bytes / (k1_ms * 1e-3) / 1e9 / hbm,
+                      "launches_per_step": None},
+        "interp": {"ms": k2_ms, "algorithmic_bytes": k2_bytes, "touched_grid_bytes": touched,
+                   "achieved_gbs": k2_bytes / (k2_ms * 1e-3) / 1e9,
+                   "frac_hbm": k2_bytes / (k2_ms * 1e-3) / 1e9 / hbm, "launches_per_step": 1},
+    }
+    stages["grid_ifft"]["launches_per_step"] = int(launches // args.steps) - 1
+    dom = "interp" if k2_ms >= k1_ms else "grid_ifft"
+    kname = "k_interp" if dom == "interp" else "grid_ifft (k_pass_a + k_pass_b)"
+    tr = NCU_TRAFFIC.get(kname)
+    traffic = tr["bytes"] if tr and tr.get("hash") == src_hash and tr.get("workload") == desc else None
+    roofline = {"bound": "hbm", "kernel": kname, "achieved": stages[dom]["achieved_gbs"],
+                "peak": hbm, "unit": "GB/s", "frac": stages[dom]["frac_hbm"], "traffic": traffic,
+                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
+                else "fallback 6.8 TB/s"}
+
+    line = {
+        "metric": "wave-field points/sec at stated err vs FP64 oracle; % of HBM roofline",
+        "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": desc, "modes": [sea["nx"], sea["ny"]], "levels": nz, "pad_n": pad,
+                   "n_tl": n_tl, "points": npts, "fields": 5,
+                   "l2": "flushed between timed steps (256 MB write outside the events)",
+                   "parallelism": f"replicas x{world}"},
+        "points_fields_per_s": value * 5,
+        "roofline": roofline,
+        "stages": stages,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "wall_s_timed": t_wall,
+        "kernel_hash": src_hash,
+    }
+
+    # ---- end to end through the C ABI with host buffers
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        h_modes = [pin(modes.A_eta.cpu().numpy()), pin(modes.A_phi.cpu().numpy()),
+                   pin(modes.A_phit.cpu().numpy()), pin(modes.omega.cpu().numpy())]
+        h_pts = pin(pts_np)
+        h_out = {k: torch.empty(npts, dtype=torch.float32).pin_memory() for k in outs}
+        d_bufs = [modes.A_eta, modes.A_phi, modes.A_phit, modes.omega]
+        h2d = sum(t.numel() * t.element_size() for t in h_modes) + h_pts.numel() * 4
+        d2h = sum(t.numel() * 4 for t in h_out.values())
+
+        def e2e_step():
+            for d, h in zip(d_bufs, h_modes):
+                d.copy_(h, non_blocking=True)
+            pts.copy_(h_pts, non_blocking=True)
+            api.fields_on_grid(modes, z, pad, tl, out=grid)
+            api.interp(grid, tq, pts, out=outs)
+            for k in outs:
+                h_out[k].copy_(outs[k], non_blocking=True)
+
+        for _ in range(max(1, args.warmup)):
+            e2e_step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ks = max(1, args.steps)
+        e0.record(stream)
+        for _ in range(ks):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e_ms = e0.elapsed_time(e1) / ks
+        if world > 1:
+            t = torch.tensor([e_ms], device=dev, dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e_ms = float(t.item())
+        line["e2e"] = {"value": world * npts / (e_ms * 1e-3), "unit": "points/s",
+                       "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                       "ms_per_step": e_ms}
+
+    # ---- CPU baseline: the FP64 oracle on a bounded sample, rank 0 at N = 1 only
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, n, vals, idx = cpu_oracle_sample(cfg, pts_np, args.cpu_seconds)
+        line["cpu_baseline"] = {
+            "value": rate, "unit": "points/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n} seeded points of the {npts}; direct FP64 modal sum over "
+                      f"{n_modes(sea)} modes (numpy, one thread)"}
+        # method error of the reconstruction at those points vs the exact modal sum
+        sel = torch.from_numpy(idx).to(dev)
+        err = {}
+        for k in ("eta", "u", "v", "w", "p"):
+            got = outs[k][sel].cpu().numpy().astype(np.float64)
+            ref = vals[k]
+            err[k] = float(np.max(np.abs(got - ref)) / max(np.max(np.abs(ref)), 1e-300))
+        line["method_error_vs_exact"] = {"norm": "max|gpu-exact|/max|exact| over the sample",
+                                         "fields": err}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import torch
+    if world > 1:
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        torch.distributed.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world)
+    finally:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,185 @@
+/*
+ * swense.h — C ABI of the GB300 (sm_103a) incident-wave reconstruction library.
+ *
+ * The library evaluates the incident-wave fields of the two-phase SWENSE method (free-surface
+ * elevation eta, velocity u, v, w, and the dynamic pressure or dphi/dt) from spectral (HOS)
+ * modal amplitudes onto arbitrary CFD points, in the two stages of the paper's reconstruction
+ * section ("Reconstruction of incident wave information on the CFD mesh"):
+ *   1. inverse transforms of the modes onto a uniform horizontal grid at arbitrary vertical
+ *      levels, refined by zero-padding the spectrum (subsection "Improvement of the
+ *      interpolation accuracy");
+ *   2. space-time interpolation of the grid fields onto cell and face centres.
+ * It also computes the finite-volume divergence used as the reconstruction-error measure
+ * (subsection "Reconstruction error: velocity divergence").
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Pointers documented "device" must be CUDA device (or managed) memory of the current device;
+ *   "host" pointers are read before the call returns. The caller owns every buffer it passes.
+ *   The library keeps a per-device scratch workspace (allocated with cudaMalloc on first use,
+ *   grown on demand, freed by swense_release); entry points that may grow it must not be
+ *   called for the first time inside a CUDA stream capture.
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream). All device work
+ *   is enqueued on it; calls return before it runs unless documented otherwise.
+ * - Calls that overlap on the GPU (different streams, no ordering) race on the library's scratch
+ *   workspace: order them on one stream.
+ * - Return value: SWENSE_OK (0) or a negative SWENSE_ERR_* code; swense_last_error() gives a
+ *   one-line description for the calling thread. Invalid arguments launch nothing.
+ * - Modal amplitudes use the one-sided half-spectrum layout: complex64 stored as interleaved
+ *   (re, im) float pairs, index [row][m] with m = 0..nx/2 (nx/2+1 columns) and rows in FFT order
+ *   (row r holds n = r for r < ny/2 and n = r - ny otherwise). Mode (m, n) has wavenumber
+ *   k = (2 pi m / Lx, 2 pi n / Ly). A real field is f(x) = sum_{m >= 0} c_m Re(sum_n F_{m,n}
+ *   e^{i k.x}) with c_0 = 1 and c_m = 2 otherwise. The Nyquist column m = nx/2 and row r = ny/2
+ *   are ignored. For a 2-D (x, z) problem ny = 1 and y is ignored everywhere.
+ * - Fields follow the paper's spectral decomposition (Eqs. whatIsSpectralMethod1 and
+ *   whatIsSpectralMethod) and the velocity sums of its "analytical evaluation":
+ *     eta  = sum A^eta e^{ik.x}
+ *     u    = sum i kx A^phi F(z) e^{ik.x},   v = sum i ky A^phi F(z) e^{ik.x}
+ *     w    = sum |k| A^phi S(z) e^{ik.x},    dphi/dt = sum A^phit F(z) e^{ik.x}
+ *   with F = cosh(|k|(z+h))/cosh(|k|h), S = sinh(|k|(z+h))/cosh(|k|h), or F = S = e^{|k|z} in
+ *   deep water, evaluated unchanged above z = 0 (section "Extension of incident wave solution
+ *   in the air"). Pressure (Bernoulli): p_dyn = -rho (dphi/dt + |u|^2/2).
+ */
+#ifndef SWENSE_H
+#define SWENSE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SWENSE_VERSION 100
+#define SWENSE_MAX_LEVELS 256   /* vertical levels per grid */
+#define SWENSE_MAX_FFT 8192     /* refined nodes per horizontal axis (pad_n * nx, pad_n * ny) */
+#define SWENSE_MAX_TL 4         /* time levels per interpolation */
+
+enum swense_status {
+  SWENSE_OK = 0,
+  SWENSE_ERR_ARG = -1,          /* NULL pointer, bad enum, non-finite or inconsistent value */
+  SWENSE_ERR_SIZE = -2,         /* size not a power of two or above a SWENSE_MAX_* limit */
+  SWENSE_ERR_LEVELS = -3,       /* vertical levels not strictly increasing / too few / too many */
+  SWENSE_ERR_OOM = -4,          /* scratch workspace allocation failed */
+  SWENSE_ERR_CUDA = -5,         /* a CUDA runtime call failed (see swense_last_error) */
+  SWENSE_ERR_TIMEOUT = -6,      /* a bounded device-side wait gave up */
+  SWENSE_ERR_UNSUPPORTED = -7   /* valid request this build does not implement */
+};
+
+enum swense_p_mode {
+  SWENSE_P_DYN = 0,    /* p = -rho (dphi/dt + |u|^2 / 2) */
+  SWENSE_P_PHIT = 1,   /* p = dphi/dt */
+  SWENSE_P_TOTAL = 2   /* p = -rho (dphi/dt + |u|^2 / 2) - rho g z */
+};
+
+/* Spectral modal amplitudes of one sea state (paper: A^eta_i, A^phi_i of Eqs.
+ * whatIsSpectralMethod1 / whatIsSpectralMethod; A^phit their time derivative's modes). */
+typedef struct swense_modes {
+  int32_t nx, ny;        /* mode counts: nx power of two in [4, SWENSE_MAX_FFT]; ny = 1 (2-D) or
+                            a power of two in [4, SWENSE_MAX_FFT] */
+  double Lx, Ly;         /* periodic domain lengths [m]; Ly ignored when ny = 1 */
+  double depth;          /* water depth h > 0 [m]; <= 0 means deep water */
+  int32_t n_snap;        /* snapshots stored in A_* (see swense_fields_on_grid) */
+  const float* A_eta;    /* device complex64 [n_snap][ny][nx/2+1] (interleaved re, im) */
+  const float* A_phi;    /* device complex64 [n_snap][ny][nx/2+1]: volume potential at z = 0 */
+  const float* A_phit;   /* device complex64 [n_snap][ny][nx/2+1]: dphi/dt at z = 0 */
+  const double* omega;   /* device [ny][nx/2+1] angular frequency of each slot, or NULL */
+  double t_ref;          /* time at which the single snapshot holds (used with omega only) */
+} swense_modes;
+
+/* The reconstruction ("HOS") grid: nx_r = pad_n*nx by ny_r = pad_n*ny (ny_r = 1 in 2-D)
+ * uniform nodes x_i = i Lx/nx_r, y_j = j Ly/ny_r, at nz arbitrary levels. */
+typedef struct swense_grid_desc {
+  int32_t pad_n;           /* zero-padding factor: 1, 2, 4 or 8 */
+  int32_t nz;              /* number of levels, 4 <= nz <= SWENSE_MAX_LEVELS */
+  const float* z_levels;   /* host [nz], strictly increasing */
+} swense_grid_desc;
+
+/*
+ * swense_fields_on_grid — stage 1: modes -> grid (paper: reconstruction section, step "IFFT",
+ * one inverse transform per vertical level, and the zero-padding refinement of subsection
+ * "Improvement of the interpolation accuracy"; levels above z = 0 per the extension into air).
+ *
+ * Time levels: if modes->omega is NULL, modes->n_snap must equal n_tl and time level l uses
+ * snapshot l (t may be NULL). Otherwise modes->n_snap must be 1 and time level l uses
+ * A * exp(-i omega (t[l] - t_ref)), the phase reduced in FP64 (t: host [n_tl]).
+ *
+ * Outputs (device, caller-allocated, 16-byte aligned):
+ *   nodes  float [n_tl][nz][ny_r][nx_r][4] = (u, v, w, dphi/dt) per node
+ *   eta    float [n_tl][ny_r][nx_r]
+ * Arithmetic: FP32 transforms, FP32 depth factors with a compensated |k| z product.
+ * Uses the scratch workspace (4 * ny_r * nx/2 complex64 per level of a level chunk) when
+ * ny > 1. Errors: ARG, SIZE, LEVELS, OOM, CUDA.
+ */
+int swense_fields_on_grid(const swense_modes* modes, int32_t n_tl, const double* t,
+                          const swense_grid_desc* desc, float* nodes, float* eta, void* stream);
+
+/* Grid fields at n_tl time levels as written by swense_fields_on_grid. */
+typedef struct swense_grid {
+  const float* nodes;       /* device float [n_tl][nz][ny_r][nx_r][4] */
+  const float* eta;         /* device float [n_tl][ny_r][nx_r] */
+  int32_t nx_r, ny_r, nz;   /* nx_r, ny_r powers of two <= SWENSE_MAX_FFT (ny_r = 1 in 2-D) */
+  int32_t n_tl;             /* 1..SWENSE_MAX_TL */
+  double Lx, Ly;            /* domain lengths (Ly ignored when ny_r = 1) */
+  const float* z_levels;    /* host [nz], strictly increasing */
+  const double* t_levels;   /* host [n_tl], strictly increasing */
+} swense_grid;
+
+/*
+ * swense_interp — stage 2: grid -> points (paper: reconstruction section, step
+ * "Interpolation"). Tensor-product 4-point Lagrange interpolation: periodic uniform nodes
+ * i0-1..i0+2 in x and y around the point's cell; in z the 4 levels around the bracketing
+ * interval [z_j, z_j+1], shifted inside [0, nz-1] at the ends; Lagrange over the n_tl time
+ * levels at time t (linear for 2, cubic for 4; the paper states no time scheme).
+ *
+ * pts: device float [np][3] (x, y, z) in the grid's frame; x and y wrap periodically.
+ * Outputs: device float [np] each, any may be NULL. Points with z outside
+ * [z_levels[0], z_levels[nz-1]] get NaN u, v, w, p (eta stays valid) and are counted.
+ * n_out_of_range: host pointer or NULL; when non-NULL the call synchronises the stream and
+ * stores the count. p_mode: enum swense_p_mode; rho, g used by P_DYN / P_TOTAL.
+ * Errors: ARG, SIZE, LEVELS, CUDA.
+ */
+int swense_interp(const swense_grid* grid, double t, const float* pts, int64_t np,
+                  float* eta, float* u, float* v, float* w, float* p,
+                  int32_t p_mode, double rho, double g, int64_t* n_out_of_range,
+                  void* stream);
+
+/*
+ * swense_fv_divergence — the finite-volume divergence of the reconstruction-error subsection:
+ * div_c = sum_f s_cf (u_f . A_f) / V_c with the face-centre velocity standing for the face
+ * average (error source 1 of that subsection).
+ *   u_face, v_face, w_face : device float [n_faces]  velocity at face centres
+ *   area                   : device float [n_faces][3] face area vectors
+ *   cell_faces             : device int32 [n_cells][6] signed face references, +(f+1) when
+ *                            A_f points out of the cell, -(f+1) when it points in
+ *   cell_volume            : device float [n_cells]
+ *   div                    : device float [n_cells] output
+ * Face references are not range-checked on the device; the caller guarantees
+ * 1 <= |ref| <= n_faces. Errors: ARG, CUDA.
+ */
+int swense_fv_divergence(const float* u_face, const float* v_face, const float* w_face,
+                         int64_t n_faces, const float* area, const int32_t* cell_faces,
+                         const float* cell_volume, int64_t n_cells, float* div, void* stream);
+
+/* Bytes of scratch workspace currently held on the current device. */
+int64_t swense_workspace_bytes(void);
+
+/* Free the scratch workspace of the current device (synchronises the device). */
+int swense_release(void);
+
+/* One-line description of the calling thread's last error ("" if none). */
+const char* swense_last_error(void);
+
+/* Static name of a status code. */
+const char* swense_strerror(int status);
+
+/* Number of kernels this process has launched through the library (all devices). */
+int64_t swense_launches(void);
+
+/* SWENSE_VERSION of the built library. */
+int swense_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SWENSE_H */

@@ -1,0 +1,190 @@
+"""ctypes binding of ``libswense.so`` (argument marshalling only).
+
+Every ``swense_*`` name here calls the C entry point of the same name in ``include/swense.h``.
+The functions accept torch CUDA tensors (their ``data_ptr()`` is passed), host numpy arrays for
+the host-side level lists, and raise ``SwenseError`` on a non-zero status. No computation of
+the method happens in Python; if the library is missing, ``load()`` raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_LIB = None
+
+
+class SwenseError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+class swense_modes(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+        ("Lx", ctypes.c_double), ("Ly", ctypes.c_double), ("depth", ctypes.c_double),
+        ("n_snap", ctypes.c_int32),
+        ("A_eta", ctypes.c_void_p), ("A_phi", ctypes.c_void_p), ("A_phit", ctypes.c_void_p),
+        ("omega", ctypes.c_void_p), ("t_ref", ctypes.c_double),
+    ]
+
+
+class swense_grid_desc(ctypes.Structure):
+    _fields_ = [("pad_n", ctypes.c_int32), ("nz", ctypes.c_int32), ("z_levels", ctypes.c_void_p)]
+
+
+class swense_grid(ctypes.Structure):
+    _fields_ = [
+        ("nodes", ctypes.c_void_p), ("eta", ctypes.c_void_p),
+        ("nx_r", ctypes.c_int32), ("ny_r", ctypes.c_int32), ("nz", ctypes.c_int32),
+        ("n_tl", ctypes.c_int32),
+        ("Lx", ctypes.c_double), ("Ly", ctypes.c_double),
+        ("z_levels", ctypes.c_void_p), ("t_levels", ctypes.c_void_p),
+    ]
+
+
+P_DYN, P_PHIT, P_TOTAL = 0, 1, 2
+P_MODES = {"dyn": P_DYN, "phit": P_PHIT, "total": P_TOTAL}
+MAX_LEVELS, MAX_FFT, MAX_TL = 256, 8192, 4
+
+# C symbol -> (restype, argtypes)
+_SIGS = {
+    "swense_fields_on_grid": (ctypes.c_int, [ctypes.POINTER(swense_modes), ctypes.c_int32,
+                                             ctypes.c_void_p, ctypes.POINTER(swense_grid_desc),
+                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "swense_interp": (ctypes.c_int, [ctypes.POINTER(swense_grid), ctypes.c_double, ctypes.c_void_p,
+                                     ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_void_p, ctypes.c_void_p]),
+    "swense_fv_divergence": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                            ctypes.c_void_p]),
+    "swense_workspace_bytes": (ctypes.c_int64, []),
+    "swense_release": (ctypes.c_int, []),
+    "swense_last_error": (ctypes.c_char_p, []),
+    "swense_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "swense_version": (ctypes.c_int, []),
+    "swense_launches": (ctypes.c_int64, []),
+}
+
+
+def lib_path():
+    return _build.LIB
+
+
+def load(build_if_missing=False):
+    """Load (and optionally build) the library; raises if it cannot be loaded."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = lib_path()
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library {path} is missing; run __graft_entry__.build() first")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _check(status):
+    if status != 0:
+        lib = load()
+        raise SwenseError(status, lib.swense_last_error().decode())
+
+
+def _ptr(t):
+    if t is None or isinstance(t, int):
+        return t
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def make_modes(nx, ny, Lx, Ly, depth, A_eta, A_phi, A_phit, n_snap=1, omega=None, t_ref=0.0):
+    """swense_modes from device tensors (complex64 viewed as float pairs, float64 omega)."""
+    m = swense_modes(nx, ny, Lx, Ly, depth, n_snap, _ptr(A_eta), _ptr(A_phi), _ptr(A_phit),
+                     _ptr(omega), t_ref)
+    m._keep = (A_eta, A_phi, A_phit, omega)
+    return m
+
+
+def make_grid_desc(pad_n, z_levels):
+    z = np.ascontiguousarray(z_levels, np.float32)
+    d = swense_grid_desc(pad_n, len(z), z.ctypes.data)
+    d._keep = z
+    return d
+
+
+def make_grid(nodes, eta, nx_r, ny_r, nz, n_tl, Lx, Ly, z_levels, t_levels):
+    z = np.ascontiguousarray(z_levels, np.float32)
+    t = np.ascontiguousarray(t_levels, np.float64)
+    g = swense_grid(_ptr(nodes), _ptr(eta), nx_r, ny_r, nz, n_tl, Lx, Ly, z.ctypes.data,
+                    t.ctypes.data)
+    g._keep = (nodes, eta, z, t)
+    return g
+
+
+def swense_fields_on_grid(modes, n_tl, t, desc, nodes, eta, stream=None):
+    lib = load()
+    tt = None if t is None else np.ascontiguousarray(t, np.float64)
+    _check(lib.swense_fields_on_grid(ctypes.byref(modes), n_tl,
+                                     None if tt is None else tt.ctypes.data,
+                                     ctypes.byref(desc), _ptr(nodes), _ptr(eta), _stream(stream)))
+
+
+def swense_interp(grid, t, pts, np_, eta=None, u=None, v=None, w=None, p=None, p_mode=P_DYN,
+                  rho=1000.0, g=9.81, count_out_of_range=False, stream=None):
+    lib = load()
+    cnt = ctypes.c_int64(-1)
+    _check(lib.swense_interp(ctypes.byref(grid), t, _ptr(pts), np_, _ptr(eta), _ptr(u), _ptr(v),
+                             _ptr(w), _ptr(p), p_mode, rho, g,
+                             ctypes.byref(cnt) if count_out_of_range else None, _stream(stream)))
+    return cnt.value if count_out_of_range else None
+
+
+def swense_fv_divergence(u_face, v_face, w_face, n_faces, area, cell_faces, cell_volume, n_cells,
+                         div, stream=None):
+    lib = load()
+    _check(lib.swense_fv_divergence(_ptr(u_face), _ptr(v_face), _ptr(w_face), n_faces, _ptr(area),
+                                    _ptr(cell_faces), _ptr(cell_volume), n_cells, _ptr(div),
+                                    _stream(stream)))
+
+
+def swense_workspace_bytes():
+    return load().swense_workspace_bytes()
+
+
+def swense_release():
+    _check(load().swense_release())
+
+
+def swense_strerror(status):
+    return load().swense_strerror(status).decode()
+
+
+def swense_version():
+    return load().swense_version()
+
+
+def swense_launches():
+    return load().swense_launches()

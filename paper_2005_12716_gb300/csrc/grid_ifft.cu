@@ -1,0 +1,425 @@
+// Stage 1 of the reconstruction: modal amplitudes -> (zero-padded) grid at arbitrary levels.
+//
+// Paper: reconstruction section, step "IFFT" (one inverse transform per vertical level onto
+// uniformly spaced nodes), the zero-padding refinement (spectrum extended n times with zero
+// modes -> n times finer grid) and the extension of the solution above z = 0.
+//
+// Two passes per level chunk (3-D, ny > 1):
+//   pass A  per (level, block of kx columns): form the four modal fields
+//             U = i kx A^phi F, V = i ky A^phi F, W = |k| A^phi S, T = A^phit F
+//           (depth factors F, S at the level), zero-pad along ky and inverse-transform along y;
+//           writes G[level][field][y][m] (complex, one-sided in m) to the scratch workspace.
+//   pass B  per (level, block of y rows): pack the two real-field pairs into one complex
+//           spectrum each, Z1 = U + iV and Z2 = W + iT (Hermitian extension over m, zero-padded
+//           to nx_r), inverse-transform along x and store float4 (u, v, w, dphi/dt) per node.
+// Level chunks are sized so G stays L2-resident between the passes. eta is one extra transform
+// per time level (pass A on A^eta; pass B packs two grid rows per complex transform).
+// 2-D (ny == 1): pass B alone, reading the modes directly.
+#include <algorithm>
+#include <cmath>
+#include <string>
+
+#include "fft.cuh"
+#include "internal.cuh"
+
+namespace swense {
+namespace {
+
+struct Levels {
+  float z[SWENSE_MAX_LEVELS];
+};
+
+struct PassAArgs {
+  const float2* A_phi;   // [ny][nxh1] of this time level
+  const float2* A_phit;
+  const float2* A_eta;
+  float2* G;             // [nlev][4][Nyr][Mh] (levels) or [Nyr][Mh] (eta)
+  const float2* tw;
+  int ny, nxh1, Mh, Nyr, log2Nyr;
+  int cb, fp;            // kx columns per CTA, fields per shared-memory pass
+  int lev0;              // first level of the chunk
+  int eta_mode;
+  float kxs, kys, depth;
+};
+
+__global__ void __launch_bounds__(256) k_pass_a(PassAArgs a, Levels L) {
+  extern __shared__ float2 sm[];
+  const int c0 = blockIdx.x * a.cb;
+  const int slot = blockIdx.y;
+  const int ncol = min(a.cb, a.Mh - c0);
+  const float z = a.eta_mode ? 0.f : L.z[a.lev0 + slot];
+  const int nfield = a.eta_mode ? 1 : 4;
+  const int nyh = a.ny >> 1;
+  for (int f0 = 0; f0 < nfield; f0 += a.fp) {
+    const int nf = min(a.fp, nfield - f0);
+    const int narr = nf * a.cb;
+    for (int i = threadIdx.x; i < narr * a.Nyr; i += blockDim.x) sm[i] = make_float2(0.f, 0.f);
+    __syncthreads();
+    for (int i = threadIdx.x; i < a.ny * a.cb; i += blockDim.x) {
+      const int c = i % a.cb, r = i / a.cb;
+      if (c >= ncol || r == nyh) continue;               // Nyquist row ignored
+      const int m = c0 + c;
+      const int n = r < nyh ? r : r - a.ny;
+      const int pos = n >= 0 ? n : a.Nyr + n;            // zero-padding between +n and -n
+      const unsigned br = bitrev(unsigned(pos), a.log2Nyr);
+      const size_t gi = size_t(r) * a.nxh1 + m;
+      if (a.eta_mode) {
+        sm[c * a.Nyr + br] = __ldg(&a.A_eta[gi]);
+        continue;
+      }
+      const float2 Ap = __ldg(&a.A_phi[gi]);
+      const float2 At = __ldg(&a.A_phit[gi]);
+      const float kx = float(m) * a.kxs, ky = float(n) * a.kys;
+      const float k = sqrtf(kx * kx + ky * ky);
+      float F, S;
+      depth_factors(k, z, a.depth, F, S);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (q < f0 || q >= f0 + nf) continue;
+        float2 v;
+        if (q == 0) v = make_float2(-kx * F * Ap.y, kx * F * Ap.x);        // i kx F A^phi
+        else if (q == 1) v = make_float2(-ky * F * Ap.y, ky * F * Ap.x);   // i ky F A^phi
+        else if (q == 2) v = make_float2(k * S * Ap.x, k * S * Ap.y);      // |k| S A^phi
+        else v = make_float2(F * At.x, F * At.y);                          // F A^phit
+        sm[((q - f0) * a.cb + c) * a.Nyr + br] = v;
+      }
+    }
+    __syncthreads();
+    fft_inv_inplace(sm, a.Nyr, a.log2Nyr, narr, a.tw);
+    for (int i = threadIdx.x; i < nf * a.Nyr * a.cb; i += blockDim.x) {
+      const int c = i % a.cb;
+      const int rest = i / a.cb;
+      const int y = rest % a.Nyr, q = rest / a.Nyr;
+      if (c >= ncol) continue;
+      const size_t go = ((size_t(slot) * nfield + f0 + q) * a.Nyr + y) * a.Mh + c0 + c;
+      a.G[go] = sm[(q * a.cb + c) * a.Nyr + y];
+    }
+    __syncthreads();
+  }
+}
+
+enum { B_LEVEL_G = 0, B_LEVEL_DIRECT = 1, B_ETA_G = 2, B_ETA_DIRECT = 3 };
+
+struct PassBArgs {
+  const float2* G;        // pass-A output (levels or eta)
+  const float2* A_phi;    // direct mode (ny == 1): modes of this time level
+  const float2* A_phit;
+  const float2* A_eta;
+  float4* nodes;          // [nz][Nyr][Nxr] of this time level
+  float* eta;             // [Nyr][Nxr] of this time level
+  const float2* tw;
+  int Mh, Nxr, log2Nxr, Nyr;
+  int rb;                 // rows (level modes) or row pairs (eta modes) per CTA
+  int lev0;
+  int mode;
+  float kxs, depth;
+};
+
+// Hermitian packing of two one-sided spectra P, Q (coefficients of real fields p, q) into one
+// full complex spectrum Z = P + iQ whose inverse transform is p + i q.
+__device__ __forceinline__ void pack_pair(float2* Z, int m, int Nxr, int log2Nxr, float2 P, float2 Q) {
+  if (m == 0) {
+    Z[0] = make_float2(P.x, Q.x);                        // bitrev(0) == 0; real parts only
+  } else {
+    Z[bitrev(unsigned(m), log2Nxr)] = make_float2(P.x - Q.y, P.y + Q.x);
+    Z[bitrev(unsigned(Nxr - m), log2Nxr)] = make_float2(P.x + Q.y, Q.x - P.y);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_pass_b(PassBArgs a, Levels L) {
+  extern __shared__ float2 sm[];
+  const int slot = blockIdx.y;
+  const bool eta_mode = a.mode >= B_ETA_G;
+  const int rows_per_cta = eta_mode ? 2 * a.rb : a.rb;
+  const int y0 = blockIdx.x * rows_per_cta;
+  const int narr = eta_mode ? a.rb : 2 * a.rb;
+  for (int i = threadIdx.x; i < narr * a.Nxr; i += blockDim.x) sm[i] = make_float2(0.f, 0.f);
+  __syncthreads();
+  if (!eta_mode) {
+    const float z = L.z[a.lev0 + slot];
+    for (int i = threadIdx.x; i < a.rb * a.Mh; i += blockDim.x) {
+      const int m = i % a.Mh, rr = i / a.Mh;
+      const int y = y0 + rr;
+      if (y >= a.Nyr) continue;
+      float2 U, V, W, T;
+      if (a.mode == B_LEVEL_G) {
+        const size_t base = (size_t(slot) * 4 * a.Nyr + y) * a.Mh + m;
+        const size_t fs = size_t(a.Nyr) * a.Mh;
+        U = __ldcg(&a.G[base]);
+        V = __ldcg(&a.G[base + fs]);
+        W = __ldcg(&a.G[base + 2 * fs]);
+        T = __ldcg(&a.G[base + 3 * fs]);
+      } else {
+        const float2 Ap = __ldg(&a.A_phi[m]);
+        const float2 At = __ldg(&a.A_phit[m]);
+        const float kx = float(m) * a.kxs;
+        float F, S;
+        depth_factors(kx, z, a.depth, F, S);
+        U = make_float2(-kx * F * Ap.y, kx * F * Ap.x);
+        V = make_float2(0.f, 0.f);
+        W = make_float2(kx * S * Ap.x, kx * S * Ap.y);
+        T = make_float2(F * At.x, F * At.y);
+      }
+      pack_pair(sm + size_t(2 * rr) * a.Nxr, m, a.Nxr, a.log2Nxr, U, V);
+      pack_pair(sm + size_t(2 * rr + 1) * a.Nxr, m, a.Nxr, a.log2Nxr, W, T);
+    }
+  } else {
+    for (int i = threadIdx.x; i < a.rb * a.Mh; i += blockDim.x) {
+      const int m = i % a.Mh, pp = i / a.Mh;
+      const int ya = y0 + 2 * pp, yb = ya + 1;
+      if (ya >= a.Nyr) continue;
+      float2 Ea, Eb = make_float2(0.f, 0.f);
+      if (a.mode == B_ETA_G) {
+        Ea = __ldcg(&a.G[size_t(ya) * a.Mh + m]);
+        if (yb < a.Nyr) Eb = __ldcg(&a.G[size_t(yb) * a.Mh + m]);
+      } else {
+        Ea = __ldg(&a.A_eta[m]);
+      }
+      pack_pair(sm + size_t(pp) * a.Nxr, m, a.Nxr, a.log2Nxr, Ea, Eb);
+    }
+  }
+  __syncthreads();
+  fft_inv_inplace(sm, a.Nxr, a.log2Nxr, narr, a.tw);
+  if (!eta_mode) {
+    float4* out = a.nodes + size_t(a.lev0 + slot) * a.Nyr * a.Nxr;
+    for (int i = threadIdx.x; i < a.rb * a.Nxr; i += blockDim.x) {
+      const int x = i % a.Nxr, rr = i / a.Nxr;
+      const int y = y0 + rr;
+      if (y >= a.Nyr) continue;
+      const float2 z1 = sm[size_t(2 * rr) * a.Nxr + x];
+      const float2 z2 = sm[size_t(2 * rr + 1) * a.Nxr + x];
+      __stcs(&out[size_t(y) * a.Nxr + x], make_float4(z1.x, z1.y, z2.x, z2.y));
+    }
+  } else {
+    for (int i = threadIdx.x; i < a.rb * a.Nxr; i += blockDim.x) {
+      const int x = i % a.Nxr, pp = i / a.Nxr;
+      const int ya = y0 + 2 * pp, yb = ya + 1;
+      if (ya >= a.Nyr) continue;
+      const float2 zz = sm[size_t(pp) * a.Nxr + x];
+      __stcs(&a.eta[size_t(ya) * a.Nxr + x], zz.x);
+      if (yb < a.Nyr) __stcs(&a.eta[size_t(yb) * a.Nxr + x], zz.y);
+    }
+  }
+}
+
+// Linear propagation of stored modes: A(t) = A(t_ref) e^{-i omega (t - t_ref)}. The phase is
+// reduced to turns in FP64 (exact enough for long simulated times); the rotation is FP32.
+__global__ void k_propagate(const float2* __restrict__ Ae, const float2* __restrict__ Ap,
+                            const float2* __restrict__ At, const double* __restrict__ omega,
+                            int nslot, double dt, float2* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nslot) return;
+  const double turns = omega[i] * dt * 0.15915494309189533577;  // theta / (2 pi)
+  const double frac = turns - rint(turns);
+  float s, c;
+  sincospif(2.f * float(frac), &s, &c);
+  const float2 src[3] = {Ae[i], Ap[i], At[i]};
+#pragma unroll
+  for (int q = 0; q < 3; ++q)
+    out[size_t(q) * nslot + i] =
+        make_float2(fmaf(src[q].x, c, src[q].y * s), fmaf(src[q].y, c, -src[q].x * s));
+}
+
+constexpr int kThreads = 256;
+constexpr size_t kSmemBudget = 64 * 1024;
+constexpr size_t kChunkBytes = size_t(32) << 20;
+
+int set_smem(const void* fn, size_t bytes) {
+  SWENSE_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes)));
+  return SWENSE_OK;
+}
+
+}  // namespace
+}  // namespace swense
+
+using namespace swense;
+
+extern "C" int swense_fields_on_grid(const swense_modes* md, int32_t n_tl, const double* t,
+                                     const swense_grid_desc* desc, float* nodes, float* eta,
+                                     void* stream_) {
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+  if (!md || !desc || !nodes || !eta) return fail(SWENSE_ERR_ARG, "NULL modes, desc or output");
+  if (!md->A_eta || !md->A_phi || !md->A_phit) return fail(SWENSE_ERR_ARG, "NULL modal amplitudes");
+  const int nx = md->nx, ny = md->ny;
+  if (!is_pow2(nx) || nx < 4 || !is_pow2(ny) || (ny != 1 && ny < 4))
+    return fail(SWENSE_ERR_SIZE, "nx must be a power of two >= 4, ny 1 or a power of two >= 4");
+  const int pad = desc->pad_n;
+  if (pad != 1 && pad != 2 && pad != 4 && pad != 8) return fail(SWENSE_ERR_ARG, "pad_n must be 1, 2, 4 or 8");
+  const int64_t Nxr = int64_t(pad) * nx, Nyr = ny > 1 ? int64_t(pad) * ny : 1;
+  if (Nxr > SWENSE_MAX_FFT || Nyr > SWENSE_MAX_FFT)
+    return fail(SWENSE_ERR_SIZE, "pad_n*nx and pad_n*ny must not exceed SWENSE_MAX_FFT");
+  if (!(md->Lx > 0) || !std::isfinite(md->Lx) || (ny > 1 && (!(md->Ly > 0) || !std::isfinite(md->Ly))))
+    return fail(SWENSE_ERR_ARG, "domain lengths must be finite and positive");
+  if (!std::isfinite(md->depth)) return fail(SWENSE_ERR_ARG, "depth must be finite");
+  if (n_tl < 1 || n_tl > 64) return fail(SWENSE_ERR_ARG, "n_tl must be in [1, 64]");
+  if (md->omega) {
+    if (md->n_snap != 1) return fail(SWENSE_ERR_ARG, "with omega, n_snap must be 1");
+    if (!t) return fail(SWENSE_ERR_ARG, "with omega, t[n_tl] is required");
+    for (int l = 0; l < n_tl; ++l)
+      if (!std::isfinite(t[l])) return fail(SWENSE_ERR_ARG, "non-finite time");
+  } else if (md->n_snap != n_tl) {
+    return fail(SWENSE_ERR_ARG, "without omega, n_snap must equal n_tl");
+  }
+  const int nz = desc->nz;
+  if (nz < 4 || nz > SWENSE_MAX_LEVELS || !desc->z_levels)
+    return fail(SWENSE_ERR_LEVELS, "need 4 <= nz <= SWENSE_MAX_LEVELS levels");
+  Levels lev;
+  for (int l = 0; l < nz; ++l) {
+    lev.z[l] = desc->z_levels[l];
+    if (!std::isfinite(lev.z[l]) || (l > 0 && !(lev.z[l] > lev.z[l - 1])))
+      return fail(SWENSE_ERR_LEVELS, "z_levels must be finite and strictly increasing");
+  }
+  if ((reinterpret_cast<uintptr_t>(nodes) & 15) || (reinterpret_cast<uintptr_t>(eta) & 3))
+    return fail(SWENSE_ERR_ARG, "nodes must be 16-byte aligned, eta 4-byte aligned");
+
+  const int nxh1 = nx / 2 + 1, Mh = nx / 2;
+  const size_t nslot = size_t(ny) * nxh1;
+  const size_t per_level = size_t(4) * Nyr * Mh * sizeof(float2);
+  const int chunk = ny > 1 ? int(std::max<size_t>(1, std::min<size_t>(nz, kChunkBytes / per_level))) : 0;
+  const size_t prop_bytes = md->omega ? size_t(n_tl) * 3 * nslot * sizeof(float2) : 0;
+  const size_t geta_bytes = ny > 1 ? size_t(Nyr) * Mh * sizeof(float2) : 0;
+  const size_t g_bytes = ny > 1 ? size_t(chunk) * per_level : 0;
+  auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+  void* ws = nullptr;
+  const size_t ws_bytes = al(prop_bytes) + al(geta_bytes) + al(g_bytes);
+  if (ws_bytes) {
+    int st = workspace(ws_bytes, stream, &ws);
+    if (st) return st;
+  }
+  const float2* tw = nullptr;
+  {
+    int st = twiddles(stream, &tw);
+    if (st) return st;
+  }
+  float2* prop = static_cast<float2*>(ws);
+  float2* g_eta = reinterpret_cast<float2*>(static_cast<char*>(ws) + al(prop_bytes));
+  float2* g_lev = reinterpret_cast<float2*>(static_cast<char*>(ws) + al(prop_bytes) + al(geta_bytes));
+
+  const float kxs = float(6.283185307179586476925 / md->Lx);
+  const float kys = ny > 1 ? float(6.283185307179586476925 / md->Ly) : 0.f;
+  const float depth = md->depth > 0 ? float(md->depth) : 0.f;
+  const int log2Nxr = ilog2(Nxr), log2Nyr = ilog2(Nyr);
+
+  // launch shapes
+  int fp = 4, cb = 1;
+  while (fp > 1 && size_t(fp) * Nyr * sizeof(float2) > kSmemBudget) fp >>= 1;
+  cb = int(std::max<size_t>(1, kSmemBudget / (size_t(fp) * Nyr * sizeof(float2))));
+  cb = std::min(cb, std::min(64, Mh));
+  int cb_eta = int(std::max<size_t>(1, kSmemBudget / (size_t(Nyr) * sizeof(float2))));
+  cb_eta = std::min(cb_eta, std::min(64, Mh));
+  const size_t rowb = size_t(2) * Nxr * sizeof(float2);
+  int rb = int(std::max<size_t>(1, kSmemBudget / rowb));
+  rb = int(std::min<int64_t>(rb, std::min<int64_t>(16, Nyr)));
+  int rb_eta = int(std::max<size_t>(1, kSmemBudget / (size_t(Nxr) * sizeof(float2))));
+  rb_eta = int(std::min<int64_t>(rb_eta, std::min<int64_t>(16, (Nyr + 1) / 2)));
+  const size_t smem_a = size_t(fp) * cb * Nyr * sizeof(float2);
+  const size_t smem_a_eta = size_t(cb_eta) * Nyr * sizeof(float2);
+  const size_t smem_b = size_t(rb) * rowb;
+  const size_t smem_b_eta = size_t(rb_eta) * Nxr * sizeof(float2);
+  {
+    int st = set_smem((const void*)k_pass_a, std::max(smem_a, smem_a_eta));
+    if (!st) st = set_smem((const void*)k_pass_b, std::max(smem_b, smem_b_eta));
+    if (st) return st;
+  }
+
+  for (int l = 0; l < n_tl; ++l) {
+    const float2 *Ae, *Ap, *At;
+    if (md->omega) {
+      float2* o = prop + size_t(l) * 3 * nslot;
+      k_propagate<<<unsigned((nslot + 255) / 256), 256, 0, stream>>>(
+          reinterpret_cast<const float2*>(md->A_eta), reinterpret_cast<const float2*>(md->A_phi),
+          reinterpret_cast<const float2*>(md->A_phit), md->omega, int(nslot), t[l] - md->t_ref, o);
+      SWENSE_CUDA_TRY(cudaGetLastError());
+      count_launches(1);
+      Ae = o;
+      Ap = o + nslot;
+      At = o + 2 * nslot;
+    } else {
+      Ae = reinterpret_cast<const float2*>(md->A_eta) + size_t(l) * nslot;
+      Ap = reinterpret_cast<const float2*>(md->A_phi) + size_t(l) * nslot;
+      At = reinterpret_cast<const float2*>(md->A_phit) + size_t(l) * nslot;
+    }
+    float4* nodes_l = reinterpret_cast<float4*>(nodes) + size_t(l) * nz * Nyr * Nxr;
+    float* eta_l = eta + size_t(l) * Nyr * Nxr;
+
+    PassBArgs b{};
+    b.A_phi = Ap;
+    b.A_phit = At;
+    b.A_eta = Ae;
+    b.nodes = nodes_l;
+    b.eta = eta_l;
+    b.tw = tw;
+    b.Mh = Mh;
+    b.Nxr = int(Nxr);
+    b.log2Nxr = log2Nxr;
+    b.Nyr = int(Nyr);
+    b.kxs = kxs;
+    b.depth = depth;
+
+    if (ny == 1) {
+      b.mode = B_ETA_DIRECT;
+      b.rb = 1;
+      b.lev0 = 0;
+      k_pass_b<<<dim3(1, 1), kThreads, size_t(Nxr) * sizeof(float2), stream>>>(b, lev);
+      SWENSE_CUDA_TRY(cudaGetLastError());
+      count_launches(1);
+      b.mode = B_LEVEL_DIRECT;
+      b.rb = 1;
+      k_pass_b<<<dim3(1, nz), kThreads, rowb, stream>>>(b, lev);
+      SWENSE_CUDA_TRY(cudaGetLastError());
+      count_launches(1);
+      continue;
+    }
+
+    PassAArgs a{};
+    a.A_phi = Ap;
+    a.A_phit = At;
+    a.A_eta = Ae;
+    a.tw = tw;
+    a.ny = ny;
+    a.nxh1 = nxh1;
+    a.Mh = Mh;
+    a.Nyr = int(Nyr);
+    a.log2Nyr = log2Nyr;
+    a.kxs = kxs;
+    a.kys = kys;
+    a.depth = depth;
+
+    // eta: pass A (eta mode) then pass B packing row pairs
+    a.G = g_eta;
+    a.eta_mode = 1;
+    a.fp = 1;
+    a.cb = cb_eta;
+    a.lev0 = 0;
+    k_pass_a<<<dim3((Mh + cb_eta - 1) / cb_eta, 1), kThreads, smem_a_eta, stream>>>(a, lev);
+    SWENSE_CUDA_TRY(cudaGetLastError());
+      count_launches(1);
+    b.G = g_eta;
+    b.mode = B_ETA_G;
+    b.rb = rb_eta;
+    b.lev0 = 0;
+    k_pass_b<<<dim3(unsigned((Nyr + 2 * rb_eta - 1) / (2 * rb_eta)), 1), kThreads, smem_b_eta, stream>>>(b, lev);
+    SWENSE_CUDA_TRY(cudaGetLastError());
+      count_launches(1);
+
+    a.eta_mode = 0;
+    a.fp = fp;
+    a.cb = cb;
+    a.G = g_lev;
+    b.G = g_lev;
+    b.mode = B_LEVEL_G;
+    b.rb = rb;
+    for (int l0 = 0; l0 < nz; l0 += chunk) {
+      const int nl = std::min(chunk, nz - l0);
+      a.lev0 = l0;
+      b.lev0 = l0;
+      k_pass_a<<<dim3((Mh + cb - 1) / cb, nl), kThreads, smem_a, stream>>>(a, lev);
+      SWENSE_CUDA_TRY(cudaGetLastError());
+      count_launches(1);
+      k_pass_b<<<dim3(unsigned((Nyr + rb - 1) / rb), nl), kThreads, smem_b, stream>>>(b, lev);
+      SWENSE_CUDA_TRY(cudaGetLastError());
+      count_launches(1);
+    }
+  }
+  return SWENSE_OK;
+}

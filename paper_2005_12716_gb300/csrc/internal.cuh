@@ -1,0 +1,51 @@
+// Internal helpers shared by the library's translation units (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+
+#include "swense.h"
+
+namespace swense {
+
+// ---------------------------------------------------------------- error reporting (host)
+void set_error(const std::string& msg);
+int fail(int status, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define SWENSE_CUDA_TRY(call)                                   \
+  do {                                                          \
+    cudaError_t e_ = (call);                                    \
+    if (e_ != cudaSuccess) return ::swense::cuda_fail(e_, #call); \
+  } while (0)
+
+// ---------------------------------------------------------------- per-device scratch
+// Returns a device pointer to at least `bytes` bytes of scratch (256-byte aligned), growing the
+// device's workspace if needed. Growing synchronises the device and is refused during capture.
+int workspace(size_t bytes, cudaStream_t stream, void** out);
+
+// Twiddle table e^{+2 pi i j / SWENSE_MAX_FFT}, j < SWENSE_MAX_FFT. The first call on a device
+// fills it with a kernel on `stream` and waits for it (refused during stream capture).
+int twiddles(cudaStream_t stream, const float2** out);
+
+// Counts kernel launches made by the library (reported by swense_launches()).
+void count_launches(int n);
+
+inline bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+inline int ilog2(int64_t v) { int r = 0; while ((int64_t(1) << r) < v) ++r; return r; }
+
+// ---------------------------------------------------------------- device complex helpers
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cmul_i(float2 a) { return make_float2(-a.y, a.x); }   // i*a
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+
+__device__ __forceinline__ unsigned bitrev(unsigned v, int bits) {
+  return bits == 0 ? 0u : (__brev(v) >> (32 - bits));
+}
+
+}  // namespace swense

@@ -1,0 +1,26 @@
+"""Shared test helpers: error norms and device/oracle plumbing (no method arithmetic)."""
+import numpy as np
+
+
+def rel_linf(got, ref):
+    """max |got - ref| / max |ref| over entries where ref is finite; NaN positions must match."""
+    got = np.asarray(got, np.float64)
+    ref = np.asarray(ref, np.float64)
+    assert got.shape == ref.shape, (got.shape, ref.shape)
+    nan_ref = ~np.isfinite(ref)
+    nan_got = ~np.isfinite(got)
+    assert np.array_equal(nan_ref, nan_got), "NaN / out-of-range positions differ"
+    if nan_ref.all():
+        return 0.0
+    scale = np.max(np.abs(ref[~nan_ref]))
+    if scale == 0:
+        return float(np.max(np.abs(got[~nan_ref])))
+    return float(np.max(np.abs(got[~nan_ref] - ref[~nan_ref])) / scale)
+
+
+def rel_l2(got, ref):
+    got = np.asarray(got, np.float64)
+    ref = np.asarray(ref, np.float64)
+    ok = np.isfinite(ref)
+    den = np.sqrt(np.mean(ref[ok] ** 2))
+    return float(np.sqrt(np.mean((got[ok] - ref[ok]) ** 2)) / max(den, 1e-300))

@@ -1,0 +1,80 @@
+"""The C-ABI library builds, loads without a GPU and exports every symbol the header declares."""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "swense.h")
+
+
+def _declared():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(swense_[a-z_0-9]+)\s*\(",
+                                 text, re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2005_12716_gb300 import build
+    build.build()
+    from paper_2005_12716_gb300 import _swense
+    return _swense.load()
+
+
+def test_header_declares_entry_points():
+    names = _declared()
+    for must in ("swense_fields_on_grid", "swense_interp", "swense_fv_divergence",
+                 "swense_strerror", "swense_last_error", "swense_release"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2005_12716_gb300 import build
+    out = subprocess.run(["nm", "-D", "--defined-only", build.LIB], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\bT\s+(swense_\w+)", out))
+    missing = [n for n in _declared() if n not in exported]
+    assert not missing, missing
+    for n in _declared():
+        getattr(lib, n)
+
+
+def test_binding_names_match_header(lib):
+    from paper_2005_12716_gb300 import _swense
+    assert set(_swense.exported_symbols()) == set(_declared())
+
+
+def test_host_side_calls_without_gpu(lib):
+    from paper_2005_12716_gb300 import _swense
+    assert _swense.swense_version() == 100
+    assert _swense.swense_strerror(-3) == "SWENSE_ERR_LEVELS"
+    assert _swense.swense_strerror(0) == "SWENSE_OK"
+
+
+def test_argument_validation_launches_nothing(lib):
+    """Invalid arguments are rejected on the host before any CUDA call."""
+    import ctypes
+    import numpy as np
+    from paper_2005_12716_gb300 import _swense as S
+    z = np.array([-1, -0.5, 0.0, 0.1], np.float32)
+    desc = S.make_grid_desc(3, z)          # pad_n = 3 is not allowed
+    m = S.swense_modes(8, 1, 1.0, 1.0, 0.0, 1, 16, 16, 16, None, 0.0)
+    st = lib.swense_fields_on_grid(ctypes.byref(m), 1, None, ctypes.byref(desc), 16, 16, None)
+    assert st == -1 and b"pad_n" in lib.swense_last_error()
+    desc = S.make_grid_desc(1, z[::-1].copy())
+    st = lib.swense_fields_on_grid(ctypes.byref(m), 1, None, ctypes.byref(desc), 16, 16, None)
+    assert st == -3
+    m2 = S.swense_modes(12, 1, 1.0, 1.0, 0.0, 1, 16, 16, 16, None, 0.0)
+    st = lib.swense_fields_on_grid(ctypes.byref(m2), 1, None, ctypes.byref(S.make_grid_desc(1, z)),
+                                   16, 16, None)
+    assert st == -2
+    g = S.make_grid(16, 16, 16, 1, 4, 1, 1.0, 1.0, z, [0.0])
+    st = lib.swense_interp(ctypes.byref(g), 0.0, 16, 10, None, None, None, None, None, 7, 1e3,
+                           9.81, None, None)
+    assert st == -1 and b"p_mode" in lib.swense_last_error()
+    g = S.make_grid(16, 16, 16, 1, 4, 5, 1.0, 1.0, z, [0.0, 1, 2, 3, 4])
+    st = lib.swense_interp(ctypes.byref(g), 0.0, 16, 10, None, None, None, None, None, 0, 1e3,
+                           9.81, None, None)
+    assert st == -1

@@ -1,0 +1,111 @@
+"""GPU parity of stage 1 (modes -> zero-padded grid) against the FP64 oracle's direct DFT.
+
+Bar (FP32 path): per field, max |gpu - oracle| / max |oracle| <= 1e-5 over every node.
+"""
+import numpy as np
+import pytest
+
+from oracle import modal
+from tests._util import rel_linf
+from wavegen import configs, seas
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def api():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2005_12716_gb300 import build
+    build.build()
+    from paper_2005_12716_gb300 import api as a
+    return a
+
+
+def _oracle_grid(sea, z, pad, t_levels):
+    nodes, eta = [], []
+    for t in t_levels:
+        n_, e_ = modal.fields_on_grid(modal.propagate(sea, t), z, pad)
+        nodes.append(n_)
+        eta.append(e_)
+    return np.stack(nodes), np.stack(eta)
+
+
+def _check(api, sea, z, pad, t_levels, snapshots=False):
+    if snapshots:
+        snaps = [modal.propagate(sea, t) for t in t_levels]
+        modes = api.upload_modes(sea, snapshots=snaps)
+    else:
+        modes = api.upload_modes(sea)
+    grid = api.fields_on_grid(modes, z, pad, t_levels)
+    ref_n, ref_e = _oracle_grid(sea, z, pad, t_levels)
+    got_n = grid.nodes.cpu().numpy()
+    errs = [rel_linf(got_n[..., q], ref_n[..., q]) for q in range(4)]
+    errs.append(rel_linf(grid.eta.cpu().numpy(), ref_e))
+    assert max(errs) <= TOL, errs
+    return errs
+
+
+@pytest.mark.parametrize("pad", [1, 2, 4])
+def test_stokes2d_grid(api, pad):
+    cfg = configs.stokes2d(n_points=10)
+    _check(api, cfg["sea"], cfg["z_levels"], pad, cfg["t_levels"])
+
+
+@pytest.mark.parametrize("pad", [1, 2])
+def test_jonswap3d_small_grid(api, pad):
+    cfg = configs.jonswap3d_small()
+    _check(api, cfg["sea"], cfg["z_levels"], pad, cfg["t_levels"])
+
+
+@pytest.mark.parametrize("nx,ny,depth,pad", [(16, 4, 0.0, 8), (8, 64, 0.7, 1), (128, 16, 1.5, 2),
+                                             (4, 4, 0.0, 1), (256, 128, 0.0, 1)])
+def test_random_sea_grid_shapes(api, nx, ny, depth, pad):
+    rng = np.random.default_rng(nx * 1000 + ny)
+    comps = seas.random_linear_components(nx, ny, 5.0, 3.0, min(24, nx * ny // 4), 0.01, rng,
+                                          kmax_frac=1.0)
+    sea = seas.linear_sea(nx, ny, 5.0, 3.0, comps, depth=depth)
+    z = np.array([-0.6, -0.31, -0.1, -0.02, 0.0, 0.04], np.float32)
+    _check(api, sea, z, pad, [0.0, 0.05, 0.1, 0.3])
+
+
+def test_snapshot_mode_equals_propagation(api):
+    """n_snap = n_tl (no omega) gives the same grid as propagating one snapshot."""
+    cfg = configs.jonswap3d_small()
+    _check(api, cfg["sea"], cfg["z_levels"], 1, cfg["t_levels"], snapshots=True)
+
+
+def test_long_time_phase_reduction(api):
+    """t ~ 1e4 s: the FP64 phase reduction keeps the propagated grid at FP32 accuracy."""
+    cfg = configs.jonswap3d_small()
+    _check(api, cfg["sea"], cfg["z_levels"], 1, [1.0e4, 1.0e4 + 0.05])
+
+
+def test_full_size_jonswap_sampled_nodes(api):
+    """512 x 256 modes, 64 levels, two time levels: 600 sampled nodes vs the direct sum."""
+    import torch
+    cfg = configs.jonswap3d(mesh_dims=(4, 8, 4))
+    sea, z, tl = cfg["sea"], cfg["z_levels"], cfg["t_levels"]
+    grid = api.fields_on_grid(api.upload_modes(sea), z, 1, tl)
+    rng = np.random.default_rng(5)
+    n = 300
+    for l, t in enumerate(tl):
+        ii, jj, kk = rng.integers(0, 512, n), rng.integers(0, 256, n), rng.integers(0, 64, n)
+        pts = np.stack([ii * sea["Lx"] / 512, jj * sea["Ly"] / 256, z[kk].astype(np.float64)], 1)
+        ref = modal.fields_at_points(modal.propagate(sea, t), pts)
+        got = grid.nodes[l].cpu().numpy()[kk, jj, ii]
+        for q, key in enumerate(("u", "v", "w", "phit")):
+            # normwise against the field's maximum over the whole grid
+            scale = float(torch.max(torch.abs(grid.nodes[l, ..., q])).item())
+            assert np.max(np.abs(got[:, q] - ref[key])) / scale <= TOL, key
+        ge = grid.eta[l].cpu().numpy()[jj, ii]
+        assert np.max(np.abs(ge - ref["eta"])) / float(torch.max(torch.abs(grid.eta[l]))) <= TOL
+
+
+def test_calm_water_grid_is_zero(api):
+    sea = seas.linear_sea(32, 8, 4.0, 2.0, [])
+    z = np.array([-1, -0.5, 0, 0.1], np.float32)
+    g = api.fields_on_grid(api.upload_modes(sea), z, 2, [0.0])
+    assert float(g.nodes.abs().max()) == 0.0 and float(g.eta.abs().max()) == 0.0

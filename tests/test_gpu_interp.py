@@ -1,0 +1,154 @@
+"""GPU parity of stage 2 (grid -> points) and the FV divergence against the FP64 oracle.
+
+T2 bar: the GPU gather of the GPU grid vs the oracle's literal Lagrange interpolation of the
+oracle's FP64 grid, same points / time / scheme: per field, max abs error / max |oracle| <= 1e-5.
+"""
+import numpy as np
+import pytest
+
+from oracle import divergence, interp as ointerp, modal
+from tests._util import rel_linf
+from wavegen import configs, points as P, seas
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+FIELDS = ("eta", "u", "v", "w", "p")
+
+
+@pytest.fixture(scope="module")
+def api():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2005_12716_gb300 import build
+    build.build()
+    from paper_2005_12716_gb300 import api as a
+    return a
+
+
+def _oracle_grid(sea, z, pad, t_levels):
+    nodes, eta = [], []
+    for t in t_levels:
+        n_, e_ = modal.fields_on_grid(modal.propagate(sea, t), z, pad)
+        nodes.append(n_)
+        eta.append(e_)
+    return np.stack(nodes), np.stack(eta)
+
+
+def _run(api, sea, z, pad, t_levels, t, pts, p_mode="dyn"):
+    import torch
+    modes = api.upload_modes(sea)
+    grid = api.fields_on_grid(modes, z, pad, t_levels)
+    out, cnt = api.interp(grid, t, torch.from_numpy(np.ascontiguousarray(pts)).cuda(), p_mode=p_mode,
+                          count_out_of_range=True)
+    rn, re_ = _oracle_grid(sea, z, pad, t_levels)
+    ref = ointerp.interp_points(rn, re_, sea["Lx"], sea["Ly"], z, t_levels, pts, t, p_mode=p_mode)
+    errs = {k: rel_linf(out[k].cpu().numpy(), ref[k]) for k in FIELDS}
+    assert cnt == int(ref["out_of_range"].sum())
+    return errs, out, ref
+
+
+@pytest.mark.parametrize("pad", [1, 2])
+def test_stokes2d_full_points(api, pad):
+    """2-D Stokes wave, 256 modes, 33 levels, 50,000 points, two time levels."""
+    cfg = configs.stokes2d()
+    errs, _, _ = _run(api, cfg["sea"], cfg["z_levels"], pad, cfg["t_levels"], cfg["t_query"],
+                      cfg["points"])
+    assert max(errs.values()) <= TOL, errs
+
+
+@pytest.mark.parametrize("n_tl,p_mode", [(2, "dyn"), (4, "total"), (1, "phit"), (3, "dyn")])
+def test_jonswap3d_small_mesh_points(api, n_tl, p_mode):
+    cfg = configs.jonswap3d_small(n_tl=n_tl)
+    pts = configs.mesh_points(cfg["mesh"])
+    errs, _, _ = _run(api, cfg["sea"], cfg["z_levels"], 2, cfg["t_levels"], cfg["t_query"], pts,
+                      p_mode)
+    assert max(errs.values()) <= TOL, errs
+
+
+def test_ragged_wrapped_and_out_of_range_points(api):
+    """Points outside [0, L) wrap; points above/below the levels are NaN and counted; a ragged
+    count (not a multiple of the block) exercises the tail."""
+    cfg = configs.jonswap3d_small()
+    sea, z = cfg["sea"], cfg["z_levels"]
+    lo = (-1.5 * sea["Lx"], -2.2 * sea["Ly"], float(z[0]) - 0.05)
+    hi = (2.5 * sea["Lx"], 1.3 * sea["Ly"], float(z[-1]) + 0.05)
+    pts = P.uniform_points(4099, lo, hi, 77)
+    # exact node positions and exact level values
+    pts[:50, 0] = np.arange(50) * sea["Lx"] / (2 * sea["nx"])
+    pts[:50, 2] = z[np.arange(50) % len(z)]
+    errs, out, ref = _run(api, sea, z, 2, cfg["t_levels"], cfg["t_query"], pts)
+    assert ref["out_of_range"].sum() > 0
+    assert max(errs.values()) <= TOL, errs
+
+
+def test_empty_point_set(api):
+    import torch
+    cfg = configs.jonswap3d_small()
+    modes = api.upload_modes(cfg["sea"])
+    grid = api.fields_on_grid(modes, cfg["z_levels"], 1, cfg["t_levels"])
+    out, cnt = api.interp(grid, 0.0, torch.empty((0, 3), device="cuda"), count_out_of_range=True)
+    assert cnt == 0 and out["u"].numel() == 0
+
+
+def test_full_size_jonswap_mesh_sampled(api):
+    """512 x 256 modes, 64 levels, 2 M cell + 6 M face centres, in the bench's launch shape.
+    Sampled points are checked against the oracle's interpolation of oracle node values that
+    are computed one by one (direct sums at each stencil node)."""
+    import torch
+    cfg = configs.jonswap3d()
+    sea, z, tl, t = cfg["sea"], cfg["z_levels"], cfg["t_levels"], cfg["t_query"]
+    pts = configs.mesh_points(cfg["mesh"])
+    modes = api.upload_modes(sea)
+    grid = api.fields_on_grid(modes, z, 1, tl)
+    out, cnt = api.interp(grid, t, torch.from_numpy(pts).cuda(), count_out_of_range=True)
+    assert cnt == 0
+    rng = np.random.default_rng(9)
+    sel = rng.choice(len(pts), 6, replace=False)
+    nxr, nyr = 512, 256
+    # oracle grid holding only the stencil nodes of the sampled points (NaN elsewhere)
+    sub_n = np.full((len(tl), len(z), nyr, nxr, 4), np.nan)
+    sub_e = np.full((len(tl), nyr, nxr), np.nan)
+    sp = pts[sel].astype(np.float64)
+    ix = np.floor(sp[:, 0] * nxr / sea["Lx"]).astype(int)[:, None] + np.arange(-1, 3)
+    iy = np.floor(sp[:, 1] * nyr / sea["Ly"]).astype(int)[:, None] + np.arange(-1, 3)
+    j0, _, _ = ointerp.level_stencil(sp[:, 2], z)
+    node_pts, node_idx = [], []
+    for p_ in range(len(sel)):
+        for a in range(4):
+            for b in range(4):
+                for c in range(-1, 5):      # one spare node each side in x for boundary cases
+                    i_, j_, l_ = (ix[p_, 0] + c) % nxr, iy[p_, b] % nyr, j0[p_] + a
+                    node_idx.append((l_, j_, i_))
+                    node_pts.append((i_ * sea["Lx"] / nxr, j_ * sea["Ly"] / nyr, float(z[l_])))
+    node_pts = np.array(node_pts)
+    for li, tt in enumerate(tl):
+        f = modal.fields_at_points(modal.propagate(sea, tt), node_pts)
+        for k_, (l_, j_, i_) in enumerate(node_idx):
+            sub_n[li, l_, j_, i_] = (f["u"][k_], f["v"][k_], f["w"][k_], f["phit"][k_])
+            sub_e[li, j_, i_] = f["eta"][k_]
+    ref = ointerp.interp_points(sub_n, sub_e, sea["Lx"], sea["Ly"], z, tl, sp, t)
+    for key in FIELDS:
+        got = out[key][torch.from_numpy(sel).cuda()].cpu().numpy()
+        scale = float(torch.max(torch.abs(out[key])).item())
+        assert np.all(np.isfinite(ref[key]))
+        assert np.max(np.abs(got - ref[key])) / scale <= TOL, key
+
+
+def test_fv_divergence_parity(api):
+    """Divergence of the oracle's exact face velocities (FP32-rounded): GPU vs FP64 oracle,
+    normwise against the largest face-flux magnitude per unit volume."""
+    import torch
+    cfg = configs.jonswap3d_small()
+    m = cfg["mesh"]
+    f = modal.fields_at_points(cfg["sea"], m["face_centres"])
+    vel = np.stack([f["u"], f["v"], f["w"]], 1).astype(np.float32)
+    area = m["face_area"].astype(np.float32)
+    vol = m["cell_volume"].astype(np.float32)
+    ref = divergence.fv_divergence(vel, area, m["cell_faces"], vol)
+    dv = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    got = api.fv_divergence(dv(vel[:, 0]), dv(vel[:, 1]), dv(vel[:, 2]), dv(area),
+                            dv(m["cell_faces"]), dv(vol)).cpu().numpy()
+    flux = np.abs(np.einsum("fk,fk->f", vel.astype(np.float64), area.astype(np.float64)))
+    scale = np.max(flux[np.abs(m["cell_faces"]) - 1].sum(1) / vol)
+    assert np.max(np.abs(got - ref)) / scale <= TOL
