@@ -188,7 +188,9 @@ __global__ void __launch_bounds__(256) k_pass_b(PassBArgs a, Levels L) {
       if (y >= a.Nyr) continue;
       const float2 z1 = sm[size_t(2 * rr) * a.Nxr + x];
       const float2 z2 = sm[size_t(2 * rr + 1) * a.Nxr + x];
-      __stcs(&out[size_t(y) * a.Nxr + x], make_float4(z1.x, z1.y, z2.x, z2.y));
+      // 2-D: v is identically zero (the imaginary part of z1 holds only round-off)
+      const float v = a.mode == B_LEVEL_DIRECT ? 0.f : z1.y;
+      __stcs(&out[size_t(y) * a.Nxr + x], make_float4(z1.x, v, z2.x, z2.y));
     }
   } else {
     for (int i = threadIdx.x; i < a.rb * a.Nxr; i += blockDim.x) {
