@@ -113,6 +113,36 @@ typedef struct swense_grid_desc {
 int swense_fields_on_grid(const swense_modes* modes, int32_t n_tl, const double* t,
                           const swense_grid_desc* desc, float* nodes, float* eta, void* stream);
 
+/*
+ * swense_fields_on_grid_noalloc — swense_fields_on_grid for callers that cannot allocate device
+ * memory (the paper has no counterpart; this is a property of the library, not of the method).
+ *
+ * Some callers must not allocate while their time loop runs: a CFD solver that reserves all
+ * device memory up front in its own pool, a plugin whose host forbids allocations outside set-up,
+ * or code that cannot afford the implicit device synchronisation a cudaMalloc/cudaFree may do.
+ * This entry point takes the same arguments and produces the same grid as swense_fields_on_grid,
+ * but it allocates nothing: it calls no cudaMalloc, cudaFree or allocating library routine. Its
+ * scratch (the transformed levels between the two passes, and the propagated modes) lives in a
+ * fixed array of SWENSE_NOALLOC_SCRATCH_BYTES inside the library's device image, which every GPU
+ * that loads the library holds until the process exits.
+ *   - Requests whose scratch for one vertical level (plus the propagated modes and the eta
+ *     transform) exceeds SWENSE_NOALLOC_SCRATCH_BYTES are rejected with SWENSE_ERR_SIZE before
+ *     anything is launched; larger requests use swense_fields_on_grid. Within the limit, levels
+ *     are processed in as many chunks as the array requires.
+ *   - The first call on each device looks up the array's device address (cudaGetSymbolAddress,
+ *     with that device current) and fills the shared twiddle table; make that first call before
+ *     any stream capture.
+ *   - Every call on a device uses the same array and leaves its contents behind. Nothing in it
+ *     has to start at zero (each call writes every scratch value before reading it), but calls
+ *     that overlap on the GPU (different streams without ordering) race on it: order them.
+ * Errors: as swense_fields_on_grid, with SWENSE_ERR_SIZE for the scratch limit and never
+ * SWENSE_ERR_OOM.
+ */
+#define SWENSE_NOALLOC_SCRATCH_BYTES (16u << 20)
+int swense_fields_on_grid_noalloc(const swense_modes* modes, int32_t n_tl, const double* t,
+                                  const swense_grid_desc* desc, float* nodes, float* eta,
+                                  void* stream);
+
 /* Grid fields at n_tl time levels as written by swense_fields_on_grid. */
 typedef struct swense_grid {
   const float* nodes;       /* device float [n_tl][nz][ny_r][nx_r][4] */

@@ -54,6 +54,11 @@ _SIGS = {
     "swense_fields_on_grid": (ctypes.c_int, [ctypes.POINTER(swense_modes), ctypes.c_int32,
                                              ctypes.c_void_p, ctypes.POINTER(swense_grid_desc),
                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "swense_fields_on_grid_noalloc": (ctypes.c_int, [ctypes.POINTER(swense_modes), ctypes.c_int32,
+                                                     ctypes.c_void_p,
+                                                     ctypes.POINTER(swense_grid_desc),
+                                                     ctypes.c_void_p, ctypes.c_void_p,
+                                                     ctypes.c_void_p]),
     "swense_interp": (ctypes.c_int, [ctypes.POINTER(swense_grid), ctypes.c_double, ctypes.c_void_p,
                                      ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -150,6 +155,15 @@ def swense_fields_on_grid(modes, n_tl, t, desc, nodes, eta, stream=None):
     _check(lib.swense_fields_on_grid(ctypes.byref(modes), n_tl,
                                      None if tt is None else tt.ctypes.data,
                                      ctypes.byref(desc), _ptr(nodes), _ptr(eta), _stream(stream)))
+
+
+def swense_fields_on_grid_noalloc(modes, n_tl, t, desc, nodes, eta, stream=None):
+    lib = load()
+    tt = None if t is None else np.ascontiguousarray(t, np.float64)
+    _check(lib.swense_fields_on_grid_noalloc(ctypes.byref(modes), n_tl,
+                                             None if tt is None else tt.ctypes.data,
+                                             ctypes.byref(desc), _ptr(nodes), _ptr(eta),
+                                             _stream(stream)))
 
 
 def swense_interp(grid, t, pts, np_, eta=None, u=None, v=None, w=None, p=None, p_mode=P_DYN,

@@ -17,6 +17,7 @@
 // 2-D (ny == 1): pass B alone, reading the modes directly.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <string>
 
 #include "fft.cuh"
@@ -231,15 +232,19 @@ int set_smem(const void* fn, size_t bytes) {
   return SWENSE_OK;
 }
 
-}  // namespace
-}  // namespace swense
 
-using namespace swense;
+// Validated sizes and derived constants of one swense_fields_on_grid request.
+struct GridPlan {
+  int nx, ny, nz, n_tl, nxh1, Mh;
+  int64_t Nxr, Nyr;
+  size_t nslot, per_level, prop_bytes, geta_bytes;
+  Levels lev;
+};
 
-extern "C" int swense_fields_on_grid(const swense_modes* md, int32_t n_tl, const double* t,
-                                     const swense_grid_desc* desc, float* nodes, float* eta,
-                                     void* stream_) {
-  cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+int plan_grid(const swense_modes* md, int32_t n_tl, const double* t, const swense_grid_desc* desc,
+              const float* nodes, const float* eta, GridPlan* p) {
   if (!md || !desc || !nodes || !eta) return fail(SWENSE_ERR_ARG, "NULL modes, desc or output");
   if (!md->A_eta || !md->A_phi || !md->A_phit) return fail(SWENSE_ERR_ARG, "NULL modal amplitudes");
   const int nx = md->nx, ny = md->ny;
@@ -265,37 +270,49 @@ extern "C" int swense_fields_on_grid(const swense_modes* md, int32_t n_tl, const
   const int nz = desc->nz;
   if (nz < 4 || nz > SWENSE_MAX_LEVELS || !desc->z_levels)
     return fail(SWENSE_ERR_LEVELS, "need 4 <= nz <= SWENSE_MAX_LEVELS levels");
-  Levels lev;
   for (int l = 0; l < nz; ++l) {
-    lev.z[l] = desc->z_levels[l];
-    if (!std::isfinite(lev.z[l]) || (l > 0 && !(lev.z[l] > lev.z[l - 1])))
+    p->lev.z[l] = desc->z_levels[l];
+    if (!std::isfinite(p->lev.z[l]) || (l > 0 && !(p->lev.z[l] > p->lev.z[l - 1])))
       return fail(SWENSE_ERR_LEVELS, "z_levels must be finite and strictly increasing");
   }
   if ((reinterpret_cast<uintptr_t>(nodes) & 15) || (reinterpret_cast<uintptr_t>(eta) & 3))
     return fail(SWENSE_ERR_ARG, "nodes must be 16-byte aligned, eta 4-byte aligned");
+  p->nx = nx;
+  p->ny = ny;
+  p->nz = nz;
+  p->n_tl = n_tl;
+  p->nxh1 = nx / 2 + 1;
+  p->Mh = nx / 2;
+  p->Nxr = Nxr;
+  p->Nyr = Nyr;
+  p->nslot = size_t(ny) * p->nxh1;
+  p->per_level = size_t(4) * Nyr * p->Mh * sizeof(float2);
+  p->prop_bytes = md->omega ? size_t(n_tl) * 3 * p->nslot * sizeof(float2) : 0;
+  p->geta_bytes = ny > 1 ? size_t(Nyr) * p->Mh * sizeof(float2) : 0;
+  return SWENSE_OK;
+}
 
-  const int nxh1 = nx / 2 + 1, Mh = nx / 2;
-  const size_t nslot = size_t(ny) * nxh1;
-  const size_t per_level = size_t(4) * Nyr * Mh * sizeof(float2);
-  const int chunk = ny > 1 ? int(std::max<size_t>(1, std::min<size_t>(nz, kChunkBytes / per_level))) : 0;
-  const size_t prop_bytes = md->omega ? size_t(n_tl) * 3 * nslot * sizeof(float2) : 0;
-  const size_t geta_bytes = ny > 1 ? size_t(Nyr) * Mh * sizeof(float2) : 0;
-  const size_t g_bytes = ny > 1 ? size_t(chunk) * per_level : 0;
-  auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
-  void* ws = nullptr;
-  const size_t ws_bytes = al(prop_bytes) + al(geta_bytes) + al(g_bytes);
-  if (ws_bytes) {
-    int st = workspace(ws_bytes, stream, &ws);
-    if (st) return st;
-  }
+// Scratch bytes for a level chunk of `chunk` levels (0 when no scratch is needed).
+size_t scratch_bytes(const GridPlan& p, int chunk) {
+  const size_t g_bytes = p.ny > 1 ? size_t(chunk) * p.per_level : 0;
+  return align256(p.prop_bytes) + align256(p.geta_bytes) + align256(g_bytes);
+}
+
+// Enqueue every kernel of the request; `ws` holds scratch_bytes(p, chunk) bytes.
+int launch_grid(const GridPlan& p, const swense_modes* md, const double* t, float* nodes, float* eta,
+                void* ws, int chunk, cudaStream_t stream) {
   const float2* tw = nullptr;
   {
     int st = twiddles(stream, &tw);
     if (st) return st;
   }
+  const int ny = p.ny, nz = p.nz, Mh = p.Mh, nxh1 = p.nxh1;
+  const int64_t Nxr = p.Nxr, Nyr = p.Nyr;
+  const size_t nslot = p.nslot;
   float2* prop = static_cast<float2*>(ws);
-  float2* g_eta = reinterpret_cast<float2*>(static_cast<char*>(ws) + al(prop_bytes));
-  float2* g_lev = reinterpret_cast<float2*>(static_cast<char*>(ws) + al(prop_bytes) + al(geta_bytes));
+  float2* g_eta = reinterpret_cast<float2*>(static_cast<char*>(ws) + align256(p.prop_bytes));
+  float2* g_lev = reinterpret_cast<float2*>(static_cast<char*>(ws) + align256(p.prop_bytes) +
+                                            align256(p.geta_bytes));
 
   const float kxs = float(6.283185307179586476925 / md->Lx);
   const float kys = ny > 1 ? float(6.283185307179586476925 / md->Ly) : 0.f;
@@ -324,7 +341,7 @@ extern "C" int swense_fields_on_grid(const swense_modes* md, int32_t n_tl, const
     if (st) return st;
   }
 
-  for (int l = 0; l < n_tl; ++l) {
+  for (int l = 0; l < p.n_tl; ++l) {
     const float2 *Ae, *Ap, *At;
     if (md->omega) {
       float2* o = prop + size_t(l) * 3 * nslot;
@@ -362,12 +379,12 @@ extern "C" int swense_fields_on_grid(const swense_modes* md, int32_t n_tl, const
       b.mode = B_ETA_DIRECT;
       b.rb = 1;
       b.lev0 = 0;
-      k_pass_b<<<dim3(1, 1), kThreads, size_t(Nxr) * sizeof(float2), stream>>>(b, lev);
+      k_pass_b<<<dim3(1, 1), kThreads, size_t(Nxr) * sizeof(float2), stream>>>(b, p.lev);
       SWENSE_CUDA_TRY(cudaGetLastError());
       count_launches(1);
       b.mode = B_LEVEL_DIRECT;
       b.rb = 1;
-      k_pass_b<<<dim3(1, nz), kThreads, rowb, stream>>>(b, lev);
+      k_pass_b<<<dim3(1, nz), kThreads, rowb, stream>>>(b, p.lev);
       SWENSE_CUDA_TRY(cudaGetLastError());
       count_launches(1);
       continue;
@@ -393,16 +410,17 @@ extern "C" int swense_fields_on_grid(const swense_modes* md, int32_t n_tl, const
     a.fp = 1;
     a.cb = cb_eta;
     a.lev0 = 0;
-    k_pass_a<<<dim3((Mh + cb_eta - 1) / cb_eta, 1), kThreads, smem_a_eta, stream>>>(a, lev);
+    k_pass_a<<<dim3((Mh + cb_eta - 1) / cb_eta, 1), kThreads, smem_a_eta, stream>>>(a, p.lev);
     SWENSE_CUDA_TRY(cudaGetLastError());
-      count_launches(1);
+    count_launches(1);
     b.G = g_eta;
     b.mode = B_ETA_G;
     b.rb = rb_eta;
     b.lev0 = 0;
-    k_pass_b<<<dim3(unsigned((Nyr + 2 * rb_eta - 1) / (2 * rb_eta)), 1), kThreads, smem_b_eta, stream>>>(b, lev);
+    k_pass_b<<<dim3(unsigned((Nyr + 2 * rb_eta - 1) / (2 * rb_eta)), 1), kThreads, smem_b_eta,
+               stream>>>(b, p.lev);
     SWENSE_CUDA_TRY(cudaGetLastError());
-      count_launches(1);
+    count_launches(1);
 
     a.eta_mode = 0;
     a.fp = fp;
@@ -415,13 +433,94 @@ extern "C" int swense_fields_on_grid(const swense_modes* md, int32_t n_tl, const
       const int nl = std::min(chunk, nz - l0);
       a.lev0 = l0;
       b.lev0 = l0;
-      k_pass_a<<<dim3((Mh + cb - 1) / cb, nl), kThreads, smem_a, stream>>>(a, lev);
+      k_pass_a<<<dim3((Mh + cb - 1) / cb, nl), kThreads, smem_a, stream>>>(a, p.lev);
       SWENSE_CUDA_TRY(cudaGetLastError());
       count_launches(1);
-      k_pass_b<<<dim3(unsigned((Nyr + rb - 1) / rb), nl), kThreads, smem_b, stream>>>(b, lev);
+      k_pass_b<<<dim3(unsigned((Nyr + rb - 1) / rb), nl), kThreads, smem_b, stream>>>(b, p.lev);
       SWENSE_CUDA_TRY(cudaGetLastError());
       count_launches(1);
     }
   }
   return SWENSE_OK;
+}
+
+}  // namespace
+}  // namespace swense
+
+using namespace swense;
+
+extern "C" int swense_fields_on_grid(const swense_modes* md, int32_t n_tl, const double* t,
+                                     const swense_grid_desc* desc, float* nodes, float* eta,
+                                     void* stream_) {
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+  GridPlan p;
+  int st = plan_grid(md, n_tl, t, desc, nodes, eta, &p);
+  if (st) return st;
+  const int chunk = p.ny > 1 ? int(std::max<size_t>(1, std::min<size_t>(p.nz, kChunkBytes / p.per_level))) : 0;
+  void* ws = nullptr;
+  const size_t ws_bytes = scratch_bytes(p, chunk);
+  if (ws_bytes) {
+    st = workspace(ws_bytes, stream, &ws);
+    if (st) return st;
+  }
+  return launch_grid(p, md, t, nodes, eta, ws, chunk, stream);
+}
+
+// ---------------------------------------------------------------------------------------------
+// swense_fields_on_grid_noalloc: the same kernels, with their scratch in a fixed device array
+// that is part of the library image instead of the cudaMalloc'ed workspace.
+namespace swense {
+namespace {
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[SWENSE_NOALLOC_SCRATCH_BYTES];
+
+std::mutex g_noalloc_mutex;
+void* g_noalloc_ptr[64] = {};
+
+// Device address of g_noalloc_scratch on the current device. The host-side symbol is only a
+// stand-in, so the address is looked up once per device (with that device current) and cached.
+int noalloc_scratch(void** out) {
+  int dev = 0;
+  SWENSE_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(SWENSE_ERR_UNSUPPORTED, "device index too large");
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return SWENSE_OK;
+}
+
+}  // namespace
+}  // namespace swense
+
+extern "C" int swense_fields_on_grid_noalloc(const swense_modes* md, int32_t n_tl, const double* t,
+                                             const swense_grid_desc* desc, float* nodes,
+                                             float* eta, void* stream_) {
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+  GridPlan p;
+  int st = plan_grid(md, n_tl, t, desc, nodes, eta, &p);
+  if (st) return st;
+  const size_t cap = size_t(SWENSE_NOALLOC_SCRATCH_BYTES);
+  const size_t fixed = scratch_bytes(p, 0);
+  int chunk = 0;
+  if (p.ny > 1) {
+    if (fixed + p.per_level > cap)
+      return fail(SWENSE_ERR_SIZE,
+                  "request needs " + std::to_string(fixed + p.per_level) +
+                      " bytes of scratch for one level; swense_fields_on_grid_noalloc has " +
+                      std::to_string(cap) + " (SWENSE_NOALLOC_SCRATCH_BYTES)");
+    chunk = int(std::min<size_t>(size_t(p.nz), (cap - fixed) / p.per_level));
+  } else if (fixed > cap) {
+    return fail(SWENSE_ERR_SIZE, "request needs " + std::to_string(fixed) +
+                                     " bytes of scratch; swense_fields_on_grid_noalloc has " +
+                                     std::to_string(cap) + " (SWENSE_NOALLOC_SCRATCH_BYTES)");
+  }
+  void* ws = nullptr;
+  st = noalloc_scratch(&ws);
+  if (st) return st;
+  return launch_grid(p, md, t, nodes, eta, ws, chunk, stream);
 }
