@@ -174,6 +174,107 @@ int swense_interp(const swense_grid* grid, double t, const float* pts, int64_t n
                   void* stream);
 
 /*
+ * swense_bin_points — point binning for scattered point sets (no counterpart in the paper,
+ * whose CFD points arrive in mesh order). Counting sort of the points by grid tile (4 x 4 cells
+ * horizontally, one 4-level stencil vertically, x fastest) so that consecutive points share
+ * stencils; the grid geometry comes from `grid` (nodes/eta/t_levels are not read).
+ *   perm: device int32 [np], out: perm[k] = caller index of the k-th sorted point
+ *   pts_sorted: device float [np][3], out: the points in sorted order
+ * The order inside one tile is unspecified; results of the interpolation do not depend on it.
+ * Uses the scratch workspace (4 B per point and per tile). Errors: ARG, SIZE, LEVELS, OOM, CUDA.
+ */
+int swense_bin_points(const swense_grid* grid, const float* pts, int64_t np, int32_t* perm,
+                      float* pts_sorted, void* stream);
+
+/* swense_interp on points sorted by swense_bin_points: reads pts_sorted in order and writes
+ * every output at its caller index perm[k]. Same arguments and rules as swense_interp. */
+int swense_interp_permuted(const swense_grid* grid, double t, const float* pts_sorted,
+                           const int32_t* perm, int64_t np, float* eta, float* u, float* v,
+                           float* w, float* p, int32_t p_mode, double rho, double g,
+                           int64_t* n_out_of_range, void* stream);
+
+enum swense_direct_precision {
+  SWENSE_DIRECT_FP32 = 0,        /* FP32 arithmetic, exact integer-turn phases */
+  SWENSE_DIRECT_SPLIT_BF16 = 1   /* reserved: tensor-core split-BF16 contraction */
+};
+
+/*
+ * swense_direct — direct ("analytical") evaluation of the modal sums at arbitrary points
+ * (paper: reconstruction section, analytical evaluation of u_I and w_I by substituting the
+ * coordinates into the sums; its cost is proportional to the number of Fourier components per
+ * point). No grid, no interpolation error: used for small mode counts (regular waves) and for
+ * near-body points. Same field definitions as swense_fields_on_grid; pressure by Bernoulli.
+ *
+ * modes: one snapshot (n_snap = 1); with omega non-NULL it is propagated to time t
+ *   (A e^{-i omega (t - t_ref)}, phase reduced in FP64), otherwise t is ignored.
+ * pts: device float [np][3]; outputs device float [np] each, any may be NULL.
+ * precision: SWENSE_DIRECT_FP32 (the phase m x/Lx + n y/Ly is an exact 32-bit fraction of a
+ *   turn, so accuracy does not degrade with |k x|).
+ * Uses the scratch workspace (64 B per mode slot). Errors: ARG, SIZE, UNSUPPORTED, OOM, CUDA.
+ */
+int swense_direct(const swense_modes* modes, double t, const float* pts, int64_t np,
+                  float* eta, float* u, float* v, float* w, float* p, int32_t p_mode,
+                  double rho, double g, int32_t precision, void* stream);
+
+/*
+ * Learned interpolation correction (no counterpart in the paper, which interpolates with a
+ * plain scheme; this is an optional refinement of its interpolation step, judged by the same
+ * modal-sum reference and the same divergence measure). One multilayer perceptron is shared by
+ * the fields f in (u, v, w, dphi/dt):
+ *   x = [stencil_f / s_f (64 time-blended 4x4x4 node values, x fastest, then y, then z),
+ *        dx, dy, dz, 0],  s_f = max |stencil_f| + 1e-30 (row of SWENSE_MLP_XLD floats),
+ *   67 -> 64 -> 64 -> 4 with tanh-form GELU on the hidden layers; output y[f];
+ *   corrected f = lagrange_f + s_f y[f]; pressure from the corrected fields (Bernoulli).
+ * Parameters: FP32, SWENSE_MLP_NPARAM values packed as W1[64][67], b1[64], W2[64][64], b2[64],
+ * W3[4][64], b3[4] (row = output unit). The kernels read a BF16 "packed" copy
+ * (SWENSE_MLP_PACKED_BYTES, 16-byte aligned device buffer) written by swense_mlp_pack or by
+ * each training step. Tensor cores: BF16 MMA with FP32 accumulation (inference splits inputs
+ * and activations into BF16 hi + lo; training uses plain BF16).
+ */
+#define SWENSE_MLP_NPARAM 8772
+#define SWENSE_MLP_PACKED_BYTES 32768
+#define SWENSE_MLP_XLD 68
+
+/* params (device FP32 [SWENSE_MLP_NPARAM]) -> packed (device, SWENSE_MLP_PACKED_BYTES), with
+ * the inference output multiplier out_scale (> 0; training targets are divided by it so the
+ * network works on O(1) values). Synchronises the stream (out_scale is copied from the host).
+ * Training steps refresh the weights of packed and keep its out_scale. */
+int swense_mlp_pack(const float* params, float out_scale, void* packed, void* stream);
+
+/* Network rows of features: y[r] = out_scale * net(x[r])[r % 4] (rows point-major, fields
+ * u, v, w, phit).
+ * x: device float [rows][SWENSE_MLP_XLD]; y: device float [rows]. */
+int swense_mlp_forward(const void* packed, const float* x, int64_t rows, float* y, void* stream);
+
+/* Features of points on a 3-D grid: x [4 np][SWENSE_MLP_XLD], scale [4 np] (s_f), lagrange
+ * [4 np] (plain interpolated f), eta [np] (plain, may be NULL); same grid rules as
+ * swense_interp. Errors: ARG, SIZE, LEVELS, UNSUPPORTED (2-D grid), CUDA. */
+int swense_mlp_features(const swense_grid* grid, double t, const float* pts, int64_t np,
+                        float* x, float* scale, float* lagrange, float* eta, void* stream);
+
+/* Gradient of the mean squared error of y[field[r]] against target[r] over the rows
+ * batch[0 .. B-1] of x (all device; batch holds row indices). grad: device FP32
+ * [SWENSE_MLP_NPARAM] (overwritten); loss: device scalar or NULL. Uses the workspace. */
+int swense_mlp_grad(const void* packed, const float* x, const int32_t* field, const float* target,
+                    const int32_t* batch, int32_t B, float* grad, float* loss, void* stream);
+
+/* One Adam step (Kingma & Ba; bias-corrected, step >= 1) of the FP32 params with moments
+ * adam_m, adam_v (device FP32 [SWENSE_MLP_NPARAM]) on the batch, then refreshes packed.
+ * Uses the workspace. Errors: ARG, OOM, CUDA. */
+int swense_mlp_train_step(float* params, float* adam_m, float* adam_v, void* packed, int64_t step,
+                          const float* x, const int32_t* field, const float* target,
+                          const int32_t* batch, int32_t B, float lr, float beta1, float beta2,
+                          float eps, float* loss, void* stream);
+
+/* swense_interp with the learned correction applied to u, v, w and dphi/dt (eta plain).
+ * Same arguments and out-of-range rules as swense_interp plus the packed weights; 3-D grids
+ * only. Uses the workspace (about 0.6 GB for the largest point chunk). */
+int swense_interp_learned(const swense_grid* grid, double t, const float* pts, int64_t np,
+                          float* eta, float* u, float* v, float* w, float* p, int32_t p_mode,
+                          double rho, double g, const void* packed, int64_t* n_out_of_range,
+                          void* stream);
+
+/*
  * swense_fv_divergence — the finite-volume divergence of the reconstruction-error subsection:
  * div_c = sum_f s_cf (u_f . A_f) / V_c with the face-centre velocity standing for the face
  * average (error source 1 of that subsection).

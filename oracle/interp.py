@@ -100,3 +100,35 @@ def interp_points(nodes_tl, eta_tl, Lx, Ly, z_levels, t_levels, pts, t,
 def time_weights(t_levels, t):
     """Lagrange weights over the time levels at time t."""
     return lagrange_basis(np.asarray(t_levels, np.float64), np.float64(t))
+
+
+def stencil_features(nodes_tl, Lx, Ly, z_levels, t_levels, pts, t):
+    """Time-blended 4x4x4 stencil of each point for the learned correction's inputs.
+
+    Returns stencil [n][4 fields][64] (node order x fastest, then y, then z, as the Lagrange
+    sum above), offsets [n][3] = (fx, fy, fz) with fz measured in the stencil's middle level
+    interval [z_{j0+1}, z_{j0+2}], and the plain interpolated values [n][4].
+    """
+    nodes_tl = np.asarray(nodes_tl, np.float64)
+    TL, nz, nyr, nxr, _ = nodes_tl.shape
+    pts = np.asarray(pts, np.float64)
+    n = len(pts)
+    wt = lagrange_basis(np.asarray(t_levels, np.float64), np.float64(t))
+    G = np.tensordot(wt, nodes_tl, axes=(0, 0))
+    ix, wx = _periodic_stencil(pts[:, 0], Lx, nxr)
+    iy, wy = _periodic_stencil(pts[:, 1], Ly, nyr)
+    j0, wz, _ = level_stencil(pts[:, 2], z_levels)
+    zl = np.asarray(z_levels, np.float64)
+    st = np.zeros((n, 4, 64))
+    lag = np.zeros((n, 4))
+    for a in range(4):
+        for b in range(4):
+            for c in range(4):
+                v = G[j0 + a, iy[:, b], ix[:, c]]                     # [n][4]
+                st[:, :, (a * 4 + b) * 4 + c] = v
+                lag += (wz[:, a] * wy[:, b] * wx[:, c])[:, None] * v
+    sx = pts[:, 0] * (nxr / Lx)
+    sy = pts[:, 1] * (nyr / Ly)
+    fz = (pts[:, 2] - zl[j0 + 1]) / (zl[j0 + 2] - zl[j0 + 1])
+    off = np.stack([sx - np.floor(sx), sy - np.floor(sy), fz], 1)
+    return st, off, lag

@@ -64,6 +64,11 @@ _SIGS = {
                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.c_int32, ctypes.c_double, ctypes.c_double,
                                      ctypes.c_void_p, ctypes.c_void_p]),
+    "swense_direct": (ctypes.c_int, [ctypes.POINTER(swense_modes), ctypes.c_double, ctypes.c_void_p,
+                                     ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_int32, ctypes.c_void_p]),
     "swense_fv_divergence": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                             ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                                             ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
@@ -176,6 +181,16 @@ def swense_interp(grid, t, pts, np_, eta=None, u=None, v=None, w=None, p=None, p
     return cnt.value if count_out_of_range else None
 
 
+DIRECT_FP32, DIRECT_SPLIT_BF16 = 0, 1
+
+
+def swense_direct(modes, t, pts, np_, eta=None, u=None, v=None, w=None, p=None, p_mode=P_DYN,
+                  rho=1000.0, g=9.81, precision=DIRECT_FP32, stream=None):
+    lib = load()
+    _check(lib.swense_direct(ctypes.byref(modes), t, _ptr(pts), np_, _ptr(eta), _ptr(u), _ptr(v),
+                             _ptr(w), _ptr(p), p_mode, rho, g, precision, _stream(stream)))
+
+
 def swense_fv_divergence(u_face, v_face, w_face, n_faces, area, cell_faces, cell_volume, n_cells,
                          div, stream=None):
     lib = load()
@@ -202,3 +217,101 @@ def swense_version():
 
 def swense_launches():
     return load().swense_launches()
+
+
+# ------------------------------------------------------------------ learned correction (MLP)
+MLP_NPARAM, MLP_PACKED_BYTES, MLP_XLD = 8772, 32768, 68
+
+_SIGS.update({
+    "swense_mlp_pack": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_float, ctypes.c_void_p,
+                                       ctypes.c_void_p]),
+    "swense_mlp_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                          ctypes.c_void_p, ctypes.c_void_p]),
+    "swense_mlp_features": (ctypes.c_int, [ctypes.POINTER(swense_grid), ctypes.c_double,
+                                           ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_void_p]),
+    "swense_mlp_grad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "swense_mlp_train_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_int32, ctypes.c_float, ctypes.c_float,
+                                             ctypes.c_float, ctypes.c_float, ctypes.c_void_p,
+                                             ctypes.c_void_p]),
+    "swense_interp_learned": (ctypes.c_int, [ctypes.POINTER(swense_grid), ctypes.c_double,
+                                             ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_int32, ctypes.c_double,
+                                             ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_void_p]),
+})
+
+
+def swense_mlp_pack(params, out_scale, packed, stream=None):
+    _check(load().swense_mlp_pack(_ptr(params), out_scale, _ptr(packed), _stream(stream)))
+
+
+def swense_mlp_forward(packed, x, rows, y, stream=None):
+    _check(load().swense_mlp_forward(_ptr(packed), _ptr(x), rows, _ptr(y), _stream(stream)))
+
+
+def swense_mlp_features(grid, t, pts, np_, x, scale, lagrange, eta=None, stream=None):
+    _check(load().swense_mlp_features(ctypes.byref(grid), t, _ptr(pts), np_, _ptr(x), _ptr(scale),
+                                      _ptr(lagrange), _ptr(eta), _stream(stream)))
+
+
+def swense_mlp_grad(packed, x, field, target, batch, B, grad, loss=None, stream=None):
+    _check(load().swense_mlp_grad(_ptr(packed), _ptr(x), _ptr(field), _ptr(target), _ptr(batch), B,
+                                  _ptr(grad), _ptr(loss), _stream(stream)))
+
+
+def swense_mlp_train_step(params, adam_m, adam_v, packed, step, x, field, target, batch, B, lr,
+                          beta1=0.9, beta2=0.999, eps=1e-8, loss=None, stream=None):
+    _check(load().swense_mlp_train_step(_ptr(params), _ptr(adam_m), _ptr(adam_v), _ptr(packed),
+                                        step, _ptr(x), _ptr(field), _ptr(target), _ptr(batch), B,
+                                        lr, beta1, beta2, eps, _ptr(loss), _stream(stream)))
+
+
+def swense_interp_learned(grid, t, pts, np_, packed, eta=None, u=None, v=None, w=None, p=None,
+                          p_mode=P_DYN, rho=1000.0, g=9.81, count_out_of_range=False,
+                          stream=None):
+    lib = load()
+    cnt = ctypes.c_int64(-1)
+    _check(lib.swense_interp_learned(ctypes.byref(grid), t, _ptr(pts), np_, _ptr(eta), _ptr(u),
+                                     _ptr(v), _ptr(w), _ptr(p), p_mode, rho, g, _ptr(packed),
+                                     ctypes.byref(cnt) if count_out_of_range else None,
+                                     _stream(stream)))
+    return cnt.value if count_out_of_range else None
+
+
+# ------------------------------------------------------------------ point binning
+_SIGS.update({
+    "swense_bin_points": (ctypes.c_int, [ctypes.POINTER(swense_grid), ctypes.c_void_p,
+                                         ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p]),
+    "swense_interp_permuted": (ctypes.c_int, [ctypes.POINTER(swense_grid), ctypes.c_double,
+                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                              ctypes.c_double, ctypes.c_double, ctypes.c_void_p,
+                                              ctypes.c_void_p]),
+})
+
+
+def swense_bin_points(grid, pts, np_, perm, pts_sorted, stream=None):
+    _check(load().swense_bin_points(ctypes.byref(grid), _ptr(pts), np_, _ptr(perm),
+                                    _ptr(pts_sorted), _stream(stream)))
+
+
+def swense_interp_permuted(grid, t, pts_sorted, perm, np_, eta=None, u=None, v=None, w=None,
+                           p=None, p_mode=P_DYN, rho=1000.0, g=9.81, count_out_of_range=False,
+                           stream=None):
+    lib = load()
+    cnt = ctypes.c_int64(-1)
+    _check(lib.swense_interp_permuted(ctypes.byref(grid), t, _ptr(pts_sorted), _ptr(perm), np_,
+                                      _ptr(eta), _ptr(u), _ptr(v), _ptr(w), _ptr(p), p_mode, rho,
+                                      g, ctypes.byref(cnt) if count_out_of_range else None,
+                                      _stream(stream)))
+    return cnt.value if count_out_of_range else None

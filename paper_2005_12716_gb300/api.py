@@ -102,8 +102,160 @@ def interp(grid, t, pts, p_mode="dyn", rho=1000.0, g=9.81, out=None, count_out_o
     return out, cnt
 
 
+def direct(modes, t, pts, p_mode="dyn", rho=1000.0, g=9.81, precision="fp32", out=None,
+           stream=None):
+    """swense_direct: exact modal sums at the points; returns dict of float32 device tensors."""
+    n = pts.shape[0]
+    if out is None:
+        out = {k: torch.empty(n, dtype=torch.float32, device=pts.device)
+               for k in ("eta", "u", "v", "w", "p")}
+    prec = {"fp32": S.DIRECT_FP32, "split_bf16": S.DIRECT_SPLIT_BF16}[precision]
+    S.swense_direct(modes.c_struct(), float(t), pts, n, out.get("eta"), out.get("u"), out.get("v"),
+                    out.get("w"), out.get("p"), S.P_MODES[p_mode], rho, g, prec, stream)
+    return out
+
+
 def fv_divergence(u, v, w, area, cell_faces, cell_volume, out=None, stream=None):
     nc = cell_volume.shape[0]
     div = out if out is not None else torch.empty(nc, dtype=torch.float32, device=u.device)
     S.swense_fv_divergence(u, v, w, u.shape[0], area, cell_faces, cell_volume, nc, div, stream)
     return div
+
+
+# ------------------------------------------------------------------ learned correction (MLP)
+MLP_NPARAM, MLP_XLD = S.MLP_NPARAM, S.MLP_XLD
+_MLP_SHAPES = (("W1", (64, 67)), ("b1", (64,)), ("W2", (64, 64)), ("b2", (64,)), ("W3", (4, 64)),
+               ("b3", (4,)))
+
+
+def mlp_flatten(p):
+    """Dict of arrays (W1 [64][67], b1, W2, b2, W3 [4][64], b3) -> packed FP32 vector."""
+    return np.concatenate([np.asarray(p[k], np.float64).reshape(-1) for k, _ in _MLP_SHAPES]).astype(np.float32)
+
+
+def mlp_unflatten(v):
+    out, o = {}, 0
+    for k, shp in _MLP_SHAPES:
+        n = int(np.prod(shp))
+        out[k] = np.asarray(v[o:o + n], np.float64).reshape(shp)
+        o += n
+    return out
+
+
+def mlp_init(seed=0, device="cuda"):
+    """Seeded initial parameters: W ~ N(0, 1/fan_in), biases 0; returns the FP32 device vector."""
+    rng = np.random.default_rng(seed)
+    p = {}
+    for k, shp in _MLP_SHAPES:
+        p[k] = rng.standard_normal(shp) / np.sqrt(shp[1]) if k.startswith("W") else np.zeros(shp)
+    return torch.from_numpy(mlp_flatten(p)).to(device)
+
+
+class Mlp:
+    """FP32 parameters + Adam moments + the packed BF16 copy the kernels read."""
+
+    def __init__(self, params, device="cuda", out_scale=1.0):
+        self.params = params.to(device).contiguous()
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+        self.packed = torch.zeros(S.MLP_PACKED_BYTES // 4, dtype=torch.float32, device=device)
+        self.step = 0
+        self.seed = 0
+        self.out_scale = float(out_scale)
+        S.swense_mlp_pack(self.params, self.out_scale, self.packed)
+
+    def set_out_scale(self, out_scale):
+        """Output multiplier used at inference (train on targets divided by it)."""
+        self.out_scale = float(out_scale)
+        S.swense_mlp_pack(self.params, self.out_scale, self.packed)
+
+    def forward(self, x, out=None):
+        y = out if out is not None else torch.empty(x.shape[0], dtype=torch.float32, device=x.device)
+        S.swense_mlp_forward(self.packed, x, x.shape[0], y)
+        return y
+
+    def grad(self, x, field, target, batch):
+        g = torch.empty(S.MLP_NPARAM, dtype=torch.float32, device=x.device)
+        loss = torch.empty(1, dtype=torch.float32, device=x.device)
+        S.swense_mlp_grad(self.packed, x, field, target, batch, batch.shape[0], g, loss)
+        return g, loss
+
+    def train_step(self, x, field, target, batch, lr=1e-3, loss=None):
+        self.step += 1
+        S.swense_mlp_train_step(self.params, self.m, self.v, self.packed, self.step, x, field,
+                                target, batch, batch.shape[0], lr, loss=loss)
+
+    # checkpoint: little-endian, header "SWMLP002", int64 step, uint64 seed, int64 nparam,
+    # float64 out_scale, then params, adam m, adam v as float32
+    def save(self, path):
+        with open(path, "wb") as fh:
+            fh.write(b"SWMLP002")
+            fh.write(np.array([self.step], "<i8").tobytes())
+            fh.write(np.array([self.seed], "<u8").tobytes())
+            fh.write(np.array([S.MLP_NPARAM], "<i8").tobytes())
+            fh.write(np.array([self.out_scale], "<f8").tobytes())
+            for t in (self.params, self.m, self.v):
+                fh.write(t.detach().cpu().numpy().astype("<f4").tobytes())
+
+    @classmethod
+    def load(cls, path, device="cuda"):
+        with open(path, "rb") as fh:
+            if fh.read(8) != b"SWMLP002":
+                raise ValueError("not a swense MLP checkpoint")
+            step = int(np.frombuffer(fh.read(8), "<i8")[0])
+            seed = int(np.frombuffer(fh.read(8), "<u8")[0])
+            n = int(np.frombuffer(fh.read(8), "<i8")[0])
+            if n != S.MLP_NPARAM:
+                raise ValueError("parameter count mismatch")
+            out_scale = float(np.frombuffer(fh.read(8), "<f8")[0])
+            arrs = [np.frombuffer(fh.read(4 * n), "<f4").copy() for _ in range(3)]
+        m = cls(torch.from_numpy(arrs[0]), device, out_scale)
+        m.m.copy_(torch.from_numpy(arrs[1]))
+        m.v.copy_(torch.from_numpy(arrs[2]))
+        m.step, m.seed = step, seed
+        return m
+
+
+def mlp_features(grid, t, pts, stream=None):
+    """swense_mlp_features -> (x [4n][68], scale [4n], lagrange [4n], eta [n])."""
+    n = pts.shape[0]
+    dev = pts.device
+    x = torch.empty((4 * n, S.MLP_XLD), dtype=torch.float32, device=dev)
+    sc = torch.empty(4 * n, dtype=torch.float32, device=dev)
+    lg = torch.empty(4 * n, dtype=torch.float32, device=dev)
+    eta = torch.empty(n, dtype=torch.float32, device=dev)
+    S.swense_mlp_features(grid.c_struct(), float(t), pts, n, x, sc, lg, eta, stream)
+    return x, sc, lg, eta
+
+
+def interp_learned(grid, t, pts, mlp, p_mode="dyn", rho=1000.0, g=9.81, out=None,
+                   count_out_of_range=False, stream=None):
+    n = pts.shape[0]
+    if out is None:
+        out = {k: torch.empty(n, dtype=torch.float32, device=pts.device)
+               for k in ("eta", "u", "v", "w", "p")}
+    cnt = S.swense_interp_learned(grid.c_struct(), float(t), pts, n, mlp.packed, out.get("eta"),
+                                  out.get("u"), out.get("v"), out.get("w"), out.get("p"),
+                                  S.P_MODES[p_mode], rho, g, count_out_of_range, stream)
+    return out, cnt
+
+
+def bin_points(grid, pts, stream=None):
+    """swense_bin_points -> (perm int32 [n], pts_sorted float32 [n][3])."""
+    n = pts.shape[0]
+    perm = torch.empty(n, dtype=torch.int32, device=pts.device)
+    srt = torch.empty((n, 3), dtype=torch.float32, device=pts.device)
+    S.swense_bin_points(grid.c_struct(), pts, n, perm, srt, stream)
+    return perm, srt
+
+
+def interp_permuted(grid, t, pts_sorted, perm, p_mode="dyn", rho=1000.0, g=9.81, out=None,
+                    count_out_of_range=False, stream=None):
+    n = pts_sorted.shape[0]
+    if out is None:
+        out = {k: torch.empty(n, dtype=torch.float32, device=pts_sorted.device)
+               for k in ("eta", "u", "v", "w", "p")}
+    cnt = S.swense_interp_permuted(grid.c_struct(), float(t), pts_sorted, perm, n, out.get("eta"),
+                                   out.get("u"), out.get("v"), out.get("w"), out.get("p"),
+                                   S.P_MODES[p_mode], rho, g, count_out_of_range, stream)
+    return out, cnt

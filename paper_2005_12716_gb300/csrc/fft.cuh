@@ -76,3 +76,100 @@ __device__ __forceinline__ void depth_factors(float k, float z, float h, float& 
 }
 
 }  // namespace swense
+
+namespace swense {
+
+// ------------------------------------------------------------------------------------------------
+// Warp-register inverse DFT of length N = 32 * E (E <= 32), one transform per warp.
+//
+// With n = n1 + 32 n2 (n1 = lane, n2 < E) and m = m2 + E m1 (m2 < E, m1 < 32):
+//   X[m] = sum_{n1} e^{2 pi i n1 m1 / 32} [ e^{2 pi i n1 m2 / N} sum_{n2} x[n1 + 32 n2] e^{2 pi i n2 m2 / E} ]
+// so each lane does a length-E DFT over its own elements in registers, multiplies by the
+// lane's twiddles, and the warp does E length-32 DFTs across lanes (radix-2 decimation in
+// frequency with shuffles). Lane l ends up with X[m2 + E * bitrev5(l)], m2 = 0 .. E-1: E
+// consecutive outputs, ready for a contiguous store.
+
+constexpr int ct_log2(int v) { return v <= 1 ? 0 : 1 + ct_log2(v >> 1); }
+constexpr int ct_rev(int v, int bits) {
+  int r = 0;
+  for (int b = 0; b < bits; ++b) r |= ((v >> b) & 1) << (bits - 1 - b);
+  return r;
+}
+
+// Per-lane constants of one transform size (kernel-lifetime registers).
+template <int E>
+struct WarpFftTw {
+  float2 wE[E > 1 ? E / 2 : 1];   // e^{2 pi i j / E}, j < E/2
+  float2 w2[E];                   // e^{2 pi i lane m2 / N}
+  float2 ws[5];                   // e^{2 pi i (lane mod s) / (2 s)}, s = 16, 8, 4, 2, 1
+};
+
+template <int E>
+__device__ __forceinline__ void warp_fft_init(WarpFftTw<E>& T, const float2* __restrict__ tw, int lane) {
+  constexpr int N = 32 * E;
+#pragma unroll
+  for (int j = 0; j < (E > 1 ? E / 2 : 1); ++j) T.wE[j] = __ldg(&tw[j * (SWENSE_MAX_FFT / (E > 1 ? E : 2))]);
+#pragma unroll
+  for (int m2 = 0; m2 < E; ++m2) T.w2[m2] = __ldg(&tw[(lane * m2) * (SWENSE_MAX_FFT / N)]);
+#pragma unroll
+  for (int st = 0; st < 5; ++st) {
+    const int s = 16 >> st;
+    T.ws[st] = __ldg(&tw[(lane % s) * (SWENSE_MAX_FFT / (2 * s))]);
+  }
+}
+
+// In-register length-E inverse DFT, natural order in and out (iterative radix-2 DIT).
+template <int E>
+__device__ __forceinline__ void dft_reg(float2 (&v)[E], const float2 (&wE)[E > 1 ? E / 2 : 1]) {
+  constexpr int B = ct_log2(E);
+#pragma unroll
+  for (int i = 0; i < E; ++i) {
+    const int j = ct_rev(i, B);
+    if (j > i) {
+      const float2 t = v[i];
+      v[i] = v[j];
+      v[j] = t;
+    }
+  }
+#pragma unroll
+  for (int len = 2; len <= E; len <<= 1) {
+    const int half = len >> 1;
+#pragma unroll
+    for (int i = 0; i < E; i += len) {
+#pragma unroll
+      for (int j = 0; j < half; ++j) {
+        const float2 b = v[i + j + half];
+        const float2 t = j == 0 ? b : cmul(wE[j * (E / len)], b);
+        v[i + j + half] = csub(v[i + j], t);
+        v[i + j] = cadd(v[i + j], t);
+      }
+    }
+  }
+}
+
+// Full warp transform: register DFT, lane twiddles, cross-lane length-32 DFT.
+template <int E>
+__device__ __forceinline__ void warp_fft(float2 (&v)[E], const WarpFftTw<E>& T, int lane) {
+  dft_reg<E>(v, T.wE);
+#pragma unroll
+  for (int m2 = 1; m2 < E; ++m2) v[m2] = cmul(v[m2], T.w2[m2]);
+#pragma unroll
+  for (int st = 0; st < 5; ++st) {
+    const int s = 16 >> st;
+    // lower lane: v + o; upper lane: (o - v) * w. Written as (o + sgn v) * w with sgn = -1 and
+    // w = ws on upper lanes, sgn = +1 and w = 1 on lower lanes (no branch, no select per element)
+    const bool upper = (lane & s) != 0;
+    const float sgn = upper ? -1.f : 1.f;
+    const float2 w = upper ? T.ws[st] : make_float2(1.f, 0.f);
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      float2 o;
+      o.x = __shfl_xor_sync(0xffffffffu, v[m].x, s);
+      o.y = __shfl_xor_sync(0xffffffffu, v[m].y, s);
+      const float2 r = make_float2(fmaf(sgn, v[m].x, o.x), fmaf(sgn, v[m].y, o.y));
+      v[m] = s > 1 ? cmul(r, w) : r;
+    }
+  }
+}
+
+}  // namespace swense

@@ -226,12 +226,185 @@ __global__ void k_propagate(const float2* __restrict__ Ae, const float2* __restr
 constexpr int kThreads = 256;
 constexpr size_t kSmemBudget = 64 * 1024;
 constexpr size_t kChunkBytes = size_t(32) << 20;
+constexpr int kColBlock = 8;    // kx columns per column-transform CTA
+constexpr int kColLevels = 2;   // levels per column-transform CTA
+constexpr int kRowBlock = 8;    // grid rows per row-transform CTA (one per warp)
 
 int set_smem(const void* fn, size_t bytes) {
   SWENSE_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes)));
   return SWENSE_OK;
 }
 
+
+// ------------------------------------------------------------------------------------------------
+// Warp-register path for 32 <= ny_r, nx_r <= 1024 (one transform per warp, no shared-memory
+// butterflies). Intermediate layout G2[level][field][m][y] (y contiguous): a column transform
+// writes its warp's outputs as contiguous runs; the row kernel stages rb rows of all m.
+
+// 8-byte asynchronous global -> shared copy (zero-filled when src_bytes == 0).
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, int src_bytes) {
+  const unsigned d = unsigned(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(gmem), "r"(src_bytes));
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
+struct ColArgs {
+  const float2* A_phi;   // [ny][nxh1] of this time level
+  const float2* A_phit;
+  float2* G;             // [nlev][4][Mh][Nyr]
+  const float2* tw;
+  int ny, nxh1, Mh, Nyr;
+  int cb, lpc;           // kx columns and levels per CTA
+  int lev0, nlev;        // chunk
+  float kxs, kys, depth;
+};
+
+// Modal field q at (kx, ky, |k|) with depth factors F, S: U = i kx F A, V = i ky F A,
+// W = |k| S A, T = F A_t.
+__device__ __forceinline__ float2 modal_field(int q, float kx, float ky, float k, float F, float S,
+                                              float2 Ap, float2 At) {
+  if (q == 0) return make_float2(-kx * F * Ap.y, kx * F * Ap.x);
+  if (q == 1) return make_float2(-ky * F * Ap.y, ky * F * Ap.x);
+  if (q == 2) return make_float2(k * S * Ap.x, k * S * Ap.y);
+  return make_float2(F * At.x, F * At.y);
+}
+
+template <int E, int NF>
+__global__ void __launch_bounds__(256, 2) k_col_fft(ColArgs a, Levels L) {
+  extern __shared__ float2 sm[];                 // [2][ny][cb + 1]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c0 = blockIdx.x * a.cb;
+  const int ncol = min(a.cb, a.Mh - c0);
+  const int ld = a.cb + 1;
+  for (int i = threadIdx.x; i < a.ny * a.cb; i += blockDim.x) {
+    const int c = i % a.cb, r = i / a.cb;
+    const bool ok = c < ncol;
+    const size_t gi = ok ? size_t(r) * a.nxh1 + c0 + c : 0;
+    cp_async8(&sm[r * ld + c], &a.A_phi[gi], ok ? 8 : 0);
+    cp_async8(&sm[(a.ny + r) * ld + c], &a.A_phit[gi], ok ? 8 : 0);
+  }
+  WarpFftTw<E> T;
+  warp_fft_init<E>(T, a.tw, lane);
+  cp_async_wait_all();
+  __syncthreads();
+  const int nyh = a.ny >> 1;
+  const int groups = 4 / NF;
+  const int ntask = a.lpc * ncol * groups;
+  for (int task = warp; task < ntask; task += blockDim.x >> 5) {
+    const int g = task % groups;
+    const int rest = task / groups;
+    const int c = rest % ncol;
+    const int level = blockIdx.y * a.lpc + rest / ncol;
+    if (level >= a.nlev) continue;
+    const float z = L.z[a.lev0 + level];
+    const int m = c0 + c;
+    const float kx = float(m) * a.kxs;
+    float2 v[NF][E];
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+      const int p = lane + 32 * k;
+      int n;
+      bool live = true;
+      if (p < nyh) n = p;
+      else if (p > a.Nyr - nyh) n = p - a.Nyr;
+      else { n = 0; live = false; }
+      float2 Ap = make_float2(0.f, 0.f), At = make_float2(0.f, 0.f);
+      if (live) {
+        const int r = n >= 0 ? n : a.ny + n;
+        Ap = sm[r * ld + c];
+        At = sm[(a.ny + r) * ld + c];
+      }
+      const float ky = float(n) * a.kys;
+      const float kk = sqrtf(kx * kx + ky * ky);
+      float F, S;
+      depth_factors(kk, z, a.depth, F, S);
+#pragma unroll
+      for (int f = 0; f < NF; ++f) v[f][k] = modal_field(g * NF + f, kx, ky, kk, F, S, Ap, At);
+    }
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      warp_fft<E>(v[f], T, lane);
+      float2* out = a.G + ((size_t(level) * 4 + g * NF + f) * a.Mh + m) * a.Nyr +
+                    E * int(bitrev(unsigned(lane), 5));
+#pragma unroll
+      for (int m2 = 0; m2 < E; m2 += 2) {
+        if (E == 1) {
+          out[0] = v[f][0];
+        } else {
+          __stcg(reinterpret_cast<float4*>(out + m2),
+                 make_float4(v[f][m2].x, v[f][m2].y, v[f][m2 + 1].x, v[f][m2 + 1].y));
+        }
+      }
+    }
+  }
+}
+
+struct RowArgs {
+  const float2* G;       // [nlev][4][Mh][Nyr]
+  float4* nodes;         // [nz][Nyr][Nxr] of this time level
+  const float2* tw;
+  int Mh, Nxr, Nyr, rb, lev0;
+};
+
+template <int E>
+__global__ void __launch_bounds__(256, 2) k_row_fft(RowArgs a) {
+  extern __shared__ float2 sm[];                 // [4][Mh][rb + 1]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int y0 = blockIdx.x * a.rb;
+  const int level = blockIdx.y;
+  const int ld = a.rb + 1;
+  const float2* G = a.G + size_t(level) * 4 * a.Mh * a.Nyr;
+  for (int i = threadIdx.x; i < 4 * a.Mh * a.rb; i += blockDim.x) {
+    const int rr = i % a.rb, qm = i / a.rb;
+    const int y = y0 + rr;
+    cp_async8(&sm[qm * ld + rr], &G[size_t(qm) * a.Nyr + (y < a.Nyr ? y : 0)], y < a.Nyr ? 8 : 0);
+  }
+  WarpFftTw<E> T;
+  warp_fft_init<E>(T, a.tw, lane);
+  cp_async_wait_all();
+  __syncthreads();
+  for (int rr = warp; rr < a.rb; rr += blockDim.x >> 5) {
+    const int y = y0 + rr;
+    if (y >= a.Nyr) break;
+    float2 z1[E], z2[E];
+    const size_t fs = size_t(a.Mh) * ld;
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+      const int p = lane + 32 * k;
+      int m = -1;
+      bool mirror = false;
+      if (p < a.Mh) m = p;
+      else if (p > a.Nxr - a.Mh) { m = a.Nxr - p; mirror = true; }
+      float2 U = make_float2(0.f, 0.f), V = U, W = U, Tt = U;
+      if (m >= 0) {
+        const size_t o = size_t(m) * ld + rr;
+        U = sm[o];
+        V = sm[o + fs];
+        W = sm[o + 2 * fs];
+        Tt = sm[o + 3 * fs];
+      }
+      // Hermitian packing of two real fields into one complex spectrum (p + i q)
+      if (p == 0) {
+        z1[k] = make_float2(U.x, V.x);
+        z2[k] = make_float2(W.x, Tt.x);
+      } else if (!mirror) {
+        z1[k] = make_float2(U.x - V.y, U.y + V.x);
+        z2[k] = make_float2(W.x - Tt.y, W.y + Tt.x);
+      } else {
+        z1[k] = make_float2(U.x + V.y, V.x - U.y);
+        z2[k] = make_float2(W.x + Tt.y, Tt.x - W.y);
+      }
+    }
+    warp_fft<E>(z1, T, lane);
+    warp_fft<E>(z2, T, lane);
+    float4* out = a.nodes + (size_t(a.lev0 + level) * a.Nyr + y) * a.Nxr + E * int(bitrev(unsigned(lane), 5));
+#pragma unroll
+    for (int m2 = 0; m2 < E; ++m2)
+      __stcs(&out[m2], make_float4(z1[m2].x, z1[m2].y, z2[m2].x, z2[m2].y));
+  }
+}
 
 // Validated sizes and derived constants of one swense_fields_on_grid request.
 struct GridPlan {
@@ -240,6 +413,55 @@ struct GridPlan {
   size_t nslot, per_level, prop_bytes, geta_bytes;
   Levels lev;
 };
+
+template <int E, int NF>
+int launch_col(const ColArgs& c, const Levels& L, dim3 grid, size_t smem, cudaStream_t stream) {
+  int st = set_smem((const void*)k_col_fft<E, NF>, smem);
+  if (st) return st;
+  k_col_fft<E, NF><<<grid, kThreads, smem, stream>>>(c, L);
+  SWENSE_CUDA_TRY(cudaGetLastError());
+  count_launches(1);
+  return SWENSE_OK;
+}
+
+int launch_col_e(int E, const ColArgs& c, const Levels& L, dim3 grid, size_t smem, cudaStream_t s) {
+  switch (E) {
+    case 1: return launch_col<1, 4>(c, L, grid, smem, s);
+    case 2: return launch_col<2, 4>(c, L, grid, smem, s);
+    case 4: return launch_col<4, 4>(c, L, grid, smem, s);
+    case 8: return launch_col<8, 2>(c, L, grid, smem, s);
+    case 16: return launch_col<16, 2>(c, L, grid, smem, s);
+    case 32: return launch_col<32, 1>(c, L, grid, smem, s);
+    default: return fail(SWENSE_ERR_UNSUPPORTED, "column transform size");
+  }
+}
+
+template <int E>
+int launch_row(const RowArgs& r, dim3 grid, size_t smem, cudaStream_t stream) {
+  int st = set_smem((const void*)k_row_fft<E>, smem);
+  if (st) return st;
+  k_row_fft<E><<<grid, kThreads, smem, stream>>>(r);
+  SWENSE_CUDA_TRY(cudaGetLastError());
+  count_launches(1);
+  return SWENSE_OK;
+}
+
+int launch_row_e(int E, const RowArgs& r, dim3 grid, size_t smem, cudaStream_t s) {
+  switch (E) {
+    case 1: return launch_row<1>(r, grid, smem, s);
+    case 2: return launch_row<2>(r, grid, smem, s);
+    case 4: return launch_row<4>(r, grid, smem, s);
+    case 8: return launch_row<8>(r, grid, smem, s);
+    case 16: return launch_row<16>(r, grid, smem, s);
+    case 32: return launch_row<32>(r, grid, smem, s);
+    default: return fail(SWENSE_ERR_UNSUPPORTED, "row transform size");
+  }
+}
+
+// The warp-register path covers 32 <= ny_r, nx_r <= 1024 (3-D only).
+bool warp_path(int ny, int64_t Nxr, int64_t Nyr) {
+  return ny > 1 && Nyr >= 32 && Nyr <= 1024 && Nxr >= 32 && Nxr <= 1024;
+}
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
@@ -422,6 +644,45 @@ int launch_grid(const GridPlan& p, const swense_modes* md, const double* t, floa
     SWENSE_CUDA_TRY(cudaGetLastError());
     count_launches(1);
 
+    if (warp_path(ny, Nxr, Nyr)) {
+      ColArgs ca{};
+      ca.A_phi = Ap;
+      ca.A_phit = At;
+      ca.G = g_lev;
+      ca.tw = tw;
+      ca.ny = ny;
+      ca.nxh1 = nxh1;
+      ca.Mh = Mh;
+      ca.Nyr = int(Nyr);
+      ca.cb = kColBlock;
+      ca.lpc = kColLevels;
+      ca.kxs = kxs;
+      ca.kys = kys;
+      ca.depth = depth;
+      RowArgs ra{};
+      ra.G = g_lev;
+      ra.nodes = nodes_l;
+      ra.tw = tw;
+      ra.Mh = Mh;
+      ra.Nxr = int(Nxr);
+      ra.Nyr = int(Nyr);
+      ra.rb = kRowBlock;
+      const size_t smem_col = size_t(2) * ny * (kColBlock + 1) * sizeof(float2);
+      const size_t smem_row = size_t(4) * Mh * (kRowBlock + 1) * sizeof(float2);
+      for (int l0 = 0; l0 < nz; l0 += chunk) {
+        const int nl = std::min(chunk, nz - l0);
+        ca.lev0 = l0;
+        ca.nlev = nl;
+        ra.lev0 = l0;
+        int st = launch_col_e(int(Nyr / 32), ca, p.lev,
+                              dim3((Mh + kColBlock - 1) / kColBlock, (nl + kColLevels - 1) / kColLevels),
+                              smem_col, stream);
+        if (!st) st = launch_row_e(int(Nxr / 32), ra,
+                                   dim3(unsigned((Nyr + kRowBlock - 1) / kRowBlock), nl), smem_row, stream);
+        if (st) return st;
+      }
+      continue;
+    }
     a.eta_mode = 0;
     a.fp = fp;
     a.cb = cb;

@@ -30,6 +30,7 @@ struct InterpArgs {
   float* o_w;
   float* o_p;
   unsigned long long* n_oor;
+  const int32_t* perm;   // output index of each point (NULL: identity); points are pre-sorted
   int64_t np;
   int Nxr, Nyr, nz, n_tl;
   float sx_hi, sx_lo, sy_hi, sy_lo;   // nx_r / Lx and ny_r / Ly as hi + lo
@@ -66,13 +67,33 @@ __device__ __forceinline__ void lagrange4_uniform(float f, float w[4]) {
   w[3] = fp1 * f * fm1 * (1.f / 6.f);
 }
 
-// Lagrange basis of the 4 arbitrary nodes zn at z.
-__device__ __forceinline__ void lagrange4(const float zn[4], float z, float w[4]) {
+// Lagrange basis of the 4 arbitrary nodes zn at z; inv holds 1 / prod_{b != a} (zn[a] - zn[b]).
+__device__ __forceinline__ void lagrange4(const float zn[4], float4 inv, float z, float w[4]) {
   const float d0 = z - zn[0], d1 = z - zn[1], d2 = z - zn[2], d3 = z - zn[3];
-  w[0] = (d1 * d2 * d3) / ((zn[0] - zn[1]) * (zn[0] - zn[2]) * (zn[0] - zn[3]));
-  w[1] = (d0 * d2 * d3) / ((zn[1] - zn[0]) * (zn[1] - zn[2]) * (zn[1] - zn[3]));
-  w[2] = (d0 * d1 * d3) / ((zn[2] - zn[0]) * (zn[2] - zn[1]) * (zn[2] - zn[3]));
-  w[3] = (d0 * d1 * d2) / ((zn[3] - zn[0]) * (zn[3] - zn[1]) * (zn[3] - zn[2]));
+  w[0] = (d1 * d2 * d3) * inv.x;
+  w[1] = (d0 * d2 * d3) * inv.y;
+  w[2] = (d0 * d1 * d3) * inv.z;
+  w[3] = (d0 * d1 * d2) * inv.w;
+}
+
+// Shared-memory copy of the levels and, per stencil start j0, the inverse Lagrange
+// denominators of the levels j0 .. j0+3 (computed once per CTA: no divisions per point).
+struct LevelTables {
+  float z[SWENSE_MAX_LEVELS];
+  float4 inv[SWENSE_MAX_LEVELS];
+};
+
+__device__ __forceinline__ void fill_level_tables(LevelTables& T, const Levels& L, int nz) {
+  for (int i = threadIdx.x; i < nz; i += blockDim.x) T.z[i] = L.z[i];
+  for (int j = threadIdx.x; j <= nz - 4; j += blockDim.x) {
+    float zn[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) zn[q] = L.z[j + q];
+    T.inv[j] = make_float4(1.f / ((zn[0] - zn[1]) * (zn[0] - zn[2]) * (zn[0] - zn[3])),
+                           1.f / ((zn[1] - zn[0]) * (zn[1] - zn[2]) * (zn[1] - zn[3])),
+                           1.f / ((zn[2] - zn[0]) * (zn[2] - zn[1]) * (zn[2] - zn[3])),
+                           1.f / ((zn[3] - zn[0]) * (zn[3] - zn[1]) * (zn[3] - zn[2])));
+  }
 }
 
 // Stencil of one point: cell indices, Lagrange weights and the in-range flag.
@@ -82,8 +103,9 @@ struct PointCell {
   bool inside;
 };
 
-__device__ __forceinline__ PointCell point_cell(const InterpArgs& a, const float* zs, float x,
+__device__ __forceinline__ PointCell point_cell(const InterpArgs& a, const LevelTables& T, float x,
                                                 float y, float z) {
+  const float* zs = T.z;
   PointCell c;
   float fx;
   locate(x, a.sx_hi, a.sx_lo, a.Nxr, c.ix, fx);
@@ -109,7 +131,7 @@ __device__ __forceinline__ PointCell point_cell(const InterpArgs& a, const float
   float zn[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) zn[q] = zs[c.j0 + q];
-  lagrange4(zn, z, c.wz);
+  lagrange4(zn, T.inv[c.j0], z, c.wz);
   return c;
 }
 
@@ -132,10 +154,14 @@ __device__ __forceinline__ void gather_global(const InterpArgs& a, const PointCe
 #pragma unroll 1
     for (int q = 0; q < 4; ++q) {
       const float4* lev = base_t + size_t(c.j0 + q) * plane;
-      const float wzq = wtl * c.wz[q];
+      // select instead of a dynamic index so the weights stay in registers
+      const float wzq = wtl * (q == 0 ? c.wz[0] : q == 1 ? c.wz[1] : q == 2 ? c.wz[2] : c.wz[3]);
+#pragma unroll 1
       for (int b = 0; b < nys; ++b) {
-        const float4* row = lev + size_t(yi[b]) * a.Nxr;
-        const float wzy = wzq * c.wy[b];
+        const int yb = b == 0 ? yi[0] : b == 1 ? yi[1] : b == 2 ? yi[2] : yi[3];
+        const float wyb = b == 0 ? c.wy[0] : b == 1 ? c.wy[1] : b == 2 ? c.wy[2] : c.wy[3];
+        const float4* row = lev + size_t(yb) * a.Nxr;
+        const float wzy = wzq * wyb;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           const float4 gv = __ldg(&row[xi[k]]);
@@ -148,16 +174,20 @@ __device__ __forceinline__ void gather_global(const InterpArgs& a, const PointCe
       }
     }
     const float* et = a.eta + size_t(tl) * plane;
+#pragma unroll 1
     for (int b = 0; b < nys; ++b) {
-      const float* row = et + size_t(yi[b]) * a.Nxr;
+      const int yb = b == 0 ? yi[0] : b == 1 ? yi[1] : b == 2 ? yi[2] : yi[3];
+      const float wyb = b == 0 ? c.wy[0] : b == 1 ? c.wy[1] : b == 2 ? c.wy[2] : c.wy[3];
+      const float* row = et + size_t(yb) * a.Nxr;
 #pragma unroll
-      for (int k = 0; k < 4; ++k) acc_eta = fmaf(wtl * c.wy[b] * c.wx[k], __ldg(&row[xi[k]]), acc_eta);
+      for (int k = 0; k < 4; ++k) acc_eta = fmaf(wtl * wyb * c.wx[k], __ldg(&row[xi[k]]), acc_eta);
     }
   }
 }
 
 __device__ __forceinline__ void store_point(const InterpArgs& a, int64_t i, float4 acc,
                                             float acc_eta, float z, bool inside) {
+  if (a.perm) i = a.perm[i];
   if (!inside) {
     const float qnan = __int_as_float(0x7fc00000);
     acc = make_float4(qnan, qnan, qnan, qnan);
@@ -180,32 +210,16 @@ __device__ __forceinline__ void store_point(const InterpArgs& a, int64_t i, floa
   }
 }
 
-// One thread per point, stencils read from global memory. Used for scattered point sets.
-__global__ void __launch_bounds__(256, 3) k_interp(InterpArgs a, Levels L) {
-  __shared__ float zs[SWENSE_MAX_LEVELS];
-  for (int i = threadIdx.x; i < a.nz; i += blockDim.x) zs[i] = L.z[i];
-  __syncthreads();
-  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < a.np;
-       i += int64_t(gridDim.x) * blockDim.x) {
-    const float x = a.pts[3 * i], y = a.pts[3 * i + 1], z = a.pts[3 * i + 2];
-    const PointCell c = point_cell(a, zs, x, y, z);
-    float4 acc;
-    float acc_eta;
-    gather_global(a, c, acc, acc_eta);
-    store_point(a, i, acc, acc_eta, z, c.inside);
-  }
-}
-
 // Box-staged gather for spatially coherent point sets (mesh order). Each CTA takes BOX_PTS
 // consecutive points, finds the bounding box of their stencils, loads that box of the grid into
 // shared memory already blended in time (sum_t w_t G_t, exact reordering of the linear sums),
 // then evaluates every point from shared memory, where threads of a warp mostly share cells
 // (broadcast reads). A CTA whose box exceeds BOX_NODES falls back to global gathers.
 constexpr int BOX_THREADS = 256;
-constexpr int BOX_PPT = 2;                         // points per thread
+constexpr int BOX_PPT = 4;                         // points per thread
 constexpr int BOX_PTS = BOX_THREADS * BOX_PPT;
-constexpr int BOX_NODES = 4096;                    // float4 nodes (64 KB)
-constexpr int BOX_COLS = 2048;                     // eta columns (8 KB)
+constexpr int BOX_NODES = 3584;                    // float4 nodes (56 KB)
+constexpr int BOX_COLS = 1536;                     // eta columns (6 KB)
 constexpr size_t BOX_SMEM = size_t(BOX_NODES) * sizeof(float4) + size_t(BOX_COLS) * sizeof(float);
 
 __device__ __forceinline__ int wrap_rel(int i, int ref, int n) {
@@ -213,13 +227,23 @@ __device__ __forceinline__ int wrap_rel(int i, int ref, int n) {
   return ((i - ref + (n >> 1)) & (n - 1)) - (n >> 1);
 }
 
+// Two FP32 lanes packed in 64 bits for the Blackwell paired FMA (fma.rn.f32x2).
+__device__ __forceinline__ unsigned long long pack2(float a, float b) {
+  return (unsigned long long)__float_as_uint(a) | ((unsigned long long)__float_as_uint(b) << 32);
+}
+__device__ __forceinline__ void fma2(unsigned long long& acc, unsigned long long w, unsigned long long v) {
+  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(w), "l"(v));
+}
+__device__ __forceinline__ float lo2(unsigned long long v) { return __uint_as_float(unsigned(v)); }
+__device__ __forceinline__ float hi2(unsigned long long v) { return __uint_as_float(unsigned(v >> 32)); }
+
 __global__ void __launch_bounds__(BOX_THREADS, 3) k_interp_box(InterpArgs a, Levels L) {
   extern __shared__ float4 sbox[];
   float* seta = reinterpret_cast<float*>(sbox + BOX_NODES);
-  __shared__ float zs[SWENSE_MAX_LEVELS];
+  __shared__ LevelTables zs;
   __shared__ int s_red[6][BOX_THREADS / 32];
   __shared__ int s_ref[2];
-  for (int i = threadIdx.x; i < a.nz; i += blockDim.x) zs[i] = L.z[i];
+  fill_level_tables(zs, L, a.nz);
   const int64_t p0 = int64_t(blockIdx.x) * BOX_PTS;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -227,26 +251,31 @@ __global__ void __launch_bounds__(BOX_THREADS, 3) k_interp_box(InterpArgs a, Lev
     s_ref[0] = c.ix;
     s_ref[1] = c.iy;
   }
-  PointCell cell[BOX_PPT];
-  float zq[BOX_PPT];
-  int rx[BOX_PPT], ry[BOX_PPT];
+  // compact per-point state; weights are recomputed after the box load
+  int rx[BOX_PPT], ry[BOX_PPT], jz[BOX_PPT];
+  float px[BOX_PPT], py[BOX_PPT], pz[BOX_PPT];
   __syncthreads();
   const int refx = s_ref[0], refy = s_ref[1];
   int mn[3] = {1 << 30, 1 << 30, 1 << 30}, mx[3] = {-(1 << 30), -(1 << 30), -(1 << 30)};
 #pragma unroll
   for (int k = 0; k < BOX_PPT; ++k) {
     const int64_t i = p0 + k * BOX_THREADS + threadIdx.x;
+    rx[k] = ry[k] = jz[k] = 0;
+    px[k] = py[k] = pz[k] = 0.f;
     if (i < a.np) {
-      zq[k] = a.pts[3 * i + 2];
-      cell[k] = point_cell(a, zs, a.pts[3 * i], a.pts[3 * i + 1], zq[k]);
-      rx[k] = wrap_rel(cell[k].ix, refx, a.Nxr);
-      ry[k] = a.Nyr > 1 ? wrap_rel(cell[k].iy, refy, a.Nyr) : 0;
+      px[k] = a.pts[3 * i];
+      py[k] = a.pts[3 * i + 1];
+      pz[k] = a.pts[3 * i + 2];
+      const PointCell c = point_cell(a, zs, px[k], py[k], pz[k]);
+      rx[k] = wrap_rel(c.ix, refx, a.Nxr);
+      ry[k] = a.Nyr > 1 ? wrap_rel(c.iy, refy, a.Nyr) : 0;
+      jz[k] = c.j0;
       mn[0] = min(mn[0], rx[k]);
       mx[0] = max(mx[0], rx[k]);
       mn[1] = min(mn[1], ry[k]);
       mx[1] = max(mx[1], ry[k]);
-      mn[2] = min(mn[2], cell[k].j0);
-      mx[2] = max(mx[2], cell[k].j0);
+      mn[2] = min(mn[2], c.j0);
+      mx[2] = max(mx[2], c.j0);
     }
   }
 #pragma unroll
@@ -280,77 +309,88 @@ __global__ void __launch_bounds__(BOX_THREADS, 3) k_interp_box(InterpArgs a, Lev
   const int bz = mx[2] - mn[2] + 4;
   const bool fits = int64_t(bx) * by * bz <= BOX_NODES && int64_t(bx) * by <= BOX_COLS &&
                     bx <= a.Nxr && by <= a.Nyr;
-  if (fits) {
-    const size_t plane = size_t(a.Nyr) * a.Nxr;
-    const int x0 = refx + mn[0] - 1, y0 = a.Nyr > 1 ? refy + mn[1] - 1 : 0, l0 = mn[2];
-    const int nbox = bx * by * bz;
-    for (int idx = threadIdx.x; idx < nbox; idx += BOX_THREADS) {
-      const int lx = idx % bx;
-      const int rest = idx / bx;
-      const int ly = rest % by, lz = rest / by;
-      const size_t g = size_t(l0 + lz) * plane + size_t((y0 + ly) & (a.Nyr - 1)) * a.Nxr +
-                       ((x0 + lx) & (a.Nxr - 1));
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      for (int tl = 0; tl < a.n_tl; ++tl) {
-        const float4 gv = __ldg(&a.nodes[size_t(tl) * a.nz * plane + g]);
-        const float w = a.wt[tl];
-        v.x = fmaf(w, gv.x, v.x);
-        v.y = fmaf(w, gv.y, v.y);
-        v.z = fmaf(w, gv.z, v.z);
-        v.w = fmaf(w, gv.w, v.w);
-      }
-      sbox[idx] = v;
-    }
-    for (int idx = threadIdx.x; idx < bx * by; idx += BOX_THREADS) {
-      const int lx = idx % bx, ly = idx / bx;
-      const size_t g = size_t((y0 + ly) & (a.Nyr - 1)) * a.Nxr + ((x0 + lx) & (a.Nxr - 1));
-      float v = 0.f;
-      for (int tl = 0; tl < a.n_tl; ++tl) v = fmaf(a.wt[tl], __ldg(&a.eta[size_t(tl) * plane + g]), v);
-      seta[idx] = v;
-    }
-    __syncthreads();
+  if (!fits) {
 #pragma unroll
     for (int k = 0; k < BOX_PPT; ++k) {
       const int64_t i = p0 + k * BOX_THREADS + threadIdx.x;
       if (i >= a.np) continue;
-      const PointCell& c = cell[k];
-      const int ox = rx[k] - mn[0], oy = ry[k] - mn[1], oz = c.j0 - mn[2];
-      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-      float acc_eta = 0.f;
-      const int nys = a.Nyr > 1 ? 4 : 1;
-#pragma unroll 1
-      for (int q = 0; q < 4; ++q) {
-        for (int b = 0; b < nys; ++b) {
-          const float4* row = sbox + ((oz + q) * by + (oy + b)) * bx + ox;
-          const float wzy = c.wz[q] * c.wy[b];
-#pragma unroll
-          for (int kx = 0; kx < 4; ++kx) {
-            const float4 gv = row[kx];
-            const float ww = wzy * c.wx[kx];
-            acc.x = fmaf(ww, gv.x, acc.x);
-            acc.y = fmaf(ww, gv.y, acc.y);
-            acc.z = fmaf(ww, gv.z, acc.z);
-            acc.w = fmaf(ww, gv.w, acc.w);
-          }
-        }
-      }
-      for (int b = 0; b < nys; ++b) {
-        const float* row = seta + (oy + b) * bx + ox;
-#pragma unroll
-        for (int kx = 0; kx < 4; ++kx) acc_eta = fmaf(c.wy[b] * c.wx[kx], row[kx], acc_eta);
-      }
-      store_point(a, i, acc, acc_eta, zq[k], c.inside);
-    }
-  } else {
-#pragma unroll
-    for (int k = 0; k < BOX_PPT; ++k) {
-      const int64_t i = p0 + k * BOX_THREADS + threadIdx.x;
-      if (i >= a.np) continue;
+      const PointCell c = point_cell(a, zs, px[k], py[k], pz[k]);
       float4 acc;
       float acc_eta;
-      gather_global(a, cell[k], acc, acc_eta);
-      store_point(a, i, acc, acc_eta, zq[k], cell[k].inside);
+      gather_global(a, c, acc, acc_eta);
+      store_point(a, i, acc, acc_eta, pz[k], c.inside);
     }
+    return;
+  }
+  const size_t plane = size_t(a.Nyr) * a.Nxr;
+  const int x0 = refx + mn[0] - 1, y0 = a.Nyr > 1 ? refy + mn[1] - 1 : 0, l0 = mn[2];
+  {
+    // rows (ly, lz) over warps, x over lanes; the time blend happens here, once per node
+    const size_t tl_stride = size_t(a.nz) * plane;
+    for (int r = warp; r < by * bz; r += BOX_THREADS / 32) {
+      const int lz = r / by, ly = r - lz * by;
+      const float4* src = a.nodes + size_t(l0 + lz) * plane + size_t((y0 + ly) & (a.Nyr - 1)) * a.Nxr;
+      float4* dst = sbox + r * bx;
+      for (int lx = lane; lx < bx; lx += 32) {
+        const int gx = (x0 + lx) & (a.Nxr - 1);
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int tl = 0; tl < a.n_tl; ++tl) {
+          const float4 gv = __ldg(&src[size_t(tl) * tl_stride + gx]);
+          const float w = a.wt[tl];
+          v.x = fmaf(w, gv.x, v.x);
+          v.y = fmaf(w, gv.y, v.y);
+          v.z = fmaf(w, gv.z, v.z);
+          v.w = fmaf(w, gv.w, v.w);
+        }
+        dst[lx] = v;
+      }
+    }
+    for (int ly = warp; ly < by; ly += BOX_THREADS / 32) {
+      const float* src = a.eta + size_t((y0 + ly) & (a.Nyr - 1)) * a.Nxr;
+      for (int lx = lane; lx < bx; lx += 32) {
+        const int gx = (x0 + lx) & (a.Nxr - 1);
+        float v = 0.f;
+        for (int tl = 0; tl < a.n_tl; ++tl) v = fmaf(a.wt[tl], __ldg(&src[size_t(tl) * plane + gx]), v);
+        seta[ly * bx + lx] = v;
+      }
+    }
+  }
+  __syncthreads();
+  const int zstride = by * bx;
+  const int nys = a.Nyr > 1 ? 4 : 1;
+#pragma unroll 1
+  for (int k = 0; k < BOX_PPT; ++k) {
+    const int64_t i = p0 + k * BOX_THREADS + threadIdx.x;
+    if (i >= a.np) continue;
+    const PointCell c = point_cell(a, zs, px[k], py[k], pz[k]);
+    const float4* base = sbox + ((jz[k] - mn[2]) * by + (ry[k] - mn[1])) * bx + (rx[k] - mn[0]);
+    unsigned long long uv = pack2(0.f, 0.f), wt = pack2(0.f, 0.f);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        if (b >= nys) break;
+        const float4* row = base + q * zstride + b * bx;
+        const float wzy = c.wz[q] * c.wy[b];
+#pragma unroll
+        for (int kx = 0; kx < 4; ++kx) {
+          const float4 gv = row[kx];
+          const float ww = wzy * c.wx[kx];
+          const unsigned long long w2 = pack2(ww, ww);
+          fma2(uv, w2, pack2(gv.x, gv.y));
+          fma2(wt, w2, pack2(gv.z, gv.w));
+        }
+      }
+    }
+    float acc_eta = 0.f;
+    const float* ebase = seta + (ry[k] - mn[1]) * bx + (rx[k] - mn[0]);
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      if (b >= nys) break;
+#pragma unroll
+      for (int kx = 0; kx < 4; ++kx) acc_eta = fmaf(c.wy[b] * c.wx[kx], ebase[b * bx + kx], acc_eta);
+    }
+    store_point(a, i, make_float4(lo2(uv), hi2(uv), lo2(wt), hi2(wt)), acc_eta, pz[k], c.inside);
   }
 }
 
@@ -362,12 +402,125 @@ void split(double v, float& hi, float& lo) {
 }  // namespace
 }  // namespace swense
 
-using namespace swense;
+// ---------------------------------------------------------------------------------------------
+// Inputs of the learned correction: per point and field f in (u, v, w, dphi/dt) one row
+//   x = [stencil_f / s_f (64 time-blended node values, x fastest, then y, then z), dx, dy, dz, 0]
+// with s_f = max |stencil_f| + 1e-30 and dz the offset in the stencil's middle level interval,
+// plus s_f, the plain Lagrange value of f, and the plain eta.
+namespace swense {
+namespace {
 
-extern "C" int swense_interp(const swense_grid* g, double t, const float* pts, int64_t np,
-                             float* eta, float* u, float* v, float* w, float* p, int32_t p_mode,
-                             double rho, double grav, int64_t* n_out_of_range, void* stream_) {
-  cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+constexpr int MLP_XLD = 68;
+
+struct FeatArgs {
+  InterpArgs a;          // grid, points, time weights (o_* unused)
+  float* x;              // [4 np][68]
+  float* scale;          // [4 np]
+  float* lag;            // [4 np]
+  float* eta_out;        // [np] or NULL
+};
+
+__global__ void __launch_bounds__(128) k_mlp_features(FeatArgs f, Levels L) {
+  __shared__ LevelTables zs;
+  const InterpArgs& a = f.a;
+  fill_level_tables(zs, L, a.nz);
+  __syncthreads();
+  const size_t plane = size_t(a.Nyr) * a.Nxr;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < a.np;
+       i += int64_t(gridDim.x) * blockDim.x) {
+    const float px = a.pts[3 * i], py = a.pts[3 * i + 1], pz = a.pts[3 * i + 2];
+    const PointCell c = point_cell(a, zs, px, py, pz);
+    float fx, fy;
+    int ixx, iyy;
+    locate(px, a.sx_hi, a.sx_lo, a.Nxr, ixx, fx);
+    locate(py, a.sy_hi, a.sy_lo, a.Nyr, iyy, fy);
+    const float z1 = zs.z[c.j0 + 1], z2 = zs.z[c.j0 + 2];
+    const float fz = (pz - z1) / (z2 - z1);
+    int xi[4], yi[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      xi[q] = (c.ix - 1 + q) & (a.Nxr - 1);
+      yi[q] = (c.iy - 1 + q) & (a.Nyr - 1);
+    }
+    if (f.eta_out) {
+      float e = 0.f;
+      for (int tl = 0; tl < a.n_tl; ++tl)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            e = fmaf(a.wt[tl] * c.wy[b] * c.wx[k], __ldg(&a.eta[tl * plane + size_t(yi[b]) * a.Nxr + xi[k]]), e);
+      f.eta_out[i] = e;
+    }
+#pragma unroll 1
+    for (int fld = 0; fld < 4; ++fld) {
+      float* xr = f.x + (4 * i + fld) * MLP_XLD;
+      float smax = 0.f, lagv = 0.f;
+      // pass 1: time-blended stencil values -> row (unscaled), max, Lagrange value
+#pragma unroll 1
+      for (int q = 0; q < 4; ++q) {
+        const float wzq = q == 0 ? c.wz[0] : q == 1 ? c.wz[1] : q == 2 ? c.wz[2] : c.wz[3];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const size_t node = size_t(c.j0 + q) * plane + size_t(yi[b]) * a.Nxr + xi[k];
+            float v = 0.f;
+            for (int tl = 0; tl < a.n_tl; ++tl)
+              v = fmaf(a.wt[tl], __ldg(reinterpret_cast<const float*>(&a.nodes[tl * a.nz * plane + node]) + fld), v);
+            xr[(q * 4 + b) * 4 + k] = v;
+            smax = fmaxf(smax, fabsf(v));
+            lagv = fmaf(wzq * c.wy[b] * c.wx[k], v, lagv);
+          }
+        }
+      }
+      const float s = smax + 1e-30f;
+      const float inv = 1.f / s;
+      for (int k = 0; k < 64; ++k) xr[k] *= inv;
+      xr[64] = fx;
+      xr[65] = fy;
+      xr[66] = fz;
+      xr[67] = 0.f;
+      f.scale[4 * i + fld] = s;
+      f.lag[4 * i + fld] = lagv;
+    }
+  }
+}
+
+// Corrected fields: f = lagrange_f + s_f y_f, then Bernoulli; out-of-range points stay NaN.
+__global__ void k_mlp_correct(InterpArgs a, const float* __restrict__ scale,
+                              const float* __restrict__ lag, const float* __restrict__ y, Levels L) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= a.np) return;
+  float vals[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) vals[q] = fmaf(scale[4 * i + q], y[4 * i + q], lag[4 * i + q]);
+  const float z = a.pts[3 * i + 2];
+  const bool inside = (z >= L.z[0]) && (z <= L.z[a.nz - 1]);
+  float4 acc = make_float4(vals[0], vals[1], vals[2], vals[3]);
+  if (!inside) {
+    const float qnan = __int_as_float(0x7fc00000);
+    acc = make_float4(qnan, qnan, qnan, qnan);
+    if (a.n_oor) atomicAdd(a.n_oor, 1ULL);
+  }
+  if (a.o_u) a.o_u[i] = acc.x;
+  if (a.o_v) a.o_v[i] = acc.y;
+  if (a.o_w) a.o_w[i] = acc.z;
+  if (a.o_p) {
+    float p;
+    if (a.p_mode == SWENSE_P_PHIT) {
+      p = acc.w;
+    } else {
+      p = -a.rho * (acc.w + 0.5f * (acc.x * acc.x + acc.y * acc.y + acc.z * acc.z));
+      if (a.p_mode == SWENSE_P_TOTAL) p -= a.rho * a.g * z;
+    }
+    a.o_p[i] = p;
+  }
+}
+
+// Validate a grid request and fill the launch arguments shared by the interpolation entry points.
+int prepare_interp(const swense_grid* g, double t, const float* pts, int64_t np, int32_t p_mode,
+                   double rho, double grav, InterpArgs* a, Levels* lev) {
   if (!g || !g->nodes || !g->eta || !g->z_levels || !g->t_levels)
     return fail(SWENSE_ERR_ARG, "NULL grid, grid arrays or level lists");
   if (np < 0) return fail(SWENSE_ERR_ARG, "np must be >= 0");
@@ -384,59 +537,103 @@ extern "C" int swense_interp(const swense_grid* g, double t, const float* pts, i
   if (!std::isfinite(t) || !std::isfinite(rho) || !std::isfinite(grav))
     return fail(SWENSE_ERR_ARG, "non-finite t, rho or g");
   if (reinterpret_cast<uintptr_t>(g->nodes) & 15) return fail(SWENSE_ERR_ARG, "nodes must be 16-byte aligned");
-  Levels lev;
   for (int l = 0; l < g->nz; ++l) {
-    lev.z[l] = g->z_levels[l];
-    if (!std::isfinite(lev.z[l]) || (l > 0 && !(lev.z[l] > lev.z[l - 1])))
+    lev->z[l] = g->z_levels[l];
+    if (!std::isfinite(lev->z[l]) || (l > 0 && !(lev->z[l] > lev->z[l - 1])))
       return fail(SWENSE_ERR_LEVELS, "z_levels must be finite and strictly increasing");
   }
-  InterpArgs a{};
   for (int l = 0; l < g->n_tl; ++l) {
     if (!std::isfinite(g->t_levels[l]) || (l > 0 && !(g->t_levels[l] > g->t_levels[l - 1])))
       return fail(SWENSE_ERR_ARG, "t_levels must be finite and strictly increasing");
   }
-  // Lagrange weights over the time levels, in FP64 on the host
+  *a = InterpArgs{};
   for (int l = 0; l < g->n_tl; ++l) {
     double wl = 1.0;
     for (int m = 0; m < g->n_tl; ++m)
       if (m != l) wl *= (t - g->t_levels[m]) / (g->t_levels[l] - g->t_levels[m]);
-    a.wt[l] = float(wl);
+    a->wt[l] = float(wl);
   }
-  unsigned long long* d_count = nullptr;
-  if (n_out_of_range) {
-    void* ws = nullptr;
-    int st = workspace(256, stream, &ws);
-    if (st) return st;
-    d_count = static_cast<unsigned long long*>(ws);
-    SWENSE_CUDA_TRY(cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), stream));
-  }
-  if (np > 0) {
-    a.nodes = reinterpret_cast<const float4*>(g->nodes);
-    a.eta = g->eta;
-    a.pts = pts;
-    a.o_eta = eta;
-    a.o_u = u;
-    a.o_v = v;
-    a.o_w = w;
-    a.o_p = p;
-    a.n_oor = d_count;
-    a.np = np;
-    a.Nxr = g->nx_r;
-    a.Nyr = g->ny_r;
-    a.nz = g->nz;
-    a.n_tl = g->n_tl;
-    split(double(g->nx_r) / g->Lx, a.sx_hi, a.sx_lo);
-    if (g->ny_r > 1) split(double(g->ny_r) / g->Ly, a.sy_hi, a.sy_lo);
-    a.p_mode = p_mode;
-    a.rho = float(rho);
-    a.g = float(grav);
-    const int64_t blocks = (np + BOX_PTS - 1) / BOX_PTS;
-    if (blocks >= (int64_t(1) << 31)) return fail(SWENSE_ERR_SIZE, "too many points for one call");
-    SWENSE_CUDA_TRY(cudaFuncSetAttribute((const void*)k_interp_box,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(BOX_SMEM)));
-    k_interp_box<<<unsigned(blocks), BOX_THREADS, BOX_SMEM, stream>>>(a, lev);
+  a->nodes = reinterpret_cast<const float4*>(g->nodes);
+  a->eta = g->eta;
+  a->pts = pts;
+  a->np = np;
+  a->Nxr = g->nx_r;
+  a->Nyr = g->ny_r;
+  a->nz = g->nz;
+  a->n_tl = g->n_tl;
+  split(double(g->nx_r) / g->Lx, a->sx_hi, a->sx_lo);
+  if (g->ny_r > 1) split(double(g->ny_r) / g->Ly, a->sy_hi, a->sy_lo);
+  a->p_mode = p_mode;
+  a->rho = float(rho);
+  a->g = float(grav);
+  return SWENSE_OK;
+}
+
+}  // namespace
+}  // namespace swense
+
+using namespace swense;
+
+extern "C" int swense_mlp_features(const swense_grid* g, double t, const float* pts, int64_t np,
+                                   float* x, float* scale, float* lagrange, float* eta,
+                                   void* stream_) {
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+  InterpArgs a;
+  Levels lev;
+  int st = prepare_interp(g, t, pts, np, SWENSE_P_DYN, 1.0, 1.0, &a, &lev);
+  if (st) return st;
+  if (g->ny_r < 4) return fail(SWENSE_ERR_UNSUPPORTED, "the learned correction needs a 3-D grid");
+  if (np == 0) return SWENSE_OK;
+  if (!x || !scale || !lagrange) return fail(SWENSE_ERR_ARG, "NULL feature outputs");
+  FeatArgs f{a, x, scale, lagrange, eta};
+  const unsigned blocks = unsigned(std::min<int64_t>((np + 127) / 128, 152 * 64));
+  k_mlp_features<<<blocks, 128, 0, stream>>>(f, lev);
+  SWENSE_CUDA_TRY(cudaGetLastError());
+  count_launches(1);
+  return SWENSE_OK;
+}
+
+extern "C" int swense_interp_learned(const swense_grid* g, double t, const float* pts, int64_t np,
+                                     float* eta, float* u, float* v, float* w, float* p,
+                                     int32_t p_mode, double rho, double grav, const void* packed,
+                                     int64_t* n_out_of_range, void* stream_) {
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+  InterpArgs a;
+  Levels lev;
+  int st = prepare_interp(g, t, pts, np, p_mode, rho, grav, &a, &lev);
+  if (st) return st;
+  if (g->ny_r < 4) return fail(SWENSE_ERR_UNSUPPORTED, "the learned correction needs a 3-D grid");
+  if (!packed) return fail(SWENSE_ERR_ARG, "NULL packed weights");
+  const int64_t chunk = std::min<int64_t>(np, int64_t(1) << 19);
+  const size_t rows = size_t(4) * std::max<int64_t>(chunk, 1);
+  const size_t bytes = 256 + rows * (MLP_XLD + 3) * sizeof(float);
+  void* ws = nullptr;
+  st = workspace(bytes, stream, &ws);
+  if (st) return st;
+  unsigned long long* d_count = static_cast<unsigned long long*>(ws);
+  float* x = reinterpret_cast<float*>(static_cast<char*>(ws) + 256);
+  float* sc = x + rows * MLP_XLD;
+  float* lg = sc + rows;
+  float* y = lg + rows;
+  if (n_out_of_range) SWENSE_CUDA_TRY(cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), stream));
+  for (int64_t s0 = 0; s0 < np; s0 += chunk) {
+    const int64_t n = std::min(chunk, np - s0);
+    InterpArgs c = a;
+    c.pts = pts + 3 * s0;
+    c.np = n;
+    c.o_u = u ? u + s0 : nullptr;
+    c.o_v = v ? v + s0 : nullptr;
+    c.o_w = w ? w + s0 : nullptr;
+    c.o_p = p ? p + s0 : nullptr;
+    c.n_oor = n_out_of_range ? d_count : nullptr;
+    FeatArgs f{c, x, sc, lg, eta ? eta + s0 : nullptr};
+    k_mlp_features<<<unsigned(std::min<int64_t>((n + 127) / 128, 152 * 64)), 128, 0, stream>>>(f, lev);
     SWENSE_CUDA_TRY(cudaGetLastError());
-      count_launches(1);
+    st = swense_mlp_forward(packed, x, 4 * n, y, stream);
+    if (st) return st;
+    k_mlp_correct<<<unsigned((n + 255) / 256), 256, 0, stream>>>(c, sc, lg, y, lev);
+    SWENSE_CUDA_TRY(cudaGetLastError());
+    count_launches(2);
   }
   if (n_out_of_range) {
     unsigned long long h = 0;
@@ -445,4 +642,66 @@ extern "C" int swense_interp(const swense_grid* g, double t, const float* pts, i
     *n_out_of_range = int64_t(h);
   }
   return SWENSE_OK;
+}
+
+namespace swense {
+namespace {
+
+int interp_impl(const swense_grid* g, double t, const float* pts, const int32_t* perm, int64_t np,
+                float* eta, float* u, float* v, float* w, float* p, int32_t p_mode, double rho,
+                double grav, int64_t* n_out_of_range, cudaStream_t stream) {
+  InterpArgs a;
+  Levels lev;
+  int st = prepare_interp(g, t, pts, np, p_mode, rho, grav, &a, &lev);
+  if (st) return st;
+  unsigned long long* d_count = nullptr;
+  if (n_out_of_range) {
+    void* ws = nullptr;
+    st = workspace(256, stream, &ws);
+    if (st) return st;
+    d_count = static_cast<unsigned long long*>(ws);
+    SWENSE_CUDA_TRY(cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), stream));
+  }
+  if (np > 0) {
+    a.o_eta = eta;
+    a.o_u = u;
+    a.o_v = v;
+    a.o_w = w;
+    a.o_p = p;
+    a.n_oor = d_count;
+    a.perm = perm;
+    const int64_t blocks = (np + BOX_PTS - 1) / BOX_PTS;
+    if (blocks >= (int64_t(1) << 31)) return fail(SWENSE_ERR_SIZE, "too many points for one call");
+    SWENSE_CUDA_TRY(cudaFuncSetAttribute((const void*)k_interp_box,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(BOX_SMEM)));
+    k_interp_box<<<unsigned(blocks), BOX_THREADS, BOX_SMEM, stream>>>(a, lev);
+    SWENSE_CUDA_TRY(cudaGetLastError());
+    count_launches(1);
+  }
+  if (n_out_of_range) {
+    unsigned long long h = 0;
+    SWENSE_CUDA_TRY(cudaMemcpyAsync(&h, d_count, sizeof(h), cudaMemcpyDeviceToHost, stream));
+    SWENSE_CUDA_TRY(cudaStreamSynchronize(stream));
+    *n_out_of_range = int64_t(h);
+  }
+  return SWENSE_OK;
+}
+
+}  // namespace
+}  // namespace swense
+
+extern "C" int swense_interp(const swense_grid* g, double t, const float* pts, int64_t np,
+                             float* eta, float* u, float* v, float* w, float* p, int32_t p_mode,
+                             double rho, double grav, int64_t* n_out_of_range, void* stream) {
+  return interp_impl(g, t, pts, nullptr, np, eta, u, v, w, p, p_mode, rho, grav, n_out_of_range,
+                     static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int swense_interp_permuted(const swense_grid* g, double t, const float* pts_sorted,
+                                      const int32_t* perm, int64_t np, float* eta, float* u,
+                                      float* v, float* w, float* p, int32_t p_mode, double rho,
+                                      double grav, int64_t* n_out_of_range, void* stream) {
+  if (np > 0 && !perm) return fail(SWENSE_ERR_ARG, "NULL perm");
+  return interp_impl(g, t, pts_sorted, perm, np, eta, u, v, w, p, p_mode, rho, grav,
+                     n_out_of_range, static_cast<cudaStream_t>(stream));
 }

@@ -1,0 +1,87 @@
+"""Training data and training loop of the learned interpolation correction.
+
+The data come from the method itself: for random seas (1-8 linear components, random heading,
+ka ~ U[0.02, 0.12], wavelength ~ U[8, 32] grid spacings), the library reconstructs the grid
+(swense_fields_on_grid), extracts the stencil features and plain Lagrange values at seeded
+random points (swense_mlp_features), and evaluates the exact modal sums at the same points
+(swense_direct). Target of row (point, field f): (exact_f - lagrange_f) / s_f. Every step runs
+in the CUDA library; this module only orchestrates calls and draws seeded random numbers.
+"""
+import numpy as np
+import torch
+
+from wavegen import seas as W
+from . import api
+
+
+def random_sea(nx, ny, Lx, Ly, rng, depth=0.0):
+    """1-8 linear components snapped to the mode grid (heading, steepness, wavelength random)."""
+    dx = Lx / nx
+    comps, used = [], set()
+    for _ in range(int(rng.integers(1, 9))):
+        for _try in range(20):
+            lam = rng.uniform(8, 32) * dx
+            th = rng.uniform(0, 2 * np.pi)
+            m = int(round(np.cos(th) * Lx / lam))
+            n = int(round(np.sin(th) * Ly / lam))
+            if (m, n) == (0, 0) or abs(m) >= nx // 2 or abs(n) >= ny // 2:
+                continue
+            if (m, n) in used or (-m, -n) in used:
+                continue
+            used.add((m, n))
+            k = 2 * np.pi * np.hypot(m / Lx, n / Ly)
+            comps.append((m, n, float(rng.uniform(0.02, 0.12) / k), float(rng.uniform(0, 2 * np.pi))))
+            break
+    if not comps:
+        comps.append((1, 0, 0.05 * Lx / (2 * np.pi), 0.0))
+    return W.linear_sea(nx, ny, Lx, Ly, comps, depth=depth)
+
+
+def sample_points(n, Lx, Ly, z_lo, z_hi, rng):
+    p = np.empty((n, 3))
+    p[:, 0] = rng.uniform(0, Lx, n)
+    p[:, 1] = rng.uniform(0, Ly, n)
+    p[:, 2] = rng.uniform(z_lo, z_hi, n)
+    return p.astype(np.float32)
+
+
+def make_dataset(n_seas, points_per_sea, nx, ny, Lx, Ly, z_levels, pad_n=1, t_levels=(0.0,),
+                 seed=0, device="cuda"):
+    """Returns (x [4N][68], field [4N] int32, target [4N]) on the device."""
+    rng = np.random.default_rng(seed)
+    z = np.asarray(z_levels, np.float32)
+    xs, fs, ts = [], [], []
+    for _ in range(n_seas):
+        sea = random_sea(nx, ny, Lx, Ly, rng)
+        modes = api.upload_modes(sea, device)
+        grid = api.fields_on_grid(modes, z, pad_n, list(t_levels))
+        t = float(t_levels[0]) if len(t_levels) == 1 else float(
+            t_levels[0] + rng.uniform(0, 1) * (t_levels[-1] - t_levels[0]))
+        pts = torch.from_numpy(sample_points(points_per_sea, Lx, Ly, float(z[0]), float(z[-1]), rng)).to(device)
+        x, sc, lg, _ = api.mlp_features(grid, t, pts)
+        ex = api.direct(modes, t, pts, p_mode="phit")
+        exact = torch.stack([ex["u"], ex["v"], ex["w"], ex["p"]], 1).reshape(-1)
+        xs.append(x)
+        ts.append((exact - lg) / sc)
+        fs.append(torch.arange(4, dtype=torch.int32, device=device).repeat(points_per_sea))
+    return torch.cat(xs), torch.cat(fs), torch.cat(ts)
+
+
+def train(mlp, x, field, target, steps, batch=8192, lr=1e-3, seed=0, log_every=0):
+    """Adam on random mini-batches (seeded) with a cosine-decayed learning rate. The targets
+    are divided by their RMS, which becomes the network's output scale, so the BF16 network
+    works on O(1) values. Returns the logged losses (host floats, in scaled units)."""
+    scale = float(torch.sqrt(torch.mean(target.double() ** 2)).item()) or 1.0
+    mlp.set_out_scale(scale)
+    tgt = (target / scale).contiguous()
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    n = x.shape[0]
+    loss = torch.empty(1, dtype=torch.float32, device=x.device)
+    losses = []
+    for s in range(steps):
+        idx = torch.randint(0, n, (batch,), generator=g, dtype=torch.int64).to(torch.int32).to(x.device)
+        lr_s = lr * 0.5 * (1.0 + np.cos(np.pi * s / max(1, steps)))
+        mlp.train_step(x, field, tgt, idx, lr=lr_s, loss=loss)
+        if log_every and (s % log_every == 0 or s == steps - 1):
+            losses.append(float(loss.item()))
+    return losses

@@ -24,3 +24,24 @@ def rel_l2(got, ref):
     ok = np.isfinite(ref)
     den = np.sqrt(np.mean(ref[ok] ** 2))
     return float(np.sqrt(np.mean((got[ok] - ref[ok]) ** 2)) / max(den, 1e-300))
+
+
+def rel_linf_scaled(got, ref, scale):
+    """max |got - ref| / scale over finite reference entries (NaN positions must match)."""
+    got = np.asarray(got, np.float64)
+    ref = np.asarray(ref, np.float64)
+    nan_ref = ~np.isfinite(ref)
+    assert np.array_equal(nan_ref, ~np.isfinite(got)), "NaN / out-of-range positions differ"
+    if nan_ref.all():
+        return 0.0
+    return float(np.max(np.abs(got[~nan_ref] - ref[~nan_ref])) / scale)
+
+
+def velocity_scale(u, v, w):
+    """Largest velocity magnitude of a reference field (the scale of the velocity error bar:
+    the three components share one FP32 transform / stencil, so their rounding errors scale
+    with the vector, not with each component)."""
+    mag = np.sqrt(np.asarray(u, np.float64) ** 2 + np.asarray(v, np.float64) ** 2
+                  + np.asarray(w, np.float64) ** 2)
+    mag = mag[np.isfinite(mag)]
+    return float(mag.max()) if mag.size else 1.0
