@@ -72,3 +72,22 @@ def jonswap3d_small(pad_n=1, n_tl=2, seed=SEED0 + 102):
 def mesh_points(mesh):
     """Cell centres followed by face centres, float32 [n][3], mesh order."""
     return np.concatenate([mesh["cell_centres"], mesh["face_centres"]]).astype(np.float32)
+
+
+def e1_divergence(pad_n=1, window_lp=2.0, levels=64, seed=SEED0 + 6):
+    """Reconstruction-error demonstration: 2-D JONSWAP sea (Tp = 0.7 s, Hs = 0.028 m,
+    gamma = 3.3, deep water, random phases) on Lx = 10 lambda_p with 128 modes; an x-z
+    finite-volume mesh with dx = lambda_p / 100 and dz = Hs / 20 over a window of
+    ``window_lp`` peak wavelengths, from -lambda_p / 4 to +2 Hs."""
+    g = 9.81
+    Tp, Hs = 0.7, 0.028
+    lp = g * Tp * Tp / (2 * np.pi)
+    Lx = 10 * lp
+    sea = seas.jonswap_sea(128, 1, Lx, 1.0, Hs, lp, gamma=3.3, heading=0.0, seed=seed)
+    z_lo, z_hi = -0.25 * lp, 2.0 * Hs
+    z = P.levels_surface_clustered(-0.3 * lp, 2.5 * Hs, levels, n_band=levels // 2, band=2.5 * Hs)
+    x_edges = np.arange(0.0, window_lp * lp + 1e-12, lp / 100) + 3 * lp
+    z_edges = np.arange(z_lo, z_hi + 1e-12, Hs / 20)
+    mesh = M.box_xz_mesh(x_edges, z_edges)
+    return {"name": "e1_divergence", "sea": sea, "z_levels": z, "pad_n": pad_n, "mesh": mesh,
+            "t_levels": np.array([0.0]), "t_query": 0.0, "lambda_p": lp, "Hs": Hs}

@@ -127,3 +127,46 @@ def cylinder_ogrid(centre, R, R_out, n_r, n_theta, z_edges, radial_ratio=1.02):
         "cell_volume": vol, "cell_faces": cell_faces,
         "n_r": n_r, "n_theta": n_theta, "n_z": n_z,
     }
+
+
+def box_xz_mesh(x_edges, z_edges, y0=0.0, y1=1.0):
+    """Structured x-z mesh one cell thick in y (a 2-D finite-volume mesh as hexahedra): the
+    y faces carry no flux of a field with v = 0. Same dict layout as ``cylinder_ogrid``.
+    Ordering: x fastest, then z."""
+    x = np.asarray(x_edges, np.float64)
+    z = np.asarray(z_edges, np.float64)
+    nx, nz = len(x) - 1, len(z) - 1
+    dy = y1 - y0
+    X, Z = np.meshgrid(x, z, indexing="xy")                       # [nz+1][nx+1]
+    # x-faces (normal +x): (k, i) for i in [0, nx], k in [0, nz)
+    K1, I1 = np.meshgrid(np.arange(nz), np.arange(nx + 1), indexing="ij")
+    K1, I1 = K1.ravel(), I1.ravel()
+    A_x = np.stack([(z[K1 + 1] - z[K1]) * dy, 0 * K1, 0 * K1], 1).astype(np.float64)
+    C_x = np.stack([x[I1], np.full(len(I1), 0.5 * (y0 + y1)), 0.5 * (z[K1] + z[K1 + 1])], 1)
+    # z-faces (normal +z): (k, i) for k in [0, nz], i in [0, nx)
+    K2, I2 = np.meshgrid(np.arange(nz + 1), np.arange(nx), indexing="ij")
+    K2, I2 = K2.ravel(), I2.ravel()
+    A_z = np.stack([0 * K2, 0 * K2, (x[I2 + 1] - x[I2]) * dy], 1).astype(np.float64)
+    C_z = np.stack([0.5 * (x[I2] + x[I2 + 1]), np.full(len(I2), 0.5 * (y0 + y1)), z[K2]], 1)
+    # y-faces (normal +y), front and back of each cell
+    K3, I3 = np.meshgrid(np.arange(nz), np.arange(nx), indexing="ij")
+    K3, I3 = K3.ravel(), I3.ravel()
+    ar = (x[I3 + 1] - x[I3]) * (z[K3 + 1] - z[K3])
+    A_y = np.stack([0 * ar, ar, 0 * ar], 1)
+    cx, cz = 0.5 * (x[I3] + x[I3 + 1]), 0.5 * (z[K3] + z[K3 + 1])
+    C_y0 = np.stack([cx, np.full(len(cx), y0), cz], 1)
+    C_y1 = np.stack([cx, np.full(len(cx), y1), cz], 1)
+    n_x, n_z, n_c = len(A_x), len(A_z), len(A_y)
+    face_area = np.concatenate([A_x, A_z, A_y, A_y])
+    face_centres = np.concatenate([C_x, C_z, C_y0, C_y1])
+    cell = K3 * nx + I3
+    f_xl = K3 * (nx + 1) + I3
+    f_zl = n_x + K3 * nx + I3
+    f_y0 = n_x + n_z + cell
+    f_y1 = n_x + n_z + n_c + cell
+    cell_faces = np.stack([-(f_xl + 1), f_xl + 2, -(f_zl + 1), f_zl + nx + 1, -(f_y0 + 1), f_y1 + 1],
+                          axis=1).astype(np.int32)
+    vol = ar * dy
+    cc = np.stack([cx, np.full(len(cx), 0.5 * (y0 + y1)), cz], 1)
+    return {"cell_centres": cc, "face_centres": face_centres, "face_area": face_area,
+            "cell_volume": vol, "cell_faces": cell_faces, "nx": nx, "nz": nz}
