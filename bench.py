@@ -34,7 +34,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--config", choices=["jonswap3d", "stokes2d"], default="jonswap3d")
+    ap.add_argument("--config", choices=["jonswap3d", "stokes2d", "batched", "learned", "e1"],
+                    default="jonswap3d")
     ap.add_argument("--pad", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -401,6 +402,185 @@ def run_ours(args, rank, world):
         print(json.dumps(line), flush=True)
 
 
+def _time_events(fn, steps, flush=None):
+    """Device time per call of fn (CUDA events on the current stream, L2 flushed in between)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for s in range(steps):
+        if flush is not None:
+            flush.zero_()
+        ev[s][0].record(stream)
+        fn()
+        ev[s][1].record(stream)
+    torch.cuda.synchronize()
+    return float(np.mean([a.elapsed_time(b) for a, b in ev]))
+
+
+def run_batched(args, rank, world):
+    """64 uneven instances (grids 128^2 .. 1024^2 modes, 32 levels, 4 time levels, 10k .. 4M
+    binned random points each), every instance's reconstruction and gather in one captured
+    CUDA graph; autotuned FFT launch shapes. Compared with the same calls launched one by one."""
+    import torch
+    from paper_2005_12716_gb300 import _swense as S
+    from paper_2005_12716_gb300 import api
+    from wavegen import points as P, seas as W
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    rng = np.random.default_rng(20051273)
+    items, nodes_bytes = [], 0
+    for i in range(64):
+        nx, ny = (int(2 ** rng.integers(7, 11)) for _ in range(2))
+        lp = 1.0
+        Hs = rng.uniform(0.02, 0.05) * lp
+        sea = W.jonswap_sea(nx, ny, nx / 16 * lp, ny / 16 * lp, Hs, lp, heading=rng.uniform(0, 2 * np.pi),
+                            seed=int(rng.integers(1 << 30)))
+        z = P.levels_surface_clustered(-lp, 1.5 * Hs, 32, n_band=12, band=1.5 * Hs)
+        npts = int(np.exp(rng.uniform(np.log(1e4), np.log(4e6))))
+        pts = P.uniform_points(npts, (0, 0, -0.95 * lp), (nx / 16 * lp, ny / 16 * lp, 1.4 * Hs),
+                               int(rng.integers(1 << 30)))
+        Tp = 2 * np.pi / sea["jonswap"]["omega_p"]
+        tl = np.arange(4) * Tp / 16
+        items.append({"sea": sea, "z_levels": z, "pad_n": 1, "t_levels": tl,
+                      "t": float(tl[1] + 0.37 * (tl[2] - tl[1])), "pts": pts, "bin": True})
+        nodes_bytes += 4 * (32 * nx * ny * 16 + nx * ny * 4)
+    b = api.Batch(items, device=dev)
+    b.autotune()
+    for _ in range(max(1, args.warmup)):
+        b.run()
+    torch.cuda.synchronize()
+    l0 = S.swense_launches()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        b.run()
+    launches_per_step = S.swense_launches() - l0
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    steps = max(3, min(args.steps, 30))
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    ms_graph = _time_events(g.replay, steps, flush)
+    clk = clocks.stop()
+    ms_plain = _time_events(b.run, max(3, steps // 3), flush)
+    npts = b.points()
+    algo = nodes_bytes + npts * (12 + 20)
+    hbm = _peak_hbm()
+    line = {
+        "metric": "wave-field points/sec at stated err vs FP64 oracle; % of HBM roofline",
+        "value": npts / (ms_graph * 1e-3), "unit": "points/s", "n_gpus": 1, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": ms_graph, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"batched: 64 uneven JONSWAP instances, grids 128^2..1024^2 modes, "
+                               f"32 levels, 4 time levels (cubic), {npts} binned random points",
+                   "launch": "one CUDA graph per step (all instances)", "l2": "flushed between steps"},
+        "per_instance_launches_ms": ms_plain, "graph_speedup": ms_plain / ms_graph,
+        "gpu_launches": int(launches_per_step * steps),
+        "roofline": {"bound": "hbm", "kernel": "whole batch (grid writes + point I/O)",
+                     "achieved": algo / (ms_graph * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                     "frac": algo / (ms_graph * 1e-3) / 1e9 / hbm, "traffic": None},
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def _peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"])
+    return FALLBACK_HBM_GBS
+
+
+def run_learned(args, rank, world):
+    """Learned correction on the 3-D JONSWAP mesh workload: train on random seas with the same
+    grid spacing and levels (GPU data + GPU training), then time the learned gather and compare
+    its error against plain Lagrange interpolation at sampled points (FP64 oracle in the
+    CPU-baseline leg)."""
+    import torch
+    from paper_2005_12716_gb300 import api, learn
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    cfg, pts_np, desc = workload("jonswap3d", 1)
+    sea, z, tl, tq = cfg["sea"], cfg["z_levels"], cfg["t_levels"], cfg["t_query"]
+    t0 = time.perf_counter()
+    x, f, tg = learn.make_dataset(80, 65536, 64, 64, 4.0, 4.0, z, seed=20051274, device=dev)
+    mlp = api.Mlp(api.mlp_init(20051275), dev)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    losses = learn.train(mlp, x, f, tg, steps=4000, batch=8192, lr=2e-3, seed=20051276, log_every=500)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del x, f, tg
+    modes = api.upload_modes(sea, dev)
+    grid = api.fields_on_grid(modes, z, 1, tl)
+    pts = torch.from_numpy(pts_np).to(dev)
+    outs_l = {k: torch.empty(len(pts_np), dtype=torch.float32, device=dev) for k in ("eta", "u", "v", "w", "p")}
+    outs_p = {k: torch.empty(len(pts_np), dtype=torch.float32, device=dev) for k in ("eta", "u", "v", "w", "p")}
+    for _ in range(max(1, args.warmup)):
+        api.interp_learned(grid, tq, pts, mlp, out=outs_l)
+        api.interp(grid, tq, pts, out=outs_p)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    steps = max(3, min(args.steps, 20))
+    ms_l = _time_events(lambda: api.interp_learned(grid, tq, pts, mlp, out=outs_l), steps, flush)
+    ms_p = _time_events(lambda: api.interp(grid, tq, pts, out=outs_p), steps, flush)
+    rows = 4 * len(pts_np)
+    flops = rows * 2 * (67 * 64 + 64 * 64 + 64 * 4)
+    line = {
+        "metric": "wave-field points/sec at stated err vs FP64 oracle; % of HBM roofline",
+        "value": len(pts_np) / (ms_l * 1e-3), "unit": "points/s", "n_gpus": 1, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": ms_l, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16 network (fp32 accumulate), f32 gather",
+        "data": "synthetic", "config": {"workload": "learned correction on " + desc},
+        "plain_gather_ms": ms_p, "train_seconds": t_train, "data_seconds": t_data,
+        "train_loss_log": losses,
+        "network_tflops_if_all_time_in_mlp": flops / (ms_l * 1e-3) / 1e12,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        from oracle import modal
+        rng = np.random.default_rng(5)
+        idx = rng.choice(len(pts_np), 4000, replace=False)
+        ex = modal.fields_at_points(modal.propagate(sea, tq), pts_np[idx].astype(np.float64))
+        sel = torch.from_numpy(idx).to(dev)
+        err = {}
+        for name, o in (("plain", outs_p), ("learned", outs_l)):
+            vs = float(np.max(np.sqrt(ex["u"] ** 2 + ex["v"] ** 2 + ex["w"] ** 2)))
+            err[name] = {k: float(np.sqrt(np.mean((o[k][sel].cpu().numpy() - ex[k]) ** 2)) / vs)
+                         for k in ("u", "v", "w")}
+        line["rms_error_vs_exact_over_vmax"] = err
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_e1(args, rank, world):
+    """Divergence of the interpolated velocity on the x-z FV mesh for zero-padding 1, 2, 4, 8."""
+    import torch
+    from paper_2005_12716_gb300 import api
+    from wavegen import configs
+    cfg = configs.e1_divergence()
+    m = cfg["mesh"]
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    dv = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    fc = dv(m["face_centres"].astype(np.float32))
+    area, cf, vol = dv(m["face_area"].astype(np.float32)), dv(m["cell_faces"]), dv(m["cell_volume"].astype(np.float32))
+    below = torch.from_numpy(m["cell_centres"][:, 2] < -cfg["Hs"]).to(dev)
+    modes = api.upload_modes(cfg["sea"], dev)
+    res = {}
+    for pad in (1, 2, 4, 8):
+        grid = api.fields_on_grid(modes, cfg["z_levels"], pad, cfg["t_levels"])
+        o, _ = api.interp(grid, 0.0, fc)
+        d = api.fv_divergence(o["u"], o["v"], o["w"], area, cf, vol)
+        res[pad] = float(torch.sqrt(torch.mean(d[below].double() ** 2)).item())
+    line = {"metric": "RMS velocity divergence of the interpolated field [1/s]",
+            "config": {"workload": "e1: 2-D JONSWAP Tp 0.7 s, Hs 0.028 m, 128 modes, FV mesh "
+                                   "dx = lambda_p/100, dz = Hs/20, cells below -Hs"},
+            "rms_by_pad": res, "ratio_pad1_over_pad4": res[1] / res[4]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -413,7 +593,8 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         torch.distributed.init_process_group("nccl")
     try:
-        run_ours(args, rank, world)
+        {"batched": run_batched, "learned": run_learned, "e1": run_e1}.get(args.config, run_ours)(
+            args, rank, world)
     finally:
         if world > 1:
             torch.distributed.destroy_process_group()

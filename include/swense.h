@@ -143,6 +143,18 @@ int swense_fields_on_grid_noalloc(const swense_modes* modes, int32_t n_tl, const
                                   const swense_grid_desc* desc, float* nodes, float* eta,
                                   void* stream);
 
+/*
+ * swense_autotune_grid — choose the launch shape of swense_fields_on_grid for this grid shape
+ * (levels per column-transform block among 1, 2, 4 and the L2-resident level-chunk size among
+ * 16, 32, 64 MB) by timing each candidate three times on `stream`; the choice is cached per
+ * (nx, ny, pad_n, nz) and used by later calls. No counterpart in the paper. Writes the grid
+ * (same outputs as swense_fields_on_grid), synchronises the stream, must not be captured.
+ * lpc_out, chunk_bytes_out: host, may be NULL. Errors: as swense_fields_on_grid.
+ */
+int swense_autotune_grid(const swense_modes* modes, int32_t n_tl, const double* t,
+                         const swense_grid_desc* desc, float* nodes, float* eta,
+                         int32_t* lpc_out, int64_t* chunk_bytes_out, void* stream);
+
 /* Grid fields at n_tl time levels as written by swense_fields_on_grid. */
 typedef struct swense_grid {
   const float* nodes;       /* device float [n_tl][nz][ny_r][nx_r][4] */
@@ -192,6 +204,32 @@ int swense_interp_permuted(const swense_grid* grid, double t, const float* pts_s
                            const int32_t* perm, int64_t np, float* eta, float* u, float* v,
                            float* w, float* p, int32_t p_mode, double rho, double g,
                            int64_t* n_out_of_range, void* stream);
+
+/* One independent sea state of a batch: modes -> grid (own buffers) -> its own points. */
+typedef struct swense_instance {
+  swense_modes modes;
+  swense_grid_desc desc;
+  int32_t n_tl;
+  const double* t_levels;   /* host [n_tl]: grid time levels (propagation times with omega) */
+  float* nodes;             /* device [n_tl][nz][ny_r][nx_r][4] */
+  float* eta;               /* device [n_tl][ny_r][nx_r] */
+  const float* pts;         /* device [np][3]; sorted by swense_bin_points when perm != NULL */
+  const int32_t* perm;      /* device [np] from swense_bin_points, or NULL */
+  int64_t np;
+  double t;                 /* query time of the gather */
+  float *out_eta, *out_u, *out_v, *out_w, *out_p;   /* device [np] each, may be NULL */
+} swense_instance;
+
+/*
+ * swense_batch_run — many independent sea states of uneven sizes in one call (no counterpart
+ * in the paper): for each instance, swense_fields_on_grid then swense_interp (or
+ * swense_interp_permuted), all enqueued in order on `stream`, so that one call can be
+ * captured as a single CUDA graph and replayed as one launch. The first call (outside any
+ * capture) sizes the shared workspace for the largest instance. Errors: those of the
+ * per-instance calls (the first failing instance stops the batch).
+ */
+int swense_batch_run(const swense_instance* instances, int32_t n_instances, int32_t p_mode,
+                     double rho, double g, void* stream);
 
 enum swense_direct_precision {
   SWENSE_DIRECT_FP32 = 0,        /* FP32 arithmetic, exact integer-turn phases */

@@ -315,3 +315,41 @@ def swense_interp_permuted(grid, t, pts_sorted, perm, np_, eta=None, u=None, v=N
                                       g, ctypes.byref(cnt) if count_out_of_range else None,
                                       _stream(stream)))
     return cnt.value if count_out_of_range else None
+
+
+# ------------------------------------------------------------------ batches and autotuning
+class swense_instance(ctypes.Structure):
+    _fields_ = [
+        ("modes", swense_modes), ("desc", swense_grid_desc), ("n_tl", ctypes.c_int32),
+        ("t_levels", ctypes.c_void_p), ("nodes", ctypes.c_void_p), ("eta", ctypes.c_void_p),
+        ("pts", ctypes.c_void_p), ("perm", ctypes.c_void_p), ("np", ctypes.c_int64),
+        ("t", ctypes.c_double), ("out_eta", ctypes.c_void_p), ("out_u", ctypes.c_void_p),
+        ("out_v", ctypes.c_void_p), ("out_w", ctypes.c_void_p), ("out_p", ctypes.c_void_p),
+    ]
+
+
+_SIGS.update({
+    "swense_batch_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                        ctypes.c_double, ctypes.c_double, ctypes.c_void_p]),
+    "swense_autotune_grid": (ctypes.c_int, [ctypes.POINTER(swense_modes), ctypes.c_int32,
+                                            ctypes.c_void_p, ctypes.POINTER(swense_grid_desc),
+                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_void_p]),
+})
+
+
+def swense_batch_run(instances, p_mode=P_DYN, rho=1000.0, g=9.81, stream=None):
+    """instances: a ctypes array of swense_instance (kept alive by the caller)."""
+    _check(load().swense_batch_run(ctypes.addressof(instances), len(instances), p_mode, rho, g,
+                                   _stream(stream)))
+
+
+def swense_autotune_grid(modes, n_tl, t, desc, nodes, eta, stream=None):
+    lpc = ctypes.c_int32(0)
+    chunk = ctypes.c_int64(0)
+    tt = None if t is None else np.ascontiguousarray(t, np.float64)
+    _check(load().swense_autotune_grid(ctypes.byref(modes), n_tl,
+                                       None if tt is None else tt.ctypes.data,
+                                       ctypes.byref(desc), _ptr(nodes), _ptr(eta),
+                                       ctypes.byref(lpc), ctypes.byref(chunk), _stream(stream)))
+    return lpc.value, chunk.value

@@ -259,3 +259,57 @@ def interp_permuted(grid, t, pts_sorted, perm, p_mode="dyn", rho=1000.0, g=9.81,
                                    out.get("u"), out.get("v"), out.get("w"), out.get("p"),
                                    S.P_MODES[p_mode], rho, g, count_out_of_range, stream)
     return out, cnt
+
+
+class Batch:
+    """Device buffers and the C instance array of a batch of independent sea states."""
+
+    def __init__(self, items, p_mode="dyn", device="cuda"):
+        """items: list of dicts with keys sea, z_levels, pad_n, t_levels, t, pts (numpy [n][3]),
+        and optional 'bin' (sort the points with swense_bin_points once)."""
+        self.items = []
+        self.arr = (S.swense_instance * len(items))()
+        self.p_mode = S.P_MODES[p_mode]
+        for i, it in enumerate(items):
+            modes = upload_modes(it["sea"], device)
+            grid = alloc_grid(modes, it["z_levels"], it["pad_n"], it["t_levels"], device)
+            pts = torch.from_numpy(np.ascontiguousarray(it["pts"], np.float32)).to(device)
+            perm = None
+            if it.get("bin", False):
+                perm, pts = bin_points(grid, pts)
+            n = pts.shape[0]
+            out = {k: torch.empty(n, dtype=torch.float32, device=device)
+                   for k in ("eta", "u", "v", "w", "p")}
+            desc = S.make_grid_desc(it["pad_n"], it["z_levels"])
+            tl = np.ascontiguousarray(it["t_levels"], np.float64)
+            c = self.arr[i]
+            c.modes = modes.c_struct()
+            c.desc = desc
+            c.n_tl = len(tl)
+            c.t_levels = tl.ctypes.data
+            c.nodes, c.eta = grid.nodes.data_ptr(), grid.eta.data_ptr()
+            c.pts = pts.data_ptr()
+            c.perm = perm.data_ptr() if perm is not None else None
+            c.np = n
+            c.t = float(it["t"])
+            c.out_eta, c.out_u, c.out_v, c.out_w, c.out_p = (out[k].data_ptr() for k in
+                                                              ("eta", "u", "v", "w", "p"))
+            self.items.append({"modes": modes, "grid": grid, "pts": pts, "perm": perm, "out": out,
+                               "desc": desc, "tl": tl})
+
+    def autotune(self):
+        """Run the grid autotuner once per distinct grid shape."""
+        seen = set()
+        for it in self.items:
+            m, g = it["modes"], it["grid"]
+            key = (m.nx, m.ny, it["desc"].pad_n, it["desc"].nz)
+            if key in seen:
+                continue
+            seen.add(key)
+            S.swense_autotune_grid(m.c_struct(), len(it["tl"]), it["tl"], it["desc"], g.nodes, g.eta)
+
+    def run(self, rho=1000.0, g=9.81, stream=None):
+        S.swense_batch_run(self.arr, self.p_mode, rho, g, stream)
+
+    def points(self):
+        return sum(int(it["pts"].shape[0]) for it in self.items)

@@ -103,6 +103,11 @@ __global__ void __launch_bounds__(kDirThreads) k_direct_fp32(DirectArgs a) {
   }
   const unsigned X = turn_fraction(x, a.inv_lx), Y = turn_fraction(y, a.inv_ly);
   const float h = a.depth;
+  // e^{i 2 pi x / Lx}: the phase step from mode m to m + 1 along a row (same n)
+  float sstep, cstep;
+  sincospif(2.f * (float(int(X)) * 2.3283064365386963e-10f), &sstep, &cstep);
+  int prev_m = -2, prev_n = 0, run = 0;
+  float sn = 0.f, cs = 1.f;
   float s_eta = 0.f, s_u = 0.f, s_v = 0.f, s_w = 0.f, s_t = 0.f;
   for (unsigned base = 0; base < nm; base += kDirTile) {
     const unsigned cnt = min(unsigned(kDirTile), nm - base);
@@ -112,10 +117,22 @@ __global__ void __launch_bounds__(kDirThreads) k_direct_fp32(DirectArgs a) {
     float t_eta = 0.f, t_u = 0.f, t_v = 0.f, t_w = 0.f, t_t = 0.f;
     for (unsigned j = 0; j < cnt; ++j) {
       const float4 c0 = tile[j].c0, c1 = tile[j].c1, c2 = tile[j].c2, c3 = tile[j].c3;
-      const unsigned ph = unsigned(__float_as_int(c0.x)) * X + unsigned(__float_as_int(c0.y)) * Y;
-      const float turns = float(int(ph)) * 2.3283064365386963e-10f;   // 2^-32, in [-0.5, 0.5)
-      float sn, cs;
-      sincospif(2.f * turns, &sn, &cs);
+      const int m = __float_as_int(c0.x), n = __float_as_int(c0.y);
+      if (m == prev_m + 1 && n == prev_n && run < 15) {
+        // consecutive mode of the same row: advance the phase by the per-point step
+        const float c2 = fmaf(cs, cstep, -sn * sstep);
+        sn = fmaf(sn, cstep, cs * sstep);
+        cs = c2;
+        ++run;
+      } else {
+        // exact phase m X + n Y (mod 2^32) every 16 modes and at row starts
+        const unsigned ph = unsigned(m) * X + unsigned(n) * Y;
+        const float turns = float(int(ph)) * 2.3283064365386963e-10f;   // 2^-32, in [-0.5, 0.5)
+        sincospif(2.f * turns, &sn, &cs);
+        run = 0;
+      }
+      prev_m = m;
+      prev_n = n;
       const float k = c0.z;
       float F, S;
       depth_factors(k, z, h, F, S);

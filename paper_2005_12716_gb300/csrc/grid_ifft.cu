@@ -16,7 +16,9 @@
 // per time level (pass A on A^eta; pass B packs two grid rows per complex transform).
 // 2-D (ny == 1): pass B alone, reading the modes directly.
 #include <algorithm>
+#include <array>
 #include <cmath>
+#include <map>
 #include <mutex>
 #include <string>
 
@@ -406,9 +408,24 @@ __global__ void __launch_bounds__(256, 2) k_row_fft(RowArgs a) {
   }
 }
 
+// Launch-shape choices of the warp-register path, per grid shape (set by swense_autotune_grid;
+// defaults otherwise).
+struct Tune {
+  int lpc = kColLevels;                 // levels per column-transform CTA
+  size_t chunk_bytes = kChunkBytes;     // scratch per level chunk (L2-resident)
+};
+std::mutex g_tune_mutex;
+std::map<std::array<int64_t, 4>, Tune> g_tune;
+
+Tune tuned(int nx, int ny, int pad, int nz) {
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  auto it = g_tune.find({nx, ny, pad, nz});
+  return it == g_tune.end() ? Tune{} : it->second;
+}
+
 // Validated sizes and derived constants of one swense_fields_on_grid request.
 struct GridPlan {
-  int nx, ny, nz, n_tl, nxh1, Mh;
+  int nx, ny, nz, n_tl, nxh1, Mh, pad;
   int64_t Nxr, Nyr;
   size_t nslot, per_level, prop_bytes, geta_bytes;
   Levels lev;
@@ -501,6 +518,7 @@ int plan_grid(const swense_modes* md, int32_t n_tl, const double* t, const swens
     return fail(SWENSE_ERR_ARG, "nodes must be 16-byte aligned, eta 4-byte aligned");
   p->nx = nx;
   p->ny = ny;
+  p->pad = pad;
   p->nz = nz;
   p->n_tl = n_tl;
   p->nxh1 = nx / 2 + 1;
@@ -522,7 +540,7 @@ size_t scratch_bytes(const GridPlan& p, int chunk) {
 
 // Enqueue every kernel of the request; `ws` holds scratch_bytes(p, chunk) bytes.
 int launch_grid(const GridPlan& p, const swense_modes* md, const double* t, float* nodes, float* eta,
-                void* ws, int chunk, cudaStream_t stream) {
+                void* ws, int chunk, cudaStream_t stream, int lpc = kColLevels) {
   const float2* tw = nullptr;
   {
     int st = twiddles(stream, &tw);
@@ -655,7 +673,7 @@ int launch_grid(const GridPlan& p, const swense_modes* md, const double* t, floa
       ca.Mh = Mh;
       ca.Nyr = int(Nyr);
       ca.cb = kColBlock;
-      ca.lpc = kColLevels;
+      ca.lpc = lpc;
       ca.kxs = kxs;
       ca.kys = kys;
       ca.depth = depth;
@@ -675,7 +693,7 @@ int launch_grid(const GridPlan& p, const swense_modes* md, const double* t, floa
         ca.nlev = nl;
         ra.lev0 = l0;
         int st = launch_col_e(int(Nyr / 32), ca, p.lev,
-                              dim3((Mh + kColBlock - 1) / kColBlock, (nl + kColLevels - 1) / kColLevels),
+                              dim3((Mh + kColBlock - 1) / kColBlock, (nl + lpc - 1) / lpc),
                               smem_col, stream);
         if (!st) st = launch_row_e(int(Nxr / 32), ra,
                                    dim3(unsigned((Nyr + kRowBlock - 1) / kRowBlock), nl), smem_row, stream);
@@ -717,14 +735,63 @@ extern "C" int swense_fields_on_grid(const swense_modes* md, int32_t n_tl, const
   GridPlan p;
   int st = plan_grid(md, n_tl, t, desc, nodes, eta, &p);
   if (st) return st;
-  const int chunk = p.ny > 1 ? int(std::max<size_t>(1, std::min<size_t>(p.nz, kChunkBytes / p.per_level))) : 0;
+  const Tune tn = tuned(p.nx, p.ny, p.pad, p.nz);
+  const int chunk = p.ny > 1 ? int(std::max<size_t>(1, std::min<size_t>(p.nz, tn.chunk_bytes / p.per_level))) : 0;
   void* ws = nullptr;
   const size_t ws_bytes = scratch_bytes(p, chunk);
   if (ws_bytes) {
     st = workspace(ws_bytes, stream, &ws);
     if (st) return st;
   }
-  return launch_grid(p, md, t, nodes, eta, ws, chunk, stream);
+  return launch_grid(p, md, t, nodes, eta, ws, chunk, stream, tn.lpc);
+}
+
+extern "C" int swense_autotune_grid(const swense_modes* md, int32_t n_tl, const double* t,
+                                    const swense_grid_desc* desc, float* nodes, float* eta,
+                                    int32_t* lpc_out, int64_t* chunk_bytes_out, void* stream_) {
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+  GridPlan p;
+  int st = plan_grid(md, n_tl, t, desc, nodes, eta, &p);
+  if (st) return st;
+  Tune best{};
+  if (warp_path(p.ny, p.Nxr, p.Nyr)) {
+    cudaEvent_t e0, e1;
+    SWENSE_CUDA_TRY(cudaEventCreate(&e0));
+    SWENSE_CUDA_TRY(cudaEventCreate(&e1));
+    float best_ms = 1e30f;
+    for (int lpc : {1, 2, 4}) {
+      for (size_t mb : {16, 32, 64}) {
+        const size_t cb = mb << 20;
+        const int chunk = int(std::max<size_t>(1, std::min<size_t>(p.nz, cb / p.per_level)));
+        void* ws = nullptr;
+        st = workspace(scratch_bytes(p, chunk), stream, &ws);
+        if (!st) st = launch_grid(p, md, t, nodes, eta, ws, chunk, stream, lpc);   // warm
+        float ms = 0.f, tot = 0.f;
+        for (int rep = 0; rep < 3 && !st; ++rep) {
+          if (cudaEventRecord(e0, stream) != cudaSuccess) { st = SWENSE_ERR_CUDA; break; }
+          st = launch_grid(p, md, t, nodes, eta, ws, chunk, stream, lpc);
+          if (cudaEventRecord(e1, stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+              cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) st = SWENSE_ERR_CUDA;
+          tot += ms;
+        }
+        if (st) break;
+        if (tot < best_ms) {
+          best_ms = tot;
+          best.lpc = lpc;
+          best.chunk_bytes = cb;
+        }
+      }
+      if (st) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st) return st == SWENSE_ERR_CUDA ? cuda_fail(cudaGetLastError(), "autotune timing") : st;
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune[{p.nx, p.ny, p.pad, p.nz}] = best;
+  }
+  if (lpc_out) *lpc_out = best.lpc;
+  if (chunk_bytes_out) *chunk_bytes_out = int64_t(best.chunk_bytes);
+  return SWENSE_OK;
 }
 
 // ---------------------------------------------------------------------------------------------
