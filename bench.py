@@ -316,7 +316,7 @@ def run_ours(args, rank, world):
     }
     stages["grid_ifft"]["launches_per_step"] = int(launches // args.steps) - 1
     dom = "interp" if k2_ms >= k1_ms else "grid_ifft"
-    kname = "k_interp" if dom == "interp" else "grid_ifft (k_pass_a + k_pass_b)"
+    kname = "k_interp_box" if dom == "interp" else "grid_ifft (k_col_stk + k_row_stk)"
     tr = NCU_TRAFFIC.get(kname)
     traffic = tr["bytes"] if tr and tr.get("hash") == src_hash and tr.get("workload") == desc else None
     roofline = {"bound": "hbm", "kernel": kname, "achieved": stages[dom]["achieved_gbs"],
@@ -493,8 +493,8 @@ def _peak_hbm():
 
 
 def run_learned(args, rank, world):
-    """Learned correction on the 3-D JONSWAP mesh workload: train on random seas with the same
-    grid spacing and levels (GPU data + GPU training), then time the learned gather and compare
+    """Learned correction on the 3-D JONSWAP mesh workload: train on random JONSWAP seas with the
+    same grid spacing and levels (GPU data + GPU training), then time the learned gather and compare
     its error against plain Lagrange interpolation at sampled points (FP64 oracle in the
     CPU-baseline leg)."""
     import torch
@@ -504,7 +504,8 @@ def run_learned(args, rank, world):
     cfg, pts_np, desc = workload("jonswap3d", 1)
     sea, z, tl, tq = cfg["sea"], cfg["z_levels"], cfg["t_levels"], cfg["t_query"]
     t0 = time.perf_counter()
-    x, f, tg = learn.make_dataset(80, 65536, 64, 64, 4.0, 4.0, z, seed=20051274, device=dev)
+    x, f, tg = learn.make_dataset(80, 65536, 64, 64, 4.0, 4.0, z, seed=20051274, device=dev,
+                                  kind="jonswap")
     mlp = api.Mlp(api.mlp_init(20051275), dev)
     torch.cuda.synchronize()
     t_data = time.perf_counter() - t0

@@ -71,6 +71,14 @@ enum swense_p_mode {
   SWENSE_P_TOTAL = 2   /* p = -rho (dphi/dt + |u|^2 / 2) - rho g z */
 };
 
+/* Horizontal interpolation scheme of the grid (vertical and time: Lagrange in both). */
+enum swense_scheme {
+  SWENSE_LAGRANGE3 = 0,  /* grid holds node values; 4-point Lagrange in x and y */
+  SWENSE_SPLINE3 = 1     /* the paper's "cubic spline": grid holds periodic cubic B-spline
+                            coefficients (modes divided by the B-spline symbol before the
+                            transforms) and the gather uses cubic B-spline weights in x and y */
+};
+
 /* Spectral modal amplitudes of one sea state (paper: A^eta_i, A^phi_i of Eqs.
  * whatIsSpectralMethod1 / whatIsSpectralMethod; A^phit their time derivative's modes). */
 typedef struct swense_modes {
@@ -92,6 +100,7 @@ typedef struct swense_grid_desc {
   int32_t pad_n;           /* zero-padding factor: 1, 2, 4 or 8 */
   int32_t nz;              /* number of levels, 4 <= nz <= SWENSE_MAX_LEVELS */
   const float* z_levels;   /* host [nz], strictly increasing */
+  int32_t scheme;          /* enum swense_scheme */
 } swense_grid_desc;
 
 /*
@@ -145,11 +154,14 @@ int swense_fields_on_grid_noalloc(const swense_modes* modes, int32_t n_tl, const
 
 /*
  * swense_autotune_grid — choose the launch shape of swense_fields_on_grid for this grid shape
- * (levels per column-transform block among 1, 2, 4 and the L2-resident level-chunk size among
- * 16, 32, 64 MB) by timing each candidate three times on `stream`; the choice is cached per
- * (nx, ny, pad_n, nz) and used by later calls. No counterpart in the paper. Writes the grid
- * (same outputs as swense_fields_on_grid), synchronises the stream, must not be captured.
- * lpc_out, chunk_bytes_out: host, may be NULL. Errors: as swense_fields_on_grid.
+ * (the transform path: warp-register kernels with 1, 2 or 4 levels per column-transform block,
+ * or the shared-memory kernels; and the L2-resident level-chunk size among 16, 32, 64 MB) by
+ * timing each candidate three times on `stream`; the choice is cached per (nx, ny, pad_n, nz)
+ * and used by later calls. No counterpart in the paper. Writes the grid (same outputs as
+ * swense_fields_on_grid), synchronises the stream, must not be captured. 2-D grids have a
+ * single path (nothing to tune; *lpc_out = -1).
+ * lpc_out (0 = shared-memory path), chunk_bytes_out: host, may be NULL. Errors: as
+ * swense_fields_on_grid.
  */
 int swense_autotune_grid(const swense_modes* modes, int32_t n_tl, const double* t,
                          const swense_grid_desc* desc, float* nodes, float* eta,
@@ -164,6 +176,7 @@ typedef struct swense_grid {
   double Lx, Ly;            /* domain lengths (Ly ignored when ny_r = 1) */
   const float* z_levels;    /* host [nz], strictly increasing */
   const double* t_levels;   /* host [n_tl], strictly increasing */
+  int32_t scheme;           /* enum swense_scheme the grid was built with */
 } swense_grid;
 
 /*

@@ -132,3 +132,84 @@ def stencil_features(nodes_tl, Lx, Ly, z_levels, t_levels, pts, t):
     fz = (pts[:, 2] - zl[j0 + 1]) / (zl[j0 + 2] - zl[j0 + 1])
     off = np.stack([sx - np.floor(sx), sy - np.floor(sy), fz], 1)
     return st, off, lag
+
+
+def _periodic_spline_second_derivs(f, h):
+    """Second derivatives M of the periodic cubic spline through f (last axis), spacing h:
+    M_{i-1} + 4 M_i + M_{i+1} = 6 (f_{i+1} - 2 f_i + f_{i-1}) / h^2, indices modulo N (textbook
+    cyclic tridiagonal system, solved directly)."""
+    f = np.asarray(f, np.float64)
+    n = f.shape[-1]
+    A = 4.0 * np.eye(n) + np.eye(n, k=1) + np.eye(n, k=-1)
+    A[0, -1] += 1.0
+    A[-1, 0] += 1.0
+    if n == 1:
+        A = np.array([[6.0]])
+    rhs = 6.0 * (np.roll(f, -1, axis=-1) - 2.0 * f + np.roll(f, 1, axis=-1)) / (h * h)
+    return np.linalg.solve(A, rhs.reshape(-1, n).T).T.reshape(f.shape)
+
+
+def _spline_eval(f, M, h, i, t):
+    """Periodic cubic spline on [x_i, x_i+1] at fraction t (arrays broadcast over the leading
+    axes; f, M indexed on the last axis)."""
+    n = f.shape[-1]
+    lead = np.broadcast_shapes(f.shape[:-1], M.shape[:-1], np.shape(i))
+    f = np.broadcast_to(f, lead + (n,))
+    M = np.broadcast_to(M, lead + (n,))
+    i = np.broadcast_to(i, lead)
+    i1 = (i + 1) % n
+    fi, fj = np.take_along_axis(f, i[..., None], -1)[..., 0], np.take_along_axis(f, i1[..., None], -1)[..., 0]
+    Mi, Mj = np.take_along_axis(M, i[..., None], -1)[..., 0], np.take_along_axis(M, i1[..., None], -1)[..., 0]
+    u = 1.0 - t
+    return u * fi + t * fj + h * h / 6.0 * ((u ** 3 - u) * Mi + (t ** 3 - t) * Mj)
+
+
+def interp_points_spline(nodes_tl, eta_tl, Lx, Ly, z_levels, t_levels, pts, t,
+                         rho=1000.0, g=9.81, p_mode="dyn"):
+    """The paper's "cubic spline" reading (SPLINE3): periodic cubic splines through the grid
+    values along x, then along y (tensor product), Lagrange over the 4 levels around the point
+    and over the time levels (as in ``interp_points``), then Bernoulli. Slow; small cases only."""
+    nodes_tl = np.asarray(nodes_tl, np.float64)
+    eta_tl = np.asarray(eta_tl, np.float64)
+    TL, nz, nyr, nxr, _ = nodes_tl.shape
+    pts = np.asarray(pts, np.float64)
+    n = len(pts)
+    wt = lagrange_basis(np.asarray(t_levels, np.float64), np.float64(t))
+    G = np.tensordot(wt, nodes_tl, axes=(0, 0))                       # [nz][ny][nx][4]
+    E = np.tensordot(wt, eta_tl, axes=(0, 0))                         # [ny][nx]
+    hx = Lx / nxr
+    hy = Ly / nyr if nyr > 1 else 1.0
+    sx = pts[:, 0] / hx
+    ix = np.floor(sx).astype(np.int64) % nxr
+    tx = sx - np.floor(sx)
+    if nyr > 1:
+        sy = pts[:, 1] / hy
+        iy = np.floor(sy).astype(np.int64) % nyr
+        ty = sy - np.floor(sy)
+    j0, wz, inside = level_stencil(pts[:, 2], z_levels)
+
+    def along_xy(field):
+        """field [ny][nx] -> spline value at each point (x then y)."""
+        Mx = _periodic_spline_second_derivs(field, hx)                # [ny][nx]
+        rows = _spline_eval(np.broadcast_to(field, (n,) + field.shape),
+                            np.broadcast_to(Mx, (n,) + field.shape), hx,
+                            np.broadcast_to(ix[:, None], (n, field.shape[0])),
+                            tx[:, None])                              # [n][ny]
+        if nyr == 1:
+            return rows[:, 0]
+        My = _periodic_spline_second_derivs(rows, hy)                 # [n][ny]
+        return _spline_eval(rows, My, hy, iy, ty)
+
+    out4 = np.zeros((n, 4))
+    for a in range(4):
+        for lev in np.unique(j0 + a):
+            sel = (j0 + a) == lev
+            for q in range(4):
+                vals = along_xy(G[lev, :, :, q])
+                out4[sel, q] += wz[sel, a] * vals[sel]
+    eta = along_xy(E)
+    u, v, w, phit = (out4[:, q].copy() for q in range(4))
+    for arr in (u, v, w, phit):
+        arr[~inside] = np.nan
+    p = bernoulli(phit, u, v, w, pts[:, 2], rho, g, p_mode)
+    return {"eta": eta, "u": u, "v": v, "w": w, "phit": phit, "p": p, "out_of_range": ~inside}

@@ -32,7 +32,8 @@ class swense_modes(ctypes.Structure):
 
 
 class swense_grid_desc(ctypes.Structure):
-    _fields_ = [("pad_n", ctypes.c_int32), ("nz", ctypes.c_int32), ("z_levels", ctypes.c_void_p)]
+    _fields_ = [("pad_n", ctypes.c_int32), ("nz", ctypes.c_int32), ("z_levels", ctypes.c_void_p),
+                ("scheme", ctypes.c_int32)]
 
 
 class swense_grid(ctypes.Structure):
@@ -42,9 +43,12 @@ class swense_grid(ctypes.Structure):
         ("n_tl", ctypes.c_int32),
         ("Lx", ctypes.c_double), ("Ly", ctypes.c_double),
         ("z_levels", ctypes.c_void_p), ("t_levels", ctypes.c_void_p),
+        ("scheme", ctypes.c_int32),
     ]
 
 
+LAGRANGE3, SPLINE3 = 0, 1
+SCHEMES = {"lagrange3": LAGRANGE3, "spline3": SPLINE3}
 P_DYN, P_PHIT, P_TOTAL = 0, 1, 2
 P_MODES = {"dyn": P_DYN, "phit": P_PHIT, "total": P_TOTAL}
 MAX_LEVELS, MAX_FFT, MAX_TL = 256, 8192, 4
@@ -138,18 +142,18 @@ def make_modes(nx, ny, Lx, Ly, depth, A_eta, A_phi, A_phit, n_snap=1, omega=None
     return m
 
 
-def make_grid_desc(pad_n, z_levels):
+def make_grid_desc(pad_n, z_levels, scheme=LAGRANGE3):
     z = np.ascontiguousarray(z_levels, np.float32)
-    d = swense_grid_desc(pad_n, len(z), z.ctypes.data)
+    d = swense_grid_desc(pad_n, len(z), z.ctypes.data, scheme)
     d._keep = z
     return d
 
 
-def make_grid(nodes, eta, nx_r, ny_r, nz, n_tl, Lx, Ly, z_levels, t_levels):
+def make_grid(nodes, eta, nx_r, ny_r, nz, n_tl, Lx, Ly, z_levels, t_levels, scheme=LAGRANGE3):
     z = np.ascontiguousarray(z_levels, np.float32)
     t = np.ascontiguousarray(t_levels, np.float64)
     g = swense_grid(_ptr(nodes), _ptr(eta), nx_r, ny_r, nz, n_tl, Lx, Ly, z.ctypes.data,
-                    t.ctypes.data)
+                    t.ctypes.data, scheme)
     g._keep = (nodes, eta, z, t)
     return g
 

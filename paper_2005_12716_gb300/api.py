@@ -60,30 +60,32 @@ class DeviceGrid:
     t_levels: np.ndarray
     Lx: float
     Ly: float
+    scheme: int = 0
 
     def c_struct(self):
         return S.make_grid(self.nodes, self.eta, self.nx_r, self.ny_r, len(self.z_levels),
-                           len(self.t_levels), self.Lx, self.Ly, self.z_levels, self.t_levels)
+                           len(self.t_levels), self.Lx, self.Ly, self.z_levels, self.t_levels,
+                           self.scheme)
 
 
 def grid_dims(modes, pad_n):
     return pad_n * modes.nx, (pad_n * modes.ny if modes.ny > 1 else 1)
 
 
-def alloc_grid(modes, z_levels, pad_n, t_levels, device="cuda"):
+def alloc_grid(modes, z_levels, pad_n, t_levels, device="cuda", scheme="lagrange3"):
     nxr, nyr = grid_dims(modes, pad_n)
     tl = len(t_levels)
     nodes = torch.empty((tl, len(z_levels), nyr, nxr, 4), dtype=torch.float32, device=device)
     eta = torch.empty((tl, nyr, nxr), dtype=torch.float32, device=device)
     return DeviceGrid(nodes, eta, nxr, nyr, np.asarray(z_levels, np.float32),
-                      np.asarray(t_levels, np.float64), modes.Lx, modes.Ly)
+                      np.asarray(t_levels, np.float64), modes.Lx, modes.Ly, S.SCHEMES[scheme])
 
 
-def fields_on_grid(modes, z_levels, pad_n, t_levels, out=None, stream=None):
+def fields_on_grid(modes, z_levels, pad_n, t_levels, out=None, stream=None, scheme="lagrange3"):
     """swense_fields_on_grid over all time levels; returns a DeviceGrid."""
     g = out if out is not None else alloc_grid(modes, z_levels, pad_n, t_levels,
-                                               modes.A_eta.device)
-    desc = S.make_grid_desc(pad_n, z_levels)
+                                               modes.A_eta.device, scheme)
+    desc = S.make_grid_desc(pad_n, z_levels, g.scheme)
     S.swense_fields_on_grid(modes.c_struct(), len(t_levels), np.asarray(t_levels, np.float64),
                             desc, g.nodes, g.eta, stream)
     return g

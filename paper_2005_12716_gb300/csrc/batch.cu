@@ -23,6 +23,7 @@ extern "C" int swense_batch_run(const swense_instance* inst, int32_t n, int32_t 
     gr.Ly = c.modes.Ly;
     gr.z_levels = c.desc.z_levels;
     gr.t_levels = c.t_levels;
+    gr.scheme = c.desc.scheme;
     st = c.perm ? swense_interp_permuted(&gr, c.t, c.pts, c.perm, c.np, c.out_eta, c.out_u, c.out_v,
                                          c.out_w, c.out_p, p_mode, rho, g, nullptr, stream)
                 : swense_interp(&gr, c.t, c.pts, c.np, c.out_eta, c.out_u, c.out_v, c.out_w, c.out_p,

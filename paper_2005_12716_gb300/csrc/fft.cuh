@@ -75,6 +75,17 @@ __device__ __forceinline__ void depth_factors(float k, float z, float h, float& 
   S = (e1 - e2) / d;
 }
 
+// Prefilter of the periodic cubic-spline scheme. The spline interpolating grid values f_i is
+// sum_j c_j B3(x/h - j) with (c_{i-1} + 4 c_i + c_{i+1}) / 6 = f_i; for one Fourier mode this
+// divides its amplitude by the symbol (2 + cos(2 pi j / N)) / 3 of that averaging, per axis. So
+// B-spline coefficients on the grid are the inverse transform of the modes divided by the
+// symbols: 1 / prod over the horizontal axes, for signed mode j on an axis of N refined nodes.
+__device__ __forceinline__ float spline_prefilter(int m, int Nx, int n, int Ny) {
+  float f = 3.f / (2.f + cospif(2.f * float(m) / float(Nx)));
+  if (Ny > 1) f *= 3.f / (2.f + cospif(2.f * float(n) / float(Ny)));
+  return f;
+}
+
 }  // namespace swense
 
 namespace swense {
@@ -170,6 +181,146 @@ __device__ __forceinline__ void warp_fft(float2 (&v)[E], const WarpFftTw<E>& T, 
       v[m] = s > 1 ? cmul(r, w) : r;
     }
   }
+}
+
+}  // namespace swense
+
+namespace swense {
+
+// ------------------------------------------------------------------------------------------------
+// Per-warp Stockham inverse DFT of length N = 32 E (E >= 8), radix-8 passes followed by one
+// radix-4 or radix-2 pass when log2 N is not a multiple of 3 (Stockham autosort: natural order in
+// and out). Butterfly j of a pass with radix R after NS points have been combined reads
+// x[j + r N/R], multiplies by e^{2 pi i (j mod NS) r / (NS R)}, takes the length-R DFT and writes
+// y[(j / NS) NS R + (j mod NS) + r NS]. Lane l owns butterflies j = l + 32 b. Between passes the
+// data go through a warp-private shared buffer with one pad element per 16 (index i + i/16),
+// which keeps every exchange at the 2-wavefront minimum; the first pass reads registers filled
+// by the caller (element b*8 + r holds position l + 32 b + r N/8) and the last pass leaves
+// element b*R + r holding output position l + 32 b + r N/R (coalesced stores).
+
+constexpr int stk_l2(int n) { return n <= 1 ? 0 : 1 + stk_l2(n >> 1); }
+constexpr int stk_npass(int n) { return stk_l2(n) / 3 + (stk_l2(n) % 3 != 0 ? 1 : 0); }
+constexpr int stk_radix(int n, int p) {
+  return p < stk_l2(n) / 3 ? 8 : (stk_l2(n) % 3 == 1 ? 2 : 4);
+}
+constexpr int stk_ns(int n, int p) { return p == 0 ? 1 : stk_ns(n, p - 1) * stk_radix(n, p - 1); }
+// distinct values of (j mod NS) among one lane's butterflies of pass p
+constexpr int stk_dist(int n, int p) {
+  return stk_ns(n, p) <= 32 ? 1
+                            : (stk_ns(n, p) / 32 < n / 32 / stk_radix(n, p) ? stk_ns(n, p) / 32
+                                                                            : n / 32 / stk_radix(n, p));
+}
+constexpr int stk_twoff(int n, int p) {
+  return p <= 1 ? 0 : stk_twoff(n, p - 1) + stk_dist(n, p - 1) * (stk_radix(n, p - 1) - 1);
+}
+// passes 1 .. stk_regpass - 1 keep their twiddles in registers; later passes read the table (L1)
+constexpr int stk_regpass(int n) { return n <= 256 ? stk_npass(n) : 2; }
+constexpr int stk_twn(int n) { return stk_twoff(n, stk_regpass(n)) > 0 ? stk_twoff(n, stk_regpass(n)) : 1; }
+constexpr int stk_buf(int n) { return n + n / 16; }   // padded buffer length (float2)
+
+__device__ __forceinline__ int stk_pad(int i) { return i + (i >> 4); }
+
+// Per-lane twiddles of the register-held passes (kernel-lifetime registers).
+// (one template instance per pass, so every register index is a compile-time constant)
+template <int N, int P = 1>
+__device__ __forceinline__ void stk_init(float2 (&T)[stk_twn(N)], const float2* __restrict__ tw, int lane) {
+  if constexpr (P < stk_regpass(N)) {
+    constexpr int R = stk_radix(N, P), NS = stk_ns(N, P), D = stk_dist(N, P), OFF = stk_twoff(N, P);
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      const int jm = NS <= 32 ? lane % NS : lane + 32 * d;
+#pragma unroll
+      for (int r = 1; r < R; ++r) T[OFF + d * (R - 1) + r - 1] = __ldg(&tw[jm * r * (SWENSE_MAX_FFT / (NS * R))]);
+    }
+    stk_init<N, P + 1>(T, tw, lane);
+  }
+}
+
+// Inverse DFTs of length 2, 4, 8 in registers (natural order), constants folded.
+__device__ __forceinline__ void stk_dft2(float2* v) {
+  const float2 a = v[0];
+  v[0] = cadd(a, v[1]);
+  v[1] = csub(a, v[1]);
+}
+__device__ __forceinline__ void stk_dft4(float2& a0, float2& a1, float2& a2, float2& a3) {
+  const float2 t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3);
+  const float2 t3 = cmul_i(csub(a1, a3));
+  a0 = cadd(t0, t2);
+  a2 = csub(t0, t2);
+  a1 = cadd(t1, t3);
+  a3 = csub(t1, t3);
+}
+__device__ __forceinline__ void stk_dft8(float2* v) {
+  float2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+  float2 o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+  stk_dft4(e0, e1, e2, e3);
+  stk_dft4(o0, o1, o2, o3);
+  const float c = 0.70710678118654752f;                         // e^{i pi/4} = c (1 + i)
+  o1 = make_float2(c * (o1.x - o1.y), c * (o1.x + o1.y));
+  o2 = cmul_i(o2);
+  o3 = make_float2(-c * (o3.x + o3.y), c * (o3.x - o3.y));      // e^{3 i pi/4} = c (-1 + i)
+  v[0] = cadd(e0, o0);
+  v[4] = csub(e0, o0);
+  v[1] = cadd(e1, o1);
+  v[5] = csub(e1, o1);
+  v[2] = cadd(e2, o2);
+  v[6] = csub(e2, o2);
+  v[3] = cadd(e3, o3);
+  v[7] = csub(e3, o3);
+}
+
+template <int N, int P>
+__device__ __forceinline__ void stk_pass(float2 (&v)[N / 32], const float2 (&T)[stk_twn(N)],
+                                         const float2* __restrict__ tw, float2* buf, int lane) {
+  constexpr int E = N / 32, R = stk_radix(N, P), NS = stk_ns(N, P), B = E / R;
+  if constexpr (P > 0 && P < stk_regpass(N)) {
+    constexpr int OFF = stk_twoff(N, P);
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const int d = NS <= 32 ? 0 : b % (NS / 32);
+#pragma unroll
+      for (int r = 1; r < R; ++r)
+        v[b * R + r] = cmul(v[b * R + r], T[OFF + d * (R - 1) + r - 1]);
+    }
+  } else if constexpr (P > 0) {
+    constexpr int step = SWENSE_MAX_FFT / (NS * R);
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const int jm = NS <= 32 ? lane % NS : lane + 32 * (b % (NS / 32));
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[b * R + r] = cmul(v[b * R + r], __ldg(&tw[jm * r * step]));
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < B; ++b) {
+    if constexpr (R == 8) stk_dft8(&v[b * 8]);
+    else if constexpr (R == 4) stk_dft4(v[b * 4], v[b * 4 + 1], v[b * 4 + 2], v[b * 4 + 3]);
+    else stk_dft2(&v[b * 2]);
+  }
+  if constexpr (P + 1 < stk_npass(N)) {
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const int j = lane + 32 * b;
+#pragma unroll
+      for (int r = 0; r < R; ++r) buf[stk_pad((j / NS) * NS * R + (j % NS) + r * NS)] = v[b * R + r];
+    }
+    __syncwarp();
+    constexpr int R2 = stk_radix(N, P + 1), B2 = E / R2;
+#pragma unroll
+    for (int b = 0; b < B2; ++b)
+#pragma unroll
+      for (int r = 0; r < R2; ++r) v[b * R2 + r] = buf[stk_pad(lane + 32 * b + r * (N / R2))];
+    __syncwarp();
+    stk_pass<N, P + 1>(v, T, tw, buf, lane);
+  }
+}
+
+// Full transform; see the block comment above for the register layouts in and out.
+template <int N>
+__device__ __forceinline__ void stk_fft(float2 (&v)[N / 32], const float2 (&T)[stk_twn(N)],
+                                        const float2* __restrict__ tw, float2* buf, int lane) {
+  static_assert(N >= 256 && N <= 1024, "per-warp Stockham sizes");
+  stk_pass<N, 0>(v, T, tw, buf, lane);
 }
 
 }  // namespace swense

@@ -43,6 +43,7 @@ struct PassAArgs {
   int lev0;              // first level of the chunk
   int eta_mode;
   float kxs, kys, depth;
+  int Nxr, spline;       // spline: store cubic B-spline coefficients (modes prefiltered)
 };
 
 __global__ void __launch_bounds__(256) k_pass_a(PassAArgs a, Levels L) {
@@ -66,12 +67,16 @@ __global__ void __launch_bounds__(256) k_pass_a(PassAArgs a, Levels L) {
       const int pos = n >= 0 ? n : a.Nyr + n;            // zero-padding between +n and -n
       const unsigned br = bitrev(unsigned(pos), a.log2Nyr);
       const size_t gi = size_t(r) * a.nxh1 + m;
+      const float pf = a.spline ? spline_prefilter(m, a.Nxr, n, a.Nyr) : 1.f;
       if (a.eta_mode) {
-        sm[c * a.Nyr + br] = __ldg(&a.A_eta[gi]);
+        const float2 e = __ldg(&a.A_eta[gi]);
+        sm[c * a.Nyr + br] = make_float2(pf * e.x, pf * e.y);
         continue;
       }
-      const float2 Ap = __ldg(&a.A_phi[gi]);
-      const float2 At = __ldg(&a.A_phit[gi]);
+      float2 Ap = __ldg(&a.A_phi[gi]);
+      float2 At = __ldg(&a.A_phit[gi]);
+      Ap = make_float2(pf * Ap.x, pf * Ap.y);
+      At = make_float2(pf * At.x, pf * At.y);
       const float kx = float(m) * a.kxs, ky = float(n) * a.kys;
       const float k = sqrtf(kx * kx + ky * ky);
       float F, S;
@@ -116,6 +121,7 @@ struct PassBArgs {
   int lev0;
   int mode;
   float kxs, depth;
+  int spline;
 };
 
 // Hermitian packing of two one-sided spectra P, Q (coefficients of real fields p, q) into one
@@ -153,8 +159,11 @@ __global__ void __launch_bounds__(256) k_pass_b(PassBArgs a, Levels L) {
         W = __ldcg(&a.G[base + 2 * fs]);
         T = __ldcg(&a.G[base + 3 * fs]);
       } else {
-        const float2 Ap = __ldg(&a.A_phi[m]);
-        const float2 At = __ldg(&a.A_phit[m]);
+        const float pf = a.spline ? spline_prefilter(m, a.Nxr, 0, 1) : 1.f;
+        float2 Ap = __ldg(&a.A_phi[m]);
+        float2 At = __ldg(&a.A_phit[m]);
+        Ap = make_float2(pf * Ap.x, pf * Ap.y);
+        At = make_float2(pf * At.x, pf * At.y);
         const float kx = float(m) * a.kxs;
         float F, S;
         depth_factors(kx, z, a.depth, F, S);
@@ -176,7 +185,9 @@ __global__ void __launch_bounds__(256) k_pass_b(PassBArgs a, Levels L) {
         Ea = __ldcg(&a.G[size_t(ya) * a.Mh + m]);
         if (yb < a.Nyr) Eb = __ldcg(&a.G[size_t(yb) * a.Mh + m]);
       } else {
+        const float pf = a.spline ? spline_prefilter(m, a.Nxr, 0, 1) : 1.f;
         Ea = __ldg(&a.A_eta[m]);
+        Ea = make_float2(pf * Ea.x, pf * Ea.y);
       }
       pack_pair(sm + size_t(pp) * a.Nxr, m, a.Nxr, a.log2Nxr, Ea, Eb);
     }
@@ -261,6 +272,7 @@ struct ColArgs {
   int cb, lpc;           // kx columns and levels per CTA
   int lev0, nlev;        // chunk
   float kxs, kys, depth;
+  int Nxr, spline;
 };
 
 // Modal field q at (kx, ky, |k|) with depth factors F, S: U = i kx F A, V = i ky F A,
@@ -317,6 +329,11 @@ __global__ void __launch_bounds__(256, 2) k_col_fft(ColArgs a, Levels L) {
         const int r = n >= 0 ? n : a.ny + n;
         Ap = sm[r * ld + c];
         At = sm[(a.ny + r) * ld + c];
+        if (a.spline) {
+          const float pf = spline_prefilter(m, a.Nxr, n, a.Nyr);
+          Ap = make_float2(pf * Ap.x, pf * Ap.y);
+          At = make_float2(pf * At.x, pf * At.y);
+        }
       }
       const float ky = float(n) * a.kys;
       const float kk = sqrtf(kx * kx + ky * ky);
@@ -408,10 +425,156 @@ __global__ void __launch_bounds__(256, 2) k_row_fft(RowArgs a) {
   }
 }
 
+// Stockham per-warp variants of the two transform kernels (N = transform length >= 256): same
+// inputs, outputs and layouts as k_col_fft / k_row_fft, with stk_fft (radix-8 register passes,
+// exchanges through a warp-private shared buffer) in place of the shuffle-based transform.
+template <int N, int NF>
+__global__ void __launch_bounds__(256, N >= 1024 ? 1 : 2) k_col_stk(ColArgs a, Levels L) {
+  extern __shared__ float2 sm[];                 // [2][ny][cb + 1] modes, then per-warp buffers
+  constexpr int E = N / 32, RL = stk_radix(N, stk_npass(N) - 1);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c0 = blockIdx.x * a.cb;
+  const int ncol = min(a.cb, a.Mh - c0);
+  const int ld = a.cb + 1;
+  float2* wbuf = sm + 2 * a.ny * ld + warp * stk_buf(N);
+  for (int i = threadIdx.x; i < a.ny * a.cb; i += blockDim.x) {
+    const int c = i % a.cb, r = i / a.cb;
+    const bool ok = c < ncol;
+    const size_t gi = ok ? size_t(r) * a.nxh1 + c0 + c : 0;
+    cp_async8(&sm[r * ld + c], &a.A_phi[gi], ok ? 8 : 0);
+    cp_async8(&sm[(a.ny + r) * ld + c], &a.A_phit[gi], ok ? 8 : 0);
+  }
+  float2 T[stk_twn(N)];
+  stk_init<N>(T, a.tw, lane);
+  cp_async_wait_all();
+  __syncthreads();
+  const int nyh = a.ny >> 1;
+  const int groups = 4 / NF;
+  const int ntask = a.lpc * ncol * groups;
+  for (int task = warp; task < ntask; task += blockDim.x >> 5) {
+    const int g = task % groups;
+    const int rest = task / groups;
+    const int c = rest % ncol;
+    const int level = blockIdx.y * a.lpc + rest / ncol;
+    if (level >= a.nlev) continue;
+    const float z = L.z[a.lev0 + level];
+    const int m = c0 + c;
+    const float kx = float(m) * a.kxs;
+    float2 v[NF][E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int p = lane + 32 * (e / 8) + (e % 8) * (N / 8);
+      int n;
+      bool live = true;
+      if (p < nyh) n = p;
+      else if (p > N - nyh) n = p - N;
+      else { n = 0; live = false; }
+      float2 Ap = make_float2(0.f, 0.f), At = make_float2(0.f, 0.f);
+      if (live) {
+        const int r = n >= 0 ? n : a.ny + n;
+        Ap = sm[r * ld + c];
+        At = sm[(a.ny + r) * ld + c];
+        if (a.spline) {
+          const float pf = spline_prefilter(m, a.Nxr, n, a.Nyr);
+          Ap = make_float2(pf * Ap.x, pf * Ap.y);
+          At = make_float2(pf * At.x, pf * At.y);
+        }
+      }
+      const float ky = float(n) * a.kys;
+      const float kk = sqrtf(kx * kx + ky * ky);
+      float F, S;
+      depth_factors(kk, z, a.depth, F, S);
+#pragma unroll
+      for (int f = 0; f < NF; ++f) v[f][e] = modal_field(g * NF + f, kx, ky, kk, F, S, Ap, At);
+    }
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      stk_fft<N>(v[f], T, a.tw, wbuf, lane);
+      float2* out = a.G + ((size_t(level) * 4 + g * NF + f) * a.Mh + m) * a.Nyr;
+#pragma unroll
+      for (int e = 0; e < E; ++e) __stcg(&out[lane + 32 * (e / RL) + (e % RL) * (N / RL)], v[f][e]);
+    }
+  }
+}
+
+// Hermitian packing of two real-output half spectra A, B (one column of the staged rows, stride
+// ld) into z = A + i B over the full length-N spectrum, in the first-pass register layout of
+// stk_fft; the upper half holds conj(A) + i conj(B) mirrored, the Nyquist slot stays zero.
+template <int N>
+__device__ __forceinline__ void row_pack(float2 (&z)[N / 32], const float2* A, const float2* B, int ld,
+                                         int Mh, int lane) {
+#pragma unroll
+  for (int e = 0; e < N / 32; ++e) {
+    const int p = lane + 32 * (e / 8) + (e % 8) * (N / 8);
+    const bool lo = p < Mh, hi = p > N - Mh;
+    float2 a = make_float2(0.f, 0.f), b = a;
+    if (lo || hi) {
+      const int o = (lo ? p : N - p) * ld;
+      a = A[o];
+      b = B[o];
+    }
+    if (p == 0) z[e] = make_float2(a.x, b.x);
+    else if (!hi) z[e] = make_float2(a.x - b.y, a.y + b.x);
+    else z[e] = make_float2(a.x + b.y, b.x - a.y);
+  }
+}
+
+template <int N>
+__global__ void __launch_bounds__(256, N >= 1024 ? 1 : 2) k_row_stk(RowArgs a) {
+  extern __shared__ float2 sm[];                 // [4][Mh][rb + 1] staging, then warp buffers
+  constexpr int E = N / 32, RL = stk_radix(N, stk_npass(N) - 1);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int y0 = blockIdx.x * a.rb;
+  const int level = blockIdx.y;
+  const int ld = a.rb + 1;
+  const float2* G = a.G + size_t(level) * 4 * a.Mh * a.Nyr;
+  float2* wbuf = sm + 4 * a.Mh * ld + warp * stk_buf(N);
+  for (int i = threadIdx.x; i < 4 * a.Mh * a.rb; i += blockDim.x) {
+    const int rr = i % a.rb, qm = i / a.rb;
+    const int y = y0 + rr;
+    cp_async8(&sm[qm * ld + rr], &G[size_t(qm) * a.Nyr + (y < a.Nyr ? y : 0)], y < a.Nyr ? 8 : 0);
+  }
+  float2 T[stk_twn(N)];
+  stk_init<N>(T, a.tw, lane);
+  cp_async_wait_all();
+  __syncthreads();
+  const size_t fs = size_t(a.Mh) * ld;
+  for (int rr = warp; rr < a.rb; rr += blockDim.x >> 5) {
+    const int y = y0 + rr;
+    if (y >= a.Nyr) break;
+    float4* out = a.nodes + (size_t(a.lev0 + level) * a.Nyr + y) * N;
+    if constexpr (N <= 256) {
+      float2 z1[E], z2[E];
+      row_pack<N>(z1, sm + rr, sm + fs + rr, ld, a.Mh, lane);
+      row_pack<N>(z2, sm + 2 * fs + rr, sm + 3 * fs + rr, ld, a.Mh, lane);
+      stk_fft<N>(z1, T, a.tw, wbuf, lane);
+      stk_fft<N>(z2, T, a.tw, wbuf, lane);
+#pragma unroll
+      for (int e = 0; e < E; ++e)
+        __stcs(&out[lane + 32 * (e / RL) + (e % RL) * (N / RL)],
+               make_float4(z1[e].x, z1[e].y, z2[e].x, z2[e].y));
+    } else {
+      // one transform at a time (register budget): each half of a node's float4 is written by
+      // its own pass; the two halves meet in L2 before the sector goes to DRAM
+      float2* o2 = reinterpret_cast<float2*>(out);
+#pragma unroll 1
+      for (int q = 0; q < 2; ++q) {
+        float2 z[E];
+        row_pack<N>(z, sm + 2 * q * fs + rr, sm + (2 * q + 1) * fs + rr, ld, a.Mh, lane);
+        stk_fft<N>(z, T, a.tw, wbuf, lane);
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+          __stcs(&o2[2 * (lane + 32 * (e / RL) + (e % RL) * (N / RL)) + q], z[e]);
+      }
+    }
+  }
+}
+
 // Launch-shape choices of the warp-register path, per grid shape (set by swense_autotune_grid;
 // defaults otherwise).
 struct Tune {
-  int lpc = kColLevels;                 // levels per column-transform CTA
+  int lpc = -1;                         // levels per column-transform CTA of the warp path;
+                                        // 0: shared-memory path; -1: default for the shape
   size_t chunk_bytes = kChunkBytes;     // scratch per level chunk (L2-resident)
 };
 std::mutex g_tune_mutex;
@@ -425,7 +588,7 @@ Tune tuned(int nx, int ny, int pad, int nz) {
 
 // Validated sizes and derived constants of one swense_fields_on_grid request.
 struct GridPlan {
-  int nx, ny, nz, n_tl, nxh1, Mh, pad;
+  int nx, ny, nz, n_tl, nxh1, Mh, pad, spline;
   int64_t Nxr, Nyr;
   size_t nslot, per_level, prop_bytes, geta_bytes;
   Levels lev;
@@ -441,14 +604,36 @@ int launch_col(const ColArgs& c, const Levels& L, dim3 grid, size_t smem, cudaSt
   return SWENSE_OK;
 }
 
+template <int N, int NF>
+int launch_col_stk(const ColArgs& c, const Levels& L, dim3 grid, size_t smem, cudaStream_t stream) {
+  smem += size_t(8) * stk_buf(N) * sizeof(float2);
+  int st = set_smem((const void*)k_col_stk<N, NF>, smem);
+  if (st) return st;
+  k_col_stk<N, NF><<<grid, kThreads, smem, stream>>>(c, L);
+  SWENSE_CUDA_TRY(cudaGetLastError());
+  count_launches(1);
+  return SWENSE_OK;
+}
+
+template <int N>
+int launch_row_stk(const RowArgs& r, dim3 grid, size_t smem, cudaStream_t stream) {
+  smem += size_t(8) * stk_buf(N) * sizeof(float2);
+  int st = set_smem((const void*)k_row_stk<N>, smem);
+  if (st) return st;
+  k_row_stk<N><<<grid, kThreads, smem, stream>>>(r);
+  SWENSE_CUDA_TRY(cudaGetLastError());
+  count_launches(1);
+  return SWENSE_OK;
+}
+
 int launch_col_e(int E, const ColArgs& c, const Levels& L, dim3 grid, size_t smem, cudaStream_t s) {
   switch (E) {
     case 1: return launch_col<1, 4>(c, L, grid, smem, s);
     case 2: return launch_col<2, 4>(c, L, grid, smem, s);
     case 4: return launch_col<4, 4>(c, L, grid, smem, s);
-    case 8: return launch_col<8, 2>(c, L, grid, smem, s);
-    case 16: return launch_col<16, 2>(c, L, grid, smem, s);
-    case 32: return launch_col<32, 1>(c, L, grid, smem, s);
+    case 8: return launch_col_stk<256, 2>(c, L, grid, smem, s);
+    case 16: return launch_col_stk<512, 1>(c, L, grid, smem, s);
+    case 32: return launch_col_stk<1024, 1>(c, L, grid, smem, s);
     default: return fail(SWENSE_ERR_UNSUPPORTED, "column transform size");
   }
 }
@@ -468,9 +653,9 @@ int launch_row_e(int E, const RowArgs& r, dim3 grid, size_t smem, cudaStream_t s
     case 1: return launch_row<1>(r, grid, smem, s);
     case 2: return launch_row<2>(r, grid, smem, s);
     case 4: return launch_row<4>(r, grid, smem, s);
-    case 8: return launch_row<8>(r, grid, smem, s);
-    case 16: return launch_row<16>(r, grid, smem, s);
-    case 32: return launch_row<32>(r, grid, smem, s);
+    case 8: return launch_row_stk<256>(r, grid, smem, s);
+    case 16: return launch_row_stk<512>(r, grid, smem, s);
+    case 32: return launch_row_stk<1024>(r, grid, smem, s);
     default: return fail(SWENSE_ERR_UNSUPPORTED, "row transform size");
   }
 }
@@ -516,6 +701,9 @@ int plan_grid(const swense_modes* md, int32_t n_tl, const double* t, const swens
   }
   if ((reinterpret_cast<uintptr_t>(nodes) & 15) || (reinterpret_cast<uintptr_t>(eta) & 3))
     return fail(SWENSE_ERR_ARG, "nodes must be 16-byte aligned, eta 4-byte aligned");
+  if (desc->scheme != SWENSE_LAGRANGE3 && desc->scheme != SWENSE_SPLINE3)
+    return fail(SWENSE_ERR_ARG, "unknown interpolation scheme");
+  p->spline = desc->scheme == SWENSE_SPLINE3;
   p->nx = nx;
   p->ny = ny;
   p->pad = pad;
@@ -614,6 +802,7 @@ int launch_grid(const GridPlan& p, const swense_modes* md, const double* t, floa
     b.Nyr = int(Nyr);
     b.kxs = kxs;
     b.depth = depth;
+    b.spline = p.spline;
 
     if (ny == 1) {
       b.mode = B_ETA_DIRECT;
@@ -643,6 +832,8 @@ int launch_grid(const GridPlan& p, const swense_modes* md, const double* t, floa
     a.kxs = kxs;
     a.kys = kys;
     a.depth = depth;
+    a.Nxr = int(Nxr);
+    a.spline = p.spline;
 
     // eta: pass A (eta mode) then pass B packing row pairs
     a.G = g_eta;
@@ -662,7 +853,7 @@ int launch_grid(const GridPlan& p, const swense_modes* md, const double* t, floa
     SWENSE_CUDA_TRY(cudaGetLastError());
     count_launches(1);
 
-    if (warp_path(ny, Nxr, Nyr)) {
+    if (lpc > 0 && warp_path(ny, Nxr, Nyr)) {
       ColArgs ca{};
       ca.A_phi = Ap;
       ca.A_phit = At;
@@ -677,6 +868,8 @@ int launch_grid(const GridPlan& p, const swense_modes* md, const double* t, floa
       ca.kxs = kxs;
       ca.kys = kys;
       ca.depth = depth;
+      ca.Nxr = int(Nxr);
+      ca.spline = p.spline;
       RowArgs ra{};
       ra.G = g_lev;
       ra.nodes = nodes_l;
@@ -743,7 +936,9 @@ extern "C" int swense_fields_on_grid(const swense_modes* md, int32_t n_tl, const
     st = workspace(ws_bytes, stream, &ws);
     if (st) return st;
   }
-  return launch_grid(p, md, t, nodes, eta, ws, chunk, stream, tn.lpc);
+  // untuned default: the warp path where its transforms stay in registers (n <= 512)
+  const int lpc = tn.lpc >= 0 ? tn.lpc : ((p.Nxr <= 512 && p.Nyr <= 512) ? kColLevels : 0);
+  return launch_grid(p, md, t, nodes, eta, ws, chunk, stream, lpc);
 }
 
 extern "C" int swense_autotune_grid(const swense_modes* md, int32_t n_tl, const double* t,
@@ -754,12 +949,13 @@ extern "C" int swense_autotune_grid(const swense_modes* md, int32_t n_tl, const 
   int st = plan_grid(md, n_tl, t, desc, nodes, eta, &p);
   if (st) return st;
   Tune best{};
-  if (warp_path(p.ny, p.Nxr, p.Nyr)) {
+  if (p.ny > 1) {
     cudaEvent_t e0, e1;
     SWENSE_CUDA_TRY(cudaEventCreate(&e0));
     SWENSE_CUDA_TRY(cudaEventCreate(&e1));
     float best_ms = 1e30f;
-    for (int lpc : {1, 2, 4}) {
+    for (int lpc : {0, 1, 2, 4}) {
+      if (lpc > 0 && !warp_path(p.ny, p.Nxr, p.Nyr)) continue;
       for (size_t mb : {16, 32, 64}) {
         const size_t cb = mb << 20;
         const int chunk = int(std::max<size_t>(1, std::min<size_t>(p.nz, cb / p.per_level)));

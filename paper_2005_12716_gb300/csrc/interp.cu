@@ -37,6 +37,7 @@ struct InterpArgs {
   float wt[SWENSE_MAX_TL];            // time weights
   int p_mode;
   float rho, g;
+  int spline;            // cubic B-spline weights in x and y (grid holds spline coefficients)
 };
 
 // Cell index (mod n) and in-cell offset f in [0, 1] of coordinate x for the node spacing
@@ -56,6 +57,15 @@ __device__ __forceinline__ void locate(float x, float s_hi, float s_lo, int n, i
     i += 1;
   }
   i0 = i & (n - 1);
+}
+
+// Uniform cubic B-spline basis of the coefficients -1, 0, 1, 2 at f.
+__device__ __forceinline__ void bspline4(float f, float w[4]) {
+  const float g = 1.f - f, f2 = f * f, f3 = f2 * f;
+  w[0] = g * g * g * (1.f / 6.f);
+  w[1] = fmaf(0.5f * f3, 1.f, fmaf(-f2, 1.f, 2.f / 3.f));      // (3f^3 - 6f^2 + 4) / 6
+  w[2] = fmaf(-0.5f, f3, fmaf(0.5f, f2, fmaf(0.5f, f, 1.f / 6.f)));   // (-3f^3 + 3f^2 + 3f + 1) / 6
+  w[3] = f3 * (1.f / 6.f);
 }
 
 // Lagrange basis of the nodes -1, 0, 1, 2 at f.
@@ -109,14 +119,14 @@ __device__ __forceinline__ PointCell point_cell(const InterpArgs& a, const Level
   PointCell c;
   float fx;
   locate(x, a.sx_hi, a.sx_lo, a.Nxr, c.ix, fx);
-  lagrange4_uniform(fx, c.wx);
+  if (a.spline) bspline4(fx, c.wx); else lagrange4_uniform(fx, c.wx);
   c.iy = 0;
   c.wy[0] = 1.f;
   c.wy[1] = c.wy[2] = c.wy[3] = 0.f;
   if (a.Nyr > 1) {
     float fy;
     locate(y, a.sy_hi, a.sy_lo, a.Nyr, c.iy, fy);
-    lagrange4_uniform(fy, c.wy);
+    if (a.spline) bspline4(fy, c.wy); else lagrange4_uniform(fy, c.wy);
   }
   // bracket: largest j with zs[j] <= z, clamped to [0, nz-2]; stencil j0 = clamp(j-1, 0, nz-4)
   const int nz = a.nz;
@@ -305,9 +315,12 @@ __global__ void __launch_bounds__(BOX_THREADS, 3) k_interp_box(InterpArgs a, Lev
   }
   // box: x nodes rel (mn0-1) .. (mx0+2), y likewise (one row in 2-D), levels mn2 .. mx2+3
   const int bx = mx[0] - mn[0] + 4;
+  // shared-memory row stride = 4 (mod 8) float4: reads of neighbouring cells (dx, dy in {0, 1})
+  // by one quarter-warp then fall into different bank groups
+  const int sbx = bx + ((4 - bx) & 7);
   const int by = a.Nyr > 1 ? mx[1] - mn[1] + 4 : 1;
   const int bz = mx[2] - mn[2] + 4;
-  const bool fits = int64_t(bx) * by * bz <= BOX_NODES && int64_t(bx) * by <= BOX_COLS &&
+  const bool fits = int64_t(sbx) * by * bz <= BOX_NODES && int64_t(sbx) * by <= BOX_COLS &&
                     bx <= a.Nxr && by <= a.Nyr;
   if (!fits) {
 #pragma unroll
@@ -330,7 +343,7 @@ __global__ void __launch_bounds__(BOX_THREADS, 3) k_interp_box(InterpArgs a, Lev
     for (int r = warp; r < by * bz; r += BOX_THREADS / 32) {
       const int lz = r / by, ly = r - lz * by;
       const float4* src = a.nodes + size_t(l0 + lz) * plane + size_t((y0 + ly) & (a.Nyr - 1)) * a.Nxr;
-      float4* dst = sbox + r * bx;
+      float4* dst = sbox + r * sbx;
       for (int lx = lane; lx < bx; lx += 32) {
         const int gx = (x0 + lx) & (a.Nxr - 1);
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -351,26 +364,26 @@ __global__ void __launch_bounds__(BOX_THREADS, 3) k_interp_box(InterpArgs a, Lev
         const int gx = (x0 + lx) & (a.Nxr - 1);
         float v = 0.f;
         for (int tl = 0; tl < a.n_tl; ++tl) v = fmaf(a.wt[tl], __ldg(&src[size_t(tl) * plane + gx]), v);
-        seta[ly * bx + lx] = v;
+        seta[ly * sbx + lx] = v;
       }
     }
   }
   __syncthreads();
-  const int zstride = by * bx;
+  const int zstride = by * sbx;
   const int nys = a.Nyr > 1 ? 4 : 1;
 #pragma unroll 1
   for (int k = 0; k < BOX_PPT; ++k) {
     const int64_t i = p0 + k * BOX_THREADS + threadIdx.x;
     if (i >= a.np) continue;
     const PointCell c = point_cell(a, zs, px[k], py[k], pz[k]);
-    const float4* base = sbox + ((jz[k] - mn[2]) * by + (ry[k] - mn[1])) * bx + (rx[k] - mn[0]);
+    const float4* base = sbox + ((jz[k] - mn[2]) * by + (ry[k] - mn[1])) * sbx + (rx[k] - mn[0]);
     unsigned long long uv = pack2(0.f, 0.f), wt = pack2(0.f, 0.f);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
         if (b >= nys) break;
-        const float4* row = base + q * zstride + b * bx;
+        const float4* row = base + q * zstride + b * sbx;
         const float wzy = c.wz[q] * c.wy[b];
 #pragma unroll
         for (int kx = 0; kx < 4; ++kx) {
@@ -383,12 +396,12 @@ __global__ void __launch_bounds__(BOX_THREADS, 3) k_interp_box(InterpArgs a, Lev
       }
     }
     float acc_eta = 0.f;
-    const float* ebase = seta + (ry[k] - mn[1]) * bx + (rx[k] - mn[0]);
+    const float* ebase = seta + (ry[k] - mn[1]) * sbx + (rx[k] - mn[0]);
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
       if (b >= nys) break;
 #pragma unroll
-      for (int kx = 0; kx < 4; ++kx) acc_eta = fmaf(c.wy[b] * c.wx[kx], ebase[b * bx + kx], acc_eta);
+      for (int kx = 0; kx < 4; ++kx) acc_eta = fmaf(c.wy[b] * c.wx[kx], ebase[b * sbx + kx], acc_eta);
     }
     store_point(a, i, make_float4(lo2(uv), hi2(uv), lo2(wt), hi2(wt)), acc_eta, pz[k], c.inside);
   }
@@ -566,6 +579,9 @@ int prepare_interp(const swense_grid* g, double t, const float* pts, int64_t np,
   a->p_mode = p_mode;
   a->rho = float(rho);
   a->g = float(grav);
+  if (g->scheme != SWENSE_LAGRANGE3 && g->scheme != SWENSE_SPLINE3)
+    return fail(SWENSE_ERR_ARG, "unknown interpolation scheme");
+  a->spline = g->scheme == SWENSE_SPLINE3;
   return SWENSE_OK;
 }
 
@@ -583,6 +599,7 @@ extern "C" int swense_mlp_features(const swense_grid* g, double t, const float* 
   int st = prepare_interp(g, t, pts, np, SWENSE_P_DYN, 1.0, 1.0, &a, &lev);
   if (st) return st;
   if (g->ny_r < 4) return fail(SWENSE_ERR_UNSUPPORTED, "the learned correction needs a 3-D grid");
+  if (a.spline) return fail(SWENSE_ERR_UNSUPPORTED, "the learned correction is defined on LAGRANGE3 grids");
   if (np == 0) return SWENSE_OK;
   if (!x || !scale || !lagrange) return fail(SWENSE_ERR_ARG, "NULL feature outputs");
   FeatArgs f{a, x, scale, lagrange, eta};
@@ -603,6 +620,7 @@ extern "C" int swense_interp_learned(const swense_grid* g, double t, const float
   int st = prepare_interp(g, t, pts, np, p_mode, rho, grav, &a, &lev);
   if (st) return st;
   if (g->ny_r < 4) return fail(SWENSE_ERR_UNSUPPORTED, "the learned correction needs a 3-D grid");
+  if (a.spline) return fail(SWENSE_ERR_UNSUPPORTED, "the learned correction is defined on LAGRANGE3 grids");
   if (!packed) return fail(SWENSE_ERR_ARG, "NULL packed weights");
   const int64_t chunk = std::min<int64_t>(np, int64_t(1) << 19);
   const size_t rows = size_t(4) * std::max<int64_t>(chunk, 1);

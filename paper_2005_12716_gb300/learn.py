@@ -37,6 +37,14 @@ def random_sea(nx, ny, Lx, Ly, rng, depth=0.0):
     return W.linear_sea(nx, ny, Lx, Ly, comps, depth=depth)
 
 
+def random_jonswap(nx, ny, Lx, Ly, rng, lambda_p_cells=16.0):
+    """JONSWAP sea with random heading, phases and Hs / lambda_p in [0.02, 0.05], with the peak
+    wavelength at ``lambda_p_cells`` grid spacings (the resolution of the target workload)."""
+    lp = lambda_p_cells * Lx / nx
+    return W.jonswap_sea(nx, ny, Lx, Ly, rng.uniform(0.02, 0.05) * lp, lp, gamma=3.3,
+                         heading=rng.uniform(0, 2 * np.pi), seed=int(rng.integers(1 << 30)))
+
+
 def sample_points(n, Lx, Ly, z_lo, z_hi, rng):
     p = np.empty((n, 3))
     p[:, 0] = rng.uniform(0, Lx, n)
@@ -46,13 +54,14 @@ def sample_points(n, Lx, Ly, z_lo, z_hi, rng):
 
 
 def make_dataset(n_seas, points_per_sea, nx, ny, Lx, Ly, z_levels, pad_n=1, t_levels=(0.0,),
-                 seed=0, device="cuda"):
-    """Returns (x [4N][68], field [4N] int32, target [4N]) on the device."""
+                 seed=0, device="cuda", kind="components"):
+    """Returns (x [4N][68], field [4N] int32, target [4N]) on the device. ``kind``:
+    "components" (random_sea) or "jonswap" (random_jonswap)."""
     rng = np.random.default_rng(seed)
     z = np.asarray(z_levels, np.float32)
     xs, fs, ts = [], [], []
     for _ in range(n_seas):
-        sea = random_sea(nx, ny, Lx, Ly, rng)
+        sea = random_sea(nx, ny, Lx, Ly, rng) if kind == "components" else random_jonswap(nx, ny, Lx, Ly, rng)
         modes = api.upload_modes(sea, device)
         grid = api.fields_on_grid(modes, z, pad_n, list(t_levels))
         t = float(t_levels[0]) if len(t_levels) == 1 else float(

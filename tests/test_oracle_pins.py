@@ -332,3 +332,35 @@ def test_fv_divergence_of_exact_wave_converges():
                                      m["cell_faces"], m["cell_volume"])
         res.append(np.sqrt(np.mean(d ** 2)))
     assert res[1] < res[0] / 3.0
+
+
+# ------------------------------------------------------------------------- cubic spline (SPLINE3)
+
+def test_periodic_spline_matches_library_and_nodes():
+    scipy_interp = pytest.importorskip("scipy.interpolate")
+    rng = np.random.default_rng(31)
+    n, L = 24, 3.0
+    xs = np.arange(n) * L / n
+    f = rng.standard_normal(n)
+    M = interp._periodic_spline_second_derivs(f, L / n)
+    xq = rng.uniform(0, L, 200)
+    sx = xq / (L / n)
+    i = np.floor(sx).astype(int) % n
+    got = interp._spline_eval(f, M, L / n, i, sx - np.floor(sx))
+    ref = scipy_interp.CubicSpline(np.append(xs, L), np.append(f, f[0]), bc_type="periodic")(xq)
+    np.testing.assert_allclose(got, ref, atol=1e-12)
+    np.testing.assert_allclose(interp._spline_eval(f, M, L / n, np.arange(n), np.zeros(n)), f, atol=1e-14)
+
+
+def test_spline_interp_converges_fourth_order():
+    """SPLINE3 on a smooth sea: error falls ~16x per grid halving (cubic spline, O(h^4))."""
+    s = _random_sea(0.0, 32, nx=32, ny=16)
+    z = np.linspace(-0.6, 0.05, 20).astype(np.float32)
+    pts = _pts(150, 6, 3, -0.55, 0.0, 33)
+    exact = modal.fields_at_points(s, pts)
+    errs = []
+    for pad in (1, 2):
+        nodes, eta = modal.fields_on_grid(s, z, pad)
+        out = interp.interp_points_spline(nodes[None], eta[None], 6.0, 3.0, z, [0.0], pts, 0.0)
+        errs.append(np.max(np.abs(out["eta"] - exact["eta"])) / np.max(np.abs(exact["eta"])))
+    assert errs[1] < errs[0] / 10
