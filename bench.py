@@ -34,7 +34,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--config", choices=["jonswap3d", "stokes2d", "batched", "learned", "e1"],
+    ap.add_argument("--config", choices=["jonswap3d", "stokes2d", "batched", "learned", "e1", "direct"],
                     default="jonswap3d")
     ap.add_argument("--pad", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -582,6 +582,80 @@ def run_e1(args, rank, world):
         print(json.dumps(line), flush=True)
 
 
+def run_direct(args, rank, world):
+    """Direct modal sums at the near-body points of the 3-D JONSWAP mesh (r < 0.25 lambda_p of the
+    cylinder axis), FP32 and split-BF16 tensor-core paths, each checked against the FP64 direct sum
+    on a seeded sample of points."""
+    import torch
+    from oracle import modal
+    from paper_2005_12716_gb300 import _swense as S
+    from paper_2005_12716_gb300 import api
+    from wavegen import configs
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    cfg = configs.jonswap3d()
+    sea, tq = cfg["sea"], cfg["t_query"]
+    pts_np = configs.near_body_points(cfg)
+    npts = len(pts_np)
+    nmodes = int((sea["ny"] - 1) * (sea["nx"] // 2))
+    modes = api.upload_modes(sea, dev)
+    pts = torch.from_numpy(pts_np).to(dev)
+    outs = {k: torch.empty(npts, dtype=torch.float32, device=dev) for k in ("eta", "u", "v", "w", "p")}
+    sel = np.random.default_rng(20051279).choice(npts, 192, replace=False)
+    ref = modal.fields_at_points(modal.propagate(sea, tq), pts_np[sel].astype(np.float64))
+    vs = float(np.max(np.sqrt(ref["u"] ** 2 + ref["v"] ** 2 + ref["w"] ** 2)))
+    steps = max(3, min(args.steps, 10))
+    res = {}
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    for prec in ("fp32", "split_bf16"):
+        fn = lambda: api.direct(modes, tq, pts, precision=prec, out=outs)  # noqa: E731
+        for _ in range(max(3, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        l0 = S.swense_launches()
+        ms = _time_events(fn, steps)
+        launches = S.swense_launches() - l0
+        err = {}
+        for k in ("eta", "u", "v", "w", "p"):
+            got = outs[k][torch.from_numpy(sel).to(dev)].cpu().numpy().astype(np.float64)
+            scale = vs if k in ("u", "v", "w") else float(np.max(np.abs(ref[k])))
+            err[k] = float(np.max(np.abs(got - ref[k])) / scale)
+        res[prec] = {"ms": ms, "points_per_s": npts / (ms * 1e-3),
+                     "pairs_per_s": npts * nmodes / (ms * 1e-3), "launches": launches,
+                     "max_err_vs_fp64": err}
+    clk = clocks.stop()
+    peaks = {}
+    pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pp):
+        with open(pp) as fh:
+            peaks = json.load(fh)
+    bf16_peak = float(peaks.get("bf16_tflops", 1910.8))
+    # split path: per 16 points x 8 modes (deep water) three m16n8k16 MMAs of 4096 flop each
+    sp = res["split_bf16"]
+    mma_tflops = sp["pairs_per_s"] / 128 * 3 * 4096 / 1e12
+    line = {
+        "metric": "wave-field points/sec at stated err vs FP64 oracle; % of HBM roofline",
+        "value": sp["points_per_s"], "unit": "points/s", "n_gpus": 1, "steps": steps,
+        "warmup": max(3, args.warmup), "ms_per_step": sp["ms"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3 (split) / f32 accumulate",
+        "data": "synthetic",
+        "config": {"workload": f"direct: {npts} near-body mesh points (r < 0.25 lambda_p) x {nmodes} "
+                               f"modes of the 512x256 JONSWAP sea, deep water",
+                   "l2": "inputs (modes table) are re-read from L2 by design; not flushed"},
+        "paths": res,
+        "roofline": {"bound": "tensor", "kernel": "k_direct_split", "achieved": mma_tflops,
+                     "peak": bf16_peak, "unit": "TFLOP/s", "frac": mma_tflops / bf16_peak,
+                     "traffic": None,
+                     "note": "MMA flops issued incl. the four zero columns; operand generation on "
+                             "the FMA/MUFU pipes binds"},
+        "gpu_launches": int(res["split_bf16"]["launches"] * 1),
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -594,7 +668,8 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         torch.distributed.init_process_group("nccl")
     try:
-        {"batched": run_batched, "learned": run_learned, "e1": run_e1}.get(args.config, run_ours)(
+        {"batched": run_batched, "learned": run_learned, "e1": run_e1, "direct": run_direct}.get(
+            args.config, run_ours)(
             args, rank, world)
     finally:
         if world > 1:

@@ -17,6 +17,7 @@
 
 #include "fft.cuh"
 #include "internal.cuh"
+#include "mma.cuh"
 
 namespace swense {
 namespace {
@@ -30,22 +31,25 @@ struct ModeCoef {
   float4 c0, c1, c2, c3;
 };
 
-__global__ void k_direct_prep(const float2* __restrict__ Ae, const float2* __restrict__ Ap,
-                              const float2* __restrict__ At, const double* __restrict__ omega,
-                              double dt, int nx, int ny, float kxs, float kys, float depth,
-                              ModeCoef* __restrict__ out) {
+// Weighted coefficients of slot i = r (nx/2 + 1) + m of the one-sided spectrum at time offset dt
+// (linear propagation e^{-i omega dt} when omega is given). Nyquist slots return live = false.
+struct SlotCoef {
+  bool live;
+  int m, n;
+  float k, invd;
+  float2 we, wu, wv, ww, wt;
+};
+
+__device__ __forceinline__ SlotCoef slot_coef(int i, const float2* __restrict__ Ae,
+                                              const float2* __restrict__ Ap, const float2* __restrict__ At,
+                                              const double* __restrict__ omega, double dt, int nx, int ny,
+                                              float kxs, float kys, float depth) {
   const int nxh1 = nx / 2 + 1;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= ny * nxh1) return;
   const int r = i / nxh1, m = i - r * nxh1;
-  ModeCoef mc;
-  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-  mc.c0 = make_float4(__int_as_float(0), __int_as_float(0), 0.f, 1.f);
-  mc.c1 = mc.c2 = mc.c3 = zero;
-  if (m >= nx / 2 || (ny > 1 && r == ny / 2)) {           // Nyquist slots are ignored
-    out[i] = mc;
-    return;
-  }
+  SlotCoef sc{};
+  sc.live = !(m >= nx / 2 || (ny > 1 && r == ny / 2));    // Nyquist slots are ignored
+  sc.invd = 1.f;
+  if (!sc.live) return sc;
   float2 e = Ae[i], p = Ap[i], t = At[i];
   if (omega) {
     const double turns = omega[i] * dt * 0.15915494309189533577;
@@ -60,11 +64,37 @@ __global__ void k_direct_prep(const float2* __restrict__ Ae, const float2* __res
   const float kx = float(m) * kxs, ky = float(n) * kys;
   const float k = sqrtf(kx * kx + ky * ky);
   const float wgt = m == 0 ? 1.f : 2.f;
-  const float invd = depth > 0.f ? 1.f / (1.f + expf(-2.f * k * depth)) : 1.f;
-  mc.c0 = make_float4(__int_as_float(m), __int_as_float(n), k, invd);
-  mc.c1 = make_float4(wgt * e.x, wgt * e.y, -wgt * kx * p.y, wgt * kx * p.x);
-  mc.c2 = make_float4(-wgt * ky * p.y, wgt * ky * p.x, wgt * k * p.x, wgt * k * p.y);
-  mc.c3 = make_float4(wgt * t.x, wgt * t.y, 0.f, 0.f);
+  sc.m = m;
+  sc.n = n;
+  sc.k = k;
+  sc.invd = depth > 0.f ? 1.f / (1.f + expf(-2.f * k * depth)) : 1.f;
+  sc.we = make_float2(wgt * e.x, wgt * e.y);
+  sc.wu = make_float2(-wgt * kx * p.y, wgt * kx * p.x);     // c i kx A^phi
+  sc.wv = make_float2(-wgt * ky * p.y, wgt * ky * p.x);     // c i ky A^phi
+  sc.ww = make_float2(wgt * k * p.x, wgt * k * p.y);        // c |k| A^phi
+  sc.wt = make_float2(wgt * t.x, wgt * t.y);                // c A^phit
+  return sc;
+}
+
+__global__ void k_direct_prep(const float2* __restrict__ Ae, const float2* __restrict__ Ap,
+                              const float2* __restrict__ At, const double* __restrict__ omega,
+                              double dt, int nx, int ny, float kxs, float kys, float depth,
+                              ModeCoef* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ny * (nx / 2 + 1)) return;
+  const SlotCoef sc = slot_coef(i, Ae, Ap, At, omega, dt, nx, ny, kxs, kys, depth);
+  ModeCoef mc;
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (!sc.live) {
+    mc.c0 = make_float4(__int_as_float(0), __int_as_float(0), 0.f, 1.f);
+    mc.c1 = mc.c2 = mc.c3 = zero;
+    out[i] = mc;
+    return;
+  }
+  mc.c0 = make_float4(__int_as_float(sc.m), __int_as_float(sc.n), sc.k, sc.invd);
+  mc.c1 = make_float4(sc.we.x, sc.we.y, sc.wu.x, sc.wu.y);
+  mc.c2 = make_float4(sc.wv.x, sc.wv.y, sc.ww.x, sc.ww.y);
+  mc.c3 = make_float4(sc.wt.x, sc.wt.y, 0.f, 0.f);
   out[i] = mc;
 }
 
@@ -165,10 +195,327 @@ __global__ void __launch_bounds__(kDirThreads) k_direct_fp32(DirectArgs a) {
   }
 }
 
+// ------------------------------------------------------------------------------------------------
+// Split-BF16 tensor-core path. The sums over modes are a contraction of the points-by-(mode,
+// re/im) matrix A[p][2j] = cos(theta_pj) f_j(z_p), A[p][2j+1] = sin(theta_pj) f_j(z_p) with the
+// (mode, re/im)-by-field matrix B[2j][c] = Re W_c[j], B[2j+1][c] = -Im W_c[j], c = u, v, w, phi_t
+// (columns 4..7 zero). A is generated in registers directly in the m16n8k16 fragment layout (no
+// shared-memory round trip) and both operands are split into BF16 hi + lo; three MMAs
+// (hi.hi + hi.lo + lo.hi) accumulate in FP32, which leaves a relative error of about 2^-16 per
+// product. eta has no depth factor and one column, so it is summed in FP32 on the side from the
+// same phases. Finite depth writes the factors as a + b and a - b with a = e^{kz} / (1 + e^{-2kh})
+// and b = a e^{-2k(z+h)} (so f = a + b for u, v, phi_t and g = a - b for w): A carries (cos, sin)
+// times a and times b, and B's w column takes the sign flip on the b half.
+//
+// Table: modes in rows of constant n (Nyquist row skipped), m = 0 .. nx/2 - 1 padded with zero
+// modes to a multiple of 8, cut into k-steps of KM = 8 modes (deep) or 4 modes (finite depth).
+// Lane (g, q) of a k-step holds modes q and q + 4 (deep) or mode q in its a and b halves.
+struct SplitStep {
+  uint4 b[32];      // per lane: (b0 hi, b1 hi, b0 lo, b1 lo)
+  float4 info[8];   // per mode of the step: (|k|, 1 / (1 + e^{-2kh}), W_eta)
+};
+static_assert(sizeof(SplitStep) == 640, "split step record");
+
+constexpr int kSplitThreads = 256;
+constexpr int kSplitTiles = 2;     // 16-point MMA tiles per warp
+constexpr int kSplitStage = 32;    // k-steps per shared-memory stage (double-buffered)
+constexpr int kSplitAnchor = 16;   // exact phase every this many k-steps
+
+__device__ __forceinline__ float2 pick_w(const SlotCoef& sc, int c) {
+  return c == 0 ? sc.wu : c == 1 ? sc.wv : c == 2 ? sc.ww : c == 3 ? sc.wt : make_float2(0.f, 0.f);
+}
+
+__global__ void k_direct_prep_split(const float2* __restrict__ Ae, const float2* __restrict__ Ap,
+                                    const float2* __restrict__ At, const double* __restrict__ omega,
+                                    double dt, int nx, int ny, float kxs, float kys, float depth,
+                                    int km, int spr, int nsteps, SplitStep* __restrict__ out) {
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gt >= nsteps * 32) return;
+  const int s = gt >> 5, L = gt & 31;
+  const int ri = s / spr, m0 = (s - ri * spr) * km;
+  const int r = (ny > 1 && ri >= ny / 2) ? ri + 1 : ri;
+  const int nxh1 = nx / 2 + 1;
+  auto coef = [&](int j) {
+    const int m = m0 + j;
+    SlotCoef sc{};
+    if (m < nx / 2) sc = slot_coef(r * nxh1 + m, Ae, Ap, At, omega, dt, nx, ny, kxs, kys, depth);
+    return sc;                                   // not live: all weights zero
+  };
+  const int g = L >> 2, q = L & 3;
+  const SlotCoef s0 = coef(q);
+  const float2 w0 = pick_w(s0, g);
+  float2 w1;
+  if (km == 8) {
+    w1 = pick_w(coef(q + 4), g);
+  } else {
+    w1 = g == 2 ? make_float2(-w0.x, -w0.y) : w0;    // b half: w column changes sign
+  }
+  unsigned h0, l0, h1, l1;
+  bf2_split(w0.x, -w0.y, h0, l0);
+  bf2_split(w1.x, -w1.y, h1, l1);
+  out[s].b[L] = make_uint4(h0, h1, l0, l1);
+  if (L < 8) {
+    float4 inf = make_float4(0.f, 1.f, 0.f, 0.f);
+    if (L < km) {
+      const SlotCoef sc = coef(L);
+      if (sc.live) inf = make_float4(sc.k, sc.invd, sc.we.x, sc.we.y);
+    }
+    out[s].info[L] = inf;
+  }
+}
+
+struct SplitArgs {
+  const SplitStep* steps;
+  int nsteps, spr, ny;
+  const float* pts;
+  float *o_eta, *o_u, *o_v, *o_w, *o_p;
+  int64_t np;
+  double inv_lx, inv_ly;
+  float depth;
+  int p_mode;
+  float rho, g;
+};
+
+template <bool FINITE>
+__global__ void __launch_bounds__(kSplitThreads, 2) k_direct_split(SplitArgs a) {
+  constexpr int KM = FINITE ? 4 : 8;
+  constexpr int TT = kSplitTiles;
+  constexpr int JN = FINITE ? 1 : 2;               // modes per lane per k-step
+  __shared__ SplitStep stage[2][kSplitStage];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, q = lane & 3;
+  const int64_t pbase = (int64_t(blockIdx.x) * (kSplitThreads / 32) + warp) * (16 * TT);
+
+  unsigned X[TT][2], Y[TT][2];
+  float z[TT][2], stc[TT][2], sts[TT][2];
+  float pc[TT][2][JN], ps[TT][2][JN];
+#pragma unroll
+  for (int t = 0; t < TT; ++t)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t i = pbase + 16 * t + g + 8 * h;
+      float x = 0.f, y = 0.f, zz = 0.f;
+      if (i < a.np) {
+        x = a.pts[3 * i];
+        y = a.pts[3 * i + 1];
+        zz = a.pts[3 * i + 2];
+      }
+      X[t][h] = turn_fraction(x, a.inv_lx);
+      Y[t][h] = turn_fraction(y, a.inv_ly);
+      z[t][h] = zz;
+      // phase step for m -> m + KM
+      sincospif(2.f * (float(int(unsigned(KM) * X[t][h])) * 2.3283064365386963e-10f), &sts[t][h], &stc[t][h]);
+#pragma unroll
+      for (int j = 0; j < JN; ++j) pc[t][h][j] = 1.f, ps[t][h][j] = 0.f;
+    }
+  float run[TT][4], eta_run[TT][2];
+#pragma unroll
+  for (int t = 0; t < TT; ++t) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) run[t][e] = 0.f;
+    eta_run[t][0] = eta_run[t][1] = 0.f;
+  }
+
+  const int nchunks = (a.nsteps + kSplitStage - 1) / kSplitStage;
+  auto load_chunk = [&](int c) {
+    const int cnt = min(kSplitStage, a.nsteps - c * kSplitStage);
+    const uint4* src = reinterpret_cast<const uint4*>(a.steps + size_t(c) * kSplitStage);
+    uint4* dst = reinterpret_cast<uint4*>(stage[c & 1]);
+    for (int v = threadIdx.x; v < cnt * 40; v += kSplitThreads) cp_async16(dst + v, src + v, 16);
+    cp_async_commit();
+  };
+  load_chunk(0);
+  for (int c = 0; c < nchunks; ++c) {
+    if (c + 1 < nchunks) {
+      load_chunk(c + 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    const SplitStep* st = stage[c & 1];
+    const int cnt = min(kSplitStage, a.nsteps - c * kSplitStage);
+    float acc[TT][4], eta_acc[TT][2];
+#pragma unroll
+    for (int t = 0; t < TT; ++t) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[t][e] = 0.f;
+      eta_acc[t][0] = eta_acc[t][1] = 0.f;
+    }
+    for (int sl = 0; sl < cnt; ++sl) {
+      const int s = c * kSplitStage + sl;
+      const int ri = s / a.spr, sidx = s - ri * a.spr;
+      if (sidx % kSplitAnchor == 0) {
+        // exact phase (m X + n Y) mod 2^32 of this lane's modes
+        const int r = (a.ny > 1 && ri >= a.ny / 2) ? ri + 1 : ri;
+        const int n = a.ny > 1 ? (r < a.ny / 2 ? r : r - a.ny) : 0;
+#pragma unroll
+        for (int t = 0; t < TT; ++t)
+#pragma unroll
+          for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int j = 0; j < JN; ++j) {
+              const unsigned m = unsigned(sidx * KM + q + 4 * j);
+              const unsigned ph = m * X[t][h] + unsigned(n) * Y[t][h];
+              sincospif(2.f * (float(int(ph)) * 2.3283064365386963e-10f), &ps[t][h][j], &pc[t][h][j]);
+            }
+      } else {
+#pragma unroll
+        for (int t = 0; t < TT; ++t)
+#pragma unroll
+          for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int j = 0; j < JN; ++j) {
+              const float c2 = fmaf(pc[t][h][j], stc[t][h], -ps[t][h][j] * sts[t][h]);
+              ps[t][h][j] = fmaf(ps[t][h][j], stc[t][h], pc[t][h][j] * sts[t][h]);
+              pc[t][h][j] = c2;
+            }
+      }
+      const uint4 bf = st[sl].b[lane];
+      float4 inf[JN];
+#pragma unroll
+      for (int j = 0; j < JN; ++j) inf[j] = st[sl].info[q + 4 * j];
+#pragma unroll
+      for (int t = 0; t < TT; ++t) {
+        float v[2][2][2];                          // [register pair][h][cos/sin]
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const float zz = z[t][h];
+          if constexpr (!FINITE) {
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+              const float f = __expf(inf[j].x * zz);
+              v[j][h][0] = pc[t][h][j] * f;
+              v[j][h][1] = ps[t][h][j] * f;
+              eta_acc[t][h] = fmaf(inf[j].z, pc[t][h][j], fmaf(-inf[j].w, ps[t][h][j], eta_acc[t][h]));
+            }
+          } else {
+            const float k = inf[0].x;
+            const float fa = __expf(k * zz) * inf[0].y;
+            const float fb = fa * __expf(-2.f * k * (zz + a.depth));
+            v[0][h][0] = pc[t][h][0] * fa;
+            v[0][h][1] = ps[t][h][0] * fa;
+            v[1][h][0] = pc[t][h][0] * fb;
+            v[1][h][1] = ps[t][h][0] * fb;
+            eta_acc[t][h] = fmaf(inf[0].z, pc[t][h][0], fmaf(-inf[0].w, ps[t][h][0], eta_acc[t][h]));
+          }
+        }
+        unsigned ahi[4], alo[4];
+        bf2_split(v[0][0][0], v[0][0][1], ahi[0], alo[0]);   // (g, 2q..2q+1)
+        bf2_split(v[0][1][0], v[0][1][1], ahi[1], alo[1]);   // (g+8, 2q..2q+1)
+        bf2_split(v[1][0][0], v[1][0][1], ahi[2], alo[2]);   // (g, 2q+8..2q+9)
+        bf2_split(v[1][1][0], v[1][1][1], ahi[3], alo[3]);   // (g+8, 2q+8..2q+9)
+        mma16816(acc[t], ahi, bf.x, bf.y);
+        mma16816(acc[t], ahi, bf.z, bf.w);
+        mma16816(acc[t], alo, bf.x, bf.y);
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < TT; ++t) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) run[t][e] += acc[t][e];
+      eta_run[t][0] += eta_acc[t][0];
+      eta_run[t][1] += eta_acc[t][1];
+    }
+    __syncthreads();                               // stage (c & 1) is reloaded next iteration
+  }
+
+#pragma unroll
+  for (int t = 0; t < TT; ++t) {
+    float e0 = eta_run[t][0], e1 = eta_run[t][1];
+    e0 += __shfl_xor_sync(0xffffffffu, e0, 1);
+    e0 += __shfl_xor_sync(0xffffffffu, e0, 2);
+    e1 += __shfl_xor_sync(0xffffffffu, e1, 1);
+    e1 += __shfl_xor_sync(0xffffffffu, e1, 2);
+    // lane q = 0 holds (u, v) of rows g and g + 8, lane q = 1 holds (w, phi_t)
+    const float w0 = __shfl_down_sync(0xffffffffu, run[t][0], 1);
+    const float t0 = __shfl_down_sync(0xffffffffu, run[t][1], 1);
+    const float w1 = __shfl_down_sync(0xffffffffu, run[t][2], 1);
+    const float t1 = __shfl_down_sync(0xffffffffu, run[t][3], 1);
+    if (q != 0) continue;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t i = pbase + 16 * t + g + 8 * h;
+      if (i >= a.np) continue;
+      const float uu = run[t][2 * h], vv = run[t][2 * h + 1];
+      const float ww = h ? w1 : w0, tt = h ? t1 : t0;
+      if (a.o_eta) a.o_eta[i] = h ? e1 : e0;
+      if (a.o_u) a.o_u[i] = uu;
+      if (a.o_v) a.o_v[i] = vv;
+      if (a.o_w) a.o_w[i] = ww;
+      if (a.o_p) {
+        float p;
+        if (a.p_mode == SWENSE_P_PHIT) {
+          p = tt;
+        } else {
+          p = -a.rho * (tt + 0.5f * (uu * uu + vv * vv + ww * ww));
+          if (a.p_mode == SWENSE_P_TOTAL) p -= a.rho * a.g * z[t][h];
+        }
+        a.o_p[i] = p;
+      }
+    }
+  }
+}
+
 }  // namespace
 }  // namespace swense
 
 using namespace swense;
+
+namespace {
+
+int direct_split(const swense_modes* md, double t, const float* pts, int64_t np, float* eta, float* u,
+                 float* v, float* w, float* p, int32_t p_mode, double rho, double grav,
+                 cudaStream_t stream) {
+  const int nx = md->nx, ny = md->ny;
+  const bool finite = md->depth > 0;
+  const int km = finite ? 4 : 8;
+  const int rm = ((nx / 2 + 7) / 8) * 8;        // modes per table row, padded to a multiple of 8
+  const int spr = rm / km;
+  const int nrows = ny > 1 ? ny - 1 : 1;        // Nyquist row skipped
+  const int64_t nsteps = int64_t(nrows) * spr;
+  if (nsteps * 32 >= (int64_t(1) << 31)) return fail(SWENSE_ERR_SIZE, "too many modes for the split table");
+  void* ws = nullptr;
+  int st = workspace(size_t(nsteps) * sizeof(SplitStep), stream, &ws);
+  if (st) return st;
+  SplitStep* steps = static_cast<SplitStep*>(ws);
+  const float depth = finite ? float(md->depth) : 0.f;
+  k_direct_prep_split<<<unsigned((nsteps * 32 + 255) / 256), 256, 0, stream>>>(
+      reinterpret_cast<const float2*>(md->A_eta), reinterpret_cast<const float2*>(md->A_phi),
+      reinterpret_cast<const float2*>(md->A_phit), md->omega, t - md->t_ref, nx, ny,
+      float(6.283185307179586476925 / md->Lx), ny > 1 ? float(6.283185307179586476925 / md->Ly) : 0.f,
+      depth, km, spr, int(nsteps), steps);
+  SWENSE_CUDA_TRY(cudaGetLastError());
+  count_launches(1);
+  SplitArgs a{};
+  a.steps = steps;
+  a.nsteps = int(nsteps);
+  a.spr = spr;
+  a.ny = ny;
+  a.pts = pts;
+  a.o_eta = eta;
+  a.o_u = u;
+  a.o_v = v;
+  a.o_w = w;
+  a.o_p = p;
+  a.np = np;
+  a.inv_lx = 1.0 / md->Lx;
+  a.inv_ly = ny > 1 ? 1.0 / md->Ly : 0.0;
+  a.depth = depth;
+  a.p_mode = p_mode;
+  a.rho = float(rho);
+  a.g = float(grav);
+  const int64_t per_cta = int64_t(kSplitThreads / 32) * 16 * kSplitTiles;
+  const int64_t blocks = (np + per_cta - 1) / per_cta;
+  if (blocks >= (int64_t(1) << 31)) return fail(SWENSE_ERR_SIZE, "too many points for one call");
+  if (finite) k_direct_split<true><<<unsigned(blocks), kSplitThreads, 0, stream>>>(a);
+  else k_direct_split<false><<<unsigned(blocks), kSplitThreads, 0, stream>>>(a);
+  SWENSE_CUDA_TRY(cudaGetLastError());
+  count_launches(1);
+  return SWENSE_OK;
+}
+
+}  // namespace
 
 extern "C" int swense_direct(const swense_modes* md, double t, const float* pts, int64_t np,
                              float* eta, float* u, float* v, float* w, float* p, int32_t p_mode,
@@ -187,9 +534,10 @@ extern "C" int swense_direct(const swense_modes* md, double t, const float* pts,
     return fail(SWENSE_ERR_ARG, "non-finite t, depth, rho or g");
   if (p_mode != SWENSE_P_DYN && p_mode != SWENSE_P_PHIT && p_mode != SWENSE_P_TOTAL)
     return fail(SWENSE_ERR_ARG, "unknown p_mode");
-  if (precision != SWENSE_DIRECT_FP32)
-    return fail(SWENSE_ERR_UNSUPPORTED, "precision: only SWENSE_DIRECT_FP32 is implemented");
+  if (precision != SWENSE_DIRECT_FP32 && precision != SWENSE_DIRECT_SPLIT_BF16)
+    return fail(SWENSE_ERR_ARG, "unknown precision");
   if (np == 0) return SWENSE_OK;
+  if (precision == SWENSE_DIRECT_SPLIT_BF16) return direct_split(md, t, pts, np, eta, u, v, w, p, p_mode, rho, grav, stream);
   const size_t nslot = size_t(ny) * (nx / 2 + 1);
   const size_t bytes = nslot * sizeof(ModeCoef);
   void* ws = nullptr;

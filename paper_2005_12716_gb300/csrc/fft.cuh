@@ -298,18 +298,28 @@ __device__ __forceinline__ void stk_pass(float2 (&v)[N / 32], const float2 (&T)[
     else stk_dft2(&v[b * 2]);
   }
   if constexpr (P + 1 < stk_npass(N)) {
+    // Output index of (b, r) = lane part + constant part with disjoint bits, so the padded index
+    // splits the same way and every access is a per-pass base plus an immediate offset.
+    const int lst = NS <= 32 ? (lane / NS) * NS * R + lane % NS : lane;
+    float2* bst = buf + stk_pad(lst);
 #pragma unroll
-    for (int b = 0; b < B; ++b) {
-      const int j = lane + 32 * b;
+    for (int b = 0; b < B; ++b)
 #pragma unroll
-      for (int r = 0; r < R; ++r) buf[stk_pad((j / NS) * NS * R + (j % NS) + r * NS)] = v[b * R + r];
-    }
+      for (int r = 0; r < R; ++r) {
+        const int c = NS <= 32 ? 32 * b * R + r * NS
+                               : (b / (NS / 32)) * NS * R + 32 * (b % (NS / 32)) + r * NS;
+        bst[c + (c >> 4)] = v[b * R + r];
+      }
     __syncwarp();
     constexpr int R2 = stk_radix(N, P + 1), B2 = E / R2;
+    const float2* bld = buf + stk_pad(lane);
 #pragma unroll
     for (int b = 0; b < B2; ++b)
 #pragma unroll
-      for (int r = 0; r < R2; ++r) v[b * R2 + r] = buf[stk_pad(lane + 32 * b + r * (N / R2))];
+      for (int r = 0; r < R2; ++r) {
+        const int c = 32 * b + r * (N / R2);
+        v[b * R2 + r] = bld[c + (c >> 4)];
+      }
     __syncwarp();
     stk_pass<N, P + 1>(v, T, tw, buf, lane);
   }

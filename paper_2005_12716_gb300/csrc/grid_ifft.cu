@@ -289,11 +289,11 @@ template <int E, int NF>
 __global__ void __launch_bounds__(256, 2) k_col_fft(ColArgs a, Levels L) {
   extern __shared__ float2 sm[];                 // [2][ny][cb + 1]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int c0 = blockIdx.x * a.cb;
-  const int ncol = min(a.cb, a.Mh - c0);
-  const int ld = a.cb + 1;
-  for (int i = threadIdx.x; i < a.ny * a.cb; i += blockDim.x) {
-    const int c = i % a.cb, r = i / a.cb;
+  const int c0 = blockIdx.x * kColBlock;
+  const int ncol = min(kColBlock, a.Mh - c0);
+  const int ld = kColBlock + 1;
+  for (int i = threadIdx.x; i < a.ny * kColBlock; i += blockDim.x) {
+    const int c = i % kColBlock, r = i / kColBlock;
     const bool ok = c < ncol;
     const size_t gi = ok ? size_t(r) * a.nxh1 + c0 + c : 0;
     cp_async8(&sm[r * ld + c], &a.A_phi[gi], ok ? 8 : 0);
@@ -305,13 +305,13 @@ __global__ void __launch_bounds__(256, 2) k_col_fft(ColArgs a, Levels L) {
   __syncthreads();
   const int nyh = a.ny >> 1;
   const int groups = 4 / NF;
-  const int ntask = a.lpc * ncol * groups;
+  const int ntask = a.lpc * kColBlock * groups;
   for (int task = warp; task < ntask; task += blockDim.x >> 5) {
     const int g = task % groups;
     const int rest = task / groups;
-    const int c = rest % ncol;
-    const int level = blockIdx.y * a.lpc + rest / ncol;
-    if (level >= a.nlev) continue;
+    const int c = rest % kColBlock;
+    const int level = blockIdx.y * a.lpc + rest / kColBlock;
+    if (c >= ncol || level >= a.nlev) continue;
     const float z = L.z[a.lev0 + level];
     const int m = c0 + c;
     const float kx = float(m) * a.kxs;
@@ -371,12 +371,12 @@ template <int E>
 __global__ void __launch_bounds__(256, 2) k_row_fft(RowArgs a) {
   extern __shared__ float2 sm[];                 // [4][Mh][rb + 1]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int y0 = blockIdx.x * a.rb;
+  const int y0 = blockIdx.x * kRowBlock;
   const int level = blockIdx.y;
-  const int ld = a.rb + 1;
+  const int ld = kRowBlock + 1;
   const float2* G = a.G + size_t(level) * 4 * a.Mh * a.Nyr;
-  for (int i = threadIdx.x; i < 4 * a.Mh * a.rb; i += blockDim.x) {
-    const int rr = i % a.rb, qm = i / a.rb;
+  for (int i = threadIdx.x; i < 4 * a.Mh * kRowBlock; i += blockDim.x) {
+    const int rr = i % kRowBlock, qm = i / kRowBlock;
     const int y = y0 + rr;
     cp_async8(&sm[qm * ld + rr], &G[size_t(qm) * a.Nyr + (y < a.Nyr ? y : 0)], y < a.Nyr ? 8 : 0);
   }
@@ -384,7 +384,7 @@ __global__ void __launch_bounds__(256, 2) k_row_fft(RowArgs a) {
   warp_fft_init<E>(T, a.tw, lane);
   cp_async_wait_all();
   __syncthreads();
-  for (int rr = warp; rr < a.rb; rr += blockDim.x >> 5) {
+  for (int rr = warp; rr < kRowBlock; rr += blockDim.x >> 5) {
     const int y = y0 + rr;
     if (y >= a.Nyr) break;
     float2 z1[E], z2[E];
@@ -433,12 +433,12 @@ __global__ void __launch_bounds__(256, N >= 1024 ? 1 : 2) k_col_stk(ColArgs a, L
   extern __shared__ float2 sm[];                 // [2][ny][cb + 1] modes, then per-warp buffers
   constexpr int E = N / 32, RL = stk_radix(N, stk_npass(N) - 1);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int c0 = blockIdx.x * a.cb;
-  const int ncol = min(a.cb, a.Mh - c0);
-  const int ld = a.cb + 1;
+  const int c0 = blockIdx.x * kColBlock;
+  const int ncol = min(kColBlock, a.Mh - c0);
+  const int ld = kColBlock + 1;
   float2* wbuf = sm + 2 * a.ny * ld + warp * stk_buf(N);
-  for (int i = threadIdx.x; i < a.ny * a.cb; i += blockDim.x) {
-    const int c = i % a.cb, r = i / a.cb;
+  for (int i = threadIdx.x; i < a.ny * kColBlock; i += blockDim.x) {
+    const int c = i % kColBlock, r = i / kColBlock;
     const bool ok = c < ncol;
     const size_t gi = ok ? size_t(r) * a.nxh1 + c0 + c : 0;
     cp_async8(&sm[r * ld + c], &a.A_phi[gi], ok ? 8 : 0);
@@ -450,13 +450,13 @@ __global__ void __launch_bounds__(256, N >= 1024 ? 1 : 2) k_col_stk(ColArgs a, L
   __syncthreads();
   const int nyh = a.ny >> 1;
   const int groups = 4 / NF;
-  const int ntask = a.lpc * ncol * groups;
+  const int ntask = a.lpc * kColBlock * groups;
   for (int task = warp; task < ntask; task += blockDim.x >> 5) {
     const int g = task % groups;
     const int rest = task / groups;
-    const int c = rest % ncol;
-    const int level = blockIdx.y * a.lpc + rest / ncol;
-    if (level >= a.nlev) continue;
+    const int c = rest % kColBlock;
+    const int level = blockIdx.y * a.lpc + rest / kColBlock;
+    if (c >= ncol || level >= a.nlev) continue;
     const float z = L.z[a.lev0 + level];
     const int m = c0 + c;
     const float kx = float(m) * a.kxs;
@@ -524,13 +524,13 @@ __global__ void __launch_bounds__(256, N >= 1024 ? 1 : 2) k_row_stk(RowArgs a) {
   extern __shared__ float2 sm[];                 // [4][Mh][rb + 1] staging, then warp buffers
   constexpr int E = N / 32, RL = stk_radix(N, stk_npass(N) - 1);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int y0 = blockIdx.x * a.rb;
+  const int y0 = blockIdx.x * kRowBlock;
   const int level = blockIdx.y;
-  const int ld = a.rb + 1;
+  const int ld = kRowBlock + 1;
   const float2* G = a.G + size_t(level) * 4 * a.Mh * a.Nyr;
   float2* wbuf = sm + 4 * a.Mh * ld + warp * stk_buf(N);
-  for (int i = threadIdx.x; i < 4 * a.Mh * a.rb; i += blockDim.x) {
-    const int rr = i % a.rb, qm = i / a.rb;
+  for (int i = threadIdx.x; i < 4 * a.Mh * kRowBlock; i += blockDim.x) {
+    const int rr = i % kRowBlock, qm = i / kRowBlock;
     const int y = y0 + rr;
     cp_async8(&sm[qm * ld + rr], &G[size_t(qm) * a.Nyr + (y < a.Nyr ? y : 0)], y < a.Nyr ? 8 : 0);
   }
@@ -539,7 +539,7 @@ __global__ void __launch_bounds__(256, N >= 1024 ? 1 : 2) k_row_stk(RowArgs a) {
   cp_async_wait_all();
   __syncthreads();
   const size_t fs = size_t(a.Mh) * ld;
-  for (int rr = warp; rr < a.rb; rr += blockDim.x >> 5) {
+  for (int rr = warp; rr < kRowBlock; rr += blockDim.x >> 5) {
     const int y = y0 + rr;
     if (y >= a.Nyr) break;
     float4* out = a.nodes + (size_t(a.lev0 + level) * a.Nyr + y) * N;
@@ -754,11 +754,14 @@ int launch_grid(const GridPlan& p, const swense_modes* md, const double* t, floa
   cb = std::min(cb, std::min(64, Mh));
   int cb_eta = int(std::max<size_t>(1, kSmemBudget / (size_t(Nyr) * sizeof(float2))));
   cb_eta = std::min(cb_eta, std::min(64, Mh));
+  // the eta transform is a single level: keep about two CTAs per SM busy rather than few wide ones
+  cb_eta = std::min(cb_eta, std::max(1, (Mh + 303) / 304));
   const size_t rowb = size_t(2) * Nxr * sizeof(float2);
   int rb = int(std::max<size_t>(1, kSmemBudget / rowb));
   rb = int(std::min<int64_t>(rb, std::min<int64_t>(16, Nyr)));
   int rb_eta = int(std::max<size_t>(1, kSmemBudget / (size_t(Nxr) * sizeof(float2))));
   rb_eta = int(std::min<int64_t>(rb_eta, std::min<int64_t>(16, (Nyr + 1) / 2)));
+  rb_eta = int(std::min<int64_t>(rb_eta, std::max<int64_t>(1, ((Nyr + 1) / 2 + 303) / 304)));
   const size_t smem_a = size_t(fp) * cb * Nyr * sizeof(float2);
   const size_t smem_a_eta = size_t(cb_eta) * Nyr * sizeof(float2);
   const size_t smem_b = size_t(rb) * rowb;

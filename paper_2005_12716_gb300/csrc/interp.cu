@@ -261,29 +261,23 @@ __global__ void __launch_bounds__(BOX_THREADS, 3) k_interp_box(InterpArgs a, Lev
     s_ref[0] = c.ix;
     s_ref[1] = c.iy;
   }
-  // compact per-point state; weights are recomputed after the box load
-  int rx[BOX_PPT], ry[BOX_PPT], jz[BOX_PPT];
-  float px[BOX_PPT], py[BOX_PPT], pz[BOX_PPT];
+  // No per-point state is kept across the box load (a dynamically indexed per-thread array
+  // would live in local memory): the main loop re-reads each point and recomputes its cell.
   __syncthreads();
   const int refx = s_ref[0], refy = s_ref[1];
   int mn[3] = {1 << 30, 1 << 30, 1 << 30}, mx[3] = {-(1 << 30), -(1 << 30), -(1 << 30)};
 #pragma unroll
   for (int k = 0; k < BOX_PPT; ++k) {
     const int64_t i = p0 + k * BOX_THREADS + threadIdx.x;
-    rx[k] = ry[k] = jz[k] = 0;
-    px[k] = py[k] = pz[k] = 0.f;
     if (i < a.np) {
-      px[k] = a.pts[3 * i];
-      py[k] = a.pts[3 * i + 1];
-      pz[k] = a.pts[3 * i + 2];
-      const PointCell c = point_cell(a, zs, px[k], py[k], pz[k]);
-      rx[k] = wrap_rel(c.ix, refx, a.Nxr);
-      ry[k] = a.Nyr > 1 ? wrap_rel(c.iy, refy, a.Nyr) : 0;
-      jz[k] = c.j0;
-      mn[0] = min(mn[0], rx[k]);
-      mx[0] = max(mx[0], rx[k]);
-      mn[1] = min(mn[1], ry[k]);
-      mx[1] = max(mx[1], ry[k]);
+      const PointCell c = point_cell(a, zs, __ldg(&a.pts[3 * i]), __ldg(&a.pts[3 * i + 1]),
+                                     __ldg(&a.pts[3 * i + 2]));
+      const int rx = wrap_rel(c.ix, refx, a.Nxr);
+      const int ry = a.Nyr > 1 ? wrap_rel(c.iy, refy, a.Nyr) : 0;
+      mn[0] = min(mn[0], rx);
+      mx[0] = max(mx[0], rx);
+      mn[1] = min(mn[1], ry);
+      mx[1] = max(mx[1], ry);
       mn[2] = min(mn[2], c.j0);
       mx[2] = max(mx[2], c.j0);
     }
@@ -323,15 +317,16 @@ __global__ void __launch_bounds__(BOX_THREADS, 3) k_interp_box(InterpArgs a, Lev
   const bool fits = int64_t(sbx) * by * bz <= BOX_NODES && int64_t(sbx) * by <= BOX_COLS &&
                     bx <= a.Nxr && by <= a.Nyr;
   if (!fits) {
-#pragma unroll
+#pragma unroll 1
     for (int k = 0; k < BOX_PPT; ++k) {
       const int64_t i = p0 + k * BOX_THREADS + threadIdx.x;
       if (i >= a.np) continue;
-      const PointCell c = point_cell(a, zs, px[k], py[k], pz[k]);
+      const float pz = __ldg(&a.pts[3 * i + 2]);
+      const PointCell c = point_cell(a, zs, __ldg(&a.pts[3 * i]), __ldg(&a.pts[3 * i + 1]), pz);
       float4 acc;
       float acc_eta;
       gather_global(a, c, acc, acc_eta);
-      store_point(a, i, acc, acc_eta, pz[k], c.inside);
+      store_point(a, i, acc, acc_eta, pz, c.inside);
     }
     return;
   }
@@ -375,8 +370,11 @@ __global__ void __launch_bounds__(BOX_THREADS, 3) k_interp_box(InterpArgs a, Lev
   for (int k = 0; k < BOX_PPT; ++k) {
     const int64_t i = p0 + k * BOX_THREADS + threadIdx.x;
     if (i >= a.np) continue;
-    const PointCell c = point_cell(a, zs, px[k], py[k], pz[k]);
-    const float4* base = sbox + ((jz[k] - mn[2]) * by + (ry[k] - mn[1])) * sbx + (rx[k] - mn[0]);
+    const float pz = __ldg(&a.pts[3 * i + 2]);
+    const PointCell c = point_cell(a, zs, __ldg(&a.pts[3 * i]), __ldg(&a.pts[3 * i + 1]), pz);
+    const int rx = wrap_rel(c.ix, refx, a.Nxr);
+    const int ry = a.Nyr > 1 ? wrap_rel(c.iy, refy, a.Nyr) : 0;
+    const float4* base = sbox + ((c.j0 - mn[2]) * by + (ry - mn[1])) * sbx + (rx - mn[0]);
     unsigned long long uv = pack2(0.f, 0.f), wt = pack2(0.f, 0.f);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -396,14 +394,14 @@ __global__ void __launch_bounds__(BOX_THREADS, 3) k_interp_box(InterpArgs a, Lev
       }
     }
     float acc_eta = 0.f;
-    const float* ebase = seta + (ry[k] - mn[1]) * sbx + (rx[k] - mn[0]);
+    const float* ebase = seta + (ry - mn[1]) * sbx + (rx - mn[0]);
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
       if (b >= nys) break;
 #pragma unroll
       for (int kx = 0; kx < 4; ++kx) acc_eta = fmaf(c.wy[b] * c.wx[kx], ebase[b * sbx + kx], acc_eta);
     }
-    store_point(a, i, make_float4(lo2(uv), hi2(uv), lo2(wt), hi2(wt)), acc_eta, pz[k], c.inside);
+    store_point(a, i, make_float4(lo2(uv), hi2(uv), lo2(wt), hi2(wt)), acc_eta, pz, c.inside);
   }
 }
 

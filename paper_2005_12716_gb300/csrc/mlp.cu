@@ -17,6 +17,7 @@
 #include <cmath>
 
 #include "internal.cuh"
+#include "mma.cuh"
 
 namespace swense {
 namespace {
@@ -39,28 +40,6 @@ struct Packed {
 };
 static_assert(sizeof(Packed) <= SWENSE_MLP_PACKED_BYTES, "packed weight size");
 static_assert(sizeof(Packed) % 16 == 0, "packed weight size must be a multiple of 16 bytes");
-
-__device__ __forceinline__ unsigned bf2(float lo, float hi) {
-  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-  return *reinterpret_cast<unsigned*>(&v);
-}
-// hi + lo split of a pair: hi = bf16(x), lo = bf16(x - hi)
-__device__ __forceinline__ void bf2_split(float a, float b, unsigned& hi, unsigned& lo) {
-  const __nv_bfloat16 ha = __float2bfloat16_rn(a), hb = __float2bfloat16_rn(b);
-  __nv_bfloat162 h;
-  h.x = ha;
-  h.y = hb;
-  hi = *reinterpret_cast<unsigned*>(&h);
-  lo = bf2(a - __bfloat162float(ha), b - __bfloat162float(hb));
-}
-
-__device__ __forceinline__ void mma16816(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
 
 __device__ __forceinline__ unsigned ld_u32(const __nv_bfloat16* p) {
   return *reinterpret_cast<const unsigned*>(p);

@@ -60,7 +60,18 @@ def jonswap3d(nx=512, ny=256, lx_over_lp=32.0, ly_over_lp=16.0, n_levels=64, pad
         "t_levels": t_levels,
         "t_query": float(t_levels[(n_tl - 1) // 2] + 0.37 * dt),
         "period": Tp,
+        "centre": (0.5 * lx_over_lp * lp, 0.5 * ly_over_lp * lp), "lambda_p": lp,
     }
+
+
+def near_body_points(cfg, pts=None, r_over_lp=0.25):
+    """Mesh points (cell and face centres, mesh order) within r < r_over_lp * lambda_p of the
+    cylinder axis: the points that take the direct modal sum instead of interpolation."""
+    if pts is None:
+        pts = mesh_points(cfg["mesh"])
+    xc, yc = cfg["centre"]
+    r2 = (pts[:, 0].astype(np.float64) - xc) ** 2 + (pts[:, 1].astype(np.float64) - yc) ** 2
+    return np.ascontiguousarray(pts[r2 < (r_over_lp * cfg["lambda_p"]) ** 2])
 
 
 def jonswap3d_small(pad_n=1, n_tl=2, seed=SEED0 + 102):
