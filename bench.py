@@ -37,6 +37,8 @@ def parse():
     ap.add_argument("--config", choices=["jonswap3d", "stokes2d", "batched", "learned", "e1", "direct"],
                     default="jonswap3d")
     ap.add_argument("--pad", type=int, default=1)
+    ap.add_argument("--points", type=int, default=0,
+                    help="direct mode: use only the first N near-body points (small profiling case)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -199,17 +201,23 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def kernel_source_hash():
+def kernel_source_hash(files=("csrc/interp.cu", "csrc/internal.cuh", "../include/swense.h")):
+    """Hash of the sources a kernel is built from (paths relative to the package)."""
     h = hashlib.sha256()
-    for f in ("interp.cu", "grid_ifft.cu", "fft.cuh"):
-        with open(os.path.join(ROOT, "paper_2005_12716_gb300", "csrc", f), "rb") as fh:
+    for f in files:
+        with open(os.path.normpath(os.path.join(ROOT, "paper_2005_12716_gb300", f)), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-# DRAM bytes per launch from ncu captures (dram__bytes_read.sum + dram__bytes_write.sum) with
-# the kernel-source hash they were taken at; a changed kernel invalidates them.
-NCU_TRAFFIC = {}
+# DRAM bytes per launch from ncu captures (dram__bytes_read.sum + dram__bytes_write.sum), with
+# the hash of the kernel's sources and the workload they were taken on; a changed kernel or
+# workload invalidates them (traffic is then reported as null).
+NCU_TRAFFIC = {
+    "k_interp_box": {"bytes": 114146048 + 118993152, "hash": "a7c6d2649eecdee0",
+                     "workload": "jonswap3d: 512x256 modes, 64 levels, pad 1, 2 time levels, "
+                                 "2048000 cell + 6177280 face centres (cylinder O-grid)"},
+}
 
 
 def run_ours(args, rank, world):
@@ -596,12 +604,14 @@ def run_direct(args, rank, world):
     cfg = configs.jonswap3d()
     sea, tq = cfg["sea"], cfg["t_query"]
     pts_np = configs.near_body_points(cfg)
+    if args.points:
+        pts_np = np.ascontiguousarray(pts_np[:args.points])
     npts = len(pts_np)
     nmodes = int((sea["ny"] - 1) * (sea["nx"] // 2))
     modes = api.upload_modes(sea, dev)
     pts = torch.from_numpy(pts_np).to(dev)
     outs = {k: torch.empty(npts, dtype=torch.float32, device=dev) for k in ("eta", "u", "v", "w", "p")}
-    sel = np.random.default_rng(20051279).choice(npts, 192, replace=False)
+    sel = np.random.default_rng(20051279).choice(npts, min(192, npts), replace=False)
     ref = modal.fields_at_points(modal.propagate(sea, tq), pts_np[sel].astype(np.float64))
     vs = float(np.max(np.sqrt(ref["u"] ** 2 + ref["v"] ** 2 + ref["w"] ** 2)))
     steps = max(3, min(args.steps, 10))

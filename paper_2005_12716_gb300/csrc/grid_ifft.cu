@@ -570,6 +570,42 @@ __global__ void __launch_bounds__(256, N >= 1024 ? 1 : 2) k_row_stk(RowArgs a) {
   }
 }
 
+// Row pass, one field pair per CTA (blockIdx.z: 0 -> (U, V) into (u, v), 1 -> (W, T) into
+// (w, dphi/dt)), one length-N transform per warp: half the registers of k_row_stk, so three CTAs
+// fit on an SM. The staged rows are dead once every warp holds its row, and the same shared
+// memory then serves as the per-warp exchange buffers. Each CTA writes one float2 half of the
+// nodes' float4; the two halves meet in L2.
+template <int N>
+__global__ void __launch_bounds__(256, 3) k_row_half(RowArgs a) {
+  extern __shared__ float2 sm[];                 // [2][Mh][rb + 1] staging, then warp buffers
+  constexpr int E = N / 32, RL = stk_radix(N, stk_npass(N) - 1);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int y0 = blockIdx.x * kRowBlock;
+  const int level = blockIdx.y;
+  const int q = blockIdx.z;
+  constexpr int ld = kRowBlock + 1;
+  const float2* G = a.G + (size_t(level) * 4 + 2 * q) * a.Mh * a.Nyr;
+  for (int i = threadIdx.x; i < 2 * a.Mh * kRowBlock; i += blockDim.x) {
+    const int rr = i % kRowBlock, fm = i / kRowBlock;
+    const int y = y0 + rr;
+    cp_async8(&sm[fm * ld + rr], &G[size_t(fm) * a.Nyr + (y < a.Nyr ? y : 0)], y < a.Nyr ? 8 : 0);
+  }
+  float2 T[stk_twn(N)];
+  stk_init<N>(T, a.tw, lane);
+  cp_async_wait_all();
+  __syncthreads();
+  const size_t fs = size_t(a.Mh) * ld;
+  float2 z[E];
+  row_pack<N>(z, sm + warp, sm + fs + warp, ld, a.Mh, lane);   // kRowBlock rows, one per warp
+  __syncthreads();
+  const int y = y0 + warp;
+  if (y >= a.Nyr) return;
+  stk_fft<N>(z, T, a.tw, sm + warp * stk_buf(N), lane);
+  float2* o2 = reinterpret_cast<float2*>(a.nodes + (size_t(a.lev0 + level) * a.Nyr + y) * N) + q;
+#pragma unroll
+  for (int e = 0; e < E; ++e) __stcs(&o2[2 * (lane + 32 * (e / RL) + (e % RL) * (N / RL))], z[e]);
+}
+
 // Launch-shape choices of the warp-register path, per grid shape (set by swense_autotune_grid;
 // defaults otherwise).
 struct Tune {
