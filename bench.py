@@ -34,9 +34,15 @@ def parse():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--config", choices=["jonswap3d", "stokes2d", "batched", "learned", "e1", "direct"],
+    ap.add_argument("--config", choices=["jonswap3d", "stokes2d", "batched", "learned", "e1", "direct",
+                                         "large"],
                     default="jonswap3d")
     ap.add_argument("--pad", type=int, default=1)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="use the untuned default launch shape of stage 1")
+    ap.add_argument("--tune", default="",
+                    help="stage-1 launch shape 'lpc,chunk_mb,row_variant' instead of autotuning "
+                         "(e.g. the autotuner's earlier choice, for a profiler run)")
     ap.add_argument("--points", type=int, default=0,
                     help="direct mode: use only the first N near-body points (small profiling case)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -241,6 +247,16 @@ def run_ours(args, rank, world):
         api.fields_on_grid(modes, z, pad, tl, out=grid)
         api.interp(grid, tq, pts, out=outs)
 
+    # launch shape of stage 1 chosen by the library's autotuner (untimed, once per grid shape)
+    if args.tune:
+        lpc_, mb_, rv_ = (int(v) for v in args.tune.split(","))
+        S.swense_set_grid_tune(sea["nx"], sea["ny"], pad, len(z), lpc_, mb_ << 20, rv_)
+        tune = {"lpc": lpc_, "chunk_bytes": mb_ << 20, "row_variant": rv_, "source": "--tune"}
+    elif not args.no_autotune:
+        tune = api.autotune_grid(modes, z, pad, tl, out=grid)
+    else:
+        tune = None
+
     for _ in range(args.warmup):
         flush.zero_()
         step()
@@ -252,14 +268,17 @@ def run_ours(args, rank, world):
         g1, g2 = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
         with torch.cuda.graph(g1):
             api.fields_on_grid(modes, z, pad, tl, out=grid)
+        launches_s1 = S.swense_launches() - launches_c0
         with torch.cuda.graph(g2):
             api.interp(grid, tq, pts, out=outs)
         stage1, stage2 = g1.replay, g2.replay
         launches_per_step = S.swense_launches() - launches_c0
+        launches_s2 = launches_per_step - launches_s1
     else:
         stage1 = lambda: api.fields_on_grid(modes, z, pad, tl, out=grid)  # noqa: E731
         stage2 = lambda: api.interp(grid, tq, pts, out=outs)  # noqa: E731
         launches_per_step = None
+        launches_s1 = launches_s2 = None
     stream = torch.cuda.current_stream(dev)
     for _ in range(2):
         stage1()
@@ -320,9 +339,10 @@ def run_ours(args, rank, world):
                       "launches_per_step": None},
         "interp": {"ms": k2_ms, "algorithmic_bytes": k2_bytes, "touched_grid_bytes": touched,
                    "achieved_gbs": k2_bytes / (k2_ms * 1e-3) / 1e9,
-                   "frac_hbm": k2_bytes / (k2_ms * 1e-3) / 1e9 / hbm, "launches_per_step": 1},
+                   "frac_hbm": k2_bytes / (k2_ms * 1e-3) / 1e9 / hbm,
+                   "launches_per_step": launches_s2},
     }
-    stages["grid_ifft"]["launches_per_step"] = int(launches // args.steps) - 1
+    stages["grid_ifft"]["launches_per_step"] = launches_s1
     dom = "interp" if k2_ms >= k1_ms else "grid_ifft"
     kname = "k_interp_box" if dom == "interp" else "grid_ifft (k_col_stk + k_row_stk)"
     tr = NCU_TRAFFIC.get(kname)
@@ -339,6 +359,7 @@ def run_ours(args, rank, world):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": desc, "modes": [sea["nx"], sea["ny"]], "levels": nz, "pad_n": pad,
                    "launch": "host launches" if args.no_graph else "CUDA graph replay per stage",
+                   "stage1_tune": tune,
                    "n_tl": n_tl, "points": npts, "fields": 5,
                    "l2": "flushed between timed steps (256 MB write outside the events)",
                    "parallelism": f"replicas x{world}"},
@@ -358,28 +379,60 @@ def run_ours(args, rank, world):
                    pin(modes.A_phit.cpu().numpy()), pin(modes.omega.cpu().numpy())]
         h_pts = pin(pts_np)
         h_out = {k: torch.empty(npts, dtype=torch.float32).pin_memory() for k in outs}
-        d_bufs = [modes.A_eta, modes.A_phi, modes.A_phit, modes.omega]
         h2d = sum(t.numel() * t.element_size() for t in h_modes) + h_pts.numel() * 4
         d2h = sum(t.numel() * 4 for t in h_out.values())
 
-        def e2e_step():
-            for d, h in zip(d_bufs, h_modes):
-                d.copy_(h, non_blocking=True)
-            pts.copy_(h_pts, non_blocking=True)
-            api.fields_on_grid(modes, z, pad, tl, out=grid)
-            api.interp(grid, tq, pts, out=outs)
-            for k in outs:
-                h_out[k].copy_(outs[k], non_blocking=True)
+        # Three streams and two buffer sets: step i's host->device copy (modes and points) runs
+        # on the copy-in stream while step i-1 computes and step i-2's outputs go back on the
+        # copy-out stream. Every step still copies its inputs in and its five fields out.
+        s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+        s_cmp = stream
+        mset = [modes, api.upload_modes(sea, dev)]
+        pset = [pts, torch.empty_like(pts)]
+        oset = [outs, {k: torch.empty_like(v) for k, v in outs.items()}]
+        ev = lambda: torch.cuda.Event()  # noqa: E731
+        done_cmp = [None, None]
+        done_out = [None, None]
 
-        for _ in range(max(1, args.warmup)):
-            e2e_step()
+        def e2e_step(i):
+            b = i % 2
+            m, pd, od = mset[b], pset[b], oset[b]
+            with torch.cuda.stream(s_in):
+                if done_cmp[b] is not None:
+                    s_in.wait_event(done_cmp[b])          # buffers b free again
+                for d, h in zip((m.A_eta, m.A_phi, m.A_phit, m.omega), h_modes):
+                    d.copy_(h, non_blocking=True)
+                pd.copy_(h_pts, non_blocking=True)
+                e_in = ev()
+                e_in.record(s_in)
+            s_cmp.wait_event(e_in)
+            if done_out[b] is not None:
+                s_cmp.wait_event(done_out[b])             # outputs b copied out
+            api.fields_on_grid(m, z, pad, tl, out=grid)
+            api.interp(grid, tq, pd, out=od)
+            e_c = ev()
+            e_c.record(s_cmp)
+            done_cmp[b] = e_c
+            with torch.cuda.stream(s_out):
+                s_out.wait_event(e_c)
+                for k in od:
+                    h_out[k].copy_(od[k], non_blocking=True)
+                e_o = ev()
+                e_o.record(s_out)
+            done_out[b] = e_o
+
+        for i in range(max(2, args.warmup)):
+            e2e_step(i)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ks = max(1, args.steps)
-        e0.record(stream)
-        for _ in range(ks):
-            e2e_step()
-        e1.record(stream)
+        e0.record(s_cmp)
+        s_in.wait_event(e0)
+        for i in range(ks):
+            e2e_step(i)
+        s_cmp.wait_stream(s_out)
+        s_cmp.wait_stream(s_in)
+        e1.record(s_cmp)
         torch.cuda.synchronize()
         e_ms = e0.elapsed_time(e1) / ks
         if world > 1:
@@ -388,7 +441,8 @@ def run_ours(args, rank, world):
             e_ms = float(t.item())
         line["e2e"] = {"value": world * npts / (e_ms * 1e-3), "unit": "points/s",
                        "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                       "ms_per_step": e_ms}
+                       "ms_per_step": e_ms,
+                       "pipeline": "copy-in, compute and copy-out streams overlap across steps"}
 
     # ---- CPU baseline: the FP64 oracle on a bounded sample, rank 0 at N = 1 only
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -666,6 +720,71 @@ def run_direct(args, rank, world):
         print(json.dumps(line), flush=True)
 
 
+def run_large(args, rank, world):
+    """Large steep sea (2048 x 1024 modes, 128 levels, two time levels): one step = the grid at both
+    time levels + the gather of 16 M points (Morton order) + the split-BF16 direct sum at 1 M
+    near-body points over all modes; also the random-order variant with device binning."""
+    import torch
+    from paper_2005_12716_gb300 import _swense as S
+    from paper_2005_12716_gb300 import api
+    from wavegen import configs
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    cfg = configs.large_sea()
+    sea, z, tl, tq = cfg["sea"], cfg["z_levels"], cfg["t_levels"], cfg["t_query"]
+    modes = api.upload_modes(sea, dev)
+    grid = api.alloc_grid(modes, z, 1, tl, dev)
+    pts = torch.from_numpy(cfg["points"]).to(dev)
+    near = torch.from_numpy(cfg["near_points"]).to(dev)
+    n, nn = len(cfg["points"]), len(cfg["near_points"])
+    outs = {k: torch.empty(n, dtype=torch.float32, device=dev) for k in ("eta", "u", "v", "w", "p")}
+    outn = {k: torch.empty(nn, dtype=torch.float32, device=dev) for k in ("eta", "u", "v", "w", "p")}
+    perm = torch.randperm(n, generator=torch.Generator().manual_seed(11)).to(dev)
+    pts_r = pts[perm].contiguous()
+    tune = api.autotune_grid(modes, z, 1, tl, out=grid)
+    stages = {
+        "grid": lambda: api.fields_on_grid(modes, z, 1, tl, out=grid),
+        "gather_morton": lambda: api.interp(grid, tq, pts, out=outs),
+        "direct_split_near": lambda: api.direct(modes, tq, near, precision="split_bf16", out=outn),
+    }
+
+    def binned():
+        order, srt = api.bin_points(grid, pts_r)
+        api.interp_permuted(grid, tq, srt, order, out=outs)
+    steps = max(3, min(args.steps, 5))
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    res = {}
+    l0 = S.swense_launches()
+    for name, fn in list(stages.items()) + [("bin_and_gather_random", binned)]:
+        for _ in range(max(3, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        res[name] = _time_events(fn, steps)
+    launches = S.swense_launches() - l0
+    clk = clocks.stop()
+    ms_step = res["grid"] + res["gather_morton"] + res["direct_split_near"]
+    hbm = _peak_hbm()
+    nx_r, ny_r = api.grid_dims(modes, 1)
+    grid_bytes = len(tl) * (len(z) * nx_r * ny_r * 16 + nx_r * ny_r * 4)
+    line = {
+        "metric": "wave-field points/sec at stated err vs FP64 oracle; % of HBM roofline",
+        "value": (n + nn) / (ms_step * 1e-3), "unit": "points/s", "n_gpus": 1, "steps": steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (direct: bf16x3 split, f32 accumulate)",
+        "data": "synthetic",
+        "config": {"workload": f"large_sea: 2048x1024 modes, 128 levels, 2 time levels, {n} Morton-order "
+                               f"points + {nn} near-body points (direct split-BF16 over all modes)",
+                   "stage1_tune": tune, "l2": "inputs larger than L2 (8.6 GB grid)"},
+        "stages_ms": res,
+        "grid_hbm_frac": grid_bytes / (res["grid"] * 1e-3) / 1e9 / hbm,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -678,7 +797,8 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         torch.distributed.init_process_group("nccl")
     try:
-        {"batched": run_batched, "learned": run_learned, "e1": run_e1, "direct": run_direct}.get(
+        {"batched": run_batched, "learned": run_learned, "e1": run_e1, "direct": run_direct,
+         "large": run_large}.get(
             args.config, run_ours)(
             args, rank, world)
     finally:

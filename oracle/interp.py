@@ -65,7 +65,18 @@ def interp_points(nodes_tl, eta_tl, Lx, Ly, z_levels, t_levels, pts, t,
     """
     nodes_tl = np.asarray(nodes_tl, np.float64)
     eta_tl = np.asarray(eta_tl, np.float64)
-    TL, nz, nyr, nxr, _ = nodes_tl.shape
+    _, _, nyr, nxr, _ = nodes_tl.shape
+    return interp_points_fetch(lambda tl, iz, iy, ix: nodes_tl[tl, iz, iy, ix],
+                               lambda tl, iy, ix: eta_tl[tl, iy, ix], nxr, nyr, Lx, Ly, z_levels,
+                               t_levels, pts, t, rho, g, p_mode)
+
+
+def interp_points_fetch(node_at, eta_at, nxr, nyr, Lx, Ly, z_levels, t_levels, pts, t,
+                        rho=1000.0, g=9.81, p_mode="dyn"):
+    """The same interpolation with the grid given by fetch functions instead of arrays (so a
+    grid too large to hold can be sampled where the stencils need it):
+    node_at(tl, iz, iy, ix) -> [n][4] values (u, v, w, phit) and eta_at(tl, iy, ix) -> [n] for
+    integer index arrays of length n."""
     pts = np.asarray(pts, np.float64)
     n = len(pts)
     wt = lagrange_basis(np.asarray(t_levels, np.float64), np.float64(t))          # [TL]
@@ -77,19 +88,21 @@ def interp_points(nodes_tl, eta_tl, Lx, Ly, z_levels, t_levels, pts, t,
     j0, wz, inside = level_stencil(pts[:, 2], z_levels)
     iz = j0[:, None] + np.arange(4)
 
-    # grid blended in time first: sum_t w_t G_t (linear, so the order does not matter)
-    G = np.tensordot(wt, nodes_tl, axes=(0, 0))                                   # [nz][ny][nx][4]
-    E = np.tensordot(wt, eta_tl, axes=(0, 0))                                     # [ny][nx]
+    # each stencil node blended in time first: sum_t w_t G_t (linear, so the order of the sums
+    # does not matter)
     out4 = np.zeros((n, 4))
     for a in range(4):
         for b in range(iy.shape[1]):
             for cidx in range(4):
-                vals = G[iz[:, a], iy[:, b], ix[:, cidx]]                          # [n][4]
+                vals = sum(wt[tl] * np.asarray(node_at(tl, iz[:, a], iy[:, b], ix[:, cidx]), np.float64)
+                           for tl in range(len(wt)))                               # [n][4]
                 out4 += (wz[:, a] * wy[:, b] * wx[:, cidx])[:, None] * vals
     eta = np.zeros(n)
     for b in range(iy.shape[1]):
         for cidx in range(4):
-            eta += wy[:, b] * wx[:, cidx] * E[iy[:, b], ix[:, cidx]]
+            e = sum(wt[tl] * np.asarray(eta_at(tl, iy[:, b], ix[:, cidx]), np.float64)
+                    for tl in range(len(wt)))
+            eta += wy[:, b] * wx[:, cidx] * e
     u, v, w, phit = (out4[:, q].copy() for q in range(4))
     for arr in (u, v, w, phit):
         arr[~inside] = np.nan

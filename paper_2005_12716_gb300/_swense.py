@@ -338,8 +338,17 @@ _SIGS.update({
     "swense_autotune_grid": (ctypes.c_int, [ctypes.POINTER(swense_modes), ctypes.c_int32,
                                             ctypes.c_void_p, ctypes.POINTER(swense_grid_desc),
                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
-                                            ctypes.c_void_p, ctypes.c_void_p]),
+                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
 })
+
+
+_SIGS["swense_set_grid_tune"] = (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                                ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
+                                                ctypes.c_int32])
+
+
+def swense_set_grid_tune(nx, ny, pad_n, nz, lpc=-1, chunk_bytes=32 << 20, row_variant=0):
+    _check(load().swense_set_grid_tune(nx, ny, pad_n, nz, lpc, chunk_bytes, row_variant))
 
 
 def swense_batch_run(instances, p_mode=P_DYN, rho=1000.0, g=9.81, stream=None):
@@ -349,11 +358,14 @@ def swense_batch_run(instances, p_mode=P_DYN, rho=1000.0, g=9.81, stream=None):
 
 
 def swense_autotune_grid(modes, n_tl, t, desc, nodes, eta, stream=None):
+    """Returns (levels per column block (0: shared-memory path), chunk bytes, row variant)."""
     lpc = ctypes.c_int32(0)
     chunk = ctypes.c_int64(0)
+    rowv = ctypes.c_int32(0)
     tt = None if t is None else np.ascontiguousarray(t, np.float64)
     _check(load().swense_autotune_grid(ctypes.byref(modes), n_tl,
                                        None if tt is None else tt.ctypes.data,
                                        ctypes.byref(desc), _ptr(nodes), _ptr(eta),
-                                       ctypes.byref(lpc), ctypes.byref(chunk), _stream(stream)))
-    return lpc.value, chunk.value
+                                       ctypes.byref(lpc), ctypes.byref(chunk), ctypes.byref(rowv),
+                                       _stream(stream)))
+    return lpc.value, chunk.value, rowv.value

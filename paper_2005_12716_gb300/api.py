@@ -91,6 +91,19 @@ def fields_on_grid(modes, z_levels, pad_n, t_levels, out=None, stream=None, sche
     return g
 
 
+def autotune_grid(modes, z_levels, pad_n, t_levels, out=None, stream=None, scheme="lagrange3"):
+    """swense_autotune_grid: time the candidate launch shapes for this grid shape, keep the
+    fastest for later swense_fields_on_grid calls (writes the grid); returns
+    {"lpc", "chunk_bytes", "row_variant"}."""
+    g = out if out is not None else alloc_grid(modes, z_levels, pad_n, t_levels,
+                                               modes.A_eta.device, scheme)
+    desc = S.make_grid_desc(pad_n, z_levels, g.scheme)
+    lpc, chunk, rowv = S.swense_autotune_grid(modes.c_struct(), len(t_levels),
+                                              np.asarray(t_levels, np.float64), desc, g.nodes,
+                                              g.eta, stream)
+    return {"lpc": lpc, "chunk_bytes": chunk, "row_variant": rowv}
+
+
 def interp(grid, t, pts, p_mode="dyn", rho=1000.0, g=9.81, out=None, count_out_of_range=False,
            stream=None):
     """swense_interp; returns dict of float32 device tensors (eta, u, v, w, p) and the count."""

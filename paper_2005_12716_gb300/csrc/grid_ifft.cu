@@ -576,7 +576,7 @@ __global__ void __launch_bounds__(256, N >= 1024 ? 1 : 2) k_row_stk(RowArgs a) {
 // memory then serves as the per-warp exchange buffers. Each CTA writes one float2 half of the
 // nodes' float4; the two halves meet in L2.
 template <int N>
-__global__ void __launch_bounds__(256, 3) k_row_half(RowArgs a) {
+__global__ void __launch_bounds__(256, N >= 1024 ? 2 : 3) k_row_half(RowArgs a) {
   extern __shared__ float2 sm[];                 // [2][Mh][rb + 1] staging, then warp buffers
   constexpr int E = N / 32, RL = stk_radix(N, stk_npass(N) - 1);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -612,6 +612,8 @@ struct Tune {
   int lpc = -1;                         // levels per column-transform CTA of the warp path;
                                         // 0: shared-memory path; -1: default for the shape
   size_t chunk_bytes = kChunkBytes;     // scratch per level chunk (L2-resident)
+  int rowv = 0;                         // row pass: 0 both field pairs per warp (k_row_stk),
+                                        // 1 one field pair per CTA (k_row_half)
 };
 std::mutex g_tune_mutex;
 std::map<std::array<int64_t, 4>, Tune> g_tune;
@@ -684,7 +686,28 @@ int launch_row(const RowArgs& r, dim3 grid, size_t smem, cudaStream_t stream) {
   return SWENSE_OK;
 }
 
-int launch_row_e(int E, const RowArgs& r, dim3 grid, size_t smem, cudaStream_t s) {
+template <int N>
+int launch_row_half(const RowArgs& r, dim3 grid, cudaStream_t stream) {
+  static_assert(kRowBlock * 32 == kThreads, "one staged row per warp");
+  const size_t smem = std::max(size_t(2) * r.Mh * (kRowBlock + 1), size_t(8) * stk_buf(N)) * sizeof(float2);
+  int st = set_smem((const void*)k_row_half<N>, smem);
+  if (st) return st;
+  grid.z = 2;
+  k_row_half<N><<<grid, kThreads, smem, stream>>>(r);
+  SWENSE_CUDA_TRY(cudaGetLastError());
+  count_launches(1);
+  return SWENSE_OK;
+}
+
+int launch_row_e(int E, const RowArgs& r, dim3 grid, size_t smem, cudaStream_t s, int rowv = 0) {
+  if (rowv == 1) {
+    switch (E) {
+      case 8: return launch_row_half<256>(r, grid, s);
+      case 16: return launch_row_half<512>(r, grid, s);
+      case 32: return launch_row_half<1024>(r, grid, s);
+      default: break;                   // shorter rows: the joint kernel
+    }
+  }
   switch (E) {
     case 1: return launch_row<1>(r, grid, smem, s);
     case 2: return launch_row<2>(r, grid, smem, s);
@@ -764,7 +787,7 @@ size_t scratch_bytes(const GridPlan& p, int chunk) {
 
 // Enqueue every kernel of the request; `ws` holds scratch_bytes(p, chunk) bytes.
 int launch_grid(const GridPlan& p, const swense_modes* md, const double* t, float* nodes, float* eta,
-                void* ws, int chunk, cudaStream_t stream, int lpc = kColLevels) {
+                void* ws, int chunk, cudaStream_t stream, int lpc = kColLevels, int rowv = 0) {
   const float2* tw = nullptr;
   {
     int st = twiddles(stream, &tw);
@@ -928,7 +951,8 @@ int launch_grid(const GridPlan& p, const swense_modes* md, const double* t, floa
                               dim3((Mh + kColBlock - 1) / kColBlock, (nl + lpc - 1) / lpc),
                               smem_col, stream);
         if (!st) st = launch_row_e(int(Nxr / 32), ra,
-                                   dim3(unsigned((Nyr + kRowBlock - 1) / kRowBlock), nl), smem_row, stream);
+                                   dim3(unsigned((Nyr + kRowBlock - 1) / kRowBlock), nl), smem_row, stream,
+                                   rowv);
         if (st) return st;
       }
       continue;
@@ -977,12 +1001,13 @@ extern "C" int swense_fields_on_grid(const swense_modes* md, int32_t n_tl, const
   }
   // untuned default: the warp path where its transforms stay in registers (n <= 512)
   const int lpc = tn.lpc >= 0 ? tn.lpc : ((p.Nxr <= 512 && p.Nyr <= 512) ? kColLevels : 0);
-  return launch_grid(p, md, t, nodes, eta, ws, chunk, stream, lpc);
+  return launch_grid(p, md, t, nodes, eta, ws, chunk, stream, lpc, tn.rowv);
 }
 
 extern "C" int swense_autotune_grid(const swense_modes* md, int32_t n_tl, const double* t,
                                     const swense_grid_desc* desc, float* nodes, float* eta,
-                                    int32_t* lpc_out, int64_t* chunk_bytes_out, void* stream_) {
+                                    int32_t* lpc_out, int64_t* chunk_bytes_out, int32_t* row_variant_out,
+                                    void* stream_) {
   cudaStream_t stream = static_cast<cudaStream_t>(stream_);
   GridPlan p;
   int st = plan_grid(md, n_tl, t, desc, nodes, eta, &p);
@@ -993,18 +1018,20 @@ extern "C" int swense_autotune_grid(const swense_modes* md, int32_t n_tl, const 
     SWENSE_CUDA_TRY(cudaEventCreate(&e0));
     SWENSE_CUDA_TRY(cudaEventCreate(&e1));
     float best_ms = 1e30f;
-    for (int lpc : {0, 1, 2, 4}) {
+    for (int lpc : {0, 1, 2, 4})
+    for (int rowv : {0, 1}) {
       if (lpc > 0 && !warp_path(p.ny, p.Nxr, p.Nyr)) continue;
+      if (rowv && (lpc == 0 || p.Nxr < 256)) continue;   // only the Stockham row sizes have two kernels
       for (size_t mb : {16, 32, 64}) {
         const size_t cb = mb << 20;
         const int chunk = int(std::max<size_t>(1, std::min<size_t>(p.nz, cb / p.per_level)));
         void* ws = nullptr;
         st = workspace(scratch_bytes(p, chunk), stream, &ws);
-        if (!st) st = launch_grid(p, md, t, nodes, eta, ws, chunk, stream, lpc);   // warm
+        if (!st) st = launch_grid(p, md, t, nodes, eta, ws, chunk, stream, lpc, rowv);   // warm
         float ms = 0.f, tot = 0.f;
         for (int rep = 0; rep < 3 && !st; ++rep) {
           if (cudaEventRecord(e0, stream) != cudaSuccess) { st = SWENSE_ERR_CUDA; break; }
-          st = launch_grid(p, md, t, nodes, eta, ws, chunk, stream, lpc);
+          st = launch_grid(p, md, t, nodes, eta, ws, chunk, stream, lpc, rowv);
           if (cudaEventRecord(e1, stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
               cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) st = SWENSE_ERR_CUDA;
           tot += ms;
@@ -1014,6 +1041,7 @@ extern "C" int swense_autotune_grid(const swense_modes* md, int32_t n_tl, const 
           best_ms = tot;
           best.lpc = lpc;
           best.chunk_bytes = cb;
+          best.rowv = rowv;
         }
       }
       if (st) break;
@@ -1026,6 +1054,23 @@ extern "C" int swense_autotune_grid(const swense_modes* md, int32_t n_tl, const 
   }
   if (lpc_out) *lpc_out = best.lpc;
   if (chunk_bytes_out) *chunk_bytes_out = int64_t(best.chunk_bytes);
+  if (row_variant_out) *row_variant_out = best.rowv;
+  return SWENSE_OK;
+}
+
+extern "C" int swense_set_grid_tune(int32_t nx, int32_t ny, int32_t pad_n, int32_t nz, int32_t lpc,
+                                    int64_t chunk_bytes, int32_t row_variant) {
+  if (lpc != -1 && lpc != 0 && lpc != 1 && lpc != 2 && lpc != 4)
+    return fail(SWENSE_ERR_ARG, "lpc must be -1 (default), 0, 1, 2 or 4");
+  if (chunk_bytes < (int64_t(1) << 20) || chunk_bytes > (int64_t(1) << 30))
+    return fail(SWENSE_ERR_ARG, "chunk_bytes must be in [1 MiB, 1 GiB]");
+  if (row_variant != 0 && row_variant != 1) return fail(SWENSE_ERR_ARG, "row_variant must be 0 or 1");
+  Tune tn;
+  tn.lpc = lpc;
+  tn.chunk_bytes = size_t(chunk_bytes);
+  tn.rowv = row_variant;
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  g_tune[{nx, ny, pad_n, nz}] = tn;
   return SWENSE_OK;
 }
 

@@ -88,12 +88,34 @@ __device__ __forceinline__ void lagrange4(const float zn[4], float4 inv, float z
 
 // Shared-memory copy of the levels and, per stencil start j0, the inverse Lagrange
 // denominators of the levels j0 .. j0+3 (computed once per CTA: no divisions per point).
+// z lookup: ZLUT equal buckets over [z_0, z_{nz-1}]; lut[b] = largest level index j with
+// z_j <= z_0 + b h. A point starts its search one bucket below its own (so rounding of the
+// bucket index cannot place it past its level) and steps up: one or two steps for any level
+// spacing that is not much finer than h.
+constexpr int ZLUT = 256;
+
 struct LevelTables {
   float z[SWENSE_MAX_LEVELS];
   float4 inv[SWENSE_MAX_LEVELS];
+  unsigned char lut[ZLUT];
+  float z0, inv_h;
 };
 
 __device__ __forceinline__ void fill_level_tables(LevelTables& T, const Levels& L, int nz) {
+  const float z0 = L.z[0], h = (L.z[nz - 1] - z0) / float(ZLUT);
+  if (threadIdx.x == 0) {
+    T.z0 = z0;
+    T.inv_h = 1.f / h;
+  }
+  for (int b = threadIdx.x; b < ZLUT; b += blockDim.x) {
+    const float zb = z0 + float(b) * h;
+    int lo = 0, hi = nz;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (L.z[mid] <= zb) lo = mid + 1; else hi = mid;
+    }
+    T.lut[b] = (unsigned char)max(lo - 1, 0);
+  }
   for (int i = threadIdx.x; i < nz; i += blockDim.x) T.z[i] = L.z[i];
   for (int j = threadIdx.x; j <= nz - 4; j += blockDim.x) {
     float zn[4];
@@ -131,12 +153,10 @@ __device__ __forceinline__ PointCell point_cell(const InterpArgs& a, const Level
   // bracket: largest j with zs[j] <= z, clamped to [0, nz-2]; stencil j0 = clamp(j-1, 0, nz-4)
   const int nz = a.nz;
   c.inside = (z >= zs[0]) && (z <= zs[nz - 1]);
-  int lo = 0, hi = nz;  // first index with zs[idx] > z
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    if (zs[mid] <= z) lo = mid + 1; else hi = mid;
-  }
-  const int j = min(max(lo - 1, 0), nz - 2);
+  const float bf = fminf(fmaxf((z - T.z0) * T.inv_h, 0.f), float(ZLUT - 1));   // NaN -> 0
+  int jj = T.lut[max(int(bf) - 1, 0)];
+  while (jj + 1 < nz && zs[jj + 1] <= z) ++jj;
+  const int j = min(jj, nz - 2);
   c.j0 = min(max(j - 1, 0), nz - 4);
   float zn[4];
 #pragma unroll
@@ -247,9 +267,11 @@ __device__ __forceinline__ void fma2(unsigned long long& acc, unsigned long long
 __device__ __forceinline__ float lo2(unsigned long long v) { return __uint_as_float(unsigned(v)); }
 __device__ __forceinline__ float hi2(unsigned long long v) { return __uint_as_float(unsigned(v >> 32)); }
 
-__global__ void __launch_bounds__(BOX_THREADS, 3) k_interp_box(InterpArgs a, Levels L) {
-  extern __shared__ float4 sbox[];
-  float* seta = reinterpret_cast<float*>(sbox + BOX_NODES);
+// Box plan of one 1024-point chunk: box origin (grid node indices, wrapped) and extents, or
+// dims = -1 when the box does not fit the shared-memory tile (the chunk then gathers from
+// global memory). Computed by its own kernel so the gather kernel can start its box load at
+// once, without first waiting for its points.
+__global__ void __launch_bounds__(BOX_THREADS) k_interp_plan(InterpArgs a, Levels L, int4* __restrict__ plan) {
   __shared__ LevelTables zs;
   __shared__ int s_red[6][BOX_THREADS / 32];
   __shared__ int s_ref[2];
@@ -261,8 +283,6 @@ __global__ void __launch_bounds__(BOX_THREADS, 3) k_interp_box(InterpArgs a, Lev
     s_ref[0] = c.ix;
     s_ref[1] = c.iy;
   }
-  // No per-point state is kept across the box load (a dynamically indexed per-thread array
-  // would live in local memory): the main loop re-reads each point and recomputes its cell.
   __syncthreads();
   const int refx = s_ref[0], refy = s_ref[1];
   int mn[3] = {1 << 30, 1 << 30, 1 << 30}, mx[3] = {-(1 << 30), -(1 << 30), -(1 << 30)};
@@ -298,6 +318,7 @@ __global__ void __launch_bounds__(BOX_THREADS, 3) k_interp_box(InterpArgs a, Lev
     }
   }
   __syncthreads();
+  if (threadIdx.x != 0) return;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     mn[d] = s_red[d][0];
@@ -309,14 +330,38 @@ __global__ void __launch_bounds__(BOX_THREADS, 3) k_interp_box(InterpArgs a, Lev
   }
   // box: x nodes rel (mn0-1) .. (mx0+2), y likewise (one row in 2-D), levels mn2 .. mx2+3
   const int bx = mx[0] - mn[0] + 4;
-  // shared-memory row stride = 4 (mod 8) float4: reads of neighbouring cells (dx, dy in {0, 1})
-  // by one quarter-warp then fall into different bank groups
   const int sbx = bx + ((4 - bx) & 7);
   const int by = a.Nyr > 1 ? mx[1] - mn[1] + 4 : 1;
   const int bz = mx[2] - mn[2] + 4;
   const bool fits = int64_t(sbx) * by * bz <= BOX_NODES && int64_t(sbx) * by <= BOX_COLS &&
                     bx <= a.Nxr && by <= a.Nyr;
-  if (!fits) {
+  plan[blockIdx.x] = make_int4((refx + mn[0] - 1) & (a.Nxr - 1),
+                               a.Nyr > 1 ? ((refy + mn[1] - 1) & (a.Nyr - 1)) : 0, mn[2],
+                               fits ? (bx | (by << 11) | (bz << 22)) : -1);
+}
+
+__global__ void __launch_bounds__(BOX_THREADS, 3) k_interp_box(InterpArgs a, Levels L,
+                                                                const int4* __restrict__ plan) {
+  extern __shared__ float4 sbox[];
+  float* seta = reinterpret_cast<float*>(sbox + BOX_NODES);
+  __shared__ LevelTables zs;
+  fill_level_tables(zs, L, a.nz);
+  const int64_t p0 = int64_t(blockIdx.x) * BOX_PTS;
+  const int4 pl = plan[blockIdx.x];
+  // the first point's coordinates are in flight during the box load; each later point's while
+  // the previous one is processed
+  float nx_ = 0.f, ny_ = 0.f, nz_ = 0.f;
+  {
+    const int64_t i = p0 + threadIdx.x;
+    if (i < a.np) {
+      nx_ = __ldg(&a.pts[3 * i]);
+      ny_ = __ldg(&a.pts[3 * i + 1]);
+      nz_ = __ldg(&a.pts[3 * i + 2]);
+    }
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (pl.w < 0) {
+    __syncthreads();
 #pragma unroll 1
     for (int k = 0; k < BOX_PPT; ++k) {
       const int64_t i = p0 + k * BOX_THREADS + threadIdx.x;
@@ -330,27 +375,41 @@ __global__ void __launch_bounds__(BOX_THREADS, 3) k_interp_box(InterpArgs a, Lev
     }
     return;
   }
+  const int bx = pl.w & 2047, by = (pl.w >> 11) & 2047, bz = pl.w >> 22;
+  // shared-memory row stride = 4 (mod 8) float4: reads of neighbouring cells (dx, dy in {0, 1})
+  // by one quarter-warp then fall into different bank groups
+  const int sbx = bx + ((4 - bx) & 7);
   const size_t plane = size_t(a.Nyr) * a.Nxr;
-  const int x0 = refx + mn[0] - 1, y0 = a.Nyr > 1 ? refy + mn[1] - 1 : 0, l0 = mn[2];
+  const int x0 = pl.x, y0 = pl.y, l0 = pl.z;
   {
-    // rows (ly, lz) over warps, x over lanes; the time blend happens here, once per node
+    // rows (ly, lz) over warps, two rows per warp at a time (more loads in flight), x over
+    // lanes; the time blend happens here, once per node
     const size_t tl_stride = size_t(a.nz) * plane;
-    for (int r = warp; r < by * bz; r += BOX_THREADS / 32) {
-      const int lz = r / by, ly = r - lz * by;
-      const float4* src = a.nodes + size_t(l0 + lz) * plane + size_t((y0 + ly) & (a.Nyr - 1)) * a.Nxr;
-      float4* dst = sbox + r * sbx;
+    constexpr int NW = BOX_THREADS / 32;
+    const int nrows = by * bz;
+    for (int r0 = warp; r0 < nrows; r0 += 2 * NW) {
+      const int r1 = min(r0 + NW, nrows - 1);     // a duplicate of r0's last row when past the end
+      const int lz0 = r0 / by, ly0 = r0 - lz0 * by, lz1 = r1 / by, ly1 = r1 - lz1 * by;
+      const float4* src0 = a.nodes + size_t(l0 + lz0) * plane + size_t((y0 + ly0) & (a.Nyr - 1)) * a.Nxr;
+      const float4* src1 = a.nodes + size_t(l0 + lz1) * plane + size_t((y0 + ly1) & (a.Nyr - 1)) * a.Nxr;
       for (int lx = lane; lx < bx; lx += 32) {
         const int gx = (x0 + lx) & (a.Nxr - 1);
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
         for (int tl = 0; tl < a.n_tl; ++tl) {
-          const float4 gv = __ldg(&src[size_t(tl) * tl_stride + gx]);
+          const float4 g0 = __ldg(&src0[size_t(tl) * tl_stride + gx]);
+          const float4 g1 = __ldg(&src1[size_t(tl) * tl_stride + gx]);
           const float w = a.wt[tl];
-          v.x = fmaf(w, gv.x, v.x);
-          v.y = fmaf(w, gv.y, v.y);
-          v.z = fmaf(w, gv.z, v.z);
-          v.w = fmaf(w, gv.w, v.w);
+          v0.x = fmaf(w, g0.x, v0.x);
+          v0.y = fmaf(w, g0.y, v0.y);
+          v0.z = fmaf(w, g0.z, v0.z);
+          v0.w = fmaf(w, g0.w, v0.w);
+          v1.x = fmaf(w, g1.x, v1.x);
+          v1.y = fmaf(w, g1.y, v1.y);
+          v1.z = fmaf(w, g1.z, v1.z);
+          v1.w = fmaf(w, g1.w, v1.w);
         }
-        dst[lx] = v;
+        sbox[r0 * sbx + lx] = v0;
+        sbox[r1 * sbx + lx] = v1;                  // same value when r1 repeats a row
       }
     }
     for (int ly = warp; ly < by; ly += BOX_THREADS / 32) {
@@ -369,12 +428,20 @@ __global__ void __launch_bounds__(BOX_THREADS, 3) k_interp_box(InterpArgs a, Lev
 #pragma unroll 1
   for (int k = 0; k < BOX_PPT; ++k) {
     const int64_t i = p0 + k * BOX_THREADS + threadIdx.x;
-    if (i >= a.np) continue;
-    const float pz = __ldg(&a.pts[3 * i + 2]);
-    const PointCell c = point_cell(a, zs, __ldg(&a.pts[3 * i]), __ldg(&a.pts[3 * i + 1]), pz);
-    const int rx = wrap_rel(c.ix, refx, a.Nxr);
-    const int ry = a.Nyr > 1 ? wrap_rel(c.iy, refy, a.Nyr) : 0;
-    const float4* base = sbox + ((c.j0 - mn[2]) * by + (ry - mn[1])) * sbx + (rx - mn[0]);
+    if (i >= a.np) break;                          // later points of this thread are past np too
+    const float px = nx_, py = ny_, pz = nz_;
+    if (k + 1 < BOX_PPT && i + BOX_THREADS < a.np) {
+      nx_ = __ldg(&a.pts[3 * (i + BOX_THREADS)]);
+      ny_ = __ldg(&a.pts[3 * (i + BOX_THREADS) + 1]);
+      nz_ = __ldg(&a.pts[3 * (i + BOX_THREADS) + 2]);
+    }
+    const PointCell c = point_cell(a, zs, px, py, pz);
+    // node offsets inside the box; the plan kernel bounded them with the same point_cell, and
+    // the clamps keep every shared-memory read inside the box regardless
+    const int lx = min(max((c.ix - 1 - x0) & (a.Nxr - 1), 0), bx - 4);
+    const int ly = a.Nyr > 1 ? min(max((c.iy - 1 - y0) & (a.Nyr - 1), 0), by - 4) : 0;
+    const int lz = min(max(c.j0 - l0, 0), bz - 4);
+    const float4* base = sbox + (lz * by + ly) * sbx + lx;
     unsigned long long uv = pack2(0.f, 0.f), wt = pack2(0.f, 0.f);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -394,7 +461,7 @@ __global__ void __launch_bounds__(BOX_THREADS, 3) k_interp_box(InterpArgs a, Lev
       }
     }
     float acc_eta = 0.f;
-    const float* ebase = seta + (ry - mn[1]) * sbx + (rx - mn[0]);
+    const float* ebase = seta + ly * sbx + lx;
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
       if (b >= nys) break;
@@ -670,11 +737,12 @@ int interp_impl(const swense_grid* g, double t, const float* pts, const int32_t*
   Levels lev;
   int st = prepare_interp(g, t, pts, np, p_mode, rho, grav, &a, &lev);
   if (st) return st;
+  // workspace: [0, 256) out-of-range counter, then one int4 box plan per 1024-point chunk
+  void* ws = nullptr;
+  st = workspace(256 + size_t((np + BOX_PTS - 1) / BOX_PTS) * sizeof(int4), stream, &ws);
+  if (st) return st;
   unsigned long long* d_count = nullptr;
   if (n_out_of_range) {
-    void* ws = nullptr;
-    st = workspace(256, stream, &ws);
-    if (st) return st;
     d_count = static_cast<unsigned long long*>(ws);
     SWENSE_CUDA_TRY(cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), stream));
   }
@@ -688,11 +756,14 @@ int interp_impl(const swense_grid* g, double t, const float* pts, const int32_t*
     a.perm = perm;
     const int64_t blocks = (np + BOX_PTS - 1) / BOX_PTS;
     if (blocks >= (int64_t(1) << 31)) return fail(SWENSE_ERR_SIZE, "too many points for one call");
+    int4* plan = reinterpret_cast<int4*>(static_cast<char*>(ws) + 256);
+    k_interp_plan<<<unsigned(blocks), BOX_THREADS, 0, stream>>>(a, lev, plan);
+    SWENSE_CUDA_TRY(cudaGetLastError());
     SWENSE_CUDA_TRY(cudaFuncSetAttribute((const void*)k_interp_box,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, int(BOX_SMEM)));
-    k_interp_box<<<unsigned(blocks), BOX_THREADS, BOX_SMEM, stream>>>(a, lev);
+    k_interp_box<<<unsigned(blocks), BOX_THREADS, BOX_SMEM, stream>>>(a, lev, plan);
     SWENSE_CUDA_TRY(cudaGetLastError());
-    count_launches(1);
+    count_launches(2);
   }
   if (n_out_of_range) {
     unsigned long long h = 0;

@@ -114,3 +114,23 @@ def test_calm_water_grid_is_zero(api):
     z = np.array([-1, -0.5, 0, 0.1], np.float32)
     g = api.fields_on_grid(api.upload_modes(sea), z, 2, [0.0])
     assert float(g.nodes.abs().max()) == 0.0 and float(g.eta.abs().max()) == 0.0
+
+
+@pytest.mark.parametrize("lpc,rowv,chunk_mb", [(0, 0, 32), (1, 0, 1), (2, 1, 32), (4, 1, 1), (2, 0, 64)])
+@pytest.mark.parametrize("shape", [(256, 64, 1), (128, 128, 2), (512, 32, 1), (512, 32, 2)])
+def test_every_launch_shape_matches_oracle(api, lpc, rowv, chunk_mb, shape):
+    """Each transform path the autotuner can choose (shared-memory kernels; 1, 2 or 4 levels per
+    column block; both or one field pair per row block; level chunks from one level up), forced
+    with swense_set_grid_tune, against the oracle: 256-, 512- and 1024-point rows, 64- to
+    256-point columns, several level chunks."""
+    from paper_2005_12716_gb300 import _swense as S
+    nx, ny, pad = shape
+    rng = np.random.default_rng(nx + ny + pad)
+    comps = seas.random_linear_components(nx, ny, 6.0, 3.0, 10, 0.01, rng)
+    sea = seas.linear_sea(nx, ny, 6.0, 3.0, comps)
+    z = np.linspace(-1.0, 0.04, 9).astype(np.float32)
+    S.swense_set_grid_tune(nx, ny, pad, len(z), lpc, chunk_mb << 20, rowv)
+    try:
+        _check(api, sea, z, pad, [0.0, 0.13])
+    finally:
+        S.swense_set_grid_tune(nx, ny, pad, len(z), -1, 32 << 20, 0)

@@ -11,6 +11,12 @@ rho = 1000 kg/m^3. Seeds are 20051270 + workload number.
                    0.075 lambda_p]; points = the cell centres and face centres of a graded hex
                    O-grid (160 radial x 128 angular x 100 vertical cells) around a vertical
                    cylinder of radius 0.039 lambda_p at the domain centre; two time levels.
+- ``large_sea``    3-D JONSWAP sea, k_p Hs / 2 = 0.12, gamma = 3.3, cos^2 spreading, 2048 x 1024
+                   modes on 128 x 64 lambda_p, 128 levels on [-lambda_p, 1.5 Hs]; 16 M uniform
+                   points over the domain and that z range, delivered in Morton order of their
+                   grid cells (or in random order, for the device-binning variant); 1 M
+                   near-body points uniform in 0.039 lambda_p < r < 0.25 lambda_p around a
+                   vertical cylinder at the domain centre; two time levels.
 - ``*_small``      the same recipes shrunk so the oracle finishes in seconds.
 """
 import numpy as np
@@ -102,3 +108,51 @@ def e1_divergence(pad_n=1, window_lp=2.0, levels=64, seed=SEED0 + 6):
     mesh = M.box_xz_mesh(x_edges, z_edges)
     return {"name": "e1_divergence", "sea": sea, "z_levels": z, "pad_n": pad_n, "mesh": mesh,
             "t_levels": np.array([0.0]), "t_query": 0.0, "lambda_p": lp, "Hs": Hs}
+
+
+def morton_order(pts, Lx, Ly, z_lo, z_hi, bits=10):
+    """Permutation sorting points by the Morton (Z-order) code of their cell on a 2^bits grid per
+    axis over [0, Lx) x [0, Ly) x [z_lo, z_hi]."""
+    n = 1 << bits
+    q = np.empty((len(pts), 3), np.uint64)
+    q[:, 0] = np.clip((pts[:, 0] / Lx * n).astype(np.int64), 0, n - 1)
+    q[:, 1] = np.clip((pts[:, 1] / Ly * n).astype(np.int64), 0, n - 1)
+    q[:, 2] = np.clip(((pts[:, 2] - z_lo) / (z_hi - z_lo) * n).astype(np.int64), 0, n - 1)
+    code = np.zeros(len(pts), np.uint64)
+    for b in range(bits):
+        for d in range(3):
+            code |= ((q[:, d] >> np.uint64(b)) & np.uint64(1)) << np.uint64(3 * b + d)
+    return np.argsort(code, kind="stable")
+
+
+def large_sea(nx=2048, ny=1024, n_levels=128, n_points=16_000_000, n_near=1_000_000,
+              seed=SEED0 + 5, n_tl=2, order="morton"):
+    lp = 1.0
+    Hs = 0.24 * lp / (2 * np.pi)                       # k_p Hs / 2 = 0.12
+    Lx, Ly = nx / 16 * lp, ny / 16 * lp                # 16 nodes per peak wavelength
+    sea = seas.jonswap_sea(nx, ny, Lx, Ly, Hs, lp, gamma=3.3, heading=0.0, seed=seed)
+    z = P.levels_surface_clustered(-lp, 1.5 * Hs, n_levels, n_band=(3 * n_levels) // 8,
+                                   band=1.5 * Hs)
+    rng = np.random.default_rng(seed + 1000)
+    pts = np.empty((n_points, 3), np.float32)
+    pts[:, 0] = rng.uniform(0.0, Lx, n_points)
+    pts[:, 1] = rng.uniform(0.0, Ly, n_points)
+    pts[:, 2] = rng.uniform(float(z[0]), float(z[-1]), n_points)
+    if order == "morton":
+        pts = np.ascontiguousarray(pts[morton_order(pts, Lx, Ly, float(z[0]), float(z[-1]))])
+    # near-body points: uniform in the annulus R < r < 0.25 lambda_p, z uniform in the level range
+    R, r_out = 0.039 * lp, 0.25 * lp
+    r = np.sqrt(rng.uniform(R * R, r_out * r_out, n_near))
+    th = rng.uniform(0.0, 2 * np.pi, n_near)
+    near = np.empty((n_near, 3), np.float32)
+    near[:, 0] = 0.5 * Lx + r * np.cos(th)
+    near[:, 1] = 0.5 * Ly + r * np.sin(th)
+    near[:, 2] = rng.uniform(float(z[0]), float(z[-1]), n_near)
+    Tp = 2 * np.pi / sea["jonswap"]["omega_p"]
+    t_levels = np.arange(n_tl) * (Tp / 16)
+    return {
+        "name": "large_sea", "sea": sea, "z_levels": z, "pad_n": 1, "points": pts,
+        "near_points": near, "t_levels": t_levels,
+        "t_query": float(t_levels[(n_tl - 1) // 2] + 0.37 * (t_levels[1] - t_levels[0])),
+        "period": Tp, "centre": (0.5 * Lx, 0.5 * Ly), "lambda_p": lp,
+    }
