@@ -273,6 +273,7 @@ struct ColArgs {
   int lev0, nlev;        // chunk
   float kxs, kys, depth;
   int Nxr, spline;
+  int ldG;               // m stride of the transposed intermediate (k_col_t)
 };
 
 // Modal field q at (kx, ky, |k|) with depth factors F, S: U = i kx F A, V = i ky F A,
@@ -365,6 +366,7 @@ struct RowArgs {
   float4* nodes;         // [nz][Nyr][Nxr] of this time level
   const float2* tw;
   int Mh, Nxr, Nyr, rb, lev0;
+  int ldG;               // m stride of the transposed intermediate (k_row_t)
 };
 
 template <int E>
@@ -606,6 +608,148 @@ __global__ void __launch_bounds__(256, N >= 1024 ? 2 : 3) k_row_half(RowArgs a) 
   for (int e = 0; e < E; ++e) __stcs(&o2[2 * (lane + 32 * (e / RL) + (e % RL) * (N / RL))], z[e]);
 }
 
+// Transposed-intermediate pair for 256- to 1024-point transforms. The column pass writes
+// G[level][field][y][m] with the m stride padded to a multiple of four (ldG), so a grid row's
+// inputs are contiguous; the row pass then reads them straight into registers with coalesced
+// loads, with no staging and no block-wide barrier.
+//
+// Column pass: the eight warps of a block own eight consecutive kx columns; each loads its
+// column's modes once (reused over the block's levels), forms NF modal fields per depth-factor
+// evaluation, transforms them, and the block writes the eight columns out row by row through a
+// padded shared tile (64-byte segments).
+template <int N, int NF>
+__global__ void __launch_bounds__(256, N >= 1024 ? 1 : 2) k_col_t(ColArgs a, Levels L) {
+  extern __shared__ float2 sm[];                 // tile [N][kColBlock + 1], then warp buffers
+  constexpr int E = N / 32, RL = stk_radix(N, stk_npass(N) - 1);
+  constexpr int TLD = kColBlock + 1;
+  static_assert(kColBlock * 32 == kThreads, "one column per warp");
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c0 = blockIdx.x * kColBlock;
+  const int m = c0 + warp;
+  const bool colok = m < a.Mh;
+  float2* tile = sm;
+  float2* wbuf = sm + N * TLD + warp * stk_buf(N);
+  float2 T[stk_twn(N)];
+  stk_init<N>(T, a.tw, lane);
+  const int nyh = a.ny >> 1;
+  const float kx = float(m) * a.kxs;
+  // modes of element e (zero in the padding and at the Nyquist row)
+  auto load_mode = [&](int e, float2& ap, float2& at) {
+    const int p = lane + 32 * (e / 8) + (e % 8) * (N / 8);
+    int n = 0;
+    bool live = colok;
+    if (p < nyh) n = p;
+    else if (p > N - nyh) n = p - N;
+    else live = false;
+    ap = at = make_float2(0.f, 0.f);
+    if (live) {
+      const size_t gi = size_t(n >= 0 ? n : a.ny + n) * a.nxh1 + m;
+      ap = __ldg(&a.A_phi[gi]);
+      at = __ldg(&a.A_phit[gi]);
+      if (a.spline) {
+        const float pf = spline_prefilter(m, a.Nxr, n, a.Nyr);
+        ap = make_float2(pf * ap.x, pf * ap.y);
+        at = make_float2(pf * at.x, pf * at.y);
+      }
+    }
+  };
+  // short columns keep their modes in registers across levels; longer ones reload (L1)
+  constexpr bool KEEP = N <= 256;
+  float2 Ap[KEEP ? E : 1], At[KEEP ? E : 1];
+  if constexpr (KEEP) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) load_mode(e, Ap[e], At[e]);
+  }
+  for (int li = 0; li < a.lpc; ++li) {
+    const int level = blockIdx.y * a.lpc + li;
+    if (level >= a.nlev) break;                  // uniform over the block
+    const float z = L.z[a.lev0 + level];
+#pragma unroll 1
+    for (int g = 0; g < 4 / NF; ++g) {
+      float2 v[NF][E];
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int p = lane + 32 * (e / 8) + (e % 8) * (N / 8);
+        const int n = p < N / 2 ? p : p - N;
+        const float ky = float(n) * a.kys;
+        const float kk = sqrtf(kx * kx + ky * ky);
+        float F, S;
+        depth_factors(kk, z, a.depth, F, S);
+        float2 ap, at;
+        if constexpr (KEEP) {
+          ap = Ap[e];
+          at = At[e];
+        } else {
+          load_mode(e, ap, at);
+        }
+#pragma unroll
+        for (int f = 0; f < NF; ++f) v[f][e] = modal_field(g * NF + f, kx, ky, kk, F, S, ap, at);
+      }
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        stk_fft<N>(v[f], T, a.tw, wbuf, lane);
+#pragma unroll
+        for (int e = 0; e < E; ++e) tile[(lane + 32 * (e / RL) + (e % RL) * (N / RL)) * TLD + warp] = v[f][e];
+        __syncthreads();
+        float2* out = a.G + (size_t(level) * 4 + g * NF + f) * a.Nyr * a.ldG + c0;
+        for (int i = threadIdx.x; i < N * kColBlock; i += kThreads) {
+          const int y = i / kColBlock, w = i % kColBlock;
+          if (c0 + w < a.Mh) __stcg(&out[size_t(y) * a.ldG + w], tile[y * TLD + w]);
+        }
+        __syncthreads();
+      }
+    }
+  }
+}
+
+// Row pass over the transposed intermediate: one warp per grid row of one level, its four
+// modal fields loaded straight from G (consecutive lanes read consecutive m), packed as
+// Z1 = U + iV and Z2 = W + iT over the full x spectrum, transformed, stored as float4.
+template <int N>
+__global__ void __launch_bounds__(256, N >= 1024 ? 1 : 2) k_row_t(RowArgs a) {
+  extern __shared__ float2 sm[];                 // warp exchange buffers
+  constexpr int E = N / 32, RL = stk_radix(N, stk_npass(N) - 1);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int y = blockIdx.x * (kThreads / 32) + warp;
+  const int level = blockIdx.y;
+  if (y >= a.Nyr) return;                        // no block-wide barrier in this kernel
+  float2 T[stk_twn(N)];
+  stk_init<N>(T, a.tw, lane);
+  float2* wbuf = sm + warp * stk_buf(N);
+  const size_t fs = size_t(a.Nyr) * a.ldG;
+  const float2* row = a.G + size_t(level) * 4 * fs + size_t(y) * a.ldG;
+  float4* out = a.nodes + (size_t(a.lev0 + level) * a.Nyr + y) * N;
+  float2 z1[E], z2[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int p = lane + 32 * (e / 8) + (e % 8) * (N / 8);
+    const bool lo = p < a.Mh, hi = p > N - a.Mh;
+    float2 U = make_float2(0.f, 0.f), V = U, W = U, Tt = U;
+    if (lo || hi) {
+      const int mm = lo ? p : N - p;
+      U = __ldcg(&row[mm]);
+      V = __ldcg(&row[fs + mm]);
+      W = __ldcg(&row[2 * fs + mm]);
+      Tt = __ldcg(&row[3 * fs + mm]);
+    }
+    if (p == 0) {
+      z1[e] = make_float2(U.x, V.x);
+      z2[e] = make_float2(W.x, Tt.x);
+    } else if (!hi) {
+      z1[e] = make_float2(U.x - V.y, U.y + V.x);
+      z2[e] = make_float2(W.x - Tt.y, W.y + Tt.x);
+    } else {
+      z1[e] = make_float2(U.x + V.y, V.x - U.y);
+      z2[e] = make_float2(W.x + Tt.y, Tt.x - W.y);
+    }
+  }
+  stk_fft<N>(z1, T, a.tw, wbuf, lane);
+  stk_fft<N>(z2, T, a.tw, wbuf, lane);
+#pragma unroll
+  for (int e = 0; e < E; ++e)
+    __stcs(&out[lane + 32 * (e / RL) + (e % RL) * (N / RL)], make_float4(z1[e].x, z1[e].y, z2[e].x, z2[e].y));
+}
+
 // Launch-shape choices of the warp-register path, per grid shape (set by swense_autotune_grid;
 // defaults otherwise).
 struct Tune {
@@ -662,6 +806,48 @@ int launch_row_stk(const RowArgs& r, dim3 grid, size_t smem, cudaStream_t stream
   SWENSE_CUDA_TRY(cudaGetLastError());
   count_launches(1);
   return SWENSE_OK;
+}
+
+template <int N, int NF>
+int launch_col_t(const ColArgs& c, const Levels& L, dim3 grid, cudaStream_t stream) {
+  const size_t smem = (size_t(N) * (kColBlock + 1) + size_t(8) * stk_buf(N)) * sizeof(float2);
+  int st = set_smem((const void*)k_col_t<N, NF>, smem);
+  if (st) return st;
+  k_col_t<N, NF><<<grid, kThreads, smem, stream>>>(c, L);
+  SWENSE_CUDA_TRY(cudaGetLastError());
+  count_launches(1);
+  return SWENSE_OK;
+}
+
+template <int N>
+int launch_row_t(const RowArgs& r, dim3 grid, cudaStream_t stream) {
+  const size_t smem = size_t(8) * stk_buf(N) * sizeof(float2);
+  int st = set_smem((const void*)k_row_t<N>, smem);
+  if (st) return st;
+  k_row_t<N><<<grid, kThreads, smem, stream>>>(r);
+  SWENSE_CUDA_TRY(cudaGetLastError());
+  count_launches(1);
+  return SWENSE_OK;
+}
+
+// Transposed-intermediate pair (row variant 2): both transform lengths in 256..1024.
+int launch_pair_t(const ColArgs& c, const RowArgs& r, const Levels& L, int nl, cudaStream_t s) {
+  const dim3 gc(unsigned((c.Mh + kColBlock - 1) / kColBlock), unsigned((nl + c.lpc - 1) / c.lpc));
+  const dim3 gr(unsigned((r.Nyr + 7) / 8), unsigned(nl));
+  int st;
+  switch (c.Nyr) {
+    case 256: st = launch_col_t<256, 2>(c, L, gc, s); break;
+    case 512: st = launch_col_t<512, 1>(c, L, gc, s); break;
+    case 1024: st = launch_col_t<1024, 1>(c, L, gc, s); break;
+    default: return fail(SWENSE_ERR_UNSUPPORTED, "transposed pair: column length");
+  }
+  if (st) return st;
+  switch (r.Nxr) {
+    case 256: return launch_row_t<256>(r, gr, s);
+    case 512: return launch_row_t<512>(r, gr, s);
+    case 1024: return launch_row_t<1024>(r, gr, s);
+    default: return fail(SWENSE_ERR_UNSUPPORTED, "transposed pair: row length");
+  }
 }
 
 int launch_col_e(int E, const ColArgs& c, const Levels& L, dim3 grid, size_t smem, cudaStream_t s) {
@@ -773,7 +959,7 @@ int plan_grid(const swense_modes* md, int32_t n_tl, const double* t, const swens
   p->Nxr = Nxr;
   p->Nyr = Nyr;
   p->nslot = size_t(ny) * p->nxh1;
-  p->per_level = size_t(4) * Nyr * p->Mh * sizeof(float2);
+  p->per_level = size_t(4) * Nyr * ((p->Mh + 3) & ~3) * sizeof(float2);
   p->prop_bytes = md->omega ? size_t(n_tl) * 3 * p->nslot * sizeof(float2) : 0;
   p->geta_bytes = ny > 1 ? size_t(Nyr) * p->Mh * sizeof(float2) : 0;
   return SWENSE_OK;
@@ -942,7 +1128,18 @@ int launch_grid(const GridPlan& p, const swense_modes* md, const double* t, floa
       ra.rb = kRowBlock;
       const size_t smem_col = size_t(2) * ny * (kColBlock + 1) * sizeof(float2);
       const size_t smem_row = size_t(4) * Mh * (kRowBlock + 1) * sizeof(float2);
+      ca.ldG = ra.ldG = (Mh + 3) & ~3;
+      const bool pair_t = rowv == 2 && Nyr >= 256 && Nxr >= 256;
       for (int l0 = 0; l0 < nz; l0 += chunk) {
+        if (pair_t) {
+          const int nl = std::min(chunk, nz - l0);
+          ca.lev0 = l0;
+          ca.nlev = nl;
+          ra.lev0 = l0;
+          int st = launch_pair_t(ca, ra, p.lev, nl, stream);
+          if (st) return st;
+          continue;
+        }
         const int nl = std::min(chunk, nz - l0);
         ca.lev0 = l0;
         ca.nlev = nl;
@@ -1019,9 +1216,10 @@ extern "C" int swense_autotune_grid(const swense_modes* md, int32_t n_tl, const 
     SWENSE_CUDA_TRY(cudaEventCreate(&e1));
     float best_ms = 1e30f;
     for (int lpc : {0, 1, 2, 4})
-    for (int rowv : {0, 1}) {
+    for (int rowv : {0, 1, 2}) {
       if (lpc > 0 && !warp_path(p.ny, p.Nxr, p.Nyr)) continue;
-      if (rowv && (lpc == 0 || p.Nxr < 256)) continue;   // only the Stockham row sizes have two kernels
+      if (rowv && (lpc == 0 || p.Nxr < 256)) continue;   // only the Stockham row sizes have variants
+      if (rowv == 2 && p.Nyr < 256) continue;
       for (size_t mb : {16, 32, 64}) {
         const size_t cb = mb << 20;
         const int chunk = int(std::max<size_t>(1, std::min<size_t>(p.nz, cb / p.per_level)));
@@ -1064,7 +1262,7 @@ extern "C" int swense_set_grid_tune(int32_t nx, int32_t ny, int32_t pad_n, int32
     return fail(SWENSE_ERR_ARG, "lpc must be -1 (default), 0, 1, 2 or 4");
   if (chunk_bytes < (int64_t(1) << 20) || chunk_bytes > (int64_t(1) << 30))
     return fail(SWENSE_ERR_ARG, "chunk_bytes must be in [1 MiB, 1 GiB]");
-  if (row_variant != 0 && row_variant != 1) return fail(SWENSE_ERR_ARG, "row_variant must be 0 or 1");
+  if (row_variant < 0 || row_variant > 2) return fail(SWENSE_ERR_ARG, "row_variant must be 0, 1 or 2");
   Tune tn;
   tn.lpc = lpc;
   tn.chunk_bytes = size_t(chunk_bytes);

@@ -10,14 +10,26 @@
 // points arrive in mesh order, so neighbouring threads share most of their stencil lines.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 
 #include "internal.cuh"
 
 namespace swense {
 namespace {
 
+// z lookup: ZLUT equal buckets over [z_0, z_{nz-1}]; lut[b] = largest level index j with
+// z_j <= z_0 + b h. A point starts its search one bucket below its own (so rounding of the
+// bucket index cannot place it past its level) and steps up: one or two steps for any level
+// spacing that is not much finer than h.
+constexpr int ZLUT = 256;
+
+// Level tables, built on the host once per call and passed as a kernel parameter: levels,
+// inverse Lagrange denominators of each 4-level window (inv[j] for nodes j..j+3) and the lookup.
 struct Levels {
   float z[SWENSE_MAX_LEVELS];
+  float4 inv[SWENSE_MAX_LEVELS];
+  unsigned lut4[ZLUT / 4];          // lut bytes, four per word
+  float z0, inv_h;
 };
 
 struct InterpArgs {
@@ -88,47 +100,25 @@ __device__ __forceinline__ void lagrange4(const float zn[4], float4 inv, float z
 
 // Shared-memory copy of the levels and, per stencil start j0, the inverse Lagrange
 // denominators of the levels j0 .. j0+3 (computed once per CTA: no divisions per point).
-// z lookup: ZLUT equal buckets over [z_0, z_{nz-1}]; lut[b] = largest level index j with
-// z_j <= z_0 + b h. A point starts its search one bucket below its own (so rounding of the
-// bucket index cannot place it past its level) and steps up: one or two steps for any level
-// spacing that is not much finer than h.
-constexpr int ZLUT = 256;
-
 struct LevelTables {
   float z[SWENSE_MAX_LEVELS];
   float4 inv[SWENSE_MAX_LEVELS];
-  unsigned char lut[ZLUT];
+  alignas(4) unsigned char lut[ZLUT];
   float z0, inv_h;
 };
 
+// Copy of the level tables in shared memory (per-thread indices would serialise on the
+// parameter bank).
 __device__ __forceinline__ void fill_level_tables(LevelTables& T, const Levels& L, int nz) {
-  const float z0 = L.z[0], h = (L.z[nz - 1] - z0) / float(ZLUT);
   if (threadIdx.x == 0) {
-    T.z0 = z0;
-    T.inv_h = 1.f / h;
+    T.z0 = L.z0;
+    T.inv_h = L.inv_h;
   }
-  for (int b = threadIdx.x; b < ZLUT; b += blockDim.x) {
-    const float zb = z0 + float(b) * h;
-    int lo = 0, hi = nz;
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      if (L.z[mid] <= zb) lo = mid + 1; else hi = mid;
-    }
-    T.lut[b] = (unsigned char)max(lo - 1, 0);
-  }
+  for (int i = threadIdx.x; i < ZLUT / 4; i += blockDim.x) reinterpret_cast<unsigned*>(T.lut)[i] = L.lut4[i];
   for (int i = threadIdx.x; i < nz; i += blockDim.x) T.z[i] = L.z[i];
-  for (int j = threadIdx.x; j <= nz - 4; j += blockDim.x) {
-    float zn[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) zn[q] = L.z[j + q];
-    T.inv[j] = make_float4(1.f / ((zn[0] - zn[1]) * (zn[0] - zn[2]) * (zn[0] - zn[3])),
-                           1.f / ((zn[1] - zn[0]) * (zn[1] - zn[2]) * (zn[1] - zn[3])),
-                           1.f / ((zn[2] - zn[0]) * (zn[2] - zn[1]) * (zn[2] - zn[3])),
-                           1.f / ((zn[3] - zn[0]) * (zn[3] - zn[1]) * (zn[3] - zn[2])));
-  }
+  for (int j = threadIdx.x; j <= nz - 4; j += blockDim.x) T.inv[j] = L.inv[j];
 }
 
-// Stencil of one point: cell indices, Lagrange weights and the in-range flag.
 struct PointCell {
   int ix, iy, j0;       // first stencil node in x, y (before the -1 shift) and first level
   float wx[4], wy[4], wz[4];
@@ -248,9 +238,13 @@ __device__ __forceinline__ void store_point(const InterpArgs& a, int64_t i, floa
 constexpr int BOX_THREADS = 256;
 constexpr int BOX_PPT = 4;                         // points per thread
 constexpr int BOX_PTS = BOX_THREADS * BOX_PPT;
-constexpr int BOX_NODES = 3584;                    // float4 nodes (56 KB)
-constexpr int BOX_COLS = 1536;                     // eta columns (6 KB)
+constexpr int BOX_NODES = 4096;                    // float4 nodes (64 KB; 99 % of the 1024-point mesh chunks fit)
+constexpr int BOX_COLS = BOX_NODES / 4;             // eta columns (a box has at least 4 levels)
 constexpr size_t BOX_SMEM = size_t(BOX_NODES) * sizeof(float4) + size_t(BOX_COLS) * sizeof(float);
+
+// Level-plane stride of the box (unpadded: padding it to separate z-neighbours' bank groups
+// removed only 6 % of the wavefronts and made more chunks miss the tile).
+__host__ __device__ __forceinline__ int box_zstride(int sbx, int by) { return by * sbx; }
 
 __device__ __forceinline__ int wrap_rel(int i, int ref, int n) {
   // i - ref folded into [-n/2, n/2)
@@ -333,7 +327,8 @@ __global__ void __launch_bounds__(BOX_THREADS) k_interp_plan(InterpArgs a, Level
   const int sbx = bx + ((4 - bx) & 7);
   const int by = a.Nyr > 1 ? mx[1] - mn[1] + 4 : 1;
   const int bz = mx[2] - mn[2] + 4;
-  const bool fits = int64_t(sbx) * by * bz <= BOX_NODES && int64_t(sbx) * by <= BOX_COLS &&
+  const int zst = box_zstride(sbx, by);
+  const bool fits = int64_t(zst) * bz <= BOX_NODES && int64_t(sbx) * by <= BOX_COLS &&
                     bx <= a.Nxr && by <= a.Nyr;
   plan[blockIdx.x] = make_int4((refx + mn[0] - 1) & (a.Nxr - 1),
                                a.Nyr > 1 ? ((refy + mn[1] - 1) & (a.Nyr - 1)) : 0, mn[2],
@@ -377,8 +372,9 @@ __global__ void __launch_bounds__(BOX_THREADS, 3) k_interp_box(InterpArgs a, Lev
   }
   const int bx = pl.w & 2047, by = (pl.w >> 11) & 2047, bz = pl.w >> 22;
   // shared-memory row stride = 4 (mod 8) float4: reads of neighbouring cells (dx, dy in {0, 1})
-  // by one quarter-warp then fall into different bank groups
+  // by one quarter-warp fall into different bank groups
   const int sbx = bx + ((4 - bx) & 7);
+  const int zst = box_zstride(sbx, by);
   const size_t plane = size_t(a.Nyr) * a.Nxr;
   const int x0 = pl.x, y0 = pl.y, l0 = pl.z;
   {
@@ -408,8 +404,8 @@ __global__ void __launch_bounds__(BOX_THREADS, 3) k_interp_box(InterpArgs a, Lev
           v1.z = fmaf(w, g1.z, v1.z);
           v1.w = fmaf(w, g1.w, v1.w);
         }
-        sbox[r0 * sbx + lx] = v0;
-        sbox[r1 * sbx + lx] = v1;                  // same value when r1 repeats a row
+        sbox[lz0 * zst + ly0 * sbx + lx] = v0;
+        sbox[lz1 * zst + ly1 * sbx + lx] = v1;     // same value when r1 repeats a row
       }
     }
     for (int ly = warp; ly < by; ly += BOX_THREADS / 32) {
@@ -423,7 +419,7 @@ __global__ void __launch_bounds__(BOX_THREADS, 3) k_interp_box(InterpArgs a, Lev
     }
   }
   __syncthreads();
-  const int zstride = by * sbx;
+  const int zstride = zst;
   const int nys = a.Nyr > 1 ? 4 : 1;
 #pragma unroll 1
   for (int k = 0; k < BOX_PPT; ++k) {
@@ -441,7 +437,7 @@ __global__ void __launch_bounds__(BOX_THREADS, 3) k_interp_box(InterpArgs a, Lev
     const int lx = min(max((c.ix - 1 - x0) & (a.Nxr - 1), 0), bx - 4);
     const int ly = a.Nyr > 1 ? min(max((c.iy - 1 - y0) & (a.Nyr - 1), 0), by - 4) : 0;
     const int lz = min(max(c.j0 - l0, 0), bz - 4);
-    const float4* base = sbox + (lz * by + ly) * sbx + lx;
+    const float4* base = sbox + lz * zst + ly * sbx + lx;
     unsigned long long uv = pack2(0.f, 0.f), wt = pack2(0.f, 0.f);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -619,6 +615,30 @@ int prepare_interp(const swense_grid* g, double t, const float* pts, int64_t np,
     lev->z[l] = g->z_levels[l];
     if (!std::isfinite(lev->z[l]) || (l > 0 && !(lev->z[l] > lev->z[l - 1])))
       return fail(SWENSE_ERR_LEVELS, "z_levels must be finite and strictly increasing");
+  }
+  {
+    const int nz = g->nz;
+    for (int j = 0; j + 3 < nz; ++j) {
+      double zn[4], d[4];
+      for (int q = 0; q < 4; ++q) zn[q] = lev->z[j + q];
+      for (int q = 0; q < 4; ++q) {
+        d[q] = 1.0;
+        for (int r = 0; r < 4; ++r)
+          if (r != q) d[q] *= zn[q] - zn[r];
+      }
+      lev->inv[j] = make_float4(float(1.0 / d[0]), float(1.0 / d[1]), float(1.0 / d[2]), float(1.0 / d[3]));
+    }
+    const double z0 = lev->z[0], h = (double(lev->z[nz - 1]) - z0) / ZLUT;
+    lev->z0 = lev->z[0];
+    lev->inv_h = float(1.0 / h);
+    unsigned char lut[ZLUT];
+    int j = 0;
+    for (int b = 0; b < ZLUT; ++b) {
+      const double zb = z0 + b * h;
+      while (j + 1 < nz && double(lev->z[j + 1]) <= zb) ++j;
+      lut[b] = (unsigned char)j;
+    }
+    std::memcpy(lev->lut4, lut, sizeof(lut));
   }
   for (int l = 0; l < g->n_tl; ++l) {
     if (!std::isfinite(g->t_levels[l]) || (l > 0 && !(g->t_levels[l] > g->t_levels[l - 1])))

@@ -116,13 +116,24 @@ def test_calm_water_grid_is_zero(api):
     assert float(g.nodes.abs().max()) == 0.0 and float(g.eta.abs().max()) == 0.0
 
 
-@pytest.mark.parametrize("lpc,rowv,chunk_mb", [(0, 0, 32), (1, 0, 1), (2, 1, 32), (4, 1, 1), (2, 0, 64)])
+@pytest.mark.parametrize("lpc,rowv,chunk_mb", [(0, 0, 32), (1, 0, 1), (2, 1, 32), (4, 1, 1), (2, 0, 64), (1, 2, 1)])
 @pytest.mark.parametrize("shape", [(256, 64, 1), (128, 128, 2), (512, 32, 1), (512, 32, 2)])
 def test_every_launch_shape_matches_oracle(api, lpc, rowv, chunk_mb, shape):
     """Each transform path the autotuner can choose (shared-memory kernels; 1, 2 or 4 levels per
     column block; both or one field pair per row block; level chunks from one level up), forced
     with swense_set_grid_tune, against the oracle: 256-, 512- and 1024-point rows, 64- to
     256-point columns, several level chunks."""
+    _forced(api, lpc, rowv, chunk_mb, shape)
+
+
+@pytest.mark.parametrize("lpc,chunk_mb", [(1, 1), (4, 32)])
+@pytest.mark.parametrize("shape", [(256, 256, 1), (512, 128, 2), (128, 512, 2), (256, 512, 1)])
+def test_transposed_pair_matches_oracle(api, lpc, chunk_mb, shape):
+    """Row variant 2 (transposed intermediate) for 256-, 512- and 1024-point columns and rows."""
+    _forced(api, lpc, 2, chunk_mb, shape)
+
+
+def _forced(api, lpc, rowv, chunk_mb, shape):
     from paper_2005_12716_gb300 import _swense as S
     nx, ny, pad = shape
     rng = np.random.default_rng(nx + ny + pad)
