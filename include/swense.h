@@ -155,7 +155,7 @@ int swense_fields_on_grid_noalloc(const swense_modes* modes, int32_t n_tl, const
 /*
  * swense_autotune_grid — choose the launch shape of swense_fields_on_grid for this grid shape
  * (the transform path: warp-register kernels with 1, 2 or 4 levels per column-transform block,
- * or the shared-memory kernels; the L2-resident level-chunk size among 16, 32, 64 MB; and, for
+ * or the shared-memory kernels; the level-chunk size among 16, 32, 64, 96, 128 MB; and, for
  * 256- to 1024-point rows, whether one row-transform block handles both field pairs or one) by
  * timing each candidate three times on `stream`; the choice is cached per (nx, ny, pad_n, nz)
  * and used by later calls. No counterpart in the paper. Writes the grid (same outputs as
@@ -174,7 +174,8 @@ int swense_autotune_grid(const swense_modes* modes, int32_t n_tl, const double* 
 /*
  * swense_set_grid_tune — set the launch shape that swense_fields_on_grid uses for grids of shape
  * (nx, ny, pad_n, nz), e.g. a choice that swense_autotune_grid returned in an earlier process.
- * lpc: -1 (default for the shape), 0 (shared-memory path), 1, 2 or 4 levels per column block;
+ * lpc: -1 (forget any choice: untuned defaults again), 0 (shared-memory path), 1, 2 or 4 levels
+ * per column block;
  * chunk_bytes in [1 MiB, 1 GiB] (L2-resident level chunk); row_variant 0, 1 or 2 (as returned
  * by swense_autotune_grid). Results do not depend on the choice beyond FP32 rounding. No
  * counterpart in the paper. Errors: SWENSE_ERR_ARG for values outside those sets.

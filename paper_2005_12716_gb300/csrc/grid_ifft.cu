@@ -238,7 +238,7 @@ __global__ void k_propagate(const float2* __restrict__ Ae, const float2* __restr
 
 constexpr int kThreads = 256;
 constexpr size_t kSmemBudget = 64 * 1024;
-constexpr size_t kChunkBytes = size_t(32) << 20;
+constexpr size_t kChunkBytes = size_t(64) << 20;
 constexpr int kColBlock = 8;    // kx columns per column-transform CTA
 constexpr int kColLevels = 2;   // levels per column-transform CTA
 constexpr int kRowBlock = 8;    // grid rows per row-transform CTA (one per warp)
@@ -1196,9 +1196,12 @@ extern "C" int swense_fields_on_grid(const swense_modes* md, int32_t n_tl, const
     st = workspace(ws_bytes, stream, &ws);
     if (st) return st;
   }
-  // untuned default: the warp path where its transforms stay in registers (n <= 512)
-  const int lpc = tn.lpc >= 0 ? tn.lpc : ((p.Nxr <= 512 && p.Nyr <= 512) ? kColLevels : 0);
-  return launch_grid(p, md, t, nodes, eta, ws, chunk, stream, lpc, tn.rowv);
+  // untuned default: the transposed Stockham pair where both lengths are 256..1024, else the
+  // warp path where its transforms stay in registers (n <= 512), else the shared-memory path
+  const bool pair = p.ny > 1 && p.Nxr >= 256 && p.Nxr <= 1024 && p.Nyr >= 256 && p.Nyr <= 1024;
+  const int lpc = tn.lpc >= 0 ? tn.lpc : (pair ? 4 : ((p.Nxr <= 512 && p.Nyr <= 512) ? kColLevels : 0));
+  const int rowv = tn.lpc >= 0 ? tn.rowv : (pair ? 2 : 0);
+  return launch_grid(p, md, t, nodes, eta, ws, chunk, stream, lpc, rowv);
 }
 
 extern "C" int swense_autotune_grid(const swense_modes* md, int32_t n_tl, const double* t,
@@ -1220,7 +1223,7 @@ extern "C" int swense_autotune_grid(const swense_modes* md, int32_t n_tl, const 
       if (lpc > 0 && !warp_path(p.ny, p.Nxr, p.Nyr)) continue;
       if (rowv && (lpc == 0 || p.Nxr < 256)) continue;   // only the Stockham row sizes have variants
       if (rowv == 2 && p.Nyr < 256) continue;
-      for (size_t mb : {16, 32, 64}) {
+      for (size_t mb : {16, 32, 64, 96, 128}) {
         const size_t cb = mb << 20;
         const int chunk = int(std::max<size_t>(1, std::min<size_t>(p.nz, cb / p.per_level)));
         void* ws = nullptr;
@@ -1263,11 +1266,15 @@ extern "C" int swense_set_grid_tune(int32_t nx, int32_t ny, int32_t pad_n, int32
   if (chunk_bytes < (int64_t(1) << 20) || chunk_bytes > (int64_t(1) << 30))
     return fail(SWENSE_ERR_ARG, "chunk_bytes must be in [1 MiB, 1 GiB]");
   if (row_variant < 0 || row_variant > 2) return fail(SWENSE_ERR_ARG, "row_variant must be 0, 1 or 2");
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  if (lpc == -1) {                      // back to the untuned defaults for this shape
+    g_tune.erase({nx, ny, pad_n, nz});
+    return SWENSE_OK;
+  }
   Tune tn;
   tn.lpc = lpc;
   tn.chunk_bytes = size_t(chunk_bytes);
   tn.rowv = row_variant;
-  std::lock_guard<std::mutex> lock(g_tune_mutex);
   g_tune[{nx, ny, pad_n, nz}] = tn;
   return SWENSE_OK;
 }
