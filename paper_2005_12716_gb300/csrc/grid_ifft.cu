@@ -750,6 +750,44 @@ __global__ void __launch_bounds__(256, N >= 1024 ? 1 : 2) k_row_t(RowArgs a) {
     __stcs(&out[lane + 32 * (e / RL) + (e % RL) * (N / RL)], make_float4(z1[e].x, z1[e].y, z2[e].x, z2[e].y));
 }
 
+// Same row pass with one transform per warp (warps 2r and 2r+1 of a block take Z1 and Z2 of
+// row r): half the registers, so more warps per SM; each warp writes one float2 half of the
+// nodes' float4 (the halves meet in L2).
+template <int N>
+__global__ void __launch_bounds__(256, N >= 1024 ? 2 : 3) k_row_t2(RowArgs a) {
+  extern __shared__ float2 sm[];                 // warp exchange buffers
+  constexpr int E = N / 32, RL = stk_radix(N, stk_npass(N) - 1);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int y = blockIdx.x * (kThreads / 64) + (warp >> 1);
+  const int q = warp & 1;                        // 0: Z1 = U + iV, 1: Z2 = W + iT
+  const int level = blockIdx.y;
+  if (y >= a.Nyr) return;                        // no block-wide barrier in this kernel
+  float2 T[stk_twn(N)];
+  stk_init<N>(T, a.tw, lane);
+  float2* wbuf = sm + warp * stk_buf(N);
+  const size_t fs = size_t(a.Nyr) * a.ldG;
+  const float2* row = a.G + (size_t(level) * 4 + 2 * q) * fs + size_t(y) * a.ldG;
+  float2 z[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int p = lane + 32 * (e / 8) + (e % 8) * (N / 8);
+    const bool lo = p < a.Mh, hi = p > N - a.Mh;
+    float2 A = make_float2(0.f, 0.f), B = A;
+    if (lo || hi) {
+      const int mm = lo ? p : N - p;
+      A = __ldcg(&row[mm]);
+      B = __ldcg(&row[fs + mm]);
+    }
+    if (p == 0) z[e] = make_float2(A.x, B.x);
+    else if (!hi) z[e] = make_float2(A.x - B.y, A.y + B.x);
+    else z[e] = make_float2(A.x + B.y, B.x - A.y);
+  }
+  stk_fft<N>(z, T, a.tw, wbuf, lane);
+  float2* out = reinterpret_cast<float2*>(a.nodes + (size_t(a.lev0 + level) * a.Nyr + y) * N) + q;
+#pragma unroll
+  for (int e = 0; e < E; ++e) __stcs(&out[2 * (lane + 32 * (e / RL) + (e % RL) * (N / RL))], z[e]);
+}
+
 // Launch-shape choices of the warp-register path, per grid shape (set by swense_autotune_grid;
 // defaults otherwise).
 struct Tune {
@@ -830,10 +868,24 @@ int launch_row_t(const RowArgs& r, dim3 grid, cudaStream_t stream) {
   return SWENSE_OK;
 }
 
-// Transposed-intermediate pair (row variant 2): both transform lengths in 256..1024.
-int launch_pair_t(const ColArgs& c, const RowArgs& r, const Levels& L, int nl, cudaStream_t s) {
+template <int N>
+int launch_row_t2(const RowArgs& r, dim3 grid, cudaStream_t stream) {
+  const size_t smem = size_t(8) * stk_buf(N) * sizeof(float2);
+  int st = set_smem((const void*)k_row_t2<N>, smem);
+  if (st) return st;
+  k_row_t2<N><<<grid, kThreads, smem, stream>>>(r);
+  SWENSE_CUDA_TRY(cudaGetLastError());
+  count_launches(1);
+  return SWENSE_OK;
+}
+
+// Transposed-intermediate pair (row variants 2 and 3): both transform lengths in 256..1024;
+// variant 3 runs one transform per warp in the row pass.
+int launch_pair_t(const ColArgs& c, const RowArgs& r, const Levels& L, int nl, cudaStream_t s,
+                  bool one_per_warp) {
   const dim3 gc(unsigned((c.Mh + kColBlock - 1) / kColBlock), unsigned((nl + c.lpc - 1) / c.lpc));
   const dim3 gr(unsigned((r.Nyr + 7) / 8), unsigned(nl));
+  const dim3 gr2(unsigned((r.Nyr + 3) / 4), unsigned(nl));
   int st;
   switch (c.Nyr) {
     case 256: st = launch_col_t<256, 2>(c, L, gc, s); break;
@@ -842,6 +894,14 @@ int launch_pair_t(const ColArgs& c, const RowArgs& r, const Levels& L, int nl, c
     default: return fail(SWENSE_ERR_UNSUPPORTED, "transposed pair: column length");
   }
   if (st) return st;
+  if (one_per_warp) {
+    switch (r.Nxr) {
+      case 256: return launch_row_t2<256>(r, gr2, s);
+      case 512: return launch_row_t2<512>(r, gr2, s);
+      case 1024: return launch_row_t2<1024>(r, gr2, s);
+      default: return fail(SWENSE_ERR_UNSUPPORTED, "transposed pair: row length");
+    }
+  }
   switch (r.Nxr) {
     case 256: return launch_row_t<256>(r, gr, s);
     case 512: return launch_row_t<512>(r, gr, s);
@@ -1129,14 +1189,14 @@ int launch_grid(const GridPlan& p, const swense_modes* md, const double* t, floa
       const size_t smem_col = size_t(2) * ny * (kColBlock + 1) * sizeof(float2);
       const size_t smem_row = size_t(4) * Mh * (kRowBlock + 1) * sizeof(float2);
       ca.ldG = ra.ldG = (Mh + 3) & ~3;
-      const bool pair_t = rowv == 2 && Nyr >= 256 && Nxr >= 256;
+      const bool pair_t = (rowv == 2 || rowv == 3) && Nyr >= 256 && Nxr >= 256;
       for (int l0 = 0; l0 < nz; l0 += chunk) {
         if (pair_t) {
           const int nl = std::min(chunk, nz - l0);
           ca.lev0 = l0;
           ca.nlev = nl;
           ra.lev0 = l0;
-          int st = launch_pair_t(ca, ra, p.lev, nl, stream);
+          int st = launch_pair_t(ca, ra, p.lev, nl, stream, rowv == 3);
           if (st) return st;
           continue;
         }
@@ -1219,10 +1279,10 @@ extern "C" int swense_autotune_grid(const swense_modes* md, int32_t n_tl, const 
     SWENSE_CUDA_TRY(cudaEventCreate(&e1));
     float best_ms = 1e30f;
     for (int lpc : {0, 1, 2, 4})
-    for (int rowv : {0, 1, 2}) {
+    for (int rowv : {0, 1, 2, 3}) {
       if (lpc > 0 && !warp_path(p.ny, p.Nxr, p.Nyr)) continue;
       if (rowv && (lpc == 0 || p.Nxr < 256)) continue;   // only the Stockham row sizes have variants
-      if (rowv == 2 && p.Nyr < 256) continue;
+      if (rowv >= 2 && p.Nyr < 256) continue;
       for (size_t mb : {16, 32, 64, 96, 128}) {
         const size_t cb = mb << 20;
         const int chunk = int(std::max<size_t>(1, std::min<size_t>(p.nz, cb / p.per_level)));
@@ -1265,7 +1325,7 @@ extern "C" int swense_set_grid_tune(int32_t nx, int32_t ny, int32_t pad_n, int32
     return fail(SWENSE_ERR_ARG, "lpc must be -1 (default), 0, 1, 2 or 4");
   if (chunk_bytes < (int64_t(1) << 20) || chunk_bytes > (int64_t(1) << 30))
     return fail(SWENSE_ERR_ARG, "chunk_bytes must be in [1 MiB, 1 GiB]");
-  if (row_variant < 0 || row_variant > 2) return fail(SWENSE_ERR_ARG, "row_variant must be 0, 1 or 2");
+  if (row_variant < 0 || row_variant > 3) return fail(SWENSE_ERR_ARG, "row_variant must be 0, 1, 2 or 3");
   std::lock_guard<std::mutex> lock(g_tune_mutex);
   if (lpc == -1) {                      // back to the untuned defaults for this shape
     g_tune.erase({nx, ny, pad_n, nz});

@@ -13,6 +13,7 @@
 #include <cstring>
 
 #include "internal.cuh"
+#include "mlp.cuh"
 
 namespace swense {
 namespace {
@@ -261,6 +262,52 @@ __device__ __forceinline__ void fma2(unsigned long long& acc, unsigned long long
 __device__ __forceinline__ float lo2(unsigned long long v) { return __uint_as_float(unsigned(v)); }
 __device__ __forceinline__ float hi2(unsigned long long v) { return __uint_as_float(unsigned(v >> 32)); }
 
+// Time-blended box of grid nodes x0..x0+bx-1, y0..y0+by-1 (wrapped), levels l0..l0+bz-1 into
+// shared memory (row stride sbx, level-plane stride zst float4), and the eta rows (stride sbx).
+// Rows (ly, lz) over warps, two rows per warp at a time (more loads in flight), x over lanes;
+// the time blend happens here, once per node.
+__device__ __forceinline__ void stage_box(const InterpArgs& a, int x0, int y0, int l0, int bx, int by,
+                                          int bz, int sbx, int zst, float4* sbox, float* seta) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const size_t plane = size_t(a.Nyr) * a.Nxr;
+  const size_t tl_stride = size_t(a.nz) * plane;
+  const int nrows = by * bz;
+  for (int r0 = warp; r0 < nrows; r0 += 2 * nw) {
+    const int r1 = min(r0 + nw, nrows - 1);       // a duplicate of r0's last row when past the end
+    const int lz0 = r0 / by, ly0 = r0 - lz0 * by, lz1 = r1 / by, ly1 = r1 - lz1 * by;
+    const float4* src0 = a.nodes + size_t(l0 + lz0) * plane + size_t((y0 + ly0) & (a.Nyr - 1)) * a.Nxr;
+    const float4* src1 = a.nodes + size_t(l0 + lz1) * plane + size_t((y0 + ly1) & (a.Nyr - 1)) * a.Nxr;
+    for (int lx = lane; lx < bx; lx += 32) {
+      const int gx = (x0 + lx) & (a.Nxr - 1);
+      float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
+      for (int tl = 0; tl < a.n_tl; ++tl) {
+        const float4 g0 = __ldg(&src0[size_t(tl) * tl_stride + gx]);
+        const float4 g1 = __ldg(&src1[size_t(tl) * tl_stride + gx]);
+        const float w = a.wt[tl];
+        v0.x = fmaf(w, g0.x, v0.x);
+        v0.y = fmaf(w, g0.y, v0.y);
+        v0.z = fmaf(w, g0.z, v0.z);
+        v0.w = fmaf(w, g0.w, v0.w);
+        v1.x = fmaf(w, g1.x, v1.x);
+        v1.y = fmaf(w, g1.y, v1.y);
+        v1.z = fmaf(w, g1.z, v1.z);
+        v1.w = fmaf(w, g1.w, v1.w);
+      }
+      sbox[lz0 * zst + ly0 * sbx + lx] = v0;
+      sbox[lz1 * zst + ly1 * sbx + lx] = v1;       // same value when r1 repeats a row
+    }
+  }
+  for (int ly = warp; ly < by; ly += nw) {
+    const float* src = a.eta + size_t((y0 + ly) & (a.Nyr - 1)) * a.Nxr;
+    for (int lx = lane; lx < bx; lx += 32) {
+      const int gx = (x0 + lx) & (a.Nxr - 1);
+      float v = 0.f;
+      for (int tl = 0; tl < a.n_tl; ++tl) v = fmaf(a.wt[tl], __ldg(&src[size_t(tl) * plane + gx]), v);
+      seta[ly * sbx + lx] = v;
+    }
+  }
+}
+
 // Box plan of one 1024-point chunk: box origin (grid node indices, wrapped) and extents, or
 // dims = -1 when the box does not fit the shared-memory tile (the chunk then gathers from
 // global memory). Computed by its own kernel so the gather kernel can start its box load at
@@ -354,7 +401,6 @@ __global__ void __launch_bounds__(BOX_THREADS, 3) k_interp_box(InterpArgs a, Lev
       nz_ = __ldg(&a.pts[3 * i + 2]);
     }
   }
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (pl.w < 0) {
     __syncthreads();
 #pragma unroll 1
@@ -375,49 +421,8 @@ __global__ void __launch_bounds__(BOX_THREADS, 3) k_interp_box(InterpArgs a, Lev
   // by one quarter-warp fall into different bank groups
   const int sbx = bx + ((4 - bx) & 7);
   const int zst = box_zstride(sbx, by);
-  const size_t plane = size_t(a.Nyr) * a.Nxr;
   const int x0 = pl.x, y0 = pl.y, l0 = pl.z;
-  {
-    // rows (ly, lz) over warps, two rows per warp at a time (more loads in flight), x over
-    // lanes; the time blend happens here, once per node
-    const size_t tl_stride = size_t(a.nz) * plane;
-    constexpr int NW = BOX_THREADS / 32;
-    const int nrows = by * bz;
-    for (int r0 = warp; r0 < nrows; r0 += 2 * NW) {
-      const int r1 = min(r0 + NW, nrows - 1);     // a duplicate of r0's last row when past the end
-      const int lz0 = r0 / by, ly0 = r0 - lz0 * by, lz1 = r1 / by, ly1 = r1 - lz1 * by;
-      const float4* src0 = a.nodes + size_t(l0 + lz0) * plane + size_t((y0 + ly0) & (a.Nyr - 1)) * a.Nxr;
-      const float4* src1 = a.nodes + size_t(l0 + lz1) * plane + size_t((y0 + ly1) & (a.Nyr - 1)) * a.Nxr;
-      for (int lx = lane; lx < bx; lx += 32) {
-        const int gx = (x0 + lx) & (a.Nxr - 1);
-        float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
-        for (int tl = 0; tl < a.n_tl; ++tl) {
-          const float4 g0 = __ldg(&src0[size_t(tl) * tl_stride + gx]);
-          const float4 g1 = __ldg(&src1[size_t(tl) * tl_stride + gx]);
-          const float w = a.wt[tl];
-          v0.x = fmaf(w, g0.x, v0.x);
-          v0.y = fmaf(w, g0.y, v0.y);
-          v0.z = fmaf(w, g0.z, v0.z);
-          v0.w = fmaf(w, g0.w, v0.w);
-          v1.x = fmaf(w, g1.x, v1.x);
-          v1.y = fmaf(w, g1.y, v1.y);
-          v1.z = fmaf(w, g1.z, v1.z);
-          v1.w = fmaf(w, g1.w, v1.w);
-        }
-        sbox[lz0 * zst + ly0 * sbx + lx] = v0;
-        sbox[lz1 * zst + ly1 * sbx + lx] = v1;     // same value when r1 repeats a row
-      }
-    }
-    for (int ly = warp; ly < by; ly += BOX_THREADS / 32) {
-      const float* src = a.eta + size_t((y0 + ly) & (a.Nyr - 1)) * a.Nxr;
-      for (int lx = lane; lx < bx; lx += 32) {
-        const int gx = (x0 + lx) & (a.Nxr - 1);
-        float v = 0.f;
-        for (int tl = 0; tl < a.n_tl; ++tl) v = fmaf(a.wt[tl], __ldg(&src[size_t(tl) * plane + gx]), v);
-        seta[ly * sbx + lx] = v;
-      }
-    }
-  }
+  stage_box(a, x0, y0, l0, bx, by, bz, sbx, zst, sbox, seta);
   __syncthreads();
   const int zstride = zst;
   const int nys = a.Nyr > 1 ? 4 : 1;
@@ -465,6 +470,245 @@ __global__ void __launch_bounds__(BOX_THREADS, 3) k_interp_box(InterpArgs a, Lev
       for (int kx = 0; kx < 4; ++kx) acc_eta = fmaf(c.wy[b] * c.wx[kx], ebase[b * sbx + kx], acc_eta);
     }
     store_point(a, i, make_float4(lo2(uv), hi2(uv), lo2(wt), hi2(wt)), acc_eta, pz, c.inside);
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Fused learned gather: the plain Lagrange gather, the network's inputs and its three layers in
+// one kernel, per 1024-point chunk. The chunk's stencils come from the staged box (as in
+// k_interp_box) when it fits, else from per-point stencil arrays gathered from global memory
+// (64 points at a time) in the same shared memory. Per sub-batch of points:
+//   A (one thread per point): cell, Lagrange weights, offsets, eta, stencil base -> LPoint;
+//   B (warps, m16n8k16): rows (point, field), 16 rows = 4 points x 4 fields per tile; each lane
+//     reads its fragment's stencil values, the quad reduces the row's Lagrange value and
+//     max |value|, the normalised values (hi + lo BF16) feed layers 1-3, and the lane holding
+//     column f of row (point, f) writes lagrange + s_f * out_scale * y[f];
+//   C (one thread per point): Bernoulli, NaN outside the levels, stores.
+struct LPoint {
+  int base;                 // staged node index of stencil node (x 0, y 0, level 0)
+  float w[12];              // wx[4], wy[4], wz[4]; the corrected fields overwrite w[0..3]
+  float off[3];             // dx, dy in the cell; dz in the stencil's middle level interval
+  float eta, z;
+  int inside, pad_;
+};
+static_assert(sizeof(LPoint) == 80, "LPoint layout");
+
+using mlpnet::PackedFwd;
+
+constexpr int LRN_SB = 128;                            // points per sub-batch (box mode)
+constexpr int LRN_SB_PP = 64;                          // points per sub-batch (per-point stencils)
+static_assert(LRN_SB_PP * 64 <= BOX_NODES, "per-point stencils fit the box area");
+constexpr size_t LRN_SMEM = size_t(BOX_NODES) * sizeof(float4) + size_t(BOX_COLS) * sizeof(float) +
+                            size_t(LRN_SB) * sizeof(LPoint) + sizeof(PackedFwd);
+
+// Phase B for `ntile` 16-row tiles of this warp. Node (x k, y b, level q) of point j is
+// nodes[rec[j].base + q * SZ + b * SY + k].
+__device__ __forceinline__ void learned_tiles(const float4* nodes, int SY, int SZ, LPoint* rec,
+                                              const PackedFwd& W, int tile0, int ntile, int npts) {
+  using namespace mlpnet;
+  const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
+  const int f = g & 3;                                 // field of rows g and g + 8
+  const float* nf = reinterpret_cast<const float*>(nodes) + f;
+  for (int t = tile0; t < tile0 + ntile; ++t) {
+    const int j0 = 4 * t + (g >> 2), j1 = j0 + 2;      // points of rows g and g + 8
+    if (4 * t >= npts) break;                          // uniform over the warp
+    float lag[2], sc[2];
+    unsigned xh[5][4], xl[5][4];
+    float v[2][4][4];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const LPoint& P = rec[min(h ? j1 : j0, npts - 1)];
+      const int base = P.base;
+      float lg = 0.f, mx = 0.f;
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int b = (q >> 1) + 2 * (e >> 1), k = 2 * (q & 1) + (e & 1);
+          const float val = nf[4 * (base + kk * SZ + b * SY + k)];
+          v[h][kk][e] = val;
+          lg = fmaf(P.w[8 + kk] * P.w[4 + b] * P.w[k], val, lg);
+          mx = fmaxf(mx, fabsf(val));
+        }
+      }
+      lg += __shfl_xor_sync(0xffffffffu, lg, 1);
+      lg += __shfl_xor_sync(0xffffffffu, lg, 2);
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+      lag[h] = lg;
+      sc[h] = mx + 1e-30f;
+    }
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const float inv = 1.f / sc[h];
+        bf2_split(v[h][kk][0] * inv, v[h][kk][1] * inv, xh[kk][h], xl[kk][h]);
+        bf2_split(v[h][kk][2] * inv, v[h][kk][3] * inv, xh[kk][2 + h], xl[kk][2 + h]);
+      }
+    }
+    // inputs 64..79: dx, dy, dz, then zeros (columns 2q, 2q+1 of the fifth k-tile)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const LPoint& P = rec[min(h ? j1 : j0, npts - 1)];
+      const float o0 = q == 0 ? P.off[0] : (q == 1 ? P.off[2] : 0.f);
+      const float o1 = q == 0 ? P.off[1] : 0.f;
+      bf2_split(o0, o1, xh[4][h], xl[4][h]);
+      xh[4][2 + h] = xl[4][2 + h] = 0u;
+    }
+    float z1[8][4];
+    layer<5, 8, true>(z1, xh, xl, &W.w1[0][0], KIN, W.b1, lane);
+    unsigned h1h[4][4], h1l[4][4];
+    to_a<8, true>(z1, h1h, h1l);
+    float z2[8][4];
+    layer<4, 8, true>(z2, h1h, h1l, &W.w2[0][0], NH, W.b2, lane);
+    unsigned h2h[4][4], h2l[4][4];
+    to_a<8, true>(z2, h2h, h2l);
+    float o[1][4];
+    layer<4, 1, true>(o, h2h, h2l, &W.w3[0][0], NH, W.b3, lane);
+    __syncwarp();                                      // every lane has read its records
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int jh = h ? j1 : j0;
+      if ((f >> 1) == q && jh < npts) rec[jh].w[f] = fmaf(sc[h] * W.out_scale, o[0][2 * h + (f & 1)], lag[h]);
+    }
+    __syncwarp();
+  }
+}
+
+__global__ void __launch_bounds__(BOX_THREADS, 2) k_interp_learned(InterpArgs a, Levels L,
+                                                                    const int4* __restrict__ plan,
+                                                                    const PackedFwd* __restrict__ Wg) {
+  extern __shared__ float4 sbox[];
+  float* seta = reinterpret_cast<float*>(sbox + BOX_NODES);
+  LPoint* rec = reinterpret_cast<LPoint*>(seta + BOX_COLS);
+  PackedFwd& W = *reinterpret_cast<PackedFwd*>(rec + LRN_SB);
+  __shared__ LevelTables zs;
+  fill_level_tables(zs, L, a.nz);
+  {
+    const int4* src = reinterpret_cast<const int4*>(Wg);
+    int4* dst = reinterpret_cast<int4*>(&W);
+    for (int i = threadIdx.x; i < int(sizeof(PackedFwd) / 16); i += blockDim.x) dst[i] = __ldg(&src[i]);
+  }
+  const int64_t p0 = int64_t(blockIdx.x) * BOX_PTS;
+  const int4 pl = plan[blockIdx.x];
+  const bool boxed = pl.w >= 0;
+  const int bx = pl.w & 2047, by = (pl.w >> 11) & 2047, bz = pl.w >> 22;
+  const int sbx = bx + ((4 - bx) & 7);
+  const int zst = box_zstride(sbx, by);
+  const int x0 = pl.x, y0 = pl.y, l0 = pl.z;
+  const size_t plane = size_t(a.Nyr) * a.Nxr;
+  if (boxed) stage_box(a, x0, y0, l0, bx, by, bz, sbx, zst, sbox, seta);
+  __syncthreads();
+  const int SB = boxed ? LRN_SB : LRN_SB_PP;
+  const int warp = threadIdx.x >> 5;
+  for (int s0 = 0; s0 < BOX_PTS; s0 += SB) {
+    const int npts = int(a.np - (p0 + s0) < int64_t(SB) ? a.np - (p0 + s0) : int64_t(SB));
+    if (npts <= 0) break;                              // uniform over the block
+    // ---- A
+    if (boxed) {
+      const int t = threadIdx.x;
+      if (t < npts) {
+        const int64_t i = p0 + s0 + t;
+        const float px = __ldg(&a.pts[3 * i]), py = __ldg(&a.pts[3 * i + 1]), pz = __ldg(&a.pts[3 * i + 2]);
+        const PointCell c = point_cell(a, zs, px, py, pz);
+        const int lx = min(max((c.ix - 1 - x0) & (a.Nxr - 1), 0), bx - 4);
+        const int ly = min(max((c.iy - 1 - y0) & (a.Nyr - 1), 0), by - 4);
+        const int lz = min(max(c.j0 - l0, 0), bz - 4);
+        LPoint& P = rec[t];
+        P.base = lz * zst + ly * sbx + lx;
+        float e = 0.f;
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+          for (int k = 0; k < 4; ++k) e = fmaf(c.wy[b] * c.wx[k], seta[(ly + b) * sbx + lx + k], e);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          P.w[k] = c.wx[k];
+          P.w[4 + k] = c.wy[k];
+          P.w[8 + k] = c.wz[k];
+        }
+        float fx, fy;
+        int ixx, iyy;
+        locate(px, a.sx_hi, a.sx_lo, a.Nxr, ixx, fx);
+        locate(py, a.sy_hi, a.sy_lo, a.Nyr, iyy, fy);
+        const float z1 = zs.z[c.j0 + 1], z2 = zs.z[c.j0 + 2];
+        P.off[0] = fx;
+        P.off[1] = fy;
+        P.off[2] = (pz - z1) / (z2 - z1);
+        P.eta = e;
+        P.z = pz;
+        P.inside = c.inside;
+      }
+    } else {
+      // per-point stencils: four threads per point, each blends 16 of its 64 nodes
+      const int j = threadIdx.x >> 2, qq = threadIdx.x & 3;
+      if (j < npts) {
+        const int64_t i = p0 + s0 + j;
+        const float px = __ldg(&a.pts[3 * i]), py = __ldg(&a.pts[3 * i + 1]), pz = __ldg(&a.pts[3 * i + 2]);
+        const PointCell c = point_cell(a, zs, px, py, pz);
+        const size_t tl_stride = size_t(a.nz) * plane;
+#pragma unroll 4
+        for (int kk = 0; kk < 16; ++kk) {
+          const int node = 16 * qq + kk, zq = node >> 4, b = (node >> 2) & 3, k = node & 3;
+          const size_t gi = size_t(c.j0 + zq) * plane + size_t((c.iy - 1 + b) & (a.Nyr - 1)) * a.Nxr +
+                            size_t((c.ix - 1 + k) & (a.Nxr - 1));
+          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+          for (int tl = 0; tl < a.n_tl; ++tl) {
+            const float4 gv = __ldg(&a.nodes[size_t(tl) * tl_stride + gi]);
+            const float w = a.wt[tl];
+            v.x = fmaf(w, gv.x, v.x);
+            v.y = fmaf(w, gv.y, v.y);
+            v.z = fmaf(w, gv.z, v.z);
+            v.w = fmaf(w, gv.w, v.w);
+          }
+          sbox[64 * j + node] = v;
+        }
+        if (qq == 0) {
+          LPoint& P = rec[j];
+          P.base = 64 * j;
+          float e = 0.f;
+          for (int tl = 0; tl < a.n_tl; ++tl)
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+#pragma unroll
+              for (int k = 0; k < 4; ++k)
+                e = fmaf(a.wt[tl] * c.wy[b] * c.wx[k],
+                         __ldg(&a.eta[size_t(tl) * plane + size_t((c.iy - 1 + b) & (a.Nyr - 1)) * a.Nxr +
+                                      ((c.ix - 1 + k) & (a.Nxr - 1))]), e);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            P.w[k] = c.wx[k];
+            P.w[4 + k] = c.wy[k];
+            P.w[8 + k] = c.wz[k];
+          }
+          float fx, fy;
+          int ixx, iyy;
+          locate(px, a.sx_hi, a.sx_lo, a.Nxr, ixx, fx);
+          locate(py, a.sy_hi, a.sy_lo, a.Nyr, iyy, fy);
+          const float z1 = zs.z[c.j0 + 1], z2 = zs.z[c.j0 + 2];
+          P.off[0] = fx;
+          P.off[1] = fy;
+          P.off[2] = (pz - z1) / (z2 - z1);
+          P.eta = e;
+          P.z = pz;
+          P.inside = c.inside;
+        }
+      }
+    }
+    __syncthreads();
+    // ---- B: SB points = SB / 4 tiles, spread over the warps
+    const int ntiles = (npts + 3) / 4, per = (SB / 4 + (blockDim.x >> 5) - 1) / (blockDim.x >> 5);
+    if (boxed) learned_tiles(sbox, sbx, zst, rec, W, warp * per, min(per, max(ntiles - warp * per, 0)), npts);
+    else learned_tiles(sbox, 4, 16, rec, W, warp * per, min(per, max(ntiles - warp * per, 0)), npts);
+    __syncthreads();
+    // ---- C
+    if (threadIdx.x < npts) {
+      const LPoint& P = rec[threadIdx.x];
+      store_point(a, p0 + s0 + threadIdx.x, make_float4(P.w[0], P.w[1], P.w[2], P.w[3]), P.eta, P.z,
+                  P.inside != 0);
+    }
+    __syncthreads();
   }
 }
 
@@ -558,37 +802,6 @@ __global__ void __launch_bounds__(128) k_mlp_features(FeatArgs f, Levels L) {
       f.scale[4 * i + fld] = s;
       f.lag[4 * i + fld] = lagv;
     }
-  }
-}
-
-// Corrected fields: f = lagrange_f + s_f y_f, then Bernoulli; out-of-range points stay NaN.
-__global__ void k_mlp_correct(InterpArgs a, const float* __restrict__ scale,
-                              const float* __restrict__ lag, const float* __restrict__ y, Levels L) {
-  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= a.np) return;
-  float vals[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) vals[q] = fmaf(scale[4 * i + q], y[4 * i + q], lag[4 * i + q]);
-  const float z = a.pts[3 * i + 2];
-  const bool inside = (z >= L.z[0]) && (z <= L.z[a.nz - 1]);
-  float4 acc = make_float4(vals[0], vals[1], vals[2], vals[3]);
-  if (!inside) {
-    const float qnan = __int_as_float(0x7fc00000);
-    acc = make_float4(qnan, qnan, qnan, qnan);
-    if (a.n_oor) atomicAdd(a.n_oor, 1ULL);
-  }
-  if (a.o_u) a.o_u[i] = acc.x;
-  if (a.o_v) a.o_v[i] = acc.y;
-  if (a.o_w) a.o_w[i] = acc.z;
-  if (a.o_p) {
-    float p;
-    if (a.p_mode == SWENSE_P_PHIT) {
-      p = acc.w;
-    } else {
-      p = -a.rho * (acc.w + 0.5f * (acc.x * acc.x + acc.y * acc.y + acc.z * acc.z));
-      if (a.p_mode == SWENSE_P_TOTAL) p -= a.rho * a.g * z;
-    }
-    a.o_p[i] = p;
   }
 }
 
@@ -707,34 +920,29 @@ extern "C" int swense_interp_learned(const swense_grid* g, double t, const float
   if (g->ny_r < 4) return fail(SWENSE_ERR_UNSUPPORTED, "the learned correction needs a 3-D grid");
   if (a.spline) return fail(SWENSE_ERR_UNSUPPORTED, "the learned correction is defined on LAGRANGE3 grids");
   if (!packed) return fail(SWENSE_ERR_ARG, "NULL packed weights");
-  const int64_t chunk = std::min<int64_t>(np, int64_t(1) << 19);
-  const size_t rows = size_t(4) * std::max<int64_t>(chunk, 1);
-  const size_t bytes = 256 + rows * (MLP_XLD + 3) * sizeof(float);
+  if (reinterpret_cast<uintptr_t>(packed) & 15) return fail(SWENSE_ERR_ARG, "packed weights must be 16-byte aligned");
+  // workspace: [0, 256) out-of-range counter, then one int4 box plan per 1024-point chunk
+  const int64_t blocks = (np + BOX_PTS - 1) / BOX_PTS;
+  if (blocks >= (int64_t(1) << 31)) return fail(SWENSE_ERR_SIZE, "too many points for one call");
   void* ws = nullptr;
-  st = workspace(bytes, stream, &ws);
+  st = workspace(256 + size_t(blocks) * sizeof(int4), stream, &ws);
   if (st) return st;
   unsigned long long* d_count = static_cast<unsigned long long*>(ws);
-  float* x = reinterpret_cast<float*>(static_cast<char*>(ws) + 256);
-  float* sc = x + rows * MLP_XLD;
-  float* lg = sc + rows;
-  float* y = lg + rows;
   if (n_out_of_range) SWENSE_CUDA_TRY(cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), stream));
-  for (int64_t s0 = 0; s0 < np; s0 += chunk) {
-    const int64_t n = std::min(chunk, np - s0);
-    InterpArgs c = a;
-    c.pts = pts + 3 * s0;
-    c.np = n;
-    c.o_u = u ? u + s0 : nullptr;
-    c.o_v = v ? v + s0 : nullptr;
-    c.o_w = w ? w + s0 : nullptr;
-    c.o_p = p ? p + s0 : nullptr;
-    c.n_oor = n_out_of_range ? d_count : nullptr;
-    FeatArgs f{c, x, sc, lg, eta ? eta + s0 : nullptr};
-    k_mlp_features<<<unsigned(std::min<int64_t>((n + 127) / 128, 152 * 64)), 128, 0, stream>>>(f, lev);
+  if (np > 0) {
+    a.o_eta = eta;
+    a.o_u = u;
+    a.o_v = v;
+    a.o_w = w;
+    a.o_p = p;
+    a.n_oor = n_out_of_range ? d_count : nullptr;
+    int4* plan = reinterpret_cast<int4*>(static_cast<char*>(ws) + 256);
+    k_interp_plan<<<unsigned(blocks), BOX_THREADS, 0, stream>>>(a, lev, plan);
     SWENSE_CUDA_TRY(cudaGetLastError());
-    st = swense_mlp_forward(packed, x, 4 * n, y, stream);
-    if (st) return st;
-    k_mlp_correct<<<unsigned((n + 255) / 256), 256, 0, stream>>>(c, sc, lg, y, lev);
+    SWENSE_CUDA_TRY(cudaFuncSetAttribute((const void*)k_interp_learned,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(LRN_SMEM)));
+    k_interp_learned<<<unsigned(blocks), BOX_THREADS, LRN_SMEM, stream>>>(
+        a, lev, plan, static_cast<const PackedFwd*>(packed));
     SWENSE_CUDA_TRY(cudaGetLastError());
     count_launches(2);
   }

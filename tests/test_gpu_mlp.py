@@ -167,3 +167,50 @@ def test_trained_correction_beats_plain_interpolation(env):
             store.append(np.sqrt(np.mean(d.astype(np.float64) ** 2)))
     assert np.mean(err_learned) < np.mean(err_plain), (err_learned, err_plain)
     assert np.mean(div_learned) <= 1.05 * np.mean(div_plain), (div_learned, div_plain)
+
+
+@pytest.mark.parametrize("order", ["mesh", "random"])
+def test_fused_learned_gather_matches_oracle(env, order):
+    """interp_learned (one fused kernel: stencil gather, features, three BF16 layers, correction)
+    against the oracle chain on the FP64 grid: stencil features -> FP64 network on the same
+    BF16-rounded weights -> lagrange + s_f * out_scale * y[f] -> Bernoulli. Mesh-ordered points
+    take the staged-box path; random points (chunks whose box does not fit) the per-point path.
+    Bar: 1e-5 of the field scale plus 1e-3 of the largest correction."""
+    torch, api, _ = env
+    cfg = configs.jonswap3d_small()
+    sea, z, tl, t = cfg["sea"], cfg["z_levels"], cfg["t_levels"], cfg["t_query"]
+    if order == "mesh":
+        pts = configs.mesh_points(cfg["mesh"])[:5000]
+    else:
+        rng = np.random.default_rng(61)
+        pts = np.stack([rng.uniform(0, sea["Lx"], 3001), rng.uniform(0, sea["Ly"], 3001),
+                        rng.uniform(float(z[0]), float(z[-1]), 3001)], 1).astype(np.float32)
+    p = _rand_params(31)
+    out_scale = 0.05
+    mlp = api.Mlp(torch.from_numpy(api.mlp_flatten(p)), out_scale=out_scale)
+    grid = api.fields_on_grid(api.upload_modes(sea), z, 2, tl)
+    got, _ = api.interp_learned(grid, t, torch.from_numpy(pts).cuda(), mlp, p_mode="phit")
+    nodes, etas = [], []
+    for tt in tl:
+        n_, e_ = modal.fields_on_grid(modal.propagate(sea, tt), z, 2)
+        nodes.append(n_)
+        etas.append(e_)
+    st, off, lag = ointerp.stencil_features(np.stack(nodes), sea["Lx"], sea["Ly"], z, tl, pts, t)
+    pr = {k: (bf16_round(v) if k.startswith("W") else np.asarray(v, np.float32).astype(np.float64))
+          for k, v in p.items()}
+    n = len(pts)
+    corr = np.zeros((n, 4))
+    for f in range(4):
+        x, s = omlp.features(st[:, f], off)
+        y, _ = omlp.forward(pr, x)
+        corr[:, f] = s * out_scale * y[:, f]
+    ref = lag + corr
+    vs = velocity_scale(ref[:, 0], ref[:, 1], ref[:, 2])
+    cmax = np.max(np.abs(corr))
+    for f, k in enumerate(("u", "v", "w", "p")):          # p_mode "phit": p is dphi/dt
+        scale = vs if f < 3 else np.max(np.abs(ref[:, 3]))
+        e = np.max(np.abs(got[k].cpu().numpy() - ref[:, f]))
+        assert e <= 1e-5 * scale + 1e-3 * cmax, (k, e, scale, cmax)
+    ref_eta = ointerp.interp_points(np.stack(nodes), np.stack(etas), sea["Lx"], sea["Ly"], z, tl,
+                                    pts, t)["eta"]
+    assert rel_linf(got["eta"].cpu().numpy(), ref_eta) <= 1e-5
