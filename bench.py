@@ -586,10 +586,25 @@ def run_learned(args, rank, world):
         api.interp(grid, tq, pts, out=outs_p)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     steps = max(3, min(args.steps, 20))
+    from paper_2005_12716_gb300 import _swense as S
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    l0 = S.swense_launches()
     ms_l = _time_events(lambda: api.interp_learned(grid, tq, pts, mlp, out=outs_l), steps, flush)
+    launches = S.swense_launches() - l0
+    clk = clocks.stop()
     ms_p = _time_events(lambda: api.interp(grid, tq, pts, out=outs_p), steps, flush)
     rows = 4 * len(pts_np)
     flops = rows * 2 * (67 * 64 + 64 * 64 + 64 * 4)
+    # MMAs issued per 16 rows: layer 1 5 k-tiles x 8 n-tiles, layer 2 4 x 8, layer 3 4 x 1, each
+    # twice (hi and lo activations), 4096 flop per m16n8k16
+    mma_flops = rows / 16 * 2 * (5 * 8 + 4 * 8 + 4 * 1) * 4096
+    peaks = {}
+    pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pp):
+        with open(pp) as fh:
+            peaks = json.load(fh)
+    bf16_peak = float(peaks.get("bf16_tflops", 1910.8))
     line = {
         "metric": "wave-field points/sec at stated err vs FP64 oracle; % of HBM roofline",
         "value": len(pts_np) / (ms_l * 1e-3), "unit": "points/s", "n_gpus": 1, "steps": steps,
@@ -599,6 +614,14 @@ def run_learned(args, rank, world):
         "plain_gather_ms": ms_p, "train_seconds": t_train, "data_seconds": t_data,
         "train_loss_log": losses,
         "network_tflops_if_all_time_in_mlp": flops / (ms_l * 1e-3) / 1e12,
+        "roofline": {"bound": "tensor", "kernel": "k_interp_learned",
+                     "achieved": mma_flops / (ms_l * 1e-3) / 1e12, "peak": bf16_peak,
+                     "unit": "TFLOP/s", "frac": mma_flops / (ms_l * 1e-3) / 1e12 / bf16_peak,
+                     "traffic": None,
+                     "note": "m16n8k16 MMA flops issued (split operands, padded shapes) over the "
+                             "whole fused kernel time, against the measured dense BF16 peak"},
+        "gpu_launches": int(launches),
+        "clocks": clk,
     }
     if rank == 0 and not args.no_cpu_baseline:
         from oracle import modal

@@ -155,7 +155,7 @@ int swense_fields_on_grid_noalloc(const swense_modes* modes, int32_t n_tl, const
 /*
  * swense_autotune_grid — choose the launch shape of swense_fields_on_grid for this grid shape
  * (the transform path: warp-register kernels with 1, 2 or 4 levels per column-transform block,
- * or the shared-memory kernels; the level-chunk size among 16, 32, 64, 96, 128 MB; and, for
+ * or the shared-memory kernels; the level-chunk size among 16, 32, 64, 96, 128, 256 MB; and, for
  * 256- to 1024-point rows, whether one row-transform block handles both field pairs or one) by
  * timing each candidate three times on `stream`; the choice is cached per (nx, ny, pad_n, nz)
  * and used by later calls. No counterpart in the paper. Writes the grid (same outputs as

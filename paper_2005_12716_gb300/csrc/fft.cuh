@@ -334,3 +334,68 @@ __device__ __forceinline__ void stk_fft(float2 (&v)[N / 32], const float2 (&T)[s
 }
 
 }  // namespace swense
+
+namespace swense {
+
+// ------------------------------------------------------------------------------------------------
+// Block-wide Stockham inverse DFT of length N by TH threads (E = N / TH >= 8 elements each), the
+// same radix-8 (then 4 or 2) passes as stk_fft with "lane" generalised to the thread index and
+// the exchange through a padded block-shared buffer under __syncthreads. Twiddles come from the
+// table (L1). Layouts: on entry element b*8 + r of thread t holds position t + TH b + r N/8; on
+// exit element b*R + r holds t + TH b + r N/R (R = radix of the last pass).
+template <int N, int TH, int P>
+__device__ __forceinline__ void stkb_pass(float2 (&v)[N / TH], const float2* __restrict__ tw,
+                                          float2* buf, int t) {
+  constexpr int E = N / TH, R = stk_radix(N, P), NS = stk_ns(N, P), B = E / R;
+  static_assert(B >= 1, "each thread holds at least one butterfly per pass");
+  if constexpr (P > 0) {
+    constexpr int step = SWENSE_MAX_FFT / (NS * R);
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const int jm = NS <= TH ? t % NS : t + TH * (b % (NS / TH));
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[b * R + r] = cmul(v[b * R + r], __ldg(&tw[jm * r * step]));
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < B; ++b) {
+    if constexpr (R == 8) stk_dft8(&v[b * 8]);
+    else if constexpr (R == 4) stk_dft4(v[b * 4], v[b * 4 + 1], v[b * 4 + 2], v[b * 4 + 3]);
+    else stk_dft2(&v[b * 2]);
+  }
+  if constexpr (P + 1 < stk_npass(N)) {
+    // thread part and constant part of each index have disjoint bits (as in stk_pass)
+    const int lst = NS <= TH ? (t / NS) * NS * R + t % NS : t;
+    float2* bst = buf + stk_pad(lst);
+#pragma unroll
+    for (int b = 0; b < B; ++b)
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int c = NS <= TH ? TH * b * R + r * NS
+                               : (b / (NS / TH)) * NS * R + TH * (b % (NS / TH)) + r * NS;
+        bst[c + (c >> 4)] = v[b * R + r];
+      }
+    __syncthreads();
+    constexpr int R2 = stk_radix(N, P + 1), B2 = E / R2;
+    const float2* bld = buf + stk_pad(t);
+#pragma unroll
+    for (int b = 0; b < B2; ++b)
+#pragma unroll
+      for (int r = 0; r < R2; ++r) {
+        const int c = TH * b + r * (N / R2);
+        v[b * R2 + r] = bld[c + (c >> 4)];
+      }
+    __syncthreads();
+    stkb_pass<N, TH, P + 1>(v, tw, buf, t);
+  }
+}
+
+template <int N, int TH>
+__device__ __forceinline__ void stkb_fft(float2 (&v)[N / TH], const float2* __restrict__ tw, float2* buf,
+                                         int t) {
+  static_assert(N / TH >= 8 && N <= SWENSE_MAX_FFT && (TH & 15) == 0, "block Stockham sizes");
+  static_assert(N / 8 >= TH, "constant index parts are multiples of the thread count");
+  stkb_pass<N, TH, 0>(v, tw, buf, t);
+}
+
+}  // namespace swense

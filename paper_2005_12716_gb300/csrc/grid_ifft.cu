@@ -632,7 +632,7 @@ __global__ void __launch_bounds__(256, N >= 1024 ? 1 : 2) k_col_t(ColArgs a, Lev
   float2 T[stk_twn(N)];
   stk_init<N>(T, a.tw, lane);
   const int nyh = a.ny >> 1;
-  const float kx = float(m) * a.kxs;
+  const float kx = colok ? float(m) * a.kxs : 0.f;
   // modes of element e (zero in the padding and at the Nyquist row)
   auto load_mode = [&](int e, float2& ap, float2& at) {
     const int p = lane + 32 * (e / 8) + (e % 8) * (N / 8);
@@ -670,7 +670,10 @@ __global__ void __launch_bounds__(256, N >= 1024 ? 1 : 2) k_col_t(ColArgs a, Lev
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         const int p = lane + 32 * (e / 8) + (e % 8) * (N / 8);
-        const int n = p < N / 2 ? p : p - N;
+        // zero-padded and Nyquist positions carry no mode: evaluate their (unused) depth factor
+        // at ky = 0, where it cannot overflow (e^{|k| z} at a padded |k| can reach inf, and
+        // inf * 0 would be NaN)
+        const int n = p < nyh ? p : (p > N - nyh ? p - N : 0);
         const float ky = float(n) * a.kys;
         const float kk = sqrtf(kx * kx + ky * ky);
         float F, S;
@@ -788,6 +791,61 @@ __global__ void __launch_bounds__(256, N >= 1024 ? 2 : 3) k_row_t2(RowArgs a) {
   for (int e = 0; e < E; ++e) __stcs(&out[2 * (lane + 32 * (e / RL) + (e % RL) * (N / RL))], z[e]);
 }
 
+// Row pass for rows longer than a warp transform (2048..8192 points): one block of kThreads per
+// grid row of one level, inputs from the transposed intermediate (coalesced), block-wide
+// Stockham transforms of Z1 = U + iV and Z2 = W + iT.
+template <int N>
+__global__ void __launch_bounds__(256, N >= 8192 ? 1 : 2) k_row_tb(RowArgs a) {
+  extern __shared__ float2 sm[];                 // one or two exchange buffers
+  constexpr int E = N / kThreads, RL = stk_radix(N, stk_npass(N) - 1);
+  constexpr bool BOTH = N <= 4096;               // both transforms' data in registers at once
+  const int t = threadIdx.x;
+  const int y = blockIdx.x;
+  const int level = blockIdx.y;
+  const size_t fs = size_t(a.Nyr) * a.ldG;
+  const float2* row = a.G + size_t(level) * 4 * fs + size_t(y) * a.ldG;
+  float4* out = a.nodes + (size_t(a.lev0 + level) * a.Nyr + y) * N;
+  auto pack = [&](float2 (&z)[E], int q) {       // q = 0: U + iV, 1: W + iT
+    const float2* A = row + 2 * q * fs;
+    const float2* B = A + fs;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int p = t + kThreads * (e / 8) + (e % 8) * (N / 8);
+      const bool lo = p < a.Mh, hi = p > N - a.Mh;
+      float2 u = make_float2(0.f, 0.f), v = u;
+      if (lo || hi) {
+        const int mm = lo ? p : N - p;
+        u = __ldcg(&A[mm]);
+        v = __ldcg(&B[mm]);
+      }
+      if (p == 0) z[e] = make_float2(u.x, v.x);
+      else if (!hi) z[e] = make_float2(u.x - v.y, u.y + v.x);
+      else z[e] = make_float2(u.x + v.y, v.x - u.y);
+    }
+  };
+  if constexpr (BOTH) {
+    float2 z1[E], z2[E];
+    pack(z1, 0);
+    pack(z2, 1);
+    stkb_fft<N, kThreads>(z1, a.tw, sm, t);
+    stkb_fft<N, kThreads>(z2, a.tw, sm + stk_buf(N), t);
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+      __stcs(&out[t + kThreads * (e / RL) + (e % RL) * (N / RL)], make_float4(z1[e].x, z1[e].y, z2[e].x, z2[e].y));
+  } else {
+    float2* o2 = reinterpret_cast<float2*>(out);
+#pragma unroll 1
+    for (int q = 0; q < 2; ++q) {
+      float2 z[E];
+      pack(z, q);
+      stkb_fft<N, kThreads>(z, a.tw, sm, t);
+#pragma unroll
+      for (int e = 0; e < E; ++e) __stcs(&o2[2 * (t + kThreads * (e / RL) + (e % RL) * (N / RL)) + q], z[e]);
+      __syncthreads();                           // the buffer is reused by the second transform
+    }
+  }
+}
+
 // Launch-shape choices of the warp-register path, per grid shape (set by swense_autotune_grid;
 // defaults otherwise).
 struct Tune {
@@ -869,6 +927,17 @@ int launch_row_t(const RowArgs& r, dim3 grid, cudaStream_t stream) {
 }
 
 template <int N>
+int launch_row_tb(const RowArgs& r, unsigned nl, cudaStream_t stream) {
+  const size_t smem = size_t(N <= 4096 ? 2 : 1) * stk_buf(N) * sizeof(float2);
+  int st = set_smem((const void*)k_row_tb<N>, smem);
+  if (st) return st;
+  k_row_tb<N><<<dim3(unsigned(r.Nyr), nl), kThreads, smem, stream>>>(r);
+  SWENSE_CUDA_TRY(cudaGetLastError());
+  count_launches(1);
+  return SWENSE_OK;
+}
+
+template <int N>
 int launch_row_t2(const RowArgs& r, dim3 grid, cudaStream_t stream) {
   const size_t smem = size_t(8) * stk_buf(N) * sizeof(float2);
   int st = set_smem((const void*)k_row_t2<N>, smem);
@@ -894,6 +963,12 @@ int launch_pair_t(const ColArgs& c, const RowArgs& r, const Levels& L, int nl, c
     default: return fail(SWENSE_ERR_UNSUPPORTED, "transposed pair: column length");
   }
   if (st) return st;
+  switch (r.Nxr) {                               // rows longer than a warp transform
+    case 2048: return launch_row_tb<2048>(r, unsigned(nl), s);
+    case 4096: return launch_row_tb<4096>(r, unsigned(nl), s);
+    case 8192: return launch_row_tb<8192>(r, unsigned(nl), s);
+    default: break;
+  }
   if (one_per_warp) {
     switch (r.Nxr) {
       case 256: return launch_row_t2<256>(r, gr2, s);
@@ -965,9 +1040,13 @@ int launch_row_e(int E, const RowArgs& r, dim3 grid, size_t smem, cudaStream_t s
   }
 }
 
-// The warp-register path covers 32 <= ny_r, nx_r <= 1024 (3-D only).
+// The warp-register path covers 32 <= ny_r, nx_r <= 1024 (3-D only); the transposed pair also
+// takes rows of 2048..8192 points (block-wide row transforms) over 256..1024-point columns.
 bool warp_path(int ny, int64_t Nxr, int64_t Nyr) {
   return ny > 1 && Nyr >= 32 && Nyr <= 1024 && Nxr >= 32 && Nxr <= 1024;
+}
+bool pair_path(int ny, int64_t Nxr, int64_t Nyr) {
+  return ny > 1 && Nyr >= 256 && Nyr <= 1024 && Nxr >= 256 && Nxr <= SWENSE_MAX_FFT;
 }
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
@@ -1161,7 +1240,7 @@ int launch_grid(const GridPlan& p, const swense_modes* md, const double* t, floa
     SWENSE_CUDA_TRY(cudaGetLastError());
     count_launches(1);
 
-    if (lpc > 0 && warp_path(ny, Nxr, Nyr)) {
+    if (lpc > 0 && (warp_path(ny, Nxr, Nyr) || (pair_path(ny, Nxr, Nyr) && (rowv == 2 || rowv == 3)))) {
       ColArgs ca{};
       ca.A_phi = Ap;
       ca.A_phit = At;
@@ -1189,7 +1268,8 @@ int launch_grid(const GridPlan& p, const swense_modes* md, const double* t, floa
       const size_t smem_col = size_t(2) * ny * (kColBlock + 1) * sizeof(float2);
       const size_t smem_row = size_t(4) * Mh * (kRowBlock + 1) * sizeof(float2);
       ca.ldG = ra.ldG = (Mh + 3) & ~3;
-      const bool pair_t = (rowv == 2 || rowv == 3) && Nyr >= 256 && Nxr >= 256;
+      const bool pair_t = (rowv == 2 || rowv == 3) && pair_path(ny, Nxr, Nyr);
+  
       for (int l0 = 0; l0 < nz; l0 += chunk) {
         if (pair_t) {
           const int nl = std::min(chunk, nz - l0);
@@ -1258,7 +1338,7 @@ extern "C" int swense_fields_on_grid(const swense_modes* md, int32_t n_tl, const
   }
   // untuned default: the transposed Stockham pair where both lengths are 256..1024, else the
   // warp path where its transforms stay in registers (n <= 512), else the shared-memory path
-  const bool pair = p.ny > 1 && p.Nxr >= 256 && p.Nxr <= 1024 && p.Nyr >= 256 && p.Nyr <= 1024;
+  const bool pair = pair_path(p.ny, p.Nxr, p.Nyr);
   const int lpc = tn.lpc >= 0 ? tn.lpc : (pair ? 4 : ((p.Nxr <= 512 && p.Nyr <= 512) ? kColLevels : 0));
   const int rowv = tn.lpc >= 0 ? tn.rowv : (pair ? 2 : 0);
   return launch_grid(p, md, t, nodes, eta, ws, chunk, stream, lpc, rowv);
@@ -1280,10 +1360,12 @@ extern "C" int swense_autotune_grid(const swense_modes* md, int32_t n_tl, const 
     float best_ms = 1e30f;
     for (int lpc : {0, 1, 2, 4})
     for (int rowv : {0, 1, 2, 3}) {
-      if (lpc > 0 && !warp_path(p.ny, p.Nxr, p.Nyr)) continue;
+      const bool wp = warp_path(p.ny, p.Nxr, p.Nyr), pp = pair_path(p.ny, p.Nxr, p.Nyr);
+      if (lpc > 0 && !wp && !(pp && rowv == 2)) continue;
       if (rowv && (lpc == 0 || p.Nxr < 256)) continue;   // only the Stockham row sizes have variants
-      if (rowv >= 2 && p.Nyr < 256) continue;
-      for (size_t mb : {16, 32, 64, 96, 128}) {
+      if (rowv >= 2 && !pp) continue;
+      if (!wp && rowv != 2 && lpc > 0) continue;
+      for (size_t mb : {16, 32, 64, 96, 128, 256}) {
         const size_t cb = mb << 20;
         const int chunk = int(std::max<size_t>(1, std::min<size_t>(p.nz, cb / p.per_level)));
         void* ws = nullptr;

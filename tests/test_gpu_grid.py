@@ -147,3 +147,31 @@ def _forced(api, lpc, rowv, chunk_mb, shape):
         _check(api, sea, z, pad, [0.0, 0.13])
     finally:
         S.swense_set_grid_tune(nx, ny, pad, len(z), -1, 32 << 20, 0)
+
+
+@pytest.mark.parametrize("shape", [(1024, 256, 2), (1024, 128, 4), (1024, 32, 8), (2048, 64, 1)])
+def test_long_rows_block_transform_sampled(api, shape):
+    """Rows of 2048, 4096 and 8192 points (block-wide Stockham row transforms behind the
+    transposed column pass, the untuned default for these shapes) at sampled nodes of every
+    level against the oracle's direct modal sum there."""
+    nx, ny, pad = shape
+    rng = np.random.default_rng(nx + ny + pad + 5)
+    Lx, Ly = 8.0, 8.0 * ny / nx
+    comps = seas.random_linear_components(nx, ny, Lx, Ly, 12, 0.01, rng)
+    sea = seas.linear_sea(nx, ny, Lx, Ly, comps)
+    z = np.linspace(-1.0, 0.04, 6).astype(np.float32)
+    tl = [0.0, 0.11]
+    grid = api.fields_on_grid(api.upload_modes(sea), z, pad, tl)
+    nyr, nxr = grid.nodes.shape[2], grid.nodes.shape[3]
+    assert nxr == pad * nx and nyr == pad * ny
+    for ti, t in enumerate(tl):
+        il = np.repeat(np.arange(len(z)), 16)
+        iy, ix = rng.integers(0, nyr, il.size), rng.integers(0, nxr, il.size)
+        pts = np.stack([ix * Lx / nxr, iy * Ly / nyr, z[il].astype(np.float64)], 1)
+        ref = modal.fields_at_points(modal.propagate(sea, t), pts)
+        g = grid.nodes[ti].cpu().numpy()[il, iy, ix].astype(np.float64)
+        vs = velocity_scale(ref["u"], ref["v"], ref["w"])
+        errs = [rel_linf_scaled(g[:, q], ref[k], vs) for q, k in enumerate(("u", "v", "w"))]
+        errs.append(rel_linf(g[:, 3], ref["phit"]))
+        errs.append(rel_linf(grid.eta[ti].cpu().numpy()[iy, ix].astype(np.float64), ref["eta"]))
+        assert max(errs) <= 1e-5, (ti, errs)
