@@ -44,7 +44,10 @@ def parse():
                     help="stage-1 launch shape 'lpc,chunk_mb,row_variant' instead of autotuning "
                          "(e.g. the autotuner's earlier choice, for a profiler run)")
     ap.add_argument("--points", type=int, default=0,
-                    help="direct mode: use only the first N near-body points (small profiling case)")
+                    help="direct mode: use only the first N near-body points; large mode: N "
+                         "points instead of 16 M (small profiling cases)")
+    ap.add_argument("--levels", type=int, default=0,
+                    help="large mode: number of levels instead of 128 (small profiling case)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -753,7 +756,8 @@ def run_large(args, rank, world):
     from wavegen import configs
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
-    cfg = configs.large_sea()
+    cfg = configs.large_sea(n_levels=args.levels or 128,
+                            n_points=args.points or 16_000_000)
     sea, z, tl, tq = cfg["sea"], cfg["z_levels"], cfg["t_levels"], cfg["t_query"]
     modes = api.upload_modes(sea, dev)
     grid = api.alloc_grid(modes, z, 1, tl, dev)
@@ -796,7 +800,7 @@ def run_large(args, rank, world):
         "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 (direct: bf16x3 split, f32 accumulate)",
         "data": "synthetic",
-        "config": {"workload": f"large_sea: 2048x1024 modes, 128 levels, 2 time levels, {n} Morton-order "
+        "config": {"workload": f"large_sea: 2048x1024 modes, {len(z)} levels, 2 time levels, {n} Morton-order "
                                f"points + {nn} near-body points (direct split-BF16 over all modes)",
                    "stage1_tune": tune, "l2": "inputs larger than L2 (8.6 GB grid)"},
         "stages_ms": res,

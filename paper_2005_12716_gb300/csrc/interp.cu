@@ -495,16 +495,28 @@ static_assert(sizeof(LPoint) == 80, "LPoint layout");
 
 using mlpnet::PackedFwd;
 
+// Shared-memory copy of the forward weights with padded rows: the B-fragment loads of a warp
+// (row 8 nt + g, word 8 kk + q) then fall into 32 different banks (an unpadded 64-wide row
+// maps all eight g to one bank).
+constexpr int W1LD = mlpnet::KIN + 8, W2LD = mlpnet::NH + 8;
+struct WeightsSmem {
+  __nv_bfloat16 w1[mlpnet::NH][W1LD];
+  __nv_bfloat16 w2[mlpnet::NH][W2LD];
+  __nv_bfloat16 w3[mlpnet::NO][W2LD];
+  float b1[mlpnet::NH], b2[mlpnet::NH], b3[mlpnet::NO];
+  float out_scale, pad_[3];
+};
+
 constexpr int LRN_SB = 128;                            // points per sub-batch (box mode)
 constexpr int LRN_SB_PP = 64;                          // points per sub-batch (per-point stencils)
 static_assert(LRN_SB_PP * 64 <= BOX_NODES, "per-point stencils fit the box area");
 constexpr size_t LRN_SMEM = size_t(BOX_NODES) * sizeof(float4) + size_t(BOX_COLS) * sizeof(float) +
-                            size_t(LRN_SB) * sizeof(LPoint) + sizeof(PackedFwd);
+                            size_t(LRN_SB) * sizeof(LPoint) + sizeof(WeightsSmem);
 
 // Phase B for `ntile` 16-row tiles of this warp. Node (x k, y b, level q) of point j is
 // nodes[rec[j].base + q * SZ + b * SY + k].
 __device__ __forceinline__ void learned_tiles(const float4* nodes, int SY, int SZ, LPoint* rec,
-                                              const PackedFwd& W, int tile0, int ntile, int npts) {
+                                              const WeightsSmem& W, int tile0, int ntile, int npts) {
   using namespace mlpnet;
   const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
   const int f = g & 3;                                 // field of rows g and g + 8
@@ -557,20 +569,21 @@ __device__ __forceinline__ void learned_tiles(const float4* nodes, int SY, int S
       xh[4][2 + h] = xl[4][2 + h] = 0u;
     }
     float z1[8][4];
-    layer<5, 8, true>(z1, xh, xl, &W.w1[0][0], KIN, W.b1, lane);
+    layer<5, 8, true>(z1, xh, xl, &W.w1[0][0], W1LD, W.b1, lane);
     unsigned h1h[4][4], h1l[4][4];
     to_a<8, true>(z1, h1h, h1l);
     float z2[8][4];
-    layer<4, 8, true>(z2, h1h, h1l, &W.w2[0][0], NH, W.b2, lane);
+    layer<4, 8, true>(z2, h1h, h1l, &W.w2[0][0], W2LD, W.b2, lane);
     unsigned h2h[4][4], h2l[4][4];
     to_a<8, true>(z2, h2h, h2l);
     float o[1][4];
-    layer<4, 1, true>(o, h2h, h2l, &W.w3[0][0], NH, W.b3, lane);
+    layer<4, 1, true>(o, h2h, h2l, &W.w3[0][0], W2LD, W.b3, lane);
     __syncwarp();                                      // every lane has read its records
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int jh = h ? j1 : j0;
-      if ((f >> 1) == q && jh < npts) rec[jh].w[f] = fmaf(sc[h] * W.out_scale, o[0][2 * h + (f & 1)], lag[h]);
+      const float yv = (f & 1) ? o[0][2 * h + 1] : o[0][2 * h];   // a select, not a local array
+      if ((f >> 1) == q && jh < npts) rec[jh].w[f] = fmaf(sc[h] * W.out_scale, yv, lag[h]);
     }
     __syncwarp();
   }
@@ -582,13 +595,27 @@ __global__ void __launch_bounds__(BOX_THREADS, 2) k_interp_learned(InterpArgs a,
   extern __shared__ float4 sbox[];
   float* seta = reinterpret_cast<float*>(sbox + BOX_NODES);
   LPoint* rec = reinterpret_cast<LPoint*>(seta + BOX_COLS);
-  PackedFwd& W = *reinterpret_cast<PackedFwd*>(rec + LRN_SB);
+  WeightsSmem& W = *reinterpret_cast<WeightsSmem*>(rec + LRN_SB);
   __shared__ LevelTables zs;
   fill_level_tables(zs, L, a.nz);
   {
-    const int4* src = reinterpret_cast<const int4*>(Wg);
-    int4* dst = reinterpret_cast<int4*>(&W);
-    for (int i = threadIdx.x; i < int(sizeof(PackedFwd) / 16); i += blockDim.x) dst[i] = __ldg(&src[i]);
+    // rows re-strided into the padded layout, 16 bytes (8 bf16) at a time
+    using namespace mlpnet;
+    const uint4* g1 = reinterpret_cast<const uint4*>(&Wg->w1[0][0]);
+    const uint4* g2 = reinterpret_cast<const uint4*>(&Wg->w2[0][0]);
+    const uint4* g3 = reinterpret_cast<const uint4*>(&Wg->w3[0][0]);
+    for (int i = threadIdx.x; i < NH * KIN / 8; i += blockDim.x)
+      *reinterpret_cast<uint4*>(&W.w1[i / (KIN / 8)][8 * (i % (KIN / 8))]) = __ldg(&g1[i]);
+    for (int i = threadIdx.x; i < NH * NH / 8; i += blockDim.x)
+      *reinterpret_cast<uint4*>(&W.w2[i / (NH / 8)][8 * (i % (NH / 8))]) = __ldg(&g2[i]);
+    for (int i = threadIdx.x; i < NO * NH / 8; i += blockDim.x)
+      *reinterpret_cast<uint4*>(&W.w3[i / (NH / 8)][8 * (i % (NH / 8))]) = __ldg(&g3[i]);
+    for (int i = threadIdx.x; i < NH; i += blockDim.x) {
+      W.b1[i] = __ldg(&Wg->b1[i]);
+      W.b2[i] = __ldg(&Wg->b2[i]);
+    }
+    if (threadIdx.x < NO) W.b3[threadIdx.x] = __ldg(&Wg->b3[threadIdx.x]);
+    if (threadIdx.x == 0) W.out_scale = __ldg(&Wg->out_scale);
   }
   const int64_t p0 = int64_t(blockIdx.x) * BOX_PTS;
   const int4 pl = plan[blockIdx.x];

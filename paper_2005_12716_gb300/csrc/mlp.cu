@@ -113,7 +113,8 @@ __global__ void __launch_bounds__(128) k_mlp_forward(const Packed* __restrict__ 
     for (int h = 0; h < 2; ++h) {
       const int64_t r = row0 + g + 8 * h;
       const int f = (g + 8 * h) & 3;               // row0 is a multiple of 16
-      if (r < rows && (f >> 1) == t) y[r] = o[0][2 * h + (f & 1)] * s.out_scale;
+      const float yv = (f & 1) ? o[0][2 * h + 1] : o[0][2 * h];   // a select, not a local array
+      if (r < rows && (f >> 1) == t) y[r] = yv * s.out_scale;
     }
   }
 }
