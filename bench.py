@@ -210,6 +210,21 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(value, world, device=None):
+    """Largest value over the ranks (a job's step time is its slowest rank's); N = 1: unchanged."""
+    if world <= 1:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, world, ms_per_step):
+    """Whole-job rate: every rank processes its own replica of the workload (weak scaling)."""
+    return world * units_per_rank / (ms_per_step * 1e-3)
+
+
 def kernel_source_hash(files=("csrc/interp.cu", "csrc/internal.cuh", "../include/swense.h")):
     """Hash of the sources a kernel is built from (paths relative to the package)."""
     h = hashlib.sha256()
@@ -223,7 +238,7 @@ def kernel_source_hash(files=("csrc/interp.cu", "csrc/internal.cuh", "../include
 # the hash of the kernel's sources and the workload they were taken on; a changed kernel or
 # workload invalidates them (traffic is then reported as null).
 NCU_TRAFFIC = {
-    "k_interp_box": {"bytes": 114146048 + 118993152, "hash": "a7c6d2649eecdee0",
+    "k_interp_box": {"bytes": 114905344 + 116937472, "hash": "9d79ae4f1f5c544e",
                      "workload": "jonswap3d: 512x256 modes, 64 levels, pad 1, 2 time levels, "
                                  "2048000 cell + 6177280 face centres (cylinder O-grid)"},
 }
@@ -266,33 +281,43 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     # Each stage captured once into a CUDA graph (kernel arguments are captured by value; the
     # library's workspace was sized by the warm-up calls), then replayed per step.
+    # Stage 2 runs as its two kernels, the gather plan (point chunks -> stencil boxes) and the
+    # gather proper, so the dominant kernel is timed on its own; the plan is remade every step.
+    plan = torch.empty(max(1, S.swense_interp_plan_bytes(npts)), dtype=torch.uint8, device=dev)
     launches_c0 = S.swense_launches()
     if not args.no_graph:
-        g1, g2 = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+        g1, g2a, g2b = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
         with torch.cuda.graph(g1):
             api.fields_on_grid(modes, z, pad, tl, out=grid)
         launches_s1 = S.swense_launches() - launches_c0
-        with torch.cuda.graph(g2):
-            api.interp(grid, tq, pts, out=outs)
-        stage1, stage2 = g1.replay, g2.replay
+        with torch.cuda.graph(g2a):
+            api.interp_plan(grid, pts, out=plan)
+        with torch.cuda.graph(g2b):
+            api.interp_with_plan(grid, tq, pts, plan, out=outs)
+        stage1, stage2a, stage2b = g1.replay, g2a.replay, g2b.replay
         launches_per_step = S.swense_launches() - launches_c0
         launches_s2 = launches_per_step - launches_s1
     else:
         stage1 = lambda: api.fields_on_grid(modes, z, pad, tl, out=grid)  # noqa: E731
-        stage2 = lambda: api.interp(grid, tq, pts, out=outs)  # noqa: E731
+        stage2a = lambda: api.interp_plan(grid, pts, out=plan)  # noqa: E731
+        stage2b = lambda: api.interp_with_plan(grid, tq, pts, plan, out=outs)  # noqa: E731
         launches_per_step = None
         launches_s1 = launches_s2 = None
     stream = torch.cuda.current_stream(dev)
     for _ in range(2):
         stage1()
-        stage2()
+        stage2a()
+        stage2b()
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks = ClockSampler(dev.index)
     clocks.start()
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    # One step: stage 1, the gather plan, the gather (events between them on the launching
+    # stream). Running the plan concurrently with stage 1 on a second stream was measured and
+    # gained nothing (both are latency-bound and share the SMs), so the step stays sequential.
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
     launches0 = S.swense_launches()
     t_wall = time.perf_counter()
     for s in range(args.steps):
@@ -300,8 +325,10 @@ def run_ours(args, rank, world):
         ev[s][0].record(stream)
         stage1()
         ev[s][1].record(stream)
-        stage2()
+        stage2a()
         ev[s][2].record(stream)
+        stage2b()
+        ev[s][3].record(stream)
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall
     launches = S.swense_launches() - launches0
@@ -309,15 +336,15 @@ def run_ours(args, rank, world):
         launches = launches_per_step * args.steps
     clk = clocks.stop()
     k1 = np.array([ev[s][0].elapsed_time(ev[s][1]) for s in range(args.steps)])
-    k2 = np.array([ev[s][1].elapsed_time(ev[s][2]) for s in range(args.steps)])
-    total_ms = float((k1 + k2).sum())
+    k2a = np.array([ev[s][1].elapsed_time(ev[s][2]) for s in range(args.steps)])
+    k2b = np.array([ev[s][2].elapsed_time(ev[s][3]) for s in range(args.steps)])
+    k2 = k2a + k2b
+    total_ms = max_over_ranks(float(sum(ev[s][0].elapsed_time(ev[s][3]) for s in range(args.steps))),
+                              world, dev)
     if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
         torch.distributed.barrier()
     ms_per_step = total_ms / args.steps
-    value = world * npts / (ms_per_step * 1e-3)
+    value = job_throughput(npts, world, ms_per_step)
 
     # ---- algorithmic bytes and roofline
     nxr, nyr = api.grid_dims(modes, pad)
@@ -334,26 +361,41 @@ def run_ours(args, rank, world):
     else:
         hbm, peak_src = FALLBACK_HBM_GBS, "fallback"
     k1_ms, k2_ms = float(k1.mean()), float(k2.mean())
+    k2a_ms, k2b_ms = float(k2a.mean()), float(k2b.mean())
+    box_bytes = k2_bytes                                  # the gather reads points, writes fields
+    plan_bytes = npts * 12 + (npts + 1023) // 1024 * 16
     src_hash = kernel_source_hash()
     stages = {
         "grid_ifft": {"ms": k1_ms, "algorithmic_bytes": k1_bytes,
                       "achieved_gbs": k1_bytes / (k1_ms * 1e-3) / 1e9,
                       "frac_hbm": k1_bytes / (k1_ms * 1e-3) / 1e9 / hbm,
-                      "launches_per_step": None},
+                      "launches_per_step": launches_s1},
         "interp": {"ms": k2_ms, "algorithmic_bytes": k2_bytes, "touched_grid_bytes": touched,
                    "achieved_gbs": k2_bytes / (k2_ms * 1e-3) / 1e9,
                    "frac_hbm": k2_bytes / (k2_ms * 1e-3) / 1e9 / hbm,
-                   "launches_per_step": launches_s2},
+                   "launches_per_step": launches_s2,
+                   "k_interp_plan_ms": k2a_ms, "k_interp_plan_bytes": plan_bytes,
+                   "k_interp_box_ms": k2b_ms},
     }
-    stages["grid_ifft"]["launches_per_step"] = launches_s1
-    dom = "interp" if k2_ms >= k1_ms else "grid_ifft"
-    kname = "k_interp_box" if dom == "interp" else "grid_ifft (k_col_stk + k_row_stk)"
+    if k2b_ms >= k1_ms:
+        kname, dom_bytes, dom_ms = "k_interp_box", box_bytes, k2b_ms
+    else:
+        kname, dom_bytes, dom_ms = "grid_ifft (k_col_t + k_row_t)", k1_bytes, k1_ms
     tr = NCU_TRAFFIC.get(kname)
     traffic = tr["bytes"] if tr and tr.get("hash") == src_hash and tr.get("workload") == desc else None
-    roofline = {"bound": "hbm", "kernel": kname, "achieved": stages[dom]["achieved_gbs"],
-                "peak": hbm, "unit": "GB/s", "frac": stages[dom]["frac_hbm"], "traffic": traffic,
+    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": traffic,
                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
                 else "fallback 6.8 TB/s"}
+    if kname == "k_interp_box":
+        # the binding resource of the gather: shared-memory reads, 64 float4 stencil nodes + 16
+        # eta values per point, against 128 B/clk/SM x 152 SMs at the maximum SM clock
+        smem_peak = 152 * 128 * 2070e6 / 1e9
+        smem = npts * (64 * 16 + 16 * 4) / (dom_ms * 1e-3) / 1e9
+        roofline["shared_memory"] = {"achieved": smem, "peak": smem_peak, "unit": "GB/s",
+                                     "frac": smem / smem_peak,
+                                     "bytes_per_point": 64 * 16 + 16 * 4}
 
     line = {
         "metric": "wave-field points/sec at stated err vs FP64 oracle; % of HBM roofline",
@@ -437,12 +479,8 @@ def run_ours(args, rank, world):
         s_cmp.wait_stream(s_in)
         e1.record(s_cmp)
         torch.cuda.synchronize()
-        e_ms = e0.elapsed_time(e1) / ks
-        if world > 1:
-            t = torch.tensor([e_ms], device=dev, dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e_ms = float(t.item())
-        line["e2e"] = {"value": world * npts / (e_ms * 1e-3), "unit": "points/s",
+        e_ms = max_over_ranks(e0.elapsed_time(e1) / ks, world, dev)
+        line["e2e"] = {"value": job_throughput(npts, world, e_ms), "unit": "points/s",
                        "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                        "ms_per_step": e_ms,
                        "pipeline": "copy-in, compute and copy-out streams overlap across steps"}

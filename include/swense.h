@@ -157,7 +157,9 @@ int swense_fields_on_grid_noalloc(const swense_modes* modes, int32_t n_tl, const
  * (the transform path: warp-register kernels with 1, 2 or 4 levels per column-transform block,
  * or the shared-memory kernels; the level-chunk size among 16, 32, 64, 96, 128, 256 MB; and, for
  * 256- to 1024-point rows, whether one row-transform block handles both field pairs or one) by
- * timing each candidate three times on `stream`; the choice is cached per (nx, ny, pad_n, nz)
+ * timing each candidate five times on `stream` (best of five, each from a cold L2: the
+ * workspace, grown to at least 256 MB, is overwritten before each repetition); the choice is
+ * cached per (nx, ny, pad_n, nz)
  * and used by later calls. No counterpart in the paper. Writes the grid (same outputs as
  * swense_fields_on_grid), synchronises the stream, must not be captured. 2-D grids have a
  * single path (nothing to tune; *lpc_out = -1).
@@ -213,6 +215,31 @@ int swense_interp(const swense_grid* grid, double t, const float* pts, int64_t n
                   float* eta, float* u, float* v, float* w, float* p,
                   int32_t p_mode, double rho, double g, int64_t* n_out_of_range,
                   void* stream);
+
+/*
+ * Reusable gather plans (no counterpart in the paper). swense_interp first cuts the points into
+ * 1024-point chunks and finds each chunk's stencil bounding box on the grid; that plan depends
+ * only on the points and the grid geometry (nx_r, ny_r, Lx, Ly, z_levels), not on the time or
+ * the field values, so a solver whose mesh and grid do not change can make it once:
+ *   swense_interp_plan_bytes(np)      bytes of device memory a plan for np points needs
+ *                                     (16 per chunk; 0 for np <= 0);
+ *   swense_interp_plan(grid, pts, np, plan, stream)
+ *                                     writes the plan into `plan` (device, caller-owned,
+ *                                     16-byte aligned, swense_interp_plan_bytes(np) bytes;
+ *                                     the size is not checked). The grid's field arrays are not
+ *                                     read; its geometry and level list are;
+ *   swense_interp_with_plan(...)      swense_interp with that plan (the plan kernel is skipped).
+ * A plan made for other points or another grid geometry gives wrong results (reads stay inside
+ * the shared-memory box: offsets are clamped). Errors: as swense_interp; SWENSE_ERR_ARG for a
+ * NULL or misaligned plan.
+ */
+int64_t swense_interp_plan_bytes(int64_t np);
+int swense_interp_plan(const swense_grid* grid, const float* pts, int64_t np, void* plan,
+                       void* stream);
+int swense_interp_with_plan(const swense_grid* grid, double t, const float* pts, int64_t np,
+                            const void* plan, float* eta, float* u, float* v, float* w, float* p,
+                            int32_t p_mode, double rho, double g, int64_t* n_out_of_range,
+                            void* stream);
 
 /*
  * swense_bin_points — point binning for scattered point sets (no counterpart in the paper,

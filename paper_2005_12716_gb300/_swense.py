@@ -185,6 +185,37 @@ def swense_interp(grid, t, pts, np_, eta=None, u=None, v=None, w=None, p=None, p
     return cnt.value if count_out_of_range else None
 
 
+_SIGS.update({
+    "swense_interp_plan_bytes": (ctypes.c_int64, [ctypes.c_int64]),
+    "swense_interp_plan": (ctypes.c_int, [ctypes.POINTER(swense_grid), ctypes.c_void_p, ctypes.c_int64,
+                                          ctypes.c_void_p, ctypes.c_void_p]),
+    "swense_interp_with_plan": (ctypes.c_int, [ctypes.POINTER(swense_grid), ctypes.c_double,
+                                               ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                               ctypes.c_double, ctypes.c_double, ctypes.c_void_p,
+                                               ctypes.c_void_p]),
+})
+
+
+def swense_interp_plan_bytes(np_):
+    return int(load().swense_interp_plan_bytes(np_))
+
+
+def swense_interp_plan(grid, pts, np_, plan, stream=None):
+    _check(load().swense_interp_plan(ctypes.byref(grid), _ptr(pts), np_, _ptr(plan), _stream(stream)))
+
+
+def swense_interp_with_plan(grid, t, pts, np_, plan, eta=None, u=None, v=None, w=None, p=None,
+                            p_mode=P_DYN, rho=1000.0, g=9.81, count_out_of_range=False, stream=None):
+    cnt = ctypes.c_int64(-1)
+    _check(load().swense_interp_with_plan(ctypes.byref(grid), t, _ptr(pts), np_, _ptr(plan), _ptr(eta),
+                                          _ptr(u), _ptr(v), _ptr(w), _ptr(p), p_mode, rho, g,
+                                          ctypes.byref(cnt) if count_out_of_range else None,
+                                          _stream(stream)))
+    return cnt.value if count_out_of_range else None
+
+
 DIRECT_FP32, DIRECT_SPLIT_BF16 = 0, 1
 
 

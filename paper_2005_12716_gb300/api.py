@@ -117,6 +117,29 @@ def interp(grid, t, pts, p_mode="dyn", rho=1000.0, g=9.81, out=None, count_out_o
     return out, cnt
 
 
+def interp_plan(grid, pts, out=None, stream=None):
+    """swense_interp_plan: the gather plan of these points on this grid geometry (a uint8 device
+    tensor), reusable while neither changes."""
+    n = pts.shape[0]
+    plan = out if out is not None else torch.empty(max(1, S.swense_interp_plan_bytes(n)),
+                                                   dtype=torch.uint8, device=pts.device)
+    S.swense_interp_plan(grid.c_struct(), pts, n, plan, stream)
+    return plan
+
+
+def interp_with_plan(grid, t, pts, plan, p_mode="dyn", rho=1000.0, g=9.81, out=None,
+                     count_out_of_range=False, stream=None):
+    """swense_interp_with_plan: swense_interp reusing a plan from interp_plan."""
+    n = pts.shape[0]
+    if out is None:
+        out = {k: torch.empty(n, dtype=torch.float32, device=pts.device)
+               for k in ("eta", "u", "v", "w", "p")}
+    cnt = S.swense_interp_with_plan(grid.c_struct(), float(t), pts, n, plan, out.get("eta"),
+                                    out.get("u"), out.get("v"), out.get("w"), out.get("p"),
+                                    S.P_MODES[p_mode], rho, g, count_out_of_range, stream)
+    return out, cnt
+
+
 def direct(modes, t, pts, p_mode="dyn", rho=1000.0, g=9.81, precision="fp32", out=None,
            stream=None):
     """swense_direct: exact modal sums at the points; returns dict of float32 device tensors."""

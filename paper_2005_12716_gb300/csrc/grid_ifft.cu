@@ -1358,6 +1358,17 @@ extern "C" int swense_autotune_grid(const swense_modes* md, int32_t n_tl, const 
     SWENSE_CUDA_TRY(cudaEventCreate(&e0));
     SWENSE_CUDA_TRY(cudaEventCreate(&e1));
     float best_ms = 1e30f;
+    // Every timed repetition starts from a cold L2, as a solver's step does (its other work
+    // evicts the grid): the workspace, sized for the largest candidate and at least twice the
+    // L2, is overwritten before each repetition (its contents are scratch).
+    constexpr size_t kFlushBytes = size_t(256) << 20;
+    const size_t max_chunk = std::max<size_t>(1, std::min<size_t>(p.nz, (size_t(256) << 20) / p.per_level));
+    const size_t ws_all = std::max(scratch_bytes(p, int(max_chunk)), kFlushBytes);
+    {
+      void* ws = nullptr;
+      st = workspace(ws_all, stream, &ws);
+      if (st) return st;
+    }
     for (int lpc : {0, 1, 2, 4})
     for (int rowv : {0, 1, 2, 3}) {
       const bool wp = warp_path(p.ny, p.Nxr, p.Nyr), pp = pair_path(p.ny, p.Nxr, p.Nyr);
@@ -1369,15 +1380,17 @@ extern "C" int swense_autotune_grid(const swense_modes* md, int32_t n_tl, const 
         const size_t cb = mb << 20;
         const int chunk = int(std::max<size_t>(1, std::min<size_t>(p.nz, cb / p.per_level)));
         void* ws = nullptr;
-        st = workspace(scratch_bytes(p, chunk), stream, &ws);
+        st = workspace(ws_all, stream, &ws);
         if (!st) st = launch_grid(p, md, t, nodes, eta, ws, chunk, stream, lpc, rowv);   // warm
-        float ms = 0.f, tot = 0.f;
-        for (int rep = 0; rep < 3 && !st; ++rep) {
+        // best of five (the fastest repetition is the least disturbed one)
+        float ms = 0.f, tot = 1e30f;
+        for (int rep = 0; rep < 5 && !st; ++rep) {
+          if (cudaMemsetAsync(ws, 0, kFlushBytes, stream) != cudaSuccess) { st = SWENSE_ERR_CUDA; break; }
           if (cudaEventRecord(e0, stream) != cudaSuccess) { st = SWENSE_ERR_CUDA; break; }
           st = launch_grid(p, md, t, nodes, eta, ws, chunk, stream, lpc, rowv);
           if (cudaEventRecord(e1, stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
               cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) st = SWENSE_ERR_CUDA;
-          tot += ms;
+          tot = std::min(tot, ms);
         }
         if (st) break;
         if (tot < best_ms) {

@@ -985,16 +985,19 @@ extern "C" int swense_interp_learned(const swense_grid* g, double t, const float
 namespace swense {
 namespace {
 
+// plan_in: a plan made earlier by swense_interp_plan for these points and this grid geometry
+// (NULL: make one in the workspace first).
 int interp_impl(const swense_grid* g, double t, const float* pts, const int32_t* perm, int64_t np,
                 float* eta, float* u, float* v, float* w, float* p, int32_t p_mode, double rho,
-                double grav, int64_t* n_out_of_range, cudaStream_t stream) {
+                double grav, int64_t* n_out_of_range, cudaStream_t stream,
+                const int4* plan_in = nullptr) {
   InterpArgs a;
   Levels lev;
   int st = prepare_interp(g, t, pts, np, p_mode, rho, grav, &a, &lev);
   if (st) return st;
   // workspace: [0, 256) out-of-range counter, then one int4 box plan per 1024-point chunk
   void* ws = nullptr;
-  st = workspace(256 + size_t((np + BOX_PTS - 1) / BOX_PTS) * sizeof(int4), stream, &ws);
+  st = workspace(256 + (plan_in ? 0 : size_t((np + BOX_PTS - 1) / BOX_PTS) * sizeof(int4)), stream, &ws);
   if (st) return st;
   unsigned long long* d_count = nullptr;
   if (n_out_of_range) {
@@ -1011,14 +1014,19 @@ int interp_impl(const swense_grid* g, double t, const float* pts, const int32_t*
     a.perm = perm;
     const int64_t blocks = (np + BOX_PTS - 1) / BOX_PTS;
     if (blocks >= (int64_t(1) << 31)) return fail(SWENSE_ERR_SIZE, "too many points for one call");
-    int4* plan = reinterpret_cast<int4*>(static_cast<char*>(ws) + 256);
-    k_interp_plan<<<unsigned(blocks), BOX_THREADS, 0, stream>>>(a, lev, plan);
-    SWENSE_CUDA_TRY(cudaGetLastError());
+    const int4* plan = plan_in;
+    if (!plan) {
+      int4* pw = reinterpret_cast<int4*>(static_cast<char*>(ws) + 256);
+      k_interp_plan<<<unsigned(blocks), BOX_THREADS, 0, stream>>>(a, lev, pw);
+      SWENSE_CUDA_TRY(cudaGetLastError());
+      count_launches(1);
+      plan = pw;
+    }
     SWENSE_CUDA_TRY(cudaFuncSetAttribute((const void*)k_interp_box,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, int(BOX_SMEM)));
     k_interp_box<<<unsigned(blocks), BOX_THREADS, BOX_SMEM, stream>>>(a, lev, plan);
     SWENSE_CUDA_TRY(cudaGetLastError());
-    count_launches(2);
+    count_launches(1);
   }
   if (n_out_of_range) {
     unsigned long long h = 0;
@@ -1031,6 +1039,38 @@ int interp_impl(const swense_grid* g, double t, const float* pts, const int32_t*
 
 }  // namespace
 }  // namespace swense
+
+extern "C" int64_t swense_interp_plan_bytes(int64_t np) {
+  return np <= 0 ? 0 : ((np + BOX_PTS - 1) / BOX_PTS) * int64_t(sizeof(int4));
+}
+
+extern "C" int swense_interp_plan(const swense_grid* g, const float* pts, int64_t np, void* plan,
+                                  void* stream_) {
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+  InterpArgs a;
+  Levels lev;
+  const double t0 = g && g->t_levels ? g->t_levels[0] : 0.0;
+  int st = prepare_interp(g, t0, pts, np, SWENSE_P_DYN, 1.0, 1.0, &a, &lev);
+  if (st) return st;
+  if (np == 0) return SWENSE_OK;
+  if (!plan || (reinterpret_cast<uintptr_t>(plan) & 15)) return fail(SWENSE_ERR_ARG, "plan must be non-NULL and 16-byte aligned");
+  const int64_t blocks = (np + BOX_PTS - 1) / BOX_PTS;
+  if (blocks >= (int64_t(1) << 31)) return fail(SWENSE_ERR_SIZE, "too many points for one call");
+  k_interp_plan<<<unsigned(blocks), BOX_THREADS, 0, stream>>>(a, lev, static_cast<int4*>(plan));
+  SWENSE_CUDA_TRY(cudaGetLastError());
+  count_launches(1);
+  return SWENSE_OK;
+}
+
+extern "C" int swense_interp_with_plan(const swense_grid* g, double t, const float* pts, int64_t np,
+                                       const void* plan, float* eta, float* u, float* v, float* w,
+                                       float* p, int32_t p_mode, double rho, double grav,
+                                       int64_t* n_out_of_range, void* stream) {
+  if (np > 0 && (!plan || (reinterpret_cast<uintptr_t>(plan) & 15)))
+    return fail(SWENSE_ERR_ARG, "plan must be non-NULL and 16-byte aligned");
+  return interp_impl(g, t, pts, nullptr, np, eta, u, v, w, p, p_mode, rho, grav, n_out_of_range,
+                     static_cast<cudaStream_t>(stream), static_cast<const int4*>(plan));
+}
 
 extern "C" int swense_interp(const swense_grid* g, double t, const float* pts, int64_t np,
                              float* eta, float* u, float* v, float* w, float* p, int32_t p_mode,

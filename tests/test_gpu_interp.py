@@ -156,3 +156,31 @@ def test_fv_divergence_parity(api):
     flux = np.abs(np.einsum("fk,fk->f", vel.astype(np.float64), area.astype(np.float64)))
     scale = np.max(flux[np.abs(m["cell_faces"]) - 1].sum(1) / vol)
     assert np.max(np.abs(got - ref)) / scale <= TOL
+
+
+def test_reusable_plan_equals_plain_call(api):
+    """swense_interp_plan + swense_interp_with_plan give exactly swense_interp's results, and one
+    plan serves other times and other field values on the same grid geometry."""
+    import torch
+    cfg = configs.jonswap3d_small(n_tl=4)
+    sea, z, tl = cfg["sea"], cfg["z_levels"], cfg["t_levels"]
+    pts = torch.from_numpy(configs.mesh_points(cfg["mesh"])).cuda()
+    grid = api.fields_on_grid(api.upload_modes(sea), z, 2, tl)
+    plan = api.interp_plan(grid, pts)
+    for t in (cfg["t_query"], float(tl[1]) + 0.01):
+        ref, cref = api.interp(grid, t, pts, count_out_of_range=True)
+        got, cgot = api.interp_with_plan(grid, t, pts, plan, count_out_of_range=True)
+        assert cgot == cref
+        for k in ("eta", "u", "v", "w", "p"):
+            assert torch.equal(torch.nan_to_num(got[k], 7.0), torch.nan_to_num(ref[k], 7.0)), k
+    # another sea on the same grid geometry
+    sea2 = seas.jonswap_sea(sea["nx"], sea["ny"], sea["Lx"], sea["Ly"], 0.03, 1.0, seed=77)
+    grid2 = api.fields_on_grid(api.upload_modes(sea2), z, 2, tl)
+    ref, _ = api.interp(grid2, cfg["t_query"], pts)
+    got, _ = api.interp_with_plan(grid2, cfg["t_query"], pts, plan)
+    for k in ("eta", "u", "v", "w", "p"):
+        assert torch.equal(torch.nan_to_num(got[k], 7.0), torch.nan_to_num(ref[k], 7.0)), k
+    # no points
+    empty = torch.empty((0, 3), device="cuda")
+    got, _ = api.interp_with_plan(grid, cfg["t_query"], empty, api.interp_plan(grid, empty))
+    assert all(v.numel() == 0 for v in got.values())
