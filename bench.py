@@ -238,7 +238,7 @@ def kernel_source_hash(files=("csrc/interp.cu", "csrc/internal.cuh", "../include
 # the hash of the kernel's sources and the workload they were taken on; a changed kernel or
 # workload invalidates them (traffic is then reported as null).
 NCU_TRAFFIC = {
-    "k_interp_box": {"bytes": 114905344 + 116937472, "hash": "9d79ae4f1f5c544e",
+    "k_interp_box": {"bytes": 114949888 + 117129984, "hash": "516769e7b0a33424",
                      "workload": "jonswap3d: 512x256 modes, 64 levels, pad 1, 2 time levels, "
                                  "2048000 cell + 6177280 face centres (cylinder O-grid)"},
 }
@@ -700,10 +700,33 @@ def run_e1(args, rank, world):
         o, _ = api.interp(grid, 0.0, fc)
         d = api.fv_divergence(o["u"], o["v"], o["w"], area, cf, vol)
         res[pad] = float(torch.sqrt(torch.mean(d[below].double() ** 2)).item())
+    # the divergence kernel's own speed on the 3-D cylinder mesh (2,048,000 cells, gathered
+    # face velocities, areas and cell-face lists)
+    from paper_2005_12716_gb300 import _swense as S
+    c3 = configs.jonswap3d()
+    m3 = c3["mesh"]
+    g3 = api.fields_on_grid(api.upload_modes(c3["sea"], dev), c3["z_levels"], 1, c3["t_levels"])
+    o3, _ = api.interp(g3, c3["t_query"], dv(m3["face_centres"].astype(np.float32)))
+    a3, cf3 = dv(m3["face_area"].astype(np.float32)), dv(m3["cell_faces"])
+    v3 = dv(m3["cell_volume"].astype(np.float32))
+    div3 = torch.empty(len(m3["cell_volume"]), dtype=torch.float32, device=dev)
+    fn = lambda: api.fv_divergence(o3["u"], o3["v"], o3["w"], a3, cf3, v3, out=div3)  # noqa: E731
+    for _ in range(3):
+        fn()
+    l0 = S.swense_launches()
+    ms = _time_events(fn, 20, torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev))
+    launches = S.swense_launches() - l0
+    nc = len(m3["cell_volume"])
+    nbytes = nc * (6 * (12 + 12 + 4) + 4 + 4)       # per cell: 6 faces (u v w, area, index), volume, out
     line = {"metric": "RMS velocity divergence of the interpolated field [1/s]",
             "config": {"workload": "e1: 2-D JONSWAP Tp 0.7 s, Hs 0.028 m, 128 modes, FV mesh "
                                    "dx = lambda_p/100, dz = Hs/20, cells below -Hs"},
-            "rms_by_pad": res, "ratio_pad1_over_pad4": res[1] / res[4]}
+            "rms_by_pad": res, "ratio_pad1_over_pad4": res[1] / res[4],
+            "fv_divergence_kernel": {"cells": nc, "ms": ms, "cells_per_s": nc / (ms * 1e-3),
+                                     "achieved_gbs": nbytes / (ms * 1e-3) / 1e9,
+                                     "frac_hbm": nbytes / (ms * 1e-3) / 1e9 / _peak_hbm(),
+                                     "gpu_launches": int(launches),
+                                     "mesh": "jonswap3d cylinder O-grid, face values gathered per cell"}}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
