@@ -364,3 +364,25 @@ def test_spline_interp_converges_fourth_order():
         out = interp.interp_points_spline(nodes[None], eta[None], 6.0, 3.0, z, [0.0], pts, 0.0)
         errs.append(np.max(np.abs(out["eta"] - exact["eta"])) / np.max(np.abs(exact["eta"])))
     assert errs[1] < errs[0] / 10
+
+
+def test_e1_workload_restates_the_papers_printed_setup():
+    """The divergence-demonstration workload carries the set-up the paper prints for it
+    (golden fixture), and the mesh spacing it builds is the stated one."""
+    import json
+    import os
+    from wavegen import configs
+    with open(os.path.join(os.path.dirname(__file__), "golden", "paper_zero_padding_divergence.json")) as fh:
+        paper = json.load(fh)
+    cfg = configs.e1_divergence()
+    assert cfg["sea"]["nx"] == paper["sea"]["hos_modes"]
+    assert abs(cfg["Tp"] - paper["sea"]["Tp_s"]) < 1e-12 and abs(cfg["Hs"] - paper["sea"]["Hs_m"]) < 1e-12
+    assert abs(cfg["sea"]["Lx"] / cfg["lambda_p"] - paper["sea"]["domain_peak_wavelengths"]) < 1e-9
+    # deep-water peak wavelength from the printed period: lambda = g T^2 / (2 pi)
+    assert abs(cfg["lambda_p"] - 9.81 * 0.7 ** 2 / (2 * np.pi)) < 1e-12
+    fc = cfg["mesh"]["cell_centres"]
+    xs = np.unique(np.round(fc[:, 0], 9))
+    zs = np.unique(np.round(fc[:, 2], 9))
+    assert np.allclose(np.diff(xs), paper["cfd_mesh"]["dx_over_lambda_p"] * cfg["lambda_p"], rtol=1e-6)
+    assert np.allclose(np.diff(zs), paper["cfd_mesh"]["dz_over_Hs"] * cfg["Hs"], rtol=1e-6)
+    assert paper["refinement_factor"] * cfg["sea"]["nx"] == paper["reconstruction_points_after_refinement"]

@@ -107,7 +107,8 @@ def e1_divergence(pad_n=1, window_lp=2.0, levels=64, seed=SEED0 + 6):
     z_edges = np.arange(z_lo, z_hi + 1e-12, Hs / 20)
     mesh = M.box_xz_mesh(x_edges, z_edges)
     return {"name": "e1_divergence", "sea": sea, "z_levels": z, "pad_n": pad_n, "mesh": mesh,
-            "t_levels": np.array([0.0]), "t_query": 0.0, "lambda_p": lp, "Hs": Hs}
+            "t_levels": np.array([0.0]), "t_query": 0.0, "lambda_p": lp, "Hs": Hs, "Tp": Tp,
+            "dx": lp / 100, "dz": Hs / 20}
 
 
 def morton_order(pts, Lx, Ly, z_lo, z_hi, bits=10):
