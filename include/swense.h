@@ -165,7 +165,8 @@ int swense_fields_on_grid_noalloc(const swense_modes* modes, int32_t n_tl, const
  * single path (nothing to tune; *lpc_out = -1).
  * lpc_out (0 = shared-memory path), chunk_bytes_out, row_variant_out (0 = both field pairs per
  * warp, 1 = one field pair per block, 2 = transposed intermediate: the row pass reads its inputs
- * straight from memory; both lengths in 256..1024; 3 = as 2 with one transform per warp):
+ * straight from memory; both lengths in 256..1024; 3 = as 2 with one transform per warp;
+ * 4 = as 2 with each warp's rows staged in shared memory by bulk asynchronous copies):
  * host, may be NULL. Errors: as swense_fields_on_grid.
  */
 int swense_autotune_grid(const swense_modes* modes, int32_t n_tl, const double* t,
@@ -178,7 +179,7 @@ int swense_autotune_grid(const swense_modes* modes, int32_t n_tl, const double* 
  * (nx, ny, pad_n, nz), e.g. a choice that swense_autotune_grid returned in an earlier process.
  * lpc: -1 (forget any choice: untuned defaults again), 0 (shared-memory path), 1, 2 or 4 levels
  * per column block;
- * chunk_bytes in [1 MiB, 1 GiB] (L2-resident level chunk); row_variant 0..3 (as returned by
+ * chunk_bytes in [1 MiB, 1 GiB] (L2-resident level chunk); row_variant 0..4 (as returned by
  * swense_autotune_grid). Results do not depend on the choice beyond FP32 rounding. No
  * counterpart in the paper. Errors: SWENSE_ERR_ARG for values outside those sets.
  */

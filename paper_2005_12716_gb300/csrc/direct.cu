@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(kDirThreads) k_direct_fp32(DirectArgs a) {
 // Lane (g, q) of a k-step holds modes q and q + 4 (deep) or mode q in its a and b halves.
 struct SplitStep {
   uint4 b[32];      // per lane: (b0 hi, b1 hi, b0 lo, b1 lo)
-  float4 info[8];   // per mode of the step: (|k|, 1 / (1 + e^{-2kh}), W_eta)
+  float4 info[8];   // per mode of the step: (|k| log2 e, 1 / (1 + e^{-2kh}), W_eta)
 };
 static_assert(sizeof(SplitStep) == 640, "split step record");
 
@@ -220,6 +220,13 @@ constexpr int kSplitThreads = 256;
 constexpr int kSplitTiles = 2;     // 16-point MMA tiles per warp
 constexpr int kSplitStage = 32;    // k-steps per shared-memory stage (double-buffered)
 constexpr int kSplitAnchor = 16;   // exact phase every this many k-steps
+
+// 2^x (PTX ex2.approx: relative error about 2^-22, far below the split products' 2^-16)
+__device__ __forceinline__ float ex2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 
 __device__ __forceinline__ float2 pick_w(const SlotCoef& sc, int c) {
   return c == 0 ? sc.wu : c == 1 ? sc.wv : c == 2 ? sc.ww : c == 3 ? sc.wt : make_float2(0.f, 0.f);
@@ -258,7 +265,7 @@ __global__ void k_direct_prep_split(const float2* __restrict__ Ae, const float2*
     float4 inf = make_float4(0.f, 1.f, 0.f, 0.f);
     if (L < km) {
       const SlotCoef sc = coef(L);
-      if (sc.live) inf = make_float4(sc.k, sc.invd, sc.we.x, sc.we.y);
+      if (sc.live) inf = make_float4(sc.k * 1.4426950408889634f, sc.invd, sc.we.x, sc.we.y);
     }
     out[s].info[L] = inf;
   }
@@ -325,6 +332,7 @@ __global__ void __launch_bounds__(kSplitThreads, 2) k_direct_split(SplitArgs a) 
     cp_async_commit();
   };
   load_chunk(0);
+  int ri = 0, sidx = 0;                             // table row and step within it of step s
   for (int c = 0; c < nchunks; ++c) {
     if (c + 1 < nchunks) {
       load_chunk(c + 1);
@@ -343,8 +351,6 @@ __global__ void __launch_bounds__(kSplitThreads, 2) k_direct_split(SplitArgs a) 
       eta_acc[t][0] = eta_acc[t][1] = 0.f;
     }
     for (int sl = 0; sl < cnt; ++sl) {
-      const int s = c * kSplitStage + sl;
-      const int ri = s / a.spr, sidx = s - ri * a.spr;
       if (sidx % kSplitAnchor == 0) {
         // exact phase (m X + n Y) mod 2^32 of this lane's modes
         const int r = (a.ny > 1 && ri >= a.ny / 2) ? ri + 1 : ri;
@@ -384,15 +390,15 @@ __global__ void __launch_bounds__(kSplitThreads, 2) k_direct_split(SplitArgs a) 
           if constexpr (!FINITE) {
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
-              const float f = __expf(inf[j].x * zz);
+              const float f = ex2(inf[j].x * zz);
               v[j][h][0] = pc[t][h][j] * f;
               v[j][h][1] = ps[t][h][j] * f;
               eta_acc[t][h] = fmaf(inf[j].z, pc[t][h][j], fmaf(-inf[j].w, ps[t][h][j], eta_acc[t][h]));
             }
           } else {
             const float k = inf[0].x;
-            const float fa = __expf(k * zz) * inf[0].y;
-            const float fb = fa * __expf(-2.f * k * (zz + a.depth));
+            const float fa = ex2(k * zz) * inf[0].y;
+            const float fb = fa * ex2(-2.f * k * (zz + a.depth));
             v[0][h][0] = pc[t][h][0] * fa;
             v[0][h][1] = ps[t][h][0] * fa;
             v[1][h][0] = pc[t][h][0] * fb;
@@ -408,6 +414,10 @@ __global__ void __launch_bounds__(kSplitThreads, 2) k_direct_split(SplitArgs a) 
         mma16816(acc[t], ahi, bf.x, bf.y);
         mma16816(acc[t], ahi, bf.z, bf.w);
         mma16816(acc[t], alo, bf.x, bf.y);
+      }
+      if (++sidx == a.spr) {                       // next step: next table row
+        sidx = 0;
+        ++ri;
       }
     }
 #pragma unroll

@@ -24,6 +24,7 @@
 
 #include "fft.cuh"
 #include "internal.cuh"
+#include "tma.cuh"
 
 namespace swense {
 namespace {
@@ -846,6 +847,93 @@ __global__ void __launch_bounds__(256, N >= 8192 ? 1 : 2) k_row_tb(RowArgs a) {
   }
 }
 
+// Row pass over the transposed intermediate with its inputs staged by bulk copies: each warp
+// takes `rpw` consecutive rows of one level; lane 0 copies a row's four field segments
+// (ldG complex values each, contiguous in G) into the warp's staging buffer with cp.async.bulk
+// on the warp's mbarrier, and the next row's copy runs while the current row is transformed.
+// A wait that does not complete within its bound sets the device error flag and ends the warp
+// (after waiting, also bounded, for a copy it still has in flight).
+__device__ int g_async_timeout;
+
+template <int N>
+__global__ void __launch_bounds__(256, N >= 1024 ? 1 : 2) k_row_tma(RowArgs a, int rpw) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  constexpr int E = N / 32, RL = stk_radix(N, stk_npass(N) - 1);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned span = unsigned(a.ldG) * unsigned(sizeof(float2));      // bytes per field row
+  const size_t per_warp = 4 * size_t(span) + size_t(stk_buf(N)) * sizeof(float2);
+  float2* stg = reinterpret_cast<float2*>(smraw + warp * per_warp);
+  float2* xbuf = reinterpret_cast<float2*>(smraw + warp * per_warp + 4 * size_t(span));
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smraw + (kThreads / 32) * per_warp) + warp;
+  const int level = blockIdx.y;
+  const int y0 = (blockIdx.x * (kThreads / 32) + warp) * rpw;
+  const int nrows = min(rpw, a.Nyr - y0);
+  if (nrows <= 0) return;                        // no block-wide barrier in this kernel
+  const size_t fs = size_t(a.Nyr) * a.ldG;
+  const float2* Gl = a.G + size_t(level) * 4 * fs;
+  if (lane == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+    fence_proxy_async();
+  }
+  __syncwarp();
+  auto issue = [&](int i) {
+    if (lane == 0) {
+      fence_proxy_async();                       // earlier reads of the buffer come first
+      mbar_arrive_expect_tx(bar, 4 * span);
+      const float2* src = Gl + size_t(y0 + i) * a.ldG;
+#pragma unroll
+      for (int f = 0; f < 4; ++f) bulk_g2s(stg + f * a.ldG, src + f * fs, span, bar);
+    }
+  };
+  issue(0);
+  float2 T[stk_twn(N)];
+  stk_init<N>(T, a.tw, lane);
+  for (int i = 0; i < nrows; ++i) {
+    if (!mbar_wait(bar, unsigned(i) & 1u)) {
+      if (lane == 0) atomicExch(&g_async_timeout, 1);
+      mbar_wait(bar, unsigned(i) & 1u);          // the copy waited on is the only one in flight
+      return;
+    }
+    float2 z1[E], z2[E];
+    const float2* U = stg;
+    const float2* V = stg + a.ldG;
+    const float2* W = stg + 2 * a.ldG;
+    const float2* Tt = stg + 3 * a.ldG;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int p = lane + 32 * (e / 8) + (e % 8) * (N / 8);
+      const bool lo = p < a.Mh, hi = p > N - a.Mh;
+      float2 u = make_float2(0.f, 0.f), v = u, w = u, t = u;
+      if (lo || hi) {
+        const int mm = lo ? p : N - p;
+        u = U[mm];
+        v = V[mm];
+        w = W[mm];
+        t = Tt[mm];
+      }
+      if (p == 0) {
+        z1[e] = make_float2(u.x, v.x);
+        z2[e] = make_float2(w.x, t.x);
+      } else if (!hi) {
+        z1[e] = make_float2(u.x - v.y, u.y + v.x);
+        z2[e] = make_float2(w.x - t.y, w.y + t.x);
+      } else {
+        z1[e] = make_float2(u.x + v.y, v.x - u.y);
+        z2[e] = make_float2(w.x + t.y, t.x - w.y);
+      }
+    }
+    __syncwarp();                                // every lane has read the staged row
+    if (i + 1 < nrows) issue(i + 1);
+    stk_fft<N>(z1, T, a.tw, xbuf, lane);
+    stk_fft<N>(z2, T, a.tw, xbuf, lane);
+    float4* out = a.nodes + (size_t(a.lev0 + level) * a.Nyr + y0 + i) * N;
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+      __stcs(&out[lane + 32 * (e / RL) + (e % RL) * (N / RL)], make_float4(z1[e].x, z1[e].y, z2[e].x, z2[e].y));
+  }
+}
+
 // Launch-shape choices of the warp-register path, per grid shape (set by swense_autotune_grid;
 // defaults otherwise).
 struct Tune {
@@ -937,6 +1025,21 @@ int launch_row_tb(const RowArgs& r, unsigned nl, cudaStream_t stream) {
   return SWENSE_OK;
 }
 
+constexpr int kRowsPerWarp = 2;     // rows a warp of the staged row pass takes in turn
+
+template <int N>
+int launch_row_tma(const RowArgs& r, unsigned nl, cudaStream_t stream) {
+  const size_t per_warp = 4 * size_t(r.ldG) * sizeof(float2) + size_t(stk_buf(N)) * sizeof(float2);
+  const size_t smem = (kThreads / 32) * per_warp + (kThreads / 32) * sizeof(uint64_t);
+  int st = set_smem((const void*)k_row_tma<N>, smem);
+  if (st) return st;
+  const unsigned per_block = (kThreads / 32) * kRowsPerWarp;
+  k_row_tma<N><<<dim3((unsigned(r.Nyr) + per_block - 1) / per_block, nl), kThreads, smem, stream>>>(r, kRowsPerWarp);
+  SWENSE_CUDA_TRY(cudaGetLastError());
+  count_launches(1);
+  return SWENSE_OK;
+}
+
 template <int N>
 int launch_row_t2(const RowArgs& r, dim3 grid, cudaStream_t stream) {
   const size_t smem = size_t(8) * stk_buf(N) * sizeof(float2);
@@ -951,7 +1054,7 @@ int launch_row_t2(const RowArgs& r, dim3 grid, cudaStream_t stream) {
 // Transposed-intermediate pair (row variants 2 and 3): both transform lengths in 256..1024;
 // variant 3 runs one transform per warp in the row pass.
 int launch_pair_t(const ColArgs& c, const RowArgs& r, const Levels& L, int nl, cudaStream_t s,
-                  bool one_per_warp) {
+                  bool one_per_warp, bool staged = false) {
   const dim3 gc(unsigned((c.Mh + kColBlock - 1) / kColBlock), unsigned((nl + c.lpc - 1) / c.lpc));
   const dim3 gr(unsigned((r.Nyr + 7) / 8), unsigned(nl));
   const dim3 gr2(unsigned((r.Nyr + 3) / 4), unsigned(nl));
@@ -968,6 +1071,14 @@ int launch_pair_t(const ColArgs& c, const RowArgs& r, const Levels& L, int nl, c
     case 4096: return launch_row_tb<4096>(r, unsigned(nl), s);
     case 8192: return launch_row_tb<8192>(r, unsigned(nl), s);
     default: break;
+  }
+  if (staged) {
+    switch (r.Nxr) {
+      case 256: return launch_row_tma<256>(r, unsigned(nl), s);
+      case 512: return launch_row_tma<512>(r, unsigned(nl), s);
+      case 1024: return launch_row_tma<1024>(r, unsigned(nl), s);
+      default: return fail(SWENSE_ERR_UNSUPPORTED, "staged row pass: row length");
+    }
   }
   if (one_per_warp) {
     switch (r.Nxr) {
@@ -1240,7 +1351,7 @@ int launch_grid(const GridPlan& p, const swense_modes* md, const double* t, floa
     SWENSE_CUDA_TRY(cudaGetLastError());
     count_launches(1);
 
-    if (lpc > 0 && (warp_path(ny, Nxr, Nyr) || (pair_path(ny, Nxr, Nyr) && (rowv == 2 || rowv == 3)))) {
+    if (lpc > 0 && (warp_path(ny, Nxr, Nyr) || (pair_path(ny, Nxr, Nyr) && rowv >= 2))) {
       ColArgs ca{};
       ca.A_phi = Ap;
       ca.A_phit = At;
@@ -1268,7 +1379,7 @@ int launch_grid(const GridPlan& p, const swense_modes* md, const double* t, floa
       const size_t smem_col = size_t(2) * ny * (kColBlock + 1) * sizeof(float2);
       const size_t smem_row = size_t(4) * Mh * (kRowBlock + 1) * sizeof(float2);
       ca.ldG = ra.ldG = (Mh + 3) & ~3;
-      const bool pair_t = (rowv == 2 || rowv == 3) && pair_path(ny, Nxr, Nyr);
+      const bool pair_t = (rowv == 2 || rowv == 3 || (rowv == 4 && Nxr <= 1024)) && pair_path(ny, Nxr, Nyr);
   
       for (int l0 = 0; l0 < nz; l0 += chunk) {
         if (pair_t) {
@@ -1276,7 +1387,7 @@ int launch_grid(const GridPlan& p, const swense_modes* md, const double* t, floa
           ca.lev0 = l0;
           ca.nlev = nl;
           ra.lev0 = l0;
-          int st = launch_pair_t(ca, ra, p.lev, nl, stream, rowv == 3);
+          int st = launch_pair_t(ca, ra, p.lev, nl, stream, rowv == 3, rowv == 4);
           if (st) return st;
           continue;
         }
@@ -1370,12 +1481,13 @@ extern "C" int swense_autotune_grid(const swense_modes* md, int32_t n_tl, const 
       if (st) return st;
     }
     for (int lpc : {0, 1, 2, 4})
-    for (int rowv : {0, 1, 2, 3}) {
+    for (int rowv : {0, 1, 2, 3, 4}) {
       const bool wp = warp_path(p.ny, p.Nxr, p.Nyr), pp = pair_path(p.ny, p.Nxr, p.Nyr);
       if (lpc > 0 && !wp && !(pp && rowv == 2)) continue;
       if (rowv && (lpc == 0 || p.Nxr < 256)) continue;   // only the Stockham row sizes have variants
       if (rowv >= 2 && !pp) continue;
       if (!wp && rowv != 2 && lpc > 0) continue;
+      if (rowv == 4 && p.Nxr > 1024) continue;
       for (size_t mb : {16, 32, 64, 96, 128, 256}) {
         const size_t cb = mb << 20;
         const int chunk = int(std::max<size_t>(1, std::min<size_t>(p.nz, cb / p.per_level)));
@@ -1420,7 +1532,7 @@ extern "C" int swense_set_grid_tune(int32_t nx, int32_t ny, int32_t pad_n, int32
     return fail(SWENSE_ERR_ARG, "lpc must be -1 (default), 0, 1, 2 or 4");
   if (chunk_bytes < (int64_t(1) << 20) || chunk_bytes > (int64_t(1) << 30))
     return fail(SWENSE_ERR_ARG, "chunk_bytes must be in [1 MiB, 1 GiB]");
-  if (row_variant < 0 || row_variant > 3) return fail(SWENSE_ERR_ARG, "row_variant must be 0, 1, 2 or 3");
+  if (row_variant < 0 || row_variant > 4) return fail(SWENSE_ERR_ARG, "row_variant must be 0..4");
   std::lock_guard<std::mutex> lock(g_tune_mutex);
   if (lpc == -1) {                      // back to the untuned defaults for this shape
     g_tune.erase({nx, ny, pad_n, nz});

@@ -126,12 +126,13 @@ def test_every_launch_shape_matches_oracle(api, lpc, rowv, chunk_mb, shape):
     _forced(api, lpc, rowv, chunk_mb, shape)
 
 
-@pytest.mark.parametrize("rowv", [2, 3])
+@pytest.mark.parametrize("rowv", [2, 3, 4])
 @pytest.mark.parametrize("lpc,chunk_mb", [(1, 1), (4, 32)])
 @pytest.mark.parametrize("shape", [(256, 256, 1), (512, 128, 2), (128, 512, 2), (256, 512, 1)])
 def test_transposed_pair_matches_oracle(api, lpc, chunk_mb, shape, rowv):
-    """Row variants 2 and 3 (transposed intermediate; both transforms or one per warp in the row
-    pass) for 256-, 512- and 1024-point columns and rows."""
+    """Row variants 2, 3 and 4 (transposed intermediate; both transforms or one per warp in the
+    row pass, or rows staged by bulk asynchronous copies) for 256-, 512- and 1024-point columns
+    and rows."""
     _forced(api, lpc, rowv, chunk_mb, shape)
 
 
