@@ -315,17 +315,18 @@ __device__ __forceinline__ void stage_box(const InterpArgs& a, int x0, int y0, i
 __global__ void __launch_bounds__(BOX_THREADS) k_interp_plan(InterpArgs a, Levels L, int4* __restrict__ plan) {
   __shared__ LevelTables zs;
   __shared__ int s_red[6][BOX_THREADS / 32];
-  __shared__ int s_ref[2];
   fill_level_tables(zs, L, a.nz);
   const int64_t p0 = int64_t(blockIdx.x) * BOX_PTS;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    const PointCell c = point_cell(a, zs, a.pts[3 * p0], a.pts[3 * p0 + 1], a.pts[3 * p0 + 2]);
-    s_ref[0] = c.ix;
-    s_ref[1] = c.iy;
+  // every thread derives the chunk's reference cell (its first point's) itself: one broadcast
+  // load instead of a wait on one thread
+  int refx, refy;
+  {
+    const PointCell c = point_cell(a, zs, __ldg(&a.pts[3 * p0]), __ldg(&a.pts[3 * p0 + 1]),
+                                   __ldg(&a.pts[3 * p0 + 2]));
+    refx = c.ix;
+    refy = c.iy;
   }
-  __syncthreads();
-  const int refx = s_ref[0], refy = s_ref[1];
   int mn[3] = {1 << 30, 1 << 30, 1 << 30}, mx[3] = {-(1 << 30), -(1 << 30), -(1 << 30)};
 #pragma unroll
   for (int k = 0; k < BOX_PPT; ++k) {
