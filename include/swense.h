@@ -116,8 +116,10 @@ typedef struct swense_grid_desc {
  *   nodes  float [n_tl][nz][ny_r][nx_r][4] = (u, v, w, dphi/dt) per node
  *   eta    float [n_tl][ny_r][nx_r]
  * Arithmetic: FP32 transforms, FP32 depth factors with a compensated |k| z product.
- * Uses the scratch workspace (4 * ny_r * nx/2 complex64 per level of a level chunk) when
- * ny > 1. Errors: ARG, SIZE, LEVELS, OOM, CUDA.
+ * Uses the scratch workspace (4 * ny_r * nx/2 complex64 per level of a level chunk, twice that
+ * for transform variant 5) when ny > 1; the workspace, the twiddle table and variant 5's
+ * second stream are created by the first call on a device, which must not be inside a stream
+ * capture. Errors: ARG, SIZE, LEVELS, OOM, CUDA.
  */
 int swense_fields_on_grid(const swense_modes* modes, int32_t n_tl, const double* t,
                           const swense_grid_desc* desc, float* nodes, float* eta, void* stream);
@@ -166,7 +168,9 @@ int swense_fields_on_grid_noalloc(const swense_modes* modes, int32_t n_tl, const
  * lpc_out (0 = shared-memory path), chunk_bytes_out, row_variant_out (0 = both field pairs per
  * warp, 1 = one field pair per block, 2 = transposed intermediate: the row pass reads its inputs
  * straight from memory; both lengths in 256..1024; 3 = as 2 with one transform per warp;
- * 4 = as 2 with each warp's rows staged in shared memory by bulk asynchronous copies):
+ * 4 = as 2 with each warp's rows staged in shared memory by bulk asynchronous copies; 5 = as 2
+ * with chunk c's row pass on a library-internal second stream while chunk c+1's column pass
+ * runs on `stream`, two intermediate buffers, joined back before the call's work ends):
  * host, may be NULL. Errors: as swense_fields_on_grid.
  */
 int swense_autotune_grid(const swense_modes* modes, int32_t n_tl, const double* t,
@@ -179,7 +183,7 @@ int swense_autotune_grid(const swense_modes* modes, int32_t n_tl, const double* 
  * (nx, ny, pad_n, nz), e.g. a choice that swense_autotune_grid returned in an earlier process.
  * lpc: -1 (forget any choice: untuned defaults again), 0 (shared-memory path), 1, 2 or 4 levels
  * per column block;
- * chunk_bytes in [1 MiB, 1 GiB] (L2-resident level chunk); row_variant 0..4 (as returned by
+ * chunk_bytes in [1 MiB, 1 GiB] (L2-resident level chunk); row_variant 0..5 (as returned by
  * swense_autotune_grid). Results do not depend on the choice beyond FP32 rounding. No
  * counterpart in the paper. Errors: SWENSE_ERR_ARG for values outside those sets.
  */

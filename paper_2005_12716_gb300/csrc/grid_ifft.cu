@@ -1054,18 +1054,20 @@ int launch_row_t2(const RowArgs& r, dim3 grid, cudaStream_t stream) {
 // Transposed-intermediate pair (row variants 2 and 3): both transform lengths in 256..1024;
 // variant 3 runs one transform per warp in the row pass.
 int launch_pair_t(const ColArgs& c, const RowArgs& r, const Levels& L, int nl, cudaStream_t s,
-                  bool one_per_warp, bool staged = false) {
+                  bool one_per_warp, bool staged = false, int which = 0) {
   const dim3 gc(unsigned((c.Mh + kColBlock - 1) / kColBlock), unsigned((nl + c.lpc - 1) / c.lpc));
   const dim3 gr(unsigned((r.Nyr + 7) / 8), unsigned(nl));
   const dim3 gr2(unsigned((r.Nyr + 3) / 4), unsigned(nl));
-  int st;
-  switch (c.Nyr) {
-    case 256: st = launch_col_t<256, 2>(c, L, gc, s); break;
-    case 512: st = launch_col_t<512, 1>(c, L, gc, s); break;
-    case 1024: st = launch_col_t<1024, 1>(c, L, gc, s); break;
-    default: return fail(SWENSE_ERR_UNSUPPORTED, "transposed pair: column length");
+  int st = SWENSE_OK;
+  if (which != 2) {
+    switch (c.Nyr) {
+      case 256: st = launch_col_t<256, 2>(c, L, gc, s); break;
+      case 512: st = launch_col_t<512, 1>(c, L, gc, s); break;
+      case 1024: st = launch_col_t<1024, 1>(c, L, gc, s); break;
+      default: return fail(SWENSE_ERR_UNSUPPORTED, "transposed pair: column length");
+    }
   }
-  if (st) return st;
+  if (st || which == 1) return st;
   switch (r.Nxr) {                               // rows longer than a warp transform
     case 2048: return launch_row_tb<2048>(r, unsigned(nl), s);
     case 4096: return launch_row_tb<4096>(r, unsigned(nl), s);
@@ -1216,14 +1218,42 @@ int plan_grid(const swense_modes* md, int32_t n_tl, const double* t, const swens
 }
 
 // Scratch bytes for a level chunk of `chunk` levels (0 when no scratch is needed).
-size_t scratch_bytes(const GridPlan& p, int chunk) {
+size_t scratch_bytes(const GridPlan& p, int chunk, int nbuf = 1) {
   const size_t g_bytes = p.ny > 1 ? size_t(chunk) * p.per_level : 0;
-  return align256(p.prop_bytes) + align256(p.geta_bytes) + align256(g_bytes);
+  return align256(p.prop_bytes) + align256(p.geta_bytes) + size_t(nbuf) * align256(g_bytes);
+}
+
+// Library-internal second stream and events (per device) for the two-stream transform
+// pipeline: chunk c's row pass runs on the second stream while chunk c+1's column pass runs on
+// the caller's stream, with two intermediate buffers. Created on first use; recording, waiting
+// and launching on them inside a stream capture joins them to the capture (fork/join).
+struct Pipe {
+  cudaStream_t side = nullptr;
+  cudaEvent_t col_done[2] = {nullptr, nullptr}, row_done[2] = {nullptr, nullptr};
+};
+std::mutex g_pipe_mutex;
+std::map<int, Pipe> g_pipe;
+
+int get_pipe(Pipe** out) {
+  int dev = 0;
+  SWENSE_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(g_pipe_mutex);
+  Pipe& pp = g_pipe[dev];
+  if (!pp.side) {
+    SWENSE_CUDA_TRY(cudaStreamCreateWithFlags(&pp.side, cudaStreamNonBlocking));
+    for (int b = 0; b < 2; ++b) {
+      SWENSE_CUDA_TRY(cudaEventCreateWithFlags(&pp.col_done[b], cudaEventDisableTiming));
+      SWENSE_CUDA_TRY(cudaEventCreateWithFlags(&pp.row_done[b], cudaEventDisableTiming));
+    }
+  }
+  *out = &pp;
+  return SWENSE_OK;
 }
 
 // Enqueue every kernel of the request; `ws` holds scratch_bytes(p, chunk) bytes.
 int launch_grid(const GridPlan& p, const swense_modes* md, const double* t, float* nodes, float* eta,
-                void* ws, int chunk, cudaStream_t stream, int lpc = kColLevels, int rowv = 0) {
+                void* ws, int chunk, cudaStream_t stream, int lpc = kColLevels, int rowv = 0,
+                int overlap = 0) {
   const float2* tw = nullptr;
   {
     int st = twiddles(stream, &tw);
@@ -1236,6 +1266,25 @@ int launch_grid(const GridPlan& p, const swense_modes* md, const double* t, floa
   float2* g_eta = reinterpret_cast<float2*>(static_cast<char*>(ws) + align256(p.prop_bytes));
   float2* g_lev = reinterpret_cast<float2*>(static_cast<char*>(ws) + align256(p.prop_bytes) +
                                             align256(p.geta_bytes));
+  // second intermediate buffer of the two-stream pipeline
+  float2* g_lev2 = reinterpret_cast<float2*>(reinterpret_cast<char*>(g_lev) +
+                                             align256(size_t(chunk) * p.per_level));
+  Pipe* pipe = nullptr;
+  const bool use_pipe = overlap && rowv == 2 && pair_path(p.ny, p.Nxr, p.Nyr);
+  if (use_pipe) {
+    int st = get_pipe(&pipe);
+    if (st) return st;
+  }
+  int chunk_no = 0;                              // chunks issued so far (over all time levels)
+  struct Join {                                  // the caller's stream waits for the second one
+    Pipe* pp;
+    int* n;
+    cudaStream_t s;
+    ~Join() {
+      if (!pp) return;
+      for (int b = 0; b < 2 && b < *n; ++b) cudaStreamWaitEvent(s, pp->row_done[b], 0);
+    }
+  } join{use_pipe ? pipe : nullptr, &chunk_no, stream};
 
   const float kxs = float(6.283185307179586476925 / md->Lx);
   const float kys = ny > 1 ? float(6.283185307179586476925 / md->Ly) : 0.f;
@@ -1382,6 +1431,25 @@ int launch_grid(const GridPlan& p, const swense_modes* md, const double* t, floa
       const bool pair_t = (rowv == 2 || rowv == 3 || (rowv == 4 && Nxr <= 1024)) && pair_path(ny, Nxr, Nyr);
   
       for (int l0 = 0; l0 < nz; l0 += chunk) {
+        if (pair_t && use_pipe) {
+          const int nl = std::min(chunk, nz - l0);
+          const int b = chunk_no & 1;
+          ca.lev0 = l0;
+          ca.nlev = nl;
+          ra.lev0 = l0;
+          ca.G = b ? g_lev2 : g_lev;
+          ra.G = ca.G;
+          if (chunk_no >= 2) SWENSE_CUDA_TRY(cudaStreamWaitEvent(stream, pipe->row_done[b], 0));
+          int st = launch_pair_t(ca, ra, p.lev, nl, stream, false, false, 1);   // column pass
+          if (st) return st;
+          SWENSE_CUDA_TRY(cudaEventRecord(pipe->col_done[b], stream));
+          SWENSE_CUDA_TRY(cudaStreamWaitEvent(pipe->side, pipe->col_done[b], 0));
+          st = launch_pair_t(ca, ra, p.lev, nl, pipe->side, false, false, 2);    // row pass
+          if (st) return st;
+          SWENSE_CUDA_TRY(cudaEventRecord(pipe->row_done[b], pipe->side));
+          ++chunk_no;
+          continue;
+        }
         if (pair_t) {
           const int nl = std::min(chunk, nz - l0);
           ca.lev0 = l0;
@@ -1442,17 +1510,18 @@ extern "C" int swense_fields_on_grid(const swense_modes* md, int32_t n_tl, const
   const Tune tn = tuned(p.nx, p.ny, p.pad, p.nz);
   const int chunk = p.ny > 1 ? int(std::max<size_t>(1, std::min<size_t>(p.nz, tn.chunk_bytes / p.per_level))) : 0;
   void* ws = nullptr;
-  const size_t ws_bytes = scratch_bytes(p, chunk);
-  if (ws_bytes) {
-    st = workspace(ws_bytes, stream, &ws);
-    if (st) return st;
-  }
   // untuned default: the transposed Stockham pair where both lengths are 256..1024, else the
   // warp path where its transforms stay in registers (n <= 512), else the shared-memory path
   const bool pair = pair_path(p.ny, p.Nxr, p.Nyr);
   const int lpc = tn.lpc >= 0 ? tn.lpc : (pair ? 4 : ((p.Nxr <= 512 && p.Nyr <= 512) ? kColLevels : 0));
   const int rowv = tn.lpc >= 0 ? tn.rowv : (pair ? 2 : 0);
-  return launch_grid(p, md, t, nodes, eta, ws, chunk, stream, lpc, rowv);
+  // variant 5: variant 2 with its column and row passes pipelined over two streams
+  const size_t ws_bytes = scratch_bytes(p, chunk, rowv == 5 ? 2 : 1);
+  if (ws_bytes) {
+    st = workspace(ws_bytes, stream, &ws);
+    if (st) return st;
+  }
+  return launch_grid(p, md, t, nodes, eta, ws, chunk, stream, lpc, rowv == 5 ? 2 : rowv, rowv == 5);
 }
 
 extern "C" int swense_autotune_grid(const swense_modes* md, int32_t n_tl, const double* t,
@@ -1474,14 +1543,14 @@ extern "C" int swense_autotune_grid(const swense_modes* md, int32_t n_tl, const 
     // L2, is overwritten before each repetition (its contents are scratch).
     constexpr size_t kFlushBytes = size_t(256) << 20;
     const size_t max_chunk = std::max<size_t>(1, std::min<size_t>(p.nz, (size_t(256) << 20) / p.per_level));
-    const size_t ws_all = std::max(scratch_bytes(p, int(max_chunk)), kFlushBytes);
+    const size_t ws_all = std::max(scratch_bytes(p, int(max_chunk), 2), kFlushBytes);
     {
       void* ws = nullptr;
       st = workspace(ws_all, stream, &ws);
       if (st) return st;
     }
     for (int lpc : {0, 1, 2, 4})
-    for (int rowv : {0, 1, 2, 3, 4}) {
+    for (int rowv : {0, 1, 2, 3, 4, 5}) {
       const bool wp = warp_path(p.ny, p.Nxr, p.Nyr), pp = pair_path(p.ny, p.Nxr, p.Nyr);
       if (lpc > 0 && !wp && !(pp && rowv == 2)) continue;
       if (rowv && (lpc == 0 || p.Nxr < 256)) continue;   // only the Stockham row sizes have variants
@@ -1493,13 +1562,14 @@ extern "C" int swense_autotune_grid(const swense_modes* md, int32_t n_tl, const 
         const int chunk = int(std::max<size_t>(1, std::min<size_t>(p.nz, cb / p.per_level)));
         void* ws = nullptr;
         st = workspace(ws_all, stream, &ws);
-        if (!st) st = launch_grid(p, md, t, nodes, eta, ws, chunk, stream, lpc, rowv);   // warm
+        const int rv = rowv == 5 ? 2 : rowv;
+        if (!st) st = launch_grid(p, md, t, nodes, eta, ws, chunk, stream, lpc, rv, rowv == 5);   // warm
         // best of five (the fastest repetition is the least disturbed one)
         float ms = 0.f, tot = 1e30f;
         for (int rep = 0; rep < 5 && !st; ++rep) {
           if (cudaMemsetAsync(ws, 0, kFlushBytes, stream) != cudaSuccess) { st = SWENSE_ERR_CUDA; break; }
           if (cudaEventRecord(e0, stream) != cudaSuccess) { st = SWENSE_ERR_CUDA; break; }
-          st = launch_grid(p, md, t, nodes, eta, ws, chunk, stream, lpc, rowv);
+          st = launch_grid(p, md, t, nodes, eta, ws, chunk, stream, lpc, rv, rowv == 5);
           if (cudaEventRecord(e1, stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
               cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) st = SWENSE_ERR_CUDA;
           tot = std::min(tot, ms);
@@ -1532,7 +1602,7 @@ extern "C" int swense_set_grid_tune(int32_t nx, int32_t ny, int32_t pad_n, int32
     return fail(SWENSE_ERR_ARG, "lpc must be -1 (default), 0, 1, 2 or 4");
   if (chunk_bytes < (int64_t(1) << 20) || chunk_bytes > (int64_t(1) << 30))
     return fail(SWENSE_ERR_ARG, "chunk_bytes must be in [1 MiB, 1 GiB]");
-  if (row_variant < 0 || row_variant > 4) return fail(SWENSE_ERR_ARG, "row_variant must be 0..4");
+  if (row_variant < 0 || row_variant > 5) return fail(SWENSE_ERR_ARG, "row_variant must be 0..5");
   std::lock_guard<std::mutex> lock(g_tune_mutex);
   if (lpc == -1) {                      // back to the untuned defaults for this shape
     g_tune.erase({nx, ny, pad_n, nz});

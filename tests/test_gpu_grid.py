@@ -126,7 +126,7 @@ def test_every_launch_shape_matches_oracle(api, lpc, rowv, chunk_mb, shape):
     _forced(api, lpc, rowv, chunk_mb, shape)
 
 
-@pytest.mark.parametrize("rowv", [2, 3, 4])
+@pytest.mark.parametrize("rowv", [2, 3, 4, 5])
 @pytest.mark.parametrize("lpc,chunk_mb", [(1, 1), (4, 32)])
 @pytest.mark.parametrize("shape", [(256, 256, 1), (512, 128, 2), (128, 512, 2), (256, 512, 1)])
 def test_transposed_pair_matches_oracle(api, lpc, chunk_mb, shape, rowv):
@@ -176,3 +176,34 @@ def test_long_rows_block_transform_sampled(api, shape):
         errs.append(rel_linf(g[:, 3], ref["phit"]))
         errs.append(rel_linf(grid.eta[ti].cpu().numpy()[iy, ix].astype(np.float64), ref["eta"]))
         assert max(errs) <= 1e-5, (ti, errs)
+
+
+def test_two_stream_pipeline_is_graph_capturable(api):
+    """Variant 5 forks its row passes onto a library stream and joins them back: captured in a
+    CUDA graph and replayed, it gives the same grid as the single-stream variant."""
+    import torch
+    from paper_2005_12716_gb300 import _swense as S
+    nx, ny, pad = 256, 256, 1
+    rng = np.random.default_rng(9)
+    comps = seas.random_linear_components(nx, ny, 6.0, 6.0, 10, 0.01, rng)
+    sea = seas.linear_sea(nx, ny, 6.0, 6.0, comps)
+    z = np.linspace(-1.0, 0.04, 9).astype(np.float32)
+    modes = api.upload_modes(sea)
+    tl = [0.0, 0.13]
+    try:
+        S.swense_set_grid_tune(nx, ny, pad, len(z), 2, 1 << 20, 2)        # one level per chunk
+        ref = api.fields_on_grid(modes, z, pad, tl)
+        torch.cuda.synchronize()
+        S.swense_set_grid_tune(nx, ny, pad, len(z), 2, 1 << 20, 5)
+        g = api.alloc_grid(modes, z, pad, tl)
+        api.fields_on_grid(modes, z, pad, tl, out=g)                      # sizes the workspace
+        torch.cuda.synchronize()
+        g.nodes.fill_(float("nan"))
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            api.fields_on_grid(modes, z, pad, tl, out=g)
+        graph.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(g.nodes, ref.nodes) and torch.equal(g.eta, ref.eta)
+    finally:
+        S.swense_set_grid_tune(nx, ny, pad, len(z), -1, 32 << 20, 0)
