@@ -78,3 +78,29 @@ def test_argument_validation_launches_nothing(lib):
     st = lib.swense_interp(ctypes.byref(g), 0.0, 16, 10, None, None, None, None, None, 0, 1e3,
                            9.81, None, None)
     assert st == -1
+
+
+def test_validation_of_tuning_plan_and_direct_entry_points(lib):
+    """The newer entry points reject bad arguments on the host, before any CUDA call."""
+    import ctypes
+    import numpy as np
+    from paper_2005_12716_gb300 import _swense as S
+    S.load()
+    assert lib.swense_set_grid_tune(64, 32, 1, 12, 3, 32 << 20, 0) == -1          # lpc 3
+    assert lib.swense_set_grid_tune(64, 32, 1, 12, 2, 1024, 0) == -1              # chunk < 1 MiB
+    assert lib.swense_set_grid_tune(64, 32, 1, 12, 2, 32 << 20, 6) == -1          # variant 6
+    assert lib.swense_set_grid_tune(64, 32, 1, 12, -1, 32 << 20, 0) == 0          # forget: fine
+    assert lib.swense_interp_plan_bytes(0) == 0
+    assert lib.swense_interp_plan_bytes(1) == 16 and lib.swense_interp_plan_bytes(1025) == 32
+    z = np.array([-1, -0.5, 0.0, 0.1], np.float32)
+    g = S.make_grid(16, 16, 16, 1, 4, 1, 1.0, 1.0, z, [0.0])
+    st = lib.swense_interp_with_plan(ctypes.byref(g), 0.0, 16, 10, None, None, None, None, None,
+                                     None, 0, 1e3, 9.81, None, None)
+    assert st == -1 and b"plan" in lib.swense_last_error()
+    st = lib.swense_interp_with_plan(ctypes.byref(g), 0.0, 16, 10, 24, None, None, None, None,
+                                     None, 0, 1e3, 9.81, None, None)
+    assert st == -1                                                                # misaligned
+    m = S.swense_modes(8, 4, 1.0, 1.0, 0.0, 1, 16, 16, 16, None, 0.0)
+    st = lib.swense_direct(ctypes.byref(m), 0.0, 16, 4, None, None, None, None, None, 0, 1e3,
+                           9.81, 7, None)
+    assert st == -1 and b"precision" in lib.swense_last_error()

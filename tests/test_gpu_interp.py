@@ -184,3 +184,15 @@ def test_reusable_plan_equals_plain_call(api):
     empty = torch.empty((0, 3), device="cuda")
     got, _ = api.interp_with_plan(grid, cfg["t_query"], empty, api.interp_plan(grid, empty))
     assert all(v.numel() == 0 for v in got.values())
+
+
+def test_maximum_levels_and_time_levels(api):
+    """The largest grid the ABI accepts in z and t: 256 vertical levels (every level-lookup
+    bucket in use) and four time levels (cubic Lagrange in time), 64 x 32 modes zero-padded
+    twice, on the small cylinder mesh."""
+    cfg = configs.jonswap3d(nx=64, ny=32, lx_over_lp=8.0, ly_over_lp=4.0, n_levels=256, pad_n=2,
+                            mesh_dims=(12, 16, 10), n_tl=4)
+    assert len(cfg["z_levels"]) == 256 and len(cfg["t_levels"]) == 4
+    pts = configs.mesh_points(cfg["mesh"])
+    errs, _, _ = _run(api, cfg["sea"], cfg["z_levels"], 2, cfg["t_levels"], cfg["t_query"], pts)
+    assert max(errs.values()) <= TOL, errs
