@@ -214,6 +214,9 @@ typedef struct swense_grid {
  * [z_levels[0], z_levels[nz-1]] get NaN u, v, w, p (eta stays valid) and are counted.
  * n_out_of_range: host pointer or NULL; when non-NULL the call synchronises the stream and
  * stores the count. p_mode: enum swense_p_mode; rho, g used by P_DYN / P_TOTAL.
+ * Points are taken in 1024-point chunks; a chunk whose points all have the same z (bitwise; a
+ * layer of cell or face centres of an extruded mesh) is interpolated in z once per grid column
+ * and then in x and y per point, which is the same tensor-product sum in another order.
  * Errors: ARG, SIZE, LEVELS, CUDA.
  */
 int swense_interp(const swense_grid* grid, double t, const float* pts, int64_t np,
@@ -235,7 +238,7 @@ int swense_interp(const swense_grid* grid, double t, const float* pts, int64_t n
  *                                     read; its geometry and level list are;
  *   swense_interp_with_plan(...)      swense_interp with that plan (the plan kernel is skipped).
  * A plan made for other points or another grid geometry gives wrong results (reads stay inside
- * the shared-memory box: offsets are clamped). Errors: as swense_interp; SWENSE_ERR_ARG for a
+ * the shared-memory box and the grid: offsets are clamped, levels checked). Errors: as swense_interp; SWENSE_ERR_ARG for a
  * NULL or misaligned plan.
  */
 int64_t swense_interp_plan_bytes(int64_t np);

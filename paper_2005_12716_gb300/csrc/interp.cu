@@ -126,10 +126,8 @@ struct PointCell {
   bool inside;
 };
 
-__device__ __forceinline__ PointCell point_cell(const InterpArgs& a, const LevelTables& T, float x,
-                                                float y, float z) {
-  const float* zs = T.z;
-  PointCell c;
+// Horizontal part of a point's cell: first stencil nodes and weights in x and y.
+__device__ __forceinline__ void point_xy(const InterpArgs& a, float x, float y, PointCell& c) {
   float fx;
   locate(x, a.sx_hi, a.sx_lo, a.Nxr, c.ix, fx);
   if (a.spline) bspline4(fx, c.wx); else lagrange4_uniform(fx, c.wx);
@@ -141,6 +139,12 @@ __device__ __forceinline__ PointCell point_cell(const InterpArgs& a, const Level
     locate(y, a.sy_hi, a.sy_lo, a.Nyr, c.iy, fy);
     if (a.spline) bspline4(fy, c.wy); else lagrange4_uniform(fy, c.wy);
   }
+}
+
+// Vertical part: first stencil level j0, level weights and whether z lies inside the levels.
+__device__ __forceinline__ void point_level(const InterpArgs& a, const LevelTables& T, float z,
+                                            PointCell& c) {
+  const float* zs = T.z;
   // bracket: largest j with zs[j] <= z, clamped to [0, nz-2]; stencil j0 = clamp(j-1, 0, nz-4)
   const int nz = a.nz;
   c.inside = (z >= zs[0]) && (z <= zs[nz - 1]);
@@ -153,6 +157,13 @@ __device__ __forceinline__ PointCell point_cell(const InterpArgs& a, const Level
 #pragma unroll
   for (int q = 0; q < 4; ++q) zn[q] = zs[c.j0 + q];
   lagrange4(zn, T.inv[c.j0], z, c.wz);
+}
+
+__device__ __forceinline__ PointCell point_cell(const InterpArgs& a, const LevelTables& T, float x,
+                                                float y, float z) {
+  PointCell c;
+  point_xy(a, x, y, c);
+  point_level(a, T, z, c);
   return c;
 }
 
@@ -242,6 +253,40 @@ constexpr int BOX_PTS = BOX_THREADS * BOX_PPT;
 constexpr int BOX_NODES = 4096;                    // float4 nodes (64 KB; 99 % of the 1024-point mesh chunks fit)
 constexpr int BOX_COLS = BOX_NODES / 4;             // eta columns (a box has at least 4 levels)
 constexpr size_t BOX_SMEM = size_t(BOX_NODES) * sizeof(float4) + size_t(BOX_COLS) * sizeof(float);
+// Level-flat chunks (every point at the same z, as the cell and face centres of one layer of an
+// extruded mesh) stage one z-collapsed plane instead of the box: float4 columns and eta.
+constexpr int FLAT_COLS = 3456;
+static_assert(size_t(FLAT_COLS) * (sizeof(float4) + sizeof(float)) <= BOX_SMEM, "flat plane fits the tile");
+
+// One chunk's plan, 16 bytes: x0, y0 (first staged node, wrapped), l0 | FLAT_BIT, extents.
+//   3-D box:  w = bx | by << 11 | bz << 22 (bz >= 4), z = l0
+//   flat:     w = bx | by << 12 (4 levels from l0), z = l0 | FLAT_BIT
+//   neither fits the tile: w = -1 (global gathers)
+constexpr int FLAT_BIT = 1 << 30;
+struct BoxPlan {
+  int x0, y0, l0, bx, by, bz;
+  bool flat;     // z-collapsed plane
+  bool box3d;    // the 3-D box fits BOX_NODES / BOX_COLS
+};
+__device__ __forceinline__ BoxPlan decode_plan(int4 pl) {
+  BoxPlan b;
+  b.x0 = pl.x;
+  b.y0 = pl.y;
+  b.flat = pl.w >= 0 && (pl.z & FLAT_BIT);
+  b.l0 = pl.z & 0xffff;
+  if (b.flat) {
+    b.bx = pl.w & 4095;
+    b.by = (pl.w >> 12) & 4095;
+    b.bz = 4;
+  } else {
+    b.bx = pl.w & 2047;
+    b.by = (pl.w >> 11) & 2047;
+    b.bz = (pl.w >> 22) & 511;
+  }
+  const int sbx = b.bx + ((4 - b.bx) & 7);
+  b.box3d = pl.w >= 0 && (!b.flat || (sbx * b.by * 4 <= BOX_NODES && sbx * b.by <= BOX_COLS));
+  return b;
+}
 
 // Level-plane stride of the box (unpadded: padding it to separate z-neighbours' bank groups
 // removed only 6 % of the wavefronts and made more chunks miss the tile).
@@ -308,6 +353,41 @@ __device__ __forceinline__ void stage_box(const InterpArgs& a, int x0, int y0, i
   }
 }
 
+// Level-flat chunk: the z-collapsed, time-blended plane P = sum_t w_t sum_q wz_q G_t[l0 + q] of
+// columns x0..x0+bx-1, y0..y0+by-1 (wrapped) into shared memory (row stride sbx), and the eta
+// rows. Columns over all threads (index -> (ly, lx)), so every thread has 4 x n_tl node loads
+// and n_tl eta loads of one column in flight.
+__device__ __forceinline__ void stage_plane(const InterpArgs& a, int x0, int y0, int l0, int bx,
+                                            int by, int sbx, const float wz[4], float4* splane,
+                                            float* seta) {
+  const size_t plane = size_t(a.Nyr) * a.Nxr;
+  const size_t tl_stride = size_t(a.nz) * plane;
+  const int ncol = bx * by;
+  for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
+    const int ly = c / bx, lx = c - ly * bx;
+    const size_t col = size_t((y0 + ly) & (a.Nyr - 1)) * a.Nxr + ((x0 + lx) & (a.Nxr - 1));
+    const float4* src = a.nodes + size_t(l0) * plane + col;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    float e = 0.f;
+#pragma unroll
+    for (int tl = 0; tl < SWENSE_MAX_TL; ++tl) {
+      if (tl >= a.n_tl) break;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float4 g = __ldg(&src[size_t(tl) * tl_stride + size_t(q) * plane]);
+        const float w = a.wt[tl] * wz[q];
+        v.x = fmaf(w, g.x, v.x);
+        v.y = fmaf(w, g.y, v.y);
+        v.z = fmaf(w, g.z, v.z);
+        v.w = fmaf(w, g.w, v.w);
+      }
+      e = fmaf(a.wt[tl], __ldg(&a.eta[size_t(tl) * plane + col]), e);
+    }
+    splane[ly * sbx + lx] = v;
+    seta[ly * sbx + lx] = e;
+  }
+}
+
 // Box plan of one 1024-point chunk: box origin (grid node indices, wrapped) and extents, or
 // dims = -1 when the box does not fit the shared-memory tile (the chunk then gathers from
 // global memory). Computed by its own kernel so the gather kernel can start its box load at
@@ -321,19 +401,21 @@ __global__ void __launch_bounds__(BOX_THREADS) k_interp_plan(InterpArgs a, Level
   // every thread derives the chunk's reference cell (its first point's) itself: one broadcast
   // load instead of a wait on one thread
   int refx, refy;
+  const float refz = __ldg(&a.pts[3 * p0 + 2]);
   {
-    const PointCell c = point_cell(a, zs, __ldg(&a.pts[3 * p0]), __ldg(&a.pts[3 * p0 + 1]),
-                                   __ldg(&a.pts[3 * p0 + 2]));
+    const PointCell c = point_cell(a, zs, __ldg(&a.pts[3 * p0]), __ldg(&a.pts[3 * p0 + 1]), refz);
     refx = c.ix;
     refy = c.iy;
   }
+  int same_z = 1;                                   // every point of the chunk at z == refz (bitwise)
   int mn[3] = {1 << 30, 1 << 30, 1 << 30}, mx[3] = {-(1 << 30), -(1 << 30), -(1 << 30)};
 #pragma unroll
   for (int k = 0; k < BOX_PPT; ++k) {
     const int64_t i = p0 + k * BOX_THREADS + threadIdx.x;
     if (i < a.np) {
-      const PointCell c = point_cell(a, zs, __ldg(&a.pts[3 * i]), __ldg(&a.pts[3 * i + 1]),
-                                     __ldg(&a.pts[3 * i + 2]));
+      const float pz = __ldg(&a.pts[3 * i + 2]);
+      const PointCell c = point_cell(a, zs, __ldg(&a.pts[3 * i]), __ldg(&a.pts[3 * i + 1]), pz);
+      same_z &= __float_as_int(pz) == __float_as_int(refz);
       const int rx = wrap_rel(c.ix, refx, a.Nxr);
       const int ry = a.Nyr > 1 ? wrap_rel(c.iy, refy, a.Nyr) : 0;
       mn[0] = min(mn[0], rx);
@@ -359,7 +441,7 @@ __global__ void __launch_bounds__(BOX_THREADS) k_interp_plan(InterpArgs a, Level
       s_red[3 + d][warp] = mx[d];
     }
   }
-  __syncthreads();
+  const int flat = __syncthreads_and(same_z);
   if (threadIdx.x != 0) return;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
@@ -376,11 +458,13 @@ __global__ void __launch_bounds__(BOX_THREADS) k_interp_plan(InterpArgs a, Level
   const int by = a.Nyr > 1 ? mx[1] - mn[1] + 4 : 1;
   const int bz = mx[2] - mn[2] + 4;
   const int zst = box_zstride(sbx, by);
-  const bool fits = int64_t(zst) * bz <= BOX_NODES && int64_t(sbx) * by <= BOX_COLS &&
-                    bx <= a.Nxr && by <= a.Nyr;
-  plan[blockIdx.x] = make_int4((refx + mn[0] - 1) & (a.Nxr - 1),
-                               a.Nyr > 1 ? ((refy + mn[1] - 1) & (a.Nyr - 1)) : 0, mn[2],
-                               fits ? (bx | (by << 11) | (bz << 22)) : -1);
+  const bool inside_grid = bx <= a.Nxr && by <= a.Nyr;
+  const bool fits = int64_t(zst) * bz <= BOX_NODES && int64_t(sbx) * by <= BOX_COLS && inside_grid;
+  const bool fits_flat = flat && int64_t(sbx) * by <= FLAT_COLS && inside_grid;
+  const int x0 = (refx + mn[0] - 1) & (a.Nxr - 1);
+  const int y0 = a.Nyr > 1 ? ((refy + mn[1] - 1) & (a.Nyr - 1)) : 0;
+  plan[blockIdx.x] = fits_flat ? make_int4(x0, y0, mn[2] | FLAT_BIT, bx | (by << 12))
+                               : make_int4(x0, y0, mn[2], fits ? (bx | (by << 11) | (bz << 22)) : -1);
 }
 
 __global__ void __launch_bounds__(BOX_THREADS, 3) k_interp_box(InterpArgs a, Levels L,
@@ -402,7 +486,8 @@ __global__ void __launch_bounds__(BOX_THREADS, 3) k_interp_box(InterpArgs a, Lev
       nz_ = __ldg(&a.pts[3 * i + 2]);
     }
   }
-  if (pl.w < 0) {
+  const BoxPlan bp = decode_plan(pl);
+  if (pl.w < 0 || bp.l0 + bp.bz > a.nz) {           // no tile, or a plan of another level list
     __syncthreads();
 #pragma unroll 1
     for (int k = 0; k < BOX_PPT; ++k) {
@@ -417,16 +502,60 @@ __global__ void __launch_bounds__(BOX_THREADS, 3) k_interp_box(InterpArgs a, Lev
     }
     return;
   }
-  const int bx = pl.w & 2047, by = (pl.w >> 11) & 2047, bz = pl.w >> 22;
+  const int bx = bp.bx, by = bp.by, bz = bp.bz;
   // shared-memory row stride = 4 (mod 8) float4: reads of neighbouring cells (dx, dy in {0, 1})
   // by one quarter-warp fall into different bank groups
   const int sbx = bx + ((4 - bx) & 7);
+  const int x0 = bp.x0, y0 = bp.y0, l0 = bp.l0;
+  const int nys = a.Nyr > 1 ? 4 : 1;
+  if (bp.flat) {
+    // one z for the whole chunk: level weights once (from the level tables, so after the
+    // barrier that completes them), then a 2-D gather of 16 float4 per point
+    const float zc = __ldg(&a.pts[3 * p0 + 2]);
+    __syncthreads();
+    PointCell cz;
+    point_level(a, zs, zc, cz);
+    float* fe = reinterpret_cast<float*>(sbox + FLAT_COLS);
+    stage_plane(a, x0, y0, l0, bx, by, sbx, cz.wz, sbox, fe);
+    __syncthreads();
+#pragma unroll 1
+    for (int k = 0; k < BOX_PPT; ++k) {
+      const int64_t i = p0 + k * BOX_THREADS + threadIdx.x;
+      if (i >= a.np) break;
+      const float px = nx_, py = ny_, pz = nz_;
+      if (k + 1 < BOX_PPT && i + BOX_THREADS < a.np) {
+        nx_ = __ldg(&a.pts[3 * (i + BOX_THREADS)]);
+        ny_ = __ldg(&a.pts[3 * (i + BOX_THREADS) + 1]);
+      }
+      PointCell c;
+      point_xy(a, px, py, c);
+      const int lx = min(max((c.ix - 1 - x0) & (a.Nxr - 1), 0), bx - 4);
+      const int ly = a.Nyr > 1 ? min(max((c.iy - 1 - y0) & (a.Nyr - 1), 0), by - 4) : 0;
+      const float4* base = sbox + ly * sbx + lx;
+      const float* ebase = fe + ly * sbx + lx;
+      unsigned long long uv = pack2(0.f, 0.f), wt = pack2(0.f, 0.f);
+      float acc_eta = 0.f;
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        if (b >= nys) break;
+#pragma unroll
+        for (int kx = 0; kx < 4; ++kx) {
+          const float4 gv = base[b * sbx + kx];
+          const float ww = c.wy[b] * c.wx[kx];
+          const unsigned long long w2 = pack2(ww, ww);
+          fma2(uv, w2, pack2(gv.x, gv.y));
+          fma2(wt, w2, pack2(gv.z, gv.w));
+          acc_eta = fmaf(ww, ebase[b * sbx + kx], acc_eta);
+        }
+      }
+      store_point(a, i, make_float4(lo2(uv), hi2(uv), lo2(wt), hi2(wt)), acc_eta, pz, cz.inside);
+    }
+    return;
+  }
   const int zst = box_zstride(sbx, by);
-  const int x0 = pl.x, y0 = pl.y, l0 = pl.z;
   stage_box(a, x0, y0, l0, bx, by, bz, sbx, zst, sbox, seta);
   __syncthreads();
   const int zstride = zst;
-  const int nys = a.Nyr > 1 ? 4 : 1;
 #pragma unroll 1
   for (int k = 0; k < BOX_PPT; ++k) {
     const int64_t i = p0 + k * BOX_THREADS + threadIdx.x;
@@ -620,11 +749,12 @@ __global__ void __launch_bounds__(BOX_THREADS, 2) k_interp_learned(InterpArgs a,
   }
   const int64_t p0 = int64_t(blockIdx.x) * BOX_PTS;
   const int4 pl = plan[blockIdx.x];
-  const bool boxed = pl.w >= 0;
-  const int bx = pl.w & 2047, by = (pl.w >> 11) & 2047, bz = pl.w >> 22;
+  const BoxPlan bp = decode_plan(pl);
+  const bool boxed = bp.box3d && bp.l0 + bp.bz <= a.nz;
+  const int bx = bp.bx, by = bp.by, bz = bp.bz;
   const int sbx = bx + ((4 - bx) & 7);
   const int zst = box_zstride(sbx, by);
-  const int x0 = pl.x, y0 = pl.y, l0 = pl.z;
+  const int x0 = bp.x0, y0 = bp.y0, l0 = bp.l0;
   const size_t plane = size_t(a.Nyr) * a.Nxr;
   if (boxed) stage_box(a, x0, y0, l0, bx, by, bz, sbx, zst, sbox, seta);
   __syncthreads();

@@ -196,3 +196,47 @@ def test_maximum_levels_and_time_levels(api):
     pts = configs.mesh_points(cfg["mesh"])
     errs, _, _ = _run(api, cfg["sea"], cfg["z_levels"], 2, cfg["t_levels"], cfg["t_query"], pts)
     assert max(errs.values()) <= TOL, errs
+
+
+def _layers(rng, zs, n_per, lo, hi):
+    """n_per points uniform in the (x, y) rectangle lo..hi at each z of zs, layer after layer."""
+    out = []
+    for zv in zs:
+        p = np.empty((n_per, 3), np.float32)
+        p[:, 0] = rng.uniform(lo[0], hi[0], n_per)
+        p[:, 1] = rng.uniform(lo[1], hi[1], n_per)
+        p[:, 2] = np.float32(zv)
+        out.append(p)
+    return np.concatenate(out)
+
+
+@pytest.mark.parametrize("patch", ["small", "wide", "domain"])
+def test_level_flat_chunks(api, patch):
+    """Chunks whose points share one z take the z-collapsed plane (small patch: the 3-D box would
+    also fit; wide patch: only the plane fits; whole domain: neither, global gathers). Layers at
+    a level node, at the top and bottom levels, between levels, above and below the levels
+    (NaN, counted), and a layer with one point moved off the layer's z (the 3-D path)."""
+    cfg = configs.jonswap3d_small()
+    sea, z = cfg["sea"], np.asarray(cfg["z_levels"], np.float32)
+    # grid spacing 1/16 (64 modes on 8 lambda_p, refined twice): ~20 x 20 columns, ~52 x 36, all
+    lo, hi = {"small": ((2.0, 1.0), (3.0, 2.0)), "wide": ((1.0, 1.0), (4.0, 3.0)),
+              "domain": ((-3.0, -1.0), (11.0, 5.0))}[patch]
+    zs = [z[3], z[-1], z[0], 0.5 * (z[5] + z[6]), z[-1] + 0.01, z[0] - 0.01, -0.0, 0.0, 0.3 * z[2]]
+    rng = np.random.default_rng(31)
+    pts = _layers(rng, zs, 2048, lo, hi)
+    pts[-1000, 2] = np.float32(0.31 * z[2])          # one chunk of the last layer is not flat
+    pts = np.concatenate([pts, _layers(rng, [z[4]], 777, lo, hi)])   # ragged flat tail
+    errs, out, ref = _run(api, sea, z, 2, cfg["t_levels"], cfg["t_query"], pts, "total")
+    assert ref["out_of_range"].sum() == 2 * 2048
+    assert max(errs.values()) <= TOL, errs
+
+
+def test_level_flat_chunks_2d(api):
+    """The 2-D Stokes wave (one grid row) with points in layers of equal z."""
+    cfg = configs.stokes2d()
+    z = np.asarray(cfg["z_levels"], np.float32)
+    rng = np.random.default_rng(32)
+    L = cfg["sea"]["Lx"]
+    pts = _layers(rng, [z[0], z[10], 0.5 * (z[20] + z[21]), z[-1]], 3000, (0.0, 0.0), (0.3 * L, 0.0))
+    errs, _, _ = _run(api, cfg["sea"], z, 1, cfg["t_levels"], cfg["t_query"], pts)
+    assert max(errs.values()) <= TOL, errs
