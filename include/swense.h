@@ -117,9 +117,10 @@ typedef struct swense_grid_desc {
  *   eta    float [n_tl][ny_r][nx_r]
  * Arithmetic: FP32 transforms, FP32 depth factors with a compensated |k| z product.
  * Uses the scratch workspace (4 * ny_r * nx/2 complex64 per level of a level chunk, twice that
- * for transform variant 5) when ny > 1; the workspace, the twiddle table and variant 5's
- * second stream are created by the first call on a device, which must not be inside a stream
- * capture. Errors: ARG, SIZE, LEVELS, OOM, CUDA.
+ * for transform variant 5) when ny > 1. When ny > 1 the eta transform runs on a second,
+ * library-owned stream, forked from `stream` and joined back before the call returns, so it
+ * overlaps the level transforms. The workspace, the twiddle table and the library's streams are
+ * created by the first call on a device, which must not be inside a stream capture. Errors: ARG, SIZE, LEVELS, OOM, CUDA.
  */
 int swense_fields_on_grid(const swense_modes* modes, int32_t n_tl, const double* t,
                           const swense_grid_desc* desc, float* nodes, float* eta, void* stream);

@@ -1230,6 +1230,9 @@ size_t scratch_bytes(const GridPlan& p, int chunk, int nbuf = 1) {
 struct Pipe {
   cudaStream_t side = nullptr;
   cudaEvent_t col_done[2] = {nullptr, nullptr}, row_done[2] = {nullptr, nullptr};
+  // the eta transform runs beside the level transforms on a stream of its own
+  cudaStream_t eta_side = nullptr;
+  cudaEvent_t eta_fork = nullptr, eta_join = nullptr;
 };
 std::mutex g_pipe_mutex;
 std::map<int, Pipe> g_pipe;
@@ -1245,15 +1248,20 @@ int get_pipe(Pipe** out) {
       SWENSE_CUDA_TRY(cudaEventCreateWithFlags(&pp.col_done[b], cudaEventDisableTiming));
       SWENSE_CUDA_TRY(cudaEventCreateWithFlags(&pp.row_done[b], cudaEventDisableTiming));
     }
+    SWENSE_CUDA_TRY(cudaStreamCreateWithFlags(&pp.eta_side, cudaStreamNonBlocking));
+    SWENSE_CUDA_TRY(cudaEventCreateWithFlags(&pp.eta_fork, cudaEventDisableTiming));
+    SWENSE_CUDA_TRY(cudaEventCreateWithFlags(&pp.eta_join, cudaEventDisableTiming));
   }
   *out = &pp;
   return SWENSE_OK;
 }
 
-// Enqueue every kernel of the request; `ws` holds scratch_bytes(p, chunk) bytes.
+// Enqueue every kernel of the request; `ws` holds scratch_bytes(p, chunk) bytes. eta_side: run
+// the eta transform of each time level on the per-device second stream, forked after that time
+// level's propagated modes exist and joined back before the call returns (graph-capturable).
 int launch_grid(const GridPlan& p, const swense_modes* md, const double* t, float* nodes, float* eta,
                 void* ws, int chunk, cudaStream_t stream, int lpc = kColLevels, int rowv = 0,
-                int overlap = 0) {
+                int overlap = 0, int eta_side = 0) {
   const float2* tw = nullptr;
   {
     int st = twiddles(stream, &tw);
@@ -1271,10 +1279,21 @@ int launch_grid(const GridPlan& p, const swense_modes* md, const double* t, floa
                                              align256(size_t(chunk) * p.per_level));
   Pipe* pipe = nullptr;
   const bool use_pipe = overlap && rowv == 2 && pair_path(p.ny, p.Nxr, p.Nyr);
-  if (use_pipe) {
+  const bool eta_fork = eta_side && p.ny > 1;
+  if (use_pipe || eta_fork) {
     int st = get_pipe(&pipe);
     if (st) return st;
   }
+  struct EtaJoin {                               // the caller's stream waits for the eta stream
+    Pipe* pp;
+    cudaStream_t s;
+    bool forked;
+    ~EtaJoin() {
+      if (!pp || !forked) return;
+      cudaEventRecord(pp->eta_join, pp->eta_side);
+      cudaStreamWaitEvent(s, pp->eta_join, 0);
+    }
+  } eta_join{eta_fork ? pipe : nullptr, stream, false};
   int chunk_no = 0;                              // chunks issued so far (over all time levels)
   struct Join {                                  // the caller's stream waits for the second one
     Pipe* pp;
@@ -1382,13 +1401,21 @@ int launch_grid(const GridPlan& p, const swense_modes* md, const double* t, floa
     a.Nxr = int(Nxr);
     a.spline = p.spline;
 
-    // eta: pass A (eta mode) then pass B packing row pairs
+    // eta: pass A (eta mode) then pass B packing row pairs; on the eta stream when forked (the
+    // time levels' eta transforms stay in order there, so they share one intermediate)
+    cudaStream_t es = stream;
+    if (eta_fork) {
+      SWENSE_CUDA_TRY(cudaEventRecord(pipe->eta_fork, stream));
+      SWENSE_CUDA_TRY(cudaStreamWaitEvent(pipe->eta_side, pipe->eta_fork, 0));
+      eta_join.forked = true;
+      es = pipe->eta_side;
+    }
     a.G = g_eta;
     a.eta_mode = 1;
     a.fp = 1;
     a.cb = cb_eta;
     a.lev0 = 0;
-    k_pass_a<<<dim3((Mh + cb_eta - 1) / cb_eta, 1), kThreads, smem_a_eta, stream>>>(a, p.lev);
+    k_pass_a<<<dim3((Mh + cb_eta - 1) / cb_eta, 1), kThreads, smem_a_eta, es>>>(a, p.lev);
     SWENSE_CUDA_TRY(cudaGetLastError());
     count_launches(1);
     b.G = g_eta;
@@ -1396,7 +1423,7 @@ int launch_grid(const GridPlan& p, const swense_modes* md, const double* t, floa
     b.rb = rb_eta;
     b.lev0 = 0;
     k_pass_b<<<dim3(unsigned((Nyr + 2 * rb_eta - 1) / (2 * rb_eta)), 1), kThreads, smem_b_eta,
-               stream>>>(b, p.lev);
+               es>>>(b, p.lev);
     SWENSE_CUDA_TRY(cudaGetLastError());
     count_launches(1);
 
@@ -1521,7 +1548,7 @@ extern "C" int swense_fields_on_grid(const swense_modes* md, int32_t n_tl, const
     st = workspace(ws_bytes, stream, &ws);
     if (st) return st;
   }
-  return launch_grid(p, md, t, nodes, eta, ws, chunk, stream, lpc, rowv == 5 ? 2 : rowv, rowv == 5);
+  return launch_grid(p, md, t, nodes, eta, ws, chunk, stream, lpc, rowv == 5 ? 2 : rowv, rowv == 5, 1);
 }
 
 extern "C" int swense_autotune_grid(const swense_modes* md, int32_t n_tl, const double* t,
@@ -1563,13 +1590,13 @@ extern "C" int swense_autotune_grid(const swense_modes* md, int32_t n_tl, const 
         void* ws = nullptr;
         st = workspace(ws_all, stream, &ws);
         const int rv = rowv == 5 ? 2 : rowv;
-        if (!st) st = launch_grid(p, md, t, nodes, eta, ws, chunk, stream, lpc, rv, rowv == 5);   // warm
+        if (!st) st = launch_grid(p, md, t, nodes, eta, ws, chunk, stream, lpc, rv, rowv == 5, 1);   // warm
         // best of five (the fastest repetition is the least disturbed one)
         float ms = 0.f, tot = 1e30f;
         for (int rep = 0; rep < 5 && !st; ++rep) {
           if (cudaMemsetAsync(ws, 0, kFlushBytes, stream) != cudaSuccess) { st = SWENSE_ERR_CUDA; break; }
           if (cudaEventRecord(e0, stream) != cudaSuccess) { st = SWENSE_ERR_CUDA; break; }
-          st = launch_grid(p, md, t, nodes, eta, ws, chunk, stream, lpc, rv, rowv == 5);
+          st = launch_grid(p, md, t, nodes, eta, ws, chunk, stream, lpc, rv, rowv == 5, 1);
           if (cudaEventRecord(e1, stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
               cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) st = SWENSE_ERR_CUDA;
           tot = std::min(tot, ms);
