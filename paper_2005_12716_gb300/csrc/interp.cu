@@ -391,15 +391,23 @@ __device__ __forceinline__ void stage_plane(const InterpArgs& a, int x0, int y0,
 // Box plan of one 1024-point chunk: box origin (grid node indices, wrapped) and extents, or
 // dims = -1 when the box does not fit the shared-memory tile (the chunk then gathers from
 // global memory). Computed by its own kernel so the gather kernel can start its box load at
-// once, without first waiting for its points.
+// once, without first waiting for its points. One warp per chunk (32 points per lane, loads
+// coalesced across the lanes): the chunk's reductions stay in the warp, with no block barrier
+// and no single-thread tail, and eight chunks of a block share one copy of the level tables.
+constexpr int PLAN_WARPS = BOX_THREADS / 32;
+__host__ __device__ __forceinline__ int64_t plan_blocks(int64_t np) {
+  return ((np + BOX_PTS - 1) / BOX_PTS + PLAN_WARPS - 1) / PLAN_WARPS;
+}
+
 __global__ void __launch_bounds__(BOX_THREADS) k_interp_plan(InterpArgs a, Levels L, int4* __restrict__ plan) {
   __shared__ LevelTables zs;
-  __shared__ int s_red[6][BOX_THREADS / 32];
   fill_level_tables(zs, L, a.nz);
-  const int64_t p0 = int64_t(blockIdx.x) * BOX_PTS;
   __syncthreads();
-  // every thread derives the chunk's reference cell (its first point's) itself: one broadcast
-  // load instead of a wait on one thread
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t chunk = int64_t(blockIdx.x) * PLAN_WARPS + warp;
+  const int64_t p0 = chunk * BOX_PTS;
+  if (p0 >= a.np) return;                           // no barrier below
+  // every lane derives the chunk's reference cell (its first point's) itself: broadcast loads
   int refx, refy;
   const float refz = __ldg(&a.pts[3 * p0 + 2]);
   {
@@ -409,9 +417,9 @@ __global__ void __launch_bounds__(BOX_THREADS) k_interp_plan(InterpArgs a, Level
   }
   int same_z = 1;                                   // every point of the chunk at z == refz (bitwise)
   int mn[3] = {1 << 30, 1 << 30, 1 << 30}, mx[3] = {-(1 << 30), -(1 << 30), -(1 << 30)};
-#pragma unroll
-  for (int k = 0; k < BOX_PPT; ++k) {
-    const int64_t i = p0 + k * BOX_THREADS + threadIdx.x;
+#pragma unroll 4
+  for (int k = 0; k < BOX_PTS / 32; ++k) {
+    const int64_t i = p0 + k * 32 + lane;
     if (i < a.np) {
       const float pz = __ldg(&a.pts[3 * i + 2]);
       const PointCell c = point_cell(a, zs, __ldg(&a.pts[3 * i]), __ldg(&a.pts[3 * i + 1]), pz);
@@ -433,25 +441,8 @@ __global__ void __launch_bounds__(BOX_THREADS) k_interp_plan(InterpArgs a, Level
       mx[d] = max(mx[d], __shfl_xor_sync(0xffffffffu, mx[d], o));
     }
   }
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) {
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      s_red[d][warp] = mn[d];
-      s_red[3 + d][warp] = mx[d];
-    }
-  }
-  const int flat = __syncthreads_and(same_z);
-  if (threadIdx.x != 0) return;
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    mn[d] = s_red[d][0];
-    mx[d] = s_red[3 + d][0];
-    for (int w = 1; w < BOX_THREADS / 32; ++w) {
-      mn[d] = min(mn[d], s_red[d][w]);
-      mx[d] = max(mx[d], s_red[3 + d][w]);
-    }
-  }
+  const bool flat = __all_sync(0xffffffffu, same_z);
+  if (lane != 0) return;
   // box: x nodes rel (mn0-1) .. (mx0+2), y likewise (one row in 2-D), levels mn2 .. mx2+3
   const int bx = mx[0] - mn[0] + 4;
   const int sbx = bx + ((4 - bx) & 7);
@@ -463,8 +454,8 @@ __global__ void __launch_bounds__(BOX_THREADS) k_interp_plan(InterpArgs a, Level
   const bool fits_flat = flat && int64_t(sbx) * by <= FLAT_COLS && inside_grid;
   const int x0 = (refx + mn[0] - 1) & (a.Nxr - 1);
   const int y0 = a.Nyr > 1 ? ((refy + mn[1] - 1) & (a.Nyr - 1)) : 0;
-  plan[blockIdx.x] = fits_flat ? make_int4(x0, y0, mn[2] | FLAT_BIT, bx | (by << 12))
-                               : make_int4(x0, y0, mn[2], fits ? (bx | (by << 11) | (bz << 22)) : -1);
+  plan[chunk] = fits_flat ? make_int4(x0, y0, mn[2] | FLAT_BIT, bx | (by << 12))
+                          : make_int4(x0, y0, mn[2], fits ? (bx | (by << 11) | (bz << 22)) : -1);
 }
 
 __global__ void __launch_bounds__(BOX_THREADS, 3) k_interp_box(InterpArgs a, Levels L,
@@ -1095,7 +1086,7 @@ extern "C" int swense_interp_learned(const swense_grid* g, double t, const float
     a.o_p = p;
     a.n_oor = n_out_of_range ? d_count : nullptr;
     int4* plan = reinterpret_cast<int4*>(static_cast<char*>(ws) + 256);
-    k_interp_plan<<<unsigned(blocks), BOX_THREADS, 0, stream>>>(a, lev, plan);
+    k_interp_plan<<<unsigned(plan_blocks(np)), BOX_THREADS, 0, stream>>>(a, lev, plan);
     SWENSE_CUDA_TRY(cudaGetLastError());
     SWENSE_CUDA_TRY(cudaFuncSetAttribute((const void*)k_interp_learned,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, int(LRN_SMEM)));
@@ -1148,7 +1139,7 @@ int interp_impl(const swense_grid* g, double t, const float* pts, const int32_t*
     const int4* plan = plan_in;
     if (!plan) {
       int4* pw = reinterpret_cast<int4*>(static_cast<char*>(ws) + 256);
-      k_interp_plan<<<unsigned(blocks), BOX_THREADS, 0, stream>>>(a, lev, pw);
+      k_interp_plan<<<unsigned(plan_blocks(np)), BOX_THREADS, 0, stream>>>(a, lev, pw);
       SWENSE_CUDA_TRY(cudaGetLastError());
       count_launches(1);
       plan = pw;
@@ -1187,7 +1178,7 @@ extern "C" int swense_interp_plan(const swense_grid* g, const float* pts, int64_
   if (!plan || (reinterpret_cast<uintptr_t>(plan) & 15)) return fail(SWENSE_ERR_ARG, "plan must be non-NULL and 16-byte aligned");
   const int64_t blocks = (np + BOX_PTS - 1) / BOX_PTS;
   if (blocks >= (int64_t(1) << 31)) return fail(SWENSE_ERR_SIZE, "too many points for one call");
-  k_interp_plan<<<unsigned(blocks), BOX_THREADS, 0, stream>>>(a, lev, static_cast<int4*>(plan));
+  k_interp_plan<<<unsigned(plan_blocks(np)), BOX_THREADS, 0, stream>>>(a, lev, static_cast<int4*>(plan));
   SWENSE_CUDA_TRY(cudaGetLastError());
   count_launches(1);
   return SWENSE_OK;
