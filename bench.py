@@ -225,7 +225,12 @@ def job_throughput(units_per_rank, world, ms_per_step):
     return world * units_per_rank / (ms_per_step * 1e-3)
 
 
-def kernel_source_hash(files=("csrc/interp.cu", "csrc/internal.cuh", "../include/swense.h")):
+GATHER_SOURCES = ("csrc/interp.cu", "csrc/internal.cuh", "../include/swense.h")
+GRID_SOURCES = ("csrc/grid_ifft.cu", "csrc/fft.cuh", "csrc/internal.cuh", "../include/swense.h")
+GRID_STAGE = "grid_ifft (stage 1: k_propagate, eta k_pass_a/k_pass_b, k_col_t, k_row_t)"
+
+
+def kernel_source_hash(files=GATHER_SOURCES):
     """Hash of the sources a kernel is built from (paths relative to the package)."""
     h = hashlib.sha256()
     for f in files:
@@ -365,6 +370,7 @@ def run_ours(args, rank, world):
     box_bytes = k2_bytes                                  # the gather reads points, writes fields
     plan_bytes = npts * 12 + (npts + 1023) // 1024 * 16
     src_hash = kernel_source_hash()
+    grid_hash = kernel_source_hash(GRID_SOURCES)
     stages = {
         "grid_ifft": {"ms": k1_ms, "algorithmic_bytes": k1_bytes,
                       "achieved_gbs": k1_bytes / (k1_ms * 1e-3) / 1e9,
@@ -378,24 +384,34 @@ def run_ours(args, rank, world):
                    "k_interp_box_ms": k2b_ms},
     }
     if k2b_ms >= k1_ms:
-        kname, dom_bytes, dom_ms = "k_interp_box", box_bytes, k2b_ms
+        kname, dom_bytes, dom_ms, dom_hash = "k_interp_box", box_bytes, k2b_ms, src_hash
     else:
-        kname, dom_bytes, dom_ms = "grid_ifft (k_col_t + k_row_t)", k1_bytes, k1_ms
+        # the stage as a whole (all its launches of one step, one stream or two)
+        kname, dom_bytes, dom_ms, dom_hash = GRID_STAGE, k1_bytes, k1_ms, grid_hash
     tr = NCU_TRAFFIC.get(kname)
-    traffic = tr["bytes"] if tr and tr.get("hash") == src_hash and tr.get("workload") == desc else None
+    traffic = tr["bytes"] if tr and tr.get("hash") == dom_hash and tr.get("workload") == desc else None
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": traffic,
                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
                 else "fallback 6.8 TB/s"}
-    if kname == "k_interp_box":
-        # the binding resource of the gather: shared-memory reads, 64 float4 stencil nodes + 16
-        # eta values per point, against 128 B/clk/SM x 152 SMs at the maximum SM clock
-        smem_peak = 152 * 128 * 2070e6 / 1e9
-        smem = npts * (64 * 16 + 16 * 4) / (dom_ms * 1e-3) / 1e9
-        roofline["shared_memory"] = {"achieved": smem, "peak": smem_peak, "unit": "GB/s",
-                                     "frac": smem / smem_peak,
-                                     "bytes_per_point": 64 * 16 + 16 * 4}
+    # the binding resource of the gather: shared-memory reads per point, 16 float4 + 16 eta for
+    # the chunks gathered from a z-collapsed plane, 64 float4 + 16 eta for the 3-D boxes, against
+    # 128 B/clk/SM x 152 SMs at the maximum SM clock. The chunk kinds are read from the plan the
+    # library made (int4 per chunk: w < 0 no tile, bit 30 of z set: flat plane).
+    pl = plan[: S.swense_interp_plan_bytes(npts)].view(torch.int32).view(-1, 4).cpu().numpy()
+    per_chunk = np.full(len(pl), 1024)
+    per_chunk[-1] = npts - 1024 * (len(pl) - 1)
+    is_flat = (pl[:, 3] >= 0) & ((pl[:, 2] & (1 << 30)) != 0)
+    is_box = (pl[:, 3] >= 0) & ~is_flat
+    smem_bytes = float(per_chunk[is_flat].sum() * (16 * 16 + 16 * 4) + per_chunk[is_box].sum() * (64 * 16 + 16 * 4))
+    smem_peak = 152 * 128 * 2070e6 / 1e9
+    smem_gbs = smem_bytes / (k2b_ms * 1e-3) / 1e9
+    stages["interp"]["chunks"] = {"flat_plane": int(is_flat.sum()), "box_3d": int(is_box.sum()),
+                                  "global": int((pl[:, 3] < 0).sum())}
+    stages["interp"]["k_interp_box_shared_memory"] = {
+        "achieved": smem_gbs, "peak": smem_peak, "unit": "GB/s", "frac": smem_gbs / smem_peak,
+        "bytes_per_point": smem_bytes / npts}
 
     line = {
         "metric": "wave-field points/sec at stated err vs FP64 oracle; % of HBM roofline",
@@ -414,7 +430,7 @@ def run_ours(args, rank, world):
         "gpu_launches": int(launches),
         "clocks": clk,
         "wall_s_timed": t_wall,
-        "kernel_hash": src_hash,
+        "kernel_hash": {"gather": src_hash, "grid": grid_hash},
     }
 
     # ---- end to end through the C ABI with host buffers

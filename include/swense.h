@@ -116,11 +116,12 @@ typedef struct swense_grid_desc {
  *   nodes  float [n_tl][nz][ny_r][nx_r][4] = (u, v, w, dphi/dt) per node
  *   eta    float [n_tl][ny_r][nx_r]
  * Arithmetic: FP32 transforms, FP32 depth factors with a compensated |k| z product.
- * Uses the scratch workspace (4 * ny_r * nx/2 complex64 per level of a level chunk, twice that
- * for transform variant 5) when ny > 1. When ny > 1 the eta transform runs on a second,
- * library-owned stream, forked from `stream` and joined back before the call returns, so it
- * overlaps the level transforms. The workspace, the twiddle table and the library's streams are
- * created by the first call on a device, which must not be inside a stream capture. Errors: ARG, SIZE, LEVELS, OOM, CUDA.
+ * Uses the scratch workspace (4 * ny_r * (nx/2 + 1) complex64 per level of a level chunk, each
+ * row padded to whole 128-byte lines; twice that for transform variant 5) when ny > 1. When
+ * ny > 1 the eta transform runs on a second, library-owned stream, forked from `stream` and
+ * joined back before the call returns, so it overlaps the level transforms. The workspace, the
+ * twiddle table and the library's streams are created by the first call on a device, which must
+ * not be inside a stream capture. Errors: ARG, SIZE, LEVELS, OOM, CUDA.
  */
 int swense_fields_on_grid(const swense_modes* modes, int32_t n_tl, const double* t,
                           const swense_grid_desc* desc, float* nodes, float* eta, void* stream);

@@ -609,8 +609,23 @@ __global__ void __launch_bounds__(256, N >= 1024 ? 2 : 3) k_row_half(RowArgs a) 
   for (int e = 0; e < E; ++e) __stcs(&o2[2 * (lane + 32 * (e / RL) + (e % RL) * (N / RL))], z[e]);
 }
 
+// m stride of the transposed intermediate: a whole number of 128-byte lines per field row, so
+// the row pass can drop the rows it has consumed from L2 without touching a neighbour's data.
+__host__ __device__ __forceinline__ int trans_ld(int Mh) { return (Mh + 15) & ~15; }
+
+// Invalidate, without write-back, the L2 lines of nf field rows (stride fs float2) of ld float2
+// each starting at row (128-byte aligned): their values are dead once the row pass has read
+// them, so the column pass's writes need not reach DRAM. Lines spread over nt threads from t.
+__device__ __forceinline__ void discard_rows(const float2* row, size_t fs, int nf, int ld, int t, int nt) {
+  const int lines = ld / 16;
+  for (int i = t; i < nf * lines; i += nt) {
+    const float2* a = row + size_t(i / lines) * fs + size_t(i % lines) * 16;
+    asm volatile("discard.global.L2 [%0], 128;" ::"l"(a) : "memory");
+  }
+}
+
 // Transposed-intermediate pair for 256- to 1024-point transforms. The column pass writes
-// G[level][field][y][m] with the m stride padded to a multiple of four (ldG), so a grid row's
+// G[level][field][y][m] with the m stride padded to whole 128-byte lines (ldG), so a grid row's
 // inputs are contiguous; the row pass then reads them straight into registers with coalesced
 // loads, with no staging and no block-wide barrier.
 //
@@ -752,6 +767,8 @@ __global__ void __launch_bounds__(256, N >= 1024 ? 1 : 2) k_row_t(RowArgs a) {
 #pragma unroll
   for (int e = 0; e < E; ++e)
     __stcs(&out[lane + 32 * (e / RL) + (e % RL) * (N / RL)], make_float4(z1[e].x, z1[e].y, z2[e].x, z2[e].y));
+  __syncwarp();                                  // every lane's reads of the row are done
+  discard_rows(row, fs, 4, a.ldG, lane, 32);
 }
 
 // Same row pass with one transform per warp (warps 2r and 2r+1 of a block take Z1 and Z2 of
@@ -790,6 +807,8 @@ __global__ void __launch_bounds__(256, N >= 1024 ? 2 : 3) k_row_t2(RowArgs a) {
   float2* out = reinterpret_cast<float2*>(a.nodes + (size_t(a.lev0 + level) * a.Nyr + y) * N) + q;
 #pragma unroll
   for (int e = 0; e < E; ++e) __stcs(&out[2 * (lane + 32 * (e / RL) + (e % RL) * (N / RL))], z[e]);
+  __syncwarp();                                  // every lane's reads of the two rows are done
+  discard_rows(row, fs, 2, a.ldG, lane, 32);
 }
 
 // Row pass for rows longer than a warp transform (2048..8192 points): one block of kThreads per
@@ -833,6 +852,8 @@ __global__ void __launch_bounds__(256, N >= 8192 ? 1 : 2) k_row_tb(RowArgs a) {
 #pragma unroll
     for (int e = 0; e < E; ++e)
       __stcs(&out[t + kThreads * (e / RL) + (e % RL) * (N / RL)], make_float4(z1[e].x, z1[e].y, z2[e].x, z2[e].y));
+    __syncthreads();                             // every thread's reads of the rows are done
+    discard_rows(row, fs, 4, a.ldG, t, kThreads);
   } else {
     float2* o2 = reinterpret_cast<float2*>(out);
 #pragma unroll 1
@@ -844,6 +865,7 @@ __global__ void __launch_bounds__(256, N >= 8192 ? 1 : 2) k_row_tb(RowArgs a) {
       for (int e = 0; e < E; ++e) __stcs(&o2[2 * (t + kThreads * (e / RL) + (e % RL) * (N / RL)) + q], z[e]);
       __syncthreads();                           // the buffer is reused by the second transform
     }
+    discard_rows(row, fs, 4, a.ldG, t, kThreads);  // after the barrier: all reads are done
   }
 }
 
@@ -924,6 +946,8 @@ __global__ void __launch_bounds__(256, N >= 1024 ? 1 : 2) k_row_tma(RowArgs a, i
       }
     }
     __syncwarp();                                // every lane has read the staged row
+    // the bulk copy that filled the staging buffer has completed: its global rows are dead
+    discard_rows(Gl + size_t(y0 + i) * a.ldG, fs, 4, a.ldG, lane, 32);
     if (i + 1 < nrows) issue(i + 1);
     stk_fft<N>(z1, T, a.tw, xbuf, lane);
     stk_fft<N>(z2, T, a.tw, xbuf, lane);
@@ -1211,7 +1235,7 @@ int plan_grid(const swense_modes* md, int32_t n_tl, const double* t, const swens
   p->Nxr = Nxr;
   p->Nyr = Nyr;
   p->nslot = size_t(ny) * p->nxh1;
-  p->per_level = size_t(4) * Nyr * ((p->Mh + 3) & ~3) * sizeof(float2);
+  p->per_level = size_t(4) * Nyr * trans_ld(p->Mh) * sizeof(float2);
   p->prop_bytes = md->omega ? size_t(n_tl) * 3 * p->nslot * sizeof(float2) : 0;
   p->geta_bytes = ny > 1 ? size_t(Nyr) * p->Mh * sizeof(float2) : 0;
   return SWENSE_OK;
@@ -1454,7 +1478,7 @@ int launch_grid(const GridPlan& p, const swense_modes* md, const double* t, floa
       ra.rb = kRowBlock;
       const size_t smem_col = size_t(2) * ny * (kColBlock + 1) * sizeof(float2);
       const size_t smem_row = size_t(4) * Mh * (kRowBlock + 1) * sizeof(float2);
-      ca.ldG = ra.ldG = (Mh + 3) & ~3;
+      ca.ldG = ra.ldG = trans_ld(Mh);
       const bool pair_t = (rowv == 2 || rowv == 3 || (rowv == 4 && Nxr <= 1024)) && pair_path(ny, Nxr, Nyr);
   
       for (int l0 = 0; l0 < nz; l0 += chunk) {
