@@ -225,8 +225,8 @@ def job_throughput(units_per_rank, world, ms_per_step):
     return world * units_per_rank / (ms_per_step * 1e-3)
 
 
-GATHER_SOURCES = ("csrc/interp.cu", "csrc/internal.cuh", "../include/swense.h")
-GRID_SOURCES = ("csrc/grid_ifft.cu", "csrc/fft.cuh", "csrc/internal.cuh", "../include/swense.h")
+GATHER_SOURCES = ("csrc/interp.cu", "csrc/internal.cuh")
+GRID_SOURCES = ("csrc/grid_ifft.cu", "csrc/fft.cuh", "csrc/internal.cuh")
 GRID_STAGE = "grid_ifft (stage 1: k_propagate, eta k_pass_a/k_pass_b, k_col_t, k_row_t)"
 
 
@@ -243,9 +243,15 @@ def kernel_source_hash(files=GATHER_SOURCES):
 # the hash of the kernel's sources and the workload they were taken on; a changed kernel or
 # workload invalidates them (traffic is then reported as null).
 NCU_TRAFFIC = {
-    "k_interp_box": {"bytes": 114949888 + 117129984, "hash": "516769e7b0a33424",
+    "k_interp_box": {"bytes": 114921984 + 117313536, "hash": "089e09e558b9ffc5",
                      "workload": "jonswap3d: 512x256 modes, 64 levels, pad 1, 2 time levels, "
                                  "2048000 cell + 6177280 face centres (cylinder O-grid)"},
+    # all 14 launches of one step, caches kept between them (--cache-control none), launch shape
+    # lpc 4, 64 MB level chunks, row variant 2
+    GRID_STAGE: {"bytes": 324033280, "hash": "5075c9ba21f043b9",
+                 "taken_with": {"lpc": 4, "chunk_bytes": 64 << 20, "row_variant": 2},
+                 "workload": "jonswap3d: 512x256 modes, 64 levels, pad 1, 2 time levels, "
+                             "2048000 cell + 6177280 face centres (cylinder O-grid)"},
 }
 
 
@@ -393,6 +399,7 @@ def run_ours(args, rank, world):
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": traffic,
+                "traffic_taken_with": (tr or {}).get("taken_with") if traffic is not None else None,
                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
                 else "fallback 6.8 TB/s"}
     # the binding resource of the gather: shared-memory reads per point, 16 float4 + 16 eta for
@@ -407,6 +414,9 @@ def run_ours(args, rank, world):
     smem_bytes = float(per_chunk[is_flat].sum() * (16 * 16 + 16 * 4) + per_chunk[is_box].sum() * (64 * 16 + 16 * 4))
     smem_peak = 152 * 128 * 2070e6 / 1e9
     smem_gbs = smem_bytes / (k2b_ms * 1e-3) / 1e9
+    tb = NCU_TRAFFIC.get("k_interp_box")
+    stages["interp"]["k_interp_box_traffic"] = (tb["bytes"] if tb and tb.get("hash") == src_hash
+                                               and tb.get("workload") == desc else None)
     stages["interp"]["chunks"] = {"flat_plane": int(is_flat.sum()), "box_3d": int(is_box.sum()),
                                   "global": int((pl[:, 3] < 0).sum())}
     stages["interp"]["k_interp_box_shared_memory"] = {
