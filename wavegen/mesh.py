@@ -170,3 +170,11 @@ def box_xz_mesh(x_edges, z_edges, y0=0.0, y1=1.0):
     cc = np.stack([cx, np.full(len(cx), 0.5 * (y0 + y1)), cz], 1)
     return {"cell_centres": cc, "face_centres": face_centres, "face_area": face_area,
             "cell_volume": vol, "cell_faces": cell_faces, "nx": nx, "nz": nz}
+
+
+def cell_z_extent(mesh):
+    """Lowest and highest face-centre z of each cell: its vertical extent for hex cells whose
+    top and bottom faces are horizontal (every cell of the meshes above)."""
+    idx = np.abs(mesh["cell_faces"]) - 1
+    fz = np.asarray(mesh["face_centres"], np.float64)[:, 2][idx]
+    return fz.min(1), fz.max(1)
