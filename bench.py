@@ -28,6 +28,23 @@ FALLBACK_HBM_GBS = 6800.0
 L2_FLUSH_BYTES = 256 << 20
 
 
+class L2Flush:
+    """Between timed steps: write a buffer larger than L2 (evicts everything the step left), then
+    read a second one, so the dirty lines of the write reach DRAM before the next timed step
+    rather than inside it: every step starts from a cold, clean L2."""
+
+    def __init__(self, dev):
+        import torch
+        self.w = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+        self.r = torch.zeros(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+        self.out = torch.empty((), dtype=torch.float32, device=dev)
+
+    def __call__(self):
+        import torch
+        self.w.zero_()
+        torch.amax(self.r, dim=0, out=self.out)
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -35,7 +52,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", choices=["jonswap3d", "stokes2d", "batched", "learned", "e1", "direct",
-                                         "large"],
+                                         "large", "relax"],
                     default="jonswap3d")
     ap.add_argument("--pad", type=int, default=1)
     ap.add_argument("--no-autotune", action="store_true",
@@ -269,7 +286,7 @@ def run_ours(args, rank, world):
     grid = api.alloc_grid(modes, z, pad, tl, dev)
     pts = torch.from_numpy(pts_np).to(dev)
     outs = {k: torch.empty(npts, dtype=torch.float32, device=dev) for k in ("eta", "u", "v", "w", "p")}
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    flush = L2Flush(dev)
     stream = torch.cuda.current_stream(dev)
 
     def step():
@@ -287,7 +304,7 @@ def run_ours(args, rank, world):
         tune = None
 
     for _ in range(args.warmup):
-        flush.zero_()
+        flush()
         step()
     torch.cuda.synchronize()
     # Each stage captured once into a CUDA graph (kernel arguments are captured by value; the
@@ -332,7 +349,7 @@ def run_ours(args, rank, world):
     launches0 = S.swense_launches()
     t_wall = time.perf_counter()
     for s in range(args.steps):
-        flush.zero_()                     # L2 flush between timed steps (outside the events)
+        flush()                     # L2 flush between timed steps (outside the events)
         ev[s][0].record(stream)
         stage1()
         ev[s][1].record(stream)
@@ -432,7 +449,8 @@ def run_ours(args, rank, world):
                    "launch": "host launches" if args.no_graph else "CUDA graph replay per stage",
                    "stage1_tune": tune,
                    "n_tl": n_tl, "points": npts, "fields": 5,
-                   "l2": "flushed between timed steps (256 MB write outside the events)",
+                   "l2": "flushed between timed steps (256 MB write, then a 256 MB read so the "
+                         "written lines reach DRAM; both outside the events)",
                    "parallelism": f"replicas x{world}"},
         "points_fields_per_s": value * 5,
         "roofline": roofline,
@@ -539,7 +557,7 @@ def _time_events(fn, steps, flush=None):
           for _ in range(steps)]
     for s in range(steps):
         if flush is not None:
-            flush.zero_()
+            flush()
         ev[s][0].record(stream)
         fn()
         ev[s][1].record(stream)
@@ -584,7 +602,7 @@ def run_batched(args, rank, world):
     with torch.cuda.graph(g):
         b.run()
     launches_per_step = S.swense_launches() - l0
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    flush = L2Flush(dev)
     steps = max(3, min(args.steps, 30))
     clocks = ClockSampler(dev.index)
     clocks.start()
@@ -651,7 +669,7 @@ def run_learned(args, rank, world):
     for _ in range(max(1, args.warmup)):
         api.interp_learned(grid, tq, pts, mlp, out=outs_l)
         api.interp(grid, tq, pts, out=outs_p)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    flush = L2Flush(dev)
     steps = max(3, min(args.steps, 20))
     from paper_2005_12716_gb300 import _swense as S
     clocks = ClockSampler(dev.index)
@@ -740,10 +758,12 @@ def run_e1(args, rank, world):
     for _ in range(3):
         fn()
     l0 = S.swense_launches()
-    ms = _time_events(fn, 20, torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev))
+    ms = _time_events(fn, 20, L2Flush(dev))
     launches = S.swense_launches() - l0
     nc = len(m3["cell_volume"])
-    nbytes = nc * (6 * (12 + 12 + 4) + 4 + 4)       # per cell: 6 faces (u v w, area, index), volume, out
+    nf = len(m3["face_area"])
+    nbytes = nf * (12 + 12) + nc * (6 * 4 + 4 + 4)   # each face's u v w and area once; per cell
+                                                     # its 6 face indices, volume and output
     line = {"metric": "RMS velocity divergence of the interpolated field [1/s]",
             "config": {"workload": "e1: 2-D JONSWAP Tp 0.7 s, Hs 0.028 m, 128 modes, FV mesh "
                                    "dx = lambda_p/100, dz = Hs/20, cells below -Hs"},
@@ -753,6 +773,68 @@ def run_e1(args, rank, world):
                                      "frac_hbm": nbytes / (ms * 1e-3) / 1e9 / _peak_hbm(),
                                      "gpu_launches": int(launches),
                                      "mesh": "jonswap3d cylinder O-grid, face values gathered per cell"}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_relax(args, rank, world):
+    """Incident VOF fraction and relaxation blending on the 2,048,000 cells of the cylinder mesh
+    (eta at the cell centres from the gather; a ring zone over the outer quarter of the O-grid
+    and three slabs)."""
+    import torch
+    from paper_2005_12716_gb300 import _swense as S
+    from paper_2005_12716_gb300 import api
+    from wavegen import configs, mesh as M
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    cfg = configs.jonswap3d()
+    m = cfg["mesh"]
+    cc = m["cell_centres"].astype(np.float32)
+    lo, hi = M.cell_z_extent(m)
+    zext = np.stack([lo, hi], 1).astype(np.float32)
+    nc = len(cc)
+    grid = api.fields_on_grid(api.upload_modes(cfg["sea"], dev), cfg["z_levels"], 1, cfg["t_levels"])
+    d_cc, d_z = torch.from_numpy(cc).to(dev), torch.from_numpy(zext).to(dev)
+    eta = api.interp(grid, cfg["t_query"], d_cc)[0]["eta"]
+    rng = np.random.default_rng(5)
+    alpha = torch.from_numpy(rng.uniform(0, 1, nc).astype(np.float32)).to(dev)
+    uc = torch.from_numpy(rng.normal(0, 0.1, (nc, 3)).astype(np.float32)).to(dev)
+    xc, yc = cfg["centre"]
+    zones = [(S.ZONE_RADIAL, 1.5, 2.0, xc, yc), (S.ZONE_X, xc + 1.2, xc + 2.0, 0.0, 0.0),
+             (S.ZONE_X, xc - 1.6, xc - 2.0, 0.0, 0.0), (S.ZONE_Y, yc - 1.7, yc - 2.0, 0.0, 0.0)]
+    a_i = torch.empty(nc, dtype=torch.float32, device=dev)
+    w = torch.empty(nc, dtype=torch.float32, device=dev)
+    fn = lambda: api.relax_cells(d_cc, d_z, eta, zones, alpha=alpha, u_c=uc, out_alpha_i=a_i,  # noqa: E731
+                                 out_weight=w)
+    for _ in range(max(3, args.warmup)):
+        fn()
+    l0 = S.swense_launches()
+    steps = max(1, args.steps)
+    ms = max_over_ranks(_time_events(fn, steps, L2Flush(dev)), world, dev)
+    launches = S.swense_launches() - l0
+    n_in = int((w > 0).sum().item())
+    nbytes = nc * (12 + 8 + 4 + 4 + 4) + n_in * 2 * (4 + 12)    # all cells; blended cells r+w
+    hbm = _peak_hbm()
+    line = {"metric": "CFD cells per second (incident VOF fraction + relaxation blend)",
+            "value": job_throughput(nc, world, ms), "unit": "cells/s", "n_gpus": world,
+            "steps": steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"relax: jonswap3d cylinder O-grid, {nc} cells, {n_in} in zones "
+                                   "(ring 1.5-2.0 lambda_p and three slabs)",
+                       "l2": "flushed between timed steps"},
+            "roofline": {"bound": "hbm", "kernel": "k_relax_cells", "achieved": nbytes / (ms * 1e-3) / 1e9,
+                         "peak": hbm, "unit": "GB/s", "frac": nbytes / (ms * 1e-3) / 1e9 / hbm,
+                         "traffic": None},
+            "gpu_launches": int(launches)}
+    if rank == 0 and not args.no_cpu_baseline:
+        from oracle import relax as R                # the CPU baseline leg only
+        t0 = time.perf_counter()
+        R.relax_cells(cc, zext[:, 0], zext[:, 1], eta.cpu().numpy(), zones,
+                      rng.uniform(0, 1, nc), rng.normal(0, 0.1, (nc, 3)))
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": nc / dt, "unit": "cells/s", "cores": 1, "kind": "oracle",
+                                "sample": f"all {nc} cells (numpy FP64)"}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -912,7 +994,7 @@ def main():
         torch.distributed.init_process_group("nccl")
     try:
         {"batched": run_batched, "learned": run_learned, "e1": run_e1, "direct": run_direct,
-         "large": run_large}.get(
+         "large": run_large, "relax": run_relax}.get(
             args.config, run_ours)(
             args, rank, world)
     finally:

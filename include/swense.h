@@ -395,6 +395,50 @@ int swense_fv_divergence(const float* u_face, const float* v_face, const float* 
                          int64_t n_faces, const float* area, const int32_t* cell_faces,
                          const float* cell_volume, int64_t n_cells, float* div, void* stream);
 
+/*
+ * Relaxation zones and the incident VOF fraction (paper: subsection on the prevention of wave
+ * reflections with the relaxation zone technique, Eqs. relaxationZone, weightFunction,
+ * swUcRelax and swVOFRelax; alpha_I reconstructed from eta_I, reconstruction section,
+ * interpolation step).
+ *
+ * A zone is a slab along x or y, or a ring about the vertical axis through (cx, cy). For a cell
+ * centre with coordinate s in it (x, y, or the horizontal distance from the axis), the
+ * non-dimensional distance is x = clamp((s - inner) / (outer - inner), 0, 1): 0 at the inner
+ * boundary (the pure CFD side), 1 at the outer one, so a zone may run in either direction. The
+ * weight is w = -2x^3 + 3x^2, the largest over the zones where they overlap, 0 outside all.
+ */
+enum swense_zone_kind { SWENSE_ZONE_X = 0, SWENSE_ZONE_Y = 1, SWENSE_ZONE_RADIAL = 2 };
+#define SWENSE_MAX_ZONES 8
+
+typedef struct {
+  int32_t kind;    /* enum swense_zone_kind */
+  float inner;     /* coordinate (x, y or radius) of the inner boundary, weight 0 */
+  float outer;     /* coordinate of the outer boundary, weight 1; finite, != inner */
+  float cx, cy;    /* axis of a ring zone (unused by slabs) */
+} swense_relax_zone;
+
+/*
+ * swense_relax_cells — per CFD cell: the incident VOF fraction, the relaxation weight and the
+ * blends applied at the end of a CFD time step.
+ *   cell_xyz  device float [nc][3] cell centres (x and y are read)
+ *   cell_zext device float [nc][2] (z_lo, z_hi), the cell's vertical extent, z_lo < z_hi;
+ *             8-byte aligned
+ *   eta_c     device float [nc] incident elevation at the cell centres (swense_interp's eta)
+ *   zones     host [n_zones], 0 <= n_zones <= SWENSE_MAX_ZONES
+ * Outputs (device, any may be NULL):
+ *   alpha_i   float [nc]  alpha_I = clamp((eta - z_lo) / (z_hi - z_lo), 0, 1): the part of the
+ *             cell's height below a surface taken as horizontal across the cell (the paper
+ *             states no formula); NaN eta gives NaN
+ *   weight    float [nc]  w
+ *   alpha     float [nc]  in place: w alpha_I + (1 - w) alpha            (Eq. swVOFRelax)
+ *   u_c       float [nc][3] in place: (1 - w) u_c, the target being 0   (Eq. swUcRelax)
+ * Cells with w = 0 keep alpha and u_c unchanged and are not written. FP32 arithmetic.
+ * Errors: ARG (bad sizes, zone kind or boundaries, NULL inputs), CUDA.
+ */
+int swense_relax_cells(const float* cell_xyz, const float* cell_zext, const float* eta_c,
+                       int64_t nc, const swense_relax_zone* zones, int32_t n_zones,
+                       float* alpha_i, float* alpha, float* u_c, float* weight, void* stream);
+
 /* Bytes of scratch workspace currently held on the current device. */
 int64_t swense_workspace_bytes(void);
 

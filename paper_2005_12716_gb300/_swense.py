@@ -36,6 +36,15 @@ class swense_grid_desc(ctypes.Structure):
                 ("scheme", ctypes.c_int32)]
 
 
+class swense_relax_zone(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("inner", ctypes.c_float), ("outer", ctypes.c_float),
+                ("cx", ctypes.c_float), ("cy", ctypes.c_float)]
+
+
+ZONE_X, ZONE_Y, ZONE_RADIAL = 0, 1, 2
+MAX_ZONES = 8
+
+
 class swense_grid(ctypes.Structure):
     _fields_ = [
         ("nodes", ctypes.c_void_p), ("eta", ctypes.c_void_p),
@@ -77,6 +86,10 @@ _SIGS = {
                                             ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                                             ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                             ctypes.c_void_p]),
+    "swense_relax_cells": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_int64, ctypes.c_void_p, ctypes.c_int32,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_void_p]),
     "swense_workspace_bytes": (ctypes.c_int64, []),
     "swense_release": (ctypes.c_int, []),
     "swense_last_error": (ctypes.c_char_p, []),
@@ -232,6 +245,17 @@ def swense_fv_divergence(u_face, v_face, w_face, n_faces, area, cell_faces, cell
     _check(lib.swense_fv_divergence(_ptr(u_face), _ptr(v_face), _ptr(w_face), n_faces, _ptr(area),
                                     _ptr(cell_faces), _ptr(cell_volume), n_cells, _ptr(div),
                                     _stream(stream)))
+
+
+def swense_relax_cells(cell_xyz, cell_zext, eta_c, nc, zones, alpha_i=None, alpha=None, u_c=None,
+                       weight=None, stream=None):
+    """zones: sequence of (kind, inner, outer, cx, cy)."""
+    lib = load()
+    arr = (swense_relax_zone * max(1, len(zones)))(*[swense_relax_zone(*z) for z in zones])
+    _check(lib.swense_relax_cells(_ptr(cell_xyz), _ptr(cell_zext), _ptr(eta_c), nc,
+                                  ctypes.cast(arr, ctypes.c_void_p) if zones else None, len(zones),
+                                  _ptr(alpha_i), _ptr(alpha), _ptr(u_c), _ptr(weight),
+                                  _stream(stream)))
 
 
 def swense_workspace_bytes():

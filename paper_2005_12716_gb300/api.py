@@ -160,6 +160,18 @@ def fv_divergence(u, v, w, area, cell_faces, cell_volume, out=None, stream=None)
     return div
 
 
+def relax_cells(cell_xyz, cell_zext, eta_c, zones, alpha=None, u_c=None, out_alpha_i=None,
+                out_weight=None, stream=None):
+    """swense_relax_cells: alpha_I and the relaxation weight per cell (returned), and the blends
+    of alpha and u_c in place when given. zones: (kind, inner, outer, cx, cy) tuples."""
+    nc = cell_xyz.shape[0]
+    dev = cell_xyz.device
+    a_i = out_alpha_i if out_alpha_i is not None else torch.empty(nc, dtype=torch.float32, device=dev)
+    w = out_weight if out_weight is not None else torch.empty(nc, dtype=torch.float32, device=dev)
+    S.swense_relax_cells(cell_xyz, cell_zext, eta_c, nc, list(zones), a_i, alpha, u_c, w, stream)
+    return a_i, w
+
+
 # ------------------------------------------------------------------ learned correction (MLP)
 MLP_NPARAM, MLP_XLD = S.MLP_NPARAM, S.MLP_XLD
 _MLP_SHAPES = (("W1", (64, 67)), ("b1", (64,)), ("W2", (64, 64)), ("b2", (64,)), ("W3", (4, 64)),

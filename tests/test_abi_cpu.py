@@ -104,3 +104,24 @@ def test_validation_of_tuning_plan_and_direct_entry_points(lib):
     st = lib.swense_direct(ctypes.byref(m), 0.0, 16, 4, None, None, None, None, None, 0, 1e3,
                            9.81, 7, None)
     assert st == -1 and b"precision" in lib.swense_last_error()
+
+
+def test_relax_cells_validation(lib):
+    """Bad zones and sizes are rejected on the host before any CUDA call."""
+    import ctypes
+    from paper_2005_12716_gb300 import _swense as S
+    S.load()
+    Z = S.swense_relax_zone
+
+    def call(zones, n=None, nc=10):
+        arr = (Z * max(1, len(zones)))(*[Z(*z) for z in zones])
+        return lib.swense_relax_cells(None, None, None, nc, ctypes.cast(arr, ctypes.c_void_p),
+                                      len(zones) if n is None else n, None, None, None, None, None)
+    assert call([(S.ZONE_X, 1.0, 2.0, 0, 0)] * 9) == -1                     # more than 8 zones
+    assert call([(7, 1.0, 2.0, 0, 0)]) == -1 and b"kind" in lib.swense_last_error()
+    assert call([(S.ZONE_RADIAL, 2.0, 2.0, 0, 0)]) == -1                     # empty zone
+    assert call([(S.ZONE_Y, float("nan"), 2.0, 0, 0)]) == -1
+    assert call([], n=-1) == -1
+    assert call([(S.ZONE_X, 1.0, 2.0, 0, 0)], nc=-5) == -1
+    assert call([(S.ZONE_X, 1.0, 2.0, 0, 0)]) == -1 and b"NULL" in lib.swense_last_error()
+    assert call([(S.ZONE_X, 1.0, 2.0, 0, 0)], nc=0) == 0                     # nothing to do
