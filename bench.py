@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", choices=["jonswap3d", "stokes2d", "batched", "learned", "e1", "direct",
-                                         "large", "relax"],
+                                         "large", "relax", "stream"],
                     default="jonswap3d")
     ap.add_argument("--pad", type=int, default=1)
     ap.add_argument("--no-autotune", action="store_true",
@@ -839,6 +839,56 @@ def run_relax(args, rank, world):
         print(json.dumps(line), flush=True)
 
 
+def run_stream(args, rank, world):
+    """Analytical evaluation of the paper's stream-function wave (T 0.7 s, H 0.058 m, h 0.6 m,
+    N = 9) at the 8,225,280 cell and face centres of a cylinder O-grid."""
+    import torch
+    from paper_2005_12716_gb300 import _swense as S
+    from paper_2005_12716_gb300 import api
+    from wavegen import configs
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    cfg = configs.progressive_wave()
+    pts_np = configs.mesh_points(cfg["mesh"])
+    npts = len(pts_np)
+    pts = torch.from_numpy(pts_np).to(dev)
+    wave = api.stream_wave(cfg["T"], cfg["H"], cfg["h"], n=cfg["n"])
+    out = {k: torch.empty(npts, dtype=torch.float32, device=dev) for k in ("eta", "u", "v", "w", "p")}
+    fn = lambda: api.stream_eval(wave, cfg["t_query"], pts, p_mode="total", out=out)  # noqa: E731
+    for _ in range(max(3, args.warmup)):
+        fn()
+    l0 = S.swense_launches()
+    steps = max(1, args.steps)
+    ms = max_over_ranks(_time_events(fn, steps, L2Flush(dev)), world, dev)
+    launches = S.swense_launches() - l0
+    nbytes = npts * (12 + 20)
+    hbm = _peak_hbm()
+    line = {"metric": "wave-field points/sec, stream-function wave (analytical evaluation)",
+            "value": job_throughput(npts, world, ms), "unit": "points/s", "n_gpus": world,
+            "steps": steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"stream: T 0.7 s, H 0.058 m, h 0.6 m, N = {cfg['n']}; {npts} "
+                                   "cell + face centres (cylinder O-grid to two wavelengths)",
+                       "l2": "flushed between timed steps"},
+            "roofline": {"bound": "hbm", "kernel": "k_stream_eval", "achieved": nbytes / (ms * 1e-3) / 1e9,
+                         "peak": hbm, "unit": "GB/s", "frac": nbytes / (ms * 1e-3) / 1e9 / hbm,
+                         "traffic": None},
+            "gpu_launches": int(launches)}
+    if rank == 0 and not args.no_cpu_baseline:
+        from oracle import stream as O               # the CPU baseline leg only
+        o = O.solve(cfg["T"], cfg["H"], cfg["h"], cfg["n"])
+        sample = pts_np[:: max(1, npts // 200000)].astype(np.float64)
+        t0 = time.perf_counter()
+        O.fields_at_points(o, sample, t=cfg["t_query"])
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": len(sample) / dt, "unit": "points/s", "cores": 1,
+                                "kind": "oracle",
+                                "sample": f"{len(sample)} of the {npts} points (numpy FP64)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_direct(args, rank, world):
     """Direct modal sums at the near-body points of the 3-D JONSWAP mesh (r < 0.25 lambda_p of the
     cylinder axis), FP32 and split-BF16 tensor-core paths, each checked against the FP64 direct sum
@@ -994,7 +1044,7 @@ def main():
         torch.distributed.init_process_group("nccl")
     try:
         {"batched": run_batched, "learned": run_learned, "e1": run_e1, "direct": run_direct,
-         "large": run_large, "relax": run_relax}.get(
+         "large": run_large, "relax": run_relax, "stream": run_stream}.get(
             args.config, run_ours)(
             args, rank, world)
     finally:

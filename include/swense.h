@@ -62,7 +62,8 @@ enum swense_status {
   SWENSE_ERR_OOM = -4,          /* scratch workspace allocation failed */
   SWENSE_ERR_CUDA = -5,         /* a CUDA runtime call failed (see swense_last_error) */
   SWENSE_ERR_TIMEOUT = -6,      /* a bounded device-side wait gave up */
-  SWENSE_ERR_UNSUPPORTED = -7   /* valid request this build does not implement */
+  SWENSE_ERR_UNSUPPORTED = -7,  /* valid request this build does not implement */
+  SWENSE_ERR_CONVERGENCE = -8   /* a host-side nonlinear solve did not converge */
 };
 
 enum swense_p_mode {
@@ -394,6 +395,58 @@ int swense_interp_learned(const swense_grid* grid, double t, const float* pts, i
 int swense_fv_divergence(const float* u_face, const float* v_face, const float* w_face,
                          int64_t n_faces, const float* area, const int32_t* cell_faces,
                          const float* cell_volume, int64_t n_cells, float* div, void* stream);
+
+/*
+ * Stream-function regular waves (paper: subsection on regular waves by stream-function theory,
+ * after Rienecker & Fenton; the "analytical evaluation" subsection: with N ~ 10 components,
+ * ka = 0.24 converging with N = 9, the fields are summed directly at the cells).
+ *
+ * A 2-D periodic wave of period T and height H travelling in +x over depth h, steady in the
+ * frame moving at its phase speed c. In that frame (crest at X = 0, z up from the mean level):
+ *   psi = -ubar (z + h) + sum_{j=1..N} B_j sinh(j k (z + h)) / cosh(j k h) cos(j k X)
+ *   eta = sum_{j=0..N} E_j cos(j k X)
+ * with U = dpsi/dz, W = -dpsi/dX. Found by collocation at X_m = m pi / (N k), m = 0..N: psi = -Q
+ * and (U^2 + W^2)/2 + g eta = R on the surface, zero mean level, crest-to-trough height H, and
+ * no mean Eulerian current (c = ubar = 2 pi / (k T)).
+ */
+#define SWENSE_STREAM_MAX_N 32
+
+typedef struct {
+  int32_t n;                              /* number of components N */
+  double k, c, ubar;                      /* wavenumber, phase speed, mean speed in the wave frame */
+  double Q, R;                            /* volume flux and Bernoulli constant (wave frame) */
+  double depth, g, period, height;
+  double B[SWENSE_STREAM_MAX_N];          /* B_1..B_N */
+  double E[SWENSE_STREAM_MAX_N + 1];      /* E_0..E_N, cosine coefficients of the surface */
+  double eta_m[SWENSE_STREAM_MAX_N + 1];  /* surface at the collocation points */
+} swense_stream_wave;
+
+/*
+ * swense_stream_solve — host only (no GPU needed): the wave's coefficients by Newton's method
+ * in FP64 with the analytic Jacobian, the height raised from the linear wave in height_steps
+ * equal steps (4 is plenty below ~80 % of the breaking height). period, height, depth, g > 0;
+ * 1 <= n <= SWENSE_STREAM_MAX_N; out: host, caller-owned.
+ * Errors: ARG, SIZE, CONVERGENCE (too steep for n or too few steps).
+ */
+int swense_stream_solve(double period, double height, double depth, double g, int32_t n,
+                        int32_t height_steps, swense_stream_wave* out);
+
+/*
+ * swense_stream_eval — the incident fields of a solved wave at points, fixed frame, time t, the
+ * crest at x = x0 at t = 0: X = x - x0 - c t,
+ *   u = c - ubar + sum_j j k B_j C_j cos(j k X),  v = 0,  w = sum_j j k B_j S_j sin(j k X),
+ *   eta = sum_j E_j cos(j k X) (at the point's x),
+ * C_j, S_j the cosh and sinh ratios at the point's z (written without overflow); pressure by
+ * Bernoulli in the wave frame with p = 0 on the surface: P_TOTAL rho (R - g z - (U^2 + W^2)/2),
+ * P_DYN that + rho g z, P_PHIT -p_dyn / rho - |u|^2 / 2, U = u - c.
+ *   pts: device float [np][3] (x, y, z); y is not used. Outputs: device float [np], any NULL.
+ * The phase is reduced in FP64 on the host and formed per point from a compensated x k product;
+ * the sums are FP32 (cos/sin and the depth ratios of the harmonics by recurrence).
+ * Errors: ARG, SIZE, CUDA.
+ */
+int swense_stream_eval(const swense_stream_wave* wave, double t, double x0, const float* pts,
+                       int64_t np, float* eta, float* u, float* v, float* w, float* p,
+                       int32_t p_mode, double rho, void* stream);
 
 /*
  * Relaxation zones and the incident VOF fraction (paper: subsection on the prevention of wave

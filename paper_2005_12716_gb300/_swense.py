@@ -36,6 +36,18 @@ class swense_grid_desc(ctypes.Structure):
                 ("scheme", ctypes.c_int32)]
 
 
+STREAM_MAX_N = 32
+
+
+class swense_stream_wave(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("k", ctypes.c_double), ("c", ctypes.c_double),
+                ("ubar", ctypes.c_double), ("Q", ctypes.c_double), ("R", ctypes.c_double),
+                ("depth", ctypes.c_double), ("g", ctypes.c_double), ("period", ctypes.c_double),
+                ("height", ctypes.c_double), ("B", ctypes.c_double * STREAM_MAX_N),
+                ("E", ctypes.c_double * (STREAM_MAX_N + 1)),
+                ("eta_m", ctypes.c_double * (STREAM_MAX_N + 1))]
+
+
 class swense_relax_zone(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("inner", ctypes.c_float), ("outer", ctypes.c_float),
                 ("cx", ctypes.c_float), ("cy", ctypes.c_float)]
@@ -90,6 +102,14 @@ _SIGS = {
                                           ctypes.c_int64, ctypes.c_void_p, ctypes.c_int32,
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.c_void_p, ctypes.c_void_p]),
+    "swense_stream_solve": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.POINTER(swense_stream_wave)]),
+    "swense_stream_eval": (ctypes.c_int, [ctypes.POINTER(swense_stream_wave), ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_void_p, ctypes.c_int64,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                          ctypes.c_double, ctypes.c_void_p]),
     "swense_workspace_bytes": (ctypes.c_int64, []),
     "swense_release": (ctypes.c_int, []),
     "swense_last_error": (ctypes.c_char_p, []),
@@ -256,6 +276,19 @@ def swense_relax_cells(cell_xyz, cell_zext, eta_c, nc, zones, alpha_i=None, alph
                                   ctypes.cast(arr, ctypes.c_void_p) if zones else None, len(zones),
                                   _ptr(alpha_i), _ptr(alpha), _ptr(u_c), _ptr(weight),
                                   _stream(stream)))
+
+
+def swense_stream_solve(period, height, depth, g=9.81, n=9, height_steps=4):
+    """Host-only solve; returns a swense_stream_wave."""
+    w = swense_stream_wave()
+    _check(load().swense_stream_solve(period, height, depth, g, n, height_steps, ctypes.byref(w)))
+    return w
+
+
+def swense_stream_eval(wave, t, x0, pts, np_, eta=None, u=None, v=None, w=None, p=None,
+                       p_mode=P_DYN, rho=1000.0, stream=None):
+    _check(load().swense_stream_eval(ctypes.byref(wave), t, x0, _ptr(pts), np_, _ptr(eta), _ptr(u),
+                                     _ptr(v), _ptr(w), _ptr(p), p_mode, rho, _stream(stream)))
 
 
 def swense_workspace_bytes():

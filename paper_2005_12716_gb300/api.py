@@ -160,6 +160,21 @@ def fv_divergence(u, v, w, area, cell_faces, cell_volume, out=None, stream=None)
     return div
 
 
+def stream_wave(period, height, depth, g=9.81, n=9, height_steps=4):
+    """swense_stream_solve (host): the stream-function wave's coefficients."""
+    return S.swense_stream_solve(period, height, depth, g, n, height_steps)
+
+
+def stream_eval(wave, t, pts, x0=0.0, p_mode="dyn", rho=1000.0, out=None, stream=None):
+    """swense_stream_eval: eta, u, v, w, p of a solved stream-function wave at points."""
+    n = pts.shape[0]
+    if out is None:
+        out = {k: torch.empty(n, dtype=torch.float32, device=pts.device) for k in ("eta", "u", "v", "w", "p")}
+    S.swense_stream_eval(wave, t, x0, pts, n, out.get("eta"), out.get("u"), out.get("v"), out.get("w"),
+                         out.get("p"), S.P_MODES[p_mode], rho, stream)
+    return out
+
+
 def relax_cells(cell_xyz, cell_zext, eta_c, zones, alpha=None, u_c=None, out_alpha_i=None,
                 out_weight=None, stream=None):
     """swense_relax_cells: alpha_I and the relaxation weight per cell (returned), and the blends

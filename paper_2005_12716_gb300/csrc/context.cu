@@ -157,6 +157,7 @@ const char* swense_strerror(int status) {
     case SWENSE_ERR_CUDA: return "SWENSE_ERR_CUDA";
     case SWENSE_ERR_TIMEOUT: return "SWENSE_ERR_TIMEOUT";
     case SWENSE_ERR_UNSUPPORTED: return "SWENSE_ERR_UNSUPPORTED";
+    case SWENSE_ERR_CONVERGENCE: return "SWENSE_ERR_CONVERGENCE";
     default: return "SWENSE_ERR_UNKNOWN";
   }
 }

@@ -157,3 +157,24 @@ def large_sea(nx=2048, ny=1024, n_levels=128, n_points=16_000_000, n_near=1_000_
         "t_query": float(t_levels[(n_tl - 1) // 2] + 0.37 * (t_levels[1] - t_levels[0])),
         "period": Tp, "centre": (0.5 * Lx, 0.5 * Ly), "lambda_p": lp,
     }
+
+
+def progressive_wave(mesh_dims=(160, 128, 100), seed=SEED0 + 7):
+    """The paper's progressive regular wave (T = 0.7 s, H = 0.058 m, h = 0.6 m; stream-function
+    theory with N = 9) and the cell and face centres of a cylinder O-grid around a vertical
+    cylinder of radius lambda/16 out to two wavelengths, from the bed to 2 H above the mean level
+    (surface band of 60 % of the layers within +-1.5 H): mesh_points(cfg["mesh"])."""
+    T, H, h, n = 0.7, 0.058, 0.6, 9
+    g = 9.81
+    om2 = (2 * np.pi / T) ** 2
+    k = om2 / g                                # deep-water estimate, only to size the mesh
+    for _ in range(50):
+        k = om2 / (g * np.tanh(k * h))
+    lam = 2 * np.pi / k
+    n_r, n_t, n_z = mesh_dims
+    n_band = max(2, int(round(0.6 * n_z)))
+    z_edges = M.clustered_z_edges(-h, 2 * H, n_z, -1.5 * H, 1.5 * H, n_band)
+    mesh = M.cylinder_ogrid((0.0, 0.0), lam / 16, 2 * lam, n_r, n_t, z_edges,
+                            radial_ratio=(1.02 ** (160.0 / n_r)))
+    return {"name": "progressive_wave", "T": T, "H": H, "h": h, "n": n, "g": g, "mesh": mesh,
+            "lambda": lam, "t_query": 0.37 * T, "x0": 0.0}

@@ -43,7 +43,7 @@ def clustered_z_edges(z_bot, z_top, n, band_lo, band_hi, n_band):
         lo_q, hi_q = 1.0, 2.0
         for _ in range(200):
             q = 0.5 * (lo_q + hi_q)
-            tot = dz * q * (q ** m - 1) / (q - 1)
+            tot = dz * q * (q ** m - 1) / (q - 1) if q > 1.0 else dz * m
             if tot > span:
                 hi_q = q
             else:
