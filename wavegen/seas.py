@@ -209,3 +209,17 @@ def random_linear_components(nx, ny, Lx, Ly, count, amp, rng, kmax_frac=0.75):
 def as_complex64_pair(A):
     """Interleaved float32 (re, im) view of a complex field, the C ABI's complex64 layout."""
     return np.ascontiguousarray(A.astype(np.complex64)).view(np.float32)
+
+
+def tank_modes(nx_t, ny_t, Lx, Ly, depth, amp, seed, slope=3.0):
+    """Seeded wave-tank cosine amplitudes A_eta, A_phi, A_phit [ny_t][nx_t] (ny_t = 1 in 2-D)
+    with a smooth power-law decay in the mode index, on a tank of Lx x Ly and depth h."""
+    rng = np.random.default_rng(seed)
+    m = np.arange(nx_t)[None, :]
+    n = np.arange(ny_t)[:, None]
+    kk = np.hypot(m / nx_t, n / max(ny_t, 1)) + 1.0 / nx_t
+    env = amp * (kk * nx_t) ** (-slope)
+    out = {"nx_t": nx_t, "ny_t": ny_t, "Lx": Lx, "Ly": Ly, "depth": depth}
+    for key in ("A_eta", "A_phi", "A_phit"):
+        out[key] = env * rng.normal(size=(ny_t, nx_t))
+    return out
