@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", choices=["jonswap3d", "stokes2d", "batched", "learned", "e1", "direct",
-                                         "large", "relax", "stream"],
+                                         "large", "relax", "stream", "tank"],
                     default="jonswap3d")
     ap.add_argument("--pad", type=int, default=1)
     ap.add_argument("--no-autotune", action="store_true",
@@ -889,6 +889,50 @@ def run_stream(args, rank, world):
         print(json.dumps(line), flush=True)
 
 
+def run_tank(args, rank, world):
+    """Wave-tank reconstruction: 257 x 129 cosine modes (two snapshots) mapped onto the mirrored
+    512 x 256 periodic grid, 64 levels, gathered at the 8,225,280 cell and face centres of a
+    cylinder O-grid in the tank. One step = mode mapping + grid + gather."""
+    import torch
+    from paper_2005_12716_gb300 import _swense as S
+    from paper_2005_12716_gb300 import api
+    from wavegen import configs
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    cfg = configs.tank3d()
+    pts_np = configs.mesh_points(cfg["mesh"])
+    npts = len(pts_np)
+    pts = torch.from_numpy(pts_np).to(dev)
+    dvA = lambda k: torch.from_numpy(np.stack([s[k] for s in cfg["snaps"]]).astype(np.float32)).to(dev)  # noqa: E731
+    Ae, Ap, At = dvA("A_eta"), dvA("A_phi"), dvA("A_phit")
+    z, tl, tq = cfg["z_levels"], cfg["t_levels"], cfg["t_query"]
+    modes = api.tank_modes(Ae, Ap, At, cfg["Lx"], cfg["Ly"], cfg["depth"])
+    grid = api.fields_on_grid(modes, z, 1, tl)
+    outs = {k: torch.empty(npts, dtype=torch.float32, device=dev) for k in ("eta", "u", "v", "w", "p")}
+
+    def step():
+        m = api.tank_modes(Ae, Ap, At, cfg["Lx"], cfg["Ly"], cfg["depth"])
+        api.fields_on_grid(m, z, 1, tl, out=grid)
+        api.interp(grid, tq, pts, out=outs)
+    for _ in range(max(3, args.warmup)):
+        step()
+    l0 = S.swense_launches()
+    steps = max(1, args.steps)
+    ms = max_over_ranks(_time_events(step, steps, L2Flush(dev)), world, dev)
+    launches = S.swense_launches() - l0
+    line = {"metric": "wave-field points/sec, wave tank (cosine basis on the mirrored grid)",
+            "value": job_throughput(npts, world, ms), "unit": "points/s", "n_gpus": world,
+            "steps": steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"tank3d: 257x129 cosine modes (2 snapshots), mirrored 512x256 grid, "
+                                   f"{len(z)} levels, {npts} cell + face centres",
+                       "launch": "host launches", "l2": "flushed between timed steps"},
+            "gpu_launches": int(launches)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_direct(args, rank, world):
     """Direct modal sums at the near-body points of the 3-D JONSWAP mesh (r < 0.25 lambda_p of the
     cylinder axis), FP32 and split-BF16 tensor-core paths, each checked against the FP64 direct sum
@@ -1044,7 +1088,7 @@ def main():
         torch.distributed.init_process_group("nccl")
     try:
         {"batched": run_batched, "learned": run_learned, "e1": run_e1, "direct": run_direct,
-         "large": run_large, "relax": run_relax, "stream": run_stream}.get(
+         "large": run_large, "relax": run_relax, "stream": run_stream, "tank": run_tank}.get(
             args.config, run_ours)(
             args, rank, world)
     finally:

@@ -397,6 +397,34 @@ int swense_fv_divergence(const float* u_face, const float* v_face, const float* 
                          const float* cell_volume, int64_t n_cells, float* div, void* stream);
 
 /*
+ * swense_tank_modes — wave-tank modes (paper: the HOS-NWT solver reproduces a rectangular tank
+ * with perfectly reflective walls, so the basis functions psi_i become cosine modes) onto the
+ * periodic pipeline. Tank fields:
+ *   eta = sum_{m,n} A^eta_mn cos(m pi x / Lx) cos(n pi y / Ly), phi likewise with the depth
+ *   factor F(|k|, z) of swense_fields_on_grid, dphi/dt likewise; u, v, w the derivatives of phi.
+ * A cosine series on the tank is the Fourier series of its even extension over 2 Lx x 2 Ly, so
+ * each real amplitude is written as its one or two half-spectrum coefficients of that doubled
+ * periodic domain (A for m = n = 0, A/2 on an axis, A/4 at each of (m, +n) and (m, -n)).
+ *   A_eta, A_phi, A_phit: device float [n_snap][ny_t][nx_t] real amplitudes, m = 0..nx_t-1
+ *       along x, n = 0..ny_t-1 along y (ny_t = 1: a 2-D tank)
+ *   nx_t: 2 (nx_t - 1) a power of two in [4, SWENSE_MAX_FFT]; ny_t = 1 or likewise
+ *   n_snap: 1..SWENSE_MAX_TL time snapshots; Lx, Ly: tank lengths; depth (<= 0: deep)
+ *   out_eta, out_phi, out_phit: device complex64 [n_snap][ny][nx/2+1] (8-byte aligned), filled
+ *   out: host; set to nx = 2 (nx_t - 1), ny = 2 (ny_t - 1) (1 in 2-D), Lx' = 2 Lx, Ly' = 2 Ly,
+ *        the depth, n_snap, omega = NULL and the three output tables.
+ * Passing *out to swense_fields_on_grid (n_tl = n_snap, the snapshots' times) gives the grid of
+ * the doubled domain. Its nodes i <= nx_t - 1 (j <= ny_t - 1) are the tank nodes
+ * x_i = i Lx / (nx_t - 1). swense_interp then evaluates points inside the tank; near a wall its
+ * stencil reads the mirrored nodes, which hold the extension the wall imposes. The highest mode
+ * of each axis (m = nx_t - 1, n = ny_t - 1) is that grid's Nyquist mode, and it is dropped like
+ * every Nyquist mode. Errors: ARG, SIZE, CUDA.
+ */
+int swense_tank_modes(const float* A_eta, const float* A_phi, const float* A_phit, int32_t nx_t,
+                      int32_t ny_t, int32_t n_snap, double Lx, double Ly, double depth,
+                      float* out_eta, float* out_phi, float* out_phit, swense_modes* out,
+                      void* stream);
+
+/*
  * Stream-function regular waves (paper: subsection on regular waves by stream-function theory,
  * after Rienecker & Fenton; the "analytical evaluation" subsection: with N ~ 10 components,
  * ka = 0.24 converging with N = 9, the fields are summed directly at the cells).

@@ -110,6 +110,11 @@ _SIGS = {
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                           ctypes.c_double, ctypes.c_void_p]),
+    "swense_tank_modes": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.POINTER(swense_modes), ctypes.c_void_p]),
     "swense_workspace_bytes": (ctypes.c_int64, []),
     "swense_release": (ctypes.c_int, []),
     "swense_last_error": (ctypes.c_char_p, []),
@@ -289,6 +294,16 @@ def swense_stream_eval(wave, t, x0, pts, np_, eta=None, u=None, v=None, w=None, 
                        p_mode=P_DYN, rho=1000.0, stream=None):
     _check(load().swense_stream_eval(ctypes.byref(wave), t, x0, _ptr(pts), np_, _ptr(eta), _ptr(u),
                                      _ptr(v), _ptr(w), _ptr(p), p_mode, rho, _stream(stream)))
+
+
+def swense_tank_modes(A_eta, A_phi, A_phit, nx_t, ny_t, n_snap, Lx, Ly, depth, out_eta, out_phi,
+                      out_phit, stream=None):
+    """Returns the swense_modes struct the library filled (pointing at the three outputs)."""
+    m = swense_modes()
+    _check(load().swense_tank_modes(_ptr(A_eta), _ptr(A_phi), _ptr(A_phit), nx_t, ny_t, n_snap, Lx,
+                                    Ly, depth, _ptr(out_eta), _ptr(out_phi), _ptr(out_phit),
+                                    ctypes.byref(m), _stream(stream)))
+    return m
 
 
 def swense_workspace_bytes():

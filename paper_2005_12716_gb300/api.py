@@ -160,6 +160,17 @@ def fv_divergence(u, v, w, area, cell_faces, cell_volume, out=None, stream=None)
     return div
 
 
+def tank_modes(A_eta, A_phi, A_phit, Lx, Ly, depth, stream=None):
+    """swense_tank_modes: device float [n_snap][ny_t][nx_t] tank amplitudes -> DeviceModes of the
+    doubled periodic domain (snapshots, no omega), ready for fields_on_grid."""
+    n_snap, ny_t, nx_t = A_eta.shape
+    nx, ny = 2 * (nx_t - 1), (2 * (ny_t - 1) if ny_t > 1 else 1)
+    dev = A_eta.device
+    outs = [torch.empty((n_snap, ny, nx // 2 + 1, 2), dtype=torch.float32, device=dev) for _ in range(3)]
+    m = S.swense_tank_modes(A_eta, A_phi, A_phit, nx_t, ny_t, n_snap, Lx, Ly, depth, *outs, stream)
+    return DeviceModes(m.nx, m.ny, m.Lx, m.Ly, m.depth, m.n_snap, outs[0], outs[1], outs[2], None, 0.0)
+
+
 def stream_wave(period, height, depth, g=9.81, n=9, height_steps=4):
     """swense_stream_solve (host): the stream-function wave's coefficients."""
     return S.swense_stream_solve(period, height, depth, g, n, height_steps)

@@ -125,3 +125,19 @@ def test_relax_cells_validation(lib):
     assert call([(S.ZONE_X, 1.0, 2.0, 0, 0)], nc=-5) == -1
     assert call([(S.ZONE_X, 1.0, 2.0, 0, 0)]) == -1 and b"NULL" in lib.swense_last_error()
     assert call([(S.ZONE_X, 1.0, 2.0, 0, 0)], nc=0) == 0                     # nothing to do
+
+
+def test_tank_modes_validation(lib):
+    import ctypes
+    from paper_2005_12716_gb300 import _swense as S
+    S.load()
+    m = S.swense_modes()
+    call = lambda nx, ny, ns=1, L=4.0: lib.swense_tank_modes(8, 8, 8, nx, ny, ns, L, 2.0, 1.0, 8, 8, 8,  # noqa: E731
+                                                             ctypes.byref(m), None)
+    assert call(4, 1) == -2                  # 2 (4 - 1) = 6 is not a power of two
+    assert call(2, 1) == -2
+    assert call(65, 4) == -2
+    assert call(65, 33, ns=0) == -1
+    assert call(65, 33, ns=5) == -1
+    assert call(65, 33, L=-1.0) == -1
+    assert lib.swense_tank_modes(None, 8, 8, 65, 33, 1, 4.0, 2.0, 1.0, 8, 8, 8, ctypes.byref(m), None) == -1

@@ -178,3 +178,23 @@ def progressive_wave(mesh_dims=(160, 128, 100), seed=SEED0 + 7):
                             radial_ratio=(1.02 ** (160.0 / n_r)))
     return {"name": "progressive_wave", "T": T, "H": H, "h": h, "n": n, "g": g, "mesh": mesh,
             "lambda": lam, "t_query": 0.37 * T, "x0": 0.0}
+
+
+def tank3d(nx_t=257, ny_t=129, Lx=16.0, Ly=8.0, depth=1.0, n_levels=64, mesh_dims=(160, 128, 100),
+           seed=SEED0 + 8):
+    """A wave tank of 16 x 8 (peak wavelength 1) and depth 1 with 257 x 129 cosine modes in two
+    snapshots dt apart (the mirrored periodic grid is 512 x 256, as in jonswap3d), 64 levels
+    clustered at the surface, and the cylinder O-grid of jonswap3d centred in the tank."""
+    from . import seas as S_
+    snaps = [S_.tank_modes(nx_t, ny_t, Lx, Ly, depth, 0.01, seed=seed + i) for i in range(2)]
+    Hs = 0.05
+    z = P.levels_surface_clustered(-1.0, 1.5 * Hs, n_levels, n_band=max(4, (3 * n_levels) // 8),
+                                   band=1.5 * Hs)
+    n_r, n_t, n_z = mesh_dims
+    n_band = max(2, int(round(0.6 * n_z)))
+    z_edges = M.clustered_z_edges(-0.9, 0.07, n_z, -1.5 * Hs, 0.07, n_band)
+    mesh = M.cylinder_ogrid((0.5 * Lx, 0.5 * Ly), 0.039, 2.0, n_r, n_t, z_edges,
+                            radial_ratio=(1.02 ** (160.0 / n_r)))
+    dt = 0.05
+    return {"name": "tank3d", "snaps": snaps, "Lx": Lx, "Ly": Ly, "depth": depth, "z_levels": z,
+            "mesh": mesh, "t_levels": np.array([0.0, dt]), "t_query": 0.37 * dt}
