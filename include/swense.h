@@ -98,7 +98,7 @@ typedef struct swense_modes {
 /* The reconstruction ("HOS") grid: nx_r = pad_n*nx by ny_r = pad_n*ny (ny_r = 1 in 2-D)
  * uniform nodes x_i = i Lx/nx_r, y_j = j Ly/ny_r, at nz arbitrary levels. */
 typedef struct swense_grid_desc {
-  int32_t pad_n;           /* zero-padding factor: 1, 2, 4 or 8 */
+  int32_t pad_n;           /* zero-padding factor, 1..8 (the paper asks for an integer) */
   int32_t nz;              /* number of levels, 4 <= nz <= SWENSE_MAX_LEVELS */
   const float* z_levels;   /* host [nz], strictly increasing */
   int32_t scheme;          /* enum swense_scheme */
@@ -116,6 +116,13 @@ typedef struct swense_grid_desc {
  * Outputs (device, caller-allocated, 16-byte aligned):
  *   nodes  float [n_tl][nz][ny_r][nx_r][4] = (u, v, w, dphi/dt) per node
  *   eta    float [n_tl][ny_r][nx_r]
+ * Padding factors that are not powers of two (3, 5, 6, 7; the paper only requires an integer):
+ * with pad_n = q p2, q odd, the node x_{qJ+s} is the p2-padded node x_J moved by s Lx/nx_r, so
+ * the grid is built from q^2 (q in 2-D) power-of-two transforms of the modes times
+ * e^{i k.shift} (the shift theorem), each scattered to every q-th node. The workspace then also
+ * holds one such sub-grid. swense_fields_on_grid_noalloc and swense_autotune_grid take
+ * power-of-two factors only (SWENSE_ERR_UNSUPPORTED otherwise); the tuned launch shape of the
+ * factor p2 is used.
  * Arithmetic: FP32 transforms, FP32 depth factors with a compensated |k| z product.
  * Uses the scratch workspace (4 * ny_r * (nx/2 + 1) complex64 per level of a level chunk, each
  * row padded to whole 128-byte lines; twice that for transform variant 5) when ny > 1. When

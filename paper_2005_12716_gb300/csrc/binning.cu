@@ -32,7 +32,9 @@ __device__ __forceinline__ int cell_of(float x, float hi, float lo, int n) {
   int i = int(fl);
   if (f < 0.f) i -= 1;
   else if (f >= 1.f) i += 1;
-  return i & (n - 1);
+  if ((n & (n - 1)) == 0) return i & (n - 1);       // power-of-two node count
+  const int r = i % n;
+  return r < 0 ? r + n : r;
 }
 
 __device__ __forceinline__ unsigned tile_key(const BinArgs& a, int64_t i) {
@@ -134,8 +136,8 @@ extern "C" int swense_bin_points(const swense_grid* g, const float* pts, int64_t
   if (np < 0 || np > int64_t(0x7fffffff)) return fail(SWENSE_ERR_SIZE, "np must be in [0, 2^31)");
   if (np == 0) return SWENSE_OK;
   if (!pts || !perm || !pts_sorted) return fail(SWENSE_ERR_ARG, "NULL points or outputs");
-  if (!is_pow2(g->nx_r) || g->nx_r < 4 || g->nx_r > SWENSE_MAX_FFT || !is_pow2(g->ny_r) ||
-      (g->ny_r != 1 && g->ny_r < 4) || g->ny_r > SWENSE_MAX_FFT)
+  if ((g->nx_r & 1) || g->nx_r < 4 || g->nx_r > SWENSE_MAX_FFT ||
+      (g->ny_r != 1 && ((g->ny_r & 1) || g->ny_r < 4)) || g->ny_r > SWENSE_MAX_FFT)
     return fail(SWENSE_ERR_SIZE, "grid sizes");
   if (g->nz < 4 || g->nz > SWENSE_MAX_LEVELS) return fail(SWENSE_ERR_LEVELS, "need 4 <= nz <= SWENSE_MAX_LEVELS");
   if (!(g->Lx > 0) || (g->ny_r > 1 && !(g->Ly > 0))) return fail(SWENSE_ERR_ARG, "domain lengths");
@@ -150,8 +152,8 @@ extern "C" int swense_bin_points(const swense_grid* g, const float* pts, int64_t
   a.Nxr = g->nx_r;
   a.Nyr = g->ny_r;
   a.nz = g->nz;
-  a.tx = std::max(1, g->nx_r / kTileX);
-  a.ty = std::max(1, g->ny_r / kTileY);
+  a.tx = std::max(1, (g->nx_r + kTileX - 1) / kTileX);
+  a.ty = std::max(1, (g->ny_r + kTileY - 1) / kTileY);
   split2(double(g->nx_r) / g->Lx, a.sx_hi, a.sx_lo);
   if (g->ny_r > 1) split2(double(g->ny_r) / g->Ly, a.sy_hi, a.sy_lo);
   const int64_t nkeys = int64_t(g->nz - 3) * a.ty * a.tx;

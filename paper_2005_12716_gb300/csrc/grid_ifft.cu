@@ -1196,7 +1196,7 @@ int plan_grid(const swense_modes* md, int32_t n_tl, const double* t, const swens
   if (!is_pow2(nx) || nx < 4 || !is_pow2(ny) || (ny != 1 && ny < 4))
     return fail(SWENSE_ERR_SIZE, "nx must be a power of two >= 4, ny 1 or a power of two >= 4");
   const int pad = desc->pad_n;
-  if (pad != 1 && pad != 2 && pad != 4 && pad != 8) return fail(SWENSE_ERR_ARG, "pad_n must be 1, 2, 4 or 8");
+  if (pad < 1 || pad > 8) return fail(SWENSE_ERR_ARG, "pad_n must lie in 1..8");
   const int64_t Nxr = int64_t(pad) * nx, Nyr = ny > 1 ? int64_t(pad) * ny : 1;
   if (Nxr > SWENSE_MAX_FFT || Nyr > SWENSE_MAX_FFT)
     return fail(SWENSE_ERR_SIZE, "pad_n*nx and pad_n*ny must not exceed SWENSE_MAX_FFT");
@@ -1549,6 +1549,133 @@ int launch_grid(const GridPlan& p, const swense_modes* md, const double* t, floa
 }  // namespace
 }  // namespace swense
 
+namespace swense {
+namespace {
+
+// Zero-padding by a factor that is not a power of two, pad = q p2 with q odd: the refined node
+// x_I, I = q J + s, is the p2-refined node x_J moved by s Lx / (pad nx), which is the p2-refined
+// transform of the modes times e^{i k_x s Lx / (pad nx)} (the shift theorem; likewise in y).
+// So the grid is q^2 (q in 2-D) power-of-two transforms of phase-shifted modes, each scattered
+// to every q-th node. The spline prefilter, which depends on the final node spacing, is applied
+// here, and the shifted transforms run as Lagrange grids.
+__global__ void __launch_bounds__(256) k_shift_modes(const float2* __restrict__ ae, const float2* __restrict__ ap,
+                                                     const float2* __restrict__ at, int nx, int ny, int64_t total,
+                                                     int sx, int sy, int Nxr, int Nyr, int spline,
+                                                     float2* __restrict__ oe, float2* __restrict__ op,
+                                                     float2* __restrict__ ot) {
+  const int nh1 = nx / 2 + 1;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total;
+       i += int64_t(gridDim.x) * blockDim.x) {
+    const int m = int(i % nh1);
+    const int r = int((i / nh1) % ny);
+    const int n = ny == 1 ? 0 : (r < ny / 2 ? r : r - ny);
+    // phase in turns, reduced exactly in integers: m sx / Nxr + n sy / Nyr
+    const int tx = int((int64_t(m) * sx) % Nxr);
+    const int ty = ny == 1 ? 0 : int(((int64_t(n) * sy) % Nyr + Nyr) % Nyr);
+    float tau = float(tx) / float(Nxr) + (ny == 1 ? 0.f : float(ty) / float(Nyr));
+    tau -= floorf(tau);
+    float sn, cs;
+    sincospif(2.f * tau, &sn, &cs);
+    const float f = spline ? spline_prefilter(m, Nxr, n, Nyr) : 1.f;
+    const float c = f * cs, s2 = f * sn;
+    const float2 e = __ldg(&ae[i]), p = __ldg(&ap[i]), t = __ldg(&at[i]);
+    oe[i] = make_float2(c * e.x - s2 * e.y, c * e.y + s2 * e.x);
+    op[i] = make_float2(c * p.x - s2 * p.y, c * p.y + s2 * p.x);
+    ot[i] = make_float2(c * t.x - s2 * t.y, c * t.y + s2 * t.x);
+  }
+}
+
+// Sub-grid node (tl, level, J_y, J_x) -> refined node (tl, level, qy J_y + sy, q J_x + sx).
+__global__ void __launch_bounds__(256) k_scatter_grid(const float4* __restrict__ sn, const float* __restrict__ se,
+                                                      int64_t n_nodes, int64_t n_eta, int nxs, int nys, int q,
+                                                      int qy, int sx, int sy, int64_t Nxr, int64_t Nyr,
+                                                      float4* __restrict__ nodes, float* __restrict__ eta) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n_nodes + n_eta;
+       i += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t k = i < n_nodes ? i : i - n_nodes;
+    const int64_t jx = k % nxs, rest = k / nxs;
+    const int64_t jy = rest % nys, slab = rest / nys;            // slab: (tl, level) or tl
+    const int64_t o = (slab * Nyr + qy * jy + sy) * Nxr + q * jx + sx;
+    if (i < n_nodes) nodes[o] = __ldg(&sn[k]);
+    else eta[o] = __ldg(&se[k]);
+  }
+}
+
+}  // namespace
+}  // namespace swense
+
+using namespace swense;
+
+namespace swense {
+namespace {
+
+int fields_on_grid_shifted(const GridPlan& p, const swense_modes* md, const double* t, float* nodes,
+                           float* eta, cudaStream_t stream) {
+  int q = p.pad, p2 = 1;
+  while (!(q & 1)) {
+    q >>= 1;
+    p2 <<= 1;
+  }
+  const int qy = p.ny > 1 ? q : 1;
+  // the plan of one shifted power-of-two transform
+  GridPlan sp = p;
+  sp.pad = p2;
+  sp.spline = 0;
+  sp.Nxr = int64_t(p2) * p.nx;
+  sp.Nyr = p.ny > 1 ? int64_t(p2) * p.ny : 1;
+  sp.per_level = size_t(4) * sp.Nyr * trans_ld(sp.Mh) * sizeof(float2);
+  sp.geta_bytes = p.ny > 1 ? size_t(sp.Nyr) * sp.Mh * sizeof(float2) : 0;
+  const Tune tn = tuned(p.nx, p.ny, p2, p.nz);
+  const int chunk = p.ny > 1 ? int(std::max<size_t>(1, std::min<size_t>(p.nz, tn.chunk_bytes / sp.per_level))) : 0;
+  const bool pair = pair_path(sp.ny, sp.Nxr, sp.Nyr);
+  const int lpc = tn.lpc >= 0 ? tn.lpc : (pair ? 4 : ((sp.Nxr <= 512 && sp.Nyr <= 512) ? kColLevels : 0));
+  const int rowv0 = tn.lpc >= 0 ? tn.rowv : (pair ? 2 : 0);
+  const int rowv = rowv0 == 5 ? 2 : rowv0;                    // one stream for the sub-grids
+  const size_t scratch = align256(scratch_bytes(sp, chunk, 1));
+  const int64_t sub_nodes = int64_t(p.n_tl) * p.nz * sp.Nyr * sp.Nxr;
+  const int64_t sub_eta = int64_t(p.n_tl) * sp.Nyr * sp.Nxr;
+  const int64_t nmodes = int64_t(md->n_snap) * p.ny * p.nxh1;
+  const size_t b_nodes = align256(size_t(sub_nodes) * sizeof(float4));
+  const size_t b_eta = align256(size_t(sub_eta) * sizeof(float));
+  const size_t b_modes = align256(size_t(nmodes) * sizeof(float2));
+  void* ws = nullptr;
+  int st = workspace(scratch + b_nodes + b_eta + 3 * b_modes, stream, &ws);
+  if (st) return st;
+  char* base = static_cast<char*>(ws);
+  float4* snodes = reinterpret_cast<float4*>(base + scratch);
+  float* seta = reinterpret_cast<float*>(base + scratch + b_nodes);
+  float2* sm = reinterpret_cast<float2*>(base + scratch + b_nodes + b_eta);
+  swense_modes shifted = *md;
+  shifted.A_eta = reinterpret_cast<const float*>(sm);
+  shifted.A_phi = reinterpret_cast<const float*>(sm + b_modes / sizeof(float2));
+  shifted.A_phit = reinterpret_cast<const float*>(sm + 2 * (b_modes / sizeof(float2)));
+  const int threads = 256;
+  for (int sy = 0; sy < qy; ++sy) {
+    for (int sx = 0; sx < q; ++sx) {
+      const int64_t mb = std::min<int64_t>((nmodes + threads - 1) / threads, int64_t(1) << 20);
+      k_shift_modes<<<unsigned(mb), threads, 0, stream>>>(
+          reinterpret_cast<const float2*>(md->A_eta), reinterpret_cast<const float2*>(md->A_phi),
+          reinterpret_cast<const float2*>(md->A_phit), p.nx, p.ny, nmodes, sx, sy, int(p.Nxr), int(p.Nyr),
+          p.spline, sm, sm + b_modes / sizeof(float2), sm + 2 * (b_modes / sizeof(float2)));
+      SWENSE_CUDA_TRY(cudaGetLastError());
+      count_launches(1);
+      st = launch_grid(sp, &shifted, t, reinterpret_cast<float*>(snodes), seta, ws, chunk, stream, lpc, rowv, 0, 0);
+      if (st) return st;
+      const int64_t tot = sub_nodes + sub_eta;
+      const int64_t gb = std::min<int64_t>((tot + threads - 1) / threads, int64_t(152) * 64);
+      k_scatter_grid<<<unsigned(gb), threads, 0, stream>>>(snodes, seta, sub_nodes, sub_eta, int(sp.Nxr),
+                                                           int(sp.Nyr), q, qy, sx, sy, p.Nxr, p.Nyr,
+                                                           reinterpret_cast<float4*>(nodes), eta);
+      SWENSE_CUDA_TRY(cudaGetLastError());
+      count_launches(1);
+    }
+  }
+  return SWENSE_OK;
+}
+
+}  // namespace
+}  // namespace swense
+
 using namespace swense;
 
 extern "C" int swense_fields_on_grid(const swense_modes* md, int32_t n_tl, const double* t,
@@ -1558,6 +1685,7 @@ extern "C" int swense_fields_on_grid(const swense_modes* md, int32_t n_tl, const
   GridPlan p;
   int st = plan_grid(md, n_tl, t, desc, nodes, eta, &p);
   if (st) return st;
+  if (!is_pow2(p.pad)) return fields_on_grid_shifted(p, md, t, nodes, eta, stream);
   const Tune tn = tuned(p.nx, p.ny, p.pad, p.nz);
   const int chunk = p.ny > 1 ? int(std::max<size_t>(1, std::min<size_t>(p.nz, tn.chunk_bytes / p.per_level))) : 0;
   void* ws = nullptr;
@@ -1583,6 +1711,8 @@ extern "C" int swense_autotune_grid(const swense_modes* md, int32_t n_tl, const 
   GridPlan p;
   int st = plan_grid(md, n_tl, t, desc, nodes, eta, &p);
   if (st) return st;
+  if (!is_pow2(p.pad))
+    return fail(SWENSE_ERR_UNSUPPORTED, "autotune the power-of-two factor of the padding instead");
   Tune best{};
   if (p.ny > 1) {
     cudaEvent_t e0, e1;
@@ -1705,6 +1835,8 @@ extern "C" int swense_fields_on_grid_noalloc(const swense_modes* md, int32_t n_t
   GridPlan p;
   int st = plan_grid(md, n_tl, t, desc, nodes, eta, &p);
   if (st) return st;
+  if (!is_pow2(p.pad))
+    return fail(SWENSE_ERR_UNSUPPORTED, "padding factors that are not powers of two need the workspace (swense_fields_on_grid)");
   const size_t cap = size_t(SWENSE_NOALLOC_SCRATCH_BYTES);
   const size_t fixed = scratch_bytes(p, 0);
   int chunk = 0;

@@ -51,10 +51,25 @@ struct InterpArgs {
   int p_mode;
   float rho, g;
   int spline;            // cubic B-spline weights in x and y (grid holds spline coefficients)
+  int p2;                // both node counts are powers of two (mask wrap; the kernels' <true>)
 };
+
+// Periodic node index i mod n. Grids whose horizontal node counts are powers of two (every
+// grid zero-padded by a power of two) wrap with a mask; the others (padding factors 3, 5, 6, 7)
+// take the remainder. The kernels are instantiated for both, so the mask path is unchanged.
+template <bool P2>
+__device__ __forceinline__ int wrapi(int i, int n) {
+  if constexpr (P2) {
+    return i & (n - 1);
+  } else {
+    const int r = i % n;
+    return r < 0 ? r + n : r;
+  }
+}
 
 // Cell index (mod n) and in-cell offset f in [0, 1] of coordinate x for the node spacing
 // 1 / (s_hi + s_lo); the product is carried as an unevaluated sum (fma residual).
+template <bool P2 = true>
 __device__ __forceinline__ void locate(float x, float s_hi, float s_lo, int n, int& i0, float& f) {
   const float p = x * s_hi;
   const float e = fmaf(x, s_hi, -p);
@@ -69,7 +84,7 @@ __device__ __forceinline__ void locate(float x, float s_hi, float s_lo, int n, i
     f -= 1.f;
     i += 1;
   }
-  i0 = i & (n - 1);
+  i0 = wrapi<P2>(i, n);
 }
 
 // Uniform cubic B-spline basis of the coefficients -1, 0, 1, 2 at f.
@@ -127,16 +142,17 @@ struct PointCell {
 };
 
 // Horizontal part of a point's cell: first stencil nodes and weights in x and y.
+template <bool P2 = true>
 __device__ __forceinline__ void point_xy(const InterpArgs& a, float x, float y, PointCell& c) {
   float fx;
-  locate(x, a.sx_hi, a.sx_lo, a.Nxr, c.ix, fx);
+  locate<P2>(x, a.sx_hi, a.sx_lo, a.Nxr, c.ix, fx);
   if (a.spline) bspline4(fx, c.wx); else lagrange4_uniform(fx, c.wx);
   c.iy = 0;
   c.wy[0] = 1.f;
   c.wy[1] = c.wy[2] = c.wy[3] = 0.f;
   if (a.Nyr > 1) {
     float fy;
-    locate(y, a.sy_hi, a.sy_lo, a.Nyr, c.iy, fy);
+    locate<P2>(y, a.sy_hi, a.sy_lo, a.Nyr, c.iy, fy);
     if (a.spline) bspline4(fy, c.wy); else lagrange4_uniform(fy, c.wy);
   }
 }
@@ -159,15 +175,17 @@ __device__ __forceinline__ void point_level(const InterpArgs& a, const LevelTabl
   lagrange4(zn, T.inv[c.j0], z, c.wz);
 }
 
+template <bool P2 = true>
 __device__ __forceinline__ PointCell point_cell(const InterpArgs& a, const LevelTables& T, float x,
                                                 float y, float z) {
   PointCell c;
-  point_xy(a, x, y, c);
+  point_xy<P2>(a, x, y, c);
   point_level(a, T, z, c);
   return c;
 }
 
 // Stencil sums straight from global memory (L1/L2), all time levels.
+template <bool P2 = true>
 __device__ __forceinline__ void gather_global(const InterpArgs& a, const PointCell& c, float4& acc,
                                               float& acc_eta) {
   const size_t plane = size_t(a.Nyr) * a.Nxr;
@@ -175,8 +193,8 @@ __device__ __forceinline__ void gather_global(const InterpArgs& a, const PointCe
   int xi[4], yi[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    xi[q] = (c.ix - 1 + q) & (a.Nxr - 1);
-    yi[q] = a.Nyr > 1 ? ((c.iy - 1 + q) & (a.Nyr - 1)) : 0;
+    xi[q] = wrapi<P2>(c.ix - 1 + q, a.Nxr);
+    yi[q] = a.Nyr > 1 ? wrapi<P2>(c.iy - 1 + q, a.Nyr) : 0;
   }
   acc = make_float4(0.f, 0.f, 0.f, 0.f);
   acc_eta = 0.f;
@@ -292,9 +310,10 @@ __device__ __forceinline__ BoxPlan decode_plan(int4 pl) {
 // removed only 6 % of the wavefronts and made more chunks miss the tile).
 __host__ __device__ __forceinline__ int box_zstride(int sbx, int by) { return by * sbx; }
 
+template <bool P2 = true>
 __device__ __forceinline__ int wrap_rel(int i, int ref, int n) {
   // i - ref folded into [-n/2, n/2)
-  return ((i - ref + (n >> 1)) & (n - 1)) - (n >> 1);
+  return wrapi<P2>(i - ref + (n >> 1), n) - (n >> 1);
 }
 
 // Two FP32 lanes packed in 64 bits for the Blackwell paired FMA (fma.rn.f32x2).
@@ -311,6 +330,7 @@ __device__ __forceinline__ float hi2(unsigned long long v) { return __uint_as_fl
 // shared memory (row stride sbx, level-plane stride zst float4), and the eta rows (stride sbx).
 // Rows (ly, lz) over warps, two rows per warp at a time (more loads in flight), x over lanes;
 // the time blend happens here, once per node.
+template <bool P2 = true>
 __device__ __forceinline__ void stage_box(const InterpArgs& a, int x0, int y0, int l0, int bx, int by,
                                           int bz, int sbx, int zst, float4* sbox, float* seta) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -320,10 +340,10 @@ __device__ __forceinline__ void stage_box(const InterpArgs& a, int x0, int y0, i
   for (int r0 = warp; r0 < nrows; r0 += 2 * nw) {
     const int r1 = min(r0 + nw, nrows - 1);       // a duplicate of r0's last row when past the end
     const int lz0 = r0 / by, ly0 = r0 - lz0 * by, lz1 = r1 / by, ly1 = r1 - lz1 * by;
-    const float4* src0 = a.nodes + size_t(l0 + lz0) * plane + size_t((y0 + ly0) & (a.Nyr - 1)) * a.Nxr;
-    const float4* src1 = a.nodes + size_t(l0 + lz1) * plane + size_t((y0 + ly1) & (a.Nyr - 1)) * a.Nxr;
+    const float4* src0 = a.nodes + size_t(l0 + lz0) * plane + size_t(wrapi<P2>(y0 + ly0, a.Nyr)) * a.Nxr;
+    const float4* src1 = a.nodes + size_t(l0 + lz1) * plane + size_t(wrapi<P2>(y0 + ly1, a.Nyr)) * a.Nxr;
     for (int lx = lane; lx < bx; lx += 32) {
-      const int gx = (x0 + lx) & (a.Nxr - 1);
+      const int gx = wrapi<P2>(x0 + lx, a.Nxr);
       float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
       for (int tl = 0; tl < a.n_tl; ++tl) {
         const float4 g0 = __ldg(&src0[size_t(tl) * tl_stride + gx]);
@@ -343,9 +363,9 @@ __device__ __forceinline__ void stage_box(const InterpArgs& a, int x0, int y0, i
     }
   }
   for (int ly = warp; ly < by; ly += nw) {
-    const float* src = a.eta + size_t((y0 + ly) & (a.Nyr - 1)) * a.Nxr;
+    const float* src = a.eta + size_t(wrapi<P2>(y0 + ly, a.Nyr)) * a.Nxr;
     for (int lx = lane; lx < bx; lx += 32) {
-      const int gx = (x0 + lx) & (a.Nxr - 1);
+      const int gx = wrapi<P2>(x0 + lx, a.Nxr);
       float v = 0.f;
       for (int tl = 0; tl < a.n_tl; ++tl) v = fmaf(a.wt[tl], __ldg(&src[size_t(tl) * plane + gx]), v);
       seta[ly * sbx + lx] = v;
@@ -357,6 +377,7 @@ __device__ __forceinline__ void stage_box(const InterpArgs& a, int x0, int y0, i
 // columns x0..x0+bx-1, y0..y0+by-1 (wrapped) into shared memory (row stride sbx), and the eta
 // rows. Columns over all threads (index -> (ly, lx)), so every thread has 4 x n_tl node loads
 // and n_tl eta loads of one column in flight.
+template <bool P2 = true>
 __device__ __forceinline__ void stage_plane(const InterpArgs& a, int x0, int y0, int l0, int bx,
                                             int by, int sbx, const float wz[4], float4* splane,
                                             float* seta) {
@@ -365,7 +386,7 @@ __device__ __forceinline__ void stage_plane(const InterpArgs& a, int x0, int y0,
   const int ncol = bx * by;
   for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
     const int ly = c / bx, lx = c - ly * bx;
-    const size_t col = size_t((y0 + ly) & (a.Nyr - 1)) * a.Nxr + ((x0 + lx) & (a.Nxr - 1));
+    const size_t col = size_t(wrapi<P2>(y0 + ly, a.Nyr)) * a.Nxr + wrapi<P2>(x0 + lx, a.Nxr);
     const float4* src = a.nodes + size_t(l0) * plane + col;
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
     float e = 0.f;
@@ -399,6 +420,7 @@ __host__ __device__ __forceinline__ int64_t plan_blocks(int64_t np) {
   return ((np + BOX_PTS - 1) / BOX_PTS + PLAN_WARPS - 1) / PLAN_WARPS;
 }
 
+template <bool P2>
 __global__ void __launch_bounds__(BOX_THREADS) k_interp_plan(InterpArgs a, Levels L, int4* __restrict__ plan) {
   __shared__ LevelTables zs;
   fill_level_tables(zs, L, a.nz);
@@ -411,7 +433,7 @@ __global__ void __launch_bounds__(BOX_THREADS) k_interp_plan(InterpArgs a, Level
   int refx, refy;
   const float refz = __ldg(&a.pts[3 * p0 + 2]);
   {
-    const PointCell c = point_cell(a, zs, __ldg(&a.pts[3 * p0]), __ldg(&a.pts[3 * p0 + 1]), refz);
+    const PointCell c = point_cell<P2>(a, zs, __ldg(&a.pts[3 * p0]), __ldg(&a.pts[3 * p0 + 1]), refz);
     refx = c.ix;
     refy = c.iy;
   }
@@ -422,10 +444,10 @@ __global__ void __launch_bounds__(BOX_THREADS) k_interp_plan(InterpArgs a, Level
     const int64_t i = p0 + k * 32 + lane;
     if (i < a.np) {
       const float pz = __ldg(&a.pts[3 * i + 2]);
-      const PointCell c = point_cell(a, zs, __ldg(&a.pts[3 * i]), __ldg(&a.pts[3 * i + 1]), pz);
+      const PointCell c = point_cell<P2>(a, zs, __ldg(&a.pts[3 * i]), __ldg(&a.pts[3 * i + 1]), pz);
       same_z &= __float_as_int(pz) == __float_as_int(refz);
-      const int rx = wrap_rel(c.ix, refx, a.Nxr);
-      const int ry = a.Nyr > 1 ? wrap_rel(c.iy, refy, a.Nyr) : 0;
+      const int rx = wrap_rel<P2>(c.ix, refx, a.Nxr);
+      const int ry = a.Nyr > 1 ? wrap_rel<P2>(c.iy, refy, a.Nyr) : 0;
       mn[0] = min(mn[0], rx);
       mx[0] = max(mx[0], rx);
       mn[1] = min(mn[1], ry);
@@ -452,12 +474,13 @@ __global__ void __launch_bounds__(BOX_THREADS) k_interp_plan(InterpArgs a, Level
   const bool inside_grid = bx <= a.Nxr && by <= a.Nyr;
   const bool fits = int64_t(zst) * bz <= BOX_NODES && int64_t(sbx) * by <= BOX_COLS && inside_grid;
   const bool fits_flat = flat && int64_t(sbx) * by <= FLAT_COLS && inside_grid;
-  const int x0 = (refx + mn[0] - 1) & (a.Nxr - 1);
-  const int y0 = a.Nyr > 1 ? ((refy + mn[1] - 1) & (a.Nyr - 1)) : 0;
+  const int x0 = wrapi<P2>(refx + mn[0] - 1, a.Nxr);
+  const int y0 = a.Nyr > 1 ? wrapi<P2>(refy + mn[1] - 1, a.Nyr) : 0;
   plan[chunk] = fits_flat ? make_int4(x0, y0, mn[2] | FLAT_BIT, bx | (by << 12))
                           : make_int4(x0, y0, mn[2], fits ? (bx | (by << 11) | (bz << 22)) : -1);
 }
 
+template <bool P2>
 __global__ void __launch_bounds__(BOX_THREADS, 3) k_interp_box(InterpArgs a, Levels L,
                                                                 const int4* __restrict__ plan) {
   extern __shared__ float4 sbox[];
@@ -485,10 +508,10 @@ __global__ void __launch_bounds__(BOX_THREADS, 3) k_interp_box(InterpArgs a, Lev
       const int64_t i = p0 + k * BOX_THREADS + threadIdx.x;
       if (i >= a.np) continue;
       const float pz = __ldg(&a.pts[3 * i + 2]);
-      const PointCell c = point_cell(a, zs, __ldg(&a.pts[3 * i]), __ldg(&a.pts[3 * i + 1]), pz);
+      const PointCell c = point_cell<P2>(a, zs, __ldg(&a.pts[3 * i]), __ldg(&a.pts[3 * i + 1]), pz);
       float4 acc;
       float acc_eta;
-      gather_global(a, c, acc, acc_eta);
+      gather_global<P2>(a, c, acc, acc_eta);
       store_point(a, i, acc, acc_eta, pz, c.inside);
     }
     return;
@@ -507,7 +530,7 @@ __global__ void __launch_bounds__(BOX_THREADS, 3) k_interp_box(InterpArgs a, Lev
     PointCell cz;
     point_level(a, zs, zc, cz);
     float* fe = reinterpret_cast<float*>(sbox + FLAT_COLS);
-    stage_plane(a, x0, y0, l0, bx, by, sbx, cz.wz, sbox, fe);
+    stage_plane<P2>(a, x0, y0, l0, bx, by, sbx, cz.wz, sbox, fe);
     __syncthreads();
 #pragma unroll 1
     for (int k = 0; k < BOX_PPT; ++k) {
@@ -519,9 +542,9 @@ __global__ void __launch_bounds__(BOX_THREADS, 3) k_interp_box(InterpArgs a, Lev
         ny_ = __ldg(&a.pts[3 * (i + BOX_THREADS) + 1]);
       }
       PointCell c;
-      point_xy(a, px, py, c);
-      const int lx = min(max((c.ix - 1 - x0) & (a.Nxr - 1), 0), bx - 4);
-      const int ly = a.Nyr > 1 ? min(max((c.iy - 1 - y0) & (a.Nyr - 1), 0), by - 4) : 0;
+      point_xy<P2>(a, px, py, c);
+      const int lx = min(max(wrapi<P2>(c.ix - 1 - x0, a.Nxr), 0), bx - 4);
+      const int ly = a.Nyr > 1 ? min(max(wrapi<P2>(c.iy - 1 - y0, a.Nyr), 0), by - 4) : 0;
       const float4* base = sbox + ly * sbx + lx;
       const float* ebase = fe + ly * sbx + lx;
       unsigned long long uv = pack2(0.f, 0.f), wt = pack2(0.f, 0.f);
@@ -544,7 +567,7 @@ __global__ void __launch_bounds__(BOX_THREADS, 3) k_interp_box(InterpArgs a, Lev
     return;
   }
   const int zst = box_zstride(sbx, by);
-  stage_box(a, x0, y0, l0, bx, by, bz, sbx, zst, sbox, seta);
+  stage_box<P2>(a, x0, y0, l0, bx, by, bz, sbx, zst, sbox, seta);
   __syncthreads();
   const int zstride = zst;
 #pragma unroll 1
@@ -557,11 +580,11 @@ __global__ void __launch_bounds__(BOX_THREADS, 3) k_interp_box(InterpArgs a, Lev
       ny_ = __ldg(&a.pts[3 * (i + BOX_THREADS) + 1]);
       nz_ = __ldg(&a.pts[3 * (i + BOX_THREADS) + 2]);
     }
-    const PointCell c = point_cell(a, zs, px, py, pz);
+    const PointCell c = point_cell<P2>(a, zs, px, py, pz);
     // node offsets inside the box; the plan kernel bounded them with the same point_cell, and
     // the clamps keep every shared-memory read inside the box regardless
-    const int lx = min(max((c.ix - 1 - x0) & (a.Nxr - 1), 0), bx - 4);
-    const int ly = a.Nyr > 1 ? min(max((c.iy - 1 - y0) & (a.Nyr - 1), 0), by - 4) : 0;
+    const int lx = min(max(wrapi<P2>(c.ix - 1 - x0, a.Nxr), 0), bx - 4);
+    const int ly = a.Nyr > 1 ? min(max(wrapi<P2>(c.iy - 1 - y0, a.Nyr), 0), by - 4) : 0;
     const int lz = min(max(c.j0 - l0, 0), bz - 4);
     const float4* base = sbox + lz * zst + ly * sbx + lx;
     unsigned long long uv = pack2(0.f, 0.f), wt = pack2(0.f, 0.f);
@@ -961,9 +984,11 @@ int prepare_interp(const swense_grid* g, double t, const float* pts, int64_t np,
     return fail(SWENSE_ERR_ARG, "NULL grid, grid arrays or level lists");
   if (np < 0) return fail(SWENSE_ERR_ARG, "np must be >= 0");
   if (np > 0 && !pts) return fail(SWENSE_ERR_ARG, "NULL pts");
-  if (!is_pow2(g->nx_r) || g->nx_r < 4 || g->nx_r > SWENSE_MAX_FFT || !is_pow2(g->ny_r) ||
-      (g->ny_r != 1 && g->ny_r < 4) || g->ny_r > SWENSE_MAX_FFT)
-    return fail(SWENSE_ERR_SIZE, "nx_r must be a power of two in [4, MAX], ny_r 1 or a power of two in [4, MAX]");
+  // node counts: even in [4, MAX] (powers of two, or a non-power-of-two padding factor times
+  // one); ny_r = 1 for a 2-D grid
+  if ((g->nx_r & 1) || g->nx_r < 4 || g->nx_r > SWENSE_MAX_FFT ||
+      (g->ny_r != 1 && ((g->ny_r & 1) || g->ny_r < 4)) || g->ny_r > SWENSE_MAX_FFT)
+    return fail(SWENSE_ERR_SIZE, "nx_r must be even in [4, MAX], ny_r 1 or even in [4, MAX]");
   if (g->nz < 4 || g->nz > SWENSE_MAX_LEVELS) return fail(SWENSE_ERR_LEVELS, "need 4 <= nz <= SWENSE_MAX_LEVELS");
   if (g->n_tl < 1 || g->n_tl > SWENSE_MAX_TL) return fail(SWENSE_ERR_ARG, "n_tl must be in [1, SWENSE_MAX_TL]");
   if (p_mode != SWENSE_P_DYN && p_mode != SWENSE_P_PHIT && p_mode != SWENSE_P_TOTAL)
@@ -1029,6 +1054,7 @@ int prepare_interp(const swense_grid* g, double t, const float* pts, int64_t np,
   if (g->scheme != SWENSE_LAGRANGE3 && g->scheme != SWENSE_SPLINE3)
     return fail(SWENSE_ERR_ARG, "unknown interpolation scheme");
   a->spline = g->scheme == SWENSE_SPLINE3;
+  a->p2 = is_pow2(g->nx_r) && is_pow2(g->ny_r);
   return SWENSE_OK;
 }
 
@@ -1047,6 +1073,7 @@ extern "C" int swense_mlp_features(const swense_grid* g, double t, const float* 
   if (st) return st;
   if (g->ny_r < 4) return fail(SWENSE_ERR_UNSUPPORTED, "the learned correction needs a 3-D grid");
   if (a.spline) return fail(SWENSE_ERR_UNSUPPORTED, "the learned correction is defined on LAGRANGE3 grids");
+  if (!a.p2) return fail(SWENSE_ERR_UNSUPPORTED, "the learned correction needs power-of-two node counts");
   if (np == 0) return SWENSE_OK;
   if (!x || !scale || !lagrange) return fail(SWENSE_ERR_ARG, "NULL feature outputs");
   FeatArgs f{a, x, scale, lagrange, eta};
@@ -1068,6 +1095,7 @@ extern "C" int swense_interp_learned(const swense_grid* g, double t, const float
   if (st) return st;
   if (g->ny_r < 4) return fail(SWENSE_ERR_UNSUPPORTED, "the learned correction needs a 3-D grid");
   if (a.spline) return fail(SWENSE_ERR_UNSUPPORTED, "the learned correction is defined on LAGRANGE3 grids");
+  if (!a.p2) return fail(SWENSE_ERR_UNSUPPORTED, "the learned correction needs power-of-two node counts");
   if (!packed) return fail(SWENSE_ERR_ARG, "NULL packed weights");
   if (reinterpret_cast<uintptr_t>(packed) & 15) return fail(SWENSE_ERR_ARG, "packed weights must be 16-byte aligned");
   // workspace: [0, 256) out-of-range counter, then one int4 box plan per 1024-point chunk
@@ -1086,7 +1114,7 @@ extern "C" int swense_interp_learned(const swense_grid* g, double t, const float
     a.o_p = p;
     a.n_oor = n_out_of_range ? d_count : nullptr;
     int4* plan = reinterpret_cast<int4*>(static_cast<char*>(ws) + 256);
-    k_interp_plan<<<unsigned(plan_blocks(np)), BOX_THREADS, 0, stream>>>(a, lev, plan);
+    k_interp_plan<true><<<unsigned(plan_blocks(np)), BOX_THREADS, 0, stream>>>(a, lev, plan);
     SWENSE_CUDA_TRY(cudaGetLastError());
     SWENSE_CUDA_TRY(cudaFuncSetAttribute((const void*)k_interp_learned,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, int(LRN_SMEM)));
@@ -1139,14 +1167,16 @@ int interp_impl(const swense_grid* g, double t, const float* pts, const int32_t*
     const int4* plan = plan_in;
     if (!plan) {
       int4* pw = reinterpret_cast<int4*>(static_cast<char*>(ws) + 256);
-      k_interp_plan<<<unsigned(plan_blocks(np)), BOX_THREADS, 0, stream>>>(a, lev, pw);
+      if (a.p2) k_interp_plan<true><<<unsigned(plan_blocks(np)), BOX_THREADS, 0, stream>>>(a, lev, pw);
+      else k_interp_plan<false><<<unsigned(plan_blocks(np)), BOX_THREADS, 0, stream>>>(a, lev, pw);
       SWENSE_CUDA_TRY(cudaGetLastError());
       count_launches(1);
       plan = pw;
     }
-    SWENSE_CUDA_TRY(cudaFuncSetAttribute((const void*)k_interp_box,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(BOX_SMEM)));
-    k_interp_box<<<unsigned(blocks), BOX_THREADS, BOX_SMEM, stream>>>(a, lev, plan);
+    const void* kbox = a.p2 ? (const void*)k_interp_box<true> : (const void*)k_interp_box<false>;
+    SWENSE_CUDA_TRY(cudaFuncSetAttribute(kbox, cudaFuncAttributeMaxDynamicSharedMemorySize, int(BOX_SMEM)));
+    if (a.p2) k_interp_box<true><<<unsigned(blocks), BOX_THREADS, BOX_SMEM, stream>>>(a, lev, plan);
+    else k_interp_box<false><<<unsigned(blocks), BOX_THREADS, BOX_SMEM, stream>>>(a, lev, plan);
     SWENSE_CUDA_TRY(cudaGetLastError());
     count_launches(1);
   }
@@ -1178,7 +1208,8 @@ extern "C" int swense_interp_plan(const swense_grid* g, const float* pts, int64_
   if (!plan || (reinterpret_cast<uintptr_t>(plan) & 15)) return fail(SWENSE_ERR_ARG, "plan must be non-NULL and 16-byte aligned");
   const int64_t blocks = (np + BOX_PTS - 1) / BOX_PTS;
   if (blocks >= (int64_t(1) << 31)) return fail(SWENSE_ERR_SIZE, "too many points for one call");
-  k_interp_plan<<<unsigned(plan_blocks(np)), BOX_THREADS, 0, stream>>>(a, lev, static_cast<int4*>(plan));
+  if (a.p2) k_interp_plan<true><<<unsigned(plan_blocks(np)), BOX_THREADS, 0, stream>>>(a, lev, static_cast<int4*>(plan));
+  else k_interp_plan<false><<<unsigned(plan_blocks(np)), BOX_THREADS, 0, stream>>>(a, lev, static_cast<int4*>(plan));
   SWENSE_CUDA_TRY(cudaGetLastError());
   count_launches(1);
   return SWENSE_OK;

@@ -59,10 +59,19 @@ def test_argument_validation_launches_nothing(lib):
     import numpy as np
     from paper_2005_12716_gb300 import _swense as S
     z = np.array([-1, -0.5, 0.0, 0.1], np.float32)
-    desc = S.make_grid_desc(3, z)          # pad_n = 3 is not allowed
+    desc = S.make_grid_desc(9, z)          # pad_n must lie in 1..8
     m = S.swense_modes(8, 1, 1.0, 1.0, 0.0, 1, 16, 16, 16, None, 0.0)
     st = lib.swense_fields_on_grid(ctypes.byref(m), 1, None, ctypes.byref(desc), 16, 16, None)
     assert st == -1 and b"pad_n" in lib.swense_last_error()
+    desc0 = S.make_grid_desc(0, z)
+    assert lib.swense_fields_on_grid(ctypes.byref(m), 1, None, ctypes.byref(desc0), 16, 16, None) == -1
+    # a padding factor that is not a power of two needs the workspace: the allocation-free entry
+    # point and the autotuner decline it before any CUDA call
+    desc3 = S.make_grid_desc(3, z)
+    assert lib.swense_fields_on_grid_noalloc(ctypes.byref(m), 1, None, ctypes.byref(desc3), 16, 16, None) == -7
+    lpc, chunk, rv = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int32()
+    assert lib.swense_autotune_grid(ctypes.byref(m), 1, None, ctypes.byref(desc3), 16, 16, ctypes.byref(lpc),
+                                    ctypes.byref(chunk), ctypes.byref(rv), None) == -7
     desc = S.make_grid_desc(1, z[::-1].copy())
     st = lib.swense_fields_on_grid(ctypes.byref(m), 1, None, ctypes.byref(desc), 16, 16, None)
     assert st == -3
