@@ -430,12 +430,13 @@ __global__ void __launch_bounds__(BOX_THREADS) k_interp_plan(InterpArgs a, Level
   const int64_t p0 = chunk * BOX_PTS;
   if (p0 >= a.np) return;                           // no barrier below
   // every lane derives the chunk's reference cell (its first point's) itself: broadcast loads
-  int refx, refy;
+  int refx, refy, refj0;
   const float refz = __ldg(&a.pts[3 * p0 + 2]);
   {
     const PointCell c = point_cell<P2>(a, zs, __ldg(&a.pts[3 * p0]), __ldg(&a.pts[3 * p0 + 1]), refz);
     refx = c.ix;
     refy = c.iy;
+    refj0 = c.j0;
   }
   int same_z = 1;                                   // every point of the chunk at z == refz (bitwise)
   int mn[3] = {1 << 30, 1 << 30, 1 << 30}, mx[3] = {-(1 << 30), -(1 << 30), -(1 << 30)};
@@ -444,8 +445,14 @@ __global__ void __launch_bounds__(BOX_THREADS) k_interp_plan(InterpArgs a, Level
     const int64_t i = p0 + k * 32 + lane;
     if (i < a.np) {
       const float pz = __ldg(&a.pts[3 * i + 2]);
-      const PointCell c = point_cell<P2>(a, zs, __ldg(&a.pts[3 * i]), __ldg(&a.pts[3 * i + 1]), pz);
-      same_z &= __float_as_int(pz) == __float_as_int(refz);
+      PointCell c;
+      point_xy<P2>(a, __ldg(&a.pts[3 * i]), __ldg(&a.pts[3 * i + 1]), c);
+      // the level window only where z differs from the chunk's first point (a layer of an
+      // extruded mesh shares one z)
+      const bool zeq = __float_as_int(pz) == __float_as_int(refz);
+      same_z &= zeq;
+      if (zeq) c.j0 = refj0;
+      else point_level(a, zs, pz, c);
       const int rx = wrap_rel<P2>(c.ix, refx, a.Nxr);
       const int ry = a.Nyr > 1 ? wrap_rel<P2>(c.iy, refy, a.Nyr) : 0;
       mn[0] = min(mn[0], rx);
