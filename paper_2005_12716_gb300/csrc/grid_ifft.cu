@@ -219,13 +219,19 @@ __global__ void __launch_bounds__(256) k_pass_b(PassBArgs a, Levels L) {
   }
 }
 
-// Linear propagation of stored modes: A(t) = A(t_ref) e^{-i omega (t - t_ref)}. The phase is
-// reduced to turns in FP64 (exact enough for long simulated times); the rotation is FP32.
+// Linear propagation of stored modes: A(t) = A(t_ref) e^{-i omega (t - t_ref)}, every time level
+// in one launch (blockIdx.y). The phase is reduced to turns in FP64 (exact enough for long
+// simulated times); the rotation is FP32.
+struct PropTimes {
+  double dt[64];       // t_l - t_ref per time level (a grid request has at most 64)
+};
 __global__ void k_propagate(const float2* __restrict__ Ae, const float2* __restrict__ Ap,
                             const float2* __restrict__ At, const double* __restrict__ omega,
-                            int nslot, double dt, float2* __restrict__ out) {
+                            int nslot, PropTimes T, float2* __restrict__ out_all) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nslot) return;
+  const double dt = T.dt[blockIdx.y];
+  float2* out = out_all + size_t(blockIdx.y) * 3 * nslot;
   const double turns = omega[i] * dt * 0.15915494309189533577;  // theta / (2 pi)
   const double frac = turns - rint(turns);
   float s, c;
@@ -1359,15 +1365,19 @@ int launch_grid(const GridPlan& p, const swense_modes* md, const double* t, floa
     if (st) return st;
   }
 
+  if (md->omega) {                                // all time levels' modes at once
+    PropTimes T{};
+    for (int l = 0; l < p.n_tl; ++l) T.dt[l] = t[l] - md->t_ref;
+    k_propagate<<<dim3(unsigned((nslot + 255) / 256), unsigned(p.n_tl)), 256, 0, stream>>>(
+        reinterpret_cast<const float2*>(md->A_eta), reinterpret_cast<const float2*>(md->A_phi),
+        reinterpret_cast<const float2*>(md->A_phit), md->omega, int(nslot), T, prop);
+    SWENSE_CUDA_TRY(cudaGetLastError());
+    count_launches(1);
+  }
   for (int l = 0; l < p.n_tl; ++l) {
     const float2 *Ae, *Ap, *At;
     if (md->omega) {
       float2* o = prop + size_t(l) * 3 * nslot;
-      k_propagate<<<unsigned((nslot + 255) / 256), 256, 0, stream>>>(
-          reinterpret_cast<const float2*>(md->A_eta), reinterpret_cast<const float2*>(md->A_phi),
-          reinterpret_cast<const float2*>(md->A_phit), md->omega, int(nslot), t[l] - md->t_ref, o);
-      SWENSE_CUDA_TRY(cudaGetLastError());
-      count_launches(1);
       Ae = o;
       Ap = o + nslot;
       At = o + 2 * nslot;
