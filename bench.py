@@ -422,7 +422,8 @@ def run_ours(args, rank, world):
     # the binding resource of the gather: shared-memory reads per point, 16 float4 + 16 eta for
     # the chunks gathered from a z-collapsed plane, 64 float4 + 16 eta for the 3-D boxes, against
     # 128 B/clk/SM x 152 SMs at the maximum SM clock. The chunk kinds are read from the plan the
-    # library made (int4 per chunk: w < 0 no tile, bit 30 of z set: flat plane).
+    # library made (int4 per chunk: w < 0 no tile, bit 30 of z set: flat plane(s), bit 29 as
+    # well: two planes).
     pl = plan[: S.swense_interp_plan_bytes(npts)].view(torch.int32).view(-1, 4).cpu().numpy()
     per_chunk = np.full(len(pl), 1024)
     per_chunk[-1] = npts - 1024 * (len(pl) - 1)
@@ -434,7 +435,9 @@ def run_ours(args, rank, world):
     tb = NCU_TRAFFIC.get("k_interp_box")
     stages["interp"]["k_interp_box_traffic"] = (tb["bytes"] if tb and tb.get("hash") == src_hash
                                                and tb.get("workload") == desc else None)
-    stages["interp"]["chunks"] = {"flat_plane": int(is_flat.sum()), "box_3d": int(is_box.sum()),
+    is_two = is_flat & ((pl[:, 2] & (1 << 29)) != 0)
+    stages["interp"]["chunks"] = {"flat_plane": int((is_flat & ~is_two).sum()),
+                                  "flat_two_planes": int(is_two.sum()), "box_3d": int(is_box.sum()),
                                   "global": int((pl[:, 3] < 0).sum())}
     stages["interp"]["k_interp_box_shared_memory"] = {
         "achieved": smem_gbs, "peak": smem_peak, "unit": "GB/s", "frac": smem_gbs / smem_peak,

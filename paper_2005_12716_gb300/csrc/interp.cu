@@ -275,15 +275,23 @@ constexpr size_t BOX_SMEM = size_t(BOX_NODES) * sizeof(float4) + size_t(BOX_COLS
 // extruded mesh) stage one z-collapsed plane instead of the box: float4 columns and eta.
 constexpr int FLAT_COLS = 3456;
 static_assert(size_t(FLAT_COLS) * (sizeof(float4) + sizeof(float)) <= BOX_SMEM, "flat plane fits the tile");
+// Chunks whose points lie at two z values (a chunk that straddles two layers) stage two
+// collapsed planes and one eta plane.
+constexpr int FLAT2_COLS = 1920;
+static_assert(size_t(FLAT2_COLS) * (2 * sizeof(float4) + sizeof(float)) <= BOX_SMEM, "two planes fit the tile");
 
 // One chunk's plan, 16 bytes: x0, y0 (first staged node, wrapped), l0 | FLAT_BIT, extents.
 //   3-D box:  w = bx | by << 11 | bz << 22 (bz >= 4), z = l0
 //   flat:     w = bx | by << 12 (4 levels from l0), z = l0 | FLAT_BIT
+//   two z:    w = bx | by << 12, z = FLAT_BIT | FLAT2_BIT (the z values are those of the chunk's
+//             first and last points; their level windows are looked up by the gather)
 //   neither fits the tile: w = -1 (global gathers)
 constexpr int FLAT_BIT = 1 << 30;
+constexpr int FLAT2_BIT = 1 << 29;
 struct BoxPlan {
   int x0, y0, l0, bx, by, bz;
   bool flat;     // z-collapsed plane
+  bool two;      // two z-collapsed planes (flat is set too)
   bool box3d;    // the 3-D box fits BOX_NODES / BOX_COLS
 };
 __device__ __forceinline__ BoxPlan decode_plan(int4 pl) {
@@ -291,6 +299,7 @@ __device__ __forceinline__ BoxPlan decode_plan(int4 pl) {
   b.x0 = pl.x;
   b.y0 = pl.y;
   b.flat = pl.w >= 0 && (pl.z & FLAT_BIT);
+  b.two = b.flat && (pl.z & FLAT2_BIT);
   b.l0 = pl.z & 0xffff;
   if (b.flat) {
     b.bx = pl.w & 4095;
@@ -302,7 +311,7 @@ __device__ __forceinline__ BoxPlan decode_plan(int4 pl) {
     b.bz = (pl.w >> 22) & 511;
   }
   const int sbx = b.bx + ((4 - b.bx) & 7);
-  b.box3d = pl.w >= 0 && (!b.flat || (sbx * b.by * 4 <= BOX_NODES && sbx * b.by <= BOX_COLS));
+  b.box3d = pl.w >= 0 && !b.two && (!b.flat || (sbx * b.by * 4 <= BOX_NODES && sbx * b.by <= BOX_COLS));
   return b;
 }
 
@@ -380,7 +389,7 @@ __device__ __forceinline__ void stage_box(const InterpArgs& a, int x0, int y0, i
 template <bool P2 = true>
 __device__ __forceinline__ void stage_plane(const InterpArgs& a, int x0, int y0, int l0, int bx,
                                             int by, int sbx, const float wz[4], float4* splane,
-                                            float* seta) {
+                                            float* seta, bool with_eta = true) {
   const size_t plane = size_t(a.Nyr) * a.Nxr;
   const size_t tl_stride = size_t(a.nz) * plane;
   const int ncol = bx * by;
@@ -402,10 +411,10 @@ __device__ __forceinline__ void stage_plane(const InterpArgs& a, int x0, int y0,
         v.z = fmaf(w, g.z, v.z);
         v.w = fmaf(w, g.w, v.w);
       }
-      e = fmaf(a.wt[tl], __ldg(&a.eta[size_t(tl) * plane + col]), e);
+      if (with_eta) e = fmaf(a.wt[tl], __ldg(&a.eta[size_t(tl) * plane + col]), e);
     }
     splane[ly * sbx + lx] = v;
-    seta[ly * sbx + lx] = e;
+    if (with_eta) seta[ly * sbx + lx] = e;
   }
 }
 
@@ -439,6 +448,8 @@ __global__ void __launch_bounds__(BOX_THREADS) k_interp_plan(InterpArgs a, Level
     refj0 = c.j0;
   }
   int same_z = 1;                                   // every point of the chunk at z == refz (bitwise)
+  int two_z = 1;                                    // every point at refz or at the last point's z
+  const float lastz = __ldg(&a.pts[3 * ((p0 + BOX_PTS < a.np ? p0 + BOX_PTS : a.np) - 1) + 2]);
   int mn[3] = {1 << 30, 1 << 30, 1 << 30}, mx[3] = {-(1 << 30), -(1 << 30), -(1 << 30)};
 #pragma unroll 4
   for (int k = 0; k < BOX_PTS / 32; ++k) {
@@ -451,6 +462,7 @@ __global__ void __launch_bounds__(BOX_THREADS) k_interp_plan(InterpArgs a, Level
       // extruded mesh shares one z)
       const bool zeq = __float_as_int(pz) == __float_as_int(refz);
       same_z &= zeq;
+      two_z &= zeq || __float_as_int(pz) == __float_as_int(lastz);
       if (zeq) c.j0 = refj0;
       else point_level(a, zs, pz, c);
       const int rx = wrap_rel<P2>(c.ix, refx, a.Nxr);
@@ -471,6 +483,7 @@ __global__ void __launch_bounds__(BOX_THREADS) k_interp_plan(InterpArgs a, Level
     }
   }
   const bool flat = __all_sync(0xffffffffu, same_z);
+  const bool flat2 = !flat && __all_sync(0xffffffffu, two_z);
   if (lane != 0) return;
   // box: x nodes rel (mn0-1) .. (mx0+2), y likewise (one row in 2-D), levels mn2 .. mx2+3
   const int bx = mx[0] - mn[0] + 4;
@@ -481,10 +494,12 @@ __global__ void __launch_bounds__(BOX_THREADS) k_interp_plan(InterpArgs a, Level
   const bool inside_grid = bx <= a.Nxr && by <= a.Nyr;
   const bool fits = int64_t(zst) * bz <= BOX_NODES && int64_t(sbx) * by <= BOX_COLS && inside_grid;
   const bool fits_flat = flat && int64_t(sbx) * by <= FLAT_COLS && inside_grid;
+  const bool fits_two = flat2 && int64_t(sbx) * by <= FLAT2_COLS && inside_grid;
   const int x0 = wrapi<P2>(refx + mn[0] - 1, a.Nxr);
   const int y0 = a.Nyr > 1 ? wrapi<P2>(refy + mn[1] - 1, a.Nyr) : 0;
-  plan[chunk] = fits_flat ? make_int4(x0, y0, mn[2] | FLAT_BIT, bx | (by << 12))
-                          : make_int4(x0, y0, mn[2], fits ? (bx | (by << 11) | (bz << 22)) : -1);
+  plan[chunk] = fits_flat  ? make_int4(x0, y0, mn[2] | FLAT_BIT, bx | (by << 12))
+              : fits_two   ? make_int4(x0, y0, FLAT_BIT | FLAT2_BIT, bx | (by << 12))
+                           : make_int4(x0, y0, mn[2], fits ? (bx | (by << 11) | (bz << 22)) : -1);
 }
 
 template <bool P2>
@@ -530,14 +545,21 @@ __global__ void __launch_bounds__(BOX_THREADS, 3) k_interp_box(InterpArgs a, Lev
   const int x0 = bp.x0, y0 = bp.y0, l0 = bp.l0;
   const int nys = a.Nyr > 1 ? 4 : 1;
   if (bp.flat) {
-    // one z for the whole chunk: level weights once (from the level tables, so after the
-    // barrier that completes them), then a 2-D gather of 16 float4 per point
+    // one z (or two: a chunk across two layers) for the whole chunk: level weights once per z
+    // (from the level tables, so after the barrier that completes them), the z-collapsed
+    // plane(s) and the eta plane, then a 2-D gather of 16 float4 per point
+    const bool two = bp.two;
     const float zc = __ldg(&a.pts[3 * p0 + 2]);
+    const float zc2 = two ? __ldg(&a.pts[3 * ((p0 + BOX_PTS < a.np ? p0 + BOX_PTS : a.np) - 1) + 2]) : zc;
     __syncthreads();
-    PointCell cz;
+    PointCell cz, cz2;
     point_level(a, zs, zc, cz);
-    float* fe = reinterpret_cast<float*>(sbox + FLAT_COLS);
-    stage_plane<P2>(a, x0, y0, l0, bx, by, sbx, cz.wz, sbox, fe);
+    if (two) point_level(a, zs, zc2, cz2);
+    else cz2 = cz;
+    float4* planeB = two ? sbox + FLAT2_COLS : sbox;
+    float* fe = reinterpret_cast<float*>(sbox + (two ? 2 * FLAT2_COLS : FLAT_COLS));
+    stage_plane<P2>(a, x0, y0, cz.j0, bx, by, sbx, cz.wz, sbox, fe);
+    if (two) stage_plane<P2>(a, x0, y0, cz2.j0, bx, by, sbx, cz2.wz, planeB, fe, false);
     __syncthreads();
 #pragma unroll 1
     for (int k = 0; k < BOX_PPT; ++k) {
@@ -547,12 +569,14 @@ __global__ void __launch_bounds__(BOX_THREADS, 3) k_interp_box(InterpArgs a, Lev
       if (k + 1 < BOX_PPT && i + BOX_THREADS < a.np) {
         nx_ = __ldg(&a.pts[3 * (i + BOX_THREADS)]);
         ny_ = __ldg(&a.pts[3 * (i + BOX_THREADS) + 1]);
+        if (two) nz_ = __ldg(&a.pts[3 * (i + BOX_THREADS) + 2]);
       }
+      const bool onA = !two || __float_as_int(pz) == __float_as_int(zc);
       PointCell c;
       point_xy<P2>(a, px, py, c);
       const int lx = min(max(wrapi<P2>(c.ix - 1 - x0, a.Nxr), 0), bx - 4);
       const int ly = a.Nyr > 1 ? min(max(wrapi<P2>(c.iy - 1 - y0, a.Nyr), 0), by - 4) : 0;
-      const float4* base = sbox + ly * sbx + lx;
+      const float4* base = (onA ? sbox : planeB) + ly * sbx + lx;
       const float* ebase = fe + ly * sbx + lx;
       unsigned long long uv = pack2(0.f, 0.f), wt = pack2(0.f, 0.f);
       float acc_eta = 0.f;
@@ -569,7 +593,8 @@ __global__ void __launch_bounds__(BOX_THREADS, 3) k_interp_box(InterpArgs a, Lev
           acc_eta = fmaf(ww, ebase[b * sbx + kx], acc_eta);
         }
       }
-      store_point(a, i, make_float4(lo2(uv), hi2(uv), lo2(wt), hi2(wt)), acc_eta, pz, cz.inside);
+      store_point(a, i, make_float4(lo2(uv), hi2(uv), lo2(wt), hi2(wt)), acc_eta, pz,
+                  onA ? cz.inside : cz2.inside);
     }
     return;
   }

@@ -240,3 +240,19 @@ def test_level_flat_chunks_2d(api):
     pts = _layers(rng, [z[0], z[10], 0.5 * (z[20] + z[21]), z[-1]], 3000, (0.0, 0.0), (0.3 * L, 0.0))
     errs, _, _ = _run(api, cfg["sea"], z, 1, cfg["t_levels"], cfg["t_query"], pts)
     assert max(errs.values()) <= TOL, errs
+
+
+def test_chunks_across_two_layers(api):
+    """Layers whose sizes are not multiples of the 1024-point chunk: chunks that straddle two
+    layers take the two-plane path (first and last point z), chunks with a third z or a point
+    outside the levels in one of the layers are covered too."""
+    cfg = configs.jonswap3d_small()
+    sea, z = cfg["sea"], np.asarray(cfg["z_levels"], np.float32)
+    rng = np.random.default_rng(41)
+    sizes = [1500, 1700, 900, 2100, 1300, 700]
+    zs = [z[2], 0.5 * (z[3] + z[4]), z[-1] + 0.02, z[6], z[0], 0.4 * z[1]]
+    pts = np.concatenate([_layers(rng, [zv], n, (1.0, 1.0), (4.0, 3.0)) for zv, n in zip(zs, sizes)])
+    pts[5000, 2] = np.float32(0.77 * z[2])           # a third z inside one straddling chunk
+    errs, out, ref = _run(api, sea, z, 2, cfg["t_levels"], cfg["t_query"], pts, "total")
+    assert ref["out_of_range"].sum() == 900
+    assert max(errs.values()) <= TOL, errs
