@@ -796,11 +796,24 @@ __global__ void __launch_bounds__(BOX_THREADS, 2) k_interp_learned(InterpArgs a,
   const int64_t p0 = int64_t(blockIdx.x) * BOX_PTS;
   const int4 pl = plan[blockIdx.x];
   const BoxPlan bp = decode_plan(pl);
-  const bool boxed = bp.box3d && bp.l0 + bp.bz <= a.nz;
-  const int bx = bp.bx, by = bp.by, bz = bp.bz;
+  const int bx = bp.bx, by = bp.by;
   const int sbx = bx + ((4 - bx) & 7);
   const int zst = box_zstride(sbx, by);
-  const int x0 = bp.x0, y0 = bp.y0, l0 = bp.l0;
+  int l0 = bp.l0, bz = bp.bz;
+  bool box3d = bp.box3d;
+  if (bp.two) {
+    // a chunk across two layers: the box spans the level windows of its first and last
+    // point's z (the level tables are complete after this barrier)
+    __syncthreads();
+    PointCell ca, cb;
+    point_level(a, zs, __ldg(&a.pts[3 * p0 + 2]), ca);
+    point_level(a, zs, __ldg(&a.pts[3 * ((p0 + BOX_PTS < a.np ? p0 + BOX_PTS : a.np) - 1) + 2]), cb);
+    l0 = min(ca.j0, cb.j0);
+    bz = abs(ca.j0 - cb.j0) + 4;
+    box3d = int64_t(zst) * bz <= BOX_NODES && int64_t(sbx) * by <= BOX_COLS;
+  }
+  const bool boxed = box3d && l0 + bz <= a.nz;
+  const int x0 = bp.x0, y0 = bp.y0;
   const size_t plane = size_t(a.Nyr) * a.Nxr;
   if (boxed) stage_box(a, x0, y0, l0, bx, by, bz, sbx, zst, sbox, seta);
   __syncthreads();
