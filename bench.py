@@ -866,10 +866,10 @@ def run_stream(args, rank, world):
     launches = S.swense_launches() - l0
     nbytes = npts * (12 + 20)
     hbm = _peak_hbm()
-    # FP32 operations per point: 24 per harmonic (17 instructions, 7 of them FMA) and about 30
+    # FP32 operations per point: 19 per harmonic (14 instructions, 5 of them FMA) and about 30
     # for the phase, Bernoulli and stores' arithmetic; sincospif and expf are not counted.
     # Peak: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz.
-    flops = npts * (24 * cfg["n"] + 30)
+    flops = npts * (19 * cfg["n"] + 30)
     fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
     line = {"metric": "wave-field points/sec, stream-function wave (analytical evaluation)",
             "value": job_throughput(npts, world, ms), "unit": "points/s", "n_gpus": world,

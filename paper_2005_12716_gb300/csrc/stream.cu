@@ -149,8 +149,7 @@ struct StreamArgs {
   float k, h, c, cu;           // cu = c - ubar (0 with no mean current)
   float R, g, rho;
   int p_mode;
-  float jkB[SWENSE_STREAM_MAX_N];      // j k B_j
-  float den[SWENSE_STREAM_MAX_N];      // 1 / (1 + e^{-2 j k h})
+  float ajk[SWENSE_STREAM_MAX_N];      // j k B_j / (1 + e^{-2 j k h})
   float E[SWENSE_STREAM_MAX_N + 1];
 };
 
@@ -170,11 +169,13 @@ __global__ void __launch_bounds__(256) k_stream_eval(StreamArgs a, const float* 
     const float e1 = expf(a.k * z), f1 = expf(-2.f * a.k * (z + a.h));
     float cj = c1, sj = s1, ej = e1, fj = f1;
     float eta = a.E[0], u = a.cu, w = 0.f;
+#pragma unroll 4
     for (int j = 1; j <= a.n; ++j) {
-      const float Cj = ej * (1.f + fj) * a.den[j - 1], Sj = ej * (1.f - fj) * a.den[j - 1];
+      // j k B_j C_j = ajk_j (e^{jkz} + e^{jkz} e^{-2jk(z+h)}), and the sinh ratio with a minus
+      const float g = ej * fj;
       eta = fmaf(a.E[j], cj, eta);
-      u = fmaf(a.jkB[j - 1] * Cj, cj, u);
-      w = fmaf(a.jkB[j - 1] * Sj, sj, w);
+      u = fmaf(a.ajk[j - 1] * (ej + g), cj, u);
+      w = fmaf(a.ajk[j - 1] * (ej - g), sj, w);
       const float cn = cj * c1 - sj * s1;
       sj = fmaf(sj, c1, cj * s1);
       cj = cn;
@@ -304,10 +305,8 @@ extern "C" int swense_stream_eval(const swense_stream_wave* wave, double t, doub
   a.g = float(wave->g);
   a.rho = float(rho);
   a.p_mode = p_mode;
-  for (int j = 1; j <= wave->n; ++j) {
-    a.jkB[j - 1] = float(j * wave->k * wave->B[j - 1]);
-    a.den[j - 1] = float(1.0 / (1.0 + std::exp(-2.0 * j * wave->k * wave->depth)));
-  }
+  for (int j = 1; j <= wave->n; ++j)
+    a.ajk[j - 1] = float(j * wave->k * wave->B[j - 1] / (1.0 + std::exp(-2.0 * j * wave->k * wave->depth)));
   for (int j = 0; j <= wave->n; ++j) a.E[j] = float(wave->E[j]);
   const int threads = 256;
   const int64_t blocks = std::min<int64_t>((np + threads - 1) / threads, int64_t(1) << 30);
