@@ -651,6 +651,9 @@ __global__ void __launch_bounds__(256, N >= 1024 ? 1 : 2) k_col_t(ColArgs a, Lev
   const bool colok = m < a.Mh;
   float2* tile = sm;
   float2* wbuf = sm + N * TLD + warp * stk_buf(N);
+  // depth factors of the current level, F and |k| S per element, made by the first field group
+  // and reused by the second (short columns only; after the warp buffers)
+  float* fks = reinterpret_cast<float*>(sm + N * TLD + (kThreads / 32) * stk_buf(N)) + warp * 2 * N;
   float2 T[stk_twn(N)];
   stk_init<N>(T, a.tw, lane);
   const int nyh = a.ny >> 1;
@@ -697,14 +700,25 @@ __global__ void __launch_bounds__(256, N >= 1024 ? 1 : 2) k_col_t(ColArgs a, Lev
         // inf * 0 would be NaN)
         const int n = p < nyh ? p : (p > N - nyh ? p - N : 0);
         const float ky = float(n) * a.kys;
-        const float kk = sqrtf(kx * kx + ky * ky);
-        float F, S;
-        depth_factors(kk, z, a.depth, F, S);
+        float kk, F, S;
         float2 ap, at;
         if constexpr (KEEP) {
           ap = Ap[e];
           at = At[e];
+          if (g == 0) {
+            kk = sqrtf(kx * kx + ky * ky);
+            depth_factors(kk, z, a.depth, F, S);
+            S *= kk;                               // modal_field takes |k| S as one factor
+            fks[e * 32 + lane] = F;
+            fks[N + e * 32 + lane] = S;
+          } else {
+            F = fks[e * 32 + lane];
+            S = fks[N + e * 32 + lane];
+          }
+          kk = 1.f;
         } else {
+          kk = sqrtf(kx * kx + ky * ky);
+          depth_factors(kk, z, a.depth, F, S);
           load_mode(e, ap, at);
         }
 #pragma unroll
@@ -717,9 +731,13 @@ __global__ void __launch_bounds__(256, N >= 1024 ? 1 : 2) k_col_t(ColArgs a, Lev
         for (int e = 0; e < E; ++e) tile[(lane + 32 * (e / RL) + (e % RL) * (N / RL)) * TLD + warp] = v[f][e];
         __syncthreads();
         float2* out = a.G + (size_t(level) * 4 + g * NF + f) * a.Nyr * a.ldG + c0;
-        for (int i = threadIdx.x; i < N * kColBlock; i += kThreads) {
-          const int y = i / kColBlock, w = i % kColBlock;
-          if (c0 + w < a.Mh) __stcg(&out[size_t(y) * a.ldG + w], tile[y * TLD + w]);
+        // two columns per thread: 16-byte stores (ldG and c0 are multiples of 16 and 8 entries)
+        for (int i = threadIdx.x; i < N * kColBlock / 2; i += kThreads) {
+          const int y = i / (kColBlock / 2), w = 2 * (i % (kColBlock / 2));
+          const float2 v0 = tile[y * TLD + w], v1 = tile[y * TLD + w + 1];
+          float2* o = &out[size_t(y) * a.ldG + w];
+          if (c0 + w + 1 < a.Mh) __stcg(reinterpret_cast<float4*>(o), make_float4(v0.x, v0.y, v1.x, v1.y));
+          else if (c0 + w < a.Mh) __stcg(o, v0);
         }
         __syncthreads();
       }
@@ -1024,7 +1042,8 @@ int launch_row_stk(const RowArgs& r, dim3 grid, size_t smem, cudaStream_t stream
 
 template <int N, int NF>
 int launch_col_t(const ColArgs& c, const Levels& L, dim3 grid, cudaStream_t stream) {
-  const size_t smem = (size_t(N) * (kColBlock + 1) + size_t(8) * stk_buf(N)) * sizeof(float2);
+  const size_t smem = (size_t(N) * (kColBlock + 1) + size_t(8) * stk_buf(N)) * sizeof(float2) +
+                      (N <= 256 ? size_t(8) * 2 * N * sizeof(float) : 0);
   int st = set_smem((const void*)k_col_t<N, NF>, smem);
   if (st) return st;
   k_col_t<N, NF><<<grid, kThreads, smem, stream>>>(c, L);
