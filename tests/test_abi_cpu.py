@@ -150,3 +150,22 @@ def test_tank_modes_validation(lib):
     assert call(65, 33, ns=5) == -1
     assert call(65, 33, L=-1.0) == -1
     assert lib.swense_tank_modes(None, 8, 8, 65, 33, 1, 4.0, 2.0, 1.0, 8, 8, 8, ctypes.byref(m), None) == -1
+
+
+def test_grid_node_count_rules(lib):
+    """Gathers take even node counts (powers of two, or a padding factor such as 3 times one);
+    odd counts are rejected, and the learned correction declines counts that are not powers of
+    two, all before any CUDA call."""
+    import ctypes
+    import numpy as np
+    from paper_2005_12716_gb300 import _swense as S
+    S.load()
+    z = np.array([-1, -0.5, -0.2, 0.0, 0.1], np.float32)
+    odd = S.make_grid(256, 256, 385, 64, 5, 1, 8.0, 4.0, z, [0.0])
+    assert lib.swense_interp(ctypes.byref(odd), 0.0, 16, 10, None, None, None, None, None, 0, 1e3,
+                             9.81, None, None) == -2
+    assert lib.swense_bin_points(ctypes.byref(odd), 16, 10, 16, 16, None) == -2
+    three = S.make_grid(256, 256, 384, 192, 5, 1, 8.0, 4.0, z, [0.0])     # padding factor 3
+    assert lib.swense_interp_learned(ctypes.byref(three), 0.0, 16, 10, None, None, None, None, None,
+                                     0, 1e3, 9.81, 256, None, None) == -7
+    assert b"power-of-two" in lib.swense_last_error()
