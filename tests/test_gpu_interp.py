@@ -256,3 +256,31 @@ def test_chunks_across_two_layers(api):
     errs, out, ref = _run(api, sea, z, 2, cfg["t_levels"], cfg["t_query"], pts, "total")
     assert ref["out_of_range"].sum() == 900
     assert max(errs.values()) <= TOL, errs
+
+
+def test_plane_chunk_plans_are_reusable(api):
+    """A plan made once for layered points (one- and two-plane chunks) gives, at other times and
+    for another sea on the same grid geometry, exactly what the plain call gives."""
+    import torch
+    cfg = configs.jonswap3d_small()
+    sea, z, tl = cfg["sea"], np.asarray(cfg["z_levels"], np.float32), cfg["t_levels"]
+    rng = np.random.default_rng(43)
+    pts_np = np.concatenate([_layers(rng, [zv], n, (1.0, 1.0), (4.0, 3.0))
+                             for zv, n in zip([z[2], z[5], z[8]], [1500, 2600, 1100])])
+    pts = torch.from_numpy(pts_np).cuda()
+    grid = api.fields_on_grid(api.upload_modes(sea), z, 2, tl)
+    plan = api.interp_plan(grid, pts)
+    kinds = plan.view(torch.int32).view(-1, 4).cpu().numpy()
+    assert np.all(kinds[:, 2] & (1 << 30))                 # every chunk takes a plane path
+    assert np.any(kinds[:, 2] & (1 << 29))                 # some of them two planes
+    for t in (cfg["t_query"], float(tl[1]) - 0.003):
+        ref, _ = api.interp(grid, t, pts)
+        got, _ = api.interp_with_plan(grid, t, pts, plan)
+        for k in ("eta", "u", "v", "w", "p"):
+            assert torch.equal(torch.nan_to_num(got[k], 7.0), torch.nan_to_num(ref[k], 7.0)), k
+    sea2 = seas.jonswap_sea(sea["nx"], sea["ny"], sea["Lx"], sea["Ly"], 0.03, 1.0, seed=78)
+    grid2 = api.fields_on_grid(api.upload_modes(sea2), z, 2, tl)
+    ref, _ = api.interp(grid2, cfg["t_query"], pts)
+    got, _ = api.interp_with_plan(grid2, cfg["t_query"], pts, plan)
+    for k in ("eta", "u", "v", "w", "p"):
+        assert torch.equal(torch.nan_to_num(got[k], 7.0), torch.nan_to_num(ref[k], 7.0)), k
