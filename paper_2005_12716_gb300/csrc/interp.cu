@@ -335,6 +335,28 @@ __device__ __forceinline__ void fma2(unsigned long long& acc, unsigned long long
 __device__ __forceinline__ float lo2(unsigned long long v) { return __uint_as_float(unsigned(v)); }
 __device__ __forceinline__ float hi2(unsigned long long v) { return __uint_as_float(unsigned(v >> 32)); }
 
+// One stencil row of four staged nodes summed along x: (u, v) and (w, phi_t) pairs with the
+// x weights given as (w, w) pairs, and (second form) the row's eta values with the same weights.
+__device__ __forceinline__ void row_sum(const float4* row, const unsigned long long (&wx2)[4],
+                                        unsigned long long& ruv, unsigned long long& rwt) {
+  ruv = pack2(0.f, 0.f);
+  rwt = pack2(0.f, 0.f);
+#pragma unroll
+  for (int kx = 0; kx < 4; ++kx) {
+    const float4 gv = row[kx];
+    fma2(ruv, wx2[kx], pack2(gv.x, gv.y));
+    fma2(rwt, wx2[kx], pack2(gv.z, gv.w));
+  }
+}
+__device__ __forceinline__ void row_sum(const float4* row, const float* erow,
+                                        const unsigned long long (&wx2)[4], const float (&wx)[4],
+                                        unsigned long long& ruv, unsigned long long& rwt, float& re) {
+  row_sum(row, wx2, ruv, rwt);
+  re = 0.f;
+#pragma unroll
+  for (int kx = 0; kx < 4; ++kx) re = fmaf(wx[kx], erow[kx], re);
+}
+
 // Time-blended box of grid nodes x0..x0+bx-1, y0..y0+by-1 (wrapped), levels l0..l0+bz-1 into
 // shared memory (row stride sbx, level-plane stride zst float4), and the eta rows (stride sbx).
 // Rows (ly, lz) over warps, two rows per warp at a time (more loads in flight), x over lanes;
@@ -578,20 +600,23 @@ __global__ void __launch_bounds__(BOX_THREADS, 3) k_interp_box(InterpArgs a, Lev
       const int ly = a.Nyr > 1 ? min(max(wrapi<P2>(c.iy - 1 - y0, a.Nyr), 0), by - 4) : 0;
       const float4* base = (onA ? sbox : planeB) + ly * sbx + lx;
       const float* ebase = fe + ly * sbx + lx;
+      // separable tensor product: each stencil row summed along x with the paired x weights,
+      // then the rows combined with the y weights
+      unsigned long long wx2[4];
+#pragma unroll
+      for (int kx = 0; kx < 4; ++kx) wx2[kx] = pack2(c.wx[kx], c.wx[kx]);
       unsigned long long uv = pack2(0.f, 0.f), wt = pack2(0.f, 0.f);
       float acc_eta = 0.f;
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
         if (b >= nys) break;
-#pragma unroll
-        for (int kx = 0; kx < 4; ++kx) {
-          const float4 gv = base[b * sbx + kx];
-          const float ww = c.wy[b] * c.wx[kx];
-          const unsigned long long w2 = pack2(ww, ww);
-          fma2(uv, w2, pack2(gv.x, gv.y));
-          fma2(wt, w2, pack2(gv.z, gv.w));
-          acc_eta = fmaf(ww, ebase[b * sbx + kx], acc_eta);
-        }
+        unsigned long long ruv, rwt;
+        float re;
+        row_sum(base + b * sbx, ebase + b * sbx, wx2, c.wx, ruv, rwt, re);
+        const unsigned long long wy2 = pack2(c.wy[b], c.wy[b]);
+        fma2(uv, wy2, ruv);
+        fma2(wt, wy2, rwt);
+        acc_eta = fmaf(c.wy[b], re, acc_eta);
       }
       store_point(a, i, make_float4(lo2(uv), hi2(uv), lo2(wt), hi2(wt)), acc_eta, pz,
                   onA ? cz.inside : cz2.inside);
@@ -619,31 +644,36 @@ __global__ void __launch_bounds__(BOX_THREADS, 3) k_interp_box(InterpArgs a, Lev
     const int ly = a.Nyr > 1 ? min(max(wrapi<P2>(c.iy - 1 - y0, a.Nyr), 0), by - 4) : 0;
     const int lz = min(max(c.j0 - l0, 0), bz - 4);
     const float4* base = sbox + lz * zst + ly * sbx + lx;
+    // separable tensor product: rows along x, then y within each level, then the levels in z
+    unsigned long long wx2[4];
+#pragma unroll
+    for (int kx = 0; kx < 4; ++kx) wx2[kx] = pack2(c.wx[kx], c.wx[kx]);
     unsigned long long uv = pack2(0.f, 0.f), wt = pack2(0.f, 0.f);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
+      unsigned long long quv = pack2(0.f, 0.f), qwt = pack2(0.f, 0.f);
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
         if (b >= nys) break;
-        const float4* row = base + q * zstride + b * sbx;
-        const float wzy = c.wz[q] * c.wy[b];
-#pragma unroll
-        for (int kx = 0; kx < 4; ++kx) {
-          const float4 gv = row[kx];
-          const float ww = wzy * c.wx[kx];
-          const unsigned long long w2 = pack2(ww, ww);
-          fma2(uv, w2, pack2(gv.x, gv.y));
-          fma2(wt, w2, pack2(gv.z, gv.w));
-        }
+        unsigned long long ruv, rwt;
+        row_sum(base + q * zstride + b * sbx, wx2, ruv, rwt);
+        const unsigned long long wy2 = pack2(c.wy[b], c.wy[b]);
+        fma2(quv, wy2, ruv);
+        fma2(qwt, wy2, rwt);
       }
+      const unsigned long long wz2 = pack2(c.wz[q], c.wz[q]);
+      fma2(uv, wz2, quv);
+      fma2(wt, wz2, qwt);
     }
     float acc_eta = 0.f;
     const float* ebase = seta + ly * sbx + lx;
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
       if (b >= nys) break;
+      float re = 0.f;
 #pragma unroll
-      for (int kx = 0; kx < 4; ++kx) acc_eta = fmaf(c.wy[b] * c.wx[kx], ebase[b * sbx + kx], acc_eta);
+      for (int kx = 0; kx < 4; ++kx) re = fmaf(c.wx[kx], ebase[b * sbx + kx], re);
+      acc_eta = fmaf(c.wy[b], re, acc_eta);
     }
     store_point(a, i, make_float4(lo2(uv), hi2(uv), lo2(wt), hi2(wt)), acc_eta, pz, c.inside);
   }
