@@ -473,28 +473,43 @@ __global__ void __launch_bounds__(BOX_THREADS) k_interp_plan(InterpArgs a, Level
   int two_z = 1;                                    // every point at refz or at the last point's z
   const float lastz = __ldg(&a.pts[3 * ((p0 + BOX_PTS < a.np ? p0 + BOX_PTS : a.np) - 1) + 2]);
   int mn[3] = {1 << 30, 1 << 30, 1 << 30}, mx[3] = {-(1 << 30), -(1 << 30), -(1 << 30)};
-#pragma unroll 4
-  for (int k = 0; k < BOX_PTS / 32; ++k) {
-    const int64_t i = p0 + k * 32 + lane;
-    if (i < a.np) {
-      const float pz = __ldg(&a.pts[3 * i + 2]);
-      PointCell c;
-      point_xy<P2>(a, __ldg(&a.pts[3 * i]), __ldg(&a.pts[3 * i + 1]), c);
-      // the level window only where z differs from the chunk's first point (a layer of an
-      // extruded mesh shares one z)
-      const bool zeq = __float_as_int(pz) == __float_as_int(refz);
-      same_z &= zeq;
-      two_z &= zeq || __float_as_int(pz) == __float_as_int(lastz);
-      if (zeq) c.j0 = refj0;
-      else point_level(a, zs, pz, c);
-      const int rx = wrap_rel<P2>(c.ix, refx, a.Nxr);
-      const int ry = a.Nyr > 1 ? wrap_rel<P2>(c.iy, refy, a.Nyr) : 0;
-      mn[0] = min(mn[0], rx);
-      mx[0] = max(mx[0], rx);
-      mn[1] = min(mn[1], ry);
-      mx[1] = max(mx[1], ry);
-      mn[2] = min(mn[2], c.j0);
-      mx[2] = max(mx[2], c.j0);
+  // four points per lane per round, their twelve loads issued before any of them is used
+  constexpr int PU = 4;
+  static_assert((BOX_PTS / 32) % PU == 0, "whole rounds");
+#pragma unroll 1
+  for (int k0 = 0; k0 < BOX_PTS / 32; k0 += PU) {
+    float qx[PU], qy[PU], qz[PU];
+#pragma unroll
+    for (int u = 0; u < PU; ++u) {
+      const int64_t i = p0 + (k0 + u) * 32 + lane;
+      const int64_t ic = i < a.np ? i : a.np - 1;     // in-bounds duplicate past the end, unused
+      qx[u] = __ldg(&a.pts[3 * ic]);
+      qy[u] = __ldg(&a.pts[3 * ic + 1]);
+      qz[u] = __ldg(&a.pts[3 * ic + 2]);
+    }
+#pragma unroll
+    for (int u = 0; u < PU; ++u) {
+      const int64_t i = p0 + (k0 + u) * 32 + lane;
+      if (i < a.np) {
+        const float pz = qz[u];
+        PointCell c;
+        point_xy<P2>(a, qx[u], qy[u], c);
+        // the level window only where z differs from the chunk's first point (a layer of an
+        // extruded mesh shares one z)
+        const bool zeq = __float_as_int(pz) == __float_as_int(refz);
+        same_z &= zeq;
+        two_z &= zeq || __float_as_int(pz) == __float_as_int(lastz);
+        if (zeq) c.j0 = refj0;
+        else point_level(a, zs, pz, c);
+        const int rx = wrap_rel<P2>(c.ix, refx, a.Nxr);
+        const int ry = a.Nyr > 1 ? wrap_rel<P2>(c.iy, refy, a.Nyr) : 0;
+        mn[0] = min(mn[0], rx);
+        mx[0] = max(mx[0], rx);
+        mn[1] = min(mn[1], ry);
+        mx[1] = max(mx[1], ry);
+        mn[2] = min(mn[2], c.j0);
+        mx[2] = max(mx[2], c.j0);
+      }
     }
   }
 #pragma unroll
