@@ -48,7 +48,7 @@ class L2Flush:
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", choices=["jonswap3d", "stokes2d", "batched", "learned", "e1", "direct",
@@ -134,7 +134,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -202,7 +202,7 @@ def run_reference(args, rank, world):
         return
     cfg, pts, desc = workload(args.config, args.pad)
     nm = n_modes(cfg["sea"])
-    budget = 150.0 / max(1, args.steps + args.warmup)
+    budget = 120.0 / max(1, args.steps + args.warmup)   # plus a 16-point probe per step
     per_step = []
     n_total = 0
     for s in range(args.warmup + args.steps):
@@ -539,15 +539,25 @@ def run_ours(args, rank, world):
             "value": rate, "unit": "points/s", "cores": 1, "kind": "oracle",
             "sample": f"{n} seeded points of the {npts}; direct FP64 modal sum over "
                       f"{n_modes(sea)} modes (numpy, one thread)"}
-        # method error of the reconstruction at those points vs the exact modal sum
+        # method error of the reconstruction at those points vs the exact modal sum, over the
+        # whole sample and over its points below the exact free surface (above it the sum's
+        # e^{|k| z} growth is carried by the shortest modes, which the grid resolves least)
         sel = torch.from_numpy(idx).to(dev)
-        err = {}
-        for k in ("eta", "u", "v", "w", "p"):
-            got = outs[k][sel].cpu().numpy().astype(np.float64)
-            ref = vals[k]
-            err[k] = float(np.max(np.abs(got - ref)) / max(np.max(np.abs(ref)), 1e-300))
-        line["method_error_vs_exact"] = {"norm": "max|gpu-exact|/max|exact| over the sample",
-                                         "fields": err}
+        water = pts_np[idx, 2].astype(np.float64) <= vals["eta"]
+
+        def rel_max(mask):
+            err = {}
+            for k in ("eta", "u", "v", "w", "p"):
+                got = outs[k][sel].cpu().numpy().astype(np.float64)[mask]
+                ref = vals[k][mask]
+                err[k] = float(np.max(np.abs(got - ref)) / max(np.max(np.abs(ref)), 1e-300)) if ref.size else None
+            return err
+        line["method_error_vs_exact"] = {
+            "norm": "max|gpu-exact|/max|exact| over the sample",
+            "fields": rel_max(np.ones(len(idx), bool)),
+            "fields_below_surface": rel_max(water),
+            "points": int(len(idx)), "points_below_surface": int(water.sum()),
+            "pad_n": int(pad)}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
