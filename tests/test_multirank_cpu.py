@@ -61,3 +61,30 @@ def test_reference_arm_other_ranks_do_no_work(capsys):
     args = argparse.Namespace(config="stokes2d", pad=1, steps=1, warmup=0, gpus=2)
     assert bench.run_reference(args, rank=1, world=2) is None
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_prints_one_contract_line(capsys, monkeypatch):
+    """Rank 0 of the reference arm times the oracle on the host and prints one JSON line with
+    the bench contract's keys (the oracle's sample shortened here to keep the test quick)."""
+    import argparse
+    import json
+    import bench
+    full = bench.cpu_oracle_sample
+    monkeypatch.setattr(bench, "cpu_oracle_sample",
+                        lambda cfg, pts, seconds, seed=1: full(cfg, pts, 0.01, seed))
+    args = argparse.Namespace(config="stokes2d", pad=1, steps=2, warmup=1, gpus=1)
+    bench.run_reference(args, rank=0, world=1)
+    lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+                "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["steps"] == 2 and d["warmup"] == 1
+    assert d["value"] > 0 and d["unit"] == "points/s" and d["higher_is_better"] is True
+    assert d["config"]["workload"].startswith("stokes2d")
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == d["value"] and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": "points/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
