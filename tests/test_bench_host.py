@@ -1,0 +1,36 @@
+"""Host-side helpers of the bench: the algorithmic bytes of the gather (unique grid nodes and
+eta columns that the points' stencils touch) against a brute-force count with Python sets."""
+import bisect
+import math
+
+import numpy as np
+
+
+def _brute(pts, Lx, Ly, z, nxr, nyr, n_tl):
+    nodes, cols = set(), set()
+    nz = len(z)
+    for x, y, zz in pts:
+        ix = math.floor(x * nxr / Lx)
+        iy = math.floor(y * nyr / Ly) if nyr > 1 else 0
+        j = min(max(bisect.bisect_right(list(z), zz) - 1, 0), nz - 2)
+        j0 = min(max(j - 1, 0), nz - 4)
+        for dx in range(-1, 3):
+            for dy in (range(-1, 3) if nyr > 1 else (0,)):
+                xi, yi = (ix + dx) % nxr, (iy + dy) % nyr
+                cols.add((yi, xi))
+                for dz in range(4):
+                    nodes.add((j0 + dz, yi, xi))
+    return len(nodes) * 16 * n_tl + len(cols) * 4 * n_tl
+
+
+def test_touched_grid_bytes_matches_brute_force():
+    import bench
+    rng = np.random.default_rng(11)
+    z = np.array([-1.0, -0.6, -0.35, -0.2, -0.1, -0.04, 0.0, 0.03, 0.06])
+    for nxr, nyr, Lx, Ly in ((32, 16, 4.0, 2.0), (64, 1, 8.0, 1.0)):
+        pts = np.stack([rng.uniform(-0.5, Lx + 0.5, 300), rng.uniform(0.0, Ly, 300),
+                        rng.uniform(-1.1, 0.1, 300)], 1).astype(np.float32)
+        pts[:40, :2] = pts[0, :2]                       # repeated cells
+        cfg = {"sea": {"Lx": Lx, "Ly": Ly}, "z_levels": z}
+        got = bench.touched_grid_bytes(cfg, pts, nxr, nyr, 2)
+        assert got == _brute(pts.astype(np.float64), Lx, Ly, z, nxr, nyr, 2)
