@@ -562,12 +562,17 @@ def run_ours(args, rank, world):
         print(json.dumps(line), flush=True)
 
 
-def _time_events(fn, steps, flush=None):
-    """Device time per call of fn (CUDA events on the current stream, L2 flushed in between)."""
+def _time_events(fn, steps, flush=None, clocks=None):
+    """Device time per call of fn (CUDA events on the current stream, L2 flushed in between).
+    With a dict ``clocks``, the SM clocks and throttle reasons sampled during the timed loop are
+    stored in it."""
     import torch
     stream = torch.cuda.current_stream()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(steps)]
+    sampler = ClockSampler(torch.cuda.current_device()) if clocks is not None else None
+    if sampler is not None:
+        sampler.start()
     for s in range(steps):
         if flush is not None:
             flush()
@@ -575,6 +580,8 @@ def _time_events(fn, steps, flush=None):
         fn()
         ev[s][1].record(stream)
     torch.cuda.synchronize()
+    if sampler is not None:
+        clocks.update(sampler.stop())
     return float(np.mean([a.elapsed_time(b) for a, b in ev]))
 
 
@@ -823,7 +830,8 @@ def run_relax(args, rank, world):
         fn()
     l0 = S.swense_launches()
     steps = max(1, args.steps)
-    ms = max_over_ranks(_time_events(fn, steps, L2Flush(dev)), world, dev)
+    clk = {}
+    ms = max_over_ranks(_time_events(fn, steps, L2Flush(dev), clk), world, dev)
     launches = S.swense_launches() - l0
     n_in = int((w > 0).sum().item())
     nbytes = nc * (12 + 8 + 4 + 4 + 4) + n_in * 2 * (4 + 12)    # all cells; blended cells r+w
@@ -839,7 +847,7 @@ def run_relax(args, rank, world):
             "roofline": {"bound": "hbm", "kernel": "k_relax_cells", "achieved": nbytes / (ms * 1e-3) / 1e9,
                          "peak": hbm, "unit": "GB/s", "frac": nbytes / (ms * 1e-3) / 1e9 / hbm,
                          "traffic": None},
-            "gpu_launches": int(launches)}
+            "clocks": clk, "gpu_launches": int(launches)}
     if rank == 0 and not args.no_cpu_baseline:
         from oracle import relax as R                # the CPU baseline leg only
         t0 = time.perf_counter()
@@ -872,7 +880,8 @@ def run_stream(args, rank, world):
         fn()
     l0 = S.swense_launches()
     steps = max(1, args.steps)
-    ms = max_over_ranks(_time_events(fn, steps, L2Flush(dev)), world, dev)
+    clk = {}
+    ms = max_over_ranks(_time_events(fn, steps, L2Flush(dev), clk), world, dev)
     launches = S.swense_launches() - l0
     nbytes = npts * (12 + 20)
     hbm = _peak_hbm()
@@ -896,7 +905,7 @@ def run_stream(args, rank, world):
                          "hbm": {"achieved_gbs": nbytes / (ms * 1e-3) / 1e9, "peak_gbs": hbm,
                                  "frac": nbytes / (ms * 1e-3) / 1e9 / hbm},
                          "issue_active_ncu": 0.79},
-            "gpu_launches": int(launches)}
+            "clocks": clk, "gpu_launches": int(launches)}
     if rank == 0 and not args.no_cpu_baseline:
         from oracle import stream as O               # the CPU baseline leg only
         o = O.solve(cfg["T"], cfg["H"], cfg["h"], cfg["n"])
@@ -940,7 +949,8 @@ def run_tank(args, rank, world):
         step()
     l0 = S.swense_launches()
     steps = max(1, args.steps)
-    ms = max_over_ranks(_time_events(step, steps, L2Flush(dev)), world, dev)
+    clk = {}
+    ms = max_over_ranks(_time_events(step, steps, L2Flush(dev), clk), world, dev)
     launches = S.swense_launches() - l0
     line = {"metric": "wave-field points/sec, wave tank (cosine basis on the mirrored grid)",
             "value": job_throughput(npts, world, ms), "unit": "points/s", "n_gpus": world,
@@ -950,7 +960,7 @@ def run_tank(args, rank, world):
             "config": {"workload": f"tank3d: 257x129 cosine modes (2 snapshots), mirrored 512x256 grid, "
                                    f"{len(z)} levels, {npts} cell + face centres",
                        "launch": "host launches", "l2": "flushed between timed steps"},
-            "gpu_launches": int(launches)}
+            "clocks": clk, "gpu_launches": int(launches)}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
