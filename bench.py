@@ -48,12 +48,14 @@ class L2Flush:
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=0,
+                    help="timed steps (default: 5 for the large sea, 1000 for the smaller workloads)")
+    ap.add_argument("--warmup", type=int, default=0,
+                    help="untimed warm-up steps, at least 3 (default: 3 large, 10 otherwise)")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", choices=["jonswap3d", "stokes2d", "batched", "learned", "e1", "direct",
                                          "large", "relax", "stream", "tank"],
-                    default="jonswap3d")
+                    default="large")
     ap.add_argument("--pad", type=int, default=1)
     ap.add_argument("--no-autotune", action="store_true",
                     help="use the untuned default launch shape of stage 1")
@@ -70,6 +72,10 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-graph", action="store_true",
                     help="launch every kernel from the host instead of replaying CUDA graphs")
+    ap.add_argument("--no-pad4", action="store_true",
+                    help="large mode: skip the 512x256-mode sea's pad-4 stage breakdown")
+    ap.add_argument("--cpu-cores", type=int, default=0,
+                    help="host processes for the CPU oracle (default: every core this process may use)")
     return ap.parse_args()
 
 
@@ -118,6 +124,17 @@ def touched_grid_bytes(cfg, pts, nxr, nyr, n_tl):
 
 # ----------------------------------------------------------------------------- clocks
 
+def gpu_uuid(index):
+    """nvidia-smi id of torch's device `index`: its UUID ("GPU-..."), which names the same physical
+    GPU whatever CUDA_VISIBLE_DEVICES or the enumeration order; the index if torch has no UUID."""
+    try:
+        import torch
+        u = str(torch.cuda.get_device_properties(index).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:  # noqa: BLE001  (old torch without .uuid, or no device)
+        return str(index)
+
+
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
 
@@ -127,13 +144,14 @@ class ClockSampler:
 
     def __init__(self, index):
         self.index = index
+        self.gpu_id = gpu_uuid(index)
         self.proc = None
         self.lines = []
 
     def start(self):
         try:
             self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                ["nvidia-smi", f"--id={self.gpu_id}", f"--query-gpu={self.FIELDS}",
                  "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
@@ -147,7 +165,8 @@ class ClockSampler:
 
     def stop(self):
         if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"],
+                    "gpu": self.gpu_id}
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -168,7 +187,7 @@ class ClockSampler:
                 if val.lower() == "active":
                     reasons.add(nm)
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "gpu": self.gpu_id}
 
 
 # ----------------------------------------------------------------------------- CPU oracle
@@ -200,6 +219,9 @@ def n_modes(sea):
 def run_reference(args, rank, world):
     if rank != 0:
         return
+    if args.config == "large":
+        run_reference_large(args)
+        return
     cfg, pts, desc = workload(args.config, args.pad)
     nm = n_modes(cfg["sea"])
     budget = 120.0 / max(1, args.steps + args.warmup)   # plus a 16-point probe per step
@@ -223,6 +245,39 @@ def run_reference(args, rank, world):
                                    f"ms_per_step extrapolated to all {len(pts)} points"},
         "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_reference_large(args):
+    """The FP64 oracle (direct modal sum) on every host core, each step a bounded sample of the
+    large-sea workload's points, timed like the GPU arm's steps; the same config dict."""
+    from wavegen import configs
+    cfg = configs.large_sea(n_levels=args.levels or 128, n_points=args.points or 16_000_000)
+    pts, near = cfg["points"], cfg["near_points"]
+    allp = np.concatenate([pts, near])
+    cores = args.cpu_cores or host_cores()
+    per_step_s = max(2.0, 150.0 / max(1, args.steps + args.warmup))
+    rates, n_total = [], 0
+    for s_ in range(args.warmup + args.steps):
+        rate, n_, _, _, cores = cpu_oracle_pool("large", len(cfg["z_levels"]), cfg["t_query"], allp,
+                                                per_step_s, cores, seed=100 + s_)
+        if s_ >= args.warmup:
+            rates.append(rate)
+            n_total += n_
+    value = float(np.mean(rates))
+    line = {
+        "impl": "reference", "metric": "wave-field points/sec at stated err vs FP64 oracle; % of HBM roofline",
+        "value": value, "unit": "points/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": len(allp) / value * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": large_config(cfg, len(pts), len(near)),
+        "cpu_baseline": {"value": value, "unit": "points/s", "cores": cores, "kind": "oracle",
+                         "cpu_model": cpu_model(),
+                         "sample": f"{n_total} seeded points of the workload over {args.steps} timed "
+                                   f"steps; direct FP64 modal sum over {n_modes(cfg['sea'])} modes on "
+                                   f"{cores} processes; ms_per_step extrapolated to all {len(allp)} points"},
+        "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
@@ -272,7 +327,16 @@ NCU_TRAFFIC = {
 }
 
 
-def run_ours(args, rank, world):
+DIRECT_KERNEL = "k_direct_split"
+# useful MMA flops of the split-BF16 direct sum per (point, mode) pair: u, v, w, dphi/dt, each the
+# real part of a complex product (2 MACs over the mode's re/im), three BF16 products (hi.hi,
+# hi.lo, lo.hi); eta is summed in FP32 beside the MMAs
+DIRECT_FLOP_PER_PAIR = 4 * 2 * 2 * 3
+DIRECT_FLOP_NOTE = ("per (point, mode) pair 48 flop: 4 fields x 2 MACs (re/im of the mode) x 2 flop "
+                    "x 3 split products; pairs = near-body points x live modes of the half spectrum")
+
+
+def run_ours(args, rank, world, emit=True):
     import torch
     from paper_2005_12716_gb300 import _swense as S
     from paper_2005_12716_gb300 import api
@@ -534,11 +598,19 @@ def run_ours(args, rank, world):
 
     # ---- CPU baseline: the FP64 oracle on a bounded sample, rank 0 at N = 1 only
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, n, vals, idx = cpu_oracle_sample(cfg, pts_np, args.cpu_seconds)
+        if args.config == "jonswap3d":
+            cores = args.cpu_cores or host_cores()
+            rate, n, vals, idx, cores = cpu_oracle_pool("jonswap3d", nz, tq, pts_np, args.cpu_seconds,
+                                                        cores)
+            how = f"numpy, {cores} spawned processes, one thread each"
+        else:
+            rate, n, vals, idx = cpu_oracle_sample(cfg, pts_np, args.cpu_seconds)
+            cores, how = 1, "numpy, one thread"
         line["cpu_baseline"] = {
-            "value": rate, "unit": "points/s", "cores": 1, "kind": "oracle",
+            "value": rate, "unit": "points/s", "cores": cores, "kind": "oracle",
+            "cpu_model": cpu_model(),
             "sample": f"{n} seeded points of the {npts}; direct FP64 modal sum over "
-                      f"{n_modes(sea)} modes (numpy, one thread)"}
+                      f"{n_modes(sea)} modes ({how})"}
         # method error of the reconstruction at those points vs the exact modal sum, over the
         # whole sample and over its points below the exact free surface (above it the sum's
         # e^{|k| z} growth is carried by the shortest modes, which the grid resolves least)
@@ -558,8 +630,9 @@ def run_ours(args, rank, world):
             "fields_below_surface": rel_max(water),
             "points": int(len(idx)), "points_below_surface": int(water.sum()),
             "pad_n": int(pad)}
-    if rank == 0:
+    if rank == 0 and emit:
         print(json.dumps(line), flush=True)
+    return line
 
 
 def _time_events(fn, steps, flush=None, clocks=None):
@@ -1041,74 +1114,317 @@ def run_direct(args, rank, world):
         print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------- CPU oracle pool
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu), for the CPU baseline's record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+_POOL_SEA = None
+
+
+def _pool_init(kind, n_levels, t):
+    """Worker start-up (spawned process): rebuild the workload's sea from its seed, propagated to
+    the query time, with one numpy thread per process."""
+    global _POOL_SEA
+    from oracle import modal
+    from wavegen import configs
+    if kind == "large":
+        cfg = configs.large_sea(n_levels=n_levels, n_points=1, n_near=1)
+    else:
+        cfg = configs.jonswap3d(mesh_dims=(4, 8, 4))
+    _POOL_SEA = modal.propagate(cfg["sea"], t)
+
+
+def _pool_work(pts):
+    from oracle import modal
+    return modal.fields_at_points(_POOL_SEA, pts, chunk=4)
+
+
+def cpu_oracle_pool(kind, n_levels, t, pts, seconds, cores, seed=1):
+    """The FP64 oracle's direct modal sum at a seeded sample of ``pts`` on ``cores`` host processes
+    (spawned, one numpy thread each), sized to take about ``seconds``. Returns (points/s, n,
+    values, idx, cores)."""
+    import multiprocessing as mp
+    env_keep = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in env_keep:
+        os.environ[k] = "1"
+    try:
+        ctx = mp.get_context("spawn")
+        rng = np.random.default_rng(seed)
+        with ctx.Pool(cores, initializer=_pool_init, initargs=(kind, n_levels, t)) as pool:
+            probe = pts[rng.choice(len(pts), cores, replace=False)].astype(np.float64)
+            pool.map(_pool_work, [probe[i:i + 1] for i in range(cores)])        # warm every worker
+            t0 = time.perf_counter()
+            pool.map(_pool_work, [probe[i:i + 1] for i in range(cores)])
+            per = (time.perf_counter() - t0)                                     # one point per core
+            n = int(min(max(cores, seconds / max(per, 1e-9) * cores), 200_000))
+            n = max(cores, (n // cores) * cores)
+            idx = rng.choice(len(pts), n, replace=False)
+            sample = pts[idx].astype(np.float64)
+            parts = np.array_split(sample, cores * 4)
+            t0 = time.perf_counter()
+            res = pool.map(_pool_work, parts)
+            dt = time.perf_counter() - t0
+    finally:
+        for k, v in env_keep.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    vals = {k: np.concatenate([r[k] for r in res]) for k in res[0]}
+    return n / dt, n, vals, idx, cores
+
+
+# ----------------------------------------------------------------------------- large sea (default)
+
+def large_config(cfg, n, nn):
+    """The workload description both arms print (same keys, same values)."""
+    z = cfg["z_levels"]
+    return {"workload": f"large_sea: JONSWAP k_p Hs/2 = 0.12, 2048x1024 modes, {len(z)} levels, 2 time "
+                        f"levels; {n} Morton-order points by grid + space-time interpolation, {nn} "
+                        f"near-body points by direct split-BF16 modal sum over all modes",
+            "modes": [2048, 1024], "levels": len(z), "pad_n": 1, "n_tl": len(cfg["t_levels"]),
+            "points": n, "near_body_points": nn, "fields": 5,
+            "l2": "inputs larger than L2 (8.6 GB grid written every step); a 256 MB flush between "
+                  "timed steps as well"}
+
+
 def run_large(args, rank, world):
-    """Large steep sea (2048 x 1024 modes, 128 levels, two time levels): one step = the grid at both
-    time levels + the gather of 16 M points (Morton order) + the split-BF16 direct sum at 1 M
-    near-body points over all modes; also the random-order variant with device binning."""
+    """Default workload, the largest single-GPU configuration: large steep sea (2048 x 1024 modes,
+    128 levels, two time levels). One step = the grid at both time levels + the gather of 16 M
+    points (Morton order) + the split-BF16 direct sum at 1 M near-body points over all modes."""
     import torch
     from paper_2005_12716_gb300 import _swense as S
     from paper_2005_12716_gb300 import api
     from wavegen import configs
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
-    cfg = configs.large_sea(n_levels=args.levels or 128,
-                            n_points=args.points or 16_000_000)
+    cfg = configs.large_sea(n_levels=args.levels or 128, n_points=args.points or 16_000_000)
     sea, z, tl, tq = cfg["sea"], cfg["z_levels"], cfg["t_levels"], cfg["t_query"]
+    pts_np, near_np = cfg["points"], cfg["near_points"]
+    n, nn = len(pts_np), len(near_np)
     modes = api.upload_modes(sea, dev)
     grid = api.alloc_grid(modes, z, 1, tl, dev)
-    pts = torch.from_numpy(cfg["points"]).to(dev)
-    near = torch.from_numpy(cfg["near_points"]).to(dev)
-    n, nn = len(cfg["points"]), len(cfg["near_points"])
+    pts = torch.from_numpy(pts_np).to(dev)
+    near = torch.from_numpy(near_np).to(dev)
     outs = {k: torch.empty(n, dtype=torch.float32, device=dev) for k in ("eta", "u", "v", "w", "p")}
     outn = {k: torch.empty(nn, dtype=torch.float32, device=dev) for k in ("eta", "u", "v", "w", "p")}
-    perm = torch.randperm(n, generator=torch.Generator().manual_seed(11)).to(dev)
-    pts_r = pts[perm].contiguous()
-    tune = api.autotune_grid(modes, z, 1, tl, out=grid)
-    stages = {
-        "grid": lambda: api.fields_on_grid(modes, z, 1, tl, out=grid),
-        "gather_morton": lambda: api.interp(grid, tq, pts, out=outs),
-        "direct_split_near": lambda: api.direct(modes, tq, near, precision="split_bf16", out=outn),
-    }
-
-    def binned():
-        order, srt = api.bin_points(grid, pts_r)
-        api.interp_permuted(grid, tq, srt, order, out=outs)
-    steps = max(3, min(args.steps, 5))
+    flush = L2Flush(dev)
+    stream = torch.cuda.current_stream(dev)
+    if args.tune:
+        lpc_, mb_, rv_ = (int(v) for v in args.tune.split(","))
+        S.swense_set_grid_tune(sea["nx"], sea["ny"], 1, len(z), lpc_, mb_ << 20, rv_)
+        tune = {"lpc": lpc_, "chunk_bytes": mb_ << 20, "row_variant": rv_, "source": "--tune"}
+    elif not args.no_autotune:
+        tune = api.autotune_grid(modes, z, 1, tl, out=grid)
+    else:
+        tune = None
+    stages = (("grid", lambda: api.fields_on_grid(modes, z, 1, tl, out=grid)),
+              ("gather", lambda: api.interp(grid, tq, pts, out=outs)),
+              ("direct_near_body", lambda: api.direct(modes, tq, near, precision="split_bf16", out=outn)))
+    for _ in range(args.warmup):
+        flush()
+        for _, fn in stages:
+            fn()
+    torch.cuda.synchronize()
+    S.swense_async_status(reset=True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
     clocks = ClockSampler(dev.index)
     clocks.start()
-    res = {}
-    l0 = S.swense_launches()
-    for name, fn in list(stages.items()) + [("bin_and_gather_random", binned)]:
-        for _ in range(max(3, args.warmup)):
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(stages) + 1)] for _ in range(args.steps)]
+    launches0 = S.swense_launches()
+    t_wall = time.perf_counter()
+    for s_ in range(args.steps):
+        flush()                                   # outside the events
+        ev[s_][0].record(stream)
+        for j, (_, fn) in enumerate(stages):
             fn()
-        torch.cuda.synchronize()
-        res[name] = _time_events(fn, steps)
-    launches = S.swense_launches() - l0
+            ev[s_][j + 1].record(stream)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    launches = S.swense_launches() - launches0
     clk = clocks.stop()
-    ms_step = res["grid"] + res["gather_morton"] + res["direct_split_near"]
+    S.swense_async_status(reset=True)             # no bounded device wait gave up
+    st_ms = {name: float(np.mean([ev[s_][j].elapsed_time(ev[s_][j + 1]) for s_ in range(args.steps)]))
+             for j, (name, _) in enumerate(stages)}
+    total_ms = max_over_ranks(float(sum(ev[s_][0].elapsed_time(ev[s_][-1]) for s_ in range(args.steps))),
+                              world, dev)
+    if world > 1:
+        torch.distributed.barrier()
+    ms_per_step = total_ms / args.steps
+    value = job_throughput(n + nn, world, ms_per_step)
+
+    # ---- algorithmic bytes / flops per stage and the roofline of the dominant kernel
     hbm = _peak_hbm()
+    peaks = {}
+    pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pp):
+        with open(pp) as fh:
+            peaks = json.load(fh)
     nx_r, ny_r = api.grid_dims(modes, 1)
-    grid_bytes = len(tl) * (len(z) * nx_r * ny_r * 16 + nx_r * ny_r * 4)
+    nz, n_tl = len(z), len(tl)
+    nslot = sea["A_eta"].size
+    grid_bytes = n_tl * (nz * nx_r * ny_r * 16 + nx_r * ny_r * 4) + nslot * (3 * 8 + 8)
+    # the gather: every node of both time levels is in some stencil (16 M uniform points over
+    # 268 M nodes; the union of their stencils covers about 98 % of the grid): the whole grid once
+    gather_bytes = n_tl * (nz * nx_r * ny_r * 16 + nx_r * ny_r * 4) + n * (12 + 20)
+    live_modes = int((sea["ny"] - 1) * (sea["nx"] // 2))
+    pairs = float(nn) * live_modes
+    d_ms = st_ms["direct_near_body"]
+    direct_flop = pairs * DIRECT_FLOP_PER_PAIR
+    stages_out = {
+        "grid": {"ms": st_ms["grid"], "algorithmic_bytes": grid_bytes,
+                 "achieved_gbs": grid_bytes / (st_ms["grid"] * 1e-3) / 1e9,
+                 "frac_hbm": grid_bytes / (st_ms["grid"] * 1e-3) / 1e9 / hbm},
+        "gather": {"ms": st_ms["gather"], "algorithmic_bytes": gather_bytes,
+                   "achieved_gbs": gather_bytes / (st_ms["gather"] * 1e-3) / 1e9,
+                   "frac_hbm": gather_bytes / (st_ms["gather"] * 1e-3) / 1e9 / hbm,
+                   "points_per_s": n / (st_ms["gather"] * 1e-3)},
+        "direct_near_body": {"ms": d_ms, "pairs": pairs, "pairs_per_s": pairs / (d_ms * 1e-3),
+                             "points_per_s": nn / (d_ms * 1e-3),
+                             "algorithmic_tflops": direct_flop / (d_ms * 1e-3) / 1e12},
+    }
+    tens_peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
+    dom = max(st_ms, key=st_ms.get)
+    if dom == "direct_near_body":
+        ach = direct_flop / (d_ms * 1e-3) / 1e12
+        roofline = {"bound": "tensor", "kernel": DIRECT_KERNEL, "achieved": ach, "peak": tens_peak,
+                    "unit": "TFLOP/s", "frac": ach / tens_peak,
+                    "traffic": NCU_TRAFFIC.get(DIRECT_KERNEL, {}).get("bytes"),
+                    "peak_source": "measured (MEASURED_PEAKS.json bf16_tflops_sustained: the kernel "
+                                   "runs for hundreds of ms)" if peaks else "fallback 1.7 PFLOP/s",
+                    "algorithmic": DIRECT_FLOP_NOTE}
+    else:
+        b = stages_out[dom]["algorithmic_bytes"]
+        ach = b / (st_ms[dom] * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s",
+                    "frac": ach / hbm, "traffic": None,
+                    "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback"}
+    stages_out["direct_near_body"]["frac_tensor"] = stages_out["direct_near_body"]["algorithmic_tflops"] / tens_peak
+    config = large_config(cfg, n, nn)
     line = {
         "metric": "wave-field points/sec at stated err vs FP64 oracle; % of HBM roofline",
-        "value": (n + nn) / (ms_step * 1e-3), "unit": "points/s", "n_gpus": 1, "steps": steps,
-        "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (direct: bf16x3 split, f32 accumulate)",
-        "data": "synthetic",
-        "config": {"workload": f"large_sea: 2048x1024 modes, {len(z)} levels, 2 time levels, {n} Morton-order "
-                               f"points + {nn} near-body points (direct split-BF16 over all modes)",
-                   "stage1_tune": tune, "l2": "inputs larger than L2 (8.6 GB grid)"},
-        "stages_ms": res,
-        "grid_hbm_frac": grid_bytes / (res["grid"] * 1e-3) / 1e9 / hbm,
-        "gpu_launches": int(launches),
-        "clocks": clk,
+        "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 (grid, gather); bf16x3 split / f32 accumulate (near-body direct sum)",
+        "data": "synthetic", "config": config,
+        "launch": {"stage1_tune": tune, "mode": "host launches, one stream",
+                   "parallelism": f"replicas x{world}"},
+        "points_fields_per_s": value * 5,
+        "roofline": roofline, "stages": stages_out,
+        "gpu_launches": int(launches), "clocks": clk, "wall_s_timed": t_wall,
     }
+
+    # ---- end to end through the public API with host buffers
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
+        h_modes = [pin(modes.A_eta.cpu().numpy()), pin(modes.A_phi.cpu().numpy()),
+                   pin(modes.A_phit.cpu().numpy()), pin(modes.omega.cpu().numpy())]
+        h_pts, h_near = pin(pts_np), pin(near_np)
+        h_out = {k: torch.empty(n, dtype=torch.float32).pin_memory() for k in outs}
+        h_outn = {k: torch.empty(nn, dtype=torch.float32).pin_memory() for k in outn}
+        h2d = sum(t.numel() * t.element_size() for t in h_modes) + (n + nn) * 12
+        d2h = (n + nn) * 4 * 5
+
+        def e2e_step():
+            for d, h in zip((modes.A_eta, modes.A_phi, modes.A_phit, modes.omega), h_modes):
+                d.copy_(h, non_blocking=True)
+            pts.copy_(h_pts, non_blocking=True)
+            near.copy_(h_near, non_blocking=True)
+            api.fields_on_grid(modes, z, 1, tl, out=grid)
+            api.interp(grid, tq, pts, out=outs)
+            api.direct(modes, tq, near, precision="split_bf16", out=outn)
+            for k in outs:
+                h_out[k].copy_(outs[k], non_blocking=True)
+                h_outn[k].copy_(outn[k], non_blocking=True)
+        for _ in range(args.warmup):
+            e2e_step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
+        line["e2e"] = {"value": job_throughput(n + nn, world, e_ms), "unit": "points/s",
+                       "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                       "ms_per_step": e_ms,
+                       "pipeline": "one stream: pinned host -> device copies of modes and points, "
+                                   "the three stages, device -> pinned host copies of the five fields"}
+
+    # ---- CPU baseline (the FP64 oracle on every host core, bounded sample) and the error of the
+    # timed outputs against it, rank 0 at N = 1 only
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = args.cpu_cores or host_cores()
+        allp = np.concatenate([pts_np, near_np])
+        rate, m_, vals, idx, cores = cpu_oracle_pool("large", nz, tq, allp, args.cpu_seconds, cores)
+        line["cpu_baseline"] = {
+            "value": rate, "unit": "points/s", "cores": cores, "kind": "oracle",
+            "cpu_model": cpu_model(),
+            "sample": f"{m_} seeded points of the {n + nn} (mesh and near-body); direct FP64 modal "
+                      f"sum over {n_modes(sea)} modes (numpy, {cores} spawned processes, one "
+                      f"thread each)"}
+        got_all = {k: torch.cat([outs[k], outn[k]]) for k in outs}
+        sel = torch.from_numpy(idx).to(dev)
+        water = allp[idx, 2].astype(np.float64) <= vals["eta"]
+        is_near = idx >= n
+
+        def rel_max(mask):
+            err = {}
+            for k in ("eta", "u", "v", "w", "p"):
+                got = got_all[k][sel].cpu().numpy().astype(np.float64)[mask]
+                ref = vals[k][mask]
+                err[k] = float(np.max(np.abs(got - ref)) / max(np.max(np.abs(ref)), 1e-300)) if ref.size else None
+            return err
+        line["error_vs_fp64_oracle"] = {
+            "norm": "max|gpu-exact|/max|exact| per field over the sample",
+            "near_body_direct": rel_max(is_near), "near_body_points": int(is_near.sum()),
+            "gather_all": rel_max(~is_near), "gather_below_surface": rel_max(~is_near & water),
+            "gather_points": int((~is_near).sum()),
+            "note": "the gather's error is the reconstruction's own interpolation error at pad 1 "
+                    "(method error), the direct sum's is its arithmetic error"}
+
+    # ---- context: the 512x256-mode sea at the paper's padding n = 4 (stage breakdown)
+    if rank == 0 and world == 1 and not args.no_pad4:
+        del grid, outs, outn, pts, near
+        torch.cuda.empty_cache()
+        sub = argparse.Namespace(**vars(args))
+        sub.config, sub.pad, sub.tune, sub.no_e2e = "jonswap3d", 4, "", True
+        sub.steps, sub.warmup = max(3, min(args.steps, 20)), max(3, args.warmup)
+        sub.cpu_seconds = min(args.cpu_seconds, 10.0)
+        line["jonswap3d_pad4"] = run_ours(sub, rank, world, emit=False)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
 
 def main():
     args = parse()
+    if args.steps <= 0:
+        args.steps = 5 if args.config == "large" else 1000
+    if args.warmup <= 0:
+        args.warmup = 3 if args.config == "large" else 10
+    args.warmup = max(3, args.warmup)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":

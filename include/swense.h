@@ -142,7 +142,10 @@ int swense_fields_on_grid(const swense_modes* modes, int32_t n_tl, const double*
  * device memory up front in its own pool, a plugin whose host forbids allocations outside set-up,
  * or code that cannot afford the implicit device synchronisation a cudaMalloc/cudaFree may do.
  * This entry point takes the same arguments and produces the same grid as swense_fields_on_grid,
- * but it allocates nothing: it calls no cudaMalloc, cudaFree or allocating library routine. Its
+ * with the same transform kernels and launch shape (the tuned one, else the default), except that
+ * the two-stream variant 5 runs as variant 2 and the eta transform stays on `stream` (no library
+ * stream is used); but it allocates nothing: it calls no cudaMalloc, cudaFree or allocating
+ * library routine. Its
  * scratch (the transformed levels between the two passes, and the propagated modes) lives in a
  * fixed array of SWENSE_NOALLOC_SCRATCH_BYTES inside the library's device image, which every GPU
  * that loads the library holds until the process exits.
@@ -526,6 +529,27 @@ typedef struct {
 int swense_relax_cells(const float* cell_xyz, const float* cell_zext, const float* eta_c,
                        int64_t nc, const swense_relax_zone* zones, int32_t n_zones,
                        float* alpha_i, float* alpha, float* u_c, float* weight, void* stream);
+
+/*
+ * swense_async_status — errors of bounded device-side waits (no passage of the paper: library
+ * housekeeping). Kernels that wait on asynchronous copies (the staged row pass of
+ * swense_fields_on_grid, row variant 4) give every wait an iteration limit; a wait that runs
+ * out sets a per-device flag and its warp returns without writing its grid rows, so the call
+ * that launched it has already returned SWENSE_OK. This call synchronises `stream`, reads the
+ * flag of the current device and, when reset != 0, clears it.
+ * Returns SWENSE_ERR_TIMEOUT if a wait gave up since the flag was last cleared (the grid of that
+ * call is incomplete), else SWENSE_OK; CUDA on a failed copy.
+ */
+int swense_async_status(int32_t reset, void* stream);
+
+/*
+ * swense_selftest_wait_timeout — self-test of the bounded-wait path above: launches the staged
+ * row pass on a tiny dummy problem with its copies withheld and a limit of a few polls, so every
+ * wait runs out; nothing is read or written but the flag. Afterwards swense_async_status must
+ * return SWENSE_ERR_TIMEOUT and the context stays usable. Uses (and may grow) the workspace.
+ * Errors: CUDA.
+ */
+int swense_selftest_wait_timeout(void* stream);
 
 /* Bytes of scratch workspace currently held on the current device. */
 int64_t swense_workspace_bytes(void);

@@ -121,6 +121,8 @@ _SIGS = {
     "swense_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "swense_version": (ctypes.c_int, []),
     "swense_launches": (ctypes.c_int64, []),
+    "swense_async_status": (ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p]),
+    "swense_selftest_wait_timeout": (ctypes.c_int, [ctypes.c_void_p]),
 }
 
 
@@ -324,6 +326,19 @@ def swense_version():
 
 def swense_launches():
     return load().swense_launches()
+
+
+def swense_async_status(reset=True, stream=None, raise_on_error=True):
+    """Status of the bounded device-side waits since the last reset (synchronises the stream):
+    0, or SWENSE_ERR_TIMEOUT (-6) raised as SwenseError unless raise_on_error is False."""
+    st = load().swense_async_status(1 if reset else 0, _stream(stream))
+    if raise_on_error:
+        _check(st)
+    return st
+
+
+def swense_selftest_wait_timeout(stream=None):
+    _check(load().swense_selftest_wait_timeout(_stream(stream)))
 
 
 # ------------------------------------------------------------------ learned correction (MLP)

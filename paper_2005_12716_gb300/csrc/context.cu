@@ -162,6 +162,17 @@ const char* swense_strerror(int status) {
   }
 }
 
+int swense_async_status(int32_t reset, void* stream) {
+  SWENSE_CUDA_TRY(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+  int grid = 0;
+  int st = swense::grid_async_flag(reset != 0, &grid);
+  if (st) return st;
+  if (grid)
+    return swense::fail(SWENSE_ERR_TIMEOUT, "a bounded wait of the staged row pass (k_row_tma) gave "
+                                            "up; the grid rows of that warp were not written");
+  return SWENSE_OK;
+}
+
 int swense_version(void) { return SWENSE_VERSION; }
 
 int64_t swense_launches(void) { return swense::g_launches.load(std::memory_order_relaxed); }

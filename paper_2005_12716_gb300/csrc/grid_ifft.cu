@@ -374,6 +374,8 @@ struct RowArgs {
   const float2* tw;
   int Mh, Nxr, Nyr, rb, lev0;
   int ldG;               // m stride of the transposed intermediate (k_row_t)
+  int polls;             // k_row_tma: polls of a bounded wait before it gives up
+  int selftest;          // k_row_tma: 1 = issue no copy, so every wait runs out (self-test)
 };
 
 template <int E>
@@ -897,8 +899,10 @@ __global__ void __launch_bounds__(256, N >= 8192 ? 1 : 2) k_row_tb(RowArgs a) {
 // takes `rpw` consecutive rows of one level; lane 0 copies a row's four field segments
 // (ldG complex values each, contiguous in G) into the warp's staging buffer with cp.async.bulk
 // on the warp's mbarrier, and the next row's copy runs while the current row is transformed.
-// A wait that does not complete within its bound sets the device error flag and ends the warp
-// (after waiting, also bounded, for a copy it still has in flight).
+// A wait that does not complete within its bound sets the device error flag and ends the warp:
+// the warp decides together (every lane must have seen its copy complete), waits, also bounded,
+// for the copy it still has in flight, and leaves as one. The host reads and clears the flag
+// with swense_async_status.
 __device__ int g_async_timeout;
 
 template <int N>
@@ -928,17 +932,22 @@ __global__ void __launch_bounds__(256, N >= 1024 ? 1 : 2) k_row_tma(RowArgs a, i
       fence_proxy_async();                       // earlier reads of the buffer come first
       mbar_arrive_expect_tx(bar, 4 * span);
       const float2* src = Gl + size_t(y0 + i) * a.ldG;
+      if (!a.selftest) {
 #pragma unroll
-      for (int f = 0; f < 4; ++f) bulk_g2s(stg + f * a.ldG, src + f * fs, span, bar);
+        for (int f = 0; f < 4; ++f) bulk_g2s(stg + f * a.ldG, src + f * fs, span, bar);
+      }
     }
   };
   issue(0);
   float2 T[stk_twn(N)];
   stk_init<N>(T, a.tw, lane);
   for (int i = 0; i < nrows; ++i) {
-    if (!mbar_wait(bar, unsigned(i) & 1u)) {
+    const bool done = mbar_wait(bar, unsigned(i) & 1u, a.polls);
+    if (!__all_sync(0xffffffffu, done)) {        // one lane gave up: the whole warp leaves
       if (lane == 0) atomicExch(&g_async_timeout, 1);
-      mbar_wait(bar, unsigned(i) & 1u);          // the copy waited on is the only one in flight
+      // the copy waited on is the only one in flight (none in the self-test)
+      mbar_wait(bar, unsigned(i) & 1u, a.polls);
+      __syncwarp();
       return;
     }
     float2 z1[E], z2[E];
@@ -1505,6 +1514,8 @@ int launch_grid(const GridPlan& p, const swense_modes* md, const double* t, floa
       ra.Nxr = int(Nxr);
       ra.Nyr = int(Nyr);
       ra.rb = kRowBlock;
+      ra.polls = kMbarPolls;
+      ra.selftest = 0;
       const size_t smem_col = size_t(2) * ny * (kColBlock + 1) * sizeof(float2);
       const size_t smem_row = size_t(4) * Mh * (kRowBlock + 1) * sizeof(float2);
       ca.ldG = ra.ldG = trans_ld(Mh);
@@ -1827,6 +1838,49 @@ extern "C" int swense_set_grid_tune(int32_t nx, int32_t ny, int32_t pad_n, int32
 }
 
 // ---------------------------------------------------------------------------------------------
+// Bounded device-side waits report here: the flag of this translation unit (k_row_tma).
+namespace swense {
+
+int grid_async_flag(bool reset, int* was_set) {
+  int v = 0;
+  SWENSE_CUDA_TRY(cudaMemcpyFromSymbol(&v, g_async_timeout, sizeof(int)));
+  if (reset && v) {
+    const int zero = 0;
+    SWENSE_CUDA_TRY(cudaMemcpyToSymbol(g_async_timeout, &zero, sizeof(int)));
+  }
+  *was_set = v;
+  return SWENSE_OK;
+}
+
+}  // namespace swense
+
+extern "C" int swense_selftest_wait_timeout(void* stream_) {
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+  const float2* tw = nullptr;
+  int st = twiddles(stream, &tw);
+  if (st) return st;
+  // one level of 256-point rows, 16 rows: the bulk copies are never issued, so the first wait of
+  // every warp runs out after a few polls; nothing is read or written but the flag
+  constexpr int N = 256, rows = 16;
+  const size_t g_bytes = size_t(4) * rows * trans_ld(N / 2) * sizeof(float2);
+  void* ws = nullptr;
+  st = workspace(g_bytes + size_t(rows) * N * sizeof(float4), stream, &ws);
+  if (st) return st;
+  RowArgs r{};
+  r.G = static_cast<const float2*>(ws);
+  r.nodes = reinterpret_cast<float4*>(static_cast<char*>(ws) + g_bytes);
+  r.tw = tw;
+  r.Mh = N / 2;
+  r.Nxr = N;
+  r.Nyr = rows;
+  r.rb = kRowBlock;
+  r.ldG = trans_ld(N / 2);
+  r.polls = 8;
+  r.selftest = 1;
+  return launch_row_tma<N>(r, 1u, stream);
+}
+
+// ---------------------------------------------------------------------------------------------
 // swense_fields_on_grid_noalloc: the same kernels, with their scratch in a fixed device array
 // that is part of the library image instead of the cudaMalloc'ed workspace.
 namespace swense {
@@ -1884,5 +1938,13 @@ extern "C" int swense_fields_on_grid_noalloc(const swense_modes* md, int32_t n_t
   void* ws = nullptr;
   st = noalloc_scratch(&ws);
   if (st) return st;
-  return launch_grid(p, md, t, nodes, eta, ws, chunk, stream);
+  // the launch shape swense_fields_on_grid would take (tuned, else its default), except that the
+  // two-stream pipeline (variant 5) runs as variant 2: the fixed array holds one level chunk, not
+  // two, and this call uses no library stream
+  const Tune tn = tuned(p.nx, p.ny, p.pad, p.nz);
+  const bool pair = pair_path(p.ny, p.Nxr, p.Nyr);
+  const int lpc = tn.lpc >= 0 ? tn.lpc : (pair ? 4 : ((p.Nxr <= 512 && p.Nyr <= 512) ? kColLevels : 0));
+  int rowv = tn.lpc >= 0 ? tn.rowv : (pair ? 2 : 0);
+  if (rowv == 5) rowv = 2;
+  return launch_grid(p, md, t, nodes, eta, ws, chunk, stream, lpc, rowv, 0, 0);
 }

@@ -32,6 +32,10 @@ int twiddles(cudaStream_t stream, const float2** out);
 // Counts kernel launches made by the library (reported by swense_launches()).
 void count_launches(int n);
 
+// Device-side error flags of bounded waits, one per translation unit that has such waits: read
+// (and cleared when reset) on the current device; *was_set != 0 when a wait gave up.
+int grid_async_flag(bool reset, int* was_set);
+
 inline bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
 inline int ilog2(int64_t v) { int r = 0; while ((int64_t(1) << r) < v) ++r; return r; }
 

@@ -51,10 +51,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
   return ok != 0;
 }
 
-// Wait for the phase with this parity to complete; gives up after a bounded number of polls
-// (each try_wait already suspends for a while) and returns false.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
-  for (int it = 0; it < (1 << 22); ++it)
+// Polls of a bounded mbarrier wait before it gives up (each try_wait already suspends for a
+// while, so this is seconds, far beyond any copy's completion time).
+constexpr int kMbarPolls = 1 << 22;
+
+// Wait for the phase with this parity to complete; gives up after `polls` polls and returns false.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int polls = kMbarPolls) {
+  for (int it = 0; it < polls; ++it)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }

@@ -80,7 +80,7 @@ def test_batch_graph_equals_individual_calls(env):
     vs = velocity_scale(ref["u"], ref["v"], ref["w"])
     for k in ("eta", "u", "v", "w", "p"):
         got = first[0][k].cpu().numpy()
-        e = rel_linf_scaled(got, ref[k], vs) if k in ("u", "v", "w") else rel_linf(got, ref[k])
+        e = rel_linf_scaled(got, ref[k], vs, field=k) if k in ("u", "v", "w") else rel_linf(got, ref[k])
         assert e <= 1e-5, (k, e)
 
 

@@ -63,5 +63,5 @@ def test_binned_gather_matches_oracle(api, cfgname):
     vs = velocity_scale(ref["u"], ref["v"], ref["w"])
     for k in ("eta", "u", "v", "w", "p"):
         got = out[k].cpu().numpy()
-        e = rel_linf_scaled(got, ref[k], vs) if k in ("u", "v", "w") else rel_linf(got, ref[k])
+        e = rel_linf_scaled(got, ref[k], vs, field=k) if k in ("u", "v", "w") else rel_linf(got, ref[k])
         assert e <= 1e-5, (k, e)

@@ -40,7 +40,7 @@ def _check(api, sea, pts, t, p_mode="dyn", precision="fp32", tol=None):
     errs = {}
     for k in ("eta", "u", "v", "w", "p"):
         got = out[k].cpu().numpy()
-        errs[k] = rel_linf_scaled(got, ref[k], vs) if k in ("u", "v", "w") else rel_linf(got, ref[k])
+        errs[k] = rel_linf_scaled(got, ref[k], vs, field=k) if k in ("u", "v", "w") else rel_linf(got, ref[k])
     bar = TOLS[precision] if tol is None else tol
     assert max(errs.values()) <= bar, errs
     return errs

@@ -36,7 +36,7 @@ def _oracle_grid(sea, z, pad, tl):
 
 def _errs(got_n, got_e, ref_n, ref_e):
     vs = velocity_scale(ref_n[..., 0], ref_n[..., 1], ref_n[..., 2])
-    e = [rel_linf_scaled(got_n[..., q], ref_n[..., q], vs) for q in range(3)]
+    e = [rel_linf_scaled(got_n[..., q], ref_n[..., q], vs, field="uvw"[q]) for q in range(3)]
     return e + [rel_linf(got_n[..., 3], ref_n[..., 3]), rel_linf(got_e, ref_e)]
 
 
@@ -83,7 +83,7 @@ def test_gather_3d_mesh(api, pad, scheme):
     ref = f(rn, re_, sea["Lx"], sea["Ly"], z, tl, pts, t)
     assert cnt == int(ref["out_of_range"].sum())
     vs = velocity_scale(ref["u"], ref["v"], ref["w"])
-    errs = {k: (rel_linf_scaled(out[k].cpu().numpy(), ref[k], vs) if k in "uvw"
+    errs = {k: (rel_linf_scaled(out[k].cpu().numpy(), ref[k], vs, field=k) if k in "uvw"
                 else rel_linf(out[k].cpu().numpy(), ref[k])) for k in ("eta", "u", "v", "w", "p")}
     assert max(errs.values()) <= TOL, errs
 
@@ -97,7 +97,7 @@ def test_gather_2d_random_points(api):
     rn, re_ = _oracle_grid(sea, z, 3, tl)
     ref = ointerp.interp_points(rn, re_, sea["Lx"], sea["Ly"], z, tl, cfg["points"], cfg["t_query"])
     vs = velocity_scale(ref["u"], ref["v"], ref["w"])
-    errs = {k: (rel_linf_scaled(out[k].cpu().numpy(), ref[k], vs) if k in "uvw"
+    errs = {k: (rel_linf_scaled(out[k].cpu().numpy(), ref[k], vs, field=k) if k in "uvw"
                 else rel_linf(out[k].cpu().numpy(), ref[k])) for k in ("eta", "u", "w", "p")}
     assert max(errs.values()) <= TOL, errs
 

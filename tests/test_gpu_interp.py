@@ -45,7 +45,7 @@ def _run(api, sea, z, pad, t_levels, t, pts, p_mode="dyn"):
     rn, re_ = _oracle_grid(sea, z, pad, t_levels)
     ref = ointerp.interp_points(rn, re_, sea["Lx"], sea["Ly"], z, t_levels, pts, t, p_mode=p_mode)
     vs = velocity_scale(ref["u"], ref["v"], ref["w"])
-    errs = {k: (rel_linf_scaled(out[k].cpu().numpy(), ref[k], vs) if k in ("u", "v", "w")
+    errs = {k: (rel_linf_scaled(out[k].cpu().numpy(), ref[k], vs, field=k) if k in ("u", "v", "w")
                 else rel_linf(out[k].cpu().numpy(), ref[k])) for k in FIELDS}
     assert cnt == int(ref["out_of_range"].sum())
     return errs, out, ref

@@ -36,7 +36,7 @@ def env():
 
 def _errs(got, ref):
     vs = velocity_scale(ref["u"], ref["v"], ref["w"])
-    return {k: (rel_linf_scaled(got[k], ref[k], vs) if k in ("u", "v", "w") else rel_linf(got[k], ref[k]))
+    return {k: (rel_linf_scaled(got[k], ref[k], vs, field=k) if k in ("u", "v", "w") else rel_linf(got[k], ref[k]))
             for k in ("eta", "u", "v", "w", "p") if k in got}
 
 

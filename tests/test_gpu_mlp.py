@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 from oracle import divergence, interp as ointerp, mlp as omlp, modal
-from tests._util import rel_linf, rel_linf_scaled, velocity_scale
+from tests._util import note_field, rel_linf, rel_linf_scaled, velocity_scale
 from wavegen import configs, mesh as M
 
 pytestmark = pytest.mark.gpu
@@ -72,7 +72,7 @@ def test_features_match_oracle(env):
     for f in range(4):
         scale = vs if f < 3 else np.max(np.abs(st[:, 3]))
         assert np.max(np.abs(gs[:, f] - st[:, f])) / scale <= 1e-5, f
-        assert rel_linf_scaled(lg.cpu().numpy().reshape(n, 4)[:, f], lag[:, f], scale) <= 1e-5
+        assert rel_linf_scaled(lg.cpu().numpy().reshape(n, 4)[:, f], lag[:, f], scale, field="uvwt"[f]) <= 1e-5
     np.testing.assert_allclose(xg[:, 0, 64:67], off, atol=2e-5)
     np.testing.assert_allclose(np.max(np.abs(xg[:, :, :64]), axis=2), 1.0, atol=1e-6)
     ref_eta = ointerp.interp_points(np.stack(nodes), np.stack(etas), sea["Lx"], sea["Ly"], z, tl,
@@ -165,8 +165,11 @@ def test_trained_correction_beats_plain_interpolation(env):
             o, _ = fn(grid, 0.0, fc)
             d = api.fv_divergence(o["u"], o["v"], o["w"], area, cf, vol).cpu().numpy()
             store.append(np.sqrt(np.mean(d.astype(np.float64) ** 2)))
+    note_field("rms_err_learned/plain", np.mean(err_learned) / np.mean(err_plain), 0.0)
+    note_field("rms_div_learned/plain", np.mean(div_learned) / np.mean(div_plain), 0.0)
     assert np.mean(err_learned) < np.mean(err_plain), (err_learned, err_plain)
-    assert np.mean(div_learned) <= 1.05 * np.mean(div_plain), (div_learned, div_plain)
+    # the interpolated divergence must be no worse than the plain interpolation's
+    assert np.mean(div_learned) <= np.mean(div_plain), (div_learned, div_plain)
 
 
 @pytest.mark.parametrize("order", ["mesh", "random"])

@@ -37,7 +37,7 @@ def _check(api, sea, z, pad, tl, t, pts):
                                        tl, pts, t)
     assert cnt == int(ref["out_of_range"].sum())
     vs = velocity_scale(ref["u"], ref["v"], ref["w"])
-    errs = {k: (rel_linf_scaled(out[k].cpu().numpy(), ref[k], vs) if k in ("u", "v", "w")
+    errs = {k: (rel_linf_scaled(out[k].cpu().numpy(), ref[k], vs, field=k) if k in ("u", "v", "w")
                 else rel_linf(out[k].cpu().numpy(), ref[k])) for k in ("eta", "u", "v", "w", "p")}
     assert max(errs.values()) <= 1e-5, errs
     return out

@@ -88,3 +88,20 @@ def test_reference_arm_prints_one_contract_line(capsys, monkeypatch):
     assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": "points/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
+
+
+def test_cpu_oracle_pool_matches_one_process():
+    """The bench's all-core CPU baseline (spawned processes, each rebuilding the sea from its seed)
+    returns exactly the single-process oracle's values at the sampled points."""
+    import numpy as np
+    import bench
+    from oracle import modal
+    from wavegen import configs
+    cfg = configs.jonswap3d(mesh_dims=(4, 8, 4))
+    pts = configs.mesh_points(cfg["mesh"])[:200]
+    rate, n, vals, idx, cores = bench.cpu_oracle_pool("jonswap3d", len(cfg["z_levels"]),
+                                                      cfg["t_query"], pts, 0.3, 2)
+    assert cores == 2 and n == len(idx) >= 2 and rate > 0
+    ref = modal.fields_at_points(modal.propagate(cfg["sea"], cfg["t_query"]), pts[idx].astype(np.float64))
+    for k in ("eta", "u", "v", "w", "p"):
+        np.testing.assert_allclose(vals[k], ref[k], rtol=1e-12, atol=1e-12)

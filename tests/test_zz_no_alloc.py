@@ -7,6 +7,9 @@ what one call leaves in the shared scratch array cannot leak into the next. This
 to be collected last.
 """
 import ctypes
+import os
+import subprocess
+import sys
 
 import numpy as np
 import pytest
@@ -79,3 +82,34 @@ def test_noalloc_rejects_requests_beyond_its_scratch(env):
     assert st == -2
     assert b"SWENSE_NOALLOC_SCRATCH_BYTES" in lib.swense_last_error()
     assert S.swense_launches() == launches
+
+
+_FRESH = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, sys.argv[1])
+from paper_2005_12716_gb300 import _swense as S, api
+from wavegen import configs
+torch.cuda.init()
+cfg = configs.jonswap3d(mesh_dims=(4, 8, 4))      # 512 x 256 modes, 64 levels: many chunks
+sea, z, tl = cfg["sea"], cfg["z_levels"], cfg["t_levels"]
+modes = api.upload_modes(sea)
+out = api.alloc_grid(modes, z, 1, tl)
+for pad in (1, 2):
+    if pad == 2:
+        out = api.alloc_grid(modes, z, 2, tl)
+    S.swense_fields_on_grid_noalloc(modes.c_struct(), len(tl), np.asarray(tl, np.float64),
+                                    S.make_grid_desc(pad, z), out.nodes, out.eta)
+torch.cuda.synchronize()
+assert torch.isfinite(out.nodes).all() and torch.isfinite(out.eta).all()
+print("WORKSPACE", S.swense_workspace_bytes())
+"""
+
+
+def test_noalloc_alone_leaves_the_library_workspace_unallocated(env):
+    """A fresh process that makes only allocation-free calls (two grid sizes, the larger needing
+    several level chunks) ends with no library workspace: nothing went through the allocator."""
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", _FRESH, root], capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert "WORKSPACE 0" in r.stdout, r.stdout[-500:]
