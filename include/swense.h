@@ -309,8 +309,9 @@ int swense_batch_run(const swense_instance* instances, int32_t n_instances, int3
                      double rho, double g, void* stream);
 
 enum swense_direct_precision {
-  SWENSE_DIRECT_FP32 = 0,        /* FP32 arithmetic, exact integer-turn phases */
-  SWENSE_DIRECT_SPLIT_BF16 = 1   /* reserved: tensor-core split-BF16 contraction */
+  SWENSE_DIRECT_FP32 = 0,              /* FP32 arithmetic, exact integer-turn phases */
+  SWENSE_DIRECT_SPLIT_BF16 = 1,        /* tcgen05 split-BF16 contraction, FP32 accumulation */
+  SWENSE_DIRECT_SPLIT_BF16_PAIRWISE = 2 /* per-pair split-BF16 mma.sync kernel (comparison) */
 };
 
 /*
@@ -323,9 +324,27 @@ enum swense_direct_precision {
  * modes: one snapshot (n_snap = 1); with omega non-NULL it is propagated to time t
  *   (A e^{-i omega (t - t_ref)}, phase reduced in FP64), otherwise t is ignored.
  * pts: device float [np][3]; outputs device float [np] each, any may be NULL.
- * precision: SWENSE_DIRECT_FP32 (the phase m x/Lx + n y/Ly is an exact 32-bit fraction of a
- *   turn, so accuracy does not degrade with |k x|).
- * Uses the scratch workspace (64 B per mode slot). Errors: ARG, SIZE, UNSUPPORTED, OOM, CUDA.
+ * precision:
+ *   SWENSE_DIRECT_FP32: one thread per point, every mode in FP32 (the phase m x/Lx + n y/Ly is
+ *     an exact 32-bit fraction of a turn, so accuracy does not degrade with |k x|).
+ *   SWENSE_DIRECT_SPLIT_BF16: the sums as a dense contraction on the tcgen05 tensor cores. The
+ *     points are sorted by z (a counting sort into 65536 buckets between their min and max z)
+ *     and cut into tiles of 128; the phase is separated, e^{i(kx x + ky y)} = X_m(x) Y_n(y), and
+ *     the depth factor is expanded about each tile's middle z0 to second order in z - z0 (exact
+ *     derivatives d/dz F = |k| S, d/dz S = |k| F); per group of 8 mode rows and 32 modes, a
+ *     [128 points x 64] x [64 x 208] product (Re/Im of u, v, w, dphi/dt at three orders, and
+ *     eta) in split BF16 (hi.hi + hi.lo + lo.hi, FP32 accumulation in tensor memory), then
+ *     Re sum_n Y_n T_n and sum_j (z - z0)^j in FP32. A tile whose max|k| x half-range of z
+ *     exceeds 0.02 (the dropped third-order term would exceed 2e-6) is evaluated by the
+ *     per-pair kernel instead. Accuracy: about 1e-5 of each field's maximum (bar 1e-3).
+ *     Points with nearly equal z are ordered by atomics, so a tile's z0, and with it the last
+ *     digits of the split products' rounding, can differ from call to call.
+ *   SWENSE_DIRECT_SPLIT_BF16_PAIRWISE: per (point, mode) pair the operand e^{i k.x} f(z) is
+ *     generated in registers and split into BF16 hi + lo for legacy mma.sync m16n8k16 products
+ *     (the same accuracy; kept for comparison and for tiles the tensor-core path leaves).
+ * Uses the scratch workspace (FP32: 64 B per mode slot; SPLIT_BF16: 32 B per mode slot, 20 B
+ * per point and 256 KB; PAIRWISE: 80 B per mode). Errors: ARG, SIZE, UNSUPPORTED, OOM, CUDA;
+ * the tensor-core kernel's bounded waits report through swense_async_status.
  */
 int swense_direct(const swense_modes* modes, double t, const float* pts, int64_t np,
                   float* eta, float* u, float* v, float* w, float* p, int32_t p_mode,
@@ -550,6 +569,25 @@ int swense_async_status(int32_t reset, void* stream);
  * Errors: CUDA.
  */
 int swense_selftest_wait_timeout(void* stream);
+
+/*
+ * swense_direct_stats — tiles of the last SWENSE_DIRECT_SPLIT_BF16 call on the current device
+ * (no passage of the paper): *tiles = tiles of 128 z-sorted points, *fallback_tiles = those whose
+ * z range was too wide for the tensor-core expansion and went to the per-pair kernel (0 and 0
+ * before any such call). Synchronises `stream`; valid until the workspace is reused or freed.
+ * Errors: ARG, CUDA.
+ */
+int swense_direct_stats(int64_t* tiles, int64_t* fallback_tiles, void* stream);
+
+/*
+ * swense_selftest_tc_gemm — self-test of the tensor-core data path used by swense_direct (no
+ * passage of the paper): D = A B^T with A device FP32 [128][K], B device FP32 [N][K] (both
+ * rounded to BF16), D device FP32 [128][N], one tcgen05 MMA chain with A in tensor memory
+ * (variant 0) or shared memory (variant 1) and B in shared memory in the K-major core-matrix
+ * layout of the direct sum. N and K multiples of 16 in 16..256. Errors: ARG, CUDA.
+ */
+int swense_selftest_tc_gemm(const float* A, const float* B, float* D, int32_t N, int32_t K,
+                            int32_t variant, void* stream);
 
 /* Bytes of scratch workspace currently held on the current device. */
 int64_t swense_workspace_bytes(void);

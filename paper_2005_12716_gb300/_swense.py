@@ -123,6 +123,10 @@ _SIGS = {
     "swense_launches": (ctypes.c_int64, []),
     "swense_async_status": (ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p]),
     "swense_selftest_wait_timeout": (ctypes.c_int, [ctypes.c_void_p]),
+    "swense_direct_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "swense_selftest_tc_gemm": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                               ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                               ctypes.c_void_p]),
 }
 
 
@@ -256,7 +260,7 @@ def swense_interp_with_plan(grid, t, pts, np_, plan, eta=None, u=None, v=None, w
     return cnt.value if count_out_of_range else None
 
 
-DIRECT_FP32, DIRECT_SPLIT_BF16 = 0, 1
+DIRECT_FP32, DIRECT_SPLIT_BF16, DIRECT_SPLIT_BF16_PAIRWISE = 0, 1, 2
 
 
 def swense_direct(modes, t, pts, np_, eta=None, u=None, v=None, w=None, p=None, p_mode=P_DYN,
@@ -339,6 +343,17 @@ def swense_async_status(reset=True, stream=None, raise_on_error=True):
 
 def swense_selftest_wait_timeout(stream=None):
     _check(load().swense_selftest_wait_timeout(_stream(stream)))
+
+
+def swense_direct_stats(stream=None):
+    """(tiles, fallback_tiles) of the last tensor-core direct sum on the current device."""
+    t, f = ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(load().swense_direct_stats(ctypes.byref(t), ctypes.byref(f), _stream(stream)))
+    return t.value, f.value
+
+
+def swense_selftest_tc_gemm(A, B, D, N, K, variant=0, stream=None):
+    _check(load().swense_selftest_tc_gemm(_ptr(A), _ptr(B), _ptr(D), N, K, variant, _stream(stream)))
 
 
 # ------------------------------------------------------------------ learned correction (MLP)

@@ -147,7 +147,8 @@ def direct(modes, t, pts, p_mode="dyn", rho=1000.0, g=9.81, precision="fp32", ou
     if out is None:
         out = {k: torch.empty(n, dtype=torch.float32, device=pts.device)
                for k in ("eta", "u", "v", "w", "p")}
-    prec = {"fp32": S.DIRECT_FP32, "split_bf16": S.DIRECT_SPLIT_BF16}[precision]
+    prec = {"fp32": S.DIRECT_FP32, "split_bf16": S.DIRECT_SPLIT_BF16,
+            "split_bf16_pairwise": S.DIRECT_SPLIT_BF16_PAIRWISE}[precision]
     S.swense_direct(modes.c_struct(), float(t), pts, n, out.get("eta"), out.get("u"), out.get("v"),
                     out.get("w"), out.get("p"), S.P_MODES[p_mode], rho, g, prec, stream)
     return out

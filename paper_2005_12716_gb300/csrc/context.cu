@@ -164,12 +164,17 @@ const char* swense_strerror(int status) {
 
 int swense_async_status(int32_t reset, void* stream) {
   SWENSE_CUDA_TRY(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
-  int grid = 0;
+  int grid = 0, direct = 0;
   int st = swense::grid_async_flag(reset != 0, &grid);
+  if (!st) st = swense::direct_async_flag(reset != 0, &direct);
   if (st) return st;
   if (grid)
     return swense::fail(SWENSE_ERR_TIMEOUT, "a bounded wait of the staged row pass (k_row_tma) gave "
                                             "up; the grid rows of that warp were not written");
+  if (direct)
+    return swense::fail(SWENSE_ERR_TIMEOUT, "a bounded wait of the tensor-core direct sum "
+                                            "(k_direct_tc) gave up; the outputs of that tile were "
+                                            "not written");
   return SWENSE_OK;
 }
 

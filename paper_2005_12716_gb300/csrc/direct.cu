@@ -113,12 +113,6 @@ struct DirectArgs {
   float rho, g;
 };
 
-// x / L as an unsigned 32-bit fraction of a turn.
-__device__ __forceinline__ unsigned turn_fraction(float x, double inv_l) {
-  const double f = double(x) * inv_l;
-  const double fr = f - floor(f);                        // [0, 1)
-  return unsigned((unsigned long long)(fr * 4294967296.0) & 0xffffffffull);
-}
 
 __global__ void __launch_bounds__(kDirThreads) k_direct_fp32(DirectArgs a) {
   __shared__ ModeCoef tile[kDirTile];
@@ -281,6 +275,11 @@ struct SplitArgs {
   float depth;
   int p_mode;
   float rho, g;
+  // points sorted by the tensor-core path: output i goes to perm[i], and only the tiles of
+  // tile_pts points that tile_bad marks are written (NULL: caller's order, every point)
+  const int32_t* perm;
+  const uint8_t* tile_bad;
+  int tile_pts;
 };
 
 template <bool FINITE>
@@ -292,6 +291,17 @@ __global__ void __launch_bounds__(kSplitThreads, 2) k_direct_split(SplitArgs a) 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane >> 2, q = lane & 3;
   const int64_t pbase = (int64_t(blockIdx.x) * (kSplitThreads / 32) + warp) * (16 * TT);
+  bool write = true;
+  if (a.tile_bad) {
+    // the block's points span whole warps of one tile each; leave at once (before any barrier)
+    // unless one of the block's tiles is marked
+    const int64_t b0 = int64_t(blockIdx.x) * (kSplitThreads / 32) * (16 * TT);
+    const int64_t t0 = b0 / a.tile_pts, t1 = (std::min(b0 + (kSplitThreads / 32) * (16 * TT), a.np) - 1) / a.tile_pts;
+    bool any = false;
+    for (int64_t tt = t0; tt <= t1; ++tt) any |= a.tile_bad[tt] != 0;
+    if (!any) return;
+    write = pbase < a.np && a.tile_bad[pbase / a.tile_pts] != 0;
+  }
 
   unsigned X[TT][2], Y[TT][2];
   float z[TT][2], stc[TT][2], sts[TT][2];
@@ -442,11 +452,12 @@ __global__ void __launch_bounds__(kSplitThreads, 2) k_direct_split(SplitArgs a) 
     const float t0 = __shfl_down_sync(0xffffffffu, run[t][1], 1);
     const float w1 = __shfl_down_sync(0xffffffffu, run[t][2], 1);
     const float t1 = __shfl_down_sync(0xffffffffu, run[t][3], 1);
-    if (q != 0) continue;
+    if (q != 0 || !write) continue;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const int64_t i = pbase + 16 * t + g + 8 * h;
-      if (i >= a.np) continue;
+      const int64_t ii = pbase + 16 * t + g + 8 * h;
+      if (ii >= a.np) continue;
+      const int64_t i = a.perm ? int64_t(a.perm[ii]) : ii;
       const float uu = run[t][2 * h], vv = run[t][2 * h + 1];
       const float ww = h ? w1 : w0, tt = h ? t1 : t0;
       if (a.o_eta) a.o_eta[i] = h ? e1 : e0;
@@ -474,9 +485,10 @@ using namespace swense;
 
 namespace {
 
-int direct_split(const swense_modes* md, double t, const float* pts, int64_t np, float* eta, float* u,
-                 float* v, float* w, float* p, int32_t p_mode, double rho, double grav,
-                 cudaStream_t stream) {
+int direct_split_impl(const swense_modes* md, double t, const float* pts, const int32_t* perm,
+                      const uint8_t* tile_bad, int tile_pts, int64_t np, float* eta, float* u,
+                      float* v, float* w, float* p, int32_t p_mode, double rho, double grav,
+                      cudaStream_t stream, size_t ws_offset) {
   const int nx = md->nx, ny = md->ny;
   const bool finite = md->depth > 0;
   const int km = finite ? 4 : 8;
@@ -486,9 +498,9 @@ int direct_split(const swense_modes* md, double t, const float* pts, int64_t np,
   const int64_t nsteps = int64_t(nrows) * spr;
   if (nsteps * 32 >= (int64_t(1) << 31)) return fail(SWENSE_ERR_SIZE, "too many modes for the split table");
   void* ws = nullptr;
-  int st = workspace(size_t(nsteps) * sizeof(SplitStep), stream, &ws);
+  int st = workspace(ws_offset + size_t(nsteps) * sizeof(SplitStep), stream, &ws);
   if (st) return st;
-  SplitStep* steps = static_cast<SplitStep*>(ws);
+  SplitStep* steps = reinterpret_cast<SplitStep*>(static_cast<char*>(ws) + ws_offset);
   const float depth = finite ? float(md->depth) : 0.f;
   k_direct_prep_split<<<unsigned((nsteps * 32 + 255) / 256), 256, 0, stream>>>(
       reinterpret_cast<const float2*>(md->A_eta), reinterpret_cast<const float2*>(md->A_phi),
@@ -515,6 +527,9 @@ int direct_split(const swense_modes* md, double t, const float* pts, int64_t np,
   a.p_mode = p_mode;
   a.rho = float(rho);
   a.g = float(grav);
+  a.perm = perm;
+  a.tile_bad = tile_bad;
+  a.tile_pts = tile_pts;
   const int64_t per_cta = int64_t(kSplitThreads / 32) * 16 * kSplitTiles;
   const int64_t blocks = (np + per_cta - 1) / per_cta;
   if (blocks >= (int64_t(1) << 31)) return fail(SWENSE_ERR_SIZE, "too many points for one call");
@@ -526,6 +541,30 @@ int direct_split(const swense_modes* md, double t, const float* pts, int64_t np,
 }
 
 }  // namespace
+
+namespace swense {
+
+size_t split_table_bytes(const swense_modes* md) {
+  const int km = md->depth > 0 ? 4 : 8;
+  const int rm = ((md->nx / 2 + 7) / 8) * 8;
+  const int nrows = md->ny > 1 ? md->ny - 1 : 1;
+  return size_t(nrows) * (rm / km) * sizeof(SplitStep);
+}
+
+int direct_split_sorted(const swense_modes* md, double t, const float* srt, const int32_t* perm,
+                        const uint8_t* tile_bad, int tile_pts, int64_t np, float* eta, float* u, float* v,
+                        float* w, float* p, int32_t p_mode, double rho, double grav, cudaStream_t stream,
+                        size_t ws_offset) {
+  static_assert((kSplitThreads / 32) * 16 * kSplitTiles % 32 == 0, "warps of 32 points");
+  if (tile_pts % (16 * kSplitTiles)) return fail(SWENSE_ERR_ARG, "tile size");
+  // the workspace already holds the sorted points and the tensor-core path's tables, which this
+  // launch reads: its own table goes at ws_offset, after them (the caller sized the workspace for
+  // both, so that nothing here grows it and frees the buffers in use)
+  return direct_split_impl(md, t, srt, perm, tile_bad, tile_pts, np, eta, u, v, w, p, p_mode, rho, grav,
+                           stream, ws_offset);
+}
+
+}  // namespace swense
 
 extern "C" int swense_direct(const swense_modes* md, double t, const float* pts, int64_t np,
                              float* eta, float* u, float* v, float* w, float* p, int32_t p_mode,
@@ -544,10 +583,14 @@ extern "C" int swense_direct(const swense_modes* md, double t, const float* pts,
     return fail(SWENSE_ERR_ARG, "non-finite t, depth, rho or g");
   if (p_mode != SWENSE_P_DYN && p_mode != SWENSE_P_PHIT && p_mode != SWENSE_P_TOTAL)
     return fail(SWENSE_ERR_ARG, "unknown p_mode");
-  if (precision != SWENSE_DIRECT_FP32 && precision != SWENSE_DIRECT_SPLIT_BF16)
+  if (precision != SWENSE_DIRECT_FP32 && precision != SWENSE_DIRECT_SPLIT_BF16 &&
+      precision != SWENSE_DIRECT_SPLIT_BF16_PAIRWISE)
     return fail(SWENSE_ERR_ARG, "unknown precision");
   if (np == 0) return SWENSE_OK;
-  if (precision == SWENSE_DIRECT_SPLIT_BF16) return direct_split(md, t, pts, np, eta, u, v, w, p, p_mode, rho, grav, stream);
+  if (precision == SWENSE_DIRECT_SPLIT_BF16)
+    return direct_tc(md, t, pts, np, eta, u, v, w, p, p_mode, rho, grav, stream);
+  if (precision == SWENSE_DIRECT_SPLIT_BF16_PAIRWISE)
+    return direct_split_impl(md, t, pts, nullptr, nullptr, 0, np, eta, u, v, w, p, p_mode, rho, grav, stream, 0);
   const size_t nslot = size_t(ny) * (nx / 2 + 1);
   const size_t bytes = nslot * sizeof(ModeCoef);
   void* ws = nullptr;

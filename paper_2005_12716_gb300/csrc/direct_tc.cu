@@ -1,0 +1,768 @@
+// Near-body direct modal sums on the fifth-generation tensor cores (tcgen05, sm_100 family).
+//
+// Paper: reconstruction section, analytical evaluation of the incident fields (the modal sums
+// of Eqs. whatIsSpectralMethod1 / whatIsSpectralMethod evaluated at the points themselves: no
+// grid, no interpolation error; cost proportional to the number of Fourier components per point).
+//
+// The sum F_c(p) = Re sum_{m,n} W_c[m,n] e^{i (kx_m x + ky_n y)} D_c(|k|, z) is reorganised so
+// that its bulk is a dense contraction, without approximating anything beyond FP32 rounding:
+//   1. separable phase: e^{i(kx x + ky y)} = X_m(x) Y_n(y), X_m = e^{i m 2 pi x / Lx};
+//   2. depth factor about the tile's centre z0: the points are sorted by z and cut into tiles of
+//      128; with D = cosh or sinh ratio (finite depth) or e^{|k| z} (deep water) and
+//      d/dz F = |k| S, d/dz S = |k| F, the Taylor series to second order in dz = z - z0 is
+//      F(z) = F0 + |k| dz S0 + (|k| dz)^2 / 2 F0 (S likewise with F0, S0 exchanged); the tile's
+//      kappa = max|k| max|dz| is bounded (kKappaMax) so the dropped third-order term stays below
+//      2e-6 relative, under the split products' own rounding;
+//   3. for each row n of modes and each field c and order j, T_{c,j,n}(p) = sum_m X_m(p)
+//      C_{c,j}[m,n] with C = W_c |k|^j / j! (F0 or S0): a (points x 2 m) by (2 m x columns)
+//      real GEMM per K-chunk of 32 modes and group of 8 rows (26 columns per row: Re and Im of
+//      u, v, w, dphi/dt at orders 0..2, and eta);
+//   4. F_c(p) = sum_j dz^j Re sum_n Y_n(p) T_{c,j,n}(p): the epilogue of every group.
+// The GEMM runs as split BF16 (A = hi + lo, B = hi + lo, three products hi.hi + hi.lo + lo.hi
+// accumulated in FP32 in tensor memory). A (the tile's X_m, 128 points x 64) lives in tensor
+// memory, written by the epilogue warps once per K-chunk; B is generated per group by eight
+// producer warps straight into shared memory in the MMA's K-major core-matrix layout; one thread
+// issues the MMAs; accumulators are double-buffered in tensor memory so the epilogue of one
+// group overlaps the MMAs of the next. Tiles whose kappa is too large (sparse z) are left to the
+// per-pair split-BF16 kernel (direct.cu), which handles them exactly.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "internal.cuh"
+#include "mma.cuh"
+#include "tcgen05.cuh"
+#include "tma.cuh"
+
+namespace swense {
+namespace {
+
+constexpr int kTcM = 128;                             // points per tile (MMA M)
+constexpr int kTcRows = 8;                            // mode rows n per group
+constexpr int kTcTerms = 3;                           // Taylor orders in dz: 0, 1, 2
+constexpr int kTcCj = 4 * kTcTerms + 1;               // 13 complex outputs per row
+constexpr int kTcN = kTcRows * 2 * kTcCj;             // 208 MMA columns
+constexpr int kTcModes = 32;                          // modes m per K-chunk
+constexpr int kTcK = 2 * kTcModes;                    // 64 K (re, im per mode)
+// B layout: column nc = col * 8 + row (col = 2 cj + {0: Re T, 1: Im T}); core matrices of
+// 8 columns x 8 K; k-blocks of 8 K are kTcLBO bytes apart (26 core matrices + 16 bytes, so that
+// the 32 lanes of a producer warp, one mode each, hit 32 different banks)
+constexpr int kTcSBO = 128;
+constexpr int kTcLBO = (kTcN / 8) * 128 + 16;
+constexpr int kTcBBytes = (kTcK / 8) * kTcLBO;        // one of hi / lo
+constexpr int kTcStageBytes = 2 * kTcBBytes;
+constexpr int kTcStages = 2;
+constexpr int kEpiWarps = 4, kProdWarps = 8;
+constexpr int kMmaWarp = kEpiWarps + kProdWarps;
+constexpr int kTcThreads = (kMmaWarp + 1) * 32;
+constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kColAhi = 0, kColAlo = 32, kColD0 = 64, kColD1 = 288;
+constexpr float kKappaMax = 0.02f;
+constexpr int kZBuckets = 1 << 16;
+constexpr uint32_t kIdesc = tc::idesc_bf16_f32(kTcM, kTcN);
+static_assert(kTcN % 16 == 0 && kTcN <= 256, "MMA N for M = 128");
+static_assert(kColD1 + kTcN <= kTmemCols && kColD0 + kTcN <= kColD1, "tensor-memory columns");
+
+// Set when a bounded wait of k_direct_tc gave up (read by swense_async_status).
+__device__ int g_direct_timeout;
+
+struct TcArgs {
+  const float4* tab;        // [rows_p][mp] x 2: (W_phi, W_phit), (W_eta, |k|, 1/(1+e^{-2kh}))
+  int rows_p, mp, ny, npos;
+  const float* spts;        // points sorted by z, [np][3]
+  const int32_t* perm;      // sorted position -> caller's index
+  int64_t np;
+  float *o_eta, *o_u, *o_v, *o_w, *o_p;
+  double inv_lx, inv_ly;
+  float kxs, kys, depth, kmax;
+  int p_mode;
+  float rho, g;
+  uint8_t* tile_bad;        // [ntiles]: 1 = left to the per-pair kernel
+};
+
+// Table rows: n = 0 .. ny/2 - 1 in rows 0 .. npos - 1, then n = -(ny/2 - 1) .. -1 from row npos
+// (npos = ny/2 rounded up to a multiple of 8; rows past each half's end are zero modes), so
+// that n rises by one from row to row inside every group of 8 rows. The Nyquist row is not in
+// the table. 2-D seas (ny = 1): row 0 holds n = 0.
+__host__ __device__ __forceinline__ int row_n(int tr, int ny, int npos) {
+  if (ny <= 1) return tr;
+  return tr < npos ? tr : tr - npos - (ny / 2 - 1);
+}
+
+// e^{k z} with the product k z carried as hi + lo (compensated), as for the grid's depth factors.
+__device__ __forceinline__ float exp_kz(float k, float z) {
+  const float kz = k * z;
+  const float lo = fmaf(k, z, -kz);
+  const float e = expf(kz);
+  return fmaf(e, lo, e);
+}
+
+// F = cosh(k(z+h))/cosh(kh), S = sinh(k(z+h))/cosh(kh) (finite depth), both e^{kz} in deep water.
+__device__ __forceinline__ void depth_fs(float k, float z, float h, float invd, float& F, float& S) {
+  const float e1 = exp_kz(k, z);
+  if (h <= 0.f) {
+    F = S = e1;
+    return;
+  }
+  const float e2 = expf(-k * (z + 2.f * h));
+  F = (e1 + e2) * invd;
+  S = (e1 - e2) * invd;
+}
+
+// Warp-collective bounded wait: every lane polls; the warp succeeds only together. A wait that
+// gives up (or sees another role give up) sets the CTA's abort flag and the device flag.
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, unsigned parity, volatile int* abort_flag) {
+  bool ok = false;
+  for (int it = 0; it < kMbarPolls; ++it) {
+    if (mbar_try_wait(bar, parity)) {
+      ok = true;
+      break;
+    }
+    if ((it & 31) == 31 && *abort_flag) break;
+  }
+  ok = __all_sync(0xffffffffu, ok);
+  if (!ok && (threadIdx.x & 31) == 0) {
+    *abort_flag = 1;
+    atomicExch(&g_direct_timeout, 1);
+  }
+  return ok;
+}
+__device__ __forceinline__ bool thread_wait(uint64_t* bar, unsigned parity, volatile int* abort_flag) {
+  for (int it = 0; it < kMbarPolls; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 31) == 31 && *abort_flag) return false;
+  }
+  *abort_flag = 1;
+  atomicExch(&g_direct_timeout, 1);
+  return false;
+}
+
+struct TcShared {
+  uint64_t b_full[kTcStages], b_empty[kTcStages], d_full[2], d_empty[2], a_ready, fin;
+  uint32_t tmem;
+  int abort_flag;
+  float zmin[kTcThreads / 32], zmax[kTcThreads / 32];
+};
+
+__global__ void __launch_bounds__(kTcThreads, 1) k_direct_tc(TcArgs a) {
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  unsigned char* bst = smraw;                                   // kTcStages x (B hi, B lo)
+  TcShared& sh = *reinterpret_cast<TcShared*>(smraw + kTcStages * kTcStageBytes);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t tile = blockIdx.x;
+  const int64_t p0 = tile * kTcM;
+
+  // ---- the tile's z range (padding points repeat the last point)
+  float zt = 0.f;
+  {
+    const int64_t i = std::min<int64_t>(p0 + (threadIdx.x & (kTcM - 1)), a.np - 1);
+    zt = a.spts[3 * i + 2];
+    float lo = zt, hi = zt;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+      hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if (lane == 0) {
+      sh.zmin[warp] = lo;
+      sh.zmax[warp] = hi;
+    }
+  }
+  if (threadIdx.x == 0) sh.abort_flag = 0;
+  __syncthreads();
+  float zmin = sh.zmin[0], zmax = sh.zmax[0];
+  for (int w = 1; w < kTcM / 32; ++w) {
+    zmin = fminf(zmin, sh.zmin[w]);
+    zmax = fmaxf(zmax, sh.zmax[w]);
+  }
+  const float z0 = 0.5f * (zmin + zmax);
+  const float half = 0.5f * (zmax - zmin);
+  if (a.kmax * half > kKappaMax) {                  // uniform over the CTA
+    if (threadIdx.x == 0) a.tile_bad[tile] = 1;
+    return;
+  }
+  if (threadIdx.x == 0) {
+    a.tile_bad[tile] = 0;
+    for (int s = 0; s < kTcStages; ++s) {
+      mbar_init(&sh.b_full[s], kProdWarps * 32);
+      mbar_init(&sh.b_empty[s], 1);
+    }
+    for (int d = 0; d < 2; ++d) {
+      mbar_init(&sh.d_full[d], 1);
+      mbar_init(&sh.d_empty[d], kEpiWarps * 32);
+    }
+    mbar_init(&sh.a_ready, kEpiWarps * 32);
+    mbar_init(&sh.fin, 1);
+    fence_mbar_init();
+  }
+  if (warp == kMmaWarp) {
+    tc::alloc(&sh.tmem, kTmemCols);
+    tc::relinquish();
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tbase = sh.tmem;
+  volatile int* abort_flag = &sh.abort_flag;
+  const int nkc = a.mp / kTcModes, ng = a.rows_p / kTcRows, ngi = nkc * ng;
+
+  if (warp < kEpiWarps) {
+    // ================================================================ epilogue: one point each
+    const int t = threadIdx.x;
+    const int64_t pi = p0 + t;
+    const bool live = pi < a.np;
+    const int64_t ps = live ? pi : a.np - 1;
+    const float x = a.spts[3 * ps], y = a.spts[3 * ps + 1], z = a.spts[3 * ps + 2];
+    const unsigned X = turn_fraction(x, a.inv_lx), Y = a.ny > 1 ? turn_fraction(y, a.inv_ly) : 0u;
+    const float dz = z - z0;
+    float sy, cy;                                   // e^{i 2 pi y / Ly}: row step n -> n + 1
+    sincospif(2.f * (float(int(Y)) * 2.3283064365386963e-10f), &sy, &cy);
+    const uint32_t lanebase = tbase + ((uint32_t(warp) * 32u) << 16);
+    float acc[kTcCj];
+#pragma unroll
+    for (int c = 0; c < kTcCj; ++c) acc[c] = 0.f;
+
+    auto consume = [&](int gi) {
+      const int g = gi % ng;
+      const uint32_t dcol = (gi & 1) ? kColD1 : kColD0;
+      // Y_n(p) of the group's eight rows (consecutive n): exact at the first, then seven steps
+      float yr[kTcRows], yi[kTcRows];
+      {
+        const unsigned ph = unsigned(row_n(g * kTcRows, a.ny, a.npos)) * Y;
+        sincospif(2.f * (float(int(ph)) * 2.3283064365386963e-10f), &yi[0], &yr[0]);
+      }
+#pragma unroll
+      for (int r = 1; r < kTcRows; ++r) {
+        yr[r] = fmaf(yr[r - 1], cy, -yi[r - 1] * sy);
+        yi[r] = fmaf(yi[r - 1], cy, yr[r - 1] * sy);
+      }
+      // columns 16 cj .. 16 cj + 15: Re T of the 8 rows, then Im T of the 8 rows
+      constexpr int kB = 4;                          // x16 loads in flight per wait
+#pragma unroll
+      for (int b0 = 0; b0 < kTcCj; b0 += kB) {
+        uint32_t r[kB][16];
+#pragma unroll
+        for (int q = 0; q < kB; ++q)
+          if (b0 + q < kTcCj) tc::ld_x16(lanebase + dcol + 16u * (b0 + q), r[q]);
+        tc::wait_ld();
+        if (b0 + kB >= kTcCj) {                      // every column of this buffer is read
+          tc::fence_before();
+          mbar_arrive(&sh.d_empty[gi & 1]);
+        }
+#pragma unroll
+        for (int q = 0; q < kB; ++q) {
+          if (b0 + q >= kTcCj) break;
+          float s = 0.f;
+#pragma unroll
+          for (int rr = 0; rr < kTcRows; ++rr)
+            s = fmaf(yr[rr], __uint_as_float(r[q][rr]), fmaf(-yi[rr], __uint_as_float(r[q][8 + rr]), s));
+          acc[b0 + q] += s;
+          // keep this batch's sums ahead of the next batch's loads (bounds live registers)
+          asm volatile("" : "+f"(acc[b0 + q]));
+        }
+      }
+    };
+
+    // A = X_m(p) of a K-chunk's 32 modes: word j = (cos, sin) as BF16 (hi, then the lo residual)
+    auto write_a = [&](int kc) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        uint32_t whi[16], wlo[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const unsigned m = unsigned(kc * kTcModes + 16 * h + j);
+          const unsigned ph = m * X;
+          float s, c;
+          sincospif(2.f * (float(int(ph)) * 2.3283064365386963e-10f), &s, &c);
+          bf2_split(c, s, whi[j], wlo[j]);
+        }
+        tc::st_x16(lanebase + kColAhi + 16u * h, whi);
+        tc::st_x16(lanebase + kColAlo + 16u * h, wlo);
+      }
+      tc::wait_st();
+      tc::fence_before();
+      mbar_arrive(&sh.a_ready);
+    };
+    write_a(0);
+    bool ok = true;
+    for (int gi = 0; gi < ngi; ++gi) {
+      ok = warp_wait(&sh.d_full[gi & 1], unsigned(gi >> 1) & 1u, abort_flag);
+      if (!ok) break;
+      tc::fence_after();
+      // the last group of a chunk is done, so are all MMAs reading this chunk's A: the next
+      // chunk's A goes in before this group's epilogue, so the MMAs resume at once
+      if ((gi + 1) % ng == 0 && gi + 1 < ngi) write_a((gi + 1) / ng);
+      consume(gi);
+    }
+    if (ok && live) {
+      const float uu = fmaf(dz, fmaf(dz, acc[2], acc[1]), acc[0]);
+      const float vv = fmaf(dz, fmaf(dz, acc[5], acc[4]), acc[3]);
+      const float ww = fmaf(dz, fmaf(dz, acc[8], acc[7]), acc[6]);
+      const float tt = fmaf(dz, fmaf(dz, acc[11], acc[10]), acc[9]);
+      const int64_t o = a.perm[pi];
+      if (a.o_eta) a.o_eta[o] = acc[12];
+      if (a.o_u) a.o_u[o] = uu;
+      if (a.o_v) a.o_v[o] = vv;
+      if (a.o_w) a.o_w[o] = ww;
+      if (a.o_p) {
+        float p;
+        if (a.p_mode == SWENSE_P_PHIT) {
+          p = tt;
+        } else {
+          p = -a.rho * (tt + 0.5f * (uu * uu + vv * vv + ww * ww));
+          if (a.p_mode == SWENSE_P_TOTAL) p -= a.rho * a.g * z;
+        }
+        a.o_p[o] = p;
+      }
+    }
+  } else if (warp < kMmaWarp) {
+    // ================================================================ producers: B per group
+    const int pw = warp - kEpiWarps;                // row of the group
+    const float h = a.depth;
+    for (int gi = 0; gi < ngi; ++gi) {
+      const int kc = gi / ng, g = gi % ng, s = gi & 1;
+      if (gi >= kTcStages && !warp_wait(&sh.b_empty[s], unsigned((gi >> 1) - 1) & 1u, abort_flag)) break;
+      const int tr = g * kTcRows + pw;
+      const int m = kc * kTcModes + lane;
+      const float4 c0 = __ldg(&a.tab[2 * (size_t(tr) * a.mp + m)]);
+      const float4 c1 = __ldg(&a.tab[2 * (size_t(tr) * a.mp + m) + 1]);
+      const int n = row_n(tr, a.ny, a.npos);
+      const float kx = float(m) * a.kxs, ky = float(n) * a.kys, k = c1.z;
+      float F0, S0;
+      depth_fs(k, z0, h, c1.w, F0, S0);
+      const float k1 = k, k2 = 0.5f * k * k;
+      const float P[kTcTerms] = {F0, k1 * S0, k2 * F0};     // F(z0 + dz) orders 0..2 (u, v, phi_t)
+      const float Q[kTcTerms] = {S0, k1 * F0, k2 * S0};     // S(z0 + dz) orders 0..2 (w)
+      // W_u = i kx A^phi, W_v = i ky A^phi, W_w = |k| A^phi, W_t = A^phit, W_eta = A^eta (the
+      // one-sided weights are in the table)
+      const float2 Wc[4] = {make_float2(-kx * c0.y, kx * c0.x), make_float2(-ky * c0.y, ky * c0.x),
+                            make_float2(k * c0.x, k * c0.y), make_float2(c0.z, c0.w)};
+      unsigned char* bhi = bst + size_t(s) * kTcStageBytes;
+      unsigned char* blo = bhi + kTcBBytes;
+      const uint32_t off = uint32_t(lane >> 2) * kTcLBO + uint32_t(pw) * 16u + uint32_t(lane & 3) * 4u;
+      auto put = [&](int cj, float re, float im) {
+        unsigned hi, lo;
+        bf2_split(re, -im, hi, lo);                 // column Re T: K pair (Re C, -Im C)
+        // column Im T: K pair (Im C, Re C) = the halves swapped, the new low half negated
+        const unsigned hi2 = __byte_perm(hi, 0u, 0x1032) ^ 0x8000u;
+        const unsigned lo2 = __byte_perm(lo, 0u, 0x1032) ^ 0x8000u;
+        const uint32_t o0 = off + uint32_t(2 * cj) * kTcSBO, o1 = o0 + kTcSBO;
+        *reinterpret_cast<unsigned*>(bhi + o0) = hi;
+        *reinterpret_cast<unsigned*>(blo + o0) = lo;
+        *reinterpret_cast<unsigned*>(bhi + o1) = hi2;
+        *reinterpret_cast<unsigned*>(blo + o1) = lo2;
+      };
+#pragma unroll
+      for (int j = 0; j < kTcTerms; ++j) {
+        put(0 * kTcTerms + j, Wc[0].x * P[j], Wc[0].y * P[j]);
+        put(1 * kTcTerms + j, Wc[1].x * P[j], Wc[1].y * P[j]);
+        put(2 * kTcTerms + j, Wc[2].x * Q[j], Wc[2].y * Q[j]);
+        put(3 * kTcTerms + j, Wc[3].x * P[j], Wc[3].y * P[j]);
+      }
+      put(4 * kTcTerms, c1.x, c1.y);
+      fence_proxy_async();                          // generic-proxy stores -> the MMA's reads
+      mbar_arrive(&sh.b_full[s]);
+    }
+  } else {
+    // ================================================================ MMA issue (one thread)
+    if (lane == 0) {
+      bool ok = true;
+      for (int kc = 0; kc < nkc && ok; ++kc) {
+        ok = thread_wait(&sh.a_ready, unsigned(kc) & 1u, abort_flag);
+        if (!ok) break;
+        tc::fence_after();
+        for (int g = 0; g < ng; ++g) {
+          const int gi = kc * ng + g, s = gi & 1, d = gi & 1;
+          ok = thread_wait(&sh.b_full[s], unsigned(gi >> 1) & 1u, abort_flag);
+          if (ok && gi >= 2) ok = thread_wait(&sh.d_empty[d], unsigned((gi >> 1) - 1) & 1u, abort_flag);
+          if (!ok) break;
+          tc::fence_after();
+          const uint32_t dt = tbase + (d ? kColD1 : kColD0);
+          unsigned char* bhi = bst + size_t(s) * kTcStageBytes;
+          unsigned char* blo = bhi + kTcBBytes;
+#pragma unroll
+          for (int ks = 0; ks < kTcK / 16; ++ks) {
+            const uint64_t dh = tc::smem_desc(bhi + 2 * ks * kTcLBO, kTcLBO, kTcSBO);
+            const uint64_t dl = tc::smem_desc(blo + 2 * ks * kTcLBO, kTcLBO, kTcSBO);
+            tc::mma_ts(dt, tbase + kColAhi + 8u * ks, dh, kIdesc, ks > 0 ? 1u : 0u);
+            tc::mma_ts(dt, tbase + kColAhi + 8u * ks, dl, kIdesc, 1u);
+            tc::mma_ts(dt, tbase + kColAlo + 8u * ks, dh, kIdesc, 1u);
+          }
+          tc::commit(&sh.b_empty[s]);
+          tc::commit(&sh.d_full[d]);
+        }
+      }
+      tc::commit(&sh.fin);                          // every MMA issued above has completed
+    }
+    __syncwarp();
+  }
+
+  // ---- teardown: the allocating warp frees tensor memory once every MMA has completed
+  tc::fence_before();
+  __syncthreads();
+  if (warp == kMmaWarp) {
+    tc::fence_after();
+    bool done = false;
+    for (int it = 0; it < kMbarPolls && !done; ++it) done = mbar_try_wait(&sh.fin, 0u);
+    done = __all_sync(0xffffffffu, done);
+    if (!done && lane == 0) atomicExch(&g_direct_timeout, 1);
+    tc::dealloc(tbase, kTmemCols);
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Mode table of the tensor-core path: rows of constant n (the Nyquist row skipped, rows padded to
+// a multiple of 8 with zero modes), m = 0 .. nx/2 - 1 padded to a multiple of 32.
+__global__ void k_tc_table(const float2* __restrict__ Ae, const float2* __restrict__ Ap,
+                           const float2* __restrict__ At, const double* __restrict__ omega, double dt,
+                           int nx, int ny, int rows_p, int mp, int npos, float kxs, float kys, float depth,
+                           float4* __restrict__ tab) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= int64_t(rows_p) * mp) return;
+  const int tr = int(i / mp), m = int(i - int64_t(tr) * mp);
+  float4 c0 = make_float4(0.f, 0.f, 0.f, 0.f), c1 = make_float4(0.f, 0.f, 0.f, 1.f);
+  const int n = row_n(tr, ny, npos);
+  const bool live_row = ny > 1 ? (n > -(ny / 2) && n < ny / 2 && (tr < npos) == (n >= 0)) : tr == 0;
+  if (live_row && m < nx / 2) {
+    const int r = n >= 0 ? n : n + ny;                   // storage row of the half spectrum
+    const size_t si = size_t(r) * (nx / 2 + 1) + m;
+    float2 e = Ae[si], p = Ap[si], t = At[si];
+    if (omega) {
+      const double turns = omega[si] * dt * 0.15915494309189533577;
+      const double frac = turns - rint(turns);
+      float s, c;
+      sincospif(2.f * float(frac), &s, &c);
+      e = make_float2(fmaf(e.x, c, e.y * s), fmaf(e.y, c, -e.x * s));
+      p = make_float2(fmaf(p.x, c, p.y * s), fmaf(p.y, c, -p.x * s));
+      t = make_float2(fmaf(t.x, c, t.y * s), fmaf(t.y, c, -t.x * s));
+    }
+    const float kx = float(m) * kxs, ky = float(n) * kys;
+    const float k = sqrtf(kx * kx + ky * ky);
+    const float wgt = m == 0 ? 1.f : 2.f;
+    c0 = make_float4(wgt * p.x, wgt * p.y, wgt * t.x, wgt * t.y);
+    c1 = make_float4(wgt * e.x, wgt * e.y, k, depth > 0.f ? 1.f / (1.f + expf(-2.f * k * depth)) : 1.f);
+  }
+  tab[2 * i] = c0;
+  tab[2 * i + 1] = c1;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Counting sort of the points by z (buckets over [min z, max z]); the order inside a bucket is
+// unspecified (atomics), so a tile's composition, hence its z0, can differ between calls: results
+// then differ at the level of the split products' rounding, never more.
+__device__ __forceinline__ unsigned fkey(float z) {
+  const unsigned u = __float_as_uint(z);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float fkey_inv(unsigned k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+__global__ void k_z_range(const float* __restrict__ pts, int64_t np, unsigned* __restrict__ mm) {
+  unsigned lo = 0xffffffffu, hi = 0u;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < np; i += int64_t(gridDim.x) * blockDim.x) {
+    const unsigned k = fkey(pts[3 * i + 2]);
+    lo = min(lo, k);
+    hi = max(hi, k);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(&mm[0], lo);
+    atomicMax(&mm[1], hi);
+  }
+}
+
+__device__ __forceinline__ int z_bucket(float z, float zlo, float scale) {
+  return min(kZBuckets - 1, max(0, int((z - zlo) * scale)));
+}
+
+__global__ void k_z_count(const float* __restrict__ pts, int64_t np, const unsigned* __restrict__ mm,
+                          unsigned* __restrict__ count) {
+  const float zlo = fkey_inv(mm[0]), zhi = fkey_inv(mm[1]);
+  const float scale = zhi > zlo ? float(kZBuckets) / (zhi - zlo) : 0.f;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < np; i += int64_t(gridDim.x) * blockDim.x)
+    atomicAdd(&count[z_bucket(pts[3 * i + 2], zlo, scale)], 1u);
+}
+
+// Exclusive scan of the kZBuckets counts by one block (64 per thread).
+__global__ void __launch_bounds__(1024) k_z_scan(unsigned* __restrict__ count) {
+  __shared__ unsigned s[1024];
+  constexpr int per = kZBuckets / 1024;
+  unsigned v[per], tot = 0;
+#pragma unroll
+  for (int j = 0; j < per; ++j) {
+    v[j] = count[threadIdx.x * per + j];
+    tot += v[j];
+  }
+  s[threadIdx.x] = tot;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    const unsigned add = threadIdx.x >= unsigned(o) ? s[threadIdx.x - o] : 0u;
+    __syncthreads();
+    s[threadIdx.x] += add;
+    __syncthreads();
+  }
+  unsigned run = s[threadIdx.x] - tot;
+#pragma unroll
+  for (int j = 0; j < per; ++j) {
+    count[threadIdx.x * per + j] = run;
+    run += v[j];
+  }
+}
+
+__global__ void k_z_scatter(const float* __restrict__ pts, int64_t np, const unsigned* __restrict__ mm,
+                            unsigned* __restrict__ cursor, int32_t* __restrict__ perm, float* __restrict__ sorted) {
+  const float zlo = fkey_inv(mm[0]), zhi = fkey_inv(mm[1]);
+  const float scale = zhi > zlo ? float(kZBuckets) / (zhi - zlo) : 0.f;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < np; i += int64_t(gridDim.x) * blockDim.x) {
+    const float x = pts[3 * i], y = pts[3 * i + 1], z = pts[3 * i + 2];
+    const unsigned pos = atomicAdd(&cursor[z_bucket(z, zlo, scale)], 1u);
+    perm[pos] = int32_t(i);
+    sorted[3 * size_t(pos)] = x;
+    sorted[3 * size_t(pos) + 1] = y;
+    sorted[3 * size_t(pos) + 2] = z;
+  }
+}
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+// ------------------------------------------------------------------------------------------------
+// Self-test of the tensor-core data path: D (128 x N) = A (128 x K) x B^T (B: N x K), BF16 inputs
+// (rounded from FP32), FP32 result, A from tensor memory (variant 0) or shared memory (variant 1),
+// B from shared memory in the K-major core-matrix layout used above (k-blocks lbo bytes apart).
+__global__ void __launch_bounds__(128, 1) k_tc_selftest(const float* __restrict__ A, const float* __restrict__ B,
+                                                        float* __restrict__ D, int N, int K, int variant) {
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  __shared__ uint64_t bar;
+  __shared__ uint32_t tm;
+  const int t = threadIdx.x, warp = t >> 5;
+  const uint32_t lbo = uint32_t(N / 8) * 128u + 16u;
+  const uint32_t lboa = (kTcM / 8) * 128u + 16u;
+  unsigned char* bs = smraw;                                    // B: (K / 8) k-blocks
+  unsigned char* as = smraw + size_t(K / 8) * lbo;              // A (variant 1)
+  for (int i = t; i < N * K / 2; i += 128) {
+    const int nn = i / (K / 2), kp = i % (K / 2), k = 2 * kp;
+    const uint32_t off = uint32_t(k / 8) * lbo + uint32_t(nn / 8) * 128u + uint32_t(nn % 8) * 16u + uint32_t(k % 8) * 2u;
+    *reinterpret_cast<unsigned*>(bs + off) = bf2(B[size_t(nn) * K + k], B[size_t(nn) * K + k + 1]);
+  }
+  if (variant == 1) {
+    for (int i = t; i < kTcM * K / 2; i += 128) {
+      const int mm = i / (K / 2), kp = i % (K / 2), k = 2 * kp;
+      const uint32_t off = uint32_t(k / 8) * lboa + uint32_t(mm / 8) * 128u + uint32_t(mm % 8) * 16u + uint32_t(k % 8) * 2u;
+      *reinterpret_cast<unsigned*>(as + off) = bf2(A[size_t(mm) * K + k], A[size_t(mm) * K + k + 1]);
+    }
+  }
+  if (t == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    tc::alloc(&tm, kTmemCols);
+    tc::relinquish();
+  }
+  fence_proxy_async();
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tb = tm;
+  const uint32_t lanebase = tb + ((uint32_t(warp) * 32u) << 16);
+  const uint32_t dcol = 256;
+  if (variant == 0) {                               // A row t into columns 0 .. K/2 - 1
+    for (int c0 = 0; c0 < K / 2; c0 += 16) {
+      uint32_t w[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        w[j] = c0 + j < K / 2 ? bf2(A[size_t(t) * K + 2 * (c0 + j)], A[size_t(t) * K + 2 * (c0 + j) + 1]) : 0u;
+      tc::st_x16(lanebase + uint32_t(c0), w);
+    }
+    tc::wait_st();
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (t == 0) {
+    tc::fence_after();
+    const uint32_t idesc = tc::idesc_bf16_f32(kTcM, N);
+    for (int ks = 0; ks < K / 16; ++ks) {
+      const uint64_t bd = tc::smem_desc(bs + 2 * ks * lbo, lbo, 128u);
+      if (variant == 0) {
+        tc::mma_ts(tb + dcol, tb + 8u * ks, bd, idesc, ks > 0 ? 1u : 0u);
+      } else {
+        const uint64_t ad = tc::smem_desc(as + 2 * ks * lboa, lboa, 128u);
+        tc::mma_ss(tb + dcol, ad, bd, idesc, ks > 0 ? 1u : 0u);
+      }
+    }
+    tc::commit(&bar);
+  }
+  __syncwarp();
+  bool done = false;
+  for (int it = 0; it < kMbarPolls && !done; ++it) done = mbar_try_wait(&bar, 0u);
+  done = __all_sync(0xffffffffu, done);
+  tc::fence_after();
+  if (done) {
+    for (int c0 = 0; c0 < N; c0 += 16) {
+      uint32_t r[16];
+      tc::ld_x16(lanebase + dcol + uint32_t(c0), r);
+      tc::wait_ld();
+#pragma unroll
+      for (int j = 0; j < 16; ++j) D[size_t(t) * N + c0 + j] = __uint_as_float(r[j]);
+    }
+  } else if ((t & 31) == 0) {
+    atomicExch(&g_direct_timeout, 1);
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after();
+    tc::dealloc(tb, kTmemCols);
+  }
+}
+
+}  // namespace
+
+int direct_async_flag(bool reset, int* was_set) {
+  int v = 0;
+  SWENSE_CUDA_TRY(cudaMemcpyFromSymbol(&v, g_direct_timeout, sizeof(int)));
+  if (reset && v) {
+    const int zero = 0;
+    SWENSE_CUDA_TRY(cudaMemcpyToSymbol(g_direct_timeout, &zero, sizeof(int)));
+  }
+  *was_set = v;
+  return SWENSE_OK;
+}
+
+// Per device: the tile flags of the last tensor-core call (for swense_direct_stats).
+struct TcLast {
+  const uint8_t* bad = nullptr;
+  int64_t ntiles = 0;
+};
+TcLast g_tc_last[64];
+
+// The tensor-core path of swense_direct (precision SWENSE_DIRECT_SPLIT_BF16): z sort, mode table,
+// k_direct_tc over tiles of 128 sorted points, and the per-pair split kernel for the tiles it
+// leaves (direct_split_sorted, direct.cu).
+int direct_tc(const swense_modes* md, double t, const float* pts, int64_t np, float* eta, float* u,
+              float* v, float* w, float* p, int32_t p_mode, double rho, double grav, cudaStream_t stream) {
+  const int nx = md->nx, ny = md->ny;
+  const int npos = ny > 1 ? (ny / 2 + kTcRows - 1) / kTcRows * kTcRows : kTcRows;
+  const int rows_p = npos + (ny > 1 ? (ny / 2 - 1 + kTcRows - 1) / kTcRows * kTcRows : 0);
+  const int mp = (nx / 2 + kTcModes - 1) / kTcModes * kTcModes;
+  const int64_t ntiles = (np + kTcM - 1) / kTcM;
+  if (ntiles >= (int64_t(1) << 31) || np >= (int64_t(1) << 31))
+    return fail(SWENSE_ERR_SIZE, "too many points for one call of the tensor-core path");
+  const size_t tab_b = align256(size_t(rows_p) * mp * 2 * sizeof(float4));
+  const size_t mm_b = 256, cnt_b = align256(size_t(kZBuckets) * sizeof(unsigned));
+  const size_t perm_b = align256(size_t(np) * sizeof(int32_t)), srt_b = align256(size_t(np) * 3 * sizeof(float));
+  const size_t bad_b = align256(size_t(ntiles));
+  const size_t split_off = tab_b + mm_b + cnt_b + perm_b + srt_b + bad_b;
+  void* ws = nullptr;
+  int st = workspace(split_off + split_table_bytes(md), stream, &ws);
+  if (st) return st;
+  char* base = static_cast<char*>(ws);
+  float4* tab = reinterpret_cast<float4*>(base);
+  unsigned* mm = reinterpret_cast<unsigned*>(base + tab_b);
+  unsigned* cnt = reinterpret_cast<unsigned*>(base + tab_b + mm_b);
+  int32_t* perm = reinterpret_cast<int32_t*>(base + tab_b + mm_b + cnt_b);
+  float* srt = reinterpret_cast<float*>(base + tab_b + mm_b + cnt_b + perm_b);
+  uint8_t* bad = reinterpret_cast<uint8_t*>(base + tab_b + mm_b + cnt_b + perm_b + srt_b);
+
+  const float kxs = float(6.283185307179586476925 / md->Lx);
+  const float kys = ny > 1 ? float(6.283185307179586476925 / md->Ly) : 0.f;
+  const float depth = md->depth > 0 ? float(md->depth) : 0.f;
+  {
+    const int64_t n = int64_t(rows_p) * mp;
+    k_tc_table<<<unsigned((n + 255) / 256), 256, 0, stream>>>(
+        reinterpret_cast<const float2*>(md->A_eta), reinterpret_cast<const float2*>(md->A_phi),
+        reinterpret_cast<const float2*>(md->A_phit), md->omega, t - md->t_ref, nx, ny, rows_p, mp, npos,
+        kxs, kys, depth, tab);
+    SWENSE_CUDA_TRY(cudaGetLastError());
+  }
+  SWENSE_CUDA_TRY(cudaMemsetAsync(mm, 0xff, sizeof(unsigned), stream));          // running min
+  SWENSE_CUDA_TRY(cudaMemsetAsync(mm + 1, 0, sizeof(unsigned), stream));         // running max
+  SWENSE_CUDA_TRY(cudaMemsetAsync(cnt, 0, size_t(kZBuckets) * sizeof(unsigned), stream));
+  const unsigned gs = unsigned(std::min<int64_t>((np + 255) / 256, 152 * 8));
+  k_z_range<<<gs, 256, 0, stream>>>(pts, np, mm);
+  k_z_count<<<gs, 256, 0, stream>>>(pts, np, mm, cnt);
+  k_z_scan<<<1, 1024, 0, stream>>>(cnt);
+  k_z_scatter<<<gs, 256, 0, stream>>>(pts, np, mm, cnt, perm, srt);
+  SWENSE_CUDA_TRY(cudaGetLastError());
+  count_launches(5);
+
+  TcArgs a{};
+  a.tab = tab;
+  a.rows_p = rows_p;
+  a.mp = mp;
+  a.ny = ny;
+  a.npos = npos;
+  a.spts = srt;
+  a.perm = perm;
+  a.np = np;
+  a.o_eta = eta;
+  a.o_u = u;
+  a.o_v = v;
+  a.o_w = w;
+  a.o_p = p;
+  a.inv_lx = 1.0 / md->Lx;
+  a.inv_ly = ny > 1 ? 1.0 / md->Ly : 0.0;
+  a.kxs = kxs;
+  a.kys = kys;
+  a.depth = depth;
+  {
+    const double kx = double(nx / 2 - 1) * kxs, ky = ny > 1 ? double(ny / 2 - 1) * kys : 0.0;
+    a.kmax = float(std::sqrt(kx * kx + ky * ky));
+  }
+  a.p_mode = p_mode;
+  a.rho = float(rho);
+  a.g = float(grav);
+  a.tile_bad = bad;
+  const size_t smem = size_t(kTcStages) * kTcStageBytes + sizeof(TcShared);
+  SWENSE_CUDA_TRY(cudaFuncSetAttribute(k_direct_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+  k_direct_tc<<<unsigned(ntiles), kTcThreads, smem, stream>>>(a);
+  SWENSE_CUDA_TRY(cudaGetLastError());
+  count_launches(1);
+  {
+    int dev = 0;
+    SWENSE_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev >= 0 && dev < 64) g_tc_last[dev] = TcLast{bad, ntiles};
+  }
+  // tiles whose z range is too wide for the expansion: the per-pair kernel
+  return direct_split_sorted(md, t, srt, perm, bad, kTcM, np, eta, u, v, w, p, p_mode, rho, grav, stream,
+                             split_off);
+}
+
+}  // namespace swense
+
+using namespace swense;
+
+extern "C" int swense_direct_stats(int64_t* tiles, int64_t* fallback_tiles, void* stream) {
+  if (!tiles || !fallback_tiles) return fail(SWENSE_ERR_ARG, "NULL output");
+  int dev = 0;
+  SWENSE_CUDA_TRY(cudaGetDevice(&dev));
+  *tiles = *fallback_tiles = 0;
+  if (dev < 0 || dev >= 64 || !g_tc_last[dev].bad) return SWENSE_OK;
+  SWENSE_CUDA_TRY(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+  std::vector<uint8_t> h(size_t(g_tc_last[dev].ntiles));
+  SWENSE_CUDA_TRY(cudaMemcpy(h.data(), g_tc_last[dev].bad, h.size(), cudaMemcpyDeviceToHost));
+  *tiles = g_tc_last[dev].ntiles;
+  int64_t nb = 0;
+  for (uint8_t b : h) nb += b != 0;
+  *fallback_tiles = nb;
+  return SWENSE_OK;
+}
+
+extern "C" int swense_selftest_tc_gemm(const float* A, const float* B, float* D, int32_t N, int32_t K,
+                                       int32_t variant, void* stream_) {
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+  if (!A || !B || !D) return fail(SWENSE_ERR_ARG, "NULL operand");
+  if (N < 16 || N > 256 || N % 16 || K < 16 || K > 256 || K % 16 || (variant != 0 && variant != 1))
+    return fail(SWENSE_ERR_ARG, "N in 16..256 (multiple of 16), K in 16..256 (multiple of 16), variant 0 or 1");
+  const size_t smem = size_t(K / 8) * ((N / 8) * 128 + 16) + size_t(K / 8) * ((kTcM / 8) * 128 + 16);
+  SWENSE_CUDA_TRY(cudaFuncSetAttribute(k_tc_selftest, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+  k_tc_selftest<<<1, 128, smem, stream>>>(A, B, D, N, K, variant);
+  SWENSE_CUDA_TRY(cudaGetLastError());
+  count_launches(1);
+  return SWENSE_OK;
+}

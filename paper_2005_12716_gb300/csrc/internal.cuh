@@ -35,6 +35,19 @@ void count_launches(int n);
 // Device-side error flags of bounded waits, one per translation unit that has such waits: read
 // (and cleared when reset) on the current device; *was_set != 0 when a wait gave up.
 int grid_async_flag(bool reset, int* was_set);
+int direct_async_flag(bool reset, int* was_set);
+
+// Near-body direct sums (direct.cu, direct_tc.cu). direct_tc: the tensor-core split-BF16 path;
+// direct_split_sorted: the per-pair split-BF16 kernel over points sorted by the tensor-core path
+// (srt, perm: sorted coordinates and sorted -> caller index), restricted to the tiles of
+// `tile_pts` sorted points that tile_bad marks.
+int direct_tc(const swense_modes* md, double t, const float* pts, int64_t np, float* eta, float* u,
+              float* v, float* w, float* p, int32_t p_mode, double rho, double grav, cudaStream_t stream);
+size_t split_table_bytes(const swense_modes* md);
+int direct_split_sorted(const swense_modes* md, double t, const float* srt, const int32_t* perm,
+                        const uint8_t* tile_bad, int tile_pts, int64_t np, float* eta, float* u, float* v,
+                        float* w, float* p, int32_t p_mode, double rho, double grav, cudaStream_t stream,
+                        size_t ws_offset);
 
 inline bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
 inline int ilog2(int64_t v) { int r = 0; while ((int64_t(1) << r) < v) ++r; return r; }
@@ -63,6 +76,14 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 }
 __device__ __forceinline__ float2 cmul_i(float2 a) { return make_float2(-a.y, a.x); }   // i*a
 __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+
+// x / L as an unsigned 32-bit fraction of a turn (FP64 once per point), so that a mode's phase
+// m X (mod 2^32) is exact whatever |k x|.
+__device__ __forceinline__ unsigned turn_fraction(float x, double inv_l) {
+  const double f = double(x) * inv_l;
+  const double fr = f - floor(f);                        // [0, 1)
+  return unsigned((unsigned long long)(fr * 4294967296.0) & 0xffffffffull);
+}
 
 __device__ __forceinline__ unsigned bitrev(unsigned v, int bits) {
   return bits == 0 ? 0u : (__brev(v) >> (32 - bits));
