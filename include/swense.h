@@ -183,7 +183,9 @@ int swense_fields_on_grid_noalloc(const swense_modes* modes, int32_t n_tl, const
  * straight from memory; both lengths in 256..1024; 3 = as 2 with one transform per warp;
  * 4 = as 2 with each warp's rows staged in shared memory by bulk asynchronous copies; 5 = as 2
  * with chunk c's row pass on a library-internal second stream while chunk c+1's column pass
- * runs on `stream`, two intermediate buffers, joined back before the call's work ends):
+ * runs on `stream`, two intermediate buffers, joined back before the call's work ends), plus 16
+ * when the transposed pair's column pass runs one modal field per block (four times the blocks
+ * per level, half the registers; the untuned default for 1024-point columns):
  * host, may be NULL. Errors: as swense_fields_on_grid.
  */
 int swense_autotune_grid(const swense_modes* modes, int32_t n_tl, const double* t,
@@ -196,8 +198,8 @@ int swense_autotune_grid(const swense_modes* modes, int32_t n_tl, const double* 
  * (nx, ny, pad_n, nz), e.g. a choice that swense_autotune_grid returned in an earlier process.
  * lpc: -1 (forget any choice: untuned defaults again), 0 (shared-memory path), 1, 2 or 4 levels
  * per column block;
- * chunk_bytes in [1 MiB, 1 GiB] (L2-resident level chunk); row_variant 0..5 (as returned by
- * swense_autotune_grid). Results do not depend on the choice beyond FP32 rounding. No
+ * chunk_bytes in [1 MiB, 1 GiB] (L2-resident level chunk); row_variant 0..5, plus 16 for the
+ * one-field column pass (as returned by swense_autotune_grid). Results do not depend on the choice beyond FP32 rounding. No
  * counterpart in the paper. Errors: SWENSE_ERR_ARG for values outside those sets.
  */
 int swense_set_grid_tune(int32_t nx, int32_t ny, int32_t pad_n, int32_t nz, int32_t lpc,

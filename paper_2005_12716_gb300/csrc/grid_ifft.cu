@@ -747,6 +747,76 @@ __global__ void __launch_bounds__(256, N >= 1024 ? 1 : 2) k_col_t(ColArgs a, Lev
   }
 }
 
+// Column pass of the transposed pair with the four modal fields in separate CTAs (blockIdx.z =
+// field U, V, W, T): four times the CTAs of k_col_t per level and half its registers, so long
+// columns fill the GPU even when a level chunk holds few levels (a 1024-point column pass has
+// only Mh / 8 CTAs per level otherwise). The output tile and the warps' exchange buffers share
+// the same shared memory (a barrier between the transforms and the tile writes).
+template <int N>
+__global__ void __launch_bounds__(256, 2) k_col_tf(ColArgs a, Levels L) {
+  extern __shared__ float2 sm[];                 // exchange buffers, then tile [N][kColBlock + 1]
+  constexpr int E = N / 32, RL = stk_radix(N, stk_npass(N) - 1);
+  constexpr int TLD = kColBlock + 1;
+  static_assert(kColBlock * 32 == kThreads, "one column per warp");
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c0 = blockIdx.x * kColBlock;
+  const int m = c0 + warp;
+  const bool colok = m < a.Mh;
+  const int q = blockIdx.z;
+  float2* tile = sm;
+  float2* wbuf = sm + warp * stk_buf(N);
+  float2 T[stk_twn(N)];
+  stk_init<N>(T, a.tw, lane);
+  const int nyh = a.ny >> 1;
+  const float kx = colok ? float(m) * a.kxs : 0.f;
+  const float2* __restrict__ A = q == 3 ? a.A_phit : a.A_phi;
+  for (int li = 0; li < a.lpc; ++li) {
+    const int level = blockIdx.y * a.lpc + li;
+    if (level >= a.nlev) break;                  // uniform over the block
+    const float z = L.z[a.lev0 + level];
+    float2 v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int p = lane + 32 * (e / 8) + (e % 8) * (N / 8);
+      int n = 0;
+      bool live = colok;
+      if (p < nyh) n = p;
+      else if (p > N - nyh) n = p - N;
+      else live = false;
+      // zero-padded and Nyquist positions carry no mode: their (unused) depth factor is taken
+      // at ky = 0, where it cannot overflow
+      const float ky = float(live ? n : 0) * a.kys;
+      const float kk = sqrtf(kx * kx + ky * ky);
+      float F, S;
+      depth_factors(kk, z, a.depth, F, S);
+      float2 am = make_float2(0.f, 0.f);
+      if (live) {
+        am = __ldg(&A[size_t(n >= 0 ? n : a.ny + n) * a.nxh1 + m]);
+        if (a.spline) {
+          const float pf = spline_prefilter(m, a.Nxr, n, a.Nyr);
+          am = make_float2(pf * am.x, pf * am.y);
+        }
+      }
+      v[e] = modal_field(q, kx, ky, kk, F, S, am, am);
+    }
+    stk_fft<N>(v, T, a.tw, wbuf, lane);
+    __syncthreads();                             // every warp is done with its exchange buffer
+#pragma unroll
+    for (int e = 0; e < E; ++e) tile[(lane + 32 * (e / RL) + (e % RL) * (N / RL)) * TLD + warp] = v[e];
+    __syncthreads();
+    float2* out = a.G + (size_t(level) * 4 + q) * a.Nyr * a.ldG + c0;
+    // two columns per thread: 16-byte stores (ldG and c0 are multiples of 16 and 8 entries)
+    for (int i = threadIdx.x; i < N * kColBlock / 2; i += kThreads) {
+      const int y = i / (kColBlock / 2), w = 2 * (i % (kColBlock / 2));
+      const float2 v0 = tile[y * TLD + w], v1 = tile[y * TLD + w + 1];
+      float2* o = &out[size_t(y) * a.ldG + w];
+      if (c0 + w + 1 < a.Mh) __stcg(reinterpret_cast<float4*>(o), make_float4(v0.x, v0.y, v1.x, v1.y));
+      else if (c0 + w < a.Mh) __stcg(o, v0);
+    }
+    __syncthreads();                             // the tile is read before the next transforms
+  }
+}
+
 // Row pass over the transposed intermediate: one warp per grid row of one level, its four
 // modal fields loaded straight from G (consecutive lanes read consecutive m), packed as
 // Z1 = U + iV and Z2 = W + iT over the full x spectrum, transformed, stored as float4.
@@ -999,6 +1069,8 @@ struct Tune {
   size_t chunk_bytes = kChunkBytes;     // scratch per level chunk (L2-resident)
   int rowv = 0;                         // row pass: 0 both field pairs per warp (k_row_stk),
                                         // 1 one field pair per CTA (k_row_half)
+  int colv = 0;                         // column pass of the transposed pair: 0 k_col_t,
+                                        // 1 k_col_tf (one modal field per CTA)
 };
 std::mutex g_tune_mutex;
 std::map<std::array<int64_t, 4>, Tune> g_tune;
@@ -1062,6 +1134,18 @@ int launch_col_t(const ColArgs& c, const Levels& L, dim3 grid, cudaStream_t stre
 }
 
 template <int N>
+int launch_col_tf(const ColArgs& c, const Levels& L, dim3 grid, cudaStream_t stream) {
+  const size_t smem = std::max(size_t(N) * (kColBlock + 1), size_t(8) * stk_buf(N)) * sizeof(float2);
+  int st = set_smem((const void*)k_col_tf<N>, smem);
+  if (st) return st;
+  grid.z = 4;
+  k_col_tf<N><<<grid, kThreads, smem, stream>>>(c, L);
+  SWENSE_CUDA_TRY(cudaGetLastError());
+  count_launches(1);
+  return SWENSE_OK;
+}
+
+template <int N>
 int launch_row_t(const RowArgs& r, dim3 grid, cudaStream_t stream) {
   const size_t smem = size_t(8) * stk_buf(N) * sizeof(float2);
   int st = set_smem((const void*)k_row_t<N>, smem);
@@ -1112,12 +1196,19 @@ int launch_row_t2(const RowArgs& r, dim3 grid, cudaStream_t stream) {
 // Transposed-intermediate pair (row variants 2 and 3): both transform lengths in 256..1024;
 // variant 3 runs one transform per warp in the row pass.
 int launch_pair_t(const ColArgs& c, const RowArgs& r, const Levels& L, int nl, cudaStream_t s,
-                  bool one_per_warp, bool staged = false, int which = 0) {
+                  bool one_per_warp, bool staged = false, int which = 0, int colv = 0) {
   const dim3 gc(unsigned((c.Mh + kColBlock - 1) / kColBlock), unsigned((nl + c.lpc - 1) / c.lpc));
   const dim3 gr(unsigned((r.Nyr + 7) / 8), unsigned(nl));
   const dim3 gr2(unsigned((r.Nyr + 3) / 4), unsigned(nl));
   int st = SWENSE_OK;
-  if (which != 2) {
+  if (which != 2 && colv == 1) {
+    switch (c.Nyr) {
+      case 256: st = launch_col_tf<256>(c, L, gc, s); break;
+      case 512: st = launch_col_tf<512>(c, L, gc, s); break;
+      case 1024: st = launch_col_tf<1024>(c, L, gc, s); break;
+      default: return fail(SWENSE_ERR_UNSUPPORTED, "transposed pair: column length");
+    }
+  } else if (which != 2) {
     switch (c.Nyr) {
       case 256: st = launch_col_t<256, 2>(c, L, gc, s); break;
       case 512: st = launch_col_t<512, 1>(c, L, gc, s); break;
@@ -1275,6 +1366,10 @@ int plan_grid(const swense_modes* md, int32_t n_tl, const double* t, const swens
   return SWENSE_OK;
 }
 
+// Untuned column-pass variant of the transposed pair: one modal field per CTA (k_col_tf) for
+// 1024-point columns, whose k_col_t runs one CTA per SM with only Mh / 8 CTAs per level.
+int default_colv(const GridPlan& p) { return pair_path(p.ny, p.Nxr, p.Nyr) && p.Nyr >= 1024 ? 1 : 0; }
+
 // Scratch bytes for a level chunk of `chunk` levels (0 when no scratch is needed).
 size_t scratch_bytes(const GridPlan& p, int chunk, int nbuf = 1) {
   const size_t g_bytes = p.ny > 1 ? size_t(chunk) * p.per_level : 0;
@@ -1319,7 +1414,7 @@ int get_pipe(Pipe** out) {
 // level's propagated modes exist and joined back before the call returns (graph-capturable).
 int launch_grid(const GridPlan& p, const swense_modes* md, const double* t, float* nodes, float* eta,
                 void* ws, int chunk, cudaStream_t stream, int lpc = kColLevels, int rowv = 0,
-                int overlap = 0, int eta_side = 0) {
+                int overlap = 0, int eta_side = 0, int colv = 0) {
   const float2* tw = nullptr;
   {
     int st = twiddles(stream, &tw);
@@ -1531,7 +1626,7 @@ int launch_grid(const GridPlan& p, const swense_modes* md, const double* t, floa
           ca.G = b ? g_lev2 : g_lev;
           ra.G = ca.G;
           if (chunk_no >= 2) SWENSE_CUDA_TRY(cudaStreamWaitEvent(stream, pipe->row_done[b], 0));
-          int st = launch_pair_t(ca, ra, p.lev, nl, stream, false, false, 1);   // column pass
+          int st = launch_pair_t(ca, ra, p.lev, nl, stream, false, false, 1, colv);   // column pass
           if (st) return st;
           SWENSE_CUDA_TRY(cudaEventRecord(pipe->col_done[b], stream));
           SWENSE_CUDA_TRY(cudaStreamWaitEvent(pipe->side, pipe->col_done[b], 0));
@@ -1546,7 +1641,7 @@ int launch_grid(const GridPlan& p, const swense_modes* md, const double* t, floa
           ca.lev0 = l0;
           ca.nlev = nl;
           ra.lev0 = l0;
-          int st = launch_pair_t(ca, ra, p.lev, nl, stream, rowv == 3, rowv == 4);
+          int st = launch_pair_t(ca, ra, p.lev, nl, stream, rowv == 3, rowv == 4, 0, colv);
           if (st) return st;
           continue;
         }
@@ -1734,13 +1829,15 @@ extern "C" int swense_fields_on_grid(const swense_modes* md, int32_t n_tl, const
   const bool pair = pair_path(p.ny, p.Nxr, p.Nyr);
   const int lpc = tn.lpc >= 0 ? tn.lpc : (pair ? 4 : ((p.Nxr <= 512 && p.Nyr <= 512) ? kColLevels : 0));
   const int rowv = tn.lpc >= 0 ? tn.rowv : (pair ? 2 : 0);
+  const int colv = tn.lpc >= 0 ? tn.colv : default_colv(p);
   // variant 5: variant 2 with its column and row passes pipelined over two streams
   const size_t ws_bytes = scratch_bytes(p, chunk, rowv == 5 ? 2 : 1);
   if (ws_bytes) {
     st = workspace(ws_bytes, stream, &ws);
     if (st) return st;
   }
-  return launch_grid(p, md, t, nodes, eta, ws, chunk, stream, lpc, rowv == 5 ? 2 : rowv, rowv == 5, 1);
+  return launch_grid(p, md, t, nodes, eta, ws, chunk, stream, lpc, rowv == 5 ? 2 : rowv, rowv == 5, 1,
+                     colv);
 }
 
 extern "C" int swense_autotune_grid(const swense_modes* md, int32_t n_tl, const double* t,
@@ -1771,7 +1868,8 @@ extern "C" int swense_autotune_grid(const swense_modes* md, int32_t n_tl, const 
       if (st) return st;
     }
     for (int lpc : {0, 1, 2, 4})
-    for (int rowv : {0, 1, 2, 3, 4, 5}) {
+    for (int rv : {0, 1, 2, 3, 4, 5, 2 + 16, 4 + 16, 5 + 16}) {
+      const int rowv = rv & 15, colv = rv >> 4;
       const bool wp = warp_path(p.ny, p.Nxr, p.Nyr), pp = pair_path(p.ny, p.Nxr, p.Nyr);
       if (lpc > 0 && !wp && !(pp && rowv == 2)) continue;
       if (rowv && (lpc == 0 || p.Nxr < 256)) continue;   // only the Stockham row sizes have variants
@@ -1783,14 +1881,14 @@ extern "C" int swense_autotune_grid(const swense_modes* md, int32_t n_tl, const 
         const int chunk = int(std::max<size_t>(1, std::min<size_t>(p.nz, cb / p.per_level)));
         void* ws = nullptr;
         st = workspace(ws_all, stream, &ws);
-        const int rv = rowv == 5 ? 2 : rowv;
-        if (!st) st = launch_grid(p, md, t, nodes, eta, ws, chunk, stream, lpc, rv, rowv == 5, 1);   // warm
+        const int rv2 = rowv == 5 ? 2 : rowv;
+        if (!st) st = launch_grid(p, md, t, nodes, eta, ws, chunk, stream, lpc, rv2, rowv == 5, 1, colv);   // warm
         // best of five (the fastest repetition is the least disturbed one)
         float ms = 0.f, tot = 1e30f;
         for (int rep = 0; rep < 5 && !st; ++rep) {
           if (cudaMemsetAsync(ws, 0, kFlushBytes, stream) != cudaSuccess) { st = SWENSE_ERR_CUDA; break; }
           if (cudaEventRecord(e0, stream) != cudaSuccess) { st = SWENSE_ERR_CUDA; break; }
-          st = launch_grid(p, md, t, nodes, eta, ws, chunk, stream, lpc, rv, rowv == 5, 1);
+          st = launch_grid(p, md, t, nodes, eta, ws, chunk, stream, lpc, rv2, rowv == 5, 1, colv);
           if (cudaEventRecord(e1, stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
               cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) st = SWENSE_ERR_CUDA;
           tot = std::min(tot, ms);
@@ -1801,6 +1899,7 @@ extern "C" int swense_autotune_grid(const swense_modes* md, int32_t n_tl, const 
           best.lpc = lpc;
           best.chunk_bytes = cb;
           best.rowv = rowv;
+          best.colv = colv;
         }
       }
       if (st) break;
@@ -1813,7 +1912,7 @@ extern "C" int swense_autotune_grid(const swense_modes* md, int32_t n_tl, const 
   }
   if (lpc_out) *lpc_out = best.lpc;
   if (chunk_bytes_out) *chunk_bytes_out = int64_t(best.chunk_bytes);
-  if (row_variant_out) *row_variant_out = best.rowv;
+  if (row_variant_out) *row_variant_out = best.rowv + 16 * best.colv;
   return SWENSE_OK;
 }
 
@@ -1823,7 +1922,8 @@ extern "C" int swense_set_grid_tune(int32_t nx, int32_t ny, int32_t pad_n, int32
     return fail(SWENSE_ERR_ARG, "lpc must be -1 (default), 0, 1, 2 or 4");
   if (chunk_bytes < (int64_t(1) << 20) || chunk_bytes > (int64_t(1) << 30))
     return fail(SWENSE_ERR_ARG, "chunk_bytes must be in [1 MiB, 1 GiB]");
-  if (row_variant < 0 || row_variant > 5) return fail(SWENSE_ERR_ARG, "row_variant must be 0..5");
+  if ((row_variant & 15) > 5 || (row_variant >> 4) > 1 || row_variant < 0)
+    return fail(SWENSE_ERR_ARG, "row_variant must be 0..5, plus 16 for the one-field column pass");
   std::lock_guard<std::mutex> lock(g_tune_mutex);
   if (lpc == -1) {                      // back to the untuned defaults for this shape
     g_tune.erase({nx, ny, pad_n, nz});
@@ -1832,7 +1932,8 @@ extern "C" int swense_set_grid_tune(int32_t nx, int32_t ny, int32_t pad_n, int32
   Tune tn;
   tn.lpc = lpc;
   tn.chunk_bytes = size_t(chunk_bytes);
-  tn.rowv = row_variant;
+  tn.rowv = row_variant & 15;
+  tn.colv = row_variant >> 4;
   g_tune[{nx, ny, pad_n, nz}] = tn;
   return SWENSE_OK;
 }
@@ -1946,5 +2047,6 @@ extern "C" int swense_fields_on_grid_noalloc(const swense_modes* md, int32_t n_t
   const int lpc = tn.lpc >= 0 ? tn.lpc : (pair ? 4 : ((p.Nxr <= 512 && p.Nyr <= 512) ? kColLevels : 0));
   int rowv = tn.lpc >= 0 ? tn.rowv : (pair ? 2 : 0);
   if (rowv == 5) rowv = 2;
-  return launch_grid(p, md, t, nodes, eta, ws, chunk, stream, lpc, rowv, 0, 0);
+  const int colv = tn.lpc >= 0 ? tn.colv : default_colv(p);
+  return launch_grid(p, md, t, nodes, eta, ws, chunk, stream, lpc, rowv, 0, 0, colv);
 }

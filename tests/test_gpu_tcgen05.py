@@ -143,7 +143,7 @@ def test_tensor_path_equals_pairwise_kernel(env):
     torch, S, api = env
     cfg = configs.jonswap3d(mesh_dims=(4, 8, 4))
     sea = cfg["sea"]
-    pts = P.uniform_points(200_000, (14.0, 6.0, -1.0), (18.0, 10.0, 0.07), 43)
+    pts = P.uniform_points(400_000, (14.0, 6.0, -0.6), (18.0, 10.0, 0.07), 43)
     modes = api.upload_modes(sea)
     d = torch.from_numpy(pts).cuda()
     a = api.direct(modes, cfg["t_query"], d, precision="split_bf16")
