@@ -402,6 +402,49 @@ int swense_mlp_train_step(float* params, float* adam_m, float* adam_v, void* pac
                           const int32_t* batch, int32_t B, float lr, float beta1, float beta2,
                           float eps, float* loss, void* stream);
 
+/* Training targets of the learned correction from the method's own data: for point i and field
+ * f (u, v, w, dphi/dt), row 4 i + f gets target = (exact_f - lagrange_f) / scale_f and field = f,
+ * with exact_* device float [np] (swense_direct, p_mode PHIT), lagrange and scale device float
+ * [4 np] (swense_mlp_features). target device float [4 np], field device int32 [4 np].
+ * Errors: ARG, CUDA. */
+int swense_mlp_targets(const float* exact_u, const float* exact_v, const float* exact_w,
+                       const float* exact_phit, const float* lagrange, const float* scale,
+                       int64_t np, float* target, int32_t* field, void* stream);
+
+/* A network and its training state. The caller owns the device buffers (params, adam_m, adam_v:
+ * FP32 [SWENSE_MLP_NPARAM]; packed: SWENSE_MLP_PACKED_BYTES, 16-byte aligned); step, seed and
+ * out_scale are host values that the calls below read and update. */
+typedef struct {
+  float* params;
+  float* adam_m;
+  float* adam_v;
+  void* packed;
+  int64_t step;       /* Adam steps taken so far */
+  uint64_t seed;      /* mini-batch generator seed */
+  float out_scale;    /* inference output multiplier; <= 0: set by the next swense_mlp_train */
+} swense_mlp;
+
+/* `steps` Adam steps (the loop runs in the library) on mini-batches of B rows of the dataset
+ * (x [n_rows][SWENSE_MLP_XLD], field [n_rows], target [n_rows], device). Batch s (s = mlp->step,
+ * 0-based) holds rows SplitMix64(seed + s 2^32 + i) mod n_rows, i < B, so a run can be split
+ * and resumed (swense_mlp_save / swense_mlp_load) with bit-identical parameters; gradients are
+ * summed in a fixed order. Learning rate lr x (1 + cos(pi min(s, schedule_steps) /
+ * schedule_steps)) / 2 (constant lr when schedule_steps <= 0). The network learns
+ * target / out_scale; if mlp->out_scale <= 0 it is first set to the RMS of the targets (one
+ * device reduction, synchronising) and packed. losses: device float [steps] (mean squared error
+ * of each step in scaled units) or NULL. Uses the workspace. Errors: ARG, OOM, CUDA. */
+int swense_mlp_train(swense_mlp* mlp, const float* x, const int32_t* field, const float* target,
+                     int64_t n_rows, int32_t steps, int32_t B, float lr, int64_t schedule_steps,
+                     float beta1, float beta2, float eps, float* losses, void* stream);
+
+/* Checkpoint (little-endian file): "SWMLP002", int64 step, uint64 seed, int64 nparam (must be
+ * SWENSE_MLP_NPARAM), float64 out_scale, then params, adam_m, adam_v as float32. save
+ * synchronises the stream; load fills the caller's buffers and mlp's host fields and repacks
+ * (synchronising). Errors: ARG (file cannot be opened, written or read, wrong header or size),
+ * CUDA. */
+int swense_mlp_save(const swense_mlp* mlp, const char* path, void* stream);
+int swense_mlp_load(swense_mlp* mlp, const char* path, void* stream);
+
 /* swense_interp with the learned correction applied to u, v, w and dphi/dt (eta plain).
  * Same arguments and out-of-range rules as swense_interp plus the packed weights; 3-D grids
  * only. Uses the workspace (about 0.6 GB for the largest point chunk). */

@@ -386,6 +386,51 @@ _SIGS.update({
 })
 
 
+class swense_mlp(ctypes.Structure):
+    _fields_ = [("params", ctypes.c_void_p), ("adam_m", ctypes.c_void_p), ("adam_v", ctypes.c_void_p),
+                ("packed", ctypes.c_void_p), ("step", ctypes.c_int64), ("seed", ctypes.c_uint64),
+                ("out_scale", ctypes.c_float)]
+
+
+_SIGS.update({
+    "swense_mlp_targets": (ctypes.c_int, [ctypes.c_void_p] * 6 + [ctypes.c_int64, ctypes.c_void_p,
+                                                                  ctypes.c_void_p, ctypes.c_void_p]),
+    "swense_mlp_train": (ctypes.c_int, [ctypes.POINTER(swense_mlp), ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                        ctypes.c_float, ctypes.c_int64, ctypes.c_float, ctypes.c_float,
+                                        ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p]),
+    "swense_mlp_save": (ctypes.c_int, [ctypes.POINTER(swense_mlp), ctypes.c_char_p, ctypes.c_void_p]),
+    "swense_mlp_load": (ctypes.c_int, [ctypes.POINTER(swense_mlp), ctypes.c_char_p, ctypes.c_void_p]),
+})
+
+
+def make_mlp(params, adam_m, adam_v, packed, step=0, seed=0, out_scale=0.0):
+    m = swense_mlp(_ptr(params), _ptr(adam_m), _ptr(adam_v), _ptr(packed), step, seed, out_scale)
+    m._keep = (params, adam_m, adam_v, packed)
+    return m
+
+
+def swense_mlp_targets(eu, ev, ew, et, lagrange, scale, np_, target, field, stream=None):
+    _check(load().swense_mlp_targets(_ptr(eu), _ptr(ev), _ptr(ew), _ptr(et), _ptr(lagrange),
+                                     _ptr(scale), np_, _ptr(target), _ptr(field), _stream(stream)))
+
+
+def swense_mlp_train(mlp, x, field, target, n_rows, steps, B, lr, schedule_steps=0, beta1=0.9,
+                     beta2=0.999, eps=1e-8, losses=None, stream=None):
+    """mlp: a swense_mlp struct (its step / out_scale are updated in place)."""
+    _check(load().swense_mlp_train(ctypes.byref(mlp), _ptr(x), _ptr(field), _ptr(target), n_rows,
+                                   steps, B, lr, schedule_steps, beta1, beta2, eps, _ptr(losses),
+                                   _stream(stream)))
+
+
+def swense_mlp_save(mlp, path, stream=None):
+    _check(load().swense_mlp_save(ctypes.byref(mlp), os.fsencode(path), _stream(stream)))
+
+
+def swense_mlp_load(mlp, path, stream=None):
+    _check(load().swense_mlp_load(ctypes.byref(mlp), os.fsencode(path), _stream(stream)))
+
+
 def swense_mlp_pack(params, out_scale, packed, stream=None):
     _check(load().swense_mlp_pack(_ptr(params), out_scale, _ptr(packed), _stream(stream)))
 

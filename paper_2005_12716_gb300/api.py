@@ -229,7 +229,8 @@ def mlp_init(seed=0, device="cuda"):
 
 
 class Mlp:
-    """FP32 parameters + Adam moments + the packed BF16 copy the kernels read."""
+    """FP32 parameters + Adam moments + the packed BF16 copy the kernels read, with the host
+    training state (step, seed, out_scale) of the library's swense_mlp."""
 
     def __init__(self, params, device="cuda", out_scale=1.0):
         self.params = params.to(device).contiguous()
@@ -239,7 +240,14 @@ class Mlp:
         self.step = 0
         self.seed = 0
         self.out_scale = float(out_scale)
-        S.swense_mlp_pack(self.params, self.out_scale, self.packed)
+        if self.out_scale > 0:
+            S.swense_mlp_pack(self.params, self.out_scale, self.packed)
+
+    def c_struct(self):
+        return S.make_mlp(self.params, self.m, self.v, self.packed, self.step, self.seed, self.out_scale)
+
+    def _take(self, c):
+        self.step, self.seed, self.out_scale = int(c.step), int(c.seed), float(c.out_scale)
 
     def set_out_scale(self, out_scale):
         """Output multiplier used at inference (train on targets divided by it)."""
@@ -262,34 +270,23 @@ class Mlp:
         S.swense_mlp_train_step(self.params, self.m, self.v, self.packed, self.step, x, field,
                                 target, batch, batch.shape[0], lr, loss=loss)
 
-    # checkpoint: little-endian, header "SWMLP002", int64 step, uint64 seed, int64 nparam,
-    # float64 out_scale, then params, adam m, adam v as float32
+    def train(self, x, field, target, steps, batch=8192, lr=1e-3, schedule_steps=0, losses=None):
+        """swense_mlp_train: `steps` Adam steps, mini-batches drawn in the library."""
+        c = self.c_struct()
+        S.swense_mlp_train(c, x, field, target, x.shape[0], steps, batch, lr, schedule_steps,
+                           losses=losses)
+        self._take(c)
+
+    # checkpoint: swense_mlp_save / swense_mlp_load (little-endian "SWMLP002" file)
     def save(self, path):
-        with open(path, "wb") as fh:
-            fh.write(b"SWMLP002")
-            fh.write(np.array([self.step], "<i8").tobytes())
-            fh.write(np.array([self.seed], "<u8").tobytes())
-            fh.write(np.array([S.MLP_NPARAM], "<i8").tobytes())
-            fh.write(np.array([self.out_scale], "<f8").tobytes())
-            for t in (self.params, self.m, self.v):
-                fh.write(t.detach().cpu().numpy().astype("<f4").tobytes())
+        S.swense_mlp_save(self.c_struct(), str(path))
 
     @classmethod
     def load(cls, path, device="cuda"):
-        with open(path, "rb") as fh:
-            if fh.read(8) != b"SWMLP002":
-                raise ValueError("not a swense MLP checkpoint")
-            step = int(np.frombuffer(fh.read(8), "<i8")[0])
-            seed = int(np.frombuffer(fh.read(8), "<u8")[0])
-            n = int(np.frombuffer(fh.read(8), "<i8")[0])
-            if n != S.MLP_NPARAM:
-                raise ValueError("parameter count mismatch")
-            out_scale = float(np.frombuffer(fh.read(8), "<f8")[0])
-            arrs = [np.frombuffer(fh.read(4 * n), "<f4").copy() for _ in range(3)]
-        m = cls(torch.from_numpy(arrs[0]), device, out_scale)
-        m.m.copy_(torch.from_numpy(arrs[1]))
-        m.v.copy_(torch.from_numpy(arrs[2]))
-        m.step, m.seed = step, seed
+        m = cls(torch.zeros(S.MLP_NPARAM, dtype=torch.float32), device, out_scale=0.0)
+        c = m.c_struct()
+        S.swense_mlp_load(c, str(path))
+        m._take(c)
         return m
 
 

@@ -188,7 +188,7 @@ __device__ __forceinline__ void warp_fft(float2 (&v)[E], const WarpFftTw<E>& T, 
 namespace swense {
 
 // ------------------------------------------------------------------------------------------------
-// Per-warp Stockham inverse DFT of length N = 32 E (E >= 8), radix-8 passes followed by one
+// Per-warp Stockham inverse DFT of length N = 32 E (8 <= E <= 64), radix-8 passes followed by one
 // radix-4 or radix-2 pass when log2 N is not a multiple of 3 (Stockham autosort: natural order in
 // and out). Butterfly j of a pass with radix R after NS points have been combined reads
 // x[j + r N/R], multiplies by e^{2 pi i (j mod NS) r / (NS R)}, takes the length-R DFT and writes
@@ -329,7 +329,7 @@ __device__ __forceinline__ void stk_pass(float2 (&v)[N / 32], const float2 (&T)[
 template <int N>
 __device__ __forceinline__ void stk_fft(float2 (&v)[N / 32], const float2 (&T)[stk_twn(N)],
                                         const float2* __restrict__ tw, float2* buf, int lane) {
-  static_assert(N >= 256 && N <= 1024, "per-warp Stockham sizes");
+  static_assert(N >= 256 && N <= 2048, "per-warp Stockham sizes");
   stk_pass<N, 0>(v, T, tw, buf, lane);
 }
 

@@ -753,7 +753,7 @@ __global__ void __launch_bounds__(256, N >= 1024 ? 1 : 2) k_col_t(ColArgs a, Lev
 // only Mh / 8 CTAs per level otherwise). The output tile and the warps' exchange buffers share
 // the same shared memory (a barrier between the transforms and the tile writes).
 template <int N>
-__global__ void __launch_bounds__(256, 2) k_col_tf(ColArgs a, Levels L) {
+__global__ void __launch_bounds__(256, N >= 1024 ? 1 : 2) k_col_tf(ColArgs a, Levels L) {
   extern __shared__ float2 sm[];                 // exchange buffers, then tile [N][kColBlock + 1]
   constexpr int E = N / 32, RL = stk_radix(N, stk_npass(N) - 1);
   constexpr int TLD = kColBlock + 1;
@@ -871,7 +871,7 @@ __global__ void __launch_bounds__(256, N >= 1024 ? 1 : 2) k_row_t(RowArgs a) {
 // row r): half the registers, so more warps per SM; each warp writes one float2 half of the
 // nodes' float4 (the halves meet in L2).
 template <int N>
-__global__ void __launch_bounds__(256, N >= 1024 ? 2 : 3) k_row_t2(RowArgs a) {
+__global__ void __launch_bounds__(256, N >= 2048 ? 1 : (N >= 1024 ? 2 : 3)) k_row_t2(RowArgs a) {
   extern __shared__ float2 sm[];                 // warp exchange buffers
   constexpr int E = N / 32, RL = stk_radix(N, stk_npass(N) - 1);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1217,6 +1217,7 @@ int launch_pair_t(const ColArgs& c, const RowArgs& r, const Levels& L, int nl, c
     }
   }
   if (st || which == 1) return st;
+  if (one_per_warp && r.Nxr == 2048) return launch_row_t2<2048>(r, gr2, s);   // 64 elements a lane
   switch (r.Nxr) {                               // rows longer than a warp transform
     case 2048: return launch_row_tb<2048>(r, unsigned(nl), s);
     case 4096: return launch_row_tb<4096>(r, unsigned(nl), s);
@@ -1868,14 +1869,19 @@ extern "C" int swense_autotune_grid(const swense_modes* md, int32_t n_tl, const 
       if (st) return st;
     }
     for (int lpc : {0, 1, 2, 4})
-    for (int rv : {0, 1, 2, 3, 4, 5, 2 + 16, 4 + 16, 5 + 16}) {
+    for (int rv : {0, 1, 2, 3, 4, 5, 2 + 16, 3 + 16, 4 + 16, 5 + 16}) {
       const int rowv = rv & 15, colv = rv >> 4;
       const bool wp = warp_path(p.ny, p.Nxr, p.Nyr), pp = pair_path(p.ny, p.Nxr, p.Nyr);
-      if (lpc > 0 && !wp && !(pp && rowv == 2)) continue;
+      // beyond the warp path, the pair runs with row variant 2 (block rows) or, for 2048-point
+      // rows, 3 (one 64-element-per-lane transform per warp)
+      const bool pair_ok = pp && (rowv == 2 || (rowv == 3 && p.Nxr == 2048));
+      if (lpc > 0 && !wp && !pair_ok) continue;
       if (rowv && (lpc == 0 || p.Nxr < 256)) continue;   // only the Stockham row sizes have variants
       if (rowv >= 2 && !pp) continue;
-      if (!wp && rowv != 2 && lpc > 0) continue;
+      if (colv && !(pp && rowv >= 2)) continue;
+      if (!wp && !pair_ok && lpc > 0) continue;
       if (rowv == 4 && p.Nxr > 1024) continue;
+      if (p.Nxr > 1024 && rowv != 2 && !(rowv == 3 && p.Nxr == 2048)) continue;
       for (size_t mb : {16, 32, 64, 96, 128, 256}) {
         const size_t cb = mb << 20;
         const int chunk = int(std::max<size_t>(1, std::min<size_t>(p.nz, cb / p.per_level)));

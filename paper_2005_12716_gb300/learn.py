@@ -11,6 +11,7 @@ import numpy as np
 import torch
 
 from wavegen import seas as W
+from . import _swense as S
 from . import api
 
 
@@ -69,28 +70,24 @@ def make_dataset(n_seas, points_per_sea, nx, ny, Lx, Ly, z_levels, pad_n=1, t_le
         pts = torch.from_numpy(sample_points(points_per_sea, Lx, Ly, float(z[0]), float(z[-1]), rng)).to(device)
         x, sc, lg, _ = api.mlp_features(grid, t, pts)
         ex = api.direct(modes, t, pts, p_mode="phit")
-        exact = torch.stack([ex["u"], ex["v"], ex["w"], ex["p"]], 1).reshape(-1)
+        tg = torch.empty(4 * points_per_sea, dtype=torch.float32, device=device)
+        fd = torch.empty(4 * points_per_sea, dtype=torch.int32, device=device)
+        S.swense_mlp_targets(ex["u"], ex["v"], ex["w"], ex["p"], lg, sc, points_per_sea, tg, fd)
         xs.append(x)
-        ts.append((exact - lg) / sc)
-        fs.append(torch.arange(4, dtype=torch.int32, device=device).repeat(points_per_sea))
+        ts.append(tg)
+        fs.append(fd)
     return torch.cat(xs), torch.cat(fs), torch.cat(ts)
 
 
 def train(mlp, x, field, target, steps, batch=8192, lr=1e-3, seed=0, log_every=0):
-    """Adam on random mini-batches (seeded) with a cosine-decayed learning rate. The targets
-    are divided by their RMS, which becomes the network's output scale, so the BF16 network
-    works on O(1) values. Returns the logged losses (host floats, in scaled units)."""
-    scale = float(torch.sqrt(torch.mean(target.double() ** 2)).item()) or 1.0
-    mlp.set_out_scale(scale)
-    tgt = (target / scale).contiguous()
-    g = torch.Generator(device="cpu").manual_seed(seed)
-    n = x.shape[0]
-    loss = torch.empty(1, dtype=torch.float32, device=x.device)
-    losses = []
-    for s in range(steps):
-        idx = torch.randint(0, n, (batch,), generator=g, dtype=torch.int64).to(torch.int32).to(x.device)
-        lr_s = lr * 0.5 * (1.0 + np.cos(np.pi * s / max(1, steps)))
-        mlp.train_step(x, field, tgt, idx, lr=lr_s, loss=loss)
-        if log_every and (s % log_every == 0 or s == steps - 1):
-            losses.append(float(loss.item()))
-    return losses
+    """swense_mlp_train from a fresh network: Adam on mini-batches drawn in the library from
+    ``seed``, cosine-decayed learning rate over ``steps``; the library divides the targets by
+    their RMS, which becomes the network's output scale, so the BF16 network works on O(1)
+    values. Returns the losses of every ``log_every``-th step and of the last (scaled units)."""
+    mlp.seed, mlp.out_scale = int(seed), 0.0
+    losses = torch.zeros(max(1, steps), dtype=torch.float32, device=x.device)
+    mlp.train(x, field, target, steps, batch=batch, lr=lr, schedule_steps=steps, losses=losses)
+    if not log_every:
+        return []
+    keep = sorted(set(list(range(0, steps, log_every)) + [steps - 1]))
+    return [float(v) for v in losses[keep].cpu().numpy()]

@@ -135,13 +135,13 @@ def test_every_launch_shape_matches_oracle(api, lpc, rowv, chunk_mb, shape):
     _forced(api, lpc, rowv, chunk_mb, shape)
 
 
-@pytest.mark.parametrize("rowv", [2, 3, 4, 5])
+@pytest.mark.parametrize("rowv", [2, 3, 4, 5, 2 + 16, 4 + 16, 5 + 16])
 @pytest.mark.parametrize("lpc,chunk_mb", [(1, 1), (4, 32)])
 @pytest.mark.parametrize("shape", [(256, 256, 1), (512, 128, 2), (128, 512, 2), (256, 512, 1)])
 def test_transposed_pair_matches_oracle(api, lpc, chunk_mb, shape, rowv):
     """Row variants 2, 3 and 4 (transposed intermediate; both transforms or one per warp in the
-    row pass, or rows staged by bulk asynchronous copies) for 256-, 512- and 1024-point columns
-    and rows."""
+    row pass, or rows staged by bulk asynchronous copies), with either column pass (+16: one
+    modal field per block), for 256-, 512- and 1024-point columns and rows."""
     _forced(api, lpc, rowv, chunk_mb, shape)
 
 
@@ -159,7 +159,8 @@ def _forced(api, lpc, rowv, chunk_mb, shape):
         S.swense_set_grid_tune(nx, ny, pad, len(z), -1, 32 << 20, 0)
 
 
-@pytest.mark.parametrize("shape", [(1024, 256, 2), (1024, 128, 4), (1024, 32, 8), (2048, 64, 1)])
+@pytest.mark.parametrize("shape", [(1024, 256, 2), (1024, 128, 4), (1024, 32, 8), (2048, 64, 1),
+                                   (1024, 512, 2)])
 def test_long_rows_block_transform_sampled(api, shape):
     """Rows of 2048, 4096 and 8192 points (block-wide Stockham row transforms behind the
     transposed column pass, the untuned default for these shapes) at sampled nodes of every

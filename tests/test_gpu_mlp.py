@@ -217,3 +217,52 @@ def test_fused_learned_gather_matches_oracle(env, order):
     ref_eta = ointerp.interp_points(np.stack(nodes), np.stack(etas), sea["Lx"], sea["Ly"], z, tl,
                                     pts, t)["eta"]
     assert rel_linf(got["eta"].cpu().numpy(), ref_eta) <= 1e-5
+
+
+def test_train_save_load_resume_bit_identical(env, tmp_path):
+    """swense_mlp_train (the training loop in the library, mini-batches drawn from the seed and
+    the step), swense_mlp_save and swense_mlp_load through the C ABI: 30 steps, a checkpoint, and
+    20 more steps from the checkpoint give bit for bit the parameters and Adam moments of 50
+    uninterrupted steps; the loss falls."""
+    torch, api, learn = env
+    z = configs.jonswap3d_small()["z_levels"]
+    x, f, tg = learn.make_dataset(4, 2048, 64, 64, 4.0, 4.0, z, seed=61)
+    losses = torch.zeros(50, dtype=torch.float32, device="cuda")
+
+    def fresh():
+        m = api.Mlp(api.mlp_init(62), out_scale=0.0)
+        m.seed = 63
+        return m
+    a = fresh()
+    a.train(x, f, tg, 30, batch=1024, lr=2e-3, schedule_steps=50, losses=losses[:30])
+    assert a.step == 30 and a.out_scale > 0
+    path = tmp_path / "mlp.bin"
+    a.save(path)
+    b = api.Mlp.load(path)
+    assert (b.step, b.seed, b.out_scale) == (a.step, a.seed, a.out_scale)
+    assert torch.equal(b.params, a.params) and torch.equal(b.m, a.m) and torch.equal(b.v, a.v)
+    b.train(x, f, tg, 20, batch=1024, lr=2e-3, schedule_steps=50, losses=losses[30:])
+    c = fresh()
+    c.train(x, f, tg, 50, batch=1024, lr=2e-3, schedule_steps=50)
+    assert c.step == b.step == 50 and c.out_scale == b.out_scale
+    for t1, t2 in ((b.params, c.params), (b.m, c.m), (b.v, c.v), (b.packed, c.packed)):
+        assert torch.equal(t1, t2)
+    lo = losses.cpu().numpy()
+    assert lo[-5:].mean() < 0.8 * lo[:5].mean()
+
+
+def test_targets_are_the_scaled_residuals(env):
+    """swense_mlp_targets: row 4 i + f = (exact_f - lagrange_f) / s_f with field id f."""
+    torch, api, learn = env
+    from paper_2005_12716_gb300 import _swense as S
+    rng = np.random.default_rng(71)
+    n = 5000
+    ex = [torch.from_numpy(rng.standard_normal(n).astype(np.float32)).cuda() for _ in range(4)]
+    lg = torch.from_numpy(rng.standard_normal(4 * n).astype(np.float32)).cuda()
+    sc = torch.from_numpy(rng.uniform(0.5, 2.0, 4 * n).astype(np.float32)).cuda()
+    tg = torch.empty(4 * n, dtype=torch.float32, device="cuda")
+    fd = torch.empty(4 * n, dtype=torch.int32, device="cuda")
+    S.swense_mlp_targets(*ex, lg, sc, n, tg, fd)
+    e = torch.stack(ex, 1).reshape(-1)
+    assert torch.equal(tg, (e - lg) / sc)
+    assert torch.equal(fd.cpu(), torch.arange(4, dtype=torch.int32).repeat(n))
