@@ -159,13 +159,25 @@ def _forced(api, lpc, rowv, chunk_mb, shape):
         S.swense_set_grid_tune(nx, ny, pad, len(z), -1, 32 << 20, 0)
 
 
-@pytest.mark.parametrize("shape", [(1024, 256, 2), (1024, 128, 4), (1024, 32, 8), (2048, 64, 1),
-                                   (1024, 512, 2)])
-def test_long_rows_block_transform_sampled(api, shape):
+@pytest.mark.parametrize("shape,tune", [((1024, 256, 2), None), ((1024, 128, 4), None), ((1024, 32, 8), None),
+                                        ((2048, 64, 1), None), ((1024, 512, 2), None),
+                                        ((1024, 256, 2), 3), ((1024, 512, 2), 3 + 16), ((1024, 512, 2), 2)])
+def test_long_rows_block_transform_sampled(api, shape, tune):
     """Rows of 2048, 4096 and 8192 points (block-wide Stockham row transforms behind the
-    transposed column pass, the untuned default for these shapes) at sampled nodes of every
-    level against the oracle's direct modal sum there."""
+    transposed column pass, the untuned default for these shapes; for 2048-point rows also one
+    64-element-per-lane transform per warp, row variant 3, and either column pass) at sampled
+    nodes of every level against the oracle's direct modal sum there."""
+    from paper_2005_12716_gb300 import _swense as S
     nx, ny, pad = shape
+    if tune is not None:
+        S.swense_set_grid_tune(nx, ny, pad, 6, 2, 8 << 20, tune)
+    try:
+        _long_rows(api, nx, ny, pad)
+    finally:
+        S.swense_set_grid_tune(nx, ny, pad, 6, -1)
+
+
+def _long_rows(api, nx, ny, pad):
     rng = np.random.default_rng(nx + ny + pad + 5)
     Lx, Ly = 8.0, 8.0 * ny / nx
     comps = seas.random_linear_components(nx, ny, Lx, Ly, 12, 0.01, rng)
