@@ -67,6 +67,8 @@ def parse():
                          "points instead of 16 M (small profiling cases)")
     ap.add_argument("--levels", type=int, default=0,
                     help="large mode: number of levels instead of 128 (small profiling case)")
+    ap.add_argument("--near", type=int, default=0,
+                    help="large mode: N near-body points instead of 1 M (small profiling case)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -327,13 +329,22 @@ NCU_TRAFFIC = {
 }
 
 
-DIRECT_KERNEL = "k_direct_split"
-# useful MMA flops of the split-BF16 direct sum per (point, mode) pair: u, v, w, dphi/dt, each the
-# real part of a complex product (2 MACs over the mode's re/im), three BF16 products (hi.hi,
-# hi.lo, lo.hi); eta is summed in FP32 beside the MMAs
+DIRECT_KERNEL = "k_direct_tc"
+# Algorithmic MMA flops of the split-BF16 direct sum (the per-unit figure of the workload's
+# definition): per (point, mode) pair of the full nx x ny spectrum, u, v, w and dphi/dt each the
+# real part of a complex product (2 MACs over the mode's re/im) in three BF16 products (hi.hi,
+# hi.lo, lo.hi): 48 flop
 DIRECT_FLOP_PER_PAIR = 4 * 2 * 2 * 3
 DIRECT_FLOP_NOTE = ("per (point, mode) pair 48 flop: 4 fields x 2 MACs (re/im of the mode) x 2 flop "
-                    "x 3 split products; pairs = near-body points x live modes of the half spectrum")
+                    "x 3 split products; pairs = near-body points x nx x ny modes (full spectrum)")
+
+
+def direct_tc_issued_flop(nx, ny, tiles):
+    """MMA flops k_direct_tc issues for `tiles` tiles of 128 points: per K-chunk of 32 modes and
+    group of 8 mode rows, 3 products of 128 x 208 x 64 (rows padded as the kernel pads them)."""
+    mp = -(-(nx // 2) // 32) * 32
+    rows = (-(-(ny // 2) // 8) * 8 + -(-(ny // 2 - 1) // 8) * 8) if ny > 1 else 8
+    return tiles * (mp // 32) * (rows // 8) * 3 * 2.0 * 128 * 208 * 64
 
 
 def run_ours(args, rank, world, emit=True):
@@ -1216,7 +1227,8 @@ def run_large(args, rank, world):
     from wavegen import configs
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
-    cfg = configs.large_sea(n_levels=args.levels or 128, n_points=args.points or 16_000_000)
+    cfg = configs.large_sea(n_levels=args.levels or 128, n_points=args.points or 16_000_000,
+                            n_near=args.near or 1_000_000)
     sea, z, tl, tq = cfg["sea"], cfg["z_levels"], cfg["t_levels"], cfg["t_query"]
     pts_np, near_np = cfg["points"], cfg["near_points"]
     n, nn = len(pts_np), len(near_np)
@@ -1287,10 +1299,11 @@ def run_large(args, rank, world):
     # the gather: every node of both time levels is in some stencil (16 M uniform points over
     # 268 M nodes; the union of their stencils covers about 98 % of the grid): the whole grid once
     gather_bytes = n_tl * (nz * nx_r * ny_r * 16 + nx_r * ny_r * 4) + n * (12 + 20)
-    live_modes = int((sea["ny"] - 1) * (sea["nx"] // 2))
-    pairs = float(nn) * live_modes
+    pairs = float(nn) * sea["nx"] * sea["ny"]
     d_ms = st_ms["direct_near_body"]
     direct_flop = pairs * DIRECT_FLOP_PER_PAIR
+    tiles, fb_tiles = S.swense_direct_stats()
+    issued = direct_tc_issued_flop(sea["nx"], sea["ny"], tiles - fb_tiles)
     stages_out = {
         "grid": {"ms": st_ms["grid"], "algorithmic_bytes": grid_bytes,
                  "achieved_gbs": grid_bytes / (st_ms["grid"] * 1e-3) / 1e9,
@@ -1301,7 +1314,9 @@ def run_large(args, rank, world):
                    "points_per_s": n / (st_ms["gather"] * 1e-3)},
         "direct_near_body": {"ms": d_ms, "pairs": pairs, "pairs_per_s": pairs / (d_ms * 1e-3),
                              "points_per_s": nn / (d_ms * 1e-3),
-                             "algorithmic_tflops": direct_flop / (d_ms * 1e-3) / 1e12},
+                             "algorithmic_tflops": direct_flop / (d_ms * 1e-3) / 1e12,
+                             "tiles": tiles, "tiles_per_pair_kernel": fb_tiles,
+                             "issued_mma_tflops": issued / (d_ms * 1e-3) / 1e12},
     }
     tens_peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
     dom = max(st_ms, key=st_ms.get)
@@ -1320,6 +1335,7 @@ def run_large(args, rank, world):
                     "frac": ach / hbm, "traffic": None,
                     "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback"}
     stages_out["direct_near_body"]["frac_tensor"] = stages_out["direct_near_body"]["algorithmic_tflops"] / tens_peak
+    stages_out["direct_near_body"]["issued_frac_tensor"] = stages_out["direct_near_body"]["issued_mma_tflops"] / tens_peak
     config = large_config(cfg, n, nn)
     line = {
         "metric": "wave-field points/sec at stated err vs FP64 oracle; % of HBM roofline",

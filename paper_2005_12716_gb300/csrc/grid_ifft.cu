@@ -770,6 +770,26 @@ __global__ void __launch_bounds__(256, N >= 1024 ? 1 : 2) k_col_tf(ColArgs a, Le
   const int nyh = a.ny >> 1;
   const float kx = colok ? float(m) * a.kxs : 0.f;
   const float2* __restrict__ A = q == 3 ? a.A_phit : a.A_phi;
+  // the column's modes of this field, loaded once and kept in registers over the CTA's levels
+  // (zero in the padding and at the Nyquist row)
+  float2 am[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int p = lane + 32 * (e / 8) + (e % 8) * (N / 8);
+    int n = 0;
+    bool live = colok;
+    if (p < nyh) n = p;
+    else if (p > N - nyh) n = p - N;
+    else live = false;
+    am[e] = make_float2(0.f, 0.f);
+    if (live) {
+      am[e] = __ldg(&A[size_t(n >= 0 ? n : a.ny + n) * a.nxh1 + m]);
+      if (a.spline) {
+        const float pf = spline_prefilter(m, a.Nxr, n, a.Nyr);
+        am[e] = make_float2(pf * am[e].x, pf * am[e].y);
+      }
+    }
+  }
   for (int li = 0; li < a.lpc; ++li) {
     const int level = blockIdx.y * a.lpc + li;
     if (level >= a.nlev) break;                  // uniform over the block
@@ -778,26 +798,14 @@ __global__ void __launch_bounds__(256, N >= 1024 ? 1 : 2) k_col_tf(ColArgs a, Le
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int p = lane + 32 * (e / 8) + (e % 8) * (N / 8);
-      int n = 0;
-      bool live = colok;
-      if (p < nyh) n = p;
-      else if (p > N - nyh) n = p - N;
-      else live = false;
       // zero-padded and Nyquist positions carry no mode: their (unused) depth factor is taken
       // at ky = 0, where it cannot overflow
-      const float ky = float(live ? n : 0) * a.kys;
+      const int n = p < nyh ? p : (p > N - nyh ? p - N : 0);
+      const float ky = float(n) * a.kys;
       const float kk = sqrtf(kx * kx + ky * ky);
       float F, S;
       depth_factors(kk, z, a.depth, F, S);
-      float2 am = make_float2(0.f, 0.f);
-      if (live) {
-        am = __ldg(&A[size_t(n >= 0 ? n : a.ny + n) * a.nxh1 + m]);
-        if (a.spline) {
-          const float pf = spline_prefilter(m, a.Nxr, n, a.Nyr);
-          am = make_float2(pf * am.x, pf * am.y);
-        }
-      }
-      v[e] = modal_field(q, kx, ky, kk, F, S, am, am);
+      v[e] = modal_field(q, kx, ky, kk, F, S, am[e], am[e]);
     }
     stk_fft<N>(v, T, a.tw, wbuf, lane);
     __syncthreads();                             // every warp is done with its exchange buffer
