@@ -398,4 +398,75 @@ __device__ __forceinline__ void stkb_fft(float2 (&v)[N / TH], const float2* __re
   stkb_pass<N, TH, 0>(v, tw, buf, t);
 }
 
+// Two block-wide transforms of the same length side by side (buffers buf1, buf2): each pass
+// applies to both before the shared barriers, so the pair takes the barriers of one transform
+// and twice the independent work between them.
+template <int N, int TH, int P>
+__device__ __forceinline__ void stkb_pass2(float2 (&v1)[N / TH], float2 (&v2)[N / TH],
+                                           const float2* __restrict__ tw, float2* buf1, float2* buf2, int t) {
+  constexpr int E = N / TH, R = stk_radix(N, P), NS = stk_ns(N, P), B = E / R;
+  if constexpr (P > 0) {
+    constexpr int step = SWENSE_MAX_FFT / (NS * R);
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const int jm = NS <= TH ? t % NS : t + TH * (b % (NS / TH));
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        const float2 w = __ldg(&tw[jm * r * step]);
+        v1[b * R + r] = cmul(v1[b * R + r], w);
+        v2[b * R + r] = cmul(v2[b * R + r], w);
+      }
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < B; ++b) {
+    if constexpr (R == 8) {
+      stk_dft8(&v1[b * 8]);
+      stk_dft8(&v2[b * 8]);
+    } else if constexpr (R == 4) {
+      stk_dft4(v1[b * 4], v1[b * 4 + 1], v1[b * 4 + 2], v1[b * 4 + 3]);
+      stk_dft4(v2[b * 4], v2[b * 4 + 1], v2[b * 4 + 2], v2[b * 4 + 3]);
+    } else {
+      stk_dft2(&v1[b * 2]);
+      stk_dft2(&v2[b * 2]);
+    }
+  }
+  if constexpr (P + 1 < stk_npass(N)) {
+    const int lst = NS <= TH ? (t / NS) * NS * R + t % NS : t;
+    float2* bst1 = buf1 + stk_pad(lst);
+    float2* bst2 = buf2 + stk_pad(lst);
+#pragma unroll
+    for (int b = 0; b < B; ++b)
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int c = NS <= TH ? TH * b * R + r * NS
+                               : (b / (NS / TH)) * NS * R + TH * (b % (NS / TH)) + r * NS;
+        bst1[c + (c >> 4)] = v1[b * R + r];
+        bst2[c + (c >> 4)] = v2[b * R + r];
+      }
+    __syncthreads();
+    constexpr int R2 = stk_radix(N, P + 1), B2 = E / R2;
+    const float2* bld1 = buf1 + stk_pad(t);
+    const float2* bld2 = buf2 + stk_pad(t);
+#pragma unroll
+    for (int b = 0; b < B2; ++b)
+#pragma unroll
+      for (int r = 0; r < R2; ++r) {
+        const int c = TH * b + r * (N / R2);
+        v1[b * R2 + r] = bld1[c + (c >> 4)];
+        v2[b * R2 + r] = bld2[c + (c >> 4)];
+      }
+    __syncthreads();
+    stkb_pass2<N, TH, P + 1>(v1, v2, tw, buf1, buf2, t);
+  }
+}
+
+template <int N, int TH>
+__device__ __forceinline__ void stkb_fft2(float2 (&v1)[N / TH], float2 (&v2)[N / TH],
+                                          const float2* __restrict__ tw, float2* buf1, float2* buf2, int t) {
+  static_assert(N / TH >= 8 && N <= SWENSE_MAX_FFT && (TH & 15) == 0, "block Stockham sizes");
+  static_assert(N / 8 >= TH, "constant index parts are multiples of the thread count");
+  stkb_pass2<N, TH, 0>(v1, v2, tw, buf1, buf2, t);
+}
+
 }  // namespace swense

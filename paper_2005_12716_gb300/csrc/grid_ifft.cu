@@ -951,8 +951,7 @@ __global__ void __launch_bounds__(256, N >= 8192 ? 1 : 2) k_row_tb(RowArgs a) {
     float2 z1[E], z2[E];
     pack(z1, 0);
     pack(z2, 1);
-    stkb_fft<N, kThreads>(z1, a.tw, sm, t);
-    stkb_fft<N, kThreads>(z2, a.tw, sm + stk_buf(N), t);
+    stkb_fft2<N, kThreads>(z1, z2, a.tw, sm, sm + stk_buf(N), t);
 #pragma unroll
     for (int e = 0; e < E; ++e)
       __stcs(&out[t + kThreads * (e / RL) + (e % RL) * (N / RL)], make_float4(z1[e].x, z1[e].y, z2[e].x, z2[e].y));

@@ -118,6 +118,37 @@ def test_full_size_jonswap_sampled_nodes(api):
         assert np.max(np.abs(ge - ref["eta"])) / float(torch.max(torch.abs(grid.eta[l]))) <= TOL
 
 
+@pytest.mark.parametrize("case", ["jonswap3d", "large_sea"])
+def test_extension_above_surface_top_levels(api, case):
+    """The levels above z = 0 (extension into the air, depth factor e^{|k| z} > 1, evaluated as
+    a compensated FP32 product and exponential) at the bench seas' full sizes: 400 (96) sampled nodes
+    of the top three levels against the oracle's FP64 sum, each field in its own norm over those
+    levels (recorded) and within 1e-5 of the field's maximum."""
+    import torch
+    if case == "jonswap3d":
+        cfg = configs.jonswap3d(mesh_dims=(4, 8, 4))
+    else:
+        cfg = configs.large_sea(n_levels=16, n_points=1, n_near=1)
+    sea, z, tl = cfg["sea"], cfg["z_levels"], cfg["t_levels"][:1]
+    assert z[-1] > 0
+    grid = api.fields_on_grid(api.upload_modes(sea), z, 1, tl)
+    nyr, nxr = grid.nodes.shape[2], grid.nodes.shape[3]
+    rng = np.random.default_rng(17)
+    n = 400 if case == "jonswap3d" else 96
+    kk = len(z) - 1 - rng.integers(0, 3, n)
+    ii, jj = rng.integers(0, nxr, n), rng.integers(0, nyr, n)
+    pts = np.stack([ii * sea["Lx"] / nxr, jj * sea["Ly"] / nyr, np.asarray(z, np.float64)[kk]], 1)
+    ref = modal.fields_at_points(modal.propagate(sea, tl[0]), pts, chunk=8)
+    got = grid.nodes[0].cpu().numpy()[kk, jj, ii].astype(np.float64)
+    top = grid.nodes[0, -3:]
+    vmax = float(torch.max(torch.linalg.vector_norm(top[..., :3], dim=-1)).item())
+    for q, key in enumerate(("u", "v", "w", "phit")):
+        own = float(torch.max(torch.abs(top[..., q])).item())
+        d = float(np.max(np.abs(got[:, q] - ref[key])))
+        note_field(key + "@top", d / own, d / (vmax if q < 3 else own), own)
+        assert d / own <= TOL, (key, d / own)
+
+
 def test_calm_water_grid_is_zero(api):
     sea = seas.linear_sea(32, 8, 4.0, 2.0, [])
     z = np.array([-1, -0.5, 0, 0.1], np.float32)
