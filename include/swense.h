@@ -301,11 +301,17 @@ typedef struct swense_instance {
 
 /*
  * swense_batch_run — many independent sea states of uneven sizes in one call (no counterpart
- * in the paper): for each instance, swense_fields_on_grid then swense_interp (or
- * swense_interp_permuted), all enqueued in order on `stream`, so that one call can be
- * captured as a single CUDA graph and replayed as one launch. The first call (outside any
- * capture) sizes the shared workspace for the largest instance. Errors: those of the
- * per-instance calls (the first failing instance stops the batch).
+ * in the paper): every instance's grid (as swense_fields_on_grid, with its tuned launch shape)
+ * and then every instance's gather (as swense_interp, or swense_interp_permuted when perm is
+ * set). The reconstructions run concurrently on four library streams forked from `stream`
+ * (largest instance first, round robin, each stream in its own part of the workspace); after
+ * they are joined back, one launch plans the point chunks of all instances and one persistent
+ * launch gathers them, its CTAs taking chunks from a device queue. Fork and join are events,
+ * so one call can be captured as a single CUDA graph and replayed as one launch. The first call
+ * with a given set of instances must be made outside any capture: it sizes the workspace and
+ * uploads the gather tables (arguments and level tables of every instance; a captured call
+ * whose tables differ from the last uploaded ones fails with SWENSE_ERR_ARG). Power-of-two
+ * padding factors only. Errors: those of the per-instance calls, UNSUPPORTED, OOM, CUDA.
  */
 int swense_batch_run(const swense_instance* instances, int32_t n_instances, int32_t p_mode,
                      double rho, double g, void* stream);

@@ -385,5 +385,21 @@ class Batch:
     def run(self, rho=1000.0, g=9.81, stream=None):
         S.swense_batch_run(self.arr, self.p_mode, rho, g, stream)
 
+    def run_individual(self, rho=1000.0, g=9.81, stream=None):
+        """The same work as one public call per instance and stage, in order on one stream
+        (swense_fields_on_grid, then swense_interp or swense_interp_permuted)."""
+        for c, it in zip(self.arr, self.items):
+            S.swense_fields_on_grid(c.modes, c.n_tl, it["tl"], it["desc"], it["grid"].nodes,
+                                    it["grid"].eta, stream)
+            gr = it["grid"].c_struct()
+            o = it["out"]
+            if it["perm"] is not None:
+                S.swense_interp_permuted(gr, c.t, it["pts"], it["perm"], c.np, o["eta"], o["u"],
+                                         o["v"], o["w"], o["p"], self.p_mode, rho, g,
+                                         stream=stream)
+            else:
+                S.swense_interp(gr, c.t, it["pts"], c.np, o["eta"], o["u"], o["v"], o["w"], o["p"],
+                                self.p_mode, rho, g, stream=stream)
+
     def points(self):
         return sum(int(it["pts"].shape[0]) for it in self.items)

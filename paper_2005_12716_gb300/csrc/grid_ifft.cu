@@ -1848,6 +1848,42 @@ extern "C" int swense_fields_on_grid(const swense_modes* md, int32_t n_tl, const
                      colv);
 }
 
+namespace swense {
+
+// Scratch one swense_fields_on_grid call needs with its current launch shape, and the same call
+// with that scratch supplied (no library stream: the eta transform and, for variant 5, the row
+// passes stay on `stream`), for callers that run several reconstructions concurrently, each in
+// its own part of the workspace (swense_batch_run).
+int grid_scratch(const swense_modes* md, int32_t n_tl, const double* t, const swense_grid_desc* desc,
+                 float* nodes, float* eta, size_t* bytes) {
+  GridPlan p;
+  int st = plan_grid(md, n_tl, t, desc, nodes, eta, &p);
+  if (st) return st;
+  if (!is_pow2(p.pad)) return fail(SWENSE_ERR_UNSUPPORTED, "batched grids take power-of-two padding factors");
+  const Tune tn = tuned(p.nx, p.ny, p.pad, p.nz);
+  const int chunk = p.ny > 1 ? int(std::max<size_t>(1, std::min<size_t>(p.nz, tn.chunk_bytes / p.per_level))) : 0;
+  *bytes = scratch_bytes(p, chunk, 1);
+  return SWENSE_OK;
+}
+
+int grid_with_scratch(const swense_modes* md, int32_t n_tl, const double* t, const swense_grid_desc* desc,
+                      float* nodes, float* eta, void* ws, cudaStream_t stream) {
+  GridPlan p;
+  int st = plan_grid(md, n_tl, t, desc, nodes, eta, &p);
+  if (st) return st;
+  if (!is_pow2(p.pad)) return fail(SWENSE_ERR_UNSUPPORTED, "batched grids take power-of-two padding factors");
+  const Tune tn = tuned(p.nx, p.ny, p.pad, p.nz);
+  const int chunk = p.ny > 1 ? int(std::max<size_t>(1, std::min<size_t>(p.nz, tn.chunk_bytes / p.per_level))) : 0;
+  const bool pair = pair_path(p.ny, p.Nxr, p.Nyr);
+  const int lpc = tn.lpc >= 0 ? tn.lpc : (pair ? 4 : ((p.Nxr <= 512 && p.Nyr <= 512) ? kColLevels : 0));
+  int rowv = tn.lpc >= 0 ? tn.rowv : (pair ? 2 : 0);
+  if (rowv == 5) rowv = 2;
+  const int colv = tn.lpc >= 0 ? tn.colv : default_colv(p);
+  return launch_grid(p, md, t, nodes, eta, ws, chunk, stream, lpc, rowv, 0, 0, colv);
+}
+
+}  // namespace swense
+
 extern "C" int swense_autotune_grid(const swense_modes* md, int32_t n_tl, const double* t,
                                     const swense_grid_desc* desc, float* nodes, float* eta,
                                     int32_t* lpc_out, int64_t* chunk_bytes_out, int32_t* row_variant_out,

@@ -43,6 +43,28 @@ int direct_async_flag(bool reset, int* was_set);
 // `tile_pts` sorted points that tile_bad marks.
 int direct_tc(const swense_modes* md, double t, const float* pts, int64_t np, float* eta, float* u,
               float* v, float* w, float* p, int32_t p_mode, double rho, double grav, cudaStream_t stream);
+// Grid reconstruction with caller-supplied scratch (grid_ifft.cu), for concurrent batches.
+int grid_scratch(const swense_modes* md, int32_t n_tl, const double* t, const swense_grid_desc* desc,
+                 float* nodes, float* eta, size_t* bytes);
+int grid_with_scratch(const swense_modes* md, int32_t n_tl, const double* t, const swense_grid_desc* desc,
+                      float* nodes, float* eta, void* ws, cudaStream_t stream);
+
+// One gather of a batch (interp.cu): the grid and the points of one instance.
+struct GatherItem {
+  swense_grid grid;
+  double t;
+  const float* pts;
+  const int32_t* perm;
+  int64_t np;
+  float *eta, *u, *v, *w, *p;
+};
+// Scratch (plan and queue counter) of interp_batch for these items, and the batch itself: every
+// item's point chunks planned by one launch and gathered by one persistent launch whose CTAs
+// take chunks from a device queue. `ws` holds interp_batch_bytes(items) bytes.
+int interp_batch_bytes(const GatherItem* items, int n, size_t* bytes);
+int interp_batch(const GatherItem* items, int n, int32_t p_mode, double rho, double grav, void* ws,
+                 cudaStream_t stream);
+
 size_t split_table_bytes(const swense_modes* md);
 int direct_split_sorted(const swense_modes* md, double t, const float* srt, const int32_t* perm,
                         const uint8_t* tile_bad, int tile_pts, int64_t np, float* eta, float* u, float* v,

@@ -11,6 +11,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
+#include <vector>
 
 #include "internal.cuh"
 #include "mlp.cuh"
@@ -451,15 +453,12 @@ __host__ __device__ __forceinline__ int64_t plan_blocks(int64_t np) {
   return ((np + BOX_PTS - 1) / BOX_PTS + PLAN_WARPS - 1) / PLAN_WARPS;
 }
 
+// Plan of chunk `chunk` of the points of `a`, by one warp (no block barrier).
 template <bool P2>
-__global__ void __launch_bounds__(BOX_THREADS) k_interp_plan(InterpArgs a, Levels L, int4* __restrict__ plan) {
-  __shared__ LevelTables zs;
-  fill_level_tables(zs, L, a.nz);
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t chunk = int64_t(blockIdx.x) * PLAN_WARPS + warp;
+__device__ __forceinline__ void plan_chunk(const InterpArgs& a, const LevelTables& zs, int64_t chunk,
+                                           int4* __restrict__ plan, int lane) {
   const int64_t p0 = chunk * BOX_PTS;
-  if (p0 >= a.np) return;                           // no barrier below
+  if (p0 >= a.np) return;
   // every lane derives the chunk's reference cell (its first point's) itself: broadcast loads
   int refx, refy, refj0;
   const float refz = __ldg(&a.pts[3 * p0 + 2]);
@@ -540,14 +539,20 @@ __global__ void __launch_bounds__(BOX_THREADS) k_interp_plan(InterpArgs a, Level
 }
 
 template <bool P2>
-__global__ void __launch_bounds__(BOX_THREADS, 3) k_interp_box(InterpArgs a, Levels L,
-                                                                const int4* __restrict__ plan) {
-  extern __shared__ float4 sbox[];
-  float* seta = reinterpret_cast<float*>(sbox + BOX_NODES);
+__global__ void __launch_bounds__(BOX_THREADS) k_interp_plan(InterpArgs a, Levels L, int4* __restrict__ plan) {
   __shared__ LevelTables zs;
   fill_level_tables(zs, L, a.nz);
-  const int64_t p0 = int64_t(blockIdx.x) * BOX_PTS;
-  const int4 pl = plan[blockIdx.x];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  plan_chunk<P2>(a, zs, int64_t(blockIdx.x) * PLAN_WARPS + warp, plan, lane);
+}
+
+// Gather of chunk `chunk` of the points of `a` with its plan `pl`, by the whole CTA; the level
+// tables zs are complete after the first barrier inside.
+template <bool P2>
+__device__ __forceinline__ void box_chunk(const InterpArgs& a, const LevelTables& zs, int64_t chunk,
+                                          const int4 pl, float4* sbox, float* seta) {
+  const int64_t p0 = chunk * BOX_PTS;
   // the first point's coordinates are in flight during the box load; each later point's while
   // the previous one is processed
   float nx_ = 0.f, ny_ = 0.f, nz_ = 0.f;
@@ -691,6 +696,95 @@ __global__ void __launch_bounds__(BOX_THREADS, 3) k_interp_box(InterpArgs a, Lev
       acc_eta = fmaf(c.wy[b], re, acc_eta);
     }
     store_point(a, i, make_float4(lo2(uv), hi2(uv), lo2(wt), hi2(wt)), acc_eta, pz, c.inside);
+  }
+}
+
+template <bool P2>
+__global__ void __launch_bounds__(BOX_THREADS, 3) k_interp_box(InterpArgs a, Levels L,
+                                                                const int4* __restrict__ plan) {
+  extern __shared__ float4 sbox[];
+  float* seta = reinterpret_cast<float*>(sbox + BOX_NODES);
+  __shared__ LevelTables zs;
+  fill_level_tables(zs, L, a.nz);
+  box_chunk<P2>(a, zs, blockIdx.x, plan[blockIdx.x], sbox, seta);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Batched gather (many instances, swense_batch_run): the point chunks of every instance form
+// one list. One launch plans them all (a warp per chunk, the warp's own copy of its instance's
+// arguments and level tables), then one persistent launch gathers them: each CTA takes the next
+// chunk from a device counter and reloads the instance's arguments and level tables only when
+// the instance changes (chunks are listed instance by instance, so rarely).
+struct BatchInst {
+  InterpArgs a;
+  Levels L;
+};
+
+__device__ __forceinline__ int batch_instance(const int64_t* chunk0, int n, int64_t c) {
+  int lo = 0, hi = n - 1;                           // last instance whose first chunk <= c
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (chunk0[mid] <= c) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ void copy_words(void* dst, const void* src, int bytes, int t, int nt) {
+  const int* s = static_cast<const int*>(src);
+  int* d = static_cast<int*>(dst);
+  for (int i = t; i < bytes / 4; i += nt) d[i] = __ldg(&s[i]);
+}
+
+__global__ void __launch_bounds__(BOX_THREADS) k_interp_plan_batch(const BatchInst* __restrict__ inst,
+                                                                   const int64_t* __restrict__ chunk0, int n,
+                                                                   int4* __restrict__ plan) {
+  extern __shared__ unsigned char smb[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  InterpArgs* sa = reinterpret_cast<InterpArgs*>(smb) + warp;
+  LevelTables* zs = reinterpret_cast<LevelTables*>(smb + PLAN_WARPS * sizeof(InterpArgs)) + warp;
+  const int64_t c = int64_t(blockIdx.x) * PLAN_WARPS + warp;
+  if (c >= chunk0[n]) return;                       // no block barrier in this kernel
+  const int i = batch_instance(chunk0, n, c);
+  copy_words(sa, &inst[i].a, int(sizeof(InterpArgs)), lane, 32);
+  const Levels& L = inst[i].L;
+  const int nz = inst[i].a.nz;
+  if (lane == 0) {
+    zs->z0 = L.z0;
+    zs->inv_h = L.inv_h;
+  }
+  for (int k = lane; k < ZLUT / 4; k += 32) reinterpret_cast<unsigned*>(zs->lut)[k] = L.lut4[k];
+  for (int k = lane; k < nz; k += 32) zs->z[k] = L.z[k];
+  for (int j = lane; j <= nz - 4; j += 32) zs->inv[j] = L.inv[j];
+  __syncwarp();
+  plan_chunk<true>(*sa, *zs, c - chunk0[i], plan + chunk0[i], lane);
+}
+
+__global__ void __launch_bounds__(BOX_THREADS, 3) k_interp_box_batch(const BatchInst* __restrict__ inst,
+                                                                      const int64_t* __restrict__ chunk0, int n,
+                                                                      const int4* __restrict__ plan,
+                                                                      unsigned* __restrict__ counter) {
+  extern __shared__ float4 sbox[];
+  float* seta = reinterpret_cast<float*>(sbox + BOX_NODES);
+  __shared__ LevelTables zs;
+  __shared__ InterpArgs sa;
+  __shared__ int64_t s_item;
+  const int64_t total = chunk0[n];
+  int cur = -1;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = int64_t(atomicAdd(counter, 1u));
+    __syncthreads();
+    const int64_t c = s_item;
+    if (c >= total) break;                          // uniform over the CTA
+    const int i = batch_instance(chunk0, n, c);
+    if (i != cur) {
+      copy_words(&sa, &inst[i].a, int(sizeof(InterpArgs)), threadIdx.x, blockDim.x);
+      fill_level_tables(zs, inst[i].L, inst[i].a.nz);
+      cur = i;
+    }
+    __syncthreads();                                // arguments and tables in place
+    box_chunk<true>(sa, zs, c - chunk0[i], plan[c], sbox, seta);
+    __syncthreads();                                // shared memory free for the next chunk
   }
 }
 
@@ -1330,3 +1424,118 @@ extern "C" int swense_interp_permuted(const swense_grid* g, double t, const floa
   return interp_impl(g, t, pts_sorted, perm, np, eta, u, v, w, p, p_mode, rho, grav,
                      n_out_of_range, static_cast<cudaStream_t>(stream));
 }
+
+namespace swense {
+namespace {
+
+// Per device: the batch tables in device memory (instances' arguments and level tables, chunk
+// offsets) and their host copy. Rewritten (synchronously, so never during a stream capture)
+// only when a batch's tables differ from the last ones; a captured batch therefore replays the
+// tables of the uncaptured call that preceded it.
+struct BatchTables {
+  void* dev = nullptr;
+  size_t cap = 0;
+  std::vector<unsigned char> host;
+};
+std::mutex g_batch_mutex;
+BatchTables g_batch[64];
+
+int batch_tables(const GatherItem* items, int n, int32_t p_mode, double rho, double grav, cudaStream_t stream,
+                 const BatchInst** d_inst, const int64_t** d_chunk0, int64_t* nchunks) {
+  std::vector<unsigned char> h(size_t(n) * sizeof(BatchInst) + size_t(n + 1) * sizeof(int64_t));
+  BatchInst* bi = reinterpret_cast<BatchInst*>(h.data());
+  int64_t* c0 = reinterpret_cast<int64_t*>(h.data() + size_t(n) * sizeof(BatchInst));
+  c0[0] = 0;
+  for (int k = 0; k < n; ++k) {
+    const GatherItem& it = items[k];
+    InterpArgs a;
+    Levels lev;
+    int st = prepare_interp(&it.grid, it.t, it.pts, it.np, p_mode, rho, grav, &a, &lev);
+    if (st) return st;
+    if (!a.p2) return fail(SWENSE_ERR_UNSUPPORTED, "batched gathers take power-of-two node counts");
+    a.o_eta = it.eta;
+    a.o_u = it.u;
+    a.o_v = it.v;
+    a.o_w = it.w;
+    a.o_p = it.p;
+    a.perm = it.perm;
+    a.n_oor = nullptr;
+    std::memcpy(&bi[k].a, &a, sizeof(InterpArgs));
+    std::memcpy(&bi[k].L, &lev, sizeof(Levels));
+    c0[k + 1] = c0[k] + (it.np + BOX_PTS - 1) / BOX_PTS;
+  }
+  int dev = 0;
+  SWENSE_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(SWENSE_ERR_UNSUPPORTED, "device index too large");
+  std::lock_guard<std::mutex> lock(g_batch_mutex);
+  BatchTables& T = g_batch[dev];
+  if (T.host != h) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    SWENSE_CUDA_TRY(cudaStreamIsCapturing(stream, &cap));
+    if (cap != cudaStreamCaptureStatusNone)
+      return fail(SWENSE_ERR_ARG, "a captured swense_batch_run must follow an uncaptured call with the "
+                                  "same instances (its tables are uploaded outside the capture)");
+    SWENSE_CUDA_TRY(cudaStreamSynchronize(stream));
+    if (h.size() > T.cap) {
+      if (T.dev) SWENSE_CUDA_TRY(cudaFree(T.dev));
+      T.dev = nullptr;
+      T.cap = 0;
+      cudaError_t e = cudaMalloc(&T.dev, h.size());
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SWENSE_ERR_OOM, "cudaMalloc of the batch tables failed");
+      }
+      T.cap = h.size();
+    }
+    SWENSE_CUDA_TRY(cudaMemcpy(T.dev, h.data(), h.size(), cudaMemcpyHostToDevice));
+    T.host.swap(h);
+  }
+  *d_inst = static_cast<const BatchInst*>(T.dev);
+  *d_chunk0 = reinterpret_cast<const int64_t*>(static_cast<const char*>(T.dev) + size_t(n) * sizeof(BatchInst));
+  *nchunks = reinterpret_cast<const int64_t*>(T.host.data() + size_t(n) * sizeof(BatchInst))[n];
+  return SWENSE_OK;
+}
+
+}  // namespace
+
+int interp_batch_bytes(const GatherItem* items, int n, size_t* bytes) {
+  int64_t chunks = 0;
+  for (int k = 0; k < n; ++k) chunks += (items[k].np + BOX_PTS - 1) / BOX_PTS;
+  *bytes = 256 + size_t(chunks) * sizeof(int4);
+  return SWENSE_OK;
+}
+
+int interp_batch(const GatherItem* items, int n, int32_t p_mode, double rho, double grav, void* ws,
+                 cudaStream_t stream) {
+  if (n <= 0) return SWENSE_OK;
+  const BatchInst* d_inst = nullptr;
+  const int64_t* d_chunk0 = nullptr;
+  int64_t nchunks = 0;
+  int st = batch_tables(items, n, p_mode, rho, grav, stream, &d_inst, &d_chunk0, &nchunks);
+  if (st) return st;
+  if (nchunks == 0) return SWENSE_OK;
+  if (nchunks >= (int64_t(1) << 31)) return fail(SWENSE_ERR_SIZE, "too many point chunks in one batch");
+  unsigned* counter = static_cast<unsigned*>(ws);
+  int4* plan = reinterpret_cast<int4*>(static_cast<char*>(ws) + 256);
+  const size_t plan_smem = size_t(PLAN_WARPS) * (sizeof(InterpArgs) + sizeof(LevelTables));
+  SWENSE_CUDA_TRY(cudaFuncSetAttribute((const void*)k_interp_plan_batch,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, int(plan_smem)));
+  k_interp_plan_batch<<<unsigned((nchunks + PLAN_WARPS - 1) / PLAN_WARPS), BOX_THREADS, plan_smem, stream>>>(
+      d_inst, d_chunk0, n, plan);
+  SWENSE_CUDA_TRY(cudaGetLastError());
+  SWENSE_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned), stream));
+  SWENSE_CUDA_TRY(cudaFuncSetAttribute((const void*)k_interp_box_batch,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, int(BOX_SMEM)));
+  int dev = 0, sms = 0, per_sm = 0;
+  SWENSE_CUDA_TRY(cudaGetDevice(&dev));
+  SWENSE_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  SWENSE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_interp_box_batch, BOX_THREADS,
+                                                                BOX_SMEM));
+  const int64_t ctas = std::min<int64_t>(nchunks, int64_t(std::max(1, sms * std::max(1, per_sm))));
+  k_interp_box_batch<<<unsigned(ctas), BOX_THREADS, BOX_SMEM, stream>>>(d_inst, d_chunk0, n, plan, counter);
+  SWENSE_CUDA_TRY(cudaGetLastError());
+  count_launches(2);
+  return SWENSE_OK;
+}
+
+}  // namespace swense
