@@ -1435,13 +1435,43 @@ namespace {
 struct BatchTables {
   void* dev = nullptr;
   size_t cap = 0;
-  std::vector<unsigned char> host;
+  std::vector<double> key;          // the inputs the tables were built from
+  int64_t nchunks = 0;
 };
+
+// Everything the batch tables depend on, field by field (no struct padding).
+std::vector<double> batch_key(const GatherItem* items, int n, int32_t p_mode, double rho, double grav) {
+  std::vector<double> k{double(n), double(p_mode), rho, grav};
+  auto ptr = [&](const void* q) { k.push_back(double(reinterpret_cast<uintptr_t>(q))); };
+  for (int i = 0; i < n; ++i) {
+    const GatherItem& it = items[i];
+    const swense_grid& g = it.grid;
+    ptr(g.nodes); ptr(g.eta); ptr(it.pts); ptr(it.perm);
+    ptr(it.eta); ptr(it.u); ptr(it.v); ptr(it.w); ptr(it.p);
+    k.insert(k.end(), {double(it.np), it.t, double(g.nx_r), double(g.ny_r), double(g.nz), double(g.n_tl),
+                       g.Lx, g.Ly, double(g.scheme)});
+    for (int l = 0; l < g.nz && g.z_levels; ++l) k.push_back(double(g.z_levels[l]));
+    for (int l = 0; l < g.n_tl && g.t_levels; ++l) k.push_back(g.t_levels[l]);
+  }
+  return k;
+}
 std::mutex g_batch_mutex;
 BatchTables g_batch[64];
 
 int batch_tables(const GatherItem* items, int n, int32_t p_mode, double rho, double grav, cudaStream_t stream,
                  const BatchInst** d_inst, const int64_t** d_chunk0, int64_t* nchunks) {
+  int dev = 0;
+  SWENSE_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(SWENSE_ERR_UNSUPPORTED, "device index too large");
+  std::vector<double> key = batch_key(items, n, p_mode, rho, grav);
+  std::lock_guard<std::mutex> lock(g_batch_mutex);
+  BatchTables& T = g_batch[dev];
+  if (T.dev && T.key == key) {                      // the same batch as last time: tables in place
+    *d_inst = static_cast<const BatchInst*>(T.dev);
+    *d_chunk0 = reinterpret_cast<const int64_t*>(static_cast<const char*>(T.dev) + size_t(n) * sizeof(BatchInst));
+    *nchunks = T.nchunks;
+    return SWENSE_OK;
+  }
   std::vector<unsigned char> h(size_t(n) * sizeof(BatchInst) + size_t(n + 1) * sizeof(int64_t));
   BatchInst* bi = reinterpret_cast<BatchInst*>(h.data());
   int64_t* c0 = reinterpret_cast<int64_t*>(h.data() + size_t(n) * sizeof(BatchInst));
@@ -1464,12 +1494,7 @@ int batch_tables(const GatherItem* items, int n, int32_t p_mode, double rho, dou
     std::memcpy(&bi[k].L, &lev, sizeof(Levels));
     c0[k + 1] = c0[k] + (it.np + BOX_PTS - 1) / BOX_PTS;
   }
-  int dev = 0;
-  SWENSE_CUDA_TRY(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 64) return fail(SWENSE_ERR_UNSUPPORTED, "device index too large");
-  std::lock_guard<std::mutex> lock(g_batch_mutex);
-  BatchTables& T = g_batch[dev];
-  if (T.host != h) {
+  {
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     SWENSE_CUDA_TRY(cudaStreamIsCapturing(stream, &cap));
     if (cap != cudaStreamCaptureStatusNone)
@@ -1488,11 +1513,12 @@ int batch_tables(const GatherItem* items, int n, int32_t p_mode, double rho, dou
       T.cap = h.size();
     }
     SWENSE_CUDA_TRY(cudaMemcpy(T.dev, h.data(), h.size(), cudaMemcpyHostToDevice));
-    T.host.swap(h);
+    T.key.swap(key);
+    T.nchunks = c0[n];
   }
   *d_inst = static_cast<const BatchInst*>(T.dev);
   *d_chunk0 = reinterpret_cast<const int64_t*>(static_cast<const char*>(T.dev) + size_t(n) * sizeof(BatchInst));
-  *nchunks = reinterpret_cast<const int64_t*>(T.host.data() + size_t(n) * sizeof(BatchInst))[n];
+  *nchunks = T.nchunks;
   return SWENSE_OK;
 }
 
