@@ -341,10 +341,10 @@ DIRECT_FLOP_NOTE = ("per (point, mode) pair 48 flop: 4 fields x 2 MACs (re/im of
 
 def direct_tc_issued_flop(nx, ny, tiles):
     """MMA flops k_direct_tc issues for `tiles` tiles of 128 points: per K-chunk of 32 modes and
-    group of 8 mode rows, 3 products of 128 x 208 x 64 (rows padded as the kernel pads them)."""
+    group of 8 mode-row pairs (n, -n), 3 products of 128 x 208 x 64 (padded as the kernel pads)."""
     mp = -(-(nx // 2) // 32) * 32
-    rows = (-(-(ny // 2) // 8) * 8 + -(-(ny // 2 - 1) // 8) * 8) if ny > 1 else 8
-    return tiles * (mp // 32) * (rows // 8) * 3 * 2.0 * 128 * 208 * 64
+    pairs = -(-(ny // 2) // 8) * 8 if ny > 1 else 8
+    return tiles * (mp // 32) * (pairs // 8) * 3 * 2.0 * 128 * 208 * 64
 
 
 def run_ours(args, rank, world, emit=True):

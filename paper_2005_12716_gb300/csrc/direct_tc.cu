@@ -14,10 +14,13 @@
 //      kappa = max|k| max|dz| is bounded (kKappaMax) so the dropped third-order term stays below
 //      2e-6 relative, under the split products' own rounding;
 //   3. for each row n of modes and each field c and order j, T_{c,j,n}(p) = sum_m X_m(p)
-//      C_{c,j}[m,n] with C = W_c |k|^j / j! (F0 or S0): a (points x 2 m) by (2 m x columns)
-//      real GEMM per K-chunk of 32 modes and group of 8 rows (26 columns per row: Re and Im of
-//      u, v, w, dphi/dt at orders 0..2, and eta);
-//   4. F_c(p) = sum_j dz^j Re sum_n Y_n(p) T_{c,j,n}(p): the epilogue of every group.
+//      C_{c,j}[m,n] with C = W_c |k|^j / j! (F0 or S0); rows n and -n share X_m and |k|, and
+//      with Y_{-n} = conj(Y_n) their two terms add up to Re(Y_n (T_n + conj(T_{-n}))), so the
+//      pair needs only Re(T_n + T_{-n}) and Im(T_n - T_{-n}): a (points x 2 m) by (2 m x
+//      columns) real GEMM per K-chunk of 32 modes and group of 8 row pairs (26 columns per pair:
+//      those two for u, v, w, dphi/dt at orders 0..2, and eta);
+//   4. F_c(p) = sum_j dz^j sum_{n >= 0} Re(Y_n(p) (T_{c,j,n} + conj T_{c,j,-n})(p)): the
+//      epilogue of every group.
 // The GEMM runs as split BF16 (A = hi + lo, B = hi + lo, three products hi.hi + hi.lo + lo.hi
 // accumulated in FP32 in tensor memory). A (the tile's X_m, 128 points x 64) lives in tensor
 // memory, written by the epilogue warps once per K-chunk; B is generated per group by eight
@@ -38,13 +41,13 @@ namespace swense {
 namespace {
 
 constexpr int kTcM = 128;                             // points per tile (MMA M)
-constexpr int kTcRows = 8;                            // mode rows n per group
+constexpr int kTcRows = 8;                            // mode row pairs (n, -n) per group
 constexpr int kTcTerms = 3;                           // Taylor orders in dz: 0, 1, 2
 constexpr int kTcCj = 4 * kTcTerms + 1;               // 13 complex outputs per row
 constexpr int kTcN = kTcRows * 2 * kTcCj;             // 208 MMA columns
 constexpr int kTcModes = 32;                          // modes m per K-chunk
 constexpr int kTcK = 2 * kTcModes;                    // 64 K (re, im per mode)
-// B layout: column nc = col * 8 + row (col = 2 cj + {0: Re T, 1: Im T}); core matrices of
+// B layout: column nc = col * 8 + pair (col = 2 cj + {0: Re(T_n + T_-n), 1: Im(T_n - T_-n)}); core matrices of
 // 8 columns x 8 K; k-blocks of 8 K are kTcLBO bytes apart (26 core matrices + 16 bytes, so that
 // the 32 lanes of a producer warp, one mode each, hit 32 different banks)
 constexpr int kTcSBO = 128;
@@ -67,8 +70,9 @@ static_assert(kColD1 + kTcN <= kTmemCols && kColD0 + kTcN <= kColD1, "tensor-mem
 __device__ int g_direct_timeout;
 
 struct TcArgs {
-  const float4* tab;        // [rows_p][mp] x 2: (W_phi, W_phit), (W_eta, |k|, 1/(1+e^{-2kh}))
-  int rows_p, mp, ny, npos;
+  const float4* tab;        // [rows_p][mp] x 4: row n then row -n, each (W_phi, W_phit),
+                            // (W_eta, |k|, 1/(1+e^{-2kh}))
+  int rows_p, mp, ny;
   const float* spts;        // points sorted by z, [np][3]
   const int32_t* perm;      // sorted position -> caller's index
   int64_t np;
@@ -80,14 +84,9 @@ struct TcArgs {
   uint8_t* tile_bad;        // [ntiles]: 1 = left to the per-pair kernel
 };
 
-// Table rows: n = 0 .. ny/2 - 1 in rows 0 .. npos - 1, then n = -(ny/2 - 1) .. -1 from row npos
-// (npos = ny/2 rounded up to a multiple of 8; rows past each half's end are zero modes), so
-// that n rises by one from row to row inside every group of 8 rows. The Nyquist row is not in
-// the table. 2-D seas (ny = 1): row 0 holds n = 0.
-__host__ __device__ __forceinline__ int row_n(int tr, int ny, int npos) {
-  if (ny <= 1) return tr;
-  return tr < npos ? tr : tr - npos - (ny / 2 - 1);
-}
+// Table row q holds the mode rows n = q and n = -q (q = 0 .. ny/2 - 1; row -0 and the rows past
+// ny/2 - 1 are zero modes; the Nyquist row is not in the table), rows padded to a multiple of 8.
+// 2-D seas (ny = 1): row 0 holds n = 0.
 
 // e^{k z} with the product k z carried as hi + lo (compensated), as for the grid's depth factors.
 __device__ __forceinline__ float exp_kz(float k, float z) {
@@ -228,7 +227,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_direct_tc(TcArgs a) {
       // Y_n(p) of the group's eight rows (consecutive n): exact at the first, then seven steps
       float yr[kTcRows], yi[kTcRows];
       {
-        const unsigned ph = unsigned(row_n(g * kTcRows, a.ny, a.npos)) * Y;
+        const unsigned ph = unsigned(g * kTcRows) * Y;
         sincospif(2.f * (float(int(ph)) * 2.3283064365386963e-10f), &yi[0], &yr[0]);
       }
 #pragma unroll
@@ -322,44 +321,46 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_direct_tc(TcArgs a) {
     for (int gi = 0; gi < ngi; ++gi) {
       const int kc = gi / ng, g = gi % ng, s = gi & 1;
       if (gi >= kTcStages && !warp_wait(&sh.b_empty[s], unsigned((gi >> 1) - 1) & 1u, abort_flag)) break;
-      const int tr = g * kTcRows + pw;
+      const int tr = g * kTcRows + pw;              // mode rows n = tr and -tr
       const int m = kc * kTcModes + lane;
-      const float4 c0 = __ldg(&a.tab[2 * (size_t(tr) * a.mp + m)]);
-      const float4 c1 = __ldg(&a.tab[2 * (size_t(tr) * a.mp + m) + 1]);
-      const int n = row_n(tr, a.ny, a.npos);
-      const float kx = float(m) * a.kxs, ky = float(n) * a.kys, k = c1.z;
+      const float4* tp = &a.tab[4 * (size_t(tr) * a.mp + m)];
+      const float4 c0 = __ldg(tp), c1 = __ldg(tp + 1), d0 = __ldg(tp + 2), d1 = __ldg(tp + 3);
+      const float kx = float(m) * a.kxs, ky = float(tr) * a.kys, k = c1.z;   // |k| is that of both rows
       float F0, S0;
       depth_fs(k, z0, h, c1.w, F0, S0);
       const float k1 = k, k2 = 0.5f * k * k;
       const float P[kTcTerms] = {F0, k1 * S0, k2 * F0};     // F(z0 + dz) orders 0..2 (u, v, phi_t)
       const float Q[kTcTerms] = {S0, k1 * F0, k2 * S0};     // S(z0 + dz) orders 0..2 (w)
-      // W_u = i kx A^phi, W_v = i ky A^phi, W_w = |k| A^phi, W_t = A^phit, W_eta = A^eta (the
-      // one-sided weights are in the table)
+      // W_u = i kx A^phi, W_v = i ky A^phi, W_w = |k| A^phi, W_t = A^phit, W_eta = A^eta of the
+      // rows n (c) and -n (d, ky negated; the one-sided weights are in the table)
       const float2 Wc[4] = {make_float2(-kx * c0.y, kx * c0.x), make_float2(-ky * c0.y, ky * c0.x),
                             make_float2(k * c0.x, k * c0.y), make_float2(c0.z, c0.w)};
+      const float2 Wd[4] = {make_float2(-kx * d0.y, kx * d0.x), make_float2(ky * d0.y, -ky * d0.x),
+                            make_float2(k * d0.x, k * d0.y), make_float2(d0.z, d0.w)};
       unsigned char* bhi = bst + size_t(s) * kTcStageBytes;
       unsigned char* blo = bhi + kTcBBytes;
       const uint32_t off = uint32_t(lane >> 2) * kTcLBO + uint32_t(pw) * 16u + uint32_t(lane & 3) * 4u;
-      auto put = [&](int cj, float re, float im) {
-        unsigned hi, lo;
-        bf2_split(re, -im, hi, lo);                 // column Re T: K pair (Re C, -Im C)
-        // column Im T: K pair (Im C, Re C) = the halves swapped, the new low half negated
-        const unsigned hi2 = __byte_perm(hi, 0u, 0x1032) ^ 0x8000u;
-        const unsigned lo2 = __byte_perm(lo, 0u, 0x1032) ^ 0x8000u;
+      // coefficients C (row n) and C' (row -n) of output cj: column Re(T + T') takes the K pair
+      // (Re U, -Im U) with U = C + C', column Im(T - T') the pair (Im V, Re V) with V = C - C'
+      auto put = [&](int cj, float2 c, float2 cp) {
+        unsigned h0, l0, h1, l1;
+        bf2_split(c.x + cp.x, -(c.y + cp.y), h0, l0);
+        bf2_split(c.y - cp.y, c.x - cp.x, h1, l1);
         const uint32_t o0 = off + uint32_t(2 * cj) * kTcSBO, o1 = o0 + kTcSBO;
-        *reinterpret_cast<unsigned*>(bhi + o0) = hi;
-        *reinterpret_cast<unsigned*>(blo + o0) = lo;
-        *reinterpret_cast<unsigned*>(bhi + o1) = hi2;
-        *reinterpret_cast<unsigned*>(blo + o1) = lo2;
+        *reinterpret_cast<unsigned*>(bhi + o0) = h0;
+        *reinterpret_cast<unsigned*>(blo + o0) = l0;
+        *reinterpret_cast<unsigned*>(bhi + o1) = h1;
+        *reinterpret_cast<unsigned*>(blo + o1) = l1;
       };
+      auto sc = [](float2 w, float f) { return make_float2(w.x * f, w.y * f); };
 #pragma unroll
       for (int j = 0; j < kTcTerms; ++j) {
-        put(0 * kTcTerms + j, Wc[0].x * P[j], Wc[0].y * P[j]);
-        put(1 * kTcTerms + j, Wc[1].x * P[j], Wc[1].y * P[j]);
-        put(2 * kTcTerms + j, Wc[2].x * Q[j], Wc[2].y * Q[j]);
-        put(3 * kTcTerms + j, Wc[3].x * P[j], Wc[3].y * P[j]);
+        put(0 * kTcTerms + j, sc(Wc[0], P[j]), sc(Wd[0], P[j]));
+        put(1 * kTcTerms + j, sc(Wc[1], P[j]), sc(Wd[1], P[j]));
+        put(2 * kTcTerms + j, sc(Wc[2], Q[j]), sc(Wd[2], Q[j]));
+        put(3 * kTcTerms + j, sc(Wc[3], P[j]), sc(Wd[3], P[j]));
       }
-      put(4 * kTcTerms, c1.x, c1.y);
+      put(4 * kTcTerms, make_float2(c1.x, c1.y), make_float2(d1.x, d1.y));
       fence_proxy_async();                          // generic-proxy stores -> the MMA's reads
       mbar_arrive(&sh.b_full[s]);
     }
@@ -411,18 +412,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_direct_tc(TcArgs a) {
 }
 
 // ------------------------------------------------------------------------------------------------
-// Mode table of the tensor-core path: rows of constant n (the Nyquist row skipped, rows padded to
-// a multiple of 8 with zero modes), m = 0 .. nx/2 - 1 padded to a multiple of 32.
+// Mode table of the tensor-core path: entry (q, m, s) for row n = q (s = 0) and n = -q (s = 1),
+// q < ny/2 (the Nyquist row is not in the table; row -0 is zero), rows padded to a multiple of 8
+// and m = 0 .. nx/2 - 1 to a multiple of 32 with zero modes.
 __global__ void k_tc_table(const float2* __restrict__ Ae, const float2* __restrict__ Ap,
                            const float2* __restrict__ At, const double* __restrict__ omega, double dt,
-                           int nx, int ny, int rows_p, int mp, int npos, float kxs, float kys, float depth,
+                           int nx, int ny, int rows_p, int mp, float kxs, float kys, float depth,
                            float4* __restrict__ tab) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= int64_t(rows_p) * mp) return;
-  const int tr = int(i / mp), m = int(i - int64_t(tr) * mp);
+  if (i >= int64_t(rows_p) * mp * 2) return;
+  const int sgn = int(i & 1);
+  const int64_t qm = i >> 1;
+  const int tr = int(qm / mp), m = int(qm - int64_t(tr) * mp);
   float4 c0 = make_float4(0.f, 0.f, 0.f, 0.f), c1 = make_float4(0.f, 0.f, 0.f, 1.f);
-  const int n = row_n(tr, ny, npos);
-  const bool live_row = ny > 1 ? (n > -(ny / 2) && n < ny / 2 && (tr < npos) == (n >= 0)) : tr == 0;
+  const int n = sgn ? -tr : tr;
+  const bool live_row = ny > 1 ? (tr < ny / 2 && !(sgn && tr == 0)) : (tr == 0 && !sgn);
   if (live_row && m < nx / 2) {
     const int r = n >= 0 ? n : n + ny;                   // storage row of the half spectrum
     const size_t si = size_t(r) * (nx / 2 + 1) + m;
@@ -647,13 +651,12 @@ TcLast g_tc_last[64];
 int direct_tc(const swense_modes* md, double t, const float* pts, int64_t np, float* eta, float* u,
               float* v, float* w, float* p, int32_t p_mode, double rho, double grav, cudaStream_t stream) {
   const int nx = md->nx, ny = md->ny;
-  const int npos = ny > 1 ? (ny / 2 + kTcRows - 1) / kTcRows * kTcRows : kTcRows;
-  const int rows_p = npos + (ny > 1 ? (ny / 2 - 1 + kTcRows - 1) / kTcRows * kTcRows : 0);
+  const int rows_p = ny > 1 ? (ny / 2 + kTcRows - 1) / kTcRows * kTcRows : kTcRows;   // row pairs
   const int mp = (nx / 2 + kTcModes - 1) / kTcModes * kTcModes;
   const int64_t ntiles = (np + kTcM - 1) / kTcM;
   if (ntiles >= (int64_t(1) << 31) || np >= (int64_t(1) << 31))
     return fail(SWENSE_ERR_SIZE, "too many points for one call of the tensor-core path");
-  const size_t tab_b = align256(size_t(rows_p) * mp * 2 * sizeof(float4));
+  const size_t tab_b = align256(size_t(rows_p) * mp * 4 * sizeof(float4));
   const size_t mm_b = 256, cnt_b = align256(size_t(kZBuckets) * sizeof(unsigned));
   const size_t perm_b = align256(size_t(np) * sizeof(int32_t)), srt_b = align256(size_t(np) * 3 * sizeof(float));
   const size_t bad_b = align256(size_t(ntiles));
@@ -673,10 +676,10 @@ int direct_tc(const swense_modes* md, double t, const float* pts, int64_t np, fl
   const float kys = ny > 1 ? float(6.283185307179586476925 / md->Ly) : 0.f;
   const float depth = md->depth > 0 ? float(md->depth) : 0.f;
   {
-    const int64_t n = int64_t(rows_p) * mp;
+    const int64_t n = int64_t(rows_p) * mp * 2;
     k_tc_table<<<unsigned((n + 255) / 256), 256, 0, stream>>>(
         reinterpret_cast<const float2*>(md->A_eta), reinterpret_cast<const float2*>(md->A_phi),
-        reinterpret_cast<const float2*>(md->A_phit), md->omega, t - md->t_ref, nx, ny, rows_p, mp, npos,
+        reinterpret_cast<const float2*>(md->A_phit), md->omega, t - md->t_ref, nx, ny, rows_p, mp,
         kxs, kys, depth, tab);
     SWENSE_CUDA_TRY(cudaGetLastError());
   }
@@ -696,7 +699,6 @@ int direct_tc(const swense_modes* md, double t, const float* pts, int64_t np, fl
   a.rows_p = rows_p;
   a.mp = mp;
   a.ny = ny;
-  a.npos = npos;
   a.spts = srt;
   a.perm = perm;
   a.np = np;
