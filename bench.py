@@ -1155,12 +1155,13 @@ def cpu_model():
 
 
 _POOL_SEA = None
+_POOL_Z = None
 
 
 def _pool_init(kind, n_levels, t):
     """Worker start-up (spawned process): rebuild the workload's sea from its seed, propagated to
     the query time, with one numpy thread per process."""
-    global _POOL_SEA
+    global _POOL_SEA, _POOL_Z
     from oracle import modal
     from wavegen import configs
     if kind == "large":
@@ -1168,11 +1169,74 @@ def _pool_init(kind, n_levels, t):
     else:
         cfg = configs.jonswap3d(mesh_dims=(4, 8, 4))
     _POOL_SEA = modal.propagate(cfg["sea"], t)
+    _POOL_Z = cfg["z_levels"]
 
 
 def _pool_work(pts):
     from oracle import modal
     return modal.fields_at_points(_POOL_SEA, pts, chunk=4)
+
+
+def _method_level(args):
+    """One worker task of the CPU method baseline: the method's grid at level l of the large sea
+    (library inverse FFTs of the four modal fields), timed."""
+    from oracle import method
+    l, pad = args
+    t0 = time.perf_counter()
+    method.grid_fft(_POOL_SEA, _POOL_Z, pad, levels=[l])
+    return time.perf_counter() - t0
+
+
+def _method_interp(args):
+    """One worker task of the CPU method baseline: the oracle's literal space-time interpolation
+    of `n` seeded points on a 4-level grid of the 512 x 256-mode sea (two time levels), timed; its
+    cost per point does not depend on the grid's size."""
+    from oracle import interp, method, modal
+    from wavegen import configs
+    n, seed = args
+    cfg = configs.jonswap3d(mesh_dims=(4, 8, 4))
+    z = np.asarray(cfg["z_levels"], np.float64)[28:32]
+    tl = cfg["t_levels"]
+    nodes, etas = zip(*(method.grid_fft(modal.propagate(cfg["sea"], t), z, 1) for t in tl))
+    rng = np.random.default_rng(seed)
+    p = np.stack([rng.uniform(0, cfg["sea"]["Lx"], n), rng.uniform(0, cfg["sea"]["Ly"], n),
+                  rng.uniform(z[1], z[2], n)], 1)
+    t0 = time.perf_counter()
+    interp.interp_points(np.stack(nodes), np.stack(etas), cfg["sea"]["Lx"], cfg["sea"]["Ly"], z, tl, p,
+                         cfg["t_query"])
+    return time.perf_counter() - t0
+
+
+def cpu_method_pool(n_levels, n_tl, t, n_points, cores, n_interp=20000):
+    """The CPU method baseline on `cores` spawned processes (one numpy thread each): the grid step
+    timed on `cores` of the large sea's levels (each a library inverse FFT per modal field) and
+    the literal interpolation timed on `cores` x n_interp points; the step's time is extrapolated
+    to all n_tl x n_levels level transforms and n_points points."""
+    import multiprocessing as mp
+    env_keep = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in env_keep:
+        os.environ[k] = "1"
+    try:
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(cores, initializer=_pool_init, initargs=("large", n_levels, t)) as pool:
+            lev = list(np.linspace(0, n_levels - 1, cores).astype(int))
+            t0 = time.perf_counter()
+            per_level = pool.map(_method_level, [(l, 1) for l in lev])
+            grid_wall = time.perf_counter() - t0
+            t0 = time.perf_counter()
+            per_interp = pool.map(_method_interp, [(n_interp, 7 + c) for c in range(cores)])
+            interp_wall = time.perf_counter() - t0
+    finally:
+        for k, v in env_keep.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    grid_s = float(np.mean(per_level)) * n_tl * n_levels / cores
+    interp_s = float(np.mean(per_interp)) / n_interp * n_points / cores
+    return {"grid_s": grid_s, "interp_s": interp_s, "level_transform_s": float(np.mean(per_level)),
+            "interp_points_per_s_per_core": n_interp / float(np.mean(per_interp)),
+            "sample_wall_s": grid_wall + interp_wall}
 
 
 def cpu_oracle_pool(kind, n_levels, t, pts, seconds, cores, seed=1):
@@ -1420,6 +1484,18 @@ def run_large(args, rank, world):
                 ref = vals[k][mask]
                 err[k] = float(np.max(np.abs(got - ref)) / max(np.max(np.abs(ref)), 1e-300)) if ref.size else None
             return err
+        meth = cpu_method_pool(nz, n_tl, tq, n, cores)
+        # the near-body points by the oracle's direct sum at the rate measured above
+        near_s = nn / rate
+        meth_step = meth["grid_s"] + meth["interp_s"] + near_s
+        line["cpu_method_baseline"] = {
+            "value": (n + nn) / meth_step, "unit": "points/s", "cores": cores,
+            "kind": "method on the CPU: numpy inverse real FFT per level and field + the oracle's "
+                    "literal Lagrange interpolation (FP64); near-body points by the direct sum",
+            "step_s": meth_step, "grid_s": meth["grid_s"], "interp_s": meth["interp_s"],
+            "near_body_s": near_s,
+            "sample": f"{cores} level transforms of the large sea and {cores} x 20000 interpolated "
+                      f"points timed, extrapolated to {n_tl} x {nz} levels and {n} points"}
         line["error_vs_fp64_oracle"] = {
             "norm": "max|gpu-exact|/max|exact| per field over the sample",
             "near_body_direct": rel_max(is_near), "near_body_points": int(is_near.sum()),

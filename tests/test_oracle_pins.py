@@ -386,3 +386,19 @@ def test_e1_workload_restates_the_papers_printed_setup():
     assert np.allclose(np.diff(xs), paper["cfd_mesh"]["dx_over_lambda_p"] * cfg["lambda_p"], rtol=1e-6)
     assert np.allclose(np.diff(zs), paper["cfd_mesh"]["dz_over_Hs"] * cfg["Hs"], rtol=1e-6)
     assert paper["refinement_factor"] * cfg["sea"]["nx"] == paper["reconstruction_points_after_refinement"]
+
+
+@pytest.mark.parametrize("depth,pad", [(0.0, 1), (0.9, 2), (0.0, 4)])
+def test_method_grid_fft_equals_direct_dft(depth, pad):
+    """The CPU method baseline's grid (library inverse FFT per level) equals the oracle's
+    separable direct DFT at every node, including the m = 0 column and the padded nodes."""
+    from oracle import method
+    s = _random_sea(depth, 21, nx=16, ny=8)
+    s["A_phi"][2, 0] += 0.01 - 0.03j                  # an m = 0 slot off the Hermitian pairs
+    z = np.array([-0.8, -0.3, 0.0, 0.06], np.float32)
+    ref_n, ref_e = modal.fields_on_grid(s, z, pad)
+    got_n, got_e = method.grid_fft(s, z, pad)
+    np.testing.assert_allclose(got_e, ref_e, atol=1e-12)
+    np.testing.assert_allclose(got_n, ref_n, atol=1e-12)
+    sub_n, _ = method.grid_fft(s, z, pad, levels=[3, 1])
+    np.testing.assert_allclose(sub_n, ref_n[[3, 1]], atol=1e-12)
