@@ -47,15 +47,20 @@ constexpr int kTcCj = 4 * kTcTerms + 1;               // 13 complex outputs per 
 constexpr int kTcN = kTcRows * 2 * kTcCj;             // 208 MMA columns
 constexpr int kTcModes = 32;                          // modes m per K-chunk
 constexpr int kTcK = 2 * kTcModes;                    // 64 K (re, im per mode)
-// B layout: column nc = col * 8 + pair (col = 2 cj + {0: Re(T_n + T_-n), 1: Im(T_n - T_-n)}); core matrices of
-// 8 columns x 8 K; k-blocks of 8 K are kTcLBO bytes apart (26 core matrices + 16 bytes, so that
-// the 32 lanes of a producer warp, one mode each, hit 32 different banks)
+// B layout: column nc = 16 cj + 2 pair + {0: Re(T_n + T_-n), 1: Im(T_n - T_-n)} (a pair's two
+// columns adjacent); core matrices of 8 columns x 8 K; k-blocks of 8 K are kTcLBO bytes apart (26
+// core matrices + 16 bytes, so that the 32 lanes of a producer warp, one mode each, hit 32
+// different banks)
 constexpr int kTcSBO = 128;
 constexpr int kTcLBO = (kTcN / 8) * 128 + 16;
 constexpr int kTcBBytes = (kTcK / 8) * kTcLBO;        // one of hi / lo
 constexpr int kTcStageBytes = 2 * kTcBBytes;
 constexpr int kTcStages = 2;
+// 13 warps: 4 epilogue warps (one point each), 8 producer warps (one row pair of a group each),
+// 1 MMA warp (one thread issues; the warp owns the tensor-memory allocation)
 constexpr int kEpiWarps = 4, kProdWarps = 8;
+constexpr int kPairsPerWarp = kTcRows / kProdWarps;
+static_assert(kPairsPerWarp * kProdWarps == kTcRows, "row pairs per producer warp");
 constexpr int kMmaWarp = kEpiWarps + kProdWarps;
 constexpr int kTcThreads = (kMmaWarp + 1) * 32;
 constexpr uint32_t kTmemCols = 512;
@@ -94,6 +99,13 @@ __device__ __forceinline__ float exp_kz(float k, float z) {
   const float lo = fmaf(k, z, -kz);
   const float e = expf(kz);
   return fmaf(e, lo, e);
+}
+
+// hi + lo BF16 split of a pair (as bf2_split), the residual taken with one packed subtraction.
+__device__ __forceinline__ void bf2_split_p(float2 v, unsigned& hi, unsigned& lo) {
+  hi = bf2(v.x, v.y);
+  const float2 r = csub(v, make_float2(__uint_as_float(hi << 16), __uint_as_float(hi & 0xffff0000u)));
+  lo = bf2(r.x, r.y);
 }
 
 // F = cosh(k(z+h))/cosh(kh), S = sinh(k(z+h))/cosh(kh) (finite depth), both e^{kz} in deep water.
@@ -217,25 +229,25 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_direct_tc(TcArgs a) {
     float sy, cy;                                   // e^{i 2 pi y / Ly}: row step n -> n + 1
     sincospif(2.f * (float(int(Y)) * 2.3283064365386963e-10f), &sy, &cy);
     const uint32_t lanebase = tbase + ((uint32_t(warp) * 32u) << 16);
-    float acc[kTcCj];
-#pragma unroll
-    for (int c = 0; c < kTcCj; ++c) acc[c] = 0.f;
+    float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};       // u, v, w, dphi/dt, eta
+    const float dzp[kTcTerms] = {1.f, dz, dz * dz};  // each order's sums enter times dz^j
 
     auto consume = [&](int gi) {
       const int g = gi % ng;
       const uint32_t dcol = (gi & 1) ? kColD1 : kColD0;
-      // Y_n(p) of the group's eight rows (consecutive n): exact at the first, then seven steps
-      float yr[kTcRows], yi[kTcRows];
+      // Y_n(p) of the group's eight rows (consecutive n) as (Re Y, -Im Y): exact at the first,
+      // then seven steps
+      float2 yv[kTcRows];
       {
         const unsigned ph = unsigned(g * kTcRows) * Y;
-        sincospif(2.f * (float(int(ph)) * 2.3283064365386963e-10f), &yi[0], &yr[0]);
+        float si, co;
+        sincospif(2.f * (float(int(ph)) * 2.3283064365386963e-10f), &si, &co);
+        yv[0] = make_float2(co, -si);
       }
 #pragma unroll
-      for (int r = 1; r < kTcRows; ++r) {
-        yr[r] = fmaf(yr[r - 1], cy, -yi[r - 1] * sy);
-        yi[r] = fmaf(yi[r - 1], cy, yr[r - 1] * sy);
-      }
-      // columns 16 cj .. 16 cj + 15: Re T of the 8 rows, then Im T of the 8 rows
+      for (int r = 1; r < kTcRows; ++r)
+        yv[r] = make_float2(fmaf(yv[r - 1].x, cy, yv[r - 1].y * sy), fmaf(yv[r - 1].y, cy, -yv[r - 1].x * sy));
+      // columns 16 cj .. 16 cj + 15: (Re, Im) of the 8 row pairs, adjacent
       constexpr int kB = 4;                          // x16 loads in flight per wait
 #pragma unroll
       for (int b0 = 0; b0 < kTcCj; b0 += kB) {
@@ -254,10 +266,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_direct_tc(TcArgs a) {
           float s = 0.f;
 #pragma unroll
           for (int rr = 0; rr < kTcRows; ++rr)
-            s = fmaf(yr[rr], __uint_as_float(r[q][rr]), fmaf(-yi[rr], __uint_as_float(r[q][8 + rr]), s));
-          acc[b0 + q] += s;
-          // keep this batch's sums ahead of the next batch's loads (bounds live registers)
-          asm volatile("" : "+f"(acc[b0 + q]));
+            s = fmaf(yv[rr].x, __uint_as_float(r[q][2 * rr]), fmaf(yv[rr].y, __uint_as_float(r[q][2 * rr + 1]), s));
+          const int cj = b0 + q;
+          acc[cj / kTcTerms] = fmaf(dzp[cj % kTcTerms], s, acc[cj / kTcTerms]);
         }
       }
     };
@@ -294,12 +305,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_direct_tc(TcArgs a) {
       consume(gi);
     }
     if (ok && live) {
-      const float uu = fmaf(dz, fmaf(dz, acc[2], acc[1]), acc[0]);
-      const float vv = fmaf(dz, fmaf(dz, acc[5], acc[4]), acc[3]);
-      const float ww = fmaf(dz, fmaf(dz, acc[8], acc[7]), acc[6]);
-      const float tt = fmaf(dz, fmaf(dz, acc[11], acc[10]), acc[9]);
+      const float uu = acc[0], vv = acc[1], ww = acc[2], tt = acc[3];
       const int64_t o = a.perm[pi];
-      if (a.o_eta) a.o_eta[o] = acc[12];
+      if (a.o_eta) a.o_eta[o] = acc[4];
       if (a.o_u) a.o_u[o] = uu;
       if (a.o_v) a.o_v[o] = vv;
       if (a.o_w) a.o_w[o] = ww;
@@ -316,56 +324,88 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_direct_tc(TcArgs a) {
     }
   } else if (warp < kMmaWarp) {
     // ================================================================ producers: B per group
-    const int pw = warp - kEpiWarps;                // row of the group
+    const int pw0 = (warp - kEpiWarps) * kPairsPerWarp;  // first row pair of this warp in a group
     const float h = a.depth;
+    // table entries of group gi for this lane's mode (rows n = tr and -tr) of pair pw0 + t
+    auto entry = [&](int gi, int t) {
+      const int kc = gi / ng, g = gi - kc * ng;
+      return &a.tab[4 * (size_t(g * kTcRows + pw0 + t) * a.mp + size_t(kc * kTcModes + lane))];
+    };
+    float4 c0[kPairsPerWarp], c1[kPairsPerWarp], d0[kPairsPerWarp], d1[kPairsPerWarp];
+#pragma unroll
+    for (int t = 0; t < kPairsPerWarp; ++t) {
+      const float4* tp = entry(0, t);
+      c0[t] = __ldg(tp), c1[t] = __ldg(tp + 1), d0[t] = __ldg(tp + 2), d1[t] = __ldg(tp + 3);
+    }
     for (int gi = 0; gi < ngi; ++gi) {
-      const int kc = gi / ng, g = gi % ng, s = gi & 1;
+      const int kc = gi / ng, g = gi - kc * ng, s = gi & 1;
+      // the next group's entries are in flight while this group's B is made
+      float4 n0[kPairsPerWarp], n1[kPairsPerWarp], n2[kPairsPerWarp], n3[kPairsPerWarp];
+#pragma unroll
+      for (int t = 0; t < kPairsPerWarp; ++t) {
+        const float4* tn = entry(gi + 1 < ngi ? gi + 1 : gi, t);
+        n0[t] = __ldg(tn), n1[t] = __ldg(tn + 1), n2[t] = __ldg(tn + 2), n3[t] = __ldg(tn + 3);
+      }
       if (gi >= kTcStages && !warp_wait(&sh.b_empty[s], unsigned((gi >> 1) - 1) & 1u, abort_flag)) break;
-      const int tr = g * kTcRows + pw;              // mode rows n = tr and -tr
-      const int m = kc * kTcModes + lane;
-      const float4* tp = &a.tab[4 * (size_t(tr) * a.mp + m)];
-      const float4 c0 = __ldg(tp), c1 = __ldg(tp + 1), d0 = __ldg(tp + 2), d1 = __ldg(tp + 3);
-      const float kx = float(m) * a.kxs, ky = float(tr) * a.kys, k = c1.z;   // |k| is that of both rows
-      float F0, S0;
-      depth_fs(k, z0, h, c1.w, F0, S0);
-      const float k1 = k, k2 = 0.5f * k * k;
-      const float P[kTcTerms] = {F0, k1 * S0, k2 * F0};     // F(z0 + dz) orders 0..2 (u, v, phi_t)
-      const float Q[kTcTerms] = {S0, k1 * F0, k2 * S0};     // S(z0 + dz) orders 0..2 (w)
-      // W_u = i kx A^phi, W_v = i ky A^phi, W_w = |k| A^phi, W_t = A^phit, W_eta = A^eta of the
-      // rows n (c) and -n (d, ky negated; the one-sided weights are in the table)
-      const float2 Wc[4] = {make_float2(-kx * c0.y, kx * c0.x), make_float2(-ky * c0.y, ky * c0.x),
-                            make_float2(k * c0.x, k * c0.y), make_float2(c0.z, c0.w)};
-      const float2 Wd[4] = {make_float2(-kx * d0.y, kx * d0.x), make_float2(ky * d0.y, -ky * d0.x),
-                            make_float2(k * d0.x, k * d0.y), make_float2(d0.z, d0.w)};
       unsigned char* bhi = bst + size_t(s) * kTcStageBytes;
       unsigned char* blo = bhi + kTcBBytes;
-      const uint32_t off = uint32_t(lane >> 2) * kTcLBO + uint32_t(pw) * 16u + uint32_t(lane & 3) * 4u;
-      // coefficients C (row n) and C' (row -n) of output cj: column Re(T + T') takes the K pair
-      // (Re U, -Im U) with U = C + C', column Im(T - T') the pair (Im V, Re V) with V = C - C'
-      auto put = [&](int cj, float2 c, float2 cp) {
-        unsigned h0, l0, h1, l1;
-        bf2_split(c.x + cp.x, -(c.y + cp.y), h0, l0);
-        bf2_split(c.y - cp.y, c.x - cp.x, h1, l1);
-        const uint32_t o0 = off + uint32_t(2 * cj) * kTcSBO, o1 = o0 + kTcSBO;
-        *reinterpret_cast<unsigned*>(bhi + o0) = h0;
-        *reinterpret_cast<unsigned*>(blo + o0) = l0;
-        *reinterpret_cast<unsigned*>(bhi + o1) = h1;
-        *reinterpret_cast<unsigned*>(blo + o1) = l1;
-      };
-      auto sc = [](float2 w, float f) { return make_float2(w.x * f, w.y * f); };
+      const int m = kc * kTcModes + lane;
+      const float kx = float(m) * a.kxs;
 #pragma unroll
-      for (int j = 0; j < kTcTerms; ++j) {
-        put(0 * kTcTerms + j, sc(Wc[0], P[j]), sc(Wd[0], P[j]));
-        put(1 * kTcTerms + j, sc(Wc[1], P[j]), sc(Wd[1], P[j]));
-        put(2 * kTcTerms + j, sc(Wc[2], Q[j]), sc(Wd[2], Q[j]));
-        put(3 * kTcTerms + j, sc(Wc[3], P[j]), sc(Wd[3], P[j]));
+      for (int t = 0; t < kPairsPerWarp; ++t) {
+        const int pw = pw0 + t, tr = g * kTcRows + pw;
+        const float ky = float(tr) * a.kys, k = c1[t].z;     // |k| is that of both rows
+        float F0, S0;
+        depth_fs(k, z0, h, c1[t].w, F0, S0);
+        const float k2 = 0.5f * k * k;
+        const float P[kTcTerms] = {F0, k * S0, k2 * F0};    // F(z0 + dz) orders 0..2 (u, v, phi_t)
+        const float Q[kTcTerms] = {S0, k * F0, k2 * S0};    // S(z0 + dz) orders 0..2 (w)
+        // rows n (c) and -n (d): sums and differences of A^phi, A^phit, A^eta. With
+        // W_u = i kx A^phi, W_v = i ky A^phi (ky negated on row -n), W_w = |k| A^phi,
+        // W_t = A^phit, U = W(n) + W(-n) and V = W(n) - W(-n), the column Re(T_n + T_-n) takes
+        // the K pair (Re U, -Im U) and the column Im(T_n - T_-n) the pair (Im V, Re V); below,
+        // those pairs per field before the depth factor.
+        const float4 A0 = c0[t], B0 = d0[t], A1 = c1[t], B1 = d1[t];
+        const float2 sp = make_float2(A0.x + B0.x, A0.y + B0.y), dp = make_float2(A0.x - B0.x, A0.y - B0.y);
+        const float2 st = make_float2(A0.z + B0.z, A0.w + B0.w), df = make_float2(A0.z - B0.z, A0.w - B0.w);
+        const float2 Rf[4] = {make_float2(-kx * sp.y, -kx * sp.x), make_float2(-ky * dp.y, -ky * dp.x),
+                              make_float2(k * sp.x, -k * sp.y), make_float2(st.x, -st.y)};
+        const float2 If[4] = {make_float2(kx * dp.x, -kx * dp.y), make_float2(ky * sp.x, -ky * sp.y),
+                              make_float2(k * dp.y, k * dp.x), make_float2(df.y, df.x)};
+        // this pair's two 16-byte rows in the core matrix of each 16-column block
+        const uint32_t off = uint32_t(lane >> 2) * kTcLBO + uint32_t(pw >> 2) * kTcSBO +
+                             uint32_t((2 * pw) & 7) * 16u + uint32_t(lane & 3) * 4u;
+        auto put = [&](int cj, float2 re, float2 im) {
+          unsigned h0, l0, h1, l1;
+          bf2_split_p(re, h0, l0);
+          bf2_split_p(im, h1, l1);
+          const uint32_t o0 = off + uint32_t(2 * cj) * kTcSBO;
+          *reinterpret_cast<unsigned*>(bhi + o0) = h0;
+          *reinterpret_cast<unsigned*>(blo + o0) = l0;
+          *reinterpret_cast<unsigned*>(bhi + o0 + 16) = h1;
+          *reinterpret_cast<unsigned*>(blo + o0 + 16) = l1;
+        };
+#pragma unroll
+        for (int j = 0; j < kTcTerms; ++j) {
+          const float2 pj = make_float2(P[j], P[j]), qj = make_float2(Q[j], Q[j]);
+          put(0 * kTcTerms + j, pmul(Rf[0], pj), pmul(If[0], pj));
+          put(1 * kTcTerms + j, pmul(Rf[1], pj), pmul(If[1], pj));
+          put(2 * kTcTerms + j, pmul(Rf[2], qj), pmul(If[2], qj));
+          put(3 * kTcTerms + j, pmul(Rf[3], pj), pmul(If[3], pj));
+        }
+        put(4 * kTcTerms, make_float2(A1.x + B1.x, -(A1.y + B1.y)), make_float2(A1.y - B1.y, A1.x - B1.x));
       }
-      put(4 * kTcTerms, make_float2(c1.x, c1.y), make_float2(d1.x, d1.y));
       fence_proxy_async();                          // generic-proxy stores -> the MMA's reads
       mbar_arrive(&sh.b_full[s]);
+#pragma unroll
+      for (int t = 0; t < kPairsPerWarp; ++t) {
+        c0[t] = n0[t];
+        c1[t] = n1[t];
+        d0[t] = n2[t];
+        d1[t] = n3[t];
+      }
     }
   } else {
-    // ================================================================ MMA issue (one thread)
     if (lane == 0) {
       bool ok = true;
       for (int kc = 0; kc < nkc && ok; ++kc) {
@@ -378,22 +418,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_direct_tc(TcArgs a) {
           if (ok && gi >= 2) ok = thread_wait(&sh.d_empty[d], unsigned((gi >> 1) - 1) & 1u, abort_flag);
           if (!ok) break;
           tc::fence_after();
-          const uint32_t dt = tbase + (d ? kColD1 : kColD0);
+          const uint32_t dacc = tbase + (d ? kColD1 : kColD0);
           unsigned char* bhi = bst + size_t(s) * kTcStageBytes;
           unsigned char* blo = bhi + kTcBBytes;
 #pragma unroll
           for (int ks = 0; ks < kTcK / 16; ++ks) {
             const uint64_t dh = tc::smem_desc(bhi + 2 * ks * kTcLBO, kTcLBO, kTcSBO);
             const uint64_t dl = tc::smem_desc(blo + 2 * ks * kTcLBO, kTcLBO, kTcSBO);
-            tc::mma_ts(dt, tbase + kColAhi + 8u * ks, dh, kIdesc, ks > 0 ? 1u : 0u);
-            tc::mma_ts(dt, tbase + kColAhi + 8u * ks, dl, kIdesc, 1u);
-            tc::mma_ts(dt, tbase + kColAlo + 8u * ks, dh, kIdesc, 1u);
+            tc::mma_ts(dacc, tbase + kColAhi + 8u * ks, dh, kIdesc, ks > 0 ? 1u : 0u);
+            tc::mma_ts(dacc, tbase + kColAhi + 8u * ks, dl, kIdesc, 1u);
+            tc::mma_ts(dacc, tbase + kColAlo + 8u * ks, dh, kIdesc, 1u);
           }
           tc::commit(&sh.b_empty[s]);
           tc::commit(&sh.d_full[d]);
         }
       }
-      tc::commit(&sh.fin);                          // every MMA issued above has completed
+      tc::commit(&sh.fin);
     }
     __syncwarp();
   }

@@ -93,6 +93,13 @@ __device__ __forceinline__ float2 csub(float2 a, float2 b) {
   asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(c_as_u64(a)), "l"(c_as_u64(b)));
   return u64_as_c(d);
 }
+// Element-wise product of pairs as one packed instruction (x with x, y with y), rounded to
+// nearest like the scalar form.
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) {
+  unsigned long long d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(c_as_u64(a)), "l"(c_as_u64(b)));
+  return u64_as_c(d);
+}
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }

@@ -36,7 +36,7 @@ def env():
 
 
 @pytest.mark.parametrize("variant", [0, 1])
-@pytest.mark.parametrize("N,K", [(16, 16), (64, 32), (208, 64), (256, 256), (48, 128)])
+@pytest.mark.parametrize("N,K", [(16, 16), (64, 32), (112, 128), (208, 64), (256, 256), (48, 128)])
 def test_selftest_gemm_is_exact(env, variant, N, K):
     torch, S, api = env
     rng = np.random.default_rng(N * 1000 + K + variant)
