@@ -40,36 +40,45 @@
 namespace swense {
 namespace {
 
-constexpr int kTcM = 128;                             // points per tile (MMA M)
+constexpr int kTcM = 128;                             // points per tile (one CTA of the pair)
 constexpr int kTcRows = 8;                            // mode row pairs (n, -n) per group
 constexpr int kTcTerms = 3;                           // Taylor orders in dz: 0, 1, 2
 constexpr int kTcCj = 4 * kTcTerms + 1;               // 13 complex outputs per row
 constexpr int kTcN = kTcRows * 2 * kTcCj;             // 208 MMA columns
+constexpr int kTcHalfRows = kTcRows / 2;              // row pairs whose B columns a CTA makes
+constexpr int kTcNh = kTcN / 2;                       // 104 B columns per CTA
 constexpr int kTcModes = 32;                          // modes m per K-chunk
 constexpr int kTcK = 2 * kTcModes;                    // 64 K (re, im per mode)
-// B layout: column nc = 16 cj + 2 pair + {0: Re(T_n + T_-n), 1: Im(T_n - T_-n)} (a pair's two
-// columns adjacent); core matrices of 8 columns x 8 K; k-blocks of 8 K are kTcLBO bytes apart (26
-// core matrices + 16 bytes, so that the 32 lanes of a producer warp, one mode each, hit 32
-// different banks)
+// B layout (each CTA's half, columns nc = 8 cj + 2 pair + {0: Re(T_n + T_-n), 1: Im(T_n - T_-n)}
+// for its 4 row pairs): one core matrix (8 columns x 8 K, 128 bytes) per output cj; k-blocks of
+// 8 K are kTcLBO bytes apart (13 core matrices + 16 bytes, so that the 32 lanes of a producer
+// warp, one mode each, hit 32 different banks). In the pair's accumulator, column c < 104 comes
+// from the even CTA's row pairs 0..3 and column 104 + c from the odd CTA's 4..7.
 constexpr int kTcSBO = 128;
-constexpr int kTcLBO = (kTcN / 8) * 128 + 16;
+constexpr int kTcLBO = (kTcNh / 8) * 128 + 16;
 constexpr int kTcBBytes = (kTcK / 8) * kTcLBO;        // one of hi / lo
 constexpr int kTcStageBytes = 2 * kTcBBytes;
-constexpr int kTcStages = 2;
-// 13 warps: 4 epilogue warps (one point each), 8 producer warps (one row pair of a group each),
-// 1 MMA warp (one thread issues; the warp owns the tensor-memory allocation)
-constexpr int kEpiWarps = 4, kProdWarps = 8;
-constexpr int kPairsPerWarp = kTcRows / kProdWarps;
-static_assert(kPairsPerWarp * kProdWarps == kTcRows, "row pairs per producer warp");
+constexpr int kTcStages = 4;
+// per point, the row anchors Y^(8 j) (j < kYLo) of its groups: one group's first row in 64
+constexpr int kYLo = 64;
+constexpr int kYTabBytes = kYLo * kTcM * 8;
+// 9 warps per CTA: 4 epilogue warps (one point each), 4 producer warps (one row pair of this
+// CTA's half each), 1 MMA warp (the even CTA's lane 0 issues for the pair; the warp owns the
+// tensor-memory allocation in both CTAs)
+constexpr int kEpiWarps = 4, kProdWarps = 4;
+static_assert(kProdWarps == kTcHalfRows, "one row pair per producer warp");
 constexpr int kMmaWarp = kEpiWarps + kProdWarps;
 constexpr int kTcThreads = (kMmaWarp + 1) * 32;
 constexpr uint32_t kTmemCols = 512;
-constexpr uint32_t kColAhi = 0, kColAlo = 32, kColD0 = 64, kColD1 = 288;
+constexpr uint32_t kColAhi = 0, kColAlo = kTcK / 2, kColD0 = kTcK, kColD1 = kTcK + kTcN;
 constexpr float kKappaMax = 0.02f;
 constexpr int kZBuckets = 1 << 16;
-constexpr uint32_t kIdesc = tc::idesc_bf16_f32(kTcM, kTcN);
-static_assert(kTcN % 16 == 0 && kTcN <= 256, "MMA N for M = 128");
-static_assert(kColD1 + kTcN <= kTmemCols && kColD0 + kTcN <= kColD1, "tensor-memory columns");
+constexpr uint32_t kIdesc = tc::idesc_bf16_f32(2 * kTcM, kTcN);
+// more than half of an SM's shared memory, so that one CTA of the kernel runs per SM (two
+// pairs' CTAs sharing an SM would wait on each other's tensor memory)
+constexpr size_t kTcSmemMin = 120 * 1024;
+static_assert(kTcN % 16 == 0 && kTcN <= 256 && kTcNh % 8 == 0, "MMA N for M = 256");
+static_assert(kColD1 + kTcN <= kTmemCols, "tensor-memory columns");
 
 // Set when a bounded wait of k_direct_tc gave up (read by swense_async_status).
 __device__ int g_direct_timeout;
@@ -87,6 +96,7 @@ struct TcArgs {
   int p_mode;
   float rho, g;
   uint8_t* tile_bad;        // [ntiles]: 1 = left to the per-pair kernel
+  int64_t ntiles;
 };
 
 // Table row q holds the mode rows n = q and n = -q (q = 0 .. ny/2 - 1; row -0 and the rows past
@@ -121,15 +131,16 @@ __device__ __forceinline__ void depth_fs(float k, float z, float h, float invd, 
 }
 
 // Warp-collective bounded wait: every lane polls; the warp succeeds only together. A wait that
-// gives up (or sees another role give up) sets the CTA's abort flag and the device flag.
+// gives up (or sees another role give up) sets the CTA's abort flag and the device flag. The
+// waits acquire at cluster scope: arrivals come from both CTAs of the pair.
 __device__ __forceinline__ bool warp_wait(uint64_t* bar, unsigned parity, volatile int* abort_flag) {
   bool ok = false;
   for (int it = 0; it < kMbarPolls; ++it) {
-    if (mbar_try_wait(bar, parity)) {
+    if (mbar_try_wait_cluster(bar, parity)) {
       ok = true;
       break;
     }
-    if ((it & 31) == 31 && *abort_flag) break;
+    if ((it & 31) == 31 && (*abort_flag || *(volatile int*)&g_direct_timeout)) break;
   }
   ok = __all_sync(0xffffffffu, ok);
   if (!ok && (threadIdx.x & 31) == 0) {
@@ -140,8 +151,11 @@ __device__ __forceinline__ bool warp_wait(uint64_t* bar, unsigned parity, volati
 }
 __device__ __forceinline__ bool thread_wait(uint64_t* bar, unsigned parity, volatile int* abort_flag) {
   for (int it = 0; it < kMbarPolls; ++it) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((it & 31) == 31 && *abort_flag) return false;
+    if (mbar_try_wait_cluster(bar, parity)) return true;
+    if ((it & 31) == 31 && (*abort_flag || *(volatile int*)&g_direct_timeout)) {
+      *abort_flag = 1;
+      return false;
+    }
   }
   *abort_flag = 1;
   atomicExch(&g_direct_timeout, 1);
@@ -155,20 +169,30 @@ struct TcShared {
   float zmin[kTcThreads / 32], zmax[kTcThreads / 32];
 };
 
-__global__ void __launch_bounds__(kTcThreads, 1) k_direct_tc(TcArgs a) {
+// One cluster of two CTAs per pair of z-sorted tiles (256 points): the pair shares one expansion
+// centre z0 and one B per group, each CTA making the B columns of 4 of the group's 8 row pairs,
+// and the even CTA issues M = 256 MMAs over both CTAs' A and B. The pair's mbarriers that count
+// arrivals of both CTAs (b_full, d_empty, a_ready) are the even CTA's; the MMA completions
+// (b_empty, d_full, fin) arrive in both CTAs.
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1) k_direct_tc(TcArgs a) {
   extern __shared__ __align__(1024) unsigned char smraw[];
   unsigned char* bst = smraw;                                   // kTcStages x (B hi, B lo)
-  TcShared& sh = *reinterpret_cast<TcShared*>(smraw + kTcStages * kTcStageBytes);
+  float2* ytab = reinterpret_cast<float2*>(smraw + kTcStages * kTcStageBytes);   // [kYLo][kTcM]
+  TcShared& sh = *reinterpret_cast<TcShared*>(smraw + kTcStages * kTcStageBytes + kYTabBytes);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t tile = blockIdx.x;
-  const int64_t p0 = tile * kTcM;
+  const unsigned rank = cluster_rank();                          // 0: even CTA, 1: odd CTA
+  const int64_t tile = blockIdx.x;                               // rank == blockIdx.x & 1
+  const int64_t p0 = tile * kTcM, pp0 = (tile - rank) * kTcM;     // this tile's, the pair's first point
 
-  // ---- the tile's z range (padding points repeat the last point)
-  float zt = 0.f;
+  // ---- the pair's z range (both CTAs compute it from the same 256 points; padding repeats the
+  // last point)
   {
-    const int64_t i = std::min<int64_t>(p0 + (threadIdx.x & (kTcM - 1)), a.np - 1);
-    zt = a.spts[3 * i + 2];
-    float lo = zt, hi = zt;
+    float lo = 3.4e38f, hi = -3.4e38f;
+    for (int j = threadIdx.x; j < 2 * kTcM; j += kTcThreads) {
+      const float zt = a.spts[3 * std::min<int64_t>(pp0 + j, a.np - 1) + 2];
+      lo = fminf(lo, zt);
+      hi = fmaxf(hi, zt);
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
@@ -182,40 +206,41 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_direct_tc(TcArgs a) {
   if (threadIdx.x == 0) sh.abort_flag = 0;
   __syncthreads();
   float zmin = sh.zmin[0], zmax = sh.zmax[0];
-  for (int w = 1; w < kTcM / 32; ++w) {
+  for (int w = 1; w < kTcThreads / 32; ++w) {
     zmin = fminf(zmin, sh.zmin[w]);
     zmax = fmaxf(zmax, sh.zmax[w]);
   }
   const float z0 = 0.5f * (zmin + zmax);
   const float half = 0.5f * (zmax - zmin);
-  if (a.kmax * half > kKappaMax) {                  // uniform over the CTA
-    if (threadIdx.x == 0) a.tile_bad[tile] = 1;
+  if (a.kmax * half > kKappaMax) {                  // the same decision in both CTAs of the pair
+    if (threadIdx.x == 0 && tile < a.ntiles) a.tile_bad[tile] = 1;
     return;
   }
   if (threadIdx.x == 0) {
-    a.tile_bad[tile] = 0;
+    if (tile < a.ntiles) a.tile_bad[tile] = 0;
     for (int s = 0; s < kTcStages; ++s) {
-      mbar_init(&sh.b_full[s], kProdWarps * 32);
+      mbar_init(&sh.b_full[s], 2 * kProdWarps * 32);
       mbar_init(&sh.b_empty[s], 1);
     }
     for (int d = 0; d < 2; ++d) {
       mbar_init(&sh.d_full[d], 1);
-      mbar_init(&sh.d_empty[d], kEpiWarps * 32);
+      mbar_init(&sh.d_empty[d], 2 * kEpiWarps * 32);
     }
-    mbar_init(&sh.a_ready, kEpiWarps * 32);
+    mbar_init(&sh.a_ready, 2 * kEpiWarps * 32);
     mbar_init(&sh.fin, 1);
     fence_mbar_init();
   }
   if (warp == kMmaWarp) {
-    tc::alloc(&sh.tmem, kTmemCols);
-    tc::relinquish();
+    tc::alloc2(&sh.tmem, kTmemCols);
+    tc::relinquish2();
   }
   tc::fence_before();
-  __syncthreads();
+  cluster_sync();                                   // both CTAs' barriers exist before any arrival
   tc::fence_after();
   const uint32_t tbase = sh.tmem;
   volatile int* abort_flag = &sh.abort_flag;
   const int nkc = a.mp / kTcModes, ng = a.rows_p / kTcRows, ngi = nkc * ng;
+  const unsigned c_a_ready = cluster_addr(&sh.a_ready, 0u);   // the even CTA's barriers
 
   if (warp < kEpiWarps) {
     // ================================================================ epilogue: one point each
@@ -232,43 +257,59 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_direct_tc(TcArgs a) {
     float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};       // u, v, w, dphi/dt, eta
     const float dzp[kTcTerms] = {1.f, dz, dz * dz};  // each order's sums enter times dz^j
 
-    auto consume = [&](int gi) {
-      const int g = gi % ng;
+    // this point's row anchors: ytab[j] = Y^(8 j) as (Re, -Im), j < kYLo (exact, one
+    // sine/cosine each); a group g >= kYLo also takes Y^(8 kYLo (g / kYLo)), kept in yhi
+    for (int j = 0; j < kYLo; ++j) {
+      const unsigned ph = unsigned(kTcRows * j) * Y;
+      float si, co;
+      sincospif(2.f * (float(int(ph)) * 2.3283064365386963e-10f), &si, &co);
+      ytab[j * kTcM + t] = make_float2(co, -si);
+    }
+    float2 yhi = make_float2(1.f, 0.f);             // (Re, Im) of Y^(8 kYLo (g / kYLo))
+
+    auto consume = [&](int gi, int g) {
       const uint32_t dcol = (gi & 1) ? kColD1 : kColD0;
-      // Y_n(p) of the group's eight rows (consecutive n) as (Re Y, -Im Y): exact at the first,
-      // then seven steps
+      // Y_n(p) of the group's eight rows (consecutive n) as (Re Y, -Im Y): the anchor, then one
+      // step per row
       float2 yv[kTcRows];
       {
-        const unsigned ph = unsigned(g * kTcRows) * Y;
-        float si, co;
-        sincospif(2.f * (float(int(ph)) * 2.3283064365386963e-10f), &si, &co);
-        yv[0] = make_float2(co, -si);
+        const float2 lo = ytab[(g % kYLo) * kTcM + t];          // (Re, -Im) of Y^(8 (g % kYLo))
+        // (Re, -Im) of yhi * Y^(8 (g % kYLo))
+        yv[0] = make_float2(fmaf(yhi.x, lo.x, yhi.y * lo.y), fmaf(yhi.x, lo.y, -yhi.y * lo.x));
       }
 #pragma unroll
       for (int r = 1; r < kTcRows; ++r)
         yv[r] = make_float2(fmaf(yv[r - 1].x, cy, yv[r - 1].y * sy), fmaf(yv[r - 1].y, cy, -yv[r - 1].x * sy));
-      // columns 16 cj .. 16 cj + 15: (Re, Im) of the 8 row pairs, adjacent
-      constexpr int kB = 4;                          // x16 loads in flight per wait
+      // output cj: columns 8 cj .. 8 cj + 7 (row pairs 0..3) and 104 + 8 cj .. (pairs 4..7),
+      // (Re, Im) of each pair adjacent
+      constexpr int kB = kTcCj;                      // every output's loads in flight, one wait
 #pragma unroll
       for (int b0 = 0; b0 < kTcCj; b0 += kB) {
-        uint32_t r[kB][16];
+        uint32_t r[kB][2][8];
 #pragma unroll
         for (int q = 0; q < kB; ++q)
-          if (b0 + q < kTcCj) tc::ld_x16(lanebase + dcol + 16u * (b0 + q), r[q]);
+          if (b0 + q < kTcCj) {
+            tc::ld_x8(lanebase + dcol + uint32_t(8 * (b0 + q)), r[q][0]);
+            tc::ld_x8(lanebase + dcol + uint32_t(kTcNh + 8 * (b0 + q)), r[q][1]);
+          }
         tc::wait_ld();
         if (b0 + kB >= kTcCj) {                      // every column of this buffer is read
           tc::fence_before();
-          mbar_arrive(&sh.d_empty[gi & 1]);
+          mbar_arrive_cluster(cluster_addr(&sh.d_empty[gi & 1], 0u));
         }
 #pragma unroll
         for (int q = 0; q < kB; ++q) {
           if (b0 + q >= kTcCj) break;
-          float s = 0.f;
+          // (Re Y, -Im Y) x (Re T, Im T) pair by pair, summed as one packed pair
+          float2 s2 = make_float2(0.f, 0.f);
 #pragma unroll
           for (int rr = 0; rr < kTcRows; ++rr)
-            s = fmaf(yv[rr].x, __uint_as_float(r[q][2 * rr]), fmaf(yv[rr].y, __uint_as_float(r[q][2 * rr + 1]), s));
+            s2 = pfma(yv[rr],
+                      make_float2(__uint_as_float(r[q][rr >> 2][2 * (rr & 3)]),
+                                  __uint_as_float(r[q][rr >> 2][2 * (rr & 3) + 1])),
+                      s2);
           const int cj = b0 + q;
-          acc[cj / kTcTerms] = fmaf(dzp[cj % kTcTerms], s, acc[cj / kTcTerms]);
+          acc[cj / kTcTerms] = fmaf(dzp[cj % kTcTerms], s2.x + s2.y, acc[cj / kTcTerms]);
         }
       }
     };
@@ -276,7 +317,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_direct_tc(TcArgs a) {
     // A = X_m(p) of a K-chunk's 32 modes: word j = (cos, sin) as BF16 (hi, then the lo residual)
     auto write_a = [&](int kc) {
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
+      for (int h = 0; h < kTcModes / 16; ++h) {
         uint32_t whi[16], wlo[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
@@ -291,18 +332,30 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_direct_tc(TcArgs a) {
       }
       tc::wait_st();
       tc::fence_before();
-      mbar_arrive(&sh.a_ready);
+      mbar_arrive_cluster(c_a_ready);
     };
     write_a(0);
     bool ok = true;
-    for (int gi = 0; gi < ngi; ++gi) {
+    for (int gi = 0, g = 0, kc = 0; gi < ngi; ++gi) {
+      if (g % kYLo == 0) {
+        if (g == 0) {
+          yhi = make_float2(1.f, 0.f);
+        } else {
+          const unsigned ph = unsigned(kTcRows * g) * Y;
+          sincospif(2.f * (float(int(ph)) * 2.3283064365386963e-10f), &yhi.y, &yhi.x);
+        }
+      }
       ok = warp_wait(&sh.d_full[gi & 1], unsigned(gi >> 1) & 1u, abort_flag);
       if (!ok) break;
       tc::fence_after();
       // the last group of a chunk is done, so are all MMAs reading this chunk's A: the next
       // chunk's A goes in before this group's epilogue, so the MMAs resume at once
-      if ((gi + 1) % ng == 0 && gi + 1 < ngi) write_a((gi + 1) / ng);
-      consume(gi);
+      if (g + 1 == ng && kc + 1 < nkc) write_a(kc + 1);
+      consume(gi, g);
+      if (++g == ng) {
+        g = 0;
+        ++kc;
+      }
     }
     if (ok && live) {
       const float uu = acc[0], vv = acc[1], ww = acc[2], tt = acc[3];
@@ -324,88 +377,64 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_direct_tc(TcArgs a) {
     }
   } else if (warp < kMmaWarp) {
     // ================================================================ producers: B per group
-    const int pw0 = (warp - kEpiWarps) * kPairsPerWarp;  // first row pair of this warp in a group
+    const int pw = warp - kEpiWarps;                // this CTA's row pair of the group
+    const int pr = int(rank) * kTcHalfRows + pw;    // the pair's row pair
     const float h = a.depth;
-    // table entries of group gi for this lane's mode (rows n = tr and -tr) of pair pw0 + t
-    auto entry = [&](int gi, int t) {
-      const int kc = gi / ng, g = gi - kc * ng;
-      return &a.tab[4 * (size_t(g * kTcRows + pw0 + t) * a.mp + size_t(kc * kTcModes + lane))];
-    };
-    float4 c0[kPairsPerWarp], c1[kPairsPerWarp], d0[kPairsPerWarp], d1[kPairsPerWarp];
-#pragma unroll
-    for (int t = 0; t < kPairsPerWarp; ++t) {
-      const float4* tp = entry(0, t);
-      c0[t] = __ldg(tp), c1[t] = __ldg(tp + 1), d0[t] = __ldg(tp + 2), d1[t] = __ldg(tp + 3);
-    }
+    // this lane's mode is K pair `lane`: k-block lane / 4, word lane % 4 of a 16-byte row; this
+    // pair's two rows (Re, Im) in each output's core matrix
+    const uint32_t off = uint32_t(lane >> 2) * kTcLBO + uint32_t(2 * pw) * 16u + uint32_t(lane & 3) * 4u;
     for (int gi = 0; gi < ngi; ++gi) {
-      const int kc = gi / ng, g = gi - kc * ng, s = gi & 1;
-      // the next group's entries are in flight while this group's B is made
-      float4 n0[kPairsPerWarp], n1[kPairsPerWarp], n2[kPairsPerWarp], n3[kPairsPerWarp];
-#pragma unroll
-      for (int t = 0; t < kPairsPerWarp; ++t) {
-        const float4* tn = entry(gi + 1 < ngi ? gi + 1 : gi, t);
-        n0[t] = __ldg(tn), n1[t] = __ldg(tn + 1), n2[t] = __ldg(tn + 2), n3[t] = __ldg(tn + 3);
-      }
-      if (gi >= kTcStages && !warp_wait(&sh.b_empty[s], unsigned((gi >> 1) - 1) & 1u, abort_flag)) break;
+      const int kc = gi / ng, g = gi - kc * ng, s = gi % kTcStages;
+      const int tr = g * kTcRows + pr;              // mode rows n = tr and -tr
+      const int m = kc * kTcModes + lane;
+      const float4* tp = &a.tab[4 * (size_t(tr) * a.mp + size_t(m))];
+      const float4 c0 = __ldg(tp), c1 = __ldg(tp + 1), d0 = __ldg(tp + 2), d1 = __ldg(tp + 3);
+      if (gi >= kTcStages &&
+          !warp_wait(&sh.b_empty[s], unsigned(gi / kTcStages - 1) & 1u, abort_flag))
+        break;
+      const float kx = float(m) * a.kxs, ky = float(tr) * a.kys, k = c1.z;   // |k| is that of both rows
+      float F0, S0;
+      depth_fs(k, z0, h, c1.w, F0, S0);
+      const float k2 = 0.5f * k * k;
+      const float P[kTcTerms] = {F0, k * S0, k2 * F0};      // F(z0 + dz) orders 0..2 (u, v, phi_t)
+      const float Q[kTcTerms] = {S0, k * F0, k2 * S0};      // S(z0 + dz) orders 0..2 (w)
+      // rows n (c) and -n (d): sums and differences of A^phi, A^phit, A^eta. With
+      // W_u = i kx A^phi, W_v = i ky A^phi (ky negated on row -n), W_w = |k| A^phi, W_t = A^phit,
+      // U = W(n) + W(-n) and V = W(n) - W(-n), the column Re(T_n + T_-n) takes the K pair
+      // (Re U, -Im U) and the column Im(T_n - T_-n) the pair (Im V, Re V); below, those pairs
+      // per field before the depth factor.
+      const float2 sp = make_float2(c0.x + d0.x, c0.y + d0.y), dp = make_float2(c0.x - d0.x, c0.y - d0.y);
+      const float2 st = make_float2(c0.z + d0.z, c0.w + d0.w), df = make_float2(c0.z - d0.z, c0.w - d0.w);
+      const float2 Rf[4] = {make_float2(-kx * sp.y, -kx * sp.x), make_float2(-ky * dp.y, -ky * dp.x),
+                            make_float2(k * sp.x, -k * sp.y), make_float2(st.x, -st.y)};
+      const float2 If[4] = {make_float2(kx * dp.x, -kx * dp.y), make_float2(ky * sp.x, -ky * sp.y),
+                            make_float2(k * dp.y, k * dp.x), make_float2(df.y, df.x)};
       unsigned char* bhi = bst + size_t(s) * kTcStageBytes;
       unsigned char* blo = bhi + kTcBBytes;
-      const int m = kc * kTcModes + lane;
-      const float kx = float(m) * a.kxs;
+      auto put = [&](int cj, float2 re, float2 im) {
+        unsigned h0, l0, h1, l1;
+        bf2_split_p(re, h0, l0);
+        bf2_split_p(im, h1, l1);
+        const uint32_t o0 = off + uint32_t(cj) * kTcSBO;
+        *reinterpret_cast<unsigned*>(bhi + o0) = h0;
+        *reinterpret_cast<unsigned*>(blo + o0) = l0;
+        *reinterpret_cast<unsigned*>(bhi + o0 + 16) = h1;
+        *reinterpret_cast<unsigned*>(blo + o0 + 16) = l1;
+      };
 #pragma unroll
-      for (int t = 0; t < kPairsPerWarp; ++t) {
-        const int pw = pw0 + t, tr = g * kTcRows + pw;
-        const float ky = float(tr) * a.kys, k = c1[t].z;     // |k| is that of both rows
-        float F0, S0;
-        depth_fs(k, z0, h, c1[t].w, F0, S0);
-        const float k2 = 0.5f * k * k;
-        const float P[kTcTerms] = {F0, k * S0, k2 * F0};    // F(z0 + dz) orders 0..2 (u, v, phi_t)
-        const float Q[kTcTerms] = {S0, k * F0, k2 * S0};    // S(z0 + dz) orders 0..2 (w)
-        // rows n (c) and -n (d): sums and differences of A^phi, A^phit, A^eta. With
-        // W_u = i kx A^phi, W_v = i ky A^phi (ky negated on row -n), W_w = |k| A^phi,
-        // W_t = A^phit, U = W(n) + W(-n) and V = W(n) - W(-n), the column Re(T_n + T_-n) takes
-        // the K pair (Re U, -Im U) and the column Im(T_n - T_-n) the pair (Im V, Re V); below,
-        // those pairs per field before the depth factor.
-        const float4 A0 = c0[t], B0 = d0[t], A1 = c1[t], B1 = d1[t];
-        const float2 sp = make_float2(A0.x + B0.x, A0.y + B0.y), dp = make_float2(A0.x - B0.x, A0.y - B0.y);
-        const float2 st = make_float2(A0.z + B0.z, A0.w + B0.w), df = make_float2(A0.z - B0.z, A0.w - B0.w);
-        const float2 Rf[4] = {make_float2(-kx * sp.y, -kx * sp.x), make_float2(-ky * dp.y, -ky * dp.x),
-                              make_float2(k * sp.x, -k * sp.y), make_float2(st.x, -st.y)};
-        const float2 If[4] = {make_float2(kx * dp.x, -kx * dp.y), make_float2(ky * sp.x, -ky * sp.y),
-                              make_float2(k * dp.y, k * dp.x), make_float2(df.y, df.x)};
-        // this pair's two 16-byte rows in the core matrix of each 16-column block
-        const uint32_t off = uint32_t(lane >> 2) * kTcLBO + uint32_t(pw >> 2) * kTcSBO +
-                             uint32_t((2 * pw) & 7) * 16u + uint32_t(lane & 3) * 4u;
-        auto put = [&](int cj, float2 re, float2 im) {
-          unsigned h0, l0, h1, l1;
-          bf2_split_p(re, h0, l0);
-          bf2_split_p(im, h1, l1);
-          const uint32_t o0 = off + uint32_t(2 * cj) * kTcSBO;
-          *reinterpret_cast<unsigned*>(bhi + o0) = h0;
-          *reinterpret_cast<unsigned*>(blo + o0) = l0;
-          *reinterpret_cast<unsigned*>(bhi + o0 + 16) = h1;
-          *reinterpret_cast<unsigned*>(blo + o0 + 16) = l1;
-        };
-#pragma unroll
-        for (int j = 0; j < kTcTerms; ++j) {
-          const float2 pj = make_float2(P[j], P[j]), qj = make_float2(Q[j], Q[j]);
-          put(0 * kTcTerms + j, pmul(Rf[0], pj), pmul(If[0], pj));
-          put(1 * kTcTerms + j, pmul(Rf[1], pj), pmul(If[1], pj));
-          put(2 * kTcTerms + j, pmul(Rf[2], qj), pmul(If[2], qj));
-          put(3 * kTcTerms + j, pmul(Rf[3], pj), pmul(If[3], pj));
-        }
-        put(4 * kTcTerms, make_float2(A1.x + B1.x, -(A1.y + B1.y)), make_float2(A1.y - B1.y, A1.x - B1.x));
+      for (int j = 0; j < kTcTerms; ++j) {
+        const float2 pj = make_float2(P[j], P[j]), qj = make_float2(Q[j], Q[j]);
+        put(0 * kTcTerms + j, pmul(Rf[0], pj), pmul(If[0], pj));
+        put(1 * kTcTerms + j, pmul(Rf[1], pj), pmul(If[1], pj));
+        put(2 * kTcTerms + j, pmul(Rf[2], qj), pmul(If[2], qj));
+        put(3 * kTcTerms + j, pmul(Rf[3], pj), pmul(If[3], pj));
       }
+      put(4 * kTcTerms, make_float2(c1.x + d1.x, -(c1.y + d1.y)), make_float2(c1.y - d1.y, c1.x - d1.x));
       fence_proxy_async();                          // generic-proxy stores -> the MMA's reads
-      mbar_arrive(&sh.b_full[s]);
-#pragma unroll
-      for (int t = 0; t < kPairsPerWarp; ++t) {
-        c0[t] = n0[t];
-        c1[t] = n1[t];
-        d0[t] = n2[t];
-        d1[t] = n3[t];
-      }
+      mbar_arrive_cluster(cluster_addr(&sh.b_full[s], 0u));
     }
-  } else {
+  } else if (rank == 0) {
+    // ================================================================ MMA issue (one thread)
     if (lane == 0) {
       bool ok = true;
       for (int kc = 0; kc < nkc && ok; ++kc) {
@@ -413,8 +442,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_direct_tc(TcArgs a) {
         if (!ok) break;
         tc::fence_after();
         for (int g = 0; g < ng; ++g) {
-          const int gi = kc * ng + g, s = gi & 1, d = gi & 1;
-          ok = thread_wait(&sh.b_full[s], unsigned(gi >> 1) & 1u, abort_flag);
+          const int gi = kc * ng + g, s = gi % kTcStages, d = gi & 1;
+          ok = thread_wait(&sh.b_full[s], unsigned(gi / kTcStages) & 1u, abort_flag);
           if (ok && gi >= 2) ok = thread_wait(&sh.d_empty[d], unsigned((gi >> 1) - 1) & 1u, abort_flag);
           if (!ok) break;
           tc::fence_after();
@@ -425,29 +454,32 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_direct_tc(TcArgs a) {
           for (int ks = 0; ks < kTcK / 16; ++ks) {
             const uint64_t dh = tc::smem_desc(bhi + 2 * ks * kTcLBO, kTcLBO, kTcSBO);
             const uint64_t dl = tc::smem_desc(blo + 2 * ks * kTcLBO, kTcLBO, kTcSBO);
-            tc::mma_ts(dacc, tbase + kColAhi + 8u * ks, dh, kIdesc, ks > 0 ? 1u : 0u);
-            tc::mma_ts(dacc, tbase + kColAhi + 8u * ks, dl, kIdesc, 1u);
-            tc::mma_ts(dacc, tbase + kColAlo + 8u * ks, dh, kIdesc, 1u);
+            tc::mma2_ts(dacc, tbase + kColAhi + 8u * ks, dh, kIdesc, ks > 0 ? 1u : 0u);
+            tc::mma2_ts(dacc, tbase + kColAhi + 8u * ks, dl, kIdesc, 1u);
+            tc::mma2_ts(dacc, tbase + kColAlo + 8u * ks, dh, kIdesc, 1u);
           }
-          tc::commit(&sh.b_empty[s]);
-          tc::commit(&sh.d_full[d]);
+          tc::commit2(&sh.b_empty[s], uint16_t(3));
+          tc::commit2(&sh.d_full[d], uint16_t(3));
         }
       }
-      tc::commit(&sh.fin);
+      tc::commit2(&sh.fin, uint16_t(3));            // every MMA issued above has completed
     }
     __syncwarp();
   }
 
-  // ---- teardown: the allocating warp frees tensor memory once every MMA has completed
-  tc::fence_before();
-  __syncthreads();
+  // ---- teardown: once every MMA of the pair has completed (fin, in both CTAs) and both CTAs
+  // are done with each other's barriers (cluster barrier), each frees its tensor memory
   if (warp == kMmaWarp) {
-    tc::fence_after();
     bool done = false;
-    for (int it = 0; it < kMbarPolls && !done; ++it) done = mbar_try_wait(&sh.fin, 0u);
+    for (int it = 0; it < kMbarPolls && !done; ++it) done = mbar_try_wait_cluster(&sh.fin, 0u);
     done = __all_sync(0xffffffffu, done);
     if (!done && lane == 0) atomicExch(&g_direct_timeout, 1);
-    tc::dealloc(tbase, kTmemCols);
+  }
+  tc::fence_before();
+  cluster_sync();
+  if (warp == kMmaWarp) {
+    tc::fence_after();
+    tc::dealloc2(tbase, kTmemCols);
   }
 }
 
@@ -760,9 +792,11 @@ int direct_tc(const swense_modes* md, double t, const float* pts, int64_t np, fl
   a.rho = float(rho);
   a.g = float(grav);
   a.tile_bad = bad;
-  const size_t smem = size_t(kTcStages) * kTcStageBytes + sizeof(TcShared);
+  a.ntiles = ntiles;
+  const size_t smem = std::max(size_t(kTcStages) * kTcStageBytes + kYTabBytes + sizeof(TcShared), kTcSmemMin);
   SWENSE_CUDA_TRY(cudaFuncSetAttribute(k_direct_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-  k_direct_tc<<<unsigned(ntiles), kTcThreads, smem, stream>>>(a);
+  // clusters of two CTAs: one per pair of tiles (the odd CTA of a last, unpaired tile has no points)
+  k_direct_tc<<<unsigned((ntiles + 1) / 2 * 2), kTcThreads, smem, stream>>>(a);
   SWENSE_CUDA_TRY(cudaGetLastError());
   count_launches(1);
   {

@@ -93,11 +93,16 @@ __device__ __forceinline__ float2 csub(float2 a, float2 b) {
   asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(c_as_u64(a)), "l"(c_as_u64(b)));
   return u64_as_c(d);
 }
-// Element-wise product of pairs as one packed instruction (x with x, y with y), rounded to
-// nearest like the scalar form.
+// Element-wise product (and fused product-sum) of pairs as one packed instruction (x with x,
+// y with y), rounded like the scalar forms.
 __device__ __forceinline__ float2 pmul(float2 a, float2 b) {
   unsigned long long d;
   asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(c_as_u64(a)), "l"(c_as_u64(b)));
+  return u64_as_c(d);
+}
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(c_as_u64(a)), "l"(c_as_u64(b)), "l"(c_as_u64(c)));
   return u64_as_c(d);
 }
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {

@@ -31,6 +31,21 @@ __device__ __forceinline__ void dealloc(uint32_t taddr, uint32_t ncols) {
   asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
 
+// The same for a CTA pair (cta_group::2, a cluster of two CTAs): one warp of each CTA executes
+// it; the pair's tensor memory is allocated at the same columns in both CTAs.
+__device__ __forceinline__ void alloc2(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   static_cast<unsigned>(__cvta_generic_to_shared(dst))),
+               "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void relinquish2() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void dealloc2(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
 // ---------------------------------------------------------------- ordering
 __device__ __forceinline__ void fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -83,6 +98,29 @@ __device__ __forceinline__ void mma_ss(uint32_t d_tmem, uint64_t a_desc, uint64_
       "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
+// CTA-pair MMA (issued by one thread of the pair's even CTA): D (M = 256) += A x B with A's rows
+// 0..127 in the even CTA's tensor memory and 128..255 in the odd CTA's (same columns), B's
+// columns 0..N/2-1 in the even CTA's shared memory and N/2..N-1 in the odd CTA's (same
+// offsets, each half in the K-major core-matrix layout of b_desc), D's rows in each CTA's own
+// tensor memory at d_tmem.
+__device__ __forceinline__ void mma2_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc,
+                                        uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::2.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// The mbarrier at the same offset in every CTA of cta_mask receives one arrival when every
+// earlier tcgen05 operation of the pair issued by this thread has completed.
+__device__ __forceinline__ void commit2(uint64_t* bar, uint16_t cta_mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          static_cast<unsigned>(__cvta_generic_to_shared(bar))),
+      "h"(cta_mask)
+      : "memory");
+}
+
 // The mbarrier receives one arrival when every earlier tcgen05 operation of this thread has
 // completed (a CTA's own shared address is a valid shared::cluster address).
 __device__ __forceinline__ void commit(uint64_t* bar) {
