@@ -330,6 +330,11 @@ NCU_TRAFFIC = {
 
 
 DIRECT_KERNEL = "k_direct_tc"
+DIRECT_SOURCES = ("csrc/direct_tc.cu", "csrc/tcgen05.cuh", "csrc/tma.cuh", "csrc/internal.cuh")
+NCU_TRAFFIC[DIRECT_KERNEL] = {
+    # ncu --set full, one launch: 1,000,000 near-body points x the 2048 x 1024-mode sea
+    "bytes": 59017216 + 9168128, "hash": "5b817db64d0f620f",
+    "workload": "near-body 1000000 points x 2048x1024 modes"}
 # Algorithmic MMA flops of the split-BF16 direct sum (the per-unit figure of the workload's
 # definition): per (point, mode) pair of the full nx x ny spectrum, u, v, w and dphi/dt each the
 # real part of a complex product (2 MACs over the mode's re/im) in three BF16 products (hi.hi,
@@ -339,9 +344,20 @@ DIRECT_FLOP_NOTE = ("per (point, mode) pair 48 flop: 4 fields x 2 MACs (re/im of
                     "x 3 split products; pairs = near-body points x nx x ny modes (full spectrum)")
 
 
+def direct_traffic(nn, sea):
+    """ncu DRAM bytes of one k_direct_tc launch, when the kernel's sources and the workload are
+    those of the capture (else None)."""
+    tr = NCU_TRAFFIC.get(DIRECT_KERNEL)
+    desc = f"near-body {nn} points x {sea['nx']}x{sea['ny']} modes"
+    if tr and tr["hash"] == kernel_source_hash(DIRECT_SOURCES) and tr["workload"] == desc:
+        return tr["bytes"]
+    return None
+
+
 def direct_tc_issued_flop(nx, ny, tiles):
-    """MMA flops k_direct_tc issues for `tiles` tiles of 128 points: per K-chunk of 32 modes and
-    group of 8 mode-row pairs (n, -n), 3 products of 128 x 208 x 64 (padded as the kernel pads)."""
+    """MMA flops k_direct_tc issues for `tiles` tiles of 128 points (two tiles, one CTA pair, per
+    M = 256 MMA): per tile, K-chunk of 32 modes and group of 8 mode-row pairs (n, -n), 3
+    products of 128 x 208 x 64 (padded as the kernel pads)."""
     mp = -(-(nx // 2) // 32) * 32
     pairs = -(-(ny // 2) // 8) * 8 if ny > 1 else 8
     return tiles * (mp // 32) * (pairs // 8) * 3 * 2.0 * 128 * 208 * 64
@@ -1395,7 +1411,7 @@ def run_large(args, rank, world):
         ach = direct_flop / (d_ms * 1e-3) / 1e12
         roofline = {"bound": "tensor", "kernel": DIRECT_KERNEL, "achieved": ach, "peak": tens_peak,
                     "unit": "TFLOP/s", "frac": ach / tens_peak,
-                    "traffic": NCU_TRAFFIC.get(DIRECT_KERNEL, {}).get("bytes"),
+                    "traffic": direct_traffic(nn, sea),
                     "peak_source": "measured (MEASURED_PEAKS.json bf16_tflops_sustained: the kernel "
                                    "runs for hundreds of ms)" if peaks else "fallback 1.7 PFLOP/s",
                     "algorithmic": DIRECT_FLOP_NOTE}
@@ -1420,6 +1436,8 @@ def run_large(args, rank, world):
         "points_fields_per_s": value * 5,
         "roofline": roofline, "stages": stages_out,
         "gpu_launches": int(launches), "clocks": clk, "wall_s_timed": t_wall,
+        "kernel_hash": {"direct": kernel_source_hash(DIRECT_SOURCES), "grid": kernel_source_hash(GRID_SOURCES),
+                        "gather": kernel_source_hash(GATHER_SOURCES)},
     }
 
     # ---- end to end through the public API with host buffers
