@@ -47,8 +47,8 @@ constexpr int kTcCj = 4 * kTcTerms + 1;               // 13 complex outputs per 
 constexpr int kTcN = kTcRows * 2 * kTcCj;             // 208 MMA columns
 constexpr int kTcHalfRows = kTcRows / 2;              // row pairs whose B columns a CTA makes
 constexpr int kTcNh = kTcN / 2;                       // 104 B columns per CTA
-constexpr int kTcModes = 32;                          // modes m per K-chunk
-constexpr int kTcK = 2 * kTcModes;                    // 64 K (re, im per mode)
+constexpr int kTcModes = 64;                          // modes m per K-chunk (one group's K)
+constexpr int kTcK = 2 * kTcModes;                    // 128 K (re, im per mode)
 // B layout (each CTA's half, columns nc = 8 cj + 2 pair + {0: Re(T_n + T_-n), 1: Im(T_n - T_-n)}
 // for its 4 row pairs): one core matrix (8 columns x 8 K, 128 bytes) per output cj; k-blocks of
 // 8 K are kTcLBO bytes apart (13 core matrices + 16 bytes, so that the 32 lanes of a producer
@@ -58,20 +58,26 @@ constexpr int kTcSBO = 128;
 constexpr int kTcLBO = (kTcNh / 8) * 128 + 16;
 constexpr int kTcBBytes = (kTcK / 8) * kTcLBO;        // one of hi / lo
 constexpr int kTcStageBytes = 2 * kTcBBytes;
-constexpr int kTcStages = 4;
+constexpr int kTcStages = 2;
+// A's lo half (this CTA's 128 points x K) in shared memory, K-major core matrices: 16 along M
+// per k-block, k-blocks kTcALBO bytes apart; its hi half is in tensor memory (columns 0..63).
+// Tensor memory then holds A hi and two accumulators (64 + 2 x 208 of 512 columns), and the
+// epilogue reads each accumulator once per 64 modes.
+constexpr int kTcALBO = (kTcM / 8) * 128 + 16;
+constexpr int kTcABytes = (kTcK / 8) * kTcALBO;
 // per point, the row anchors Y^(8 j) (j < kYLo) of its groups: one group's first row in 64
 constexpr int kYLo = 64;
 constexpr int kYTabBytes = kYLo * kTcM * 8;
 // 13 warps per CTA: 4 epilogue warps (one point each), 8 producer warps (two per row pair of
-// this CTA's half, taking the even and the odd groups, so that one warp's fence before its
-// arrival overlaps the other's work), 1 MMA warp (the even CTA's lane 0 issues for the pair; the
-// warp owns the tensor-memory allocation in both CTAs)
+// this CTA's half, one per 32 modes of a group), 1 MMA warp (the even CTA's lane 0 issues for the
+// pair; the warp owns the tensor-memory allocation in both CTAs)
 constexpr int kEpiWarps = 4, kProdWarps = 8;
-static_assert(kProdWarps == 2 * kTcHalfRows, "two producer warps per row pair");
+constexpr int kModeHalves = kTcModes / 32;
+static_assert(kProdWarps == kModeHalves * kTcHalfRows, "one (row pair, 32 modes) block per producer warp");
 constexpr int kMmaWarp = kEpiWarps + kProdWarps;
 constexpr int kTcThreads = (kMmaWarp + 1) * 32;
 constexpr uint32_t kTmemCols = 512;
-constexpr uint32_t kColAhi = 0, kColAlo = kTcK / 2, kColD0 = kTcK, kColD1 = kTcK + kTcN;
+constexpr uint32_t kColAhi = 0, kColD0 = kTcK / 2, kColD1 = kTcK / 2 + kTcN;
 constexpr float kKappaMax = 0.02f;
 constexpr int kZBuckets = 1 << 16;
 constexpr uint32_t kIdesc = tc::idesc_bf16_f32(2 * kTcM, kTcN);
@@ -80,6 +86,7 @@ constexpr uint32_t kIdesc = tc::idesc_bf16_f32(2 * kTcM, kTcN);
 constexpr size_t kTcSmemMin = 120 * 1024;
 static_assert(kTcN % 16 == 0 && kTcN <= 256 && kTcNh % 8 == 0, "MMA N for M = 256");
 static_assert(kColD1 + kTcN <= kTmemCols, "tensor-memory columns");
+static_assert(kTcStages * kTcStageBytes + kTcABytes + kYTabBytes + 2048 <= 227 * 1024, "shared memory");
 
 // Set when a bounded wait of k_direct_tc gave up (read by swense_async_status).
 __device__ int g_direct_timeout;
@@ -185,8 +192,9 @@ struct TcShared {
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1) k_direct_tc(TcArgs a) {
   extern __shared__ __align__(1024) unsigned char smraw[];
   unsigned char* bst = smraw;                                   // kTcStages x (B hi, B lo)
-  float2* ytab = reinterpret_cast<float2*>(smraw + kTcStages * kTcStageBytes);   // [kYLo][kTcM]
-  TcShared& sh = *reinterpret_cast<TcShared*>(smraw + kTcStages * kTcStageBytes + kYTabBytes);
+  unsigned char* alo = smraw + kTcStages * kTcStageBytes;        // A lo (this CTA's points)
+  float2* ytab = reinterpret_cast<float2*>(alo + kTcABytes);       // [kYLo][kTcM]
+  TcShared& sh = *reinterpret_cast<TcShared*>(alo + kTcABytes + kYTabBytes);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned rank = cluster_rank();                          // 0: even CTA, 1: odd CTA
   const int64_t tile = blockIdx.x;                               // rank == blockIdx.x & 1
@@ -227,7 +235,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1) k_dir
   if (threadIdx.x == 0) {
     if (tile < a.ntiles) a.tile_bad[tile] = 0;
     for (int s = 0; s < kTcStages; ++s) {
-      mbar_init(&sh.b_full[s], 2 * kTcHalfRows);    // one arrival per producer warp of the group
+      mbar_init(&sh.b_full[s], 2 * kProdWarps);     // one arrival per producer warp
       mbar_init(&sh.b_empty[s], 1);
     }
     for (int d = 0; d < 2; ++d) {
@@ -326,9 +334,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1) k_dir
       }
     };
 
-    // A = X_m(p) of a K-chunk's 32 modes: word j = (cos, sin) as BF16 (hi, then the lo residual)
+    // A = X_m(p) of a K-chunk's 64 modes: word j = (cos, sin) of mode j as BF16, the hi halves
+    // into tensor memory (column j), the lo residuals into shared memory (K pair j: k-block j / 4,
+    // word j % 4 of this point's 16-byte row)
     auto write_a = [&](int kc) {
-#pragma unroll
+      unsigned char* arow = alo + (t >> 3) * 128 + (t & 7) * 16;
+#pragma unroll 1
       for (int h = 0; h < kTcModes / 16; ++h) {
         uint32_t whi[16], wlo[16];
 #pragma unroll
@@ -340,9 +351,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1) k_dir
           bf2_split(c, s, whi[j], wlo[j]);
         }
         tc::st_x16(lanebase + kColAhi + 16u * h, whi);
-        tc::st_x16(lanebase + kColAlo + 16u * h, wlo);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          *reinterpret_cast<uint4*>(arow + (4 * h + q) * kTcALBO) =
+              make_uint4(wlo[4 * q], wlo[4 * q + 1], wlo[4 * q + 2], wlo[4 * q + 3]);
       }
       tc::wait_st();
+      fence_proxy_async();                          // A lo: generic-proxy stores -> the MMA's reads
       tc::fence_before();
       pair_arrive(&sh.a_ready, lane);
     };
@@ -390,21 +405,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1) k_dir
   } else if (warp < kMmaWarp) {
     // ================================================================ producers: B per group
     const int pw = (warp - kEpiWarps) % kTcHalfRows;   // this CTA's row pair of the group
-    const int par = (warp - kEpiWarps) / kTcHalfRows;  // this warp's groups: gi = par (mod 2)
+    const int mh = (warp - kEpiWarps) / kTcHalfRows;   // this warp's 32 modes of the group's 64
     const int pr = int(rank) * kTcHalfRows + pw;    // the pair's row pair
     const float h = a.depth;
-    // this lane's mode is K pair `lane`: k-block lane / 4, word lane % 4 of a 16-byte row; this
-    // pair's two rows (Re, Im) in each output's core matrix
-    const uint32_t off = uint32_t(lane >> 2) * kTcLBO + uint32_t(2 * pw) * 16u + uint32_t(lane & 3) * 4u;
-    int g = par, kc = 0;
-    while (g >= ng) {
-      g -= ng;
-      ++kc;
-    }
-    for (int gi = par; gi < ngi; gi += 2) {
+    // this lane's mode is K pair 32 mh + lane: k-block 8 mh + lane / 4, word lane % 4 of a
+    // 16-byte row; this pair's two rows (Re, Im) in each output's core matrix
+    const uint32_t off = uint32_t(8 * mh + (lane >> 2)) * kTcLBO + uint32_t(2 * pw) * 16u + uint32_t(lane & 3) * 4u;
+    int g = 0, kc = 0;
+    for (int gi = 0; gi < ngi; ++gi) {
       const int s = gi % kTcStages;
       const int tr = g * kTcRows + pr;              // mode rows n = tr and -tr
-      const int m = kc * kTcModes + lane;
+      const int m = kc * kTcModes + 32 * mh + lane;
       const float4* tp = &a.tab[4 * (size_t(tr) * a.mp + size_t(m))];
       const float4 c0 = __ldg(tp), c1 = __ldg(tp + 1), d0 = __ldg(tp + 2), d1 = __ldg(tp + 3);
       if (gi >= kTcStages &&
@@ -456,7 +467,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1) k_dir
       put(4 * kTcTerms, make_float2(c1.x + d1.x, -(c1.y + d1.y)), make_float2(c1.y - d1.y, c1.x - d1.x));
       fence_proxy_async();                          // generic-proxy stores -> the MMA's reads
       pair_arrive(&sh.b_full[s], lane);
-      for (g += 2; g >= ng; g -= ng) ++kc;
+      if (++g == ng) {
+        g = 0;
+        ++kc;
+      }
     }
   } else if (rank == 0) {
     // ================================================================ MMA issue (one thread)
@@ -481,7 +495,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1) k_dir
             const uint64_t dl = tc::smem_desc(blo + 2 * ks * kTcLBO, kTcLBO, kTcSBO);
             tc::mma2_ts(dacc, tbase + kColAhi + 8u * ks, dh, kIdesc, ks > 0 ? 1u : 0u);
             tc::mma2_ts(dacc, tbase + kColAhi + 8u * ks, dl, kIdesc, 1u);
-            tc::mma2_ts(dacc, tbase + kColAlo + 8u * ks, dh, kIdesc, 1u);
+            tc::mma2_ss(dacc, tc::smem_desc(alo + 2 * ks * kTcALBO, kTcALBO, 128u), dh, kIdesc, 1u);
           }
           tc::commit2(&sh.b_empty[s], uint16_t(3));
           tc::commit2(&sh.d_full[d], uint16_t(3));
@@ -818,7 +832,8 @@ int direct_tc(const swense_modes* md, double t, const float* pts, int64_t np, fl
   a.g = float(grav);
   a.tile_bad = bad;
   a.ntiles = ntiles;
-  const size_t smem = std::max(size_t(kTcStages) * kTcStageBytes + kYTabBytes + sizeof(TcShared), kTcSmemMin);
+  const size_t smem =
+      std::max(size_t(kTcStages) * kTcStageBytes + kTcABytes + kYTabBytes + sizeof(TcShared), kTcSmemMin);
   SWENSE_CUDA_TRY(cudaFuncSetAttribute(k_direct_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
   // clusters of two CTAs: one per pair of tiles (the odd CTA of a last, unpaired tile has no points)
   k_direct_tc<<<unsigned((ntiles + 1) / 2 * 2), kTcThreads, smem, stream>>>(a);
