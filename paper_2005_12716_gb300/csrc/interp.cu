@@ -547,9 +547,34 @@ __global__ void __launch_bounds__(BOX_THREADS) k_interp_plan(InterpArgs a, Level
   plan_chunk<P2>(a, zs, int64_t(blockIdx.x) * PLAN_WARPS + warp, plan, lane);
 }
 
-// Gather of chunk `chunk` of the points of `a` with its plan `pl`, by the whole CTA; the level
-// tables zs are complete after the first barrier inside.
+// True when a chunk's plan stages no tile (or is a plan made for another level list): its points
+// gather their stencils from global memory.
+__device__ __forceinline__ bool plan_is_global(const int4 pl, int nz) {
+  if (pl.w < 0) return true;
+  const BoxPlan bp = decode_plan(pl);
+  return bp.l0 + bp.bz > nz;
+}
+
+// Points p0 + k * BOX_THREADS + threadIdx.x (k < BOX_PPT) gathered from global memory.
 template <bool P2>
+__device__ __forceinline__ void global_points(const InterpArgs& a, const LevelTables& zs, int64_t p0) {
+#pragma unroll 1
+  for (int k = 0; k < BOX_PPT; ++k) {
+    const int64_t i = p0 + k * BOX_THREADS + threadIdx.x;
+    if (i >= a.np) break;                           // later points of this thread are past np too
+    const float pz = __ldg(&a.pts[3 * i + 2]);
+    const PointCell c = point_cell<P2>(a, zs, __ldg(&a.pts[3 * i]), __ldg(&a.pts[3 * i + 1]), pz);
+    float4 acc;
+    float acc_eta;
+    gather_global<P2>(a, c, acc, acc_eta);
+    store_point(a, i, acc, acc_eta, pz, c.inside);
+  }
+}
+
+// Gather of chunk `chunk` of the points of `a` with its plan `pl`, by the whole CTA; the level
+// tables zs are complete after the first barrier inside. kGlobal: also the chunks without a
+// staged tile (else those are left to k_interp_global).
+template <bool P2, bool kGlobal = true>
 __device__ __forceinline__ void box_chunk(const InterpArgs& a, const LevelTables& zs, int64_t chunk,
                                           const int4 pl, float4* sbox, float* seta) {
   const int64_t p0 = chunk * BOX_PTS;
@@ -565,19 +590,9 @@ __device__ __forceinline__ void box_chunk(const InterpArgs& a, const LevelTables
     }
   }
   const BoxPlan bp = decode_plan(pl);
-  if (pl.w < 0 || bp.l0 + bp.bz > a.nz) {           // no tile, or a plan of another level list
+  if (plan_is_global(pl, a.nz)) {                  // no tile, or a plan of another level list
     __syncthreads();
-#pragma unroll 1
-    for (int k = 0; k < BOX_PPT; ++k) {
-      const int64_t i = p0 + k * BOX_THREADS + threadIdx.x;
-      if (i >= a.np) continue;
-      const float pz = __ldg(&a.pts[3 * i + 2]);
-      const PointCell c = point_cell<P2>(a, zs, __ldg(&a.pts[3 * i]), __ldg(&a.pts[3 * i + 1]), pz);
-      float4 acc;
-      float acc_eta;
-      gather_global<P2>(a, c, acc, acc_eta);
-      store_point(a, i, acc, acc_eta, pz, c.inside);
-    }
+    if (kGlobal) global_points<P2>(a, zs, p0);
     return;
   }
   const int bx = bp.bx, by = bp.by, bz = bp.bz;
@@ -699,14 +714,34 @@ __device__ __forceinline__ void box_chunk(const InterpArgs& a, const LevelTables
   }
 }
 
+// The chunks with a staged tile (box, plane or two planes); k_interp_global takes the others.
 template <bool P2>
 __global__ void __launch_bounds__(BOX_THREADS, 3) k_interp_box(InterpArgs a, Levels L,
                                                                 const int4* __restrict__ plan) {
   extern __shared__ float4 sbox[];
   float* seta = reinterpret_cast<float*>(sbox + BOX_NODES);
   __shared__ LevelTables zs;
+  const int4 pl = plan[blockIdx.x];
+  if (plan_is_global(pl, a.nz)) return;             // uniform over the CTA
   fill_level_tables(zs, L, a.nz);
-  box_chunk<P2>(a, zs, blockIdx.x, plan[blockIdx.x], sbox, seta);
+  box_chunk<P2, false>(a, zs, blockIdx.x, pl, sbox, seta);
+}
+
+// The chunks without a staged tile (scattered points: the stencils of a 1024-point chunk span
+// more nodes than shared memory holds). No dynamic shared memory, so that L1 keeps the rows
+// neighbouring points share: launched apart from k_interp_box, whose 68 KB tile per CTA would
+// leave L1 a fifth of its size.
+// One chunk per CTA, in chunk order (the CTAs in flight then cover consecutive chunks, whose
+// stencils share rows in L2); the chunks with a staged tile exit at once.
+template <bool P2>
+__global__ void __launch_bounds__(BOX_THREADS, 4) k_interp_global(InterpArgs a, Levels L,
+                                                                   const int4* __restrict__ plan) {
+  __shared__ LevelTables zs;
+  const int4 pl = plan[blockIdx.x];
+  if (!plan_is_global(pl, a.nz)) return;            // uniform over the CTA
+  fill_level_tables(zs, L, a.nz);
+  __syncthreads();
+  global_points<P2>(a, zs, int64_t(blockIdx.x) * BOX_PTS);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -1361,8 +1396,10 @@ int interp_impl(const swense_grid* g, double t, const float* pts, const int32_t*
     SWENSE_CUDA_TRY(cudaFuncSetAttribute(kbox, cudaFuncAttributeMaxDynamicSharedMemorySize, int(BOX_SMEM)));
     if (a.p2) k_interp_box<true><<<unsigned(blocks), BOX_THREADS, BOX_SMEM, stream>>>(a, lev, plan);
     else k_interp_box<false><<<unsigned(blocks), BOX_THREADS, BOX_SMEM, stream>>>(a, lev, plan);
+    if (a.p2) k_interp_global<true><<<unsigned(blocks), BOX_THREADS, 0, stream>>>(a, lev, plan);
+    else k_interp_global<false><<<unsigned(blocks), BOX_THREADS, 0, stream>>>(a, lev, plan);
     SWENSE_CUDA_TRY(cudaGetLastError());
-    count_launches(1);
+    count_launches(2);
   }
   if (n_out_of_range) {
     unsigned long long h = 0;
