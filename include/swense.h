@@ -622,6 +622,17 @@ int swense_async_status(int32_t reset, void* stream);
 int swense_selftest_wait_timeout(void* stream);
 
 /*
+ * swense_selftest_direct_wait_timeout — self-test switch of the tensor-core direct sum's bounded
+ * waits (no passage of the paper: library housekeeping). While on (on != 0) for the current
+ * device, every SWENSE_DIRECT_SPLIT_BF16 call runs k_direct_tc with its A-ready arrivals withheld
+ * and a limit of a few polls per wait: the MMA thread's first wait runs out, the pair aborts
+ * without issuing an MMA, its tiles' outputs are not written, and swense_async_status then
+ * returns SWENSE_ERR_TIMEOUT. Switch it off (on = 0) before any real call. Errors: UNSUPPORTED,
+ * CUDA.
+ */
+int swense_selftest_direct_wait_timeout(int32_t on);
+
+/*
  * swense_direct_stats — tiles of the last SWENSE_DIRECT_SPLIT_BF16 call on the current device
  * (no passage of the paper): *tiles = tiles of 128 z-sorted points, *fallback_tiles = those whose
  * z range was too wide for the tensor-core expansion and went to the per-pair kernel (0 and 0

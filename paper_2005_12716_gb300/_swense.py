@@ -123,6 +123,7 @@ _SIGS = {
     "swense_launches": (ctypes.c_int64, []),
     "swense_async_status": (ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p]),
     "swense_selftest_wait_timeout": (ctypes.c_int, [ctypes.c_void_p]),
+    "swense_selftest_direct_wait_timeout": (ctypes.c_int, [ctypes.c_int32]),
     "swense_direct_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "swense_selftest_tc_gemm": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
@@ -343,6 +344,10 @@ def swense_async_status(reset=True, stream=None, raise_on_error=True):
 
 def swense_selftest_wait_timeout(stream=None):
     _check(load().swense_selftest_wait_timeout(_stream(stream)))
+
+
+def swense_selftest_direct_wait_timeout(on):
+    _check(load().swense_selftest_direct_wait_timeout(1 if on else 0))
 
 
 def swense_direct_stats(stream=None):

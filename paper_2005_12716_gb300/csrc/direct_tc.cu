@@ -105,6 +105,8 @@ struct TcArgs {
   float rho, g;
   uint8_t* tile_bad;        // [ntiles]: 1 = left to the per-pair kernel
   int64_t ntiles;
+  int polls;                // polls of a bounded wait (kMbarPolls; a few for the self-test)
+  int withhold_a;           // self-test: A's arrivals are withheld, so the MMA's first wait runs out
 };
 
 // Table row q holds the mode rows n = q and n = -q (q = 0 .. ny/2 - 1; row -0 and the rows past
@@ -141,9 +143,9 @@ __device__ __forceinline__ void depth_fs(float k, float z, float h, float invd, 
 // Warp-collective bounded wait: every lane polls; the warp succeeds only together. A wait that
 // gives up (or sees another role give up) sets the CTA's abort flag and the device flag. The
 // waits acquire at cluster scope: arrivals come from both CTAs of the pair.
-__device__ __forceinline__ bool warp_wait(uint64_t* bar, unsigned parity, volatile int* abort_flag) {
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, unsigned parity, volatile int* abort_flag, int polls) {
   bool ok = false;
-  for (int it = 0; it < kMbarPolls; ++it) {
+  for (int it = 0; it < polls; ++it) {
     if (mbar_try_wait_cluster(bar, parity)) {
       ok = true;
       break;
@@ -157,8 +159,8 @@ __device__ __forceinline__ bool warp_wait(uint64_t* bar, unsigned parity, volati
   }
   return ok;
 }
-__device__ __forceinline__ bool thread_wait(uint64_t* bar, unsigned parity, volatile int* abort_flag) {
-  for (int it = 0; it < kMbarPolls; ++it) {
+__device__ __forceinline__ bool thread_wait(uint64_t* bar, unsigned parity, volatile int* abort_flag, int polls) {
+  for (int it = 0; it < polls; ++it) {
     if (mbar_try_wait_cluster(bar, parity)) return true;
     if ((it & 31) == 31 && (*abort_flag || *(volatile int*)&g_direct_timeout)) {
       *abort_flag = 1;
@@ -359,7 +361,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1) k_dir
       tc::wait_st();
       fence_proxy_async();                          // A lo: generic-proxy stores -> the MMA's reads
       tc::fence_before();
-      pair_arrive(&sh.a_ready, lane);
+      if (!a.withhold_a) pair_arrive(&sh.a_ready, lane);
     };
     write_a(0);
     bool ok = true;
@@ -372,7 +374,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1) k_dir
           sincospif(2.f * (float(int(ph)) * 2.3283064365386963e-10f), &yhi.y, &yhi.x);
         }
       }
-      ok = warp_wait(&sh.d_full[gi & 1], unsigned(gi >> 1) & 1u, abort_flag);
+      ok = warp_wait(&sh.d_full[gi & 1], unsigned(gi >> 1) & 1u, abort_flag, a.polls);
       if (!ok) break;
       tc::fence_after();
       // the last group of a chunk is done, so are all MMAs reading this chunk's A: the next
@@ -419,7 +421,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1) k_dir
       const float4* tp = &a.tab[4 * (size_t(tr) * a.mp + size_t(m))];
       const float4 c0 = __ldg(tp), c1 = __ldg(tp + 1), d0 = __ldg(tp + 2), d1 = __ldg(tp + 3);
       if (gi >= kTcStages &&
-          !warp_wait(&sh.b_empty[s], unsigned(gi / kTcStages - 1) & 1u, abort_flag))
+          !warp_wait(&sh.b_empty[s], unsigned(gi / kTcStages - 1) & 1u, abort_flag, a.polls))
         break;
       const float kx = float(m) * a.kxs, ky = float(tr) * a.kys, k = c1.z;   // |k| is that of both rows
       float F0, S0;
@@ -477,13 +479,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1) k_dir
     if (lane == 0) {
       bool ok = true;
       for (int kc = 0; kc < nkc && ok; ++kc) {
-        ok = thread_wait(&sh.a_ready, unsigned(kc) & 1u, abort_flag);
+        ok = thread_wait(&sh.a_ready, unsigned(kc) & 1u, abort_flag, a.polls);
         if (!ok) break;
         tc::fence_after();
         for (int g = 0; g < ng; ++g) {
           const int gi = kc * ng + g, s = gi % kTcStages, d = gi & 1;
-          ok = thread_wait(&sh.b_full[s], unsigned(gi / kTcStages) & 1u, abort_flag);
-          if (ok && gi >= 2) ok = thread_wait(&sh.d_empty[d], unsigned((gi >> 1) - 1) & 1u, abort_flag);
+          ok = thread_wait(&sh.b_full[s], unsigned(gi / kTcStages) & 1u, abort_flag, a.polls);
+          if (ok && gi >= 2)
+            ok = thread_wait(&sh.d_empty[d], unsigned((gi >> 1) - 1) & 1u, abort_flag, a.polls);
           if (!ok) break;
           tc::fence_after();
           const uint32_t dacc = tbase + (d ? kColD1 : kColD0);
@@ -755,6 +758,8 @@ struct TcLast {
   int64_t ntiles = 0;
 };
 TcLast g_tc_last[64];
+// self-test of the bounded waits, per device (swense_selftest_direct_wait_timeout)
+bool g_tc_selftest[64];
 
 // The tensor-core path of swense_direct (precision SWENSE_DIRECT_SPLIT_BF16): z sort, mode table,
 // k_direct_tc over tiles of 128 sorted points, and the per-pair split kernel for the tiles it
@@ -831,6 +836,16 @@ int direct_tc(const swense_modes* md, double t, const float* pts, int64_t np, fl
   a.rho = float(rho);
   a.g = float(grav);
   a.tile_bad = bad;
+  a.polls = kMbarPolls;
+  a.withhold_a = 0;
+  {
+    int dev = 0;
+    SWENSE_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev >= 0 && dev < 64 && g_tc_selftest[dev]) {
+      a.polls = 8;
+      a.withhold_a = 1;
+    }
+  }
   a.ntiles = ntiles;
   const size_t smem =
       std::max(size_t(kTcStages) * kTcStageBytes + kTcABytes + kYTabBytes + sizeof(TcShared), kTcSmemMin);
@@ -880,5 +895,13 @@ extern "C" int swense_selftest_tc_gemm(const float* A, const float* B, float* D,
   k_tc_selftest<<<1, 128, smem, stream>>>(A, B, D, N, K, variant);
   SWENSE_CUDA_TRY(cudaGetLastError());
   count_launches(1);
+  return SWENSE_OK;
+}
+
+extern "C" int swense_selftest_direct_wait_timeout(int32_t on) {
+  int dev = 0;
+  SWENSE_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(SWENSE_ERR_UNSUPPORTED, "device index too large");
+  g_tc_selftest[dev] = on != 0;
   return SWENSE_OK;
 }

@@ -59,3 +59,36 @@ def test_context_usable_after_timeout_and_staged_path_reports_ok(env):
         assert rel_linf_scaled(got[..., q], ref[..., q], vs, field="uvw"[q]) <= 1e-5
     assert rel_linf(got[..., 3], ref[..., 3]) <= 1e-5
     assert rel_linf(grid.eta[0].cpu().numpy(), ref_eta) <= 1e-5
+
+
+def test_direct_sum_wait_that_runs_out_is_reported(env):
+    """The tensor-core direct sum with its A-ready arrivals withheld and a few polls per wait:
+    every CTA pair aborts without issuing an MMA, the call itself returns, the host reads
+    SWENSE_ERR_TIMEOUT, and with the switch off the same call is exact again."""
+    torch, S, api = env
+    from tests._util import velocity_scale as vscale
+    sea = configs.jonswap3d_small()["sea"]
+    rng = np.random.default_rng(3)
+    pts = np.stack([rng.uniform(0, sea["Lx"], 1024), rng.uniform(0, sea["Ly"], 1024),
+                    np.full(1024, -0.2)], 1).astype(np.float32)      # one z: every pair on the tensor path
+    modes = api.upload_modes(sea)
+    d = torch.from_numpy(pts).cuda()
+    assert S.swense_async_status(reset=True) == 0
+    S.swense_selftest_direct_wait_timeout(True)
+    try:
+        api.direct(modes, 0.3, d, precision="split_bf16")
+        st = S.swense_async_status(reset=True, raise_on_error=False)
+    finally:
+        S.swense_selftest_direct_wait_timeout(False)
+    assert st == -6 and S.swense_strerror(st) == "SWENSE_ERR_TIMEOUT"
+    assert S.swense_async_status(reset=True) == 0
+    out = api.direct(modes, 0.3, d, precision="split_bf16")
+    assert S.swense_async_status(reset=True) == 0
+    tiles, fb = S.swense_direct_stats()
+    assert fb == 0
+    ref = modal.fields_at_points(modal.propagate(sea, 0.3), pts.astype(np.float64))
+    vs = vscale(ref["u"], ref["v"], ref["w"])
+    for k in ("eta", "u", "v", "w", "p"):
+        got = out[k].cpu().numpy()
+        err = rel_linf_scaled(got, ref[k], vs, field=k) if k in "uvw" else rel_linf(got, ref[k])
+        assert err <= 1e-4, (k, err)
