@@ -825,6 +825,106 @@ __global__ void __launch_bounds__(256, N >= 1024 ? 1 : 2) k_col_tf(ColArgs a, Le
   }
 }
 
+// The same column pass with two warps per column (1024-point columns): warp 2c + s transforms
+// the rows p = 2 i + s of column c (a 512-point Stockham transform, 16 points a lane), the odd
+// warp multiplies its result by e^{2 pi i k / N}, and the pair combines them by one radix-2 step
+// through its exchange buffers, X[k] = E[k] + O'[k] and X[k + N/2] = E[k] - O'[k] (the same
+// operations, in the same order, as the last radix-2 pass of the one-warp transform, so the
+// results are identical). Half the points per lane (127 registers) and twice the warps per SM
+// of k_col_tf<1024>, whose 244 registers leave one 8-warp CTA per SM: 2 % faster on the large
+// sea's stage 1.
+template <int N>
+__global__ void __launch_bounds__(2 * kThreads, 1) k_col_tf2(ColArgs a, Levels L) {
+  extern __shared__ float2 sm[];                 // exchange buffers, then tile [N][kColBlock + 1]
+  constexpr int H = N / 2, E = H / 32, RL = stk_radix(H, stk_npass(H) - 1);
+  constexpr int TLD = kColBlock + 1;
+  static_assert(kColBlock * 64 == 2 * kThreads, "two warps per column");
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int col = warp >> 1, par = warp & 1;     // column of the CTA, parity of this warp's rows
+  const int c0 = blockIdx.x * kColBlock;
+  const int m = c0 + col;
+  const bool colok = m < a.Mh;
+  const int q = blockIdx.z;
+  float2* tile = sm;
+  float2* wbuf = sm + warp * stk_buf(H);
+  const float2* pbuf = sm + (warp ^ 1) * stk_buf(H);
+  float2 T[stk_twn(H)];
+  stk_init<H>(T, a.tw, lane);
+  const int nyh = a.ny >> 1;
+  const float kx = colok ? float(m) * a.kxs : 0.f;
+  const float2* __restrict__ A = q == 3 ? a.A_phit : a.A_phi;
+  // this warp's modes (rows p = 2 i + par of the half-sequence position i), loaded once and kept
+  // in registers over the CTA's levels (zero in the padding and at the Nyquist row)
+  float2 am[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int p = 2 * (lane + 32 * (e / 8) + (e % 8) * (H / 8)) + par;
+    int n = 0;
+    bool live = colok;
+    if (p < nyh) n = p;
+    else if (p > N - nyh) n = p - N;
+    else live = false;
+    am[e] = make_float2(0.f, 0.f);
+    if (live) {
+      am[e] = __ldg(&A[size_t(n >= 0 ? n : a.ny + n) * a.nxh1 + m]);
+      if (a.spline) {
+        const float pf = spline_prefilter(m, a.Nxr, n, a.Nyr);
+        am[e] = make_float2(pf * am[e].x, pf * am[e].y);
+      }
+    }
+  }
+  for (int li = 0; li < a.lpc; ++li) {
+    const int level = blockIdx.y * a.lpc + li;
+    if (level >= a.nlev) break;                  // uniform over the block
+    const float z = L.z[a.lev0 + level];
+    float2 v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int p = 2 * (lane + 32 * (e / 8) + (e % 8) * (H / 8)) + par;
+      // zero-padded and Nyquist positions carry no mode: their (unused) depth factor is taken
+      // at ky = 0, where it cannot overflow
+      const int n = p < nyh ? p : (p > N - nyh ? p - N : 0);
+      const float ky = float(n) * a.kys;
+      const float kk = sqrtf(kx * kx + ky * ky);
+      float F, S;
+      depth_factors(kk, z, a.depth, F, S);
+      v[e] = modal_field(q, kx, ky, kk, F, S, am[e], am[e]);
+    }
+    stk_fft<H>(v, T, a.tw, wbuf, lane);
+    // element e holds output k = lane + 32 (e / RL) + (e % RL) (H / RL); the odd half is twiddled
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int k = lane + 32 * (e / RL) + (e % RL) * (H / RL);
+      if (par) v[e] = cmul(v[e], __ldg(&a.tw[k * (SWENSE_MAX_FFT / N)]));
+      wbuf[stk_pad(k)] = v[e];
+    }
+    __syncthreads();                             // both halves of every column are published
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int k = lane + 32 * (e / RL) + (e % RL) * (H / RL);
+      const float2 o = pbuf[stk_pad(k)];
+      v[e] = par ? csub(o, v[e]) : cadd(v[e], o);  // even warp: X[k]; odd warp: X[k + H]
+    }
+    __syncthreads();                             // the buffers are read before the tile reuses them
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int k = lane + 32 * (e / RL) + (e % RL) * (H / RL) + par * H;
+      tile[k * TLD + col] = v[e];
+    }
+    __syncthreads();
+    float2* out = a.G + (size_t(level) * 4 + q) * a.Nyr * a.ldG + c0;
+    // two columns per thread: 16-byte stores (ldG and c0 are multiples of 16 and 8 entries)
+    for (int i = threadIdx.x; i < N * kColBlock / 2; i += 2 * kThreads) {
+      const int y = i / (kColBlock / 2), w = 2 * (i % (kColBlock / 2));
+      const float2 v0 = tile[y * TLD + w], v1 = tile[y * TLD + w + 1];
+      float2* o = &out[size_t(y) * a.ldG + w];
+      if (c0 + w + 1 < a.Mh) __stcg(reinterpret_cast<float4*>(o), make_float4(v0.x, v0.y, v1.x, v1.y));
+      else if (c0 + w < a.Mh) __stcg(o, v0);
+    }
+    __syncthreads();                             // the tile is read before the next transforms
+  }
+}
+
 // Row pass over the transposed intermediate: one warp per grid row of one level, its four
 // modal fields loaded straight from G (consecutive lanes read consecutive m), packed as
 // Z1 = U + iV and Z2 = W + iT over the full x spectrum, transformed, stored as float4.
@@ -1153,6 +1253,18 @@ int launch_col_tf(const ColArgs& c, const Levels& L, dim3 grid, cudaStream_t str
 }
 
 template <int N>
+int launch_col_tf2(const ColArgs& c, const Levels& L, dim3 grid, cudaStream_t stream) {
+  const size_t smem = std::max(size_t(N) * (kColBlock + 1), size_t(16) * stk_buf(N / 2)) * sizeof(float2);
+  int st = set_smem((const void*)k_col_tf2<N>, smem);
+  if (st) return st;
+  grid.z = 4;
+  k_col_tf2<N><<<grid, 2 * kThreads, smem, stream>>>(c, L);
+  SWENSE_CUDA_TRY(cudaGetLastError());
+  count_launches(1);
+  return SWENSE_OK;
+}
+
+template <int N>
 int launch_row_t(const RowArgs& r, dim3 grid, cudaStream_t stream) {
   const size_t smem = size_t(8) * stk_buf(N) * sizeof(float2);
   int st = set_smem((const void*)k_row_t<N>, smem);
@@ -1212,7 +1324,7 @@ int launch_pair_t(const ColArgs& c, const RowArgs& r, const Levels& L, int nl, c
     switch (c.Nyr) {
       case 256: st = launch_col_tf<256>(c, L, gc, s); break;
       case 512: st = launch_col_tf<512>(c, L, gc, s); break;
-      case 1024: st = launch_col_tf<1024>(c, L, gc, s); break;
+      case 1024: st = launch_col_tf2<1024>(c, L, gc, s); break;
       default: return fail(SWENSE_ERR_UNSUPPORTED, "transposed pair: column length");
     }
   } else if (which != 2) {
