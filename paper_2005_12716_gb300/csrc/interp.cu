@@ -731,17 +731,27 @@ __global__ void __launch_bounds__(BOX_THREADS, 3) k_interp_box(InterpArgs a, Lev
 // more nodes than shared memory holds). No dynamic shared memory, so that L1 keeps the rows
 // neighbouring points share: launched apart from k_interp_box, whose 68 KB tile per CTA would
 // leave L1 a fifth of its size.
-// One chunk per CTA, in chunk order (the CTAs in flight then cover consecutive chunks, whose
-// stencils share rows in L2); the chunks with a staged tile exit at once.
+// One quarter of a chunk (256 points, one a thread) per CTA, in point order: the CTAs in flight
+// then cover consecutive points, whose stencils share rows in L2, over a quarter of the span that
+// whole chunks per CTA would (3 % faster on the large sea); the quarters of chunks with a staged
+// tile exit at once.
 template <bool P2>
 __global__ void __launch_bounds__(BOX_THREADS, 4) k_interp_global(InterpArgs a, Levels L,
                                                                    const int4* __restrict__ plan) {
   __shared__ LevelTables zs;
-  const int4 pl = plan[blockIdx.x];
+  const int64_t sub = blockIdx.x, chunk = sub / BOX_PPT;
+  const int4 pl = plan[chunk];
   if (!plan_is_global(pl, a.nz)) return;            // uniform over the CTA
   fill_level_tables(zs, L, a.nz);
   __syncthreads();
-  global_points<P2>(a, zs, int64_t(blockIdx.x) * BOX_PTS);
+  const int64_t i = chunk * BOX_PTS + (sub % BOX_PPT) * BOX_THREADS + threadIdx.x;
+  if (i >= a.np) return;
+  const float pz = __ldg(&a.pts[3 * i + 2]);
+  const PointCell c = point_cell<P2>(a, zs, __ldg(&a.pts[3 * i]), __ldg(&a.pts[3 * i + 1]), pz);
+  float4 acc;
+  float acc_eta;
+  gather_global<P2>(a, c, acc, acc_eta);
+  store_point(a, i, acc, acc_eta, pz, c.inside);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -1396,8 +1406,8 @@ int interp_impl(const swense_grid* g, double t, const float* pts, const int32_t*
     SWENSE_CUDA_TRY(cudaFuncSetAttribute(kbox, cudaFuncAttributeMaxDynamicSharedMemorySize, int(BOX_SMEM)));
     if (a.p2) k_interp_box<true><<<unsigned(blocks), BOX_THREADS, BOX_SMEM, stream>>>(a, lev, plan);
     else k_interp_box<false><<<unsigned(blocks), BOX_THREADS, BOX_SMEM, stream>>>(a, lev, plan);
-    if (a.p2) k_interp_global<true><<<unsigned(blocks), BOX_THREADS, 0, stream>>>(a, lev, plan);
-    else k_interp_global<false><<<unsigned(blocks), BOX_THREADS, 0, stream>>>(a, lev, plan);
+    if (a.p2) k_interp_global<true><<<unsigned(blocks * BOX_PPT), BOX_THREADS, 0, stream>>>(a, lev, plan);
+    else k_interp_global<false><<<unsigned(blocks * BOX_PPT), BOX_THREADS, 0, stream>>>(a, lev, plan);
     SWENSE_CUDA_TRY(cudaGetLastError());
     count_launches(2);
   }
