@@ -337,13 +337,15 @@ enum swense_direct_precision {
  *     an exact 32-bit fraction of a turn, so accuracy does not degrade with |k x|).
  *   SWENSE_DIRECT_SPLIT_BF16: the sums as a dense contraction on the tcgen05 tensor cores. The
  *     points are sorted by z (a counting sort into 65536 buckets between their min and max z)
- *     and cut into tiles of 128; the phase is separated, e^{i(kx x + ky y)} = X_m(x) Y_n(y), and
- *     the depth factor is expanded about each tile's middle z0 to second order in z - z0 (exact
- *     derivatives d/dz F = |k| S, d/dz S = |k| F); per group of 8 mode rows and 32 modes, a
- *     [128 points x 64] x [64 x 208] product (Re/Im of u, v, w, dphi/dt at three orders, and
- *     eta) in split BF16 (hi.hi + hi.lo + lo.hi, FP32 accumulation in tensor memory), then
- *     Re sum_n Y_n T_n and sum_j (z - z0)^j in FP32. A tile whose max|k| x half-range of z
- *     exceeds 0.02 (the dropped third-order term would exceed 2e-6) is evaluated by the
+ *     and cut into tiles of 128, two tiles per cluster of two CTAs (cta_group::2); the phase
+ *     is separated, e^{i(kx x + ky y)} = X_m(x) Y_n(y), and the depth factor is expanded about
+ *     the tile pair's middle z0 to second order in z - z0 (exact derivatives d/dz F = |k| S,
+ *     d/dz S = |k| F); rows n and -n are paired (Y_-n = conj Y_n); per group of 8 row pairs and
+ *     64 modes, a [256 points x 128] x [128 x 208] product (Re(T_n + T_-n), Im(T_n - T_-n) of
+ *     u, v, w, dphi/dt at three orders, and eta) in split BF16 (hi.hi + hi.lo + lo.hi; the
+ *     order-2 columns without their lo half), FP32 accumulation in tensor memory, then
+ *     Re sum_n Y_n (...) and sum_j (z - z0)^j in FP32. A tile pair whose max|k| x half-range of
+ *     z exceeds 0.02 (the dropped third-order term would exceed 2e-6) is evaluated by the
  *     per-pair kernel instead. Accuracy: about 1e-5 of each field's maximum (bar 1e-3).
  *     Points with nearly equal z are ordered by atomics, so a tile's z0, and with it the last
  *     digits of the split products' rounding, can differ from call to call.
