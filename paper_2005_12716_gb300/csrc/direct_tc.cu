@@ -65,8 +65,13 @@ constexpr int kTcStages = 2;
 // epilogue reads each accumulator once per 64 modes.
 constexpr int kTcALBO = (kTcM / 8) * 128 + 16;
 constexpr int kTcABytes = (kTcK / 8) * kTcALBO;
+// the next chunk's A is made while the current chunk's groups run: its lo half into the other of
+// two lo buffers, its hi half into a staging area (word j of point t at [j][t]) that is copied
+// into tensor memory once the current chunk's MMAs are done
+constexpr int kTcAHiBytes = kTcModes * kTcM * 4;
+constexpr int kTcASmem = 2 * kTcABytes + kTcAHiBytes;
 // per point, the row anchors Y^(8 j) (j < kYLo) of its groups: one group's first row in 64
-constexpr int kYLo = 64;
+constexpr int kYLo = 16;
 constexpr int kYTabBytes = kYLo * kTcM * 8;
 // 13 warps per CTA: 4 epilogue warps (one point each), 8 producer warps (two per row pair of
 // this CTA's half, one per 32 modes of a group), 1 MMA warp (the even CTA's lane 0 issues for the
@@ -86,7 +91,7 @@ constexpr uint32_t kIdesc = tc::idesc_bf16_f32(2 * kTcM, kTcN);
 constexpr size_t kTcSmemMin = 120 * 1024;
 static_assert(kTcN % 16 == 0 && kTcN <= 256 && kTcNh % 8 == 0, "MMA N for M = 256");
 static_assert(kColD1 + kTcN <= kTmemCols, "tensor-memory columns");
-static_assert(kTcStages * kTcStageBytes + kTcABytes + kYTabBytes + 2048 <= 227 * 1024, "shared memory");
+static_assert(kTcStages * kTcStageBytes + kTcASmem + kYTabBytes + 2048 <= 227 * 1024, "shared memory");
 
 // Set when a bounded wait of k_direct_tc gave up (read by swense_async_status).
 __device__ int g_direct_timeout;
@@ -194,9 +199,10 @@ struct TcShared {
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1) k_direct_tc(TcArgs a) {
   extern __shared__ __align__(1024) unsigned char smraw[];
   unsigned char* bst = smraw;                                   // kTcStages x (B hi, B lo)
-  unsigned char* alo = smraw + kTcStages * kTcStageBytes;        // A lo (this CTA's points)
-  float2* ytab = reinterpret_cast<float2*>(alo + kTcABytes);       // [kYLo][kTcM]
-  TcShared& sh = *reinterpret_cast<TcShared*>(alo + kTcABytes + kYTabBytes);
+  unsigned char* alo = smraw + kTcStages * kTcStageBytes;        // A lo, two chunks (this CTA's points)
+  uint32_t* ahs = reinterpret_cast<uint32_t*>(alo + 2 * kTcABytes);  // next chunk's A hi [kTcModes][kTcM]
+  float2* ytab = reinterpret_cast<float2*>(alo + kTcASmem);        // [kYLo][kTcM]
+  TcShared& sh = *reinterpret_cast<TcShared*>(alo + kTcASmem + kYTabBytes);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned rank = cluster_rank();                          // 0: even CTA, 1: odd CTA
   const int64_t tile = blockIdx.x;                               // rank == blockIdx.x & 1
@@ -336,35 +342,46 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1) k_dir
       }
     };
 
-    // A = X_m(p) of a K-chunk's 64 modes: word j = (cos, sin) of mode j as BF16, the hi halves
-    // into tensor memory (column j), the lo residuals into shared memory (K pair j: k-block j / 4,
-    // word j % 4 of this point's 16-byte row)
-    auto write_a = [&](int kc) {
-      unsigned char* arow = alo + (t >> 3) * 128 + (t & 7) * 16;
+    // A = X_m(p) of a K-chunk's 64 modes: word j = (cos, sin) of mode j as BF16. make_a: modes
+    // 16 h .. 16 h + 15 of chunk kc, the lo residuals into the chunk's lo buffer (K pair j:
+    // k-block j / 4, word j % 4 of this point's 16-byte row), the hi halves into the staging
+    // area; put_a: the staged hi halves into tensor memory (columns 0..63), then the chunk's A
+    // is announced
+    auto make_a = [&](int kc, int h) {
+      unsigned char* arow = alo + (kc & 1) * kTcABytes + (t >> 3) * 128 + (t & 7) * 16;
+      uint32_t whi[16], wlo[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const unsigned m = unsigned(kc * kTcModes + 16 * h + j);
+        const unsigned ph = m * X;
+        float s, c;
+        sincospif(2.f * (float(int(ph)) * 2.3283064365386963e-10f), &s, &c);
+        bf2_split(c, s, whi[j], wlo[j]);
+        ahs[(16 * h + j) * kTcM + t] = whi[j];
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        *reinterpret_cast<uint4*>(arow + (4 * h + q) * kTcALBO) =
+            make_uint4(wlo[4 * q], wlo[4 * q + 1], wlo[4 * q + 2], wlo[4 * q + 3]);
+    };
+    auto put_a = [&]() {
 #pragma unroll 1
       for (int h = 0; h < kTcModes / 16; ++h) {
-        uint32_t whi[16], wlo[16];
+        uint32_t whi[16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const unsigned m = unsigned(kc * kTcModes + 16 * h + j);
-          const unsigned ph = m * X;
-          float s, c;
-          sincospif(2.f * (float(int(ph)) * 2.3283064365386963e-10f), &s, &c);
-          bf2_split(c, s, whi[j], wlo[j]);
-        }
+        for (int j = 0; j < 16; ++j) whi[j] = ahs[(16 * h + j) * kTcM + t];
         tc::st_x16(lanebase + kColAhi + 16u * h, whi);
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          *reinterpret_cast<uint4*>(arow + (4 * h + q) * kTcALBO) =
-              make_uint4(wlo[4 * q], wlo[4 * q + 1], wlo[4 * q + 2], wlo[4 * q + 3]);
       }
       tc::wait_st();
       fence_proxy_async();                          // A lo: generic-proxy stores -> the MMA's reads
       tc::fence_before();
       if (!a.withhold_a) pair_arrive(&sh.a_ready, lane);
     };
-    write_a(0);
+#pragma unroll 1
+    for (int h = 0; h < kTcModes / 16; ++h) make_a(0, h);
+    put_a();
     bool ok = true;
+    int made = 0;                                   // blocks of 16 modes of the next chunk's A made
     for (int gi = 0, g = 0, kc = 0; gi < ngi; ++gi) {
       if (g % kYLo == 0) {
         if (g == 0) {
@@ -378,10 +395,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1) k_dir
       if (!ok) break;
       tc::fence_after();
       // the last group of a chunk is done, so are all MMAs reading this chunk's A: the next
-      // chunk's A goes in before this group's epilogue, so the MMAs resume at once
-      if (g + 1 == ng && kc + 1 < nkc) write_a(kc + 1);
+      // chunk's A (made during this chunk) goes in before this group's epilogue
+      if (g + 1 == ng && kc + 1 < nkc) {
+        while (made < kTcModes / 16) make_a(kc + 1, made++);
+        put_a();
+      }
       consume(gi, g);
+      if (g + 1 < ng && kc + 1 < nkc) {             // the next chunk's A, spread over this chunk
+        while (made < ((kTcModes / 16) * (g + 1)) / (ng - 1)) make_a(kc + 1, made++);   // all by g = ng - 2
+      }
       if (++g == ng) {
+        made = 0;
         g = 0;
         ++kc;
       }
@@ -498,7 +522,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1) k_dir
             const uint64_t dl = tc::smem_desc(blo + 2 * ks * kTcLBO, kTcLBO, kTcSBO);
             tc::mma2_ts(dacc, tbase + kColAhi + 8u * ks, dh, kIdesc, ks > 0 ? 1u : 0u);
             tc::mma2_ts(dacc, tbase + kColAhi + 8u * ks, dl, kIdesc, 1u);
-            tc::mma2_ss(dacc, tc::smem_desc(alo + 2 * ks * kTcALBO, kTcALBO, 128u), dh, kIdesc, 1u);
+            tc::mma2_ss(dacc, tc::smem_desc(alo + (kc & 1) * kTcABytes + 2 * ks * kTcALBO, kTcALBO, 128u), dh,
+                        kIdesc, 1u);
           }
           tc::commit2(&sh.b_empty[s], uint16_t(3));
           tc::commit2(&sh.d_full[d], uint16_t(3));
@@ -848,7 +873,7 @@ int direct_tc(const swense_modes* md, double t, const float* pts, int64_t np, fl
   }
   a.ntiles = ntiles;
   const size_t smem =
-      std::max(size_t(kTcStages) * kTcStageBytes + kTcABytes + kYTabBytes + sizeof(TcShared), kTcSmemMin);
+      std::max(size_t(kTcStages) * kTcStageBytes + kTcASmem + kYTabBytes + sizeof(TcShared), kTcSmemMin);
   SWENSE_CUDA_TRY(cudaFuncSetAttribute(k_direct_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
   // clusters of two CTAs: one per pair of tiles (the odd CTA of a last, unpaired tile has no points)
   k_direct_tc<<<unsigned((ntiles + 1) / 2 * 2), kTcThreads, smem, stream>>>(a);
