@@ -333,7 +333,7 @@ DIRECT_KERNEL = "k_direct_tc"
 DIRECT_SOURCES = ("csrc/direct_tc.cu", "csrc/tcgen05.cuh", "csrc/tma.cuh", "csrc/internal.cuh")
 NCU_TRAFFIC[DIRECT_KERNEL] = {
     # ncu --set full, one launch: 1,000,000 near-body points x the 2048 x 1024-mode sea
-    "bytes": 59056896 + 9442560, "hash": "c17b44e5d64dea29",
+    "bytes": 59206656 + 9181952, "hash": "a991ed0c82f96b6d",
     "workload": "near-body 1000000 points x 2048x1024 modes"}
 # Algorithmic MMA flops of the split-BF16 direct sum (the per-unit figure of the workload's
 # definition): per (point, mode) pair of the full nx x ny spectrum, u, v, w and dphi/dt each the
