@@ -827,17 +827,18 @@ __global__ void __launch_bounds__(256, N >= 1024 ? 1 : 2) k_col_tf(ColArgs a, Le
 
 // The same column pass with two warps per column (1024-point columns): warp 2c + s transforms
 // the rows p = 2 i + s of column c (a 512-point Stockham transform, 16 points a lane), the odd
-// warp multiplies its result by e^{2 pi i k / N}, and the pair combines them by one radix-2 step
-// through its exchange buffers, X[k] = E[k] + O'[k] and X[k + N/2] = E[k] - O'[k] (the same
-// operations, in the same order, as the last radix-2 pass of the one-warp transform, so the
-// results are identical). Half the points per lane (127 registers) and twice the warps per SM
-// of k_col_tf<1024>, whose 244 registers leave one 8-warp CTA per SM: 2 % faster on the large
-// sea's stage 1.
+// warp multiplies its result by e^{2 pi i k / N}, both halves go to the CTA's tile, and the
+// radix-2 combine X[k] = E[k] + O'[k], X[k + N/2] = E[k] - O'[k] is done while the tile is
+// written out (the operations of the one-warp transform's last pass, in the same order, so the
+// results are identical). Half the points per lane (128 registers) and twice the warps per SM of
+// k_col_tf<1024>, whose 244 registers leave one 8-warp CTA per SM; bank-conflict-free tile
+// (XOR swizzle) and no separate exchange for the combine: stage 1 of the large sea 17.65 ->
+// 16.67 ms.
 template <int N>
 __global__ void __launch_bounds__(2 * kThreads, 1) k_col_tf2(ColArgs a, Levels L) {
-  extern __shared__ float2 sm[];                 // exchange buffers, then tile [N][kColBlock + 1]
+  extern __shared__ float2 sm[];                 // exchange buffers, then tile [N][kColBlock] (swizzled)
   constexpr int H = N / 2, E = H / 32, RL = stk_radix(H, stk_npass(H) - 1);
-  constexpr int TLD = kColBlock + 1;
+  static_assert(kColBlock == 8, "the tile swizzle spans 8 columns");
   static_assert(kColBlock * 64 == 2 * kThreads, "two warps per column");
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int col = warp >> 1, par = warp & 1;     // column of the CTA, parity of this warp's rows
@@ -847,7 +848,6 @@ __global__ void __launch_bounds__(2 * kThreads, 1) k_col_tf2(ColArgs a, Levels L
   const int q = blockIdx.z;
   float2* tile = sm;
   float2* wbuf = sm + warp * stk_buf(H);
-  const float2* pbuf = sm + (warp ^ 1) * stk_buf(H);
   float2 T[stk_twn(H)];
   stk_init<H>(T, a.tw, lane);
   const int nyh = a.ny >> 1;
@@ -891,35 +891,29 @@ __global__ void __launch_bounds__(2 * kThreads, 1) k_col_tf2(ColArgs a, Levels L
       v[e] = modal_field(q, kx, ky, kk, F, S, am[e], am[e]);
     }
     stk_fft<H>(v, T, a.tw, wbuf, lane);
-    // element e holds output k = lane + 32 (e / RL) + (e % RL) (H / RL); the odd half is twiddled
+    __syncthreads();                             // every warp is done with its exchange buffer
+    // element e holds output k = lane + 32 (e / RL) + (e % RL) (H / RL) of this half; the odd half,
+    // twiddled, goes to tile row H + k. Tile rows hold the CTA's 8 columns with column c at
+    // c ^ ((row >> 1) & 7): the column writes (16 consecutive rows a half-warp) and the row reads
+    // (two rows of 8 columns a half-warp) both hit 32 different banks.
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int k = lane + 32 * (e / RL) + (e % RL) * (H / RL);
       if (par) v[e] = cmul(v[e], __ldg(&a.tw[k * (SWENSE_MAX_FFT / N)]));
-      wbuf[stk_pad(k)] = v[e];
-    }
-    __syncthreads();                             // both halves of every column are published
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-      const int k = lane + 32 * (e / RL) + (e % RL) * (H / RL);
-      const float2 o = pbuf[stk_pad(k)];
-      v[e] = par ? csub(o, v[e]) : cadd(v[e], o);  // even warp: X[k]; odd warp: X[k + H]
-    }
-    __syncthreads();                             // the buffers are read before the tile reuses them
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-      const int k = lane + 32 * (e / RL) + (e % RL) * (H / RL) + par * H;
-      tile[k * TLD + col] = v[e];
+      const int row = k + par * H;
+      tile[row * kColBlock + (col ^ ((row >> 1) & 7))] = v[e];
     }
     __syncthreads();
     float2* out = a.G + (size_t(level) * 4 + q) * a.Nyr * a.ldG + c0;
-    // two columns per thread: 16-byte stores (ldG and c0 are multiples of 16 and 8 entries)
-    for (int i = threadIdx.x; i < N * kColBlock / 2; i += 2 * kThreads) {
-      const int y = i / (kColBlock / 2), w = 2 * (i % (kColBlock / 2));
-      const float2 v0 = tile[y * TLD + w], v1 = tile[y * TLD + w + 1];
-      float2* o = &out[size_t(y) * a.ldG + w];
-      if (c0 + w + 1 < a.Mh) __stcg(reinterpret_cast<float4*>(o), make_float4(v0.x, v0.y, v1.x, v1.y));
-      else if (c0 + w < a.Mh) __stcg(o, v0);
+    // the radix-2 combine on the way out: X[y] = E[y] + O'[y], X[y + H] = E[y] - O'[y]
+    for (int i = threadIdx.x; i < H * kColBlock; i += 2 * kThreads) {
+      const int y = i / kColBlock, w = i % kColBlock;
+      const float2 ev = tile[y * kColBlock + (w ^ ((y >> 1) & 7))];
+      const float2 od = tile[(y + H) * kColBlock + (w ^ (((y + H) >> 1) & 7))];
+      if (c0 + w < a.Mh) {
+        __stcg(&out[size_t(y) * a.ldG + w], cadd(ev, od));
+        __stcg(&out[size_t(y + H) * a.ldG + w], csub(ev, od));
+      }
     }
     __syncthreads();                             // the tile is read before the next transforms
   }
@@ -1254,7 +1248,7 @@ int launch_col_tf(const ColArgs& c, const Levels& L, dim3 grid, cudaStream_t str
 
 template <int N>
 int launch_col_tf2(const ColArgs& c, const Levels& L, dim3 grid, cudaStream_t stream) {
-  const size_t smem = std::max(size_t(N) * (kColBlock + 1), size_t(16) * stk_buf(N / 2)) * sizeof(float2);
+  const size_t smem = std::max(size_t(N) * kColBlock, size_t(16) * stk_buf(N / 2)) * sizeof(float2);
   int st = set_smem((const void*)k_col_tf2<N>, smem);
   if (st) return st;
   grid.z = 4;
