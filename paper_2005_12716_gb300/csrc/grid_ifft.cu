@@ -641,6 +641,13 @@ __device__ __forceinline__ void discard_rows(const float2* row, size_t fs, int n
 // column's modes once (reused over the block's levels), forms NF modal fields per depth-factor
 // evaluation, transforms them, and the block writes the eight columns out row by row through a
 // padded shared tile (64-byte segments).
+// Position of (row, column) in the 8-column tiles through which the column passes transpose
+// their output: a row's columns are XOR-swizzled by (row >> 1) & 7, so that a warp's column
+// writes (16 consecutive rows a half-warp) and the row reads (two rows of 8 columns a
+// half-warp) each hit 32 different banks.
+static_assert(kColBlock == 8, "the tile swizzle spans 8 columns");
+__device__ __forceinline__ int tile_pos(int row, int col) { return row * kColBlock + (col ^ ((row >> 1) & 7)); }
+
 template <int N, int NF>
 __global__ void __launch_bounds__(256, N >= 1024 ? 1 : 2) k_col_t(ColArgs a, Levels L) {
   extern __shared__ float2 sm[];                 // tile [N][kColBlock + 1], then warp buffers
@@ -730,16 +737,13 @@ __global__ void __launch_bounds__(256, N >= 1024 ? 1 : 2) k_col_t(ColArgs a, Lev
       for (int f = 0; f < NF; ++f) {
         stk_fft<N>(v[f], T, a.tw, wbuf, lane);
 #pragma unroll
-        for (int e = 0; e < E; ++e) tile[(lane + 32 * (e / RL) + (e % RL) * (N / RL)) * TLD + warp] = v[f][e];
+        for (int e = 0; e < E; ++e) tile[tile_pos(lane + 32 * (e / RL) + (e % RL) * (N / RL), warp)] = v[f][e];
         __syncthreads();
         float2* out = a.G + (size_t(level) * 4 + g * NF + f) * a.Nyr * a.ldG + c0;
-        // two columns per thread: 16-byte stores (ldG and c0 are multiples of 16 and 8 entries)
-        for (int i = threadIdx.x; i < N * kColBlock / 2; i += kThreads) {
-          const int y = i / (kColBlock / 2), w = 2 * (i % (kColBlock / 2));
-          const float2 v0 = tile[y * TLD + w], v1 = tile[y * TLD + w + 1];
-          float2* o = &out[size_t(y) * a.ldG + w];
-          if (c0 + w + 1 < a.Mh) __stcg(reinterpret_cast<float4*>(o), make_float4(v0.x, v0.y, v1.x, v1.y));
-          else if (c0 + w < a.Mh) __stcg(o, v0);
+        // rows of 8 columns: 64 contiguous bytes of the intermediate per row
+        for (int i = threadIdx.x; i < N * kColBlock; i += kThreads) {
+          const int y = i / kColBlock, w = i % kColBlock;
+          if (c0 + w < a.Mh) __stcg(&out[size_t(y) * a.ldG + w], tile[tile_pos(y, w)]);
         }
         __syncthreads();
       }
@@ -756,7 +760,6 @@ template <int N>
 __global__ void __launch_bounds__(256, N >= 1024 ? 1 : 2) k_col_tf(ColArgs a, Levels L) {
   extern __shared__ float2 sm[];                 // exchange buffers, then tile [N][kColBlock + 1]
   constexpr int E = N / 32, RL = stk_radix(N, stk_npass(N) - 1);
-  constexpr int TLD = kColBlock + 1;
   static_assert(kColBlock * 32 == kThreads, "one column per warp");
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int c0 = blockIdx.x * kColBlock;
@@ -810,16 +813,13 @@ __global__ void __launch_bounds__(256, N >= 1024 ? 1 : 2) k_col_tf(ColArgs a, Le
     stk_fft<N>(v, T, a.tw, wbuf, lane);
     __syncthreads();                             // every warp is done with its exchange buffer
 #pragma unroll
-    for (int e = 0; e < E; ++e) tile[(lane + 32 * (e / RL) + (e % RL) * (N / RL)) * TLD + warp] = v[e];
+    for (int e = 0; e < E; ++e) tile[tile_pos(lane + 32 * (e / RL) + (e % RL) * (N / RL), warp)] = v[e];
     __syncthreads();
     float2* out = a.G + (size_t(level) * 4 + q) * a.Nyr * a.ldG + c0;
-    // two columns per thread: 16-byte stores (ldG and c0 are multiples of 16 and 8 entries)
-    for (int i = threadIdx.x; i < N * kColBlock / 2; i += kThreads) {
-      const int y = i / (kColBlock / 2), w = 2 * (i % (kColBlock / 2));
-      const float2 v0 = tile[y * TLD + w], v1 = tile[y * TLD + w + 1];
-      float2* o = &out[size_t(y) * a.ldG + w];
-      if (c0 + w + 1 < a.Mh) __stcg(reinterpret_cast<float4*>(o), make_float4(v0.x, v0.y, v1.x, v1.y));
-      else if (c0 + w < a.Mh) __stcg(o, v0);
+    // rows of 8 columns: 64 contiguous bytes of the intermediate per row
+    for (int i = threadIdx.x; i < N * kColBlock; i += kThreads) {
+      const int y = i / kColBlock, w = i % kColBlock;
+      if (c0 + w < a.Mh) __stcg(&out[size_t(y) * a.ldG + w], tile[tile_pos(y, w)]);
     }
     __syncthreads();                             // the tile is read before the next transforms
   }
@@ -901,15 +901,14 @@ __global__ void __launch_bounds__(2 * kThreads, 1) k_col_tf2(ColArgs a, Levels L
       const int k = lane + 32 * (e / RL) + (e % RL) * (H / RL);
       if (par) v[e] = cmul(v[e], __ldg(&a.tw[k * (SWENSE_MAX_FFT / N)]));
       const int row = k + par * H;
-      tile[row * kColBlock + (col ^ ((row >> 1) & 7))] = v[e];
+      tile[tile_pos(row, col)] = v[e];
     }
     __syncthreads();
     float2* out = a.G + (size_t(level) * 4 + q) * a.Nyr * a.ldG + c0;
     // the radix-2 combine on the way out: X[y] = E[y] + O'[y], X[y + H] = E[y] - O'[y]
     for (int i = threadIdx.x; i < H * kColBlock; i += 2 * kThreads) {
       const int y = i / kColBlock, w = i % kColBlock;
-      const float2 ev = tile[y * kColBlock + (w ^ ((y >> 1) & 7))];
-      const float2 od = tile[(y + H) * kColBlock + (w ^ (((y + H) >> 1) & 7))];
+      const float2 ev = tile[tile_pos(y, w)], od = tile[tile_pos(y + H, w)];
       if (c0 + w < a.Mh) {
         __stcg(&out[size_t(y) * a.ldG + w], cadd(ev, od));
         __stcg(&out[size_t(y + H) * a.ldG + w], csub(ev, od));

@@ -714,17 +714,18 @@ __device__ __forceinline__ void box_chunk(const InterpArgs& a, const LevelTables
   }
 }
 
-// The chunks with a staged tile (box, plane or two planes); k_interp_global takes the others.
-template <bool P2>
+// The chunks with a staged tile (box, plane or two planes); kSplit: k_interp_global takes the
+// others, else this kernel gathers them too (from global memory, with L1 reduced by the tile).
+template <bool P2, bool kSplit>
 __global__ void __launch_bounds__(BOX_THREADS, 3) k_interp_box(InterpArgs a, Levels L,
                                                                 const int4* __restrict__ plan) {
   extern __shared__ float4 sbox[];
   float* seta = reinterpret_cast<float*>(sbox + BOX_NODES);
   __shared__ LevelTables zs;
   const int4 pl = plan[blockIdx.x];
-  if (plan_is_global(pl, a.nz)) return;             // uniform over the CTA
+  if (kSplit && plan_is_global(pl, a.nz)) return;   // uniform over the CTA
   fill_level_tables(zs, L, a.nz);
-  box_chunk<P2, false>(a, zs, blockIdx.x, pl, sbox, seta);
+  box_chunk<P2, !kSplit>(a, zs, blockIdx.x, pl, sbox, seta);
 }
 
 // The chunks without a staged tile (scattered points: the stencils of a 1024-point chunk span
@@ -1402,14 +1403,26 @@ int interp_impl(const swense_grid* g, double t, const float* pts, const int32_t*
       count_launches(1);
       plan = pw;
     }
-    const void* kbox = a.p2 ? (const void*)k_interp_box<true> : (const void*)k_interp_box<false>;
+    // Sparse point sets (fewer points than a quarter of a time level's nodes: a chunk's
+    // stencils then rarely fit a tile) send the chunks without a tile to k_interp_global, where
+    // L1 is not reduced by the tile; dense ones (meshes at their grid's resolution) gather the
+    // rare such chunks inside k_interp_box and skip the second launch.
+    const bool split = double(np) < 0.25 * double(a.Nxr) * double(a.Nyr) * double(a.nz);
+    const void* kbox = a.p2 ? (split ? (const void*)k_interp_box<true, true> : (const void*)k_interp_box<true, false>)
+                            : (split ? (const void*)k_interp_box<false, true> : (const void*)k_interp_box<false, false>);
     SWENSE_CUDA_TRY(cudaFuncSetAttribute(kbox, cudaFuncAttributeMaxDynamicSharedMemorySize, int(BOX_SMEM)));
-    if (a.p2) k_interp_box<true><<<unsigned(blocks), BOX_THREADS, BOX_SMEM, stream>>>(a, lev, plan);
-    else k_interp_box<false><<<unsigned(blocks), BOX_THREADS, BOX_SMEM, stream>>>(a, lev, plan);
-    if (a.p2) k_interp_global<true><<<unsigned(blocks * BOX_PPT), BOX_THREADS, 0, stream>>>(a, lev, plan);
-    else k_interp_global<false><<<unsigned(blocks * BOX_PPT), BOX_THREADS, 0, stream>>>(a, lev, plan);
+    if (split) {
+      if (a.p2) k_interp_box<true, true><<<unsigned(blocks), BOX_THREADS, BOX_SMEM, stream>>>(a, lev, plan);
+      else k_interp_box<false, true><<<unsigned(blocks), BOX_THREADS, BOX_SMEM, stream>>>(a, lev, plan);
+      if (a.p2) k_interp_global<true><<<unsigned(blocks * BOX_PPT), BOX_THREADS, 0, stream>>>(a, lev, plan);
+      else k_interp_global<false><<<unsigned(blocks * BOX_PPT), BOX_THREADS, 0, stream>>>(a, lev, plan);
+      count_launches(2);
+    } else {
+      if (a.p2) k_interp_box<true, false><<<unsigned(blocks), BOX_THREADS, BOX_SMEM, stream>>>(a, lev, plan);
+      else k_interp_box<false, false><<<unsigned(blocks), BOX_THREADS, BOX_SMEM, stream>>>(a, lev, plan);
+      count_launches(1);
+    }
     SWENSE_CUDA_TRY(cudaGetLastError());
-    count_launches(2);
   }
   if (n_out_of_range) {
     unsigned long long h = 0;
