@@ -284,3 +284,23 @@ def test_plane_chunk_plans_are_reusable(api):
     got, _ = api.interp_with_plan(grid2, cfg["t_query"], pts, plan)
     for k in ("eta", "u", "v", "w", "p"):
         assert torch.equal(torch.nan_to_num(got[k], 7.0), torch.nan_to_num(ref[k], 7.0)), k
+
+
+@pytest.mark.parametrize("dense", [True, False])
+def test_mixed_staged_and_untiled_chunks(api, dense):
+    """Mesh chunks (staged tiles) followed by scattered chunks (stencils too spread for a tile):
+    with more points than a quarter of a time level's nodes the untiled chunks are gathered
+    inside the tile kernel, with fewer by the separate global kernel; both against the oracle,
+    including a ragged last chunk."""
+    cfg = configs.jonswap3d_small()
+    sea, z = cfg["sea"], np.asarray(cfg["z_levels"], np.float64)
+    mesh = configs.mesh_points(cfg["mesh"])
+    nodes = 64 * 32 * len(z)                         # one time level's nodes at pad 1
+    n_scat = (nodes // 2 if dense else nodes // 16) + 333
+    rng = np.random.default_rng(21)
+    scat = np.stack([rng.uniform(0, sea["Lx"], n_scat), rng.uniform(0, sea["Ly"], n_scat),
+                     rng.uniform(z[1], z[-2], n_scat)], 1)
+    pts = np.concatenate([mesh[: 4096 if dense else 1024], scat]).astype(np.float32)
+    assert (len(pts) >= 0.25 * nodes) == dense
+    errs, _, _ = _run(api, sea, cfg["z_levels"], 1, cfg["t_levels"], cfg["t_query"], pts)
+    assert max(errs.values()) <= TOL, errs
