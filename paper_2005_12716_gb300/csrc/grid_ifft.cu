@@ -1010,9 +1010,11 @@ __global__ void __launch_bounds__(256, N >= 2048 ? 1 : (N >= 1024 ? 2 : 3)) k_ro
 
 // Row pass for rows longer than a warp transform (2048..8192 points): one block of kThreads per
 // grid row of one level, inputs from the transposed intermediate (coalesced), block-wide
-// Stockham transforms of Z1 = U + iV and Z2 = W + iT.
+// Stockham transforms of Z1 = U + iV and Z2 = W + iT. 2048-point rows: three blocks per SM (80
+// registers) hide more of the intermediate's load latency than two (92): stage 1 of the large
+// sea 16.64 -> 16.12 ms.
 template <int N>
-__global__ void __launch_bounds__(256, N >= 8192 ? 1 : 2) k_row_tb(RowArgs a) {
+__global__ void __launch_bounds__(256, N >= 8192 ? 1 : (N >= 4096 ? 2 : 3)) k_row_tb(RowArgs a) {
   extern __shared__ float2 sm[];                 // one or two exchange buffers
   constexpr int E = N / kThreads, RL = stk_radix(N, stk_npass(N) - 1);
   constexpr bool BOTH = N <= 4096;               // both transforms' data in registers at once
