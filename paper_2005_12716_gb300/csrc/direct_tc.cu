@@ -7,27 +7,31 @@
 // The sum F_c(p) = Re sum_{m,n} W_c[m,n] e^{i (kx_m x + ky_n y)} D_c(|k|, z) is reorganised so
 // that its bulk is a dense contraction, without approximating anything beyond FP32 rounding:
 //   1. separable phase: e^{i(kx x + ky y)} = X_m(x) Y_n(y), X_m = e^{i m 2 pi x / Lx};
-//   2. depth factor about the tile's centre z0: the points are sorted by z and cut into tiles of
-//      128; with D = cosh or sinh ratio (finite depth) or e^{|k| z} (deep water) and
-//      d/dz F = |k| S, d/dz S = |k| F, the Taylor series to second order in dz = z - z0 is
-//      F(z) = F0 + |k| dz S0 + (|k| dz)^2 / 2 F0 (S likewise with F0, S0 exchanged); the tile's
-//      kappa = max|k| max|dz| is bounded (kKappaMax) so the dropped third-order term stays below
-//      2e-6 relative, under the split products' own rounding;
+//   2. depth factor about a centre z0: the points are sorted by z and cut into tiles of 128, two
+//      consecutive tiles per CTA pair sharing z0 (the middle of their z range); with D = cosh or
+//      sinh ratio (finite depth) or e^{|k| z} (deep water) and d/dz F = |k| S, d/dz S = |k| F,
+//      the Taylor series to second order in dz = z - z0 is F(z) = F0 + |k| dz S0 +
+//      (|k| dz)^2 / 2 F0 (S likewise with F0, S0 exchanged); the pair's kappa = max|k| max|dz|
+//      is bounded (kKappaMax) so the dropped third-order term stays below 2e-6 relative, under
+//      the split products' own rounding;
 //   3. for each row n of modes and each field c and order j, T_{c,j,n}(p) = sum_m X_m(p)
 //      C_{c,j}[m,n] with C = W_c |k|^j / j! (F0 or S0); rows n and -n share X_m and |k|, and
 //      with Y_{-n} = conj(Y_n) their two terms add up to Re(Y_n (T_n + conj(T_{-n}))), so the
 //      pair needs only Re(T_n + T_{-n}) and Im(T_n - T_{-n}): a (points x 2 m) by (2 m x
-//      columns) real GEMM per K-chunk of 32 modes and group of 8 row pairs (26 columns per pair:
+//      columns) real GEMM per K-chunk of 64 modes and group of 8 row pairs (26 columns per pair:
 //      those two for u, v, w, dphi/dt at orders 0..2, and eta);
 //   4. F_c(p) = sum_j dz^j sum_{n >= 0} Re(Y_n(p) (T_{c,j,n} + conj T_{c,j,-n})(p)): the
 //      epilogue of every group.
 // The GEMM runs as split BF16 (A = hi + lo, B = hi + lo, three products hi.hi + hi.lo + lo.hi
-// accumulated in FP32 in tensor memory). A (the tile's X_m, 128 points x 64) lives in tensor
-// memory, written by the epilogue warps once per K-chunk; B is generated per group by eight
-// producer warps straight into shared memory in the MMA's K-major core-matrix layout; one thread
-// issues the MMAs; accumulators are double-buffered in tensor memory so the epilogue of one
-// group overlaps the MMAs of the next. Tiles whose kappa is too large (sparse z) are left to the
-// per-pair split-BF16 kernel (direct.cu), which handles them exactly.
+// accumulated in FP32 in tensor memory; the order-2 columns of B have no lo half). Each cluster
+// of two CTAs (cta_group::2) takes a tile pair: the even CTA's thread issues M = 256 MMAs over
+// both CTAs' A (hi in tensor memory, lo in shared memory) and B halves (each CTA's producer warps
+// make the columns of 4 of the group's 8 row pairs straight into its shared memory in the MMA's
+// K-major core-matrix layout); accumulators are double-buffered in tensor memory so the epilogue
+// of one group overlaps the MMAs of the next, and the next chunk's A is made while the current
+// chunk runs. The epilogue reads each accumulator once per 64 modes, which keeps it under the
+// MMA time. Tile pairs whose kappa is too large (sparse z) are left to the per-pair split-BF16
+// kernel (direct.cu), which handles them exactly.
 #include <algorithm>
 #include <cmath>
 #include <vector>
