@@ -34,3 +34,19 @@ def test_touched_grid_bytes_matches_brute_force():
         cfg = {"sea": {"Lx": Lx, "Ly": Ly}, "z_levels": z}
         got = bench.touched_grid_bytes(cfg, pts, nxr, nyr, 2)
         assert got == _brute(pts.astype(np.float64), Lx, Ly, z, nxr, nyr, 2)
+
+
+def test_kernel_source_hash_ignores_comments_only(tmp_path, monkeypatch):
+    """The hash that keeps an ncu capture valid: unchanged by comment and blank-line edits,
+    changed by any code edit."""
+    import bench
+    pkg = tmp_path / "paper_2005_12716_gb300"
+    pkg.mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    src = pkg / "k.cu"
+    src.write_text("int f(int a) {  // add one\n  return a + 1;\n}\n")
+    h0 = bench.kernel_source_hash(("k.cu",))
+    src.write_text("// a new header\nint f(int a) {  // add one to a\n\n  return a + 1;\n}\n")
+    assert bench.kernel_source_hash(("k.cu",)) == h0
+    src.write_text("int f(int a) {\n  return a + 2;\n}\n")
+    assert bench.kernel_source_hash(("k.cu",)) != h0
