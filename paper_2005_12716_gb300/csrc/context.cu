@@ -4,6 +4,7 @@
 #include <mutex>
 #include <string>
 
+#include "fft.cuh"
 #include "internal.cuh"
 
 namespace swense {
@@ -38,16 +39,37 @@ struct DeviceState {
 std::mutex g_mutex;
 DeviceState g_dev[kMaxDevices];
 
-// e^{+2 pi i j / N}; computed in FP64 with sincospi (exact argument scaling) and rounded once.
-__device__ float2 g_twiddle[SWENSE_MAX_FFT];
+// Entry j holds e^{+2 pi i e / SWENSE_MAX_FFT}: e = j in the plain table (j < SWENSE_MAX_FFT); in
+// the pass-major tables above it (layout at stk_twp), e = jm r SWENSE_MAX_FFT / (NS R) of the
+// transform size, pass, r and jm that the slot stands for (e = 0 in the unused slots). Computed in
+// FP64 with sincospi (exact argument scaling) and rounded once, so each pass-major entry equals the
+// plain entry of the same e bit for bit.
+__device__ float2 g_twiddle[kTwiddleLen];
 
 __global__ void k_fill_twiddles() {
-  int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j < SWENSE_MAX_FFT) {
-    double s, c;
-    sincospi(2.0 * double(j) / double(SWENSE_MAX_FFT), &s, &c);
-    g_twiddle[j] = make_float2(float(c), float(s));
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= kTwiddleLen) return;
+  int e = j;
+  if (j >= SWENSE_MAX_FFT) {
+    e = 0;
+    const int i = j - SWENSE_MAX_FFT;
+    int n = 1;
+    while (2 * n <= i) n *= 2;                     // slot i lies in [n, 2n): the tables of size n
+    int ns = stk_radix(n, 0);                      // stride NS_1 of pass 1
+    const int o = i - n + ns;                      // pass p holds NS_p <= o < NS_{p+1}
+    for (int p = 1; p < stk_npass(n); ++p) {
+      const int R = stk_radix(n, p);
+      if (o < ns * R) {
+        const int q = o - ns;                      // (r - 1) NS + jm
+        e = (q % ns) * (q / ns + 1) * (SWENSE_MAX_FFT / (ns * R));
+        break;
+      }
+      ns *= R;
+    }
   }
+  double s, c;
+  sincospi(2.0 * double(e) / double(SWENSE_MAX_FFT), &s, &c);
+  g_twiddle[j] = make_float2(float(c), float(s));
 }
 
 int current_device(int* dev) {
@@ -106,7 +128,7 @@ int twiddles(cudaStream_t stream, const float2** out) {
       if (cap != cudaStreamCaptureStatusNone)
         return fail(SWENSE_ERR_ARG, "the first call on a device must not be inside a stream "
                                     "capture (it fills the twiddle table)");
-      k_fill_twiddles<<<(SWENSE_MAX_FFT + 255) / 256, 256, 0, stream>>>();
+      k_fill_twiddles<<<(kTwiddleLen + 255) / 256, 256, 0, stream>>>();
       SWENSE_CUDA_TRY(cudaGetLastError());
       count_launches(1);
       SWENSE_CUDA_TRY(cudaStreamSynchronize(stream));

@@ -213,10 +213,22 @@ constexpr int stk_dist(int n, int p) {
 constexpr int stk_twoff(int n, int p) {
   return p <= 1 ? 0 : stk_twoff(n, p - 1) + stk_dist(n, p - 1) * (stk_radix(n, p - 1) - 1);
 }
-// passes 1 .. stk_regpass - 1 keep their twiddles in registers; later passes read the table (L1)
+// passes 1 .. stk_regpass - 1 keep their twiddles in registers; later passes read the pass-major
+// tables below (L1)
 constexpr int stk_regpass(int n) { return n <= 256 ? stk_npass(n) : 2; }
 constexpr int stk_twn(int n) { return stk_twoff(n, stk_regpass(n)) > 0 ? stk_twoff(n, stk_regpass(n)) : 1; }
 constexpr int stk_buf(int n) { return n + n / 16; }   // padded buffer length (float2)
+
+// Pass-major twiddles. Pass p >= 1 of an N-point transform (stride NS, radix R) multiplies by
+// e^{+2 pi i jm r / (NS R)}, jm < NS, 0 < r < R. In the plain table that factor sits at
+// jm r SWENSE_MAX_FFT / (NS R), so the lanes of a warp (consecutive jm) read entries r
+// SWENSE_MAX_FFT / (NS R) apart: up to one L1 wavefront per lane. The twiddle array therefore also
+// holds each factor at stk_twp(N, p) + (r - 1) NS + jm, where consecutive lanes read consecutive
+// entries (2 wavefronts a warp). The tables of an N-point transform fill [SWENSE_MAX_FFT + N,
+// SWENSE_MAX_FFT + 2 N): pass q holds NS_q (R_q - 1) = NS_{q+1} - NS_q entries, so pass p starts
+// NS_p - NS_1 entries in.
+constexpr int stk_twp(int n, int p) { return SWENSE_MAX_FFT + n + stk_ns(n, p) - stk_ns(n, 1); }
+constexpr int kTwiddleLen = 3 * SWENSE_MAX_FFT;       // plain table + pass-major tables
 
 __device__ __forceinline__ int stk_pad(int i) { return i + (i >> 4); }
 
@@ -283,12 +295,12 @@ __device__ __forceinline__ void stk_pass(float2 (&v)[N / 32], const float2 (&T)[
         v[b * R + r] = cmul(v[b * R + r], T[OFF + d * (R - 1) + r - 1]);
     }
   } else if constexpr (P > 0) {
-    constexpr int step = SWENSE_MAX_FFT / (NS * R);
+    constexpr int TP = stk_twp(N, P);
 #pragma unroll
     for (int b = 0; b < B; ++b) {
       const int jm = NS <= 32 ? lane % NS : lane + 32 * (b % (NS / 32));
 #pragma unroll
-      for (int r = 1; r < R; ++r) v[b * R + r] = cmul(v[b * R + r], __ldg(&tw[jm * r * step]));
+      for (int r = 1; r < R; ++r) v[b * R + r] = cmul(v[b * R + r], __ldg(&tw[TP + (r - 1) * NS + jm]));
     }
   }
 #pragma unroll
@@ -341,20 +353,20 @@ namespace swense {
 // Block-wide Stockham inverse DFT of length N by TH threads (E = N / TH >= 8 elements each), the
 // same radix-8 (then 4 or 2) passes as stk_fft with "lane" generalised to the thread index and
 // the exchange through a padded block-shared buffer under __syncthreads. Twiddles come from the
-// table (L1). Layouts: on entry element b*8 + r of thread t holds position t + TH b + r N/8; on
-// exit element b*R + r holds t + TH b + r N/R (R = radix of the last pass).
+// pass-major tables (L1). Layouts: on entry element b*8 + r of thread t holds position
+// t + TH b + r N/8; on exit element b*R + r holds t + TH b + r N/R (R = radix of the last pass).
 template <int N, int TH, int P>
 __device__ __forceinline__ void stkb_pass(float2 (&v)[N / TH], const float2* __restrict__ tw,
                                           float2* buf, int t) {
   constexpr int E = N / TH, R = stk_radix(N, P), NS = stk_ns(N, P), B = E / R;
   static_assert(B >= 1, "each thread holds at least one butterfly per pass");
   if constexpr (P > 0) {
-    constexpr int step = SWENSE_MAX_FFT / (NS * R);
+    constexpr int TP = stk_twp(N, P);
 #pragma unroll
     for (int b = 0; b < B; ++b) {
       const int jm = NS <= TH ? t % NS : t + TH * (b % (NS / TH));
 #pragma unroll
-      for (int r = 1; r < R; ++r) v[b * R + r] = cmul(v[b * R + r], __ldg(&tw[jm * r * step]));
+      for (int r = 1; r < R; ++r) v[b * R + r] = cmul(v[b * R + r], __ldg(&tw[TP + (r - 1) * NS + jm]));
     }
   }
 #pragma unroll
@@ -406,13 +418,13 @@ __device__ __forceinline__ void stkb_pass2(float2 (&v1)[N / TH], float2 (&v2)[N 
                                            const float2* __restrict__ tw, float2* buf1, float2* buf2, int t) {
   constexpr int E = N / TH, R = stk_radix(N, P), NS = stk_ns(N, P), B = E / R;
   if constexpr (P > 0) {
-    constexpr int step = SWENSE_MAX_FFT / (NS * R);
+    constexpr int TP = stk_twp(N, P);
 #pragma unroll
     for (int b = 0; b < B; ++b) {
       const int jm = NS <= TH ? t % NS : t + TH * (b % (NS / TH));
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        const float2 w = __ldg(&tw[jm * r * step]);
+        const float2 w = __ldg(&tw[TP + (r - 1) * NS + jm]);
         v1[b * R + r] = cmul(v1[b * R + r], w);
         v2[b * R + r] = cmul(v2[b * R + r], w);
       }

@@ -840,6 +840,11 @@ __global__ void __launch_bounds__(2 * kThreads, 1) k_col_tf2(ColArgs a, Levels L
   constexpr int H = N / 2, E = H / 32, RL = stk_radix(H, stk_npass(H) - 1);
   static_assert(kColBlock == 8, "the tile swizzle spans 8 columns");
   static_assert(kColBlock * 64 == 2 * kThreads, "two warps per column");
+  // e^{2 pi i k / N}, k < H: the factors of the N-point transform's last pass (radix 2, stride H),
+  // read from its pass-major table (consecutive k in consecutive entries)
+  static_assert(stk_radix(N, stk_npass(N) - 1) == 2 && stk_ns(N, stk_npass(N) - 1) == H,
+                "the combine is the last radix-2 pass of the N-point transform");
+  constexpr int kTwC = stk_twp(N, stk_npass(N) - 1);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int col = warp >> 1, par = warp & 1;     // column of the CTA, parity of this warp's rows
   const int c0 = blockIdx.x * kColBlock;
@@ -899,7 +904,7 @@ __global__ void __launch_bounds__(2 * kThreads, 1) k_col_tf2(ColArgs a, Levels L
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int k = lane + 32 * (e / RL) + (e % RL) * (H / RL);
-      if (par) v[e] = cmul(v[e], __ldg(&a.tw[k * (SWENSE_MAX_FFT / N)]));
+      if (par) v[e] = cmul(v[e], __ldg(&a.tw[kTwC + k]));
       const int row = k + par * H;
       tile[tile_pos(row, col)] = v[e];
     }

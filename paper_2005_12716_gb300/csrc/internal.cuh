@@ -25,8 +25,9 @@ int cuda_fail(cudaError_t e, const char* what);
 // device's workspace if needed. Growing synchronises the device and is refused during capture.
 int workspace(size_t bytes, cudaStream_t stream, void** out);
 
-// Twiddle table e^{+2 pi i j / SWENSE_MAX_FFT}, j < SWENSE_MAX_FFT. The first call on a device
-// fills it with a kernel on `stream` and waits for it (refused during stream capture).
+// Twiddle array: the plain table e^{+2 pi i j / SWENSE_MAX_FFT}, j < SWENSE_MAX_FFT, followed by
+// the Stockham passes' pass-major tables (fft.cuh, stk_twp). The first call on a device fills it
+// with a kernel on `stream` and waits for it (refused during stream capture).
 int twiddles(cudaStream_t stream, const float2** out);
 
 // Counts kernel launches made by the library (reported by swense_launches()).
