@@ -360,11 +360,12 @@ def direct_traffic(nn, sea):
 
 def direct_tc_issued_flop(nx, ny, tiles):
     """MMA flops k_direct_tc issues for `tiles` tiles of 128 points (two tiles, one CTA pair, per
-    M = 256 MMA): per tile, K-chunk of 32 modes and group of 8 mode-row pairs (n, -n), 3
-    products of 128 x 208 x 64 (padded as the kernel pads)."""
+    M = 256 MMA): per tile, K-chunk of 32 modes and group of 8 mode-row pairs (n, -n), the
+    products hi.hi and lo.hi of 128 x 208 x 64 and hi.lo of 128 x 144 x 64 (the columns with a lo
+    half), padded as the kernel pads."""
     mp = -(-(nx // 2) // 64) * 64
     pairs = -(-(ny // 2) // 8) * 8 if ny > 1 else 8
-    return tiles * (mp // 32) * (pairs // 8) * 3 * 2.0 * 128 * 208 * 64
+    return tiles * (mp // 32) * (pairs // 8) * (2 * 208 + 144) * 2.0 * 128 * 64
 
 
 def run_ours(args, rank, world, emit=True):

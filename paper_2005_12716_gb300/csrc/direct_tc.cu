@@ -23,7 +23,8 @@
 //   4. F_c(p) = sum_j dz^j sum_{n >= 0} Re(Y_n(p) (T_{c,j,n} + conj T_{c,j,-n})(p)): the
 //      epilogue of every group.
 // The GEMM runs as split BF16 (A = hi + lo, B = hi + lo, three products hi.hi + hi.lo + lo.hi
-// accumulated in FP32 in tensor memory; the order-2 columns of B have no lo half). Each cluster
+// accumulated in FP32 in tensor memory; the order-2 columns of B have no lo half, and the hi.lo
+// product covers only the 144 columns that have one: an M = 256 MMA takes N / 2 cycles). Each cluster
 // of two CTAs (cta_group::2) takes a tile pair: the even CTA's thread issues M = 256 MMAs over
 // both CTAs' A (hi in tensor memory, lo in shared memory) and B halves (each CTA's producer warps
 // make the columns of 4 of the group's 8 row pairs straight into its shared memory in the MMA's
@@ -53,15 +54,35 @@ constexpr int kTcHalfRows = kTcRows / 2;              // row pairs whose B colum
 constexpr int kTcNh = kTcN / 2;                       // 104 B columns per CTA
 constexpr int kTcModes = 64;                          // modes m per K-chunk (one group's K)
 constexpr int kTcK = 2 * kTcModes;                    // 128 K (re, im per mode)
-// B layout (each CTA's half, columns nc = 8 cj + 2 pair + {0: Re(T_n + T_-n), 1: Im(T_n - T_-n)}
-// for its 4 row pairs): one core matrix (8 columns x 8 K, 128 bytes) per output cj; k-blocks of
-// 8 K are kTcLBO bytes apart (13 core matrices + 16 bytes, so that the 32 lanes of a producer
-// warp, one mode each, hit 32 different banks). In the pair's accumulator, column c < 104 comes
-// from the even CTA's row pairs 0..3 and column 104 + c from the odd CTA's 4..7.
+// B layout (each CTA's half, columns nc = 8 slot + 2 pair + {0: Re(T_n + T_-n), 1: Im(T_n - T_-n)}
+// for its 4 row pairs): one core matrix (8 columns x 8 K, 128 bytes) per output cj, at the slot
+// tc_hslot gives; k-blocks of 8 K are kTcLBO bytes apart (13 core matrices + 16 bytes, so that
+// the 32 lanes of a producer warp, one mode each, hit 32 different banks). In the pair's
+// accumulator, column c < 104 comes from the even CTA's row pairs 0..3 and column 104 + c from
+// the odd CTA's 4..7. The lo half holds only the 9 outputs below order 2 (slot tc_li, kTcLBOlo
+// bytes per k-block); the hi.lo MMA (N = 144) writes accumulator columns 32 .. 175: the even
+// CTA's slots 4..12 (its order-2 outputs take slots 0..3), then the odd CTA's 0..8 (its order-2
+// outputs take 9..12).
+constexpr int kTcNoLo = 4;                            // order-2 outputs (u, v, w, dphi/dt)
+constexpr int kTcLoCj = kTcCj - kTcNoLo;              // 9 outputs with a lo half
+constexpr int kTcNlo = kTcRows * 2 * kTcLoCj;         // 144: N of the hi.lo MMA
+constexpr int kColLo = 8 * kTcNoLo;                   // its first accumulator column
 constexpr int kTcSBO = 128;
 constexpr int kTcLBO = (kTcNh / 8) * 128 + 16;
-constexpr int kTcBBytes = (kTcK / 8) * kTcLBO;        // one of hi / lo
-constexpr int kTcStageBytes = 2 * kTcBBytes;
+constexpr int kTcLBOlo = (kTcNlo / 2 / 8) * 128 + 16;
+constexpr int kTcBBytes = (kTcK / 8) * kTcLBO;        // B hi
+constexpr int kTcBLoBytes = (kTcK / 8) * kTcLBOlo;    // B lo
+constexpr int kTcStageBytes = kTcBBytes + kTcBLoBytes;
+constexpr bool tc_nolo(int cj) { return cj < 4 * kTcTerms && cj % kTcTerms == 2; }
+// lo slot of an output with a lo half (cj order)
+constexpr int tc_li(int cj) { return cj < 4 * kTcTerms ? (cj / kTcTerms) * 2 + cj % kTcTerms : 2 * 4; }
+// hi slot of output cj in the B half of CTA `rank`
+constexpr int tc_hslot(int rank, int cj) {
+  return tc_nolo(cj) ? (rank ? kTcLoCj : 0) + cj / kTcTerms : (rank ? 0 : kTcNoLo) + tc_li(cj);
+}
+static_assert(tc_li(4 * kTcTerms) == kTcLoCj - 1 && tc_hslot(0, 4 * kTcTerms) == kTcCj - 1 &&
+              tc_hslot(1, 4 * kTcTerms - 1) == kTcCj - 1, "slot maps");
+static_assert(kColLo + kTcNlo == kTcNh + 8 * kTcLoCj, "the lo columns: the even CTA's last 9 slots, the odd CTA's first 9");
 constexpr int kTcStages = 2;
 // A's lo half (this CTA's 128 points x K) in shared memory, K-major core matrices: 16 along M
 // per k-block, k-blocks kTcALBO bytes apart; its hi half is in tensor memory (columns 0..63).
@@ -90,10 +111,11 @@ constexpr uint32_t kColAhi = 0, kColD0 = kTcK / 2, kColD1 = kTcK / 2 + kTcN;
 constexpr float kKappaMax = 0.02f;
 constexpr int kZBuckets = 1 << 16;
 constexpr uint32_t kIdesc = tc::idesc_bf16_f32(2 * kTcM, kTcN);
+constexpr uint32_t kIdescLo = tc::idesc_bf16_f32(2 * kTcM, kTcNlo);
 // more than half of an SM's shared memory, so that one CTA of the kernel runs per SM (two
 // pairs' CTAs sharing an SM would wait on each other's tensor memory)
 constexpr size_t kTcSmemMin = 120 * 1024;
-static_assert(kTcN % 16 == 0 && kTcN <= 256 && kTcNh % 8 == 0, "MMA N for M = 256");
+static_assert(kTcN % 16 == 0 && kTcN <= 256 && kTcNh % 8 == 0 && kTcNlo % 16 == 0, "MMA N for M = 256");
 static_assert(kColD1 + kTcN <= kTmemCols, "tensor-memory columns");
 static_assert(kTcStages * kTcStageBytes + kTcASmem + kYTabBytes + 2048 <= 227 * 1024, "shared memory");
 
@@ -258,11 +280,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1) k_dir
     mbar_init(&sh.fin, 1);
     fence_mbar_init();
   }
-  // B starts zero: the lo halves of the order-2 columns stay zero (their hi halves alone are
-  // exact to 2^-9 relative, times (kappa^2 / 2) < 2e-4 from the expansion: below 4e-7)
-  for (int i = threadIdx.x; i < kTcStages * kTcStageBytes / 16; i += kTcThreads)
-    reinterpret_cast<uint4*>(bst)[i] = make_uint4(0u, 0u, 0u, 0u);
-  fence_proxy_async();
   if (warp == kMmaWarp) {
     tc::alloc2(&sh.tmem, kTmemCols);
     tc::relinquish2();
@@ -312,8 +329,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1) k_dir
 #pragma unroll
       for (int r = 1; r < kTcRows; ++r)
         yv[r] = make_float2(fmaf(yv[r - 1].x, cy, yv[r - 1].y * sy), fmaf(yv[r - 1].y, cy, -yv[r - 1].x * sy));
-      // output cj: columns 8 cj .. 8 cj + 7 (row pairs 0..3) and 104 + 8 cj .. (pairs 4..7),
-      // (Re, Im) of each pair adjacent
+      // output cj: columns 8 tc_hslot(0, cj) .. + 7 (row pairs 0..3) and 104 + 8 tc_hslot(1, cj)
+      // .. + 7 (pairs 4..7), (Re, Im) of each pair adjacent
       constexpr int kB = kTcCj;                      // every output's loads in flight, one wait
 #pragma unroll
       for (int b0 = 0; b0 < kTcCj; b0 += kB) {
@@ -321,8 +338,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1) k_dir
 #pragma unroll
         for (int q = 0; q < kB; ++q)
           if (b0 + q < kTcCj) {
-            tc::ld_x8(lanebase + dcol + uint32_t(8 * (b0 + q)), r[q][0]);
-            tc::ld_x8(lanebase + dcol + uint32_t(kTcNh + 8 * (b0 + q)), r[q][1]);
+            tc::ld_x8(lanebase + dcol + uint32_t(8 * tc_hslot(0, b0 + q)), r[q][0]);
+            tc::ld_x8(lanebase + dcol + uint32_t(kTcNh + 8 * tc_hslot(1, b0 + q)), r[q][1]);
           }
         tc::wait_ld();
         if (b0 + kB >= kTcCj) {                      // every column of this buffer is read
@@ -440,7 +457,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1) k_dir
     const float h = a.depth;
     // this lane's mode is K pair 32 mh + lane: k-block 8 mh + lane / 4, word lane % 4 of a
     // 16-byte row; this pair's two rows (Re, Im) in each output's core matrix
-    const uint32_t off = uint32_t(8 * mh + (lane >> 2)) * kTcLBO + uint32_t(2 * pw) * 16u + uint32_t(lane & 3) * 4u;
+    const uint32_t inrow = uint32_t(2 * pw) * 16u + uint32_t(lane & 3) * 4u;
+    const uint32_t offh = uint32_t(8 * mh + (lane >> 2)) * kTcLBO + inrow;
+    const uint32_t offl = uint32_t(8 * mh + (lane >> 2)) * kTcLBOlo + inrow;
     int g = 0, kc = 0;
     for (int gi = 0; gi < ngi; ++gi) {
       const int s = gi % kTcStages;
@@ -470,21 +489,23 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1) k_dir
                             make_float2(k * dp.y, k * dp.x), make_float2(df.y, df.x)};
       unsigned char* bhi = bst + size_t(s) * kTcStageBytes;
       unsigned char* blo = bhi + kTcBBytes;
-      // the lo halves of the order-2 columns stay zero (see the clearing of B)
+      // the order-2 columns have no lo half (their hi halves alone are exact to 2^-9 relative,
+      // times (kappa^2 / 2) < 2e-4 from the expansion: below 4e-7)
       auto put = [&](int cj, float2 re, float2 im) {
-        const uint32_t o0 = off + uint32_t(cj) * kTcSBO;
-        if (cj < 4 * kTcTerms && cj % kTcTerms == 2) {
-          *reinterpret_cast<unsigned*>(bhi + o0) = bf2(re.x, re.y);
-          *reinterpret_cast<unsigned*>(bhi + o0 + 16) = bf2(im.x, im.y);
+        const uint32_t oh = offh + uint32_t(rank ? tc_hslot(1, cj) : tc_hslot(0, cj)) * kTcSBO;
+        if (tc_nolo(cj)) {
+          *reinterpret_cast<unsigned*>(bhi + oh) = bf2(re.x, re.y);
+          *reinterpret_cast<unsigned*>(bhi + oh + 16) = bf2(im.x, im.y);
           return;
         }
+        const uint32_t ol = offl + uint32_t(tc_li(cj)) * kTcSBO;
         unsigned h0, l0, h1, l1;
         bf2_split_p(re, h0, l0);
         bf2_split_p(im, h1, l1);
-        *reinterpret_cast<unsigned*>(bhi + o0) = h0;
-        *reinterpret_cast<unsigned*>(blo + o0) = l0;
-        *reinterpret_cast<unsigned*>(bhi + o0 + 16) = h1;
-        *reinterpret_cast<unsigned*>(blo + o0 + 16) = l1;
+        *reinterpret_cast<unsigned*>(bhi + oh) = h0;
+        *reinterpret_cast<unsigned*>(blo + ol) = l0;
+        *reinterpret_cast<unsigned*>(bhi + oh + 16) = h1;
+        *reinterpret_cast<unsigned*>(blo + ol + 16) = l1;
       };
 #pragma unroll
       for (int j = 0; j < kTcTerms; ++j) {
@@ -523,9 +544,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1) k_dir
 #pragma unroll
           for (int ks = 0; ks < kTcK / 16; ++ks) {
             const uint64_t dh = tc::smem_desc(bhi + 2 * ks * kTcLBO, kTcLBO, kTcSBO);
-            const uint64_t dl = tc::smem_desc(blo + 2 * ks * kTcLBO, kTcLBO, kTcSBO);
+            const uint64_t dl = tc::smem_desc(blo + 2 * ks * kTcLBOlo, kTcLBOlo, kTcSBO);
             tc::mma2_ts(dacc, tbase + kColAhi + 8u * ks, dh, kIdesc, ks > 0 ? 1u : 0u);
-            tc::mma2_ts(dacc, tbase + kColAhi + 8u * ks, dl, kIdesc, 1u);
+            tc::mma2_ts(dacc + kColLo, tbase + kColAhi + 8u * ks, dl, kIdescLo, 1u);
             tc::mma2_ss(dacc, tc::smem_desc(alo + (kc & 1) * kTcABytes + 2 * ks * kTcALBO, kTcALBO, 128u), dh,
                         kIdesc, 1u);
           }
