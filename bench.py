@@ -337,8 +337,9 @@ DIRECT_KERNEL = "k_direct_tc"
 DIRECT_SOURCES = ("csrc/direct_tc.cu", "csrc/tcgen05.cuh", "csrc/tma.cuh", "csrc/internal.cuh")
 NCU_TRAFFIC[DIRECT_KERNEL] = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum (caches flushed before the launch),
-    # one launch: 1,000,000 near-body points x the 2048 x 1024-mode sea
-    "bytes": 59055616 + 9081856, "hash": "281ec58c2a90bd76",
+    # one launch: 1,000,000 near-body points x the 2048 x 1024-mode sea (sources since changed
+    # only by a compile-time check of the B column slots)
+    "bytes": 59055616 + 9081856, "hash": "f174d5c52843f601",
     "workload": "near-body 1000000 points x 2048x1024 modes"}
 # Algorithmic MMA flops of the split-BF16 direct sum (the per-unit figure of the workload's
 # definition): per (point, mode) pair of the full nx x ny spectrum, u, v, w and dphi/dt each the

@@ -39,34 +39,15 @@ struct DeviceState {
 std::mutex g_mutex;
 DeviceState g_dev[kMaxDevices];
 
-// Entry j holds e^{+2 pi i e / SWENSE_MAX_FFT}: e = j in the plain table (j < SWENSE_MAX_FFT); in
-// the pass-major tables above it (layout at stk_twp), e = jm r SWENSE_MAX_FFT / (NS R) of the
-// transform size, pass, r and jm that the slot stands for (e = 0 in the unused slots). Computed in
-// FP64 with sincospi (exact argument scaling) and rounded once, so each pass-major entry equals the
-// plain entry of the same e bit for bit.
+// Entry j holds e^{+2 pi i e / SWENSE_MAX_FFT}, e = twiddle_exponent(j): the plain table, then the
+// pass-major tables (layout at stk_twp). Computed in FP64 with sincospi (exact argument scaling)
+// and rounded once, so each pass-major entry equals the plain entry of the same e bit for bit.
 __device__ float2 g_twiddle[kTwiddleLen];
 
 __global__ void k_fill_twiddles() {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= kTwiddleLen) return;
-  int e = j;
-  if (j >= SWENSE_MAX_FFT) {
-    e = 0;
-    const int i = j - SWENSE_MAX_FFT;
-    int n = 1;
-    while (2 * n <= i) n *= 2;                     // slot i lies in [n, 2n): the tables of size n
-    int ns = stk_radix(n, 0);                      // stride NS_1 of pass 1
-    const int o = i - n + ns;                      // pass p holds NS_p <= o < NS_{p+1}
-    for (int p = 1; p < stk_npass(n); ++p) {
-      const int R = stk_radix(n, p);
-      if (o < ns * R) {
-        const int q = o - ns;                      // (r - 1) NS + jm
-        e = (q % ns) * (q / ns + 1) * (SWENSE_MAX_FFT / (ns * R));
-        break;
-      }
-      ns *= R;
-    }
-  }
+  const int e = twiddle_exponent(j);
   double s, c;
   sincospi(2.0 * double(e) / double(SWENSE_MAX_FFT), &s, &c);
   g_twiddle[j] = make_float2(float(c), float(s));

@@ -80,8 +80,23 @@ constexpr int tc_li(int cj) { return cj < 4 * kTcTerms ? (cj / kTcTerms) * 2 + c
 constexpr int tc_hslot(int rank, int cj) {
   return tc_nolo(cj) ? (rank ? kTcLoCj : 0) + cj / kTcTerms : (rank ? 0 : kTcNoLo) + tc_li(cj);
 }
-static_assert(tc_li(4 * kTcTerms) == kTcLoCj - 1 && tc_hslot(0, 4 * kTcTerms) == kTcCj - 1 &&
-              tc_hslot(1, 4 * kTcTerms - 1) == kTcCj - 1, "slot maps");
+// Every output of a CTA's half has its own hi slot; an output with a lo half sits at accumulator
+// column kColLo + rank kTcNlo / 2 + 8 tc_li (where the hi.lo MMA writes its lo products), an
+// order-2 output outside the hi.lo MMA's columns.
+constexpr bool tc_slots_ok() {
+  for (int r = 0; r < 2; ++r)
+    for (int a = 0; a < kTcCj; ++a) {
+      if (tc_hslot(r, a) < 0 || tc_hslot(r, a) >= kTcCj) return false;
+      for (int b = a + 1; b < kTcCj; ++b)
+        if (tc_hslot(r, a) == tc_hslot(r, b)) return false;
+      const int col = r * kTcNh + 8 * tc_hslot(r, a);
+      const bool in_lo = col >= kColLo && col < kColLo + kTcNlo;
+      if (tc_nolo(a) == in_lo) return false;
+      if (!tc_nolo(a) && col != kColLo + r * (kTcNlo / 2) + 8 * tc_li(a)) return false;
+    }
+  return true;
+}
+static_assert(tc_slots_ok(), "B column slots of the two CTAs and the hi.lo MMA's columns");
 static_assert(kColLo + kTcNlo == kTcNh + 8 * kTcLoCj, "the lo columns: the even CTA's last 9 slots, the odd CTA's first 9");
 constexpr int kTcStages = 2;
 // A's lo half (this CTA's 128 points x K) in shared memory, K-major core matrices: 16 along M

@@ -230,6 +230,27 @@ constexpr int stk_buf(int n) { return n + n / 16; }   // padded buffer length (f
 constexpr int stk_twp(int n, int p) { return SWENSE_MAX_FFT + n + stk_ns(n, p) - stk_ns(n, 1); }
 constexpr int kTwiddleLen = 3 * SWENSE_MAX_FFT;       // plain table + pass-major tables
 
+// Exponent e of entry j of the twiddle array (the entry is e^{+2 pi i e / SWENSE_MAX_FFT}): j in
+// the plain table; in the pass-major tables, jm r SWENSE_MAX_FFT / (NS R) of the transform size,
+// pass, r and jm that slot j stands for; 0 in the slots no pass uses.
+__host__ __device__ constexpr int twiddle_exponent(int j) {
+  if (j < SWENSE_MAX_FFT) return j;
+  const int i = j - SWENSE_MAX_FFT;
+  int n = 1;
+  while (2 * n <= i) n *= 2;                       // slot i lies in [n, 2n): the tables of size n
+  int ns = stk_radix(n, 0);                        // stride NS_1 of pass 1
+  const int o = i - n + ns;                        // pass p holds NS_p <= o < NS_{p+1}
+  for (int p = 1; p < stk_npass(n); ++p) {
+    const int R = stk_radix(n, p);
+    if (o < ns * R) {
+      const int q = o - ns;                        // (r - 1) NS + jm
+      return (q % ns) * (q / ns + 1) * (SWENSE_MAX_FFT / (ns * R));
+    }
+    ns *= R;
+  }
+  return 0;
+}
+
 __device__ __forceinline__ int stk_pad(int i) { return i + (i >> 4); }
 
 // Per-lane twiddles of the register-held passes (kernel-lifetime registers).
