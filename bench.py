@@ -1262,26 +1262,36 @@ def cpu_method_pool(n_levels, n_tl, t, n_points, cores, n_interp=20000):
             "sample_wall_s": grid_wall + interp_wall}
 
 
+ORACLE_SAMPLE_CAP = 200_000
+
+
+def oracle_sample_order(n_pts, seed=1):
+    """Seeded order of the points the CPU oracle evaluates. A run takes its first n entries, n set
+    by the time bound, so runs that admit different n share their first points and their error
+    figures compare."""
+    return np.random.default_rng(seed).choice(n_pts, min(n_pts, ORACLE_SAMPLE_CAP), replace=False)
+
+
 def cpu_oracle_pool(kind, n_levels, t, pts, seconds, cores, seed=1):
     """The FP64 oracle's direct modal sum at a seeded sample of ``pts`` on ``cores`` host processes
-    (spawned, one numpy thread each), sized to take about ``seconds``. Returns (points/s, n,
-    values, idx, cores)."""
+    (spawned, one numpy thread each), sized to take about ``seconds``: the first n points of
+    ``oracle_sample_order``. Returns (points/s, n, values, idx, cores)."""
     import multiprocessing as mp
     env_keep = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
     for k in env_keep:
         os.environ[k] = "1"
     try:
         ctx = mp.get_context("spawn")
-        rng = np.random.default_rng(seed)
+        order = oracle_sample_order(len(pts), seed)
         with ctx.Pool(cores, initializer=_pool_init, initargs=(kind, n_levels, t)) as pool:
-            probe = pts[rng.choice(len(pts), cores, replace=False)].astype(np.float64)
+            probe = pts[order[np.arange(cores) % len(order)]].astype(np.float64)
             pool.map(_pool_work, [probe[i:i + 1] for i in range(cores)])        # warm every worker
             t0 = time.perf_counter()
             pool.map(_pool_work, [probe[i:i + 1] for i in range(cores)])
             per = (time.perf_counter() - t0)                                     # one point per core
-            n = int(min(max(cores, seconds / max(per, 1e-9) * cores), 200_000))
-            n = max(cores, (n // cores) * cores)
-            idx = rng.choice(len(pts), n, replace=False)
+            n = int(min(max(cores, seconds / max(per, 1e-9) * cores), len(order)))
+            n = min(len(order), max(cores, (n // cores) * cores))
+            idx = order[:n]
             sample = pts[idx].astype(np.float64)
             parts = np.array_split(sample, cores * 4)
             t0 = time.perf_counter()

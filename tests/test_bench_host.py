@@ -50,3 +50,19 @@ def test_kernel_source_hash_ignores_comments_only(tmp_path, monkeypatch):
     assert bench.kernel_source_hash(("k.cu",)) == h0
     src.write_text("int f(int a) {\n  return a + 2;\n}\n")
     assert bench.kernel_source_hash(("k.cu",)) != h0
+
+
+def test_oracle_sample_is_a_seeded_prefix():
+    """The CPU oracle's sample is the first n entries of one seeded order of distinct points, so
+    two runs whose time bounds admit different n evaluate the same leading points (the reported
+    errors of the two runs compare on their common points)."""
+    import numpy as np
+    import bench
+    a = bench.oracle_sample_order(1_000_000)
+    b = bench.oracle_sample_order(1_000_000)
+    assert np.array_equal(a, b)
+    assert len(a) == bench.ORACLE_SAMPLE_CAP and len(np.unique(a)) == len(a)
+    assert a.min() >= 0 and a.max() < 1_000_000
+    small = bench.oracle_sample_order(500)
+    assert sorted(small.tolist()) == list(range(500))
+    assert not np.array_equal(a, bench.oracle_sample_order(1_000_000, seed=2))
