@@ -343,7 +343,8 @@ enum swense_direct_precision {
  *     d/dz S = |k| F); rows n and -n are paired (Y_-n = conj Y_n); per group of 8 row pairs and
  *     64 modes, a [256 points x 128] x [128 x 208] product (Re(T_n + T_-n), Im(T_n - T_-n) of
  *     u, v, w, dphi/dt at three orders, and eta) in split BF16 (hi.hi + hi.lo + lo.hi; the
- *     order-2 columns without their lo half), FP32 accumulation in tensor memory, then
+ *     order-2 columns without their lo half, so hi.lo spans the other 144), FP32 accumulation
+ *     in tensor memory, then
  *     Re sum_n Y_n (...) and sum_j (z - z0)^j in FP32. A tile pair whose max|k| x half-range of
  *     z exceeds 0.02 (the dropped third-order term would exceed 2e-6) is evaluated by the
  *     per-pair kernel instead. Accuracy: about 1e-5 of each field's maximum (bar 1e-3).
